@@ -1,0 +1,265 @@
+"""FP64 CPU oracle of the periphery fit step (test infrastructure).
+
+A plain, slow, obviously-correct implementation of what the GPU path
+computes, used only by the tests, the benchmark's CPU-baseline leg and the
+smoke check. The product path never imports it. It shares no code with the
+CUDA kernels: the C++ sources under ``oracle/src`` are compiled here into
+``oracle/_build/liboracle.so`` and called through ctypes.
+
+Conventions (Section 4.2 fits a 3DGS model; the splatting details follow
+standard 3DGS): see the header comments of each C++ file. Inputs are the
+float32 scene dicts of :mod:`scenes`; everything is computed in float64
+except the float32 values that decide integers (depth key, depth cull, tile
+rectangle), which are reproduced in float32 with a fixed operation order.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from pathlib import Path
+
+import numpy as np
+
+HERE = Path(__file__).resolve().parent
+SRC = HERE / "src"
+LIB = HERE / "_build" / "liboracle.so"
+
+SMOOTH = 1
+
+# Fields of the projected record (mirror of ProjField in src/oracle.h).
+PROJ_FIELDS = [
+    "visible", "depth32", "u", "v", "u32", "v32", "radius",
+    "conic_a", "conic_b", "conic_c", "cov_a", "cov_b", "cov_c", "opacity",
+    "r", "g", "b", "clamp_r", "clamp_g", "clamp_b",
+    "rect_x0", "rect_y0", "rect_x1", "rect_y1", "tiles", "near_boundary",
+]
+F = {name: i for i, name in enumerate(PROJ_FIELDS)}
+
+_lib = None
+
+
+def build(force: bool = False) -> Path:
+    """Compile the oracle (g++, OpenMP, no FP contraction)."""
+    sources = sorted(str(p) for p in SRC.glob("*.cpp"))
+    headers = sorted(SRC.glob("*.h"))
+    if LIB.exists() and not force:
+        newest = max(os.path.getmtime(p) for p in list(map(Path, sources)) + headers)
+        if os.path.getmtime(LIB) >= newest:
+            return LIB
+    LIB.parent.mkdir(exist_ok=True)
+    tmp = LIB.with_suffix(f".{os.getpid()}.tmp")
+    cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-fno-fast-math", "-o", str(tmp)] + sources
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(str(LIB))
+        P = ctypes.c_void_p
+        i, d, ll = ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+        L.oracle_proj_stride.restype = i
+        L.oracle_total_tiles.argtypes = [i, P, i]
+        L.oracle_total_tiles.restype = i
+        L.oracle_project.argtypes = [i, i, P, i, P, i, i, P]
+        L.oracle_bin.argtypes = [i, i, P, i, P, P, P, ll, P]
+        L.oracle_bin.restype = ll
+        L.oracle_render_fwd.argtypes = [i, i, P, i, P, P, P, P, i, P, P, P, P, P]
+        L.oracle_render_bwd.argtypes = [i, i, P, i, P, i, P, P, P, P, i, P, P, P, P, P]
+        L.oracle_loss.argtypes = [i, P, P, P, P, P, P, P, d, P, P, P]
+        L.oracle_loss.restype = d
+        L.oracle_adam.argtypes = [ll, P, P, P, P, P, d, d, d, i]
+        L.oracle_real_sh.argtypes = [i, P, P, P]
+        L.oracle_set_threads.argtypes = [i]
+        L.oracle_max_threads.restype = i
+        assert L.oracle_proj_stride() == len(PROJ_FIELDS)
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"], "array must be contiguous"
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def set_threads(n: int) -> None:
+    lib().oracle_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(lib().oracle_max_threads())
+
+
+# ---------------------------------------------------------------------------
+# packing of the shared scene dicts
+# ---------------------------------------------------------------------------
+
+def pack_gaussians(gs: dict) -> np.ndarray:
+    n = gs["means"].shape[0]
+    K = gs["sh"].shape[1]
+    out = np.empty((n, 11 + 3 * K), dtype=np.float64)
+    out[:, 0:3] = gs["means"]
+    out[:, 3:6] = gs["log_scales"]
+    out[:, 6:10] = gs["quats"]
+    out[:, 10] = gs["opacity_logits"]
+    out[:, 11:] = gs["sh"].reshape(n, 3 * K)
+    return out
+
+
+def unpack_gaussians(flat: np.ndarray, K: int) -> dict:
+    n = flat.shape[0]
+    return {
+        "means": flat[:, 0:3].copy(),
+        "log_scales": flat[:, 3:6].copy(),
+        "quats": flat[:, 6:10].copy(),
+        "opacity_logits": flat[:, 10].copy(),
+        "sh": flat[:, 11:].reshape(n, K, 3).copy(),
+    }
+
+
+def pack_cameras(cams: dict) -> np.ndarray:
+    V = len(cams["width"])
+    out = np.zeros((V, 24), dtype=np.float64)
+    out[:, 0:12] = cams["viewmat"].reshape(V, 12)
+    out[:, 12:15] = cams["campos"]
+    for j, k in enumerate(["fx", "fy", "cx", "cy", "near"]):
+        out[:, 15 + j] = cams[k]
+    out[:, 20] = cams["width"]
+    out[:, 21] = cams["height"]
+    return out
+
+
+def pixel_offsets(cams: dict) -> np.ndarray:
+    P = cams["width"].astype(np.int64) * cams["height"].astype(np.int64)
+    return np.concatenate([[0], np.cumsum(P)])
+
+
+def total_tiles(cams: dict, tile: int) -> int:
+    c = pack_cameras(cams)
+    return int(lib().oracle_total_tiles(len(c), _p(c), tile))
+
+
+# ---------------------------------------------------------------------------
+# stages
+# ---------------------------------------------------------------------------
+
+def project(gs: dict, cams: dict, tile: int = 16, smooth: bool = False) -> np.ndarray:
+    """(V, N, len(PROJ_FIELDS)) projected records."""
+    g = pack_gaussians(gs)
+    c = pack_cameras(cams)
+    n, K, V = g.shape[0], gs["sh"].shape[1], c.shape[0]
+    proj = np.zeros((V, n, len(PROJ_FIELDS)), dtype=np.float64)
+    lib().oracle_project(n, K, _p(g), V, _p(c), tile, SMOOTH if smooth else 0, _p(proj))
+    return proj
+
+
+def bin_tiles(proj: np.ndarray, cams: dict, tile: int = 16):
+    """Sorted keys (uint64), values (uint32 Gaussian index), ranges (T, 2)."""
+    c = pack_cameras(cams)
+    V, n = proj.shape[0], proj.shape[1]
+    T = total_tiles(cams, tile)
+    ranges = np.zeros((T, 2), dtype=np.uint32)
+    cap = int(proj[:, :, F["tiles"]].sum())
+    keys = np.zeros(max(cap, 1), dtype=np.uint64)
+    vals = np.zeros(max(cap, 1), dtype=np.uint32)
+    cnt = lib().oracle_bin(n, V, _p(c), tile, _p(np.ascontiguousarray(proj)), _p(keys), _p(vals), cap, _p(ranges))
+    assert cnt == cap
+    return keys[:cnt], vals[:cnt], ranges
+
+
+def render(gs: dict, cams: dict, bg: np.ndarray, tile: int = 16, smooth: bool = False) -> dict:
+    """Forward render. Images are packed per view: rgb (3 planes of H x W per
+    view), alpha / T_final / n_contrib / ambiguous (one plane per view)."""
+    proj = project(gs, cams, tile, smooth)
+    keys, vals, ranges = bin_tiles(proj, cams, tile)
+    c = pack_cameras(cams)
+    V, n = proj.shape[0], proj.shape[1]
+    P = int(pixel_offsets(cams)[-1])
+    rgb = np.zeros(3 * P)
+    alpha = np.zeros(P)
+    T = np.zeros(P)
+    nc = np.zeros(P, dtype=np.int32)
+    amb = np.zeros(P, dtype=np.uint8)
+    bgd = np.ascontiguousarray(bg, dtype=np.float64).reshape(V, 3)
+    vals_c = np.ascontiguousarray(vals) if vals.size else np.zeros(1, np.uint32)
+    lib().oracle_render_fwd(n, V, _p(c), tile, _p(proj), _p(vals_c), _p(ranges), _p(bgd),
+                            SMOOTH if smooth else 0, _p(rgb), _p(alpha), _p(T), _p(nc), _p(amb))
+    return {"rgb": rgb, "alpha": alpha, "T_final": T, "n_contrib": nc, "ambiguous": amb.astype(bool),
+            "proj": proj, "keys": keys, "vals": vals, "ranges": ranges}
+
+
+def render_bwd(gs: dict, cams: dict, bg: np.ndarray, dL_drgb: np.ndarray, dL_dalpha: np.ndarray,
+               tile: int = 16, smooth: bool = False, fwd: dict | None = None) -> dict:
+    """Adjoint of :func:`render`: gradients of sum(dL_drgb * rgb) +
+    sum(dL_dalpha * alpha) w.r.t. every parameter group."""
+    if fwd is None:
+        fwd = render(gs, cams, bg, tile, smooth)
+    proj = fwd["proj"]
+    g = pack_gaussians(gs)
+    c = pack_cameras(cams)
+    V, n = proj.shape[0], proj.shape[1]
+    K = gs["sh"].shape[1]
+    grad2d = np.zeros((V, n, 9))
+    grads = np.zeros_like(g)
+    amb = np.zeros((V, n), dtype=np.uint8)
+    bgd = np.ascontiguousarray(bg, dtype=np.float64).reshape(V, 3)
+    vals_c = np.ascontiguousarray(fwd["vals"]) if fwd["vals"].size else np.zeros(1, np.uint32)
+    lib().oracle_render_bwd(n, K, _p(g), V, _p(c), tile, _p(proj), _p(vals_c), _p(fwd["ranges"]), _p(bgd),
+                            SMOOTH if smooth else 0,
+                            _p(np.ascontiguousarray(dL_drgb, dtype=np.float64)),
+                            _p(np.ascontiguousarray(dL_dalpha, dtype=np.float64)),
+                            _p(grad2d), _p(grads), _p(amb))
+    return {"grads": unpack_gaussians(grads, K), "grads_flat": grads, "grad2d": grad2d,
+            "gauss_ambiguous": amb.astype(bool)}
+
+
+def loss(rgb, alpha, target_rgb, target_alpha, bg, cams: dict, lam: float = 0.2):
+    """(loss, dL/drgb, dL/dalpha, per-view SSIM) in the packed image layout."""
+    V = len(cams["width"])
+    W = np.ascontiguousarray(cams["width"], dtype=np.int32)
+    H = np.ascontiguousarray(cams["height"], dtype=np.int32)
+    f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+    rgb, alpha, target_rgb, target_alpha = f64(rgb), f64(alpha), f64(target_rgb), f64(target_alpha)
+    bgd = f64(bg).reshape(V, 3)
+    g_rgb = np.zeros_like(rgb)
+    g_a = np.zeros_like(alpha)
+    ssim = np.zeros(V)
+    L = lib().oracle_loss(V, _p(W), _p(H), _p(rgb), _p(alpha), _p(target_rgb), _p(target_alpha), _p(bgd),
+                          float(lam), _p(g_rgb), _p(g_a), _p(ssim))
+    return L, g_rgb, g_a, ssim
+
+
+def adam(p, g, m, v, lr, b1: float = 0.9, b2: float = 0.999, eps: float = 1e-15, step: int = 1):
+    """In-place Adam step on float64 arrays; lr is per element (broadcast)."""
+    n = p.size
+    lr_full = np.ascontiguousarray(np.broadcast_to(np.asarray(lr, dtype=np.float64), p.shape)).reshape(-1)
+    for a in (p, m, v):
+        assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    gg = np.ascontiguousarray(g, dtype=np.float64)
+    lib().oracle_adam(n, _p(p), _p(gg), _p(m), _p(v), _p(lr_full), b1, b2, eps, int(step))
+
+
+def real_sh(deg: int, dirs: np.ndarray):
+    """Real SH basis values (n, K) and gradients (n, K, 3) at directions."""
+    dirs = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 3)
+    K = (deg + 1) ** 2
+    Y = np.zeros((dirs.shape[0], K))
+    dY = np.zeros((dirs.shape[0], K, 3))
+    for i in range(dirs.shape[0]):
+        y = np.zeros(K)
+        dy = np.zeros(3 * K)
+        lib().oracle_real_sh(deg, _p(dirs[i].copy()), _p(y), _p(dy))
+        Y[i] = y
+        dY[i] = dy.reshape(K, 3)
+    return Y, dY
+
+
+def grad_groups_flat(K: int) -> dict:
+    """Column slices of the packed Gaussian record per parameter group."""
+    return {"means": slice(0, 3), "log_scales": slice(3, 6), "quats": slice(6, 10),
+            "opacity_logits": slice(10, 11), "sh": slice(11, 11 + 3 * K)}

@@ -1,0 +1,288 @@
+// Tile binning, front-to-back compositing and its adjoint.
+//
+// Section 4.2: the periphery is rendered and trained as a 3DGS model with
+// alpha training and randomised backgrounds. Per pixel, the Gaussians whose
+// tile rectangle covers the pixel's tile are taken in order of increasing
+// float32 depth (ties by Gaussian index) and composited front to back:
+//   power = -1/2 (a' dx^2 + c' dy^2) - b' dx dy,  skipped if power > 0
+//   alpha = min(0.99, o exp(power)),              skipped if alpha < 1/255
+//   stop before a Gaussian that would take T below 1e-4
+//   C = sum c_i alpha_i T_i + T_N bg,   A = 1 - T_N
+// n_contrib is one past the list position of the last blended Gaussian.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "oracle.h"
+
+namespace oracle {
+
+// Keys ((global tile id) << 32 | float32 depth bits) and values (Gaussian
+// index) of every (Gaussian, covered tile) pair, emitted view by view,
+// Gaussian by Gaussian, tiles row-major, then stably sorted by key; and the
+// [start, end) range of every tile. Returns the number of pairs.
+long long bin_tiles(int n, const std::vector<Camera>& cams, const double* proj, std::vector<uint64_t>& keys,
+                    std::vector<uint32_t>& vals, std::vector<uint32_t>& ranges) {
+    keys.clear();
+    vals.clear();
+    const int V = (int)cams.size();
+    for (int v = 0; v < V; ++v) {
+        const Camera& cam = cams[v];
+        for (int i = 0; i < n; ++i) {
+            const double* p = proj + ((size_t)v * n + i) * P_STRIDE;
+            if (p[P_VISIBLE] == 0.0 || p[P_TILES] == 0.0) continue;
+            float d = (float)p[P_DEPTH32];
+            uint32_t bits;
+            std::memcpy(&bits, &d, 4);
+            for (int ty = (int)p[P_RECT_Y0]; ty < (int)p[P_RECT_Y1]; ++ty)
+                for (int tx = (int)p[P_RECT_X0]; tx < (int)p[P_RECT_X1]; ++tx) {
+                    const uint64_t tile = (uint64_t)(cam.tile_offset + ty * cam.tiles_x + tx);
+                    keys.push_back((tile << 32) | bits);
+                    vals.push_back((uint32_t)i);
+                }
+        }
+    }
+    std::vector<size_t> order(keys.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return keys[a] < keys[b]; });
+    std::vector<uint64_t> k2(keys.size());
+    std::vector<uint32_t> v2(vals.size());
+    for (size_t j = 0; j < order.size(); ++j) {
+        k2[j] = keys[order[j]];
+        v2[j] = vals[order[j]];
+    }
+    keys.swap(k2);
+    vals.swap(v2);
+    const int T = total_tiles(cams);
+    ranges.assign(2 * (size_t)T, 0u);
+    for (size_t j = 0; j < keys.size(); ++j) {
+        const uint32_t t = (uint32_t)(keys[j] >> 32);
+        if (j == 0 || (uint32_t)(keys[j - 1] >> 32) != t) ranges[2 * t] = (uint32_t)j;
+        if (j + 1 == keys.size() || (uint32_t)(keys[j + 1] >> 32) != t) ranges[2 * t + 1] = (uint32_t)(j + 1);
+    }
+    return (long long)keys.size();
+}
+
+namespace {
+
+struct Blend {
+    int pos, gauss;
+    double alpha, T, G, dx, dy;
+    bool clamped;
+};
+
+struct Pixel {
+    double C[3], T;
+    int n_contrib;
+    bool ambiguous;
+    std::vector<Blend> blends;
+};
+
+// |x - thr| within a relative margin: float32 rounding on the GPU side could
+// take the other branch of this comparison.
+inline bool near_threshold(double x, double thr) { return std::fabs(x - thr) <= 2e-4 * thr; }
+
+void composite_pixel(int px, int py, const uint32_t* list, int count, const double* proj_v, int flags, Pixel& out) {
+    const bool smooth = flags & FLAG_SMOOTH;
+    double T = 1.0, C[3] = {0.0, 0.0, 0.0};
+    out.n_contrib = 0;
+    out.ambiguous = false;
+    out.blends.clear();
+    for (int j = 0; j < count; ++j) {
+        const int gi = (int)list[j];
+        const double* p = proj_v + (size_t)gi * P_STRIDE;
+        const double dx = px - p[P_U], dy = py - p[P_V];
+        const double power = -0.5 * (p[P_CONIC_A] * dx * dx + p[P_CONIC_C] * dy * dy) - p[P_CONIC_B] * dx * dy;
+        if (power > 0.0) continue;
+        const double G = std::exp(power);
+        const double a = p[P_OPACITY] * G;
+        const bool clamped = a > ALPHA_CLAMP;
+        const double alpha = clamped ? ALPHA_CLAMP : a;
+        if (near_threshold(a, ALPHA_CLAMP)) out.ambiguous = true;
+        if (!smooth) {
+            if (near_threshold(a, ALPHA_SKIP)) out.ambiguous = true;
+            if (alpha < ALPHA_SKIP) continue;
+        }
+        const double Tn = T * (1.0 - alpha);
+        if (!smooth) {
+            if (near_threshold(Tn, T_STOP)) out.ambiguous = true;
+            if (Tn < T_STOP) break;
+        }
+        for (int ch = 0; ch < 3; ++ch) C[ch] += p[P_R + ch] * alpha * T;
+        out.blends.push_back(Blend{j, gi, alpha, T, G, dx, dy, clamped});
+        T = Tn;
+        out.n_contrib = j + 1;
+    }
+    for (int ch = 0; ch < 3; ++ch) out.C[ch] = C[ch];
+    out.T = T;
+}
+
+// The pixel's list: its tile's sorted range (normal mode) or every visible
+// Gaussian of the view in depth order (smooth mode).
+struct ViewLists {
+    std::vector<uint32_t> all_sorted;
+};
+
+std::vector<uint32_t> depth_sorted_visible(int n, const double* proj_v) {
+    std::vector<uint32_t> idx;
+    for (int i = 0; i < n; ++i)
+        if (proj_v[(size_t)i * P_STRIDE + P_VISIBLE] != 0.0) idx.push_back((uint32_t)i);
+    std::stable_sort(idx.begin(), idx.end(), [&](uint32_t a, uint32_t b) {
+        float da = (float)proj_v[(size_t)a * P_STRIDE + P_DEPTH32];
+        float db = (float)proj_v[(size_t)b * P_STRIDE + P_DEPTH32];
+        return da < db;
+    });
+    return idx;
+}
+
+struct WorkItem {
+    int v, tx, ty;
+};
+
+std::vector<WorkItem> work_items(const std::vector<Camera>& cams) {
+    std::vector<WorkItem> w;
+    for (int v = 0; v < (int)cams.size(); ++v)
+        for (int ty = 0; ty < cams[v].tiles_y; ++ty)
+            for (int tx = 0; tx < cams[v].tiles_x; ++tx) w.push_back(WorkItem{v, tx, ty});
+    return w;
+}
+
+}  // namespace
+
+void render_fwd(int n, const std::vector<Camera>& cams, int tile, const double* proj, const uint32_t* vals,
+                const uint32_t* ranges, const double* bg, int flags, double* rgb, double* alpha, double* T_final,
+                int32_t* n_contrib, uint8_t* ambiguous) {
+    const int V = (int)cams.size();
+    std::vector<std::vector<uint32_t>> sorted(V);
+    if (flags & FLAG_SMOOTH)
+        for (int v = 0; v < V; ++v) sorted[v] = depth_sorted_visible(n, proj + (size_t)v * n * P_STRIDE);
+    const std::vector<WorkItem> items = work_items(cams);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (long long w = 0; w < (long long)items.size(); ++w) {
+        const WorkItem it = items[w];
+        const Camera& cam = cams[it.v];
+        const double* proj_v = proj + (size_t)it.v * n * P_STRIDE;
+        const uint32_t* list;
+        int count;
+        if (flags & FLAG_SMOOTH) {
+            list = sorted[it.v].data();
+            count = (int)sorted[it.v].size();
+        } else {
+            const int t = cam.tile_offset + it.ty * cam.tiles_x + it.tx;
+            list = vals + ranges[2 * t];
+            count = (int)(ranges[2 * t + 1] - ranges[2 * t]);
+        }
+        Pixel px;
+        for (int py = it.ty * tile; py < std::min((it.ty + 1) * tile, cam.H); ++py)
+            for (int pxx = it.tx * tile; pxx < std::min((it.tx + 1) * tile, cam.W); ++pxx) {
+                composite_pixel(pxx, py, list, count, proj_v, flags, px);
+                const long long pix = cam.pixel_offset + (long long)py * cam.W + pxx;
+                const long long plane = (long long)cam.W * cam.H;
+                for (int ch = 0; ch < 3; ++ch)
+                    rgb[3 * cam.pixel_offset + ch * plane + (long long)py * cam.W + pxx] =
+                        px.C[ch] + px.T * bg[3 * it.v + ch];
+                alpha[pix] = 1.0 - px.T;
+                T_final[pix] = px.T;
+                n_contrib[pix] = px.n_contrib;
+                ambiguous[pix] = px.ambiguous ? 1 : 0;
+            }
+    }
+}
+
+void project_bwd_one(const double* g, int K, const Camera& cam, const double g2[9], double* gout);
+
+// Adjoint of render_fwd followed by the projection adjoint. dL_drgb and
+// dL_dalpha are the upstream gradients in the image layout; grad2d receives
+// dL/d(u, v, a', b', c', opacity, r, g, b) per (view, Gaussian) and grads the
+// sum over views of dL/d(parameters). gauss_ambiguous marks (view, Gaussian)
+// pairs blended at a pixel with a near-threshold decision.
+void render_bwd(int n, int K, const double* gauss, const std::vector<Camera>& cams, int tile, const double* proj,
+                const uint32_t* vals, const uint32_t* ranges, const double* bg, int flags, const double* dL_drgb,
+                const double* dL_dalpha, double* grad2d, double* grads, uint8_t* gauss_ambiguous) {
+    const int V = (int)cams.size();
+    std::memset(grad2d, 0, sizeof(double) * 9 * (size_t)V * n);
+    std::memset(gauss_ambiguous, 0, (size_t)V * n);
+    std::vector<std::vector<uint32_t>> sorted(V);
+    if (flags & FLAG_SMOOTH)
+        for (int v = 0; v < V; ++v) sorted[v] = depth_sorted_visible(n, proj + (size_t)v * n * P_STRIDE);
+    const std::vector<WorkItem> items = work_items(cams);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (long long w = 0; w < (long long)items.size(); ++w) {
+        const WorkItem it = items[w];
+        const Camera& cam = cams[it.v];
+        const double* proj_v = proj + (size_t)it.v * n * P_STRIDE;
+        double* g2v = grad2d + (size_t)it.v * n * 9;
+        const uint32_t* list;
+        int count;
+        if (flags & FLAG_SMOOTH) {
+            list = sorted[it.v].data();
+            count = (int)sorted[it.v].size();
+        } else {
+            const int t = cam.tile_offset + it.ty * cam.tiles_x + it.tx;
+            list = vals + ranges[2 * t];
+            count = (int)(ranges[2 * t + 1] - ranges[2 * t]);
+        }
+        Pixel px;
+        const long long plane = (long long)cam.W * cam.H;
+        for (int py = it.ty * tile; py < std::min((it.ty + 1) * tile, cam.H); ++py)
+            for (int pxx = it.tx * tile; pxx < std::min((it.tx + 1) * tile, cam.W); ++pxx) {
+                composite_pixel(pxx, py, list, count, proj_v, flags, px);
+                const long long pix = cam.pixel_offset + (long long)py * cam.W + pxx;
+                double dC[3];
+                for (int ch = 0; ch < 3; ++ch)
+                    dC[ch] = dL_drgb[3 * cam.pixel_offset + ch * plane + (long long)py * cam.W + pxx];
+                const double dA = dL_dalpha[pix];
+                const double TN = px.T;
+                double S[3] = {0.0, 0.0, 0.0};  // sum over later Gaussians of c alpha T
+                for (int b = (int)px.blends.size() - 1; b >= 0; --b) {
+                    const Blend& e = px.blends[b];
+                    const double* p = proj_v + (size_t)e.gauss * P_STRIDE;
+                    double dalpha = dA * TN / (1.0 - e.alpha);
+                    double* out = g2v + (size_t)e.gauss * 9;
+                    for (int ch = 0; ch < 3; ++ch) {
+                        const double c = p[P_R + ch];
+                        dalpha += dC[ch] * (e.T * c - (S[ch] + TN * bg[3 * it.v + ch]) / (1.0 - e.alpha));
+#pragma omp atomic
+                        out[6 + ch] += dC[ch] * e.alpha * e.T;
+                    }
+                    for (int ch = 0; ch < 3; ++ch) S[ch] += p[P_R + ch] * e.alpha * e.T;
+                    if (e.clamped) continue;  // alpha = 0.99 does not depend on o or power
+                    const double dpower = dalpha * e.alpha;
+                    const double gu = dpower * (p[P_CONIC_A] * e.dx + p[P_CONIC_B] * e.dy);
+                    const double gv = dpower * (p[P_CONIC_C] * e.dy + p[P_CONIC_B] * e.dx);
+                    const double ga = dpower * (-0.5 * e.dx * e.dx);
+                    const double gb = dpower * (-e.dx * e.dy);
+                    const double gc = dpower * (-0.5 * e.dy * e.dy);
+                    const double go = dalpha * e.G;
+#pragma omp atomic
+                    out[0] += gu;
+#pragma omp atomic
+                    out[1] += gv;
+#pragma omp atomic
+                    out[2] += ga;
+#pragma omp atomic
+                    out[3] += gb;
+#pragma omp atomic
+                    out[4] += gc;
+#pragma omp atomic
+                    out[5] += go;
+                }
+                if (px.ambiguous) {
+                    for (const Blend& e : px.blends) gauss_ambiguous[(size_t)it.v * n + e.gauss] = 1;
+                }
+            }
+    }
+    const int stride = gauss_stride(K);
+    std::memset(grads, 0, sizeof(double) * (size_t)n * stride);
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < n; ++i)
+        for (int v = 0; v < V; ++v) {
+            const double* p = proj + ((size_t)v * n + i) * P_STRIDE;
+            if (p[P_VISIBLE] == 0.0) continue;
+            project_bwd_one(gauss + (size_t)i * stride, K, cams[v], grad2d + ((size_t)v * n + i) * 9,
+                            grads + (size_t)i * stride);
+        }
+}
+
+}  // namespace oracle
