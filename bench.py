@@ -1,0 +1,402 @@
+"""Throughput of the Gaussian-Splatting periphery fit step on GB300.
+
+Workload: 1,000,000 Gaussians (SH degree 3) seeded from a procedural
+512x512x400 CT volume through a transfer function, fitted against a batch of
+16 views of uneven size per iteration (two 1920^2 stereo periphery frames and
+14 foveal crops of 256..768 px at 512 px / 20 degrees), targets rendered from
+a second seeded Gaussian set, random backgrounds per view and iteration.
+One step = project + bin/sort + render + loss + adjoint + Adam over the whole
+batch, replayed as one CUDA graph; float32 throughout.
+
+Also measured in the same run: per-stage durations (CUDA events), the
+end-to-end rate through the C ABI with the step's target images copied from
+pinned host memory every step, the plain float32 single-view form (one view
+per launch, no graph), and the FP64 CPU oracle on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import scenes  # noqa: E402
+
+METRIC = "fit iters/s (fwd+bwd+Adam), 1M Gaussians, batched views; vs plain FP32 form"
+WORKLOAD = ("batched periphery: 1M Gaussians SH3 from a 512x512x400 CT volume, 16 views/iteration "
+            "(2x1920^2 stereo periphery + 14 foveal crops 256..768 px), fp32")
+HBM_FALLBACK_GBS = 6800.0
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured", "sm_max_mhz": float(d.get("sm_max_mhz", 2070))}
+    return {"hbm_gbs": HBM_FALLBACK_GBS, "source": "fallback", "sm_max_mhz": 2070.0}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.reader = threading.Thread(target=self._read, daemon=True)
+            self.reader.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.reader.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+
+def build_state(seed: int = 0):
+    import torch
+    from paper_2601_22026_gb300.fit import FitState, boosted_lr
+    sc = scenes.batched_periphery_scene(seed)
+    cams = sc["cameras"]
+    V = len(cams["width"])
+    tgt = FitState(sc["target_gaussians"], cams, bg=np.zeros((V, 3), np.float32))
+    tgt.forward()
+    torch.cuda.synchronize()
+    st = FitState(sc["gaussians"], cams, bg=sc["bg"], lr=boosted_lr())
+    st.target_rgb.copy_(tgt.rgb)
+    st.target_alpha.copy_(tgt.alpha)
+    del tgt
+    torch.cuda.empty_cache()
+    return sc, st
+
+
+def stage_bytes(st, n_inst: int, n_vis: int, n_passes: int) -> dict:
+    """Algorithmic HBM bytes per launch of the memory-bound stages."""
+    n, V, P, npl = st.n, st.V, st.P, st.n_planes
+    return {
+        # read every parameter plane once; write a 20-byte centre record + tile
+        # count per (view, Gaussian) and 32 more bytes for binned records
+        "project": n * npl * 16 + V * n * 20 + n_vis * 32,
+        # tile counts read twice, binned centres once; pairs emitted (12 B),
+        # histogram read (8 B), n_passes x (read + write 12 B), range scan (8 B)
+        "bin_sort": V * n * 8 + n_vis * 16 + n_inst * (12 + 8 + 24 * n_passes + 8),
+        # render colour + alpha, target colour + alpha read; gradients written
+        "loss": P * 4 * 12,
+        # p, g, m, v read; p, m, v written: 28 bytes per parameter (float4 planes)
+        "adam": npl * n * 16 * 7,
+    }
+
+
+def time_stages(st, reps: int) -> dict:
+    import torch
+    evs = {k: [] for k in st.STAGES}
+    for _ in range(reps):
+        marks = []
+        for name in st.STAGES:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            getattr(st, name)()
+            b.record()
+            marks.append((name, a, b))
+        torch.cuda.synchronize()
+        for name, a, b in marks:
+            evs[name].append(a.elapsed_time(b))
+    return {k: float(np.mean(v)) for k, v in evs.items()}
+
+
+def plain_single_view_rate(sc, st, steps: int) -> float:
+    """The plain float32 single-view form: the same kernels with one view per
+    launch sequence, no graph; returns 16-view batches per second."""
+    import torch
+    from paper_2601_22026_gb300.fit import FitState
+    cams = sc["cameras"]
+    V = len(cams["width"])
+    per_view = []
+    off = 0
+    for v in range(V):
+        c1 = scenes.camera_subset(cams, [v])
+        s1 = FitState({k: x[:1] for k, x in sc["gaussians"].items()}, c1, bg=sc["bg"][v:v + 1], capacity=16)
+        # share the Gaussian parameters and optimiser state of the batched state
+        s1.n = st.n
+        s1.params, s1.grads, s1.m, s1.v, s1.step_count = st.params, st.grads, st.m, st.v, st.step_count
+        s1.lr = st.lr
+        s1.set_cameras(c1, bg=sc["bg"][v:v + 1])
+        P = int(cams["width"][v]) * int(cams["height"][v])
+        s1.target_rgb.copy_(st.target_rgb[3 * off:3 * (off + P)])
+        s1.target_alpha.copy_(st.target_alpha[off:off + P])
+        s1.capacity = 0
+        s1.ensure_capacity()
+        per_view.append(s1)
+        off += P
+    for s1 in per_view:  # warm-up
+        s1.step()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        for s1 in per_view:
+            s1.step()
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    del per_view
+    torch.cuda.empty_cache()
+    return 1000.0 / ms
+
+
+def e2e_rate(st, host_rgb, host_alpha, host_bg, steps: int) -> dict:
+    """Same step through the C ABI with the step's inputs (target images,
+    backgrounds) copied from pinned host memory every step and the loss read
+    back to the host every step."""
+    import torch
+    loss_host = torch.empty(1, dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(steps):
+        st.target_rgb.copy_(host_rgb, non_blocking=True)
+        st.target_alpha.copy_(host_alpha, non_blocking=True)
+        st.bg.copy_(host_bg[k % host_bg.shape[0]], non_blocking=True)
+        st.replay()
+        loss_host.copy_(st.loss_out, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    dt = time.perf_counter() - t0
+    h2d = (host_rgb.numel() + host_alpha.numel()) * 4 + host_bg[0].numel() * 4
+    return {"value": steps / dt, "unit": "iters/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 4}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample
+# ---------------------------------------------------------------------------
+
+SAMPLE_VIEWS = [2, 3, 4, 5]  # four foveal crops of the 16-view batch
+
+
+def oracle_sample(sc, seconds_cap: float = 30.0) -> dict:
+    """One full fit iteration of the FP64 oracle (project, bin, composite,
+    loss, adjoint, Adam) over all 1M Gaussians and a subset of the views;
+    extrapolated to the whole batch by pixel count."""
+    import oracle
+    oracle.build()
+    cams = sc["cameras"]
+    sub = scenes.camera_subset(cams, SAMPLE_VIEWS)
+    bg = sc["bg"][SAMPLE_VIEWS]
+    gs = sc["gaussians"]
+    P_sub = scenes.num_pixels(sub)
+    P_all = scenes.num_pixels(cams)
+    g = scenes.rng(5)
+    tr = g.uniform(0, 1, 3 * P_sub)
+    ta = g.uniform(0, 1, P_sub)
+    t0 = time.perf_counter()
+    fwd = oracle.render(gs, sub, bg)
+    L, grgb, ga, _ = oracle.loss(fwd["rgb"], fwd["alpha"], tr, ta, bg, sub)
+    b = oracle.render_bwd(gs, sub, bg, grgb, ga, fwd=fwd)
+    flat = oracle.pack_gaussians(gs)
+    m = np.zeros_like(flat)
+    v = np.zeros_like(flat)
+    oracle.adam(flat, b["grads_flat"], m, v, 1e-3)
+    dt = time.perf_counter() - t0
+    est = dt * P_all / P_sub
+    return {"value": 1.0 / est, "unit": "iters/s", "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": (f"one full FP64 iteration over all {scenes.num_gaussians(gs)} Gaussians and views "
+                       f"{SAMPLE_VIEWS} ({P_sub} px of {P_all}); {dt:.1f} s, scaled by pixel count"),
+            "sample_seconds": dt}
+
+
+def run_reference(args) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sc = scenes.batched_periphery_scene(0)
+    vals = []
+    for _ in range(max(1, args.warmup)):
+        oracle_sample(sc)
+    for _ in range(max(1, args.steps)):
+        vals.append(oracle_sample(sc))
+    v = float(np.mean([x["value"] for x in vals]))
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "iters/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD + " (FP64 CPU oracle, bounded sample per step)"},
+           "cpu_baseline": {"value": v, "unit": "iters/s", "cores": vals[0]["cores"], "kind": "oracle",
+                            "sample": vals[0]["sample"]},
+           "e2e": {"value": v, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+# ---------------------------------------------------------------------------
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
+    ap.add_argument("--no-plain", action="store_true", help="skip the single-view comparison")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import paper_2601_22026_gb300 as pkg
+    pkg.build()
+
+    sc, st = build_state(0)
+    V = st.V
+    bg_table = torch.from_numpy(scenes.backgrounds(V, 3, n_steps=args.warmup + args.steps)).cuda()
+    st.capture()
+    for k in range(args.warmup):
+        st.bg.copy_(bg_table[k])
+        st.replay()
+    torch.cuda.synchronize()
+    status = st.check_status()
+    if status != 0:
+        raise RuntimeError(f"device status {status} after warm-up")
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for k in range(args.steps):
+        st.bg.copy_(bg_table[args.warmup + k])
+        st.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    ms_total = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms_total], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_per_step = ms_total / args.steps
+    value = world * 1000.0 / ms_per_step
+    status = st.check_status()
+    if status != 0:
+        raise RuntimeError(f"device status {status} after the timed steps")
+    loss_now = float(st.loss_out.item())
+    n_inst = int(st.n_instances.item())
+    n_vis = int((st.proj.tiles > 0).sum().item())
+
+    # per-stage durations (eager launches bracketed by events) and roofline
+    stage_ms = time_stages(st, reps=max(5, min(30, args.steps // 10)))
+    from paper_2601_22026_gb300.fit import FitState  # noqa: F401
+    n_passes = 4 + (int(np.ceil(np.log2(max(2, st.T)))) + 7) // 8
+    sb = stage_bytes(st, n_inst, n_vis, n_passes)
+    peaks = measured_peaks()
+    hbm_stages = {k: sb[k] / (stage_ms[k] * 1e-3) / 1e9 for k in sb}
+    dominant = max(stage_ms, key=stage_ms.get)
+    launches_per_step = 1 + (5 + n_passes) + 1 + 2 + 2 + 2
+    if dominant in sb:
+        roof = {"kernel": dominant, "bound": "hbm", "achieved": hbm_stages[dominant], "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": hbm_stages[dominant] / peaks["hbm_gbs"], "traffic": None,
+                "peak_source": peaks["source"]}
+    else:
+        # ALU-bound compositing stages: report the HBM-bound stage fractions
+        # alongside (their FLOP accounting is in the profiles)
+        roof = {"kernel": dominant, "bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s",
+                "frac": None, "traffic": None}
+    roof["stages_hbm_frac"] = {k: round(hbm_stages[k] / peaks["hbm_gbs"], 4) for k in hbm_stages}
+
+    out = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "gaussians": st.n, "views": V, "pixels": st.P, "tiles": st.T,
+                      "pairs_per_step": n_inst, "parallelism": "replicas" if world > 1 else "single",
+                      "l2": "working set > L2 (no flush)", "graph": True, "loss_last": loss_now},
+           "gpu_launches": launches_per_step * args.steps,
+           "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+           "roofline": roof, "clocks": clk}
+
+    if rank == 0 and not args.no_plain:
+        plain = plain_single_view_rate(sc, st, steps=max(3, min(20, args.steps // 20)))
+        out["plain_fp32_single_view"] = {"value": plain, "unit": "16-view batches/s",
+                                         "speedup_of_batched": value / world / plain}
+    if rank == 0:
+        host_rgb = st.target_rgb.cpu().pin_memory()
+        host_alpha = st.target_alpha.cpu().pin_memory()
+        host_bg = bg_table.cpu().pin_memory()
+        out["e2e"] = e2e_rate(st, host_rgb, host_alpha, host_bg, steps=max(5, min(50, args.steps // 5)))
+        out["e2e"]["value"] *= world
+    if rank == 0 and world == 1 and not args.no_cpu:
+        out["cpu_baseline"] = oracle_sample(sc)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

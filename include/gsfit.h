@@ -1,0 +1,272 @@
+/*
+ * gsfit.h -- C ABI of the Gaussian-Splatting periphery fit step (sm_103a).
+ *
+ * The peripheral model of the paper (Section 4.2) is a 3D Gaussian Splatting
+ * model fitted to posed path-traced views with alpha supervision and
+ * randomised backgrounds; one fit iteration is
+ *
+ *   gsfit_project     EWA projection of every Gaussian into every view, with
+ *                     spherical-harmonic colour
+ *   gsfit_bin_sort    (tile | depth) key generation, radix sort, tile ranges
+ *   gsfit_render_fwd  front-to-back alpha compositing per pixel
+ *   gsfit_loss        L1 + 0.2 D-SSIM on colour + L1 on alpha, and dL/dimage
+ *   gsfit_render_bwd  back-to-front adjoint of the compositing, then the
+ *                     adjoint of the projection, summed over views
+ *   gsfit_adam_step   Adam update of all parameters
+ *
+ * The paper does not write the splatting math out; every convention is that
+ * of standard 3DGS (Kerbl et al. 2023, EWA splatting after Zwicker et al.
+ * 2001) and is stated at each call below.
+ *
+ * Conventions shared by every call
+ *   - All data pointers are DEVICE pointers owned by the caller unless the
+ *     argument says "host". The library allocates nothing; scratch space is
+ *     passed in as a workspace whose size a *_workspace_size query returns.
+ *   - Every call is asynchronous on the given stream and performs no
+ *     host/device synchronisation, so a whole iteration can be captured in a
+ *     CUDA graph. Return values report argument errors and launch errors
+ *     (GSFIT_ERR_INVALID_ARG, GSFIT_ERR_CUDA) only; conditions found on the
+ *     device (instance capacity exceeded, a bounded wait that ran out) are
+ *     written to the caller's int32 status word, read after a synchronise.
+ *   - Sizes: n Gaussians (n < 2^31), V views (1 <= V <= GSFIT_MAX_VIEWS),
+ *     tile size B = 16 pixels.
+ *
+ * Data layouts
+ *   Gaussian parameters (and their gradients, and the Adam moments) are
+ *   float4 planes: plane p of Gaussian i is at float4 index p * n + i.
+ *     plane 0          (mean x, mean y, mean z, opacity logit)
+ *     plane 1          rotation quaternion (w, x, y, z), normalised on use
+ *     plane 2          (log scale x, log scale y, log scale z, 0)
+ *     planes 3 ..      SH coefficients k = 0 .. K-1 (K = (degree+1)^2),
+ *                      flattened as k0.r k0.g k0.b k1.r ..., four per plane,
+ *                      zero padded: gsfit_num_planes(degree) planes in all.
+ *   Images of a view batch are packed view after view. View v starts at
+ *   pixel pixel_offset_v (gsfit_camera.pixel_offset); colour images hold
+ *   three H x W planes (r, g, b) per view starting at 3 * pixel_offset_v;
+ *   single-channel images (alpha, T_final, n_contrib) one plane per view.
+ *   Pixel (x, y) of a view samples the image plane at integer (x, y); a
+ *   centred camera has cx = W/2 - 0.5, cy = H/2 - 0.5.
+ */
+#ifndef GSFIT_H_
+#define GSFIT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GSFIT_ABI_VERSION 1
+#define GSFIT_MAX_VIEWS 256
+#define GSFIT_TILE 16
+
+/* Return and status codes. */
+#define GSFIT_OK 0
+#define GSFIT_ERR_INVALID_ARG (-1)
+#define GSFIT_ERR_CAPACITY (-2)  /* more (Gaussian, tile) pairs than capacity  */
+#define GSFIT_ERR_CUDA (-3)      /* a CUDA launch or runtime call failed        */
+#define GSFIT_ERR_TIMEOUT (-4)   /* a bounded device-side wait ran out          */
+
+/*
+ * One pinhole camera: 128 bytes, identical on host and device.
+ * viewmat is world -> camera, row-major 3 x 4 [R | t]; camera axes are
+ * +x right, +y down, +z forward, so p_cam = R p_world + t. campos is the
+ * camera centre in world space (-R^T t), used for the SH view direction.
+ * A Gaussian is culled in a view when its float32 depth is <= near_plane
+ * (3DGS uses 0.2). tile_offset is the global id of the view's first tile and
+ * pixel_offset its first pixel in the packed images; gsfit_camera_layout
+ * fills both for a batch.
+ */
+typedef struct gsfit_camera {
+    float viewmat[12];
+    float campos[3];
+    float fx, fy, cx, cy;
+    float near_plane;
+    int32_t width, height;
+    int32_t tile_offset;
+    int32_t pixel_offset;
+    int32_t reserved[8];
+} gsfit_camera;
+
+/* A Gaussian set (device, float4 planes as described above). */
+typedef struct gsfit_gaussians {
+    const float* params;  /* gsfit_num_planes(sh_degree) * n float4 */
+    int32_t n;
+    int32_t sh_degree;    /* 0 .. 3 */
+} gsfit_gaussians;
+
+/*
+ * Per-(view, Gaussian) projected records, index r = v * n + i (device).
+ *   xyd[r]     float4 (u, v, depth, radius): pixel-space centre, float32
+ *              camera-space depth, integer pixel radius ceil(3 sqrt(lambda_max))
+ *              stored as a float; radius 0 marks a culled record.
+ *   conic[r]   float4 (a', b', c', opacity): inverse 2D covariance and the
+ *              activated opacity; power = -1/2 (a' dx^2 + c' dy^2) - b' dx dy.
+ *   rgb[r]     float4 (r, g, b, mask): colour after the clamp at 0; mask holds
+ *              (clamped r) + 2 (clamped g) + 4 (clamped b) as a float.
+ *   tiles[r]   number of tiles the record's rectangle covers (0 if culled).
+ */
+typedef struct gsfit_proj {
+    float* xyd;
+    float* conic;
+    float* rgb;
+    uint32_t* tiles;
+} gsfit_proj;
+
+/* Number of float4 parameter planes for an SH degree (3 + ceil(3K/4)). */
+int gsfit_num_planes(int sh_degree);
+
+/* ABI version, for a loader to check against GSFIT_ABI_VERSION. */
+int gsfit_abi_version(void);
+
+/* Human-readable name of a return / status code (static string). */
+const char* gsfit_status_string(int code);
+
+/*
+ * Host helper: fills tile_offset and pixel_offset of V HOST cameras for tile
+ * size `tile`, laying views out in order, and returns the batch totals.
+ * Returns GSFIT_ERR_INVALID_ARG for a non-positive size or V out of range.
+ */
+int gsfit_camera_layout(gsfit_camera* cams_host, int n_views, int tile, int32_t* total_tiles,
+                        int64_t* total_pixels);
+
+/*
+ * gsfit_project -- EWA projection with SH colour (3DGS forward projection).
+ *   Per (view v, Gaussian i): s = exp(log_scale), q normalised, opacity =
+ *   sigmoid(logit), Sigma = R(q) diag(s^2) R(q)^T; t = R_v mu + t_v; culled
+ *   if t_z <= near. Sigma' = J R_v Sigma R_v^T J^T + 0.3 I with the EWA
+ *   Jacobian J at t (t_x/t_z, t_y/t_z clamped to +-1.3 tan(fov/2) inside J);
+ *   conic = Sigma'^-1 (culled if det <= 0); radius = ceil(3 sqrt(lambda_max)),
+ *   lambda_max = m + sqrt(max(0.1, m^2 - det)), m = (a + c)/2; centre
+ *   u = fx t_x/t_z + cx, v = fy t_y/t_z + cy; tile rectangle
+ *   [floor((u-r)/B), floor((u+r+B-1)/B)) in x (likewise y) clamped to the
+ *   view; colour = max(0, sum_k Y_k(dir) k_k + 0.5), dir = normalise(mu -
+ *   campos), real SH with Condon-Shortley phase, m = -l..l per band.
+ *   Depth, centre and rectangle are computed with a fixed order of correctly
+ *   rounded float32 operations (no contraction) so that keys are
+ *   reproducible.
+ * Arguments: g (device params), cams (device, n_views records laid out by
+ *   gsfit_camera_layout), out (device arrays of n_views * n records each).
+ * Errors: GSFIT_ERR_INVALID_ARG for null pointers, n <= 0, bad degree or V;
+ *   GSFIT_ERR_CUDA if the launch fails.
+ */
+int gsfit_project(const gsfit_gaussians* g, const gsfit_camera* cams, int32_t n_views, gsfit_proj* out,
+                  cudaStream_t stream);
+
+/*
+ * Workspace bytes gsfit_bin_sort needs for n_views * n projected records,
+ * `capacity` (Gaussian, tile) pairs and `total_tiles` tiles.
+ */
+size_t gsfit_bin_sort_workspace_size(int64_t n_records, int64_t capacity, int32_t total_tiles);
+
+/*
+ * gsfit_bin_sort -- tile binning of the projected records (3DGS).
+ *   Exclusive scan of tiles[]; for every record with tiles > 0 and every
+ *   tile (row-major) of its rectangle, one pair key = (global tile id << 32)
+ *   | float32 bits of depth, value = Gaussian index i, emitted in record
+ *   order; a stable LSD radix sort of the pairs by key (the order is the
+ *   unique order by (key, view, Gaussian index)); and per global tile t the
+ *   range ranges[2t], ranges[2t+1] = [first, last+1) of its pairs, [0, 0)
+ *   if empty.
+ * Arguments: proj/cams as for gsfit_project (n Gaussians, n_views views,
+ *   total_tiles = sum over views of tiles); ws/ws_bytes: device workspace of
+ *   at least gsfit_bin_sort_workspace_size bytes (contents need not be
+ *   initialised); keys (uint64) and vals (uint32): device, `capacity`
+ *   entries each, sorted output; n_instances: device uint32, receives the
+ *   number of pairs (also when it exceeds capacity); ranges: device uint32,
+ *   2 * total_tiles entries; status: device int32, set to GSFIT_ERR_CAPACITY
+ *   when the pairs exceed capacity (nothing is then emitted and every range
+ *   is empty) and to GSFIT_ERR_TIMEOUT if a bounded wait of the sort ran out;
+ *   it is not cleared by this call.
+ * Errors: GSFIT_ERR_INVALID_ARG (null pointers, sizes, workspace too small,
+ *   capacity >= 2^30), GSFIT_ERR_CUDA.
+ */
+int gsfit_bin_sort(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_views, int32_t n,
+                   int32_t total_tiles, void* ws, size_t ws_bytes, uint64_t* keys, uint32_t* vals,
+                   int64_t capacity, uint32_t* n_instances, uint32_t* ranges, int32_t* status,
+                   cudaStream_t stream);
+
+/*
+ * gsfit_render_fwd -- front-to-back compositing (3DGS, with the alpha output
+ * used for alpha supervision, Section 4.2).
+ *   For each pixel, over its tile's sorted pairs: power as in gsfit_proj,
+ *   skipped if power > 0; alpha = min(0.99, opacity exp(power)), skipped if
+ *   alpha < 1/255; stop before a Gaussian that would take T below 1e-4;
+ *   C = sum c alpha T + T_N bg_v, A = 1 - T_N. n_contrib is one past the
+ *   list position (within the tile's range) of the last blended Gaussian.
+ * Arguments: bg: device float, 3 per view; rgb: 3 * total_pixels floats,
+ *   alpha, T_final: total_pixels floats, n_contrib: total_pixels uint32
+ *   (device). vals/ranges from gsfit_bin_sort.
+ * Errors: GSFIT_ERR_INVALID_ARG, GSFIT_ERR_CUDA.
+ */
+int gsfit_render_fwd(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_views, int32_t n,
+                     int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges, const float* bg,
+                     float* rgb, float* alpha, float* T_final, uint32_t* n_contrib, cudaStream_t stream);
+
+/*
+ * gsfit_loss -- photometric loss of a view batch and its gradient.
+ *   Target colour y = target_rgb + (1 - target_alpha) bg_v (premultiplied
+ *   target composited over the render's background). Per view
+ *   L_v = (1 - lambda) mean|x - y| + lambda (1 - mean SSIM(x, y))
+ *         + mean|A - target_alpha|,  L = (1/V) sum_v L_v,
+ *   SSIM with an 11 x 11 Gaussian window (sigma 1.5), zero padding, C1 =
+ *   0.01^2, C2 = 0.03^2, averaged over channels and pixels (3DGS). Writes
+ *   dL/drgb and dL/dalpha (the L1 subgradient at 0 is 0) and, if loss_out is
+ *   not null, the scalar loss (device float).
+ * Arguments: images in the packed layout (device); ws: device workspace of
+ *   gsfit_loss_workspace_size(n_views) bytes.
+ * Errors: GSFIT_ERR_INVALID_ARG, GSFIT_ERR_CUDA.
+ */
+size_t gsfit_loss_workspace_size(int32_t n_views);
+int gsfit_loss(const gsfit_camera* cams, int32_t n_views, const float* rgb, const float* alpha,
+               const float* target_rgb, const float* target_alpha, const float* bg, float lambda,
+               float* dL_drgb, float* dL_dalpha, float* loss_out, void* ws, size_t ws_bytes,
+               cudaStream_t stream);
+
+/*
+ * gsfit_render_bwd -- adjoint of gsfit_render_fwd and gsfit_project.
+ *   Per pixel, back to front from n_contrib - 1, recovering T_i = T_{i+1} /
+ *   (1 - alpha_i) from T_final (no per-(pixel, Gaussian) state is stored):
+ *   dC/dc_i = alpha_i T_i; dC/dalpha_i = T_i c_i - (S_i + T_N bg) / (1 -
+ *   alpha_i) with S_i the colour composited behind i; dA/dalpha_i = T_N /
+ *   (1 - alpha_i); dalpha/d(opacity, power) = 0 where the 0.99 clamp is
+ *   active. Per-(view, Gaussian) gradients of (u, v, conic, opacity, rgb) are
+ *   reduced per warp and accumulated with atomics in grad2d, then chained
+ *   through the projection (zero derivative where the frustum guard or the
+ *   colour clamp is active) and summed over views into `grads`.
+ * Arguments: g: the Gaussians that were projected; dL_drgb/dL_dalpha in the
+ *   image layout; grad2d: device workspace of 12 floats per record
+ *   (n_views * n * 48 bytes) that must be zero before the first call; this
+ *   call leaves it zero again. grads: device, same layout as the parameters,
+ *   fully overwritten (no zeroing needed).
+ * Errors: GSFIT_ERR_INVALID_ARG, GSFIT_ERR_CUDA.
+ */
+int gsfit_render_bwd(const gsfit_gaussians* g, const gsfit_proj* proj, const gsfit_camera* cams,
+                     int32_t n_views, int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges,
+                     const float* bg, const float* T_final, const uint32_t* n_contrib, const float* dL_drgb,
+                     const float* dL_dalpha, float* grad2d, float* grads, cudaStream_t stream);
+
+/*
+ * gsfit_adam_step -- Adam (Kingma & Ba) with bias correction over all
+ * parameter planes (the paper raises the scale, opacity and colour rates by
+ * about 50% and resets the state on restart, Section 4.2; both are choices of
+ * the caller's lr table and moment buffers).
+ *   m = b1 m + (1 - b1) g; v = b2 v + (1 - b2) g^2;
+ *   p -= lr * (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps),
+ *   with t = *step + 1; *step is incremented on the device afterwards.
+ * Arguments: params, grads, m, v: n_planes * n float4 (device); lr: HOST
+ *   array of 4 * n_planes floats, the rate of each component of each plane
+ *   (0 freezes it); step: device int32 count of completed steps.
+ * Errors: GSFIT_ERR_INVALID_ARG, GSFIT_ERR_CUDA.
+ */
+int gsfit_adam_step(float* params, const float* grads, float* m, float* v, int32_t n, int32_t n_planes,
+                    const float* lr, float beta1, float beta2, float eps, int32_t* step, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GSFIT_H_ */

@@ -46,7 +46,8 @@ enum ProjField {
     P_VISIBLE = 0,  // 1 if the Gaussian is binned into at least one tile
     P_DEPTH32,      // float32 camera-space depth (exact value)
     P_U, P_V,       // FP64 pixel-space centre
-    P_U32, P_V32,   // float32 pixel-space centre (decides the tile rectangle)
+    P_U32, P_V32,   // float32 pixel-space centre: decides the tile rectangle and
+                    // is the centre used in compositing
     P_RADIUS,       // integer pixel radius ceil(3 sqrt(lambda_max))
     P_CONIC_A, P_CONIC_B, P_CONIC_C,  // inverse 2D covariance (a', b', c')
     P_COV_A, P_COV_B, P_COV_C,        // dilated 2D covariance

@@ -77,6 +77,7 @@ struct Pixel {
     int n_contrib;
     bool ambiguous;
     std::vector<Blend> blends;
+    std::vector<int> ambiguous_gauss;  // Gaussians whose own decision was near a threshold
 };
 
 // |x - thr| within a relative margin: float32 rounding on the GPU side could
@@ -89,24 +90,35 @@ void composite_pixel(int px, int py, const uint32_t* list, int count, const doub
     out.n_contrib = 0;
     out.ambiguous = false;
     out.blends.clear();
+    out.ambiguous_gauss.clear();
     for (int j = 0; j < count; ++j) {
         const int gi = (int)list[j];
         const double* p = proj_v + (size_t)gi * P_STRIDE;
-        const double dx = px - p[P_U], dy = py - p[P_V];
+        // Normal mode takes the splat centre at its float32 value (computed
+        // with correctly rounded float32 operations, it is identical in every
+        // implementation and already decides the tile rectangle); smooth mode
+        // keeps the FP64 centre so the image is differentiable in the mean.
+        const double dx = px - (smooth ? p[P_U] : p[P_U32]);
+        const double dy = py - (smooth ? p[P_V] : p[P_V32]);
         const double power = -0.5 * (p[P_CONIC_A] * dx * dx + p[P_CONIC_C] * dy * dy) - p[P_CONIC_B] * dx * dy;
         if (power > 0.0) continue;
         const double G = std::exp(power);
         const double a = p[P_OPACITY] * G;
         const bool clamped = a > ALPHA_CLAMP;
         const double alpha = clamped ? ALPHA_CLAMP : a;
-        if (near_threshold(a, ALPHA_CLAMP)) out.ambiguous = true;
-        if (!smooth) {
-            if (near_threshold(a, ALPHA_SKIP)) out.ambiguous = true;
-            if (alpha < ALPHA_SKIP) continue;
+        bool amb = near_threshold(a, ALPHA_CLAMP);
+        if (!smooth) amb = amb || near_threshold(a, ALPHA_SKIP);
+        if (amb) {
+            out.ambiguous = true;
+            out.ambiguous_gauss.push_back(gi);
         }
+        if (!smooth && alpha < ALPHA_SKIP) continue;
         const double Tn = T * (1.0 - alpha);
         if (!smooth) {
-            if (near_threshold(Tn, T_STOP)) out.ambiguous = true;
+            if (near_threshold(Tn, T_STOP)) {
+                out.ambiguous = true;
+                out.ambiguous_gauss.push_back(gi);
+            }
             if (Tn < T_STOP) break;
         }
         for (int ch = 0; ch < 3; ++ch) C[ch] += p[P_R + ch] * alpha * T;
@@ -118,12 +130,8 @@ void composite_pixel(int px, int py, const uint32_t* list, int count, const doub
     out.T = T;
 }
 
-// The pixel's list: its tile's sorted range (normal mode) or every visible
+// The pixel's list is its tile's sorted range (normal mode) or every visible
 // Gaussian of the view in depth order (smooth mode).
-struct ViewLists {
-    std::vector<uint32_t> all_sorted;
-};
-
 std::vector<uint32_t> depth_sorted_visible(int n, const double* proj_v) {
     std::vector<uint32_t> idx;
     for (int i = 0; i < n; ++i)
@@ -268,9 +276,7 @@ void render_bwd(int n, int K, const double* gauss, const std::vector<Camera>& ca
 #pragma omp atomic
                     out[5] += go;
                 }
-                if (px.ambiguous) {
-                    for (const Blend& e : px.blends) gauss_ambiguous[(size_t)it.v * n + e.gauss] = 1;
-                }
+                for (int gi : px.ambiguous_gauss) gauss_ambiguous[(size_t)it.v * n + gi] = 1;
             }
     }
     const int stride = gauss_stride(K);

@@ -1,0 +1,84 @@
+// Internal helpers shared by the gsfit kernels (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gsfit.h"
+
+#define GSFIT_CUDA_CHECK(expr)                          \
+    do {                                                \
+        cudaError_t err_ = (expr);                      \
+        if (err_ != cudaSuccess) return GSFIT_ERR_CUDA; \
+    } while (0)
+
+#define GSFIT_LAUNCH_CHECK() GSFIT_CUDA_CHECK(cudaGetLastError())
+
+namespace gsfit {
+
+constexpr int kTile = GSFIT_TILE;
+constexpr int kTilePixels = kTile * kTile;
+constexpr float kAlphaClamp = 0.99f;
+constexpr float kAlphaSkip = 1.0f / 255.0f;
+constexpr float kTStop = 1e-4f;
+constexpr float kDilation = 0.3f;
+constexpr float kFrustumGuard = 1.3f;
+
+inline int num_planes(int deg) {
+    const int K = (deg + 1) * (deg + 1);
+    return 3 + (3 * K + 3) / 4;
+}
+
+// Index of the view that owns global tile `t` (binary search over the
+// per-view tile offsets held in shared memory; views are laid out in order).
+__device__ __forceinline__ int view_of_tile(const gsfit_camera* cams, int n_views, int t) {
+    int lo = 0, hi = n_views - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (cams[mid].tile_offset <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Copies the camera table into shared memory (whole block participates).
+__device__ __forceinline__ void load_cameras(gsfit_camera* dst, const gsfit_camera* src, int n_views) {
+    const int words = n_views * (int)(sizeof(gsfit_camera) / sizeof(int4));
+    const int4* s = reinterpret_cast<const int4*>(src);
+    int4* d = reinterpret_cast<int4*>(dst);
+    for (int k = threadIdx.x; k < words; k += blockDim.x) d[k] = s[k];
+}
+
+__device__ __forceinline__ int tiles_x_of(const gsfit_camera& c) { return (c.width + kTile - 1) / kTile; }
+__device__ __forceinline__ int tiles_y_of(const gsfit_camera& c) { return (c.height + kTile - 1) / kTile; }
+
+// Tile rectangle [x0, x1) x [y0, y1) of a splat with centre (u, w) and
+// integer radius r (3DGS): x0 = floor((u - r) / B), x1 = floor(((u + r) + (B -
+// 1)) / B), clamped to the view; every operation correctly rounded, so the
+// projection and the key emission agree bit for bit.
+struct Rect {
+    int x0, y0, x1, y1;
+};
+
+__device__ __forceinline__ Rect tile_rect(float u, float w, float radius, int tiles_x, int tiles_y) {
+    const float Bf = (float)kTile, Bm1 = (float)(kTile - 1);
+    Rect t;
+    t.x0 = min(tiles_x, max(0, (int)floorf(__fdiv_rn(__fsub_rn(u, radius), Bf))));
+    t.x1 = min(tiles_x, max(0, (int)floorf(__fdiv_rn(__fadd_rn(__fadd_rn(u, radius), Bm1), Bf))));
+    t.y0 = min(tiles_y, max(0, (int)floorf(__fdiv_rn(__fsub_rn(w, radius), Bf))));
+    t.y1 = min(tiles_y, max(0, (int)floorf(__fdiv_rn(__fadd_rn(__fadd_rn(w, radius), Bm1), Bf))));
+    return t;
+}
+
+// Exponent of a splat at pixel offset (dx, dy) = pixel - centre:
+// power = -1/2 (a' dx^2 + c' dy^2) - b' dx dy. The forward pass and the
+// adjoint both call this, so they take identical skip decisions.
+__device__ __forceinline__ float splat_power(float4 co, float dx, float dy) {
+    return -0.5f * (co.x * dx * dx + co.z * dy * dy) - co.y * dx * dy;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace gsfit

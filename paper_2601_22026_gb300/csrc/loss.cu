@@ -1,0 +1,265 @@
+// Photometric loss of a view batch and its gradient (3DGS loss on colour with
+// an added L1 term on alpha for the alpha supervision of Section 4.2; targets
+// are composited over the same randomised background as the render).
+//
+// Design: one work item is a 32 x 32 output tile of one colour channel of one
+// view. The item loads render and target over the tile plus a 10-pixel halo
+// into shared memory, forms the five windowed moments on the tile plus a
+// 5-pixel halo with two separable 11-tap passes, evaluates the SSIM map and
+// its partials there, and convolves the partials back onto the tile: the
+// gradient of the windowed SSIM never leaves shared memory, so the kernel
+// reads each input pixel once and writes each gradient once. Channel-0 items
+// also handle the alpha term. Persistent CTAs stride over the items.
+#include "common.cuh"
+
+namespace gsfit {
+
+namespace {
+
+constexpr int kOut = 32;             // output tile edge
+constexpr int kR1 = kOut + 10;       // moments / partials region (halo 5)
+constexpr int kR2 = kOut + 20;       // input region (halo 10)
+constexpr int kLossThreads = 256;
+constexpr float kC1 = 0.01f * 0.01f;
+constexpr float kC2 = 0.03f * 0.03f;
+
+struct LossSmem {
+    float x[kR2][kR2];
+    float y[kR2][kR2];
+    float h[5][kR2][kR1];   // horizontal pass; later reused for the partials
+    float m[5][kR1][kR1];   // moments; later reused for the horizontal pass of the partials
+};
+
+// Normalised 11-tap Gaussian, sigma = 1.5.
+__device__ __forceinline__ void window(float w[11]) {
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < 11; ++i) {
+        const float d = (float)(i - 5);
+        w[i] = expf(-d * d / (2.0f * 1.5f * 1.5f));
+        s += w[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 11; ++i) w[i] /= s;
+}
+
+__global__ void __launch_bounds__(kLossThreads) loss_kernel(
+    const gsfit_camera* __restrict__ cams_g, int n_views, const float* __restrict__ rgb,
+    const float* __restrict__ alpha, const float* __restrict__ t_rgb, const float* __restrict__ t_alpha,
+    const float* __restrict__ bg, float lambda, float* __restrict__ g_rgb, float* __restrict__ g_alpha,
+    float* __restrict__ acc /* 3 per view: sum|x-y|, sum SSIM, sum|A-A*| */) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    LossSmem& S = *reinterpret_cast<LossSmem*>(smem_raw);
+    __shared__ int s_item_off[GSFIT_MAX_VIEWS + 1];
+    __shared__ float s_red[3][kLossThreads / 32];
+    if (threadIdx.x == 0) {
+        int o = 0;
+        for (int v = 0; v < n_views; ++v) {
+            s_item_off[v] = o;
+            const int tx = (cams_g[v].width + kOut - 1) / kOut, ty = (cams_g[v].height + kOut - 1) / kOut;
+            o += 3 * tx * ty;
+        }
+        s_item_off[n_views] = o;
+    }
+    float w[11];
+    window(w);
+    __syncthreads();
+    const int n_items = s_item_off[n_views];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        int v = 0;
+        while (s_item_off[v + 1] <= item) ++v;
+        const gsfit_camera& cam = cams_g[v];
+        const int W = cam.width, H = cam.height;
+        const int txn = (W + kOut - 1) / kOut;
+        const int local = item - s_item_off[v];
+        const int ch = local % 3;
+        const int tile = local / 3;
+        const int oy = (tile / txn) * kOut, ox = (tile % txn) * kOut;
+        const long long P = (long long)W * H;
+        const float* X = rgb + 3ll * cam.pixel_offset + ch * P;
+        const float* Yt = t_rgb + 3ll * cam.pixel_offset + ch * P;
+        const float* At = t_alpha + cam.pixel_offset;
+        const float bgc = bg[3 * v + ch];
+        const float inv3PV = 1.0f / (3.0f * (float)P * (float)n_views);
+
+        // 1. inputs over the 52 x 52 region, zero outside the image
+        for (int k = tid; k < kR2 * kR2; k += kLossThreads) {
+            const int r = k / kR2, cidx = k - r * kR2;
+            const int gy = oy - 10 + r, gx = ox - 10 + cidx;
+            float xv = 0.f, yv = 0.f;
+            if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
+                const long long q = (long long)gy * W + gx;
+                xv = X[q];
+                yv = Yt[q] + (1.0f - At[q]) * bgc;
+            }
+            S.x[r][cidx] = xv;
+            S.y[r][cidx] = yv;
+        }
+        __syncthreads();
+        // 2. horizontal pass of x, y, x^2, y^2, xy: rows 0..51, columns 0..41
+        for (int k = tid; k < kR2 * kR1; k += kLossThreads) {
+            const int r = k / kR1, cidx = k - r * kR1;
+            float a = 0.f, b = 0.f, c = 0.f, d = 0.f, e = 0.f;
+#pragma unroll
+            for (int j = 0; j < 11; ++j) {
+                const float xv = S.x[r][cidx + j], yv = S.y[r][cidx + j];
+                a += w[j] * xv;
+                b += w[j] * yv;
+                c += w[j] * xv * xv;
+                d += w[j] * yv * yv;
+                e += w[j] * xv * yv;
+            }
+            S.h[0][r][cidx] = a; S.h[1][r][cidx] = b; S.h[2][r][cidx] = c; S.h[3][r][cidx] = d; S.h[4][r][cidx] = e;
+        }
+        __syncthreads();
+        // 3. vertical pass: moments on the 42 x 42 region
+        for (int k = tid; k < kR1 * kR1; k += kLossThreads) {
+            const int r = k / kR1, cidx = k - r * kR1;
+#pragma unroll
+            for (int f = 0; f < 5; ++f) {
+                float a = 0.f;
+#pragma unroll
+                for (int j = 0; j < 11; ++j) a += w[j] * S.h[f][r + j][cidx];
+                S.m[f][r][cidx] = a;
+            }
+        }
+        __syncthreads();
+        // 4. SSIM and its partials w.r.t. (mu_x, E[x^2], E[xy]) on the region;
+        //    zero outside the image (those windows do not exist).
+        float ssim_sum = 0.f;
+        float (*part)[kR2][kR1] = S.h;  // reuse: part[0..2][r][c] for r, c < 42
+        for (int k = tid; k < kR1 * kR1; k += kLossThreads) {
+            const int r = k / kR1, cidx = k - r * kR1;
+            const int gy = oy - 5 + r, gx = ox - 5 + cidx;
+            float dmu = 0.f, dxx = 0.f, dxy = 0.f;
+            if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
+                const float mx = S.m[0][r][cidx], my = S.m[1][r][cidx];
+                const float sx = S.m[2][r][cidx] - mx * mx, sy = S.m[3][r][cidx] - my * my;
+                const float sxy = S.m[4][r][cidx] - mx * my;
+                const float A1 = 2.f * mx * my + kC1, A2 = 2.f * sxy + kC2;
+                const float B1 = mx * mx + my * my + kC1, B2 = sx + sy + kC2;
+                const float iB = 1.0f / (B1 * B2);
+                const float ss = A1 * A2 * iB;
+                dmu = (2.f * my * A2 - 2.f * my * A1) * iB - ss * (2.f * mx / B1 - 2.f * mx / B2);
+                dxx = -ss / B2;
+                dxy = 2.f * A1 * iB;
+                if (r >= 5 && r < 5 + kOut && cidx >= 5 && cidx < 5 + kOut) ssim_sum += ss;
+            }
+            part[0][r][cidx] = dmu;
+            part[1][r][cidx] = dxx;
+            part[2][r][cidx] = dxy;
+        }
+        __syncthreads();
+        // 5. horizontal pass of the partials: rows 0..41, columns 0..31
+        float (*hp)[kR1][kR1] = S.m;  // reuse: hp[0..2][r][c] for r < 42, c < 32
+        for (int k = tid; k < kR1 * kOut; k += kLossThreads) {
+            const int r = k / kOut, cidx = k - r * kOut;
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                float a = 0.f;
+#pragma unroll
+                for (int j = 0; j < 11; ++j) a += w[j] * part[f][r][cidx + j];
+                hp[f][r][cidx] = a;
+            }
+        }
+        __syncthreads();
+        // 6. vertical pass onto the tile and the gradient
+        float l1 = 0.f, la = 0.f;
+        for (int k = tid; k < kOut * kOut; k += kLossThreads) {
+            const int r = k / kOut, cidx = k - r * kOut;
+            const int gy = oy + r, gx = ox + cidx;
+            if (gy >= H || gx >= W) continue;
+            float cm = 0.f, cxx = 0.f, cxy = 0.f;
+#pragma unroll
+            for (int j = 0; j < 11; ++j) {
+                cm += w[j] * hp[0][r + j][cidx];
+                cxx += w[j] * hp[1][r + j][cidx];
+                cxy += w[j] * hp[2][r + j][cidx];
+            }
+            const float xv = S.x[r + 10][cidx + 10], yv = S.y[r + 10][cidx + 10];
+            const float dssim = cm + 2.f * xv * cxx + yv * cxy;
+            const float diff = xv - yv;
+            const float sg = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
+            l1 += fabsf(diff);
+            const long long q = (long long)gy * W + gx;
+            g_rgb[3ll * cam.pixel_offset + ch * P + q] = ((1.0f - lambda) * sg - lambda * dssim) * inv3PV;
+            if (ch == 0) {
+                const float da = alpha[cam.pixel_offset + q] - At[q];
+                la += fabsf(da);
+                g_alpha[cam.pixel_offset + q] =
+                    (da > 0.f ? 1.f : (da < 0.f ? -1.f : 0.f)) / ((float)P * (float)n_views);
+            }
+        }
+        // block sums of the loss terms
+        ssim_sum = warp_sum(ssim_sum);
+        l1 = warp_sum(l1);
+        la = warp_sum(la);
+        if (lane == 0) {
+            s_red[0][wid] = l1;
+            s_red[1][wid] = ssim_sum;
+            s_red[2][wid] = la;
+        }
+        __syncthreads();
+        if (tid < 3) {
+            float s = 0.f;
+            for (int k = 0; k < kLossThreads / 32; ++k) s += s_red[tid][k];
+            atomicAdd(&acc[3 * v + tid], s);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void loss_finalize_kernel(const gsfit_camera* __restrict__ cams, int n_views, float lambda,
+                                     const float* __restrict__ acc, float* __restrict__ loss_out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    float L = 0.f;
+    for (int v = 0; v < n_views; ++v) {
+        const float P = (float)cams[v].width * (float)cams[v].height;
+        const float l1 = acc[3 * v] / (3.f * P), ssim = acc[3 * v + 1] / (3.f * P), la = acc[3 * v + 2] / P;
+        L += (1.f - lambda) * l1 + lambda * (1.f - ssim) + la;
+    }
+    *loss_out = L / (float)n_views;
+}
+
+}  // namespace
+
+}  // namespace gsfit
+
+using namespace gsfit;
+
+extern "C" size_t gsfit_loss_workspace_size(int32_t n_views) {
+    if (n_views < 1 || n_views > GSFIT_MAX_VIEWS) return 0;
+    return (size_t)(3 * n_views) * sizeof(float);
+}
+
+extern "C" int gsfit_loss(const gsfit_camera* cams, int32_t n_views, const float* rgb, const float* alpha,
+                          const float* target_rgb, const float* target_alpha, const float* bg, float lambda,
+                          float* dL_drgb, float* dL_dalpha, float* loss_out, void* ws, size_t ws_bytes,
+                          cudaStream_t stream) {
+    if (!cams || n_views < 1 || n_views > GSFIT_MAX_VIEWS || !rgb || !alpha || !target_rgb || !target_alpha ||
+        !bg || !dL_drgb || !dL_dalpha || !ws || ws_bytes < gsfit_loss_workspace_size(n_views))
+        return GSFIT_ERR_INVALID_ARG;
+    static bool attr_done[64] = {false};
+    int dev = 0;
+    GSFIT_CUDA_CHECK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return GSFIT_ERR_CUDA;
+    const size_t smem = sizeof(LossSmem);
+    if (!attr_done[dev]) {
+        GSFIT_CUDA_CHECK(cudaFuncSetAttribute(loss_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_done[dev] = true;
+    }
+    int sms = 0;
+    GSFIT_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    float* acc = static_cast<float*>(ws);
+    GSFIT_CUDA_CHECK(cudaMemsetAsync(acc, 0, sizeof(float) * 3 * n_views, stream));
+    loss_kernel<<<2 * sms, kLossThreads, smem, stream>>>(cams, n_views, rgb, alpha, target_rgb, target_alpha, bg,
+                                                         lambda, dL_drgb, dL_dalpha, acc);
+    GSFIT_LAUNCH_CHECK();
+    if (loss_out) {
+        loss_finalize_kernel<<<1, 32, 0, stream>>>(cams, n_views, lambda, acc, loss_out);
+        GSFIT_LAUNCH_CHECK();
+    }
+    return GSFIT_OK;
+}

@@ -1,0 +1,524 @@
+// EWA projection with spherical-harmonic colour, and its adjoint.
+//
+// The peripheral model is a 3DGS model (Section 4.2); its projection is the
+// EWA splat of 3DGS (not written out in the paper): Sigma = R(q) S^2 R(q)^T,
+// Sigma' = J W Sigma W^T J^T + 0.3 I, conic = Sigma'^-1, radius =
+// ceil(3 sqrt(lambda_max)), colour = SH(view direction) + 0.5 clamped at 0.
+//
+// Design: one thread per Gaussian loops over all views of the batch. The
+// Gaussian's float4 planes are read once (coalesced: a warp reads 512
+// contiguous bytes per plane) and kept in registers; the camera table sits in
+// shared memory. Culled records write only their 16-byte centre record (radius
+// 0) and a zero tile count, so narrow foveal crops cost little.
+#include "common.cuh"
+
+namespace gsfit {
+
+namespace {
+
+// Real SH constants N_lm * (polynomial factor), from
+// N_lm = sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) (x sqrt 2 for m != 0) and the
+// Condon-Shortley phase; the basis is ordered m = -l..l per band.
+constexpr float kY00 = 0.28209479177387814f;   // 1 / (2 sqrt(pi))
+constexpr float kY1 = 0.48860251190291992f;    // sqrt(3 / (4 pi))
+constexpr float kY2xy = 1.0925484305920792f;   // m = -2 (xy), -1 (yz), 1 (xz)
+constexpr float kY20 = 0.31539156525252005f;   // m = 0: (3 z^2 - 1)
+constexpr float kY22 = 0.54627421529603959f;   // m = 2: (x^2 - y^2)
+constexpr float kY33 = 0.59004358992664352f;   // m = -3, 3
+constexpr float kY32a = 2.8906114426405547f;   // m = -2: xyz
+constexpr float kY31 = 0.45704579946446577f;   // m = -1, 1: (5 z^2 - 1)
+constexpr float kY30 = 0.37317633259011540f;   // m = 0: z (5 z^2 - 3)
+constexpr float kY32b = 1.4453057213202773f;   // m = 2: z (x^2 - y^2)
+
+template <int DEG>
+struct SH {
+    static constexpr int K = (DEG + 1) * (DEG + 1);
+};
+
+// Y_k(d) for the unit direction d.
+template <int DEG>
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float* Y) {
+    Y[0] = kY00;
+    if (DEG >= 1) {
+        Y[1] = -kY1 * y;
+        Y[2] = kY1 * z;
+        Y[3] = -kY1 * x;
+    }
+    if (DEG >= 2) {
+        Y[4] = kY2xy * x * y;
+        Y[5] = -kY2xy * y * z;
+        Y[6] = kY20 * (3.0f * z * z - 1.0f);
+        Y[7] = -kY2xy * x * z;
+        Y[8] = kY22 * (x * x - y * y);
+    }
+    if (DEG >= 3) {
+        const float z5 = 5.0f * z * z;
+        Y[9] = -kY33 * y * (3.0f * x * x - y * y);
+        Y[10] = kY32a * x * y * z;
+        Y[11] = -kY31 * y * (z5 - 1.0f);
+        Y[12] = kY30 * z * (z5 - 3.0f);
+        Y[13] = -kY31 * x * (z5 - 1.0f);
+        Y[14] = kY32b * z * (x * x - y * y);
+        Y[15] = -kY33 * x * (x * x - 3.0f * y * y);
+    }
+}
+
+// sum_k w_k dY_k/d(x, y, z) for the polynomial forms above.
+template <int DEG>
+__device__ __forceinline__ float3 sh_basis_vjp(float x, float y, float z, const float* w) {
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+    if (DEG >= 1) {
+        gy -= kY1 * w[1];
+        gz += kY1 * w[2];
+        gx -= kY1 * w[3];
+    }
+    if (DEG >= 2) {
+        gx += kY2xy * y * w[4];
+        gy += kY2xy * x * w[4];
+        gy -= kY2xy * z * w[5];
+        gz -= kY2xy * y * w[5];
+        gz += 6.0f * kY20 * z * w[6];
+        gx -= kY2xy * z * w[7];
+        gz -= kY2xy * x * w[7];
+        gx += 2.0f * kY22 * x * w[8];
+        gy -= 2.0f * kY22 * y * w[8];
+    }
+    if (DEG >= 3) {
+        const float z5m1 = 5.0f * z * z - 1.0f;
+        gx -= 6.0f * kY33 * x * y * w[9];
+        gy -= 3.0f * kY33 * (x * x - y * y) * w[9];
+        gx += kY32a * y * z * w[10];
+        gy += kY32a * x * z * w[10];
+        gz += kY32a * x * y * w[10];
+        gy -= kY31 * z5m1 * w[11];
+        gz -= 10.0f * kY31 * y * z * w[11];
+        gz += kY30 * (15.0f * z * z - 3.0f) * w[12];
+        gx -= kY31 * z5m1 * w[13];
+        gz -= 10.0f * kY31 * x * z * w[13];
+        gx += 2.0f * kY32b * x * z * w[14];
+        gy -= 2.0f * kY32b * y * z * w[14];
+        gz += kY32b * (x * x - y * y) * w[14];
+        gx -= 3.0f * kY33 * (x * x - y * y) * w[15];
+        gy += 6.0f * kY33 * x * y * w[15];
+    }
+    return make_float3(gx, gy, gz);
+}
+
+// Camera-space coordinate row k in the fixed order ((R_k0 x + R_k1 y) + R_k2 z)
+// + t_k with every operation correctly rounded (no contraction): depth cull,
+// depth key and tile rectangle are decided on these bits.
+__device__ __forceinline__ float cam_row(const gsfit_camera& c, int k, float x, float y, float z) {
+    float s = __fadd_rn(__fmul_rn(c.viewmat[4 * k + 0], x), __fmul_rn(c.viewmat[4 * k + 1], y));
+    s = __fadd_rn(s, __fmul_rn(c.viewmat[4 * k + 2], z));
+    return __fadd_rn(s, c.viewmat[4 * k + 3]);
+}
+
+// Rotation matrix of the normalised quaternion (w, x, y, z).
+__device__ __forceinline__ void quat_rot(float w, float x, float y, float z, float R[9]) {
+    R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z);       R[2] = 2.f * (x * z + w * y);
+    R[3] = 2.f * (x * y + w * z);       R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+    R[6] = 2.f * (x * z - w * y);       R[7] = 2.f * (y * z + w * x);       R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+// Compensated a*c - b*b (Kahan's two-product difference): the determinant of
+// the dilated 2D covariance keeps full float32 accuracy even for long thin
+// splats whose a*c and b*b nearly cancel.
+__device__ __forceinline__ float det2(float a, float b, float c) {
+    const float bb = b * b;
+    const float e = fmaf(-b, b, bb);
+    const float f = fmaf(a, c, -bb);
+    return f + e;
+}
+
+struct Gauss {
+    float mx, my, mz, logit;
+    float qw, qx, qy, qz, qn;
+    float s[3];
+    float Sig[6];  // xx xy xz yy yz zz
+    float R[9];
+};
+
+__device__ __forceinline__ void load_gauss(const float4* __restrict__ P, int n, int i, Gauss& g) {
+    const float4 p0 = P[i];
+    const float4 p1 = P[(size_t)n + i];
+    const float4 p2 = P[2 * (size_t)n + i];
+    g.mx = p0.x; g.my = p0.y; g.mz = p0.z; g.logit = p0.w;
+    g.qn = sqrtf(p1.x * p1.x + p1.y * p1.y + p1.z * p1.z + p1.w * p1.w);
+    const float inv = 1.0f / g.qn;
+    g.qw = p1.x * inv; g.qx = p1.y * inv; g.qy = p1.z * inv; g.qz = p1.w * inv;
+    g.s[0] = expf(p2.x); g.s[1] = expf(p2.y); g.s[2] = expf(p2.z);
+    quat_rot(g.qw, g.qx, g.qy, g.qz, g.R);
+    const float* R = g.R;
+    const float s0 = g.s[0] * g.s[0], s1 = g.s[1] * g.s[1], s2 = g.s[2] * g.s[2];
+    // Sigma_ij = sum_k R_ik s_k^2 R_jk
+    g.Sig[0] = R[0] * R[0] * s0 + R[1] * R[1] * s1 + R[2] * R[2] * s2;
+    g.Sig[1] = R[0] * R[3] * s0 + R[1] * R[4] * s1 + R[2] * R[5] * s2;
+    g.Sig[2] = R[0] * R[6] * s0 + R[1] * R[7] * s1 + R[2] * R[8] * s2;
+    g.Sig[3] = R[3] * R[3] * s0 + R[4] * R[4] * s1 + R[5] * R[5] * s2;
+    g.Sig[4] = R[3] * R[6] * s0 + R[4] * R[7] * s1 + R[5] * R[8] * s2;
+    g.Sig[5] = R[6] * R[6] * s0 + R[7] * R[7] * s1 + R[8] * R[8] * s2;
+}
+
+template <int DEG>
+__device__ __forceinline__ void load_sh(const float4* __restrict__ P, int n, int i, float* sh) {
+    constexpr int K3 = 3 * SH<DEG>::K;
+    constexpr int NP = (K3 + 3) / 4;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        const float4 q = P[(size_t)(3 + p) * n + i];
+        if (4 * p + 0 < K3) sh[4 * p + 0] = q.x;
+        if (4 * p + 1 < K3) sh[4 * p + 1] = q.y;
+        if (4 * p + 2 < K3) sh[4 * p + 2] = q.z;
+        if (4 * p + 3 < K3) sh[4 * p + 3] = q.w;
+    }
+}
+
+// Per-view geometric quantities shared by the forward and adjoint passes.
+struct ViewGeom {
+    float tx, ty, tz;
+    float rx, ry;          // t_x/t_z, t_y/t_z after the frustum guard
+    bool gx, gy;           // guard active
+    float M0[3], M1[3];    // rows of J W
+    float a, b, c, det;    // dilated 2D covariance
+};
+
+__device__ __forceinline__ void view_geom(const gsfit_camera& cam, const Gauss& g, ViewGeom& o) {
+    o.tx = cam_row(cam, 0, g.mx, g.my, g.mz);
+    o.ty = cam_row(cam, 1, g.mx, g.my, g.mz);
+    o.tz = cam_row(cam, 2, g.mx, g.my, g.mz);
+    const float limx = kFrustumGuard * (0.5f * (float)cam.width / cam.fx);
+    const float limy = kFrustumGuard * (0.5f * (float)cam.height / cam.fy);
+    const float rx = o.tx / o.tz, ry = o.ty / o.tz;
+    o.gx = (rx < -limx) || (rx > limx);
+    o.gy = (ry < -limy) || (ry > limy);
+    o.rx = fminf(limx, fmaxf(-limx, rx));
+    o.ry = fminf(limy, fmaxf(-limy, ry));
+    const float iz = 1.0f / o.tz;
+    const float J00 = cam.fx * iz, J02 = -cam.fx * o.rx * iz;
+    const float J11 = cam.fy * iz, J12 = -cam.fy * o.ry * iz;
+    const float* W = cam.viewmat;  // rows 0..2 at W[0..2], W[4..6], W[8..10]
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        o.M0[j] = J00 * W[j] + J02 * W[8 + j];
+        o.M1[j] = J11 * W[4 + j] + J12 * W[8 + j];
+    }
+    const float* S = g.Sig;
+    const float sm0x = S[0] * o.M0[0] + S[1] * o.M0[1] + S[2] * o.M0[2];
+    const float sm0y = S[1] * o.M0[0] + S[3] * o.M0[1] + S[4] * o.M0[2];
+    const float sm0z = S[2] * o.M0[0] + S[4] * o.M0[1] + S[5] * o.M0[2];
+    const float sm1x = S[0] * o.M1[0] + S[1] * o.M1[1] + S[2] * o.M1[2];
+    const float sm1y = S[1] * o.M1[0] + S[3] * o.M1[1] + S[4] * o.M1[2];
+    const float sm1z = S[2] * o.M1[0] + S[4] * o.M1[1] + S[5] * o.M1[2];
+    o.a = o.M0[0] * sm0x + o.M0[1] * sm0y + o.M0[2] * sm0z + kDilation;
+    o.b = o.M0[0] * sm1x + o.M0[1] * sm1y + o.M0[2] * sm1z;
+    o.c = o.M1[0] * sm1x + o.M1[1] * sm1y + o.M1[2] * sm1z + kDilation;
+    o.det = det2(o.a, o.b, o.c);
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(256) project_kernel(const float4* __restrict__ P, int n,
+                                                      const gsfit_camera* __restrict__ cams_g, int n_views,
+                                                      float4* __restrict__ xyd, float4* __restrict__ conic,
+                                                      float4* __restrict__ rgb, uint32_t* __restrict__ tiles) {
+    extern __shared__ gsfit_camera cams[];
+    load_cameras(cams, cams_g, n_views);
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    constexpr int K = SH<DEG>::K;
+    Gauss g;
+    load_gauss(P, n, i, g);
+    float sh[3 * K];
+    load_sh<DEG>(P, n, i, sh);
+    const float opacity = 1.0f / (1.0f + expf(-g.logit));
+
+    for (int v = 0; v < n_views; ++v) {
+        const gsfit_camera& cam = cams[v];
+        const size_t r = (size_t)v * n + i;
+        ViewGeom vg;
+        view_geom(cam, g, vg);
+        if (!(vg.tz > cam.near_plane) || !(vg.det > 0.0f)) {
+            xyd[r] = make_float4(0.f, 0.f, vg.tz, 0.f);
+            tiles[r] = 0u;
+            continue;
+        }
+        const float inv_det = 1.0f / fmaxf(vg.det, 1e-12f);
+        const float mid = 0.5f * (vg.a + vg.c);
+        const float lambda = mid + sqrtf(fmaxf(0.1f, mid * mid - vg.det));
+        const float radius = ceilf(3.0f * sqrtf(lambda));
+        // centre, correctly rounded in a fixed order: (fx * t_x) / t_z + cx
+        const float u = __fadd_rn(__fdiv_rn(__fmul_rn(cam.fx, vg.tx), vg.tz), cam.cx);
+        const float w = __fadd_rn(__fdiv_rn(__fmul_rn(cam.fy, vg.ty), vg.tz), cam.cy);
+        const Rect rc = tile_rect(u, w, radius, tiles_x_of(cam), tiles_y_of(cam));
+        const uint32_t nt = (uint32_t)((rc.x1 - rc.x0) * (rc.y1 - rc.y0));
+        if (nt == 0u) {
+            xyd[r] = make_float4(u, w, vg.tz, 0.f);
+            tiles[r] = 0u;
+            continue;
+        }
+        // view-dependent colour
+        float dx = g.mx - cam.campos[0], dy = g.my - cam.campos[1], dz = g.mz - cam.campos[2];
+        const float idist = rsqrtf(dx * dx + dy * dy + dz * dz);
+        dx *= idist; dy *= idist; dz *= idist;
+        float Y[K];
+        sh_basis<DEG>(dx, dy, dz, Y);
+        float col[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc += Y[k] * sh[3 * k + ch];
+            col[ch] = acc + 0.5f;
+        }
+        const float mask = (col[0] < 0.f ? 1.f : 0.f) + (col[1] < 0.f ? 2.f : 0.f) + (col[2] < 0.f ? 4.f : 0.f);
+        xyd[r] = make_float4(u, w, vg.tz, radius);
+        conic[r] = make_float4(vg.c * inv_det, -vg.b * inv_det, vg.a * inv_det, opacity);
+        rgb[r] = make_float4(fmaxf(col[0], 0.f), fmaxf(col[1], 0.f), fmaxf(col[2], 0.f), mask);
+        tiles[r] = nt;
+    }
+}
+
+// Adjoint of project_kernel. One thread per Gaussian, looping over views:
+// reads the per-(view, Gaussian) 2D gradients accumulated by the blend
+// adjoint (and zeroes them for the next iteration), chains them through the
+// projection and writes the summed parameter gradients once.
+template <int DEG>
+__global__ void __launch_bounds__(256) project_bwd_kernel(const float4* __restrict__ P, int n,
+                                                          const gsfit_camera* __restrict__ cams_g, int n_views,
+                                                          const float4* __restrict__ xyd,
+                                                          const float4* __restrict__ conic,
+                                                          const float4* __restrict__ rgbm,
+                                                          float4* __restrict__ grad2d, float4* __restrict__ G) {
+    extern __shared__ gsfit_camera cams[];
+    load_cameras(cams, cams_g, n_views);
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    constexpr int K = SH<DEG>::K;
+    Gauss g;
+    load_gauss(P, n, i, g);
+    float sh[3 * K];
+    load_sh<DEG>(P, n, i, sh);
+    const float opacity = 1.0f / (1.0f + expf(-g.logit));
+
+    float dmean[3] = {0.f, 0.f, 0.f};
+    float dSig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // xx xy xz yy yz zz (symmetric, dL/dSigma_ij)
+    float dlogit = 0.f;
+    float dsh[3 * K];
+#pragma unroll
+    for (int k = 0; k < 3 * K; ++k) dsh[k] = 0.f;
+
+    for (int v = 0; v < n_views; ++v) {
+        const size_t r = (size_t)v * n + i;
+        if (xyd[r].w == 0.0f) continue;  // culled in this view
+        const float4 ga = grad2d[3 * r + 0];  // du, dv, dopacity
+        const float4 gb = grad2d[3 * r + 1];  // da', db', dc'
+        const float4 gc = grad2d[3 * r + 2];  // dr, dg, db
+        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+        grad2d[3 * r + 0] = zero;
+        grad2d[3 * r + 1] = zero;
+        grad2d[3 * r + 2] = zero;
+        const gsfit_camera& cam = cams[v];
+        ViewGeom vg;
+        view_geom(cam, g, vg);
+        const float iz = 1.0f / vg.tz, iz2 = iz * iz;
+        float dtx = ga.x * cam.fx * iz;
+        float dty = ga.y * cam.fy * iz;
+        float dtz = -(ga.x * cam.fx * vg.tx + ga.y * cam.fy * vg.ty) * iz2;
+
+        // conic Q = S^-1: dL/dS = -Q G Q with G = [[da', db'/2], [db'/2, dc']]
+        const float4 cq = conic[r];
+        const float q00 = cq.x, q01 = cq.y, q11 = cq.z;
+        const float g00 = gb.x, g01 = 0.5f * gb.y, g11 = gb.z;
+        const float t00 = q00 * g00 + q01 * g01, t01 = q00 * g01 + q01 * g11;
+        const float t10 = q01 * g00 + q11 * g01, t11 = q01 * g01 + q11 * g11;
+        const float dS00 = -(t00 * q00 + t01 * q01);
+        const float dS01 = -(t00 * q01 + t01 * q11);
+        const float dS11 = -(t10 * q01 + t11 * q11);
+
+        // S = M Sigma M^T: dSigma += M^T dS M; dM = 2 dS M Sigma
+        const float* M0 = vg.M0;
+        const float* M1 = vg.M1;
+        float u0[3], u1[3];  // dS rows applied to M: u0 = dS00 M0 + dS01 M1, u1 = dS01 M0 + dS11 M1
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            u0[j] = dS00 * M0[j] + dS01 * M1[j];
+            u1[j] = dS01 * M0[j] + dS11 * M1[j];
+        }
+        dSig[0] += M0[0] * u0[0] + M1[0] * u1[0];
+        dSig[1] += M0[0] * u0[1] + M1[0] * u1[1];
+        dSig[2] += M0[0] * u0[2] + M1[0] * u1[2];
+        dSig[3] += M0[1] * u0[1] + M1[1] * u1[1];
+        dSig[4] += M0[1] * u0[2] + M1[1] * u1[2];
+        dSig[5] += M0[2] * u0[2] + M1[2] * u1[2];
+        const float* S = g.Sig;
+        float dM0[3], dM1[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float sk0 = (k == 0) ? S[0] : (k == 1) ? S[1] : S[2];
+            const float sk1 = (k == 0) ? S[1] : (k == 1) ? S[3] : S[4];
+            const float sk2 = (k == 0) ? S[2] : (k == 1) ? S[4] : S[5];
+            dM0[k] = 2.f * (u0[0] * sk0 + u0[1] * sk1 + u0[2] * sk2);
+            dM1[k] = 2.f * (u1[0] * sk0 + u1[1] * sk1 + u1[2] * sk2);
+        }
+        // M = J W: dJ = dM W^T (only J00, J02, J11, J12 are non-zero)
+        const float* W = cam.viewmat;
+        const float dJ00 = dM0[0] * W[0] + dM0[1] * W[1] + dM0[2] * W[2];
+        const float dJ02 = dM0[0] * W[8] + dM0[1] * W[9] + dM0[2] * W[10];
+        const float dJ11 = dM1[0] * W[4] + dM1[1] * W[5] + dM1[2] * W[6];
+        const float dJ12 = dM1[0] * W[8] + dM1[1] * W[9] + dM1[2] * W[10];
+        dtz += -dJ00 * cam.fx * iz2 - dJ11 * cam.fy * iz2 + dJ02 * cam.fx * vg.rx * iz2 +
+               dJ12 * cam.fy * vg.ry * iz2;
+        const float drx = -dJ02 * cam.fx * iz, dry = -dJ12 * cam.fy * iz;
+        if (!vg.gx) {
+            dtx += drx * iz;
+            dtz -= drx * vg.tx * iz2;
+        }
+        if (!vg.gy) {
+            dty += dry * iz;
+            dtz -= dry * vg.ty * iz2;
+        }
+        // t = W mu + t_w
+#pragma unroll
+        for (int j = 0; j < 3; ++j) dmean[j] += W[j] * dtx + W[4 + j] * dty + W[8 + j] * dtz;
+
+        dlogit += ga.z * opacity * (1.f - opacity);
+
+        // colour: clamped channels pass no gradient
+        const float4 cm = rgbm[r];
+        const int mask = (int)cm.w;
+        const float gcol[3] = {(mask & 1) ? 0.f : gc.x, (mask & 2) ? 0.f : gc.y, (mask & 4) ? 0.f : gc.z};
+        float dx = g.mx - cam.campos[0], dy = g.my - cam.campos[1], dz = g.mz - cam.campos[2];
+        const float dist = sqrtf(dx * dx + dy * dy + dz * dz);
+        const float idist = 1.0f / dist;
+        dx *= idist; dy *= idist; dz *= idist;
+        float Y[K];
+        sh_basis<DEG>(dx, dy, dz, Y);
+        float wk[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            dsh[3 * k + 0] += Y[k] * gcol[0];
+            dsh[3 * k + 1] += Y[k] * gcol[1];
+            dsh[3 * k + 2] += Y[k] * gcol[2];
+            wk[k] = sh[3 * k + 0] * gcol[0] + sh[3 * k + 1] * gcol[1] + sh[3 * k + 2] * gcol[2];
+        }
+        if (DEG > 0) {
+            const float3 dd = sh_basis_vjp<DEG>(dx, dy, dz, wk);
+            const float proj = dx * dd.x + dy * dd.y + dz * dd.z;
+            dmean[0] += (dd.x - dx * proj) * idist;
+            dmean[1] += (dd.y - dy * proj) * idist;
+            dmean[2] += (dd.z - dz * proj) * idist;
+        }
+    }
+
+    // Sigma = Ms Ms^T, Ms = R diag(s): dMs = 2 dSigma Ms
+    const float* R = g.R;
+    float dls[3], dR[9];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        // column k of Ms is s_k R[:, k]
+        const float c0 = R[0 + k] * g.s[k], c1 = R[3 + k] * g.s[k], c2 = R[6 + k] * g.s[k];
+        const float m0 = 2.f * (dSig[0] * c0 + dSig[1] * c1 + dSig[2] * c2);
+        const float m1 = 2.f * (dSig[1] * c0 + dSig[3] * c1 + dSig[4] * c2);
+        const float m2 = 2.f * (dSig[2] * c0 + dSig[4] * c1 + dSig[5] * c2);
+        dls[k] = (m0 * R[0 + k] + m1 * R[3 + k] + m2 * R[6 + k]) * g.s[k];
+        dR[0 + k] = m0 * g.s[k];
+        dR[3 + k] = m1 * g.s[k];
+        dR[6 + k] = m2 * g.s[k];
+    }
+    const float w = g.qw, x = g.qx, y = g.qy, z = g.qz;
+    float dq[4];
+    dq[0] = 2.f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
+    dq[1] = 2.f * (y * dR[1] + z * dR[2] + y * dR[3] - 2.f * x * dR[4] - w * dR[5] + z * dR[6] + w * dR[7] -
+                   2.f * x * dR[8]);
+    dq[2] = 2.f * (-2.f * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] - w * dR[6] + z * dR[7] -
+                   2.f * y * dR[8]);
+    dq[3] = 2.f * (-2.f * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.f * z * dR[4] + y * dR[5] +
+                   x * dR[6] + y * dR[7]);
+    const float qd = w * dq[0] + x * dq[1] + y * dq[2] + z * dq[3];
+    const float iq = 1.0f / g.qn;
+
+    G[i] = make_float4(dmean[0], dmean[1], dmean[2], dlogit);
+    G[(size_t)n + i] = make_float4((dq[0] - w * qd) * iq, (dq[1] - x * qd) * iq, (dq[2] - y * qd) * iq,
+                                   (dq[3] - z * qd) * iq);
+    G[2 * (size_t)n + i] = make_float4(dls[0], dls[1], dls[2], 0.f);
+    constexpr int K3 = 3 * K;
+    constexpr int NP = (K3 + 3) / 4;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        float4 q;
+        q.x = (4 * p + 0 < K3) ? dsh[4 * p + 0] : 0.f;
+        q.y = (4 * p + 1 < K3) ? dsh[4 * p + 1] : 0.f;
+        q.z = (4 * p + 2 < K3) ? dsh[4 * p + 2] : 0.f;
+        q.w = (4 * p + 3 < K3) ? dsh[4 * p + 3] : 0.f;
+        G[(size_t)(3 + p) * n + i] = q;
+    }
+}
+
+template <int DEG>
+int launch_project(const gsfit_gaussians* g, const gsfit_camera* cams, int V, gsfit_proj* out, cudaStream_t s) {
+    const int threads = 256;
+    const int blocks = (g->n + threads - 1) / threads;
+    const size_t smem = sizeof(gsfit_camera) * V;
+    project_kernel<DEG><<<blocks, threads, smem, s>>>(
+        reinterpret_cast<const float4*>(g->params), g->n, cams, V, reinterpret_cast<float4*>(out->xyd),
+        reinterpret_cast<float4*>(out->conic), reinterpret_cast<float4*>(out->rgb), out->tiles);
+    GSFIT_LAUNCH_CHECK();
+    return GSFIT_OK;
+}
+
+template <int DEG>
+int launch_project_bwd(const gsfit_gaussians* g, const gsfit_proj* proj, const gsfit_camera* cams, int V,
+                       float* grad2d, float* grads, cudaStream_t s) {
+    const int threads = 256;
+    const int blocks = (g->n + threads - 1) / threads;
+    const size_t smem = sizeof(gsfit_camera) * V;
+    project_bwd_kernel<DEG><<<blocks, threads, smem, s>>>(
+        reinterpret_cast<const float4*>(g->params), g->n, cams, V, reinterpret_cast<const float4*>(proj->xyd),
+        reinterpret_cast<const float4*>(proj->conic), reinterpret_cast<const float4*>(proj->rgb),
+        reinterpret_cast<float4*>(grad2d), reinterpret_cast<float4*>(grads));
+    GSFIT_LAUNCH_CHECK();
+    return GSFIT_OK;
+}
+
+}  // namespace
+
+bool valid_gaussians(const gsfit_gaussians* g) {
+    return g && g->params && g->n > 0 && g->sh_degree >= 0 && g->sh_degree <= 3 &&
+           (reinterpret_cast<uintptr_t>(g->params) % 16) == 0;
+}
+
+bool valid_proj(const gsfit_proj* p) {
+    return p && p->xyd && p->conic && p->rgb && p->tiles && (reinterpret_cast<uintptr_t>(p->xyd) % 16) == 0 &&
+           (reinterpret_cast<uintptr_t>(p->conic) % 16) == 0 && (reinterpret_cast<uintptr_t>(p->rgb) % 16) == 0;
+}
+
+int project_bwd(const gsfit_gaussians* g, const gsfit_proj* proj, const gsfit_camera* cams, int V, float* grad2d,
+                float* grads, cudaStream_t s) {
+    switch (g->sh_degree) {
+        case 0: return launch_project_bwd<0>(g, proj, cams, V, grad2d, grads, s);
+        case 1: return launch_project_bwd<1>(g, proj, cams, V, grad2d, grads, s);
+        case 2: return launch_project_bwd<2>(g, proj, cams, V, grad2d, grads, s);
+        default: return launch_project_bwd<3>(g, proj, cams, V, grad2d, grads, s);
+    }
+}
+
+}  // namespace gsfit
+
+extern "C" int gsfit_num_planes(int sh_degree) {
+    if (sh_degree < 0 || sh_degree > 3) return GSFIT_ERR_INVALID_ARG;
+    return gsfit::num_planes(sh_degree);
+}
+
+extern "C" int gsfit_project(const gsfit_gaussians* g, const gsfit_camera* cams, int32_t n_views, gsfit_proj* out,
+                             cudaStream_t stream) {
+    if (!gsfit::valid_gaussians(g) || !cams || !gsfit::valid_proj(out) || n_views < 1 ||
+        n_views > GSFIT_MAX_VIEWS)
+        return GSFIT_ERR_INVALID_ARG;
+    switch (g->sh_degree) {
+        case 0: return gsfit::launch_project<0>(g, cams, n_views, out, stream);
+        case 1: return gsfit::launch_project<1>(g, cams, n_views, out, stream);
+        case 2: return gsfit::launch_project<2>(g, cams, n_views, out, stream);
+        default: return gsfit::launch_project<3>(g, cams, n_views, out, stream);
+    }
+}

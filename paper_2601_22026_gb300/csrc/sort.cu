@@ -1,0 +1,454 @@
+// Tile binning: pair emission, LSD radix sort of 64-bit (tile | depth) keys,
+// per-tile ranges.
+//
+// 3DGS (which the fitted peripheral model is, Section 4.2) renders by sorting
+// every (Gaussian, covered tile) pair by (tile id, depth) once per image and
+// compositing each tile's range front to back. Here:
+//   1. reduce_kernel / scan_kernel: a spin-free reduce-then-scan over the
+//      per-record tile counts gives each record its output offset and the
+//      total pair count (kept on the device; checked against capacity).
+//   2. emit_kernel: rescans its block in record order and writes the pairs.
+//   3. hist_kernel: one read of the keys builds the digit histograms of every
+//      pass (8-bit digits over the 32 depth bits and the significant tile-id
+//      bits), and clears the look-back tables and tile ranges.
+//   4. onesweep_kernel, once per digit: a stable counting pass in the
+//      Onesweep style (Adinets & Merrill 2022): each CTA ranks a 4096-key
+//      partition in shared memory, publishes its digit counts, obtains its
+//      global digit offsets by decoupled look-back over earlier partitions
+//      (every wait bounded: on expiry the status word gets GSFIT_ERR_TIMEOUT),
+//      and writes its keys digit-run by digit-run so stores coalesce. One read
+//      and one write of (key, value) per pass: 24 bytes per pair.
+//   5. ranges_kernel: [first, last+1) of each tile from adjacent keys.
+// Pair counts never leave the device, so the sequence can be captured in a
+// CUDA graph; launches are sized by capacity and idle CTAs exit at once.
+#include "common.cuh"
+
+namespace gsfit {
+
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanChunk = kScanThreads * kScanItems;  // records per block
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortItems = 16;
+constexpr int kPart = kSortThreads * kSortItems;  // keys per partition
+constexpr int kRadix = 256;
+constexpr int kMaxPasses = 8;
+constexpr uint32_t kFlagAgg = 1u << 30;
+constexpr uint32_t kFlagInc = 1u << 31;
+constexpr uint32_t kValMask = kFlagAgg - 1u;
+constexpr int kSpinLimit = 1 << 20;  // x ~100 ns sleeps: about a tenth of a second
+constexpr int kHistBlocks = 1024;
+
+struct SortCtl {
+    uint32_t n_sort;      // pairs to sort (0 when the capacity was exceeded)
+    uint32_t pad;
+    unsigned long long total;  // exact pair count
+    uint32_t part_counter[kMaxPasses];
+    uint32_t hist[kMaxPasses][kRadix];
+};
+
+// Block-wide exclusive scan of one value per thread (blockDim == 256).
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t* s_warp, uint32_t& total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    uint32_t wpre = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        const uint32_t s = s_warp[w];
+        if (w < wid) wpre += s;
+        tot += s;
+    }
+    __syncthreads();
+    total = tot;
+    return wpre + incl - x;
+}
+
+__global__ void __launch_bounds__(kScanThreads) reduce_kernel(const uint32_t* __restrict__ tiles, long long n_rec,
+                                                              uint32_t* __restrict__ block_sums) {
+    __shared__ uint32_t s_warp[8];
+    const long long base = (long long)blockIdx.x * kScanChunk;
+    uint32_t acc = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        const long long r = base + (long long)j * kScanThreads + threadIdx.x;
+        if (r < n_rec) acc += tiles[r];
+    }
+    uint32_t total;
+    block_excl_scan(acc, s_warp, total);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+// Single block: exclusive scan of the block sums, total, capacity check, and
+// reset of the sort control block.
+__global__ void __launch_bounds__(1024) scan_kernel(uint32_t* __restrict__ block_sums, int n_blocks,
+                                                    SortCtl* __restrict__ ctl, uint32_t* __restrict__ n_instances,
+                                                    long long capacity, int32_t* __restrict__ status) {
+    __shared__ unsigned long long s_warp[32];
+    __shared__ unsigned long long s_carry;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_carry = 0;
+    for (int k = threadIdx.x; k < kMaxPasses * kRadix; k += blockDim.x) (&ctl->hist[0][0])[k] = 0u;
+    if (threadIdx.x < kMaxPasses) ctl->part_counter[threadIdx.x] = 0u;
+    __syncthreads();
+    for (int base = 0; base < n_blocks; base += 1024) {
+        const int b = base + threadIdx.x;
+        const unsigned long long x = b < n_blocks ? block_sums[b] : 0ull;
+        unsigned long long incl = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) s_warp[wid] = incl;
+        __syncthreads();
+        unsigned long long wpre = 0, tot = 0;
+        for (int w = 0; w < 32; ++w) {
+            if (w < wid) wpre += s_warp[w];
+            tot += s_warp[w];
+        }
+        const unsigned long long carry = s_carry;
+        if (b < n_blocks) block_sums[b] = (uint32_t)(carry + wpre + incl - x);
+        __syncthreads();
+        if (threadIdx.x == 0) s_carry = carry + tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const unsigned long long total = s_carry;
+        ctl->total = total;
+        *n_instances = total > 0xffffffffull ? 0xffffffffu : (uint32_t)total;
+        if (total > (unsigned long long)capacity) {
+            ctl->n_sort = 0u;
+            *status = GSFIT_ERR_CAPACITY;
+        } else {
+            ctl->n_sort = (uint32_t)total;
+        }
+    }
+}
+
+// Rescans each block's records in order and writes their pairs.
+__global__ void __launch_bounds__(kScanThreads) emit_kernel(const uint32_t* __restrict__ tiles,
+                                                            const float4* __restrict__ xyd, int n, int n_views,
+                                                            const gsfit_camera* __restrict__ cams_g,
+                                                            const uint32_t* __restrict__ block_sums,
+                                                            const SortCtl* __restrict__ ctl,
+                                                            unsigned long long* __restrict__ keys,
+                                                            uint32_t* __restrict__ vals) {
+    extern __shared__ gsfit_camera cams[];
+    __shared__ uint32_t s_warp[8];
+    load_cameras(cams, cams_g, n_views);
+    __syncthreads();
+    if (ctl->total > (unsigned long long)ctl->n_sort) return;  // capacity exceeded: emit nothing
+    const long long n_rec = (long long)n * n_views;
+    const long long base = (long long)blockIdx.x * kScanChunk;
+    uint32_t offset = block_sums[blockIdx.x];
+    for (int j = 0; j < kScanItems; ++j) {
+        const long long r = base + (long long)j * kScanThreads + threadIdx.x;
+        const uint32_t t = r < n_rec ? tiles[r] : 0u;
+        uint32_t row_total;
+        const uint32_t ex = block_excl_scan(t, s_warp, row_total);
+        if (t > 0u) {
+            const int v = (int)(r / n);
+            const int i = (int)(r - (long long)v * n);
+            const gsfit_camera& cam = cams[v];
+            const float4 p = xyd[r];
+            const int txn = tiles_x_of(cam);
+            const Rect rc = tile_rect(p.x, p.y, p.w, txn, tiles_y_of(cam));
+            const unsigned long long depth = (unsigned long long)__float_as_uint(p.z);
+            uint32_t o = offset + ex;
+            for (int ty = rc.y0; ty < rc.y1; ++ty)
+                for (int tx = rc.x0; tx < rc.x1; ++tx) {
+                    const unsigned long long tile = (unsigned long long)(cam.tile_offset + ty * txn + tx);
+                    keys[o] = (tile << 32) | depth;
+                    vals[o] = (uint32_t)i;
+                    ++o;
+                }
+        }
+        offset += row_total;
+    }
+}
+
+// Digit histograms of every pass in one read of the keys; also clears the
+// look-back tables and the tile ranges for this sort.
+__global__ void __launch_bounds__(256) hist_kernel(const unsigned long long* __restrict__ keys,
+                                                   SortCtl* __restrict__ ctl, int n_passes,
+                                                   uint32_t* __restrict__ lookback, long long lookback_words,
+                                                   uint32_t* __restrict__ ranges, long long range_words) {
+    __shared__ uint32_t s_hist[kMaxPasses][kRadix];
+    for (int k = threadIdx.x; k < kMaxPasses * kRadix; k += blockDim.x) (&s_hist[0][0])[k] = 0u;
+    __syncthreads();
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (long long k = tid; k < lookback_words; k += stride) lookback[k] = 0u;
+    for (long long k = tid; k < range_words; k += stride) ranges[k] = 0u;
+    const uint32_t n = ctl->n_sort;
+    for (long long k = tid; k < n; k += stride) {
+        const unsigned long long key = keys[k];
+        for (int p = 0; p < n_passes; ++p) atomicAdd(&s_hist[p][(key >> (8 * p)) & 0xff], 1u);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < n_passes * kRadix; k += blockDim.x) {
+        const uint32_t c = (&s_hist[0][0])[k];
+        if (c) atomicAdd(&ctl->hist[0][0] + k, c);
+    }
+}
+
+struct OnesweepSmem {
+    unsigned long long keys[kPart];
+    uint32_t vals[kPart];
+    uint32_t warp_hist[kSortWarps][kRadix + 1];  // bin kRadix collects padding keys
+    uint32_t local_start[kRadix];
+    uint32_t glob_off[kRadix];  // global position of local index j is glob_off[d] + j
+    uint32_t scan_warp[8];
+    uint32_t part;
+};
+
+__global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const unsigned long long* __restrict__ keys_in,
+                                                                const uint32_t* __restrict__ vals_in,
+                                                                unsigned long long* __restrict__ keys_out,
+                                                                uint32_t* __restrict__ vals_out,
+                                                                SortCtl* __restrict__ ctl, int pass,
+                                                                uint32_t* __restrict__ lookback,
+                                                                int32_t* __restrict__ status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    OnesweepSmem& S = *reinterpret_cast<OnesweepSmem*>(smem_raw);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint32_t n = ctl->n_sort;
+    const uint32_t n_parts = (n + kPart - 1) / kPart;
+    if (threadIdx.x == 0) S.part = atomicAdd(&ctl->part_counter[pass], 1u);
+    for (int k = threadIdx.x; k < kSortWarps * (kRadix + 1); k += kSortThreads) (&S.warp_hist[0][0])[k] = 0u;
+    __syncthreads();
+    const uint32_t part = S.part;
+    if (part >= n_parts) return;
+    const int shift = 8 * pass;
+    const uint32_t base = part * kPart;
+    const uint32_t valid = min((uint32_t)kPart, n - base);
+
+    // Load (warp-striped, coalesced) and rank within the warp per digit.
+    unsigned long long k_reg[kSortItems];
+    uint32_t v_reg[kSortItems];
+    uint32_t d_reg[kSortItems];
+    uint32_t r_reg[kSortItems];
+    const uint32_t lt_mask = (1u << lane) - 1u;
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+        const uint32_t idx = (uint32_t)wid * (32 * kSortItems) + j * 32 + lane;
+        const bool ok = idx < valid;
+        k_reg[j] = ok ? keys_in[base + idx] : 0ull;
+        v_reg[j] = ok ? vals_in[base + idx] : 0u;
+        d_reg[j] = ok ? (uint32_t)((k_reg[j] >> shift) & 0xff) : (uint32_t)kRadix;
+    }
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+        const uint32_t d = d_reg[j];
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t cnt = S.warp_hist[wid][d];
+        __syncwarp();
+        const int leader = 31 - __clz(peers);
+        if (lane == leader) S.warp_hist[wid][d] = cnt + __popc(peers);
+        __syncwarp();
+        r_reg[j] = cnt + __popc(peers & lt_mask);
+    }
+    __syncthreads();
+
+    // Per digit: prefix over warps, block count, block-local digit start.
+    const int d = threadIdx.x;  // kSortThreads == kRadix
+    uint32_t dcount = 0;
+    for (int w = 0; w < kSortWarps; ++w) {
+        const uint32_t c = S.warp_hist[w][d];
+        S.warp_hist[w][d] = dcount;
+        dcount += c;
+    }
+    // publish this partition's aggregate before looking back
+    uint32_t* lb = lookback;  // this pass's table
+    if (part == 0) {
+        atomicExch(&lb[d], kFlagInc | dcount);
+    } else {
+        atomicExch(&lb[(size_t)part * kRadix + d], kFlagAgg | dcount);
+    }
+    uint32_t tot;
+    const uint32_t lstart = block_excl_scan(dcount, S.scan_warp, tot);
+    S.local_start[d] = lstart;
+
+    // decoupled look-back over earlier partitions for digit d
+    uint32_t excl = 0;
+    if (part > 0) {
+        int p = (int)part - 1;
+        int spins = 0;
+        while (p >= 0) {
+            const uint32_t f = *((volatile uint32_t*)&lb[(size_t)p * kRadix + d]);
+            if (f & kFlagInc) {
+                excl += f & kValMask;
+                break;
+            }
+            if (f & kFlagAgg) {
+                excl += f & kValMask;
+                --p;
+                continue;
+            }
+            if (++spins > kSpinLimit) {
+                atomicExch(status, GSFIT_ERR_TIMEOUT);
+                break;
+            }
+            __nanosleep(100);
+        }
+        atomicExch(&lb[(size_t)part * kRadix + d], kFlagInc | (excl + dcount));
+    }
+    // global exclusive offset of digit d over all keys of this pass
+    uint32_t htot;
+    const uint32_t gexcl = block_excl_scan(ctl->hist[pass][d], S.scan_warp, htot);
+    S.glob_off[d] = gexcl + excl - lstart;
+    __syncthreads();
+
+    // scatter into shared memory in digit order (stable: warp, item, lane order)
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+        const uint32_t dd = d_reg[j];
+        if (dd < (uint32_t)kRadix) {
+            const uint32_t pos = S.local_start[dd] + S.warp_hist[wid][dd] + r_reg[j];
+            S.keys[pos] = k_reg[j];
+            S.vals[pos] = v_reg[j];
+        }
+    }
+    __syncthreads();
+    // write runs of equal digits to consecutive global addresses
+    for (uint32_t j = threadIdx.x; j < valid; j += kSortThreads) {
+        const unsigned long long key = S.keys[j];
+        const uint32_t dd = (uint32_t)((key >> shift) & 0xff);
+        const uint32_t o = S.glob_off[dd] + j;
+        if (o < n) {  // always true unless a look-back wait ran out
+            keys_out[o] = key;
+            vals_out[o] = S.vals[j];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) ranges_kernel(const unsigned long long* __restrict__ keys,
+                                                     const SortCtl* __restrict__ ctl,
+                                                     uint32_t* __restrict__ ranges, uint32_t total_tiles) {
+    const uint32_t n = ctl->n_sort;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+        const uint32_t t = (uint32_t)(keys[k] >> 32);
+        if (t >= total_tiles) continue;  // only after a failed sort
+        if (k == 0 || (uint32_t)(keys[k - 1] >> 32) != t) ranges[2 * (size_t)t] = (uint32_t)k;
+        if (k + 1 == n || (uint32_t)(keys[k + 1] >> 32) != t) ranges[2 * (size_t)t + 1] = (uint32_t)(k + 1);
+    }
+}
+
+inline size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct SortLayout {
+    size_t block_sums, ctl, lookback, keys_alt, vals_alt, total;
+    int n_blocks, n_passes;
+    long long max_parts;
+};
+
+int passes_for(int total_tiles) {
+    int bits = 0;
+    while ((1ll << bits) < (long long)total_tiles) ++bits;  // tile ids 0 .. total_tiles-1
+    return 4 + (bits + 7) / 8;
+}
+
+SortLayout layout(long long n_rec, long long capacity, int total_tiles) {
+    SortLayout L;
+    L.n_blocks = (int)((n_rec + kScanChunk - 1) / kScanChunk);
+    L.n_passes = passes_for(total_tiles);
+    L.max_parts = (capacity + kPart - 1) / kPart;
+    size_t o = 0;
+    L.block_sums = o; o = align_up(o + sizeof(uint32_t) * (size_t)(L.n_blocks > 0 ? L.n_blocks : 1));
+    L.ctl = o; o = align_up(o + sizeof(SortCtl));
+    L.lookback = o; o = align_up(o + sizeof(uint32_t) * (size_t)L.n_passes * (size_t)(L.max_parts > 0 ? L.max_parts : 1) * kRadix);
+    L.keys_alt = o; o = align_up(o + sizeof(unsigned long long) * (size_t)(capacity > 0 ? capacity : 1));
+    L.vals_alt = o; o = align_up(o + sizeof(uint32_t) * (size_t)(capacity > 0 ? capacity : 1));
+    L.total = o;
+    return L;
+}
+
+// Opt-in to more than 48 KB of dynamic shared memory, once per device.
+int enable_onesweep_smem(size_t smem) {
+    static bool done[64] = {false};
+    int dev = 0;
+    GSFIT_CUDA_CHECK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return GSFIT_ERR_CUDA;
+    if (!done[dev]) {
+        GSFIT_CUDA_CHECK(cudaFuncSetAttribute(onesweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        done[dev] = true;
+    }
+    return GSFIT_OK;
+}
+
+}  // namespace
+
+bool valid_proj(const gsfit_proj* p);
+
+}  // namespace gsfit
+
+using namespace gsfit;
+
+extern "C" size_t gsfit_bin_sort_workspace_size(int64_t n_records, int64_t capacity, int32_t total_tiles) {
+    if (n_records < 0 || capacity < 0 || total_tiles < 1) return 0;
+    return layout(n_records, capacity, total_tiles).total;
+}
+
+extern "C" int gsfit_bin_sort(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_views, int32_t n,
+                              int32_t total_tiles, void* ws, size_t ws_bytes, uint64_t* keys, uint32_t* vals,
+                              int64_t capacity, uint32_t* n_instances, uint32_t* ranges, int32_t* status,
+                              cudaStream_t stream) {
+    if (!valid_proj(proj) || !cams || n_views < 1 || n_views > GSFIT_MAX_VIEWS || n < 1 || total_tiles < 1 ||
+        !ws || !keys || !vals || !n_instances || !ranges || !status || capacity < 1 ||
+        capacity >= (int64_t)kFlagAgg)
+        return GSFIT_ERR_INVALID_ARG;
+    const long long n_rec = (long long)n * n_views;
+    const SortLayout L = layout(n_rec, capacity, total_tiles);
+    if (ws_bytes < L.total || (reinterpret_cast<uintptr_t>(ws) % 256) != 0) return GSFIT_ERR_INVALID_ARG;
+    char* base = static_cast<char*>(ws);
+    uint32_t* block_sums = reinterpret_cast<uint32_t*>(base + L.block_sums);
+    SortCtl* ctl = reinterpret_cast<SortCtl*>(base + L.ctl);
+    uint32_t* lookback = reinterpret_cast<uint32_t*>(base + L.lookback);
+    unsigned long long* keys_alt = reinterpret_cast<unsigned long long*>(base + L.keys_alt);
+    uint32_t* vals_alt = reinterpret_cast<uint32_t*>(base + L.vals_alt);
+    unsigned long long* keys_out = reinterpret_cast<unsigned long long*>(keys);
+
+    // Pairs are emitted into the buffer that, after an odd or even number of
+    // ping-pong passes, leaves the sorted result in keys/vals.
+    const bool emit_to_alt = (L.n_passes % 2) == 1;
+    unsigned long long* k_cur = emit_to_alt ? keys_alt : keys_out;
+    uint32_t* v_cur = emit_to_alt ? vals_alt : vals;
+    unsigned long long* k_nxt = emit_to_alt ? keys_out : keys_alt;
+    uint32_t* v_nxt = emit_to_alt ? vals : vals_alt;
+
+    reduce_kernel<<<L.n_blocks, kScanThreads, 0, stream>>>(proj->tiles, n_rec, block_sums);
+    GSFIT_LAUNCH_CHECK();
+    scan_kernel<<<1, 1024, 0, stream>>>(block_sums, L.n_blocks, ctl, n_instances, capacity, status);
+    GSFIT_LAUNCH_CHECK();
+    emit_kernel<<<L.n_blocks, kScanThreads, sizeof(gsfit_camera) * n_views, stream>>>(
+        proj->tiles, reinterpret_cast<const float4*>(proj->xyd), n, n_views, cams, block_sums, ctl, k_cur, v_cur);
+    GSFIT_LAUNCH_CHECK();
+    const long long lb_words = (long long)L.n_passes * L.max_parts * kRadix;
+    hist_kernel<<<kHistBlocks, 256, 0, stream>>>(k_cur, ctl, L.n_passes, lookback, lb_words, ranges,
+                                                 2ll * total_tiles);
+    GSFIT_LAUNCH_CHECK();
+    const size_t smem = sizeof(OnesweepSmem);
+    const int rc = enable_onesweep_smem(smem);
+    if (rc != GSFIT_OK) return rc;
+    for (int p = 0; p < L.n_passes; ++p) {
+        onesweep_kernel<<<(unsigned)L.max_parts, kSortThreads, smem, stream>>>(
+            k_cur, v_cur, k_nxt, v_nxt, ctl, p, lookback + (size_t)p * L.max_parts * kRadix, status);
+        GSFIT_LAUNCH_CHECK();
+        std::swap(k_cur, k_nxt);
+        std::swap(v_cur, v_nxt);
+    }
+    ranges_kernel<<<kHistBlocks, 256, 0, stream>>>(keys_out, ctl, ranges, (uint32_t)total_tiles);
+    GSFIT_LAUNCH_CHECK();
+    return GSFIT_OK;
+}

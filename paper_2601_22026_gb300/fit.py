@@ -1,0 +1,215 @@
+"""Fit-step driver: device buffers for one Gaussian set and one view batch,
+the iteration project -> bin/sort -> render -> loss -> adjoint -> Adam as
+calls into libgsfit, CUDA-graph capture of the whole iteration, and a
+torch.autograd.Function around render.
+
+PyTorch provides device memory, streams and graphs only; every arithmetic
+step runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import torch
+
+from . import gsfit as G
+
+# 3DGS learning rates; the paper raises scale, opacity and colour by ~50% for
+# its abbreviated regeneration run (Section 4.2).
+DEFAULT_LR = dict(lr_means=1.6e-4, lr_quats=1e-3, lr_scales=5e-3, lr_opacity=5e-2, lr_sh_dc=2.5e-3)
+
+
+def boosted_lr(scale: float = 1.5) -> dict:
+    lr = dict(DEFAULT_LR)
+    for k in ("lr_scales", "lr_opacity", "lr_sh_dc"):
+        lr[k] *= scale
+    return lr
+
+
+class FitState:
+    """All device buffers of the fit step for one scene and one view batch."""
+
+    def __init__(self, gaussians: dict, cams: dict, *, target_rgb=None, target_alpha=None, bg=None,
+                 capacity: int | None = None, lr: dict | None = None, eps: float = 1e-15,
+                 lam: float = 0.2, device: str = "cuda"):
+        self.device = device
+        self.n = int(gaussians["means"].shape[0])
+        self.sh_degree = int(round(gaussians["sh"].shape[1] ** 0.5)) - 1
+        self.n_planes = G.num_planes(self.sh_degree)
+        self.params = torch.from_numpy(G.pack_params(gaussians)).to(device).contiguous()
+        self.grads = torch.zeros_like(self.params)
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.step_count = torch.zeros(1, dtype=torch.int32, device=device)
+        self.lam = float(lam)
+        self.eps = float(eps)
+        self.lr = G.lr_table(self.sh_degree, **(lr or DEFAULT_LR))
+        self.loss_out = torch.zeros(1, dtype=torch.float32, device=device)
+        self.status = torch.zeros(1, dtype=torch.int32, device=device)
+        self.n_instances = torch.zeros(1, dtype=torch.int32, device=device)
+        self.set_cameras(cams, bg=bg)
+        if target_rgb is not None:
+            self.set_targets(target_rgb, target_alpha)
+        self.capacity = 0
+        self.ensure_capacity(capacity)
+        self.graph = None
+
+    # -- view batch -----------------------------------------------------
+    def set_cameras(self, cams: dict, bg=None) -> None:
+        self.table = G.camera_table(cams)
+        self.V = self.table.n_views
+        self.T = self.table.total_tiles
+        self.P = self.table.total_pixels
+        self.cams_dev = G.cameras_to_device(self.table, self.device)
+        dev, f32 = self.device, torch.float32
+        self.proj = G.ProjBuffers.allocate(self.V * self.n, dev)
+        self.rgb = torch.zeros(3 * self.P, dtype=f32, device=dev)
+        self.alpha = torch.zeros(self.P, dtype=f32, device=dev)
+        self.T_final = torch.zeros(self.P, dtype=f32, device=dev)
+        self.n_contrib = torch.zeros(self.P, dtype=torch.int32, device=dev)
+        self.dL_drgb = torch.zeros(3 * self.P, dtype=f32, device=dev)
+        self.dL_dalpha = torch.zeros(self.P, dtype=f32, device=dev)
+        self.target_rgb = torch.zeros(3 * self.P, dtype=f32, device=dev)
+        self.target_alpha = torch.zeros(self.P, dtype=f32, device=dev)
+        self.ranges = torch.zeros(2 * self.T, dtype=torch.int32, device=dev)
+        self.grad2d = torch.zeros(self.V * self.n * 12, dtype=f32, device=dev)
+        self.loss_ws = torch.zeros(G.gsfit_loss_workspace_size(self.V) // 4 + 1, dtype=f32, device=dev)
+        bgv = np.zeros((self.V, 3), np.float32) if bg is None else np.asarray(bg, np.float32).reshape(self.V, 3)
+        self.bg = torch.from_numpy(bgv.copy()).to(dev)
+        self.graph = None
+
+    def set_targets(self, target_rgb, target_alpha) -> None:
+        self.target_rgb.copy_(torch.as_tensor(np.asarray(target_rgb, np.float32)).reshape(-1))
+        self.target_alpha.copy_(torch.as_tensor(np.asarray(target_alpha, np.float32)).reshape(-1))
+
+    def set_bg(self, bg) -> None:
+        self.bg.copy_(torch.as_tensor(np.asarray(bg, np.float32)).reshape(self.V, 3))
+
+    # -- capacity -------------------------------------------------------
+    def count_instances(self) -> int:
+        """Pairs the current parameters produce (projects once; syncs)."""
+        G.gsfit_project(self.params, self.n, self.sh_degree, self.cams_dev, self.V, self.proj)
+        return int(self.proj.tiles.to(torch.int64).sum().item())
+
+    def ensure_capacity(self, capacity: int | None = None, slack: float = 1.5) -> None:
+        need = capacity if capacity is not None else max(1024, int(math.ceil(self.count_instances() * slack)))
+        if need <= self.capacity:
+            return
+        self.capacity = int(need)
+        dev = self.device
+        self.keys = torch.empty(self.capacity, dtype=torch.int64, device=dev)
+        self.vals = torch.empty(self.capacity, dtype=torch.int32, device=dev)
+        ws_bytes = G.gsfit_bin_sort_workspace_size(self.V * self.n, self.capacity, self.T)
+        self.sort_ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+        self.graph = None
+
+    def check_status(self) -> int:
+        """Reads (and clears) the device status word; syncs."""
+        s = int(self.status.item())
+        if s != 0:
+            self.status.zero_()
+        return s
+
+    # -- stages ---------------------------------------------------------
+    def project(self, stream=None):
+        G.gsfit_project(self.params, self.n, self.sh_degree, self.cams_dev, self.V, self.proj, stream)
+
+    def bin_sort(self, stream=None):
+        G.gsfit_bin_sort(self.proj, self.cams_dev, self.V, self.n, self.T, self.sort_ws, self.keys, self.vals,
+                         self.capacity, self.n_instances, self.ranges, self.status, stream)
+
+    def render_fwd(self, stream=None):
+        G.gsfit_render_fwd(self.proj, self.cams_dev, self.V, self.n, self.T, self.vals, self.ranges, self.bg,
+                           self.rgb, self.alpha, self.T_final, self.n_contrib, stream)
+
+    def loss(self, stream=None):
+        G.gsfit_loss(self.cams_dev, self.V, self.rgb, self.alpha, self.target_rgb, self.target_alpha, self.bg,
+                     self.lam, self.dL_drgb, self.dL_dalpha, self.loss_out, self.loss_ws, stream)
+
+    def render_bwd(self, stream=None):
+        G.gsfit_render_bwd(self.params, self.n, self.sh_degree, self.proj, self.cams_dev, self.V, self.T,
+                           self.vals, self.ranges, self.bg, self.T_final, self.n_contrib, self.dL_drgb,
+                           self.dL_dalpha, self.grad2d, self.grads, stream)
+
+    def adam(self, stream=None):
+        G.gsfit_adam_step(self.params, self.grads, self.m, self.v, self.n, self.n_planes, self.lr, 0.9, 0.999,
+                          self.eps, self.step_count, stream)
+
+    def forward(self, stream=None):
+        self.project(stream)
+        self.bin_sort(stream)
+        self.render_fwd(stream)
+
+    def step(self, stream=None):
+        """One fit iteration (no host synchronisation)."""
+        self.forward(stream)
+        self.loss(stream)
+        self.render_bwd(stream)
+        self.adam(stream)
+
+    STAGES = ("project", "bin_sort", "render_fwd", "loss", "render_bwd", "adam")
+
+    # -- graphs ---------------------------------------------------------
+    def capture(self, warmup: int = 1):
+        """Captures one iteration in a CUDA graph (replay with .replay())."""
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            for _ in range(warmup):
+                self.step(s)
+        torch.cuda.current_stream().wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.step()
+        self.graph = g
+        return g
+
+    def replay(self):
+        if self.graph is None:
+            self.capture()
+        self.graph.replay()
+
+    def reset_optimizer(self):
+        """Discards the optimiser state (restart of the refinement, Section 4.2)."""
+        self.m.zero_()
+        self.v.zero_()
+        self.step_count.zero_()
+
+    # -- host views -----------------------------------------------------
+    def gaussians(self) -> dict:
+        return G.unpack_params(self.params.cpu().numpy(), self.sh_degree)
+
+    def gradients(self) -> dict:
+        return G.unpack_params(self.grads.cpu().numpy(), self.sh_degree)
+
+
+class GsfitRender(torch.autograd.Function):
+    """Differentiable render of a FitState's view batch.
+
+    forward: project + bin/sort + composite; keeps the projected records, the
+    sorted lists, T_final and n_contrib (no per-(pixel, Gaussian) state).
+    backward: the hand-written adjoint (recomputes per-pixel transmittance
+    from T_final and n_contrib) chained through the projection.
+    """
+
+    @staticmethod
+    def forward(ctx, params, state: FitState):
+        if params.data_ptr() != state.params.data_ptr():
+            state.params.copy_(params.detach())
+        state.forward()
+        ctx.state = state
+        ctx.save_for_backward(state.T_final, state.n_contrib)
+        return state.rgb.clone(), state.alpha.clone()
+
+    @staticmethod
+    def backward(ctx, g_rgb, g_alpha):
+        st = ctx.state
+        st.dL_drgb.copy_(g_rgb if g_rgb is not None else torch.zeros_like(st.dL_drgb))
+        st.dL_dalpha.copy_(g_alpha if g_alpha is not None else torch.zeros_like(st.dL_dalpha))
+        st.render_bwd()
+        return st.grads.clone(), None
+
+
+def render(params, state: FitState):
+    return GsfitRender.apply(params, state)

@@ -1,0 +1,108 @@
+"""The C-ABI library: builds, loads, exports every symbol include/gsfit.h
+declares, and its host-side helpers behave (no GPU needed: nothing here
+launches a kernel)."""
+import ctypes
+import re
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+from paper_2601_22026_gb300 import _build
+from paper_2601_22026_gb300 import gsfit as G
+
+ROOT = Path(__file__).resolve().parents[1]
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return G.load()
+
+
+def declared_functions():
+    text = (ROOT / "include" / "gsfit.h").read_text()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gsfit_\w+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 12
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(G.SIGNATURES), "binding and header disagree"
+
+
+def test_abi_version_and_status_strings(lib):
+    assert lib.gsfit_abi_version() == 1
+    assert lib.gsfit_status_string(G.GSFIT_ERR_CAPACITY) == b"instance capacity exceeded"
+    assert lib.gsfit_status_string(G.GSFIT_ERR_TIMEOUT) == b"bounded device wait ran out"
+
+
+def test_num_planes(lib):
+    for deg, expect in [(0, 4), (1, 6), (2, 10), (3, 15)]:
+        assert lib.gsfit_num_planes(deg) == expect == G.num_planes(deg)
+    assert lib.gsfit_num_planes(4) == G.GSFIT_ERR_INVALID_ARG
+
+
+def test_camera_layout_matches_oracle_tiles(lib):
+    cams = scenes.periphery_batch_cameras(7)
+    table = G.camera_table(cams)
+    assert table.total_tiles == oracle.total_tiles(cams, 16)
+    assert table.total_pixels == scenes.num_pixels(cams)
+    off = oracle.pixel_offsets(cams)
+    toff = 0
+    for v in range(table.n_views):
+        c = table.host[v]
+        assert c.pixel_offset == off[v]
+        assert c.tile_offset == toff
+        toff += (-(-c.width // 16)) * (-(-c.height // 16))
+
+
+def test_pack_roundtrip_and_lr_table():
+    for deg in range(4):
+        gs = scenes.random_gaussians(37, deg, 3)
+        P = G.pack_params(gs)
+        assert P.shape == (G.num_planes(deg), 37, 4)
+        back = G.unpack_params(P, deg)
+        for k in gs:
+            np.testing.assert_array_equal(back[k], gs[k])
+        L = G.lr_table(deg, 1.0, 2.0, 3.0, 4.0, 5.0)
+        assert L[0, 3] == 4.0 and L[2, 3] == 0.0 and L[1, 0] == 2.0
+        K3 = 3 * (deg + 1) ** 2
+        flat = L[3:].reshape(-1)
+        assert np.all(flat[:3] == 5.0) and np.all(flat[3:K3] == 0.25) and np.all(flat[K3:] == 0)
+
+
+def test_invalid_arguments_rejected_on_host(lib):
+    g = G.Gaussians(None, 10, 0)
+    p = G.Proj(None, None, None, None)
+    assert lib.gsfit_project(ctypes.byref(g), None, 1, ctypes.byref(p), None) == G.GSFIT_ERR_INVALID_ARG
+    g = G.Gaussians(16, 10, 7)  # bad degree
+    fake = 256
+    p = G.Proj(fake, fake, fake, fake)
+    assert lib.gsfit_project(ctypes.byref(g), fake, 1, ctypes.byref(p), None) == G.GSFIT_ERR_INVALID_ARG
+    g = G.Gaussians(fake, 10, 0)
+    assert lib.gsfit_project(ctypes.byref(g), fake, 0, ctypes.byref(p), None) == G.GSFIT_ERR_INVALID_ARG
+    assert lib.gsfit_project(ctypes.byref(g), fake, 257, ctypes.byref(p), None) == G.GSFIT_ERR_INVALID_ARG
+    # capacity at or above 2^30 and undersized workspaces are refused before any launch
+    assert lib.gsfit_bin_sort(ctypes.byref(p), fake, 1, 10, 4, fake, 1 << 40, fake, fake, 1 << 30, fake, fake,
+                              fake, None) == G.GSFIT_ERR_INVALID_ARG
+    need = lib.gsfit_bin_sort_workspace_size(10, 1000, 4)
+    assert need > 0
+    assert lib.gsfit_bin_sort(ctypes.byref(p), fake, 1, 10, 4, fake, need - 1, fake, fake, 1000, fake, fake,
+                              fake, None) == G.GSFIT_ERR_INVALID_ARG
+    assert lib.gsfit_adam_step(fake, fake, fake, fake, 10, 17, None, 0.9, 0.999, 1e-15, fake,
+                               None) == G.GSFIT_ERR_INVALID_ARG
+    assert lib.gsfit_loss_workspace_size(0) == 0
+
+
+def test_workspace_size_grows_with_capacity(lib):
+    a = lib.gsfit_bin_sort_workspace_size(1000, 10_000, 64)
+    b = lib.gsfit_bin_sort_workspace_size(1000, 20_000, 64)
+    c = lib.gsfit_bin_sort_workspace_size(1000, 20_000, 70_000)  # more tile bits: one more pass
+    assert 0 < a < b < c
+    assert b - a >= 10_000 * 12
