@@ -227,6 +227,31 @@ int gsfit_loss(const gsfit_camera* cams, int32_t n_views, const float* rgb, cons
                cudaStream_t stream);
 
 /*
+ * gsfit_loss_noalloc -- gsfit_loss for callers that cannot allocate device
+ * memory. The paper has no counterpart; this is a deployment convenience.
+ *   Some callers must not call cudaMalloc on their path: a real-time frame
+ *   loop, where an allocation can synchronise the device and stall the frame,
+ *   or a plug-in inside an application that owns every device allocation
+ *   (its own pool and accounting). They still pass inputs and outputs, but no
+ *   workspace: the per-view accumulators live in a fixed array inside this
+ *   library (3 * GSFIT_MAX_VIEWS floats = 3 KB per GPU, held by every GPU that
+ *   loads the library until the process exits).
+ *   Same arguments and results as gsfit_loss without ws / ws_bytes.
+ *   n_views above GSFIT_MAX_VIEWS (256) is rejected with
+ *   GSFIT_ERR_INVALID_ARG. The first call on a device looks up the array's
+ *   device address (with that device current) and caches it; make that first
+ *   call before any stream capture. Every call clears the accumulators it uses
+ *   before using them. All calls share the one array: calls whose executions
+ *   overlap on the GPU (different streams, or graphs replayed concurrently)
+ *   race on it and may return wrong loss values; serialise them.
+ * Errors: GSFIT_ERR_INVALID_ARG, GSFIT_ERR_CUDA (including a failed address
+ *   lookup).
+ */
+int gsfit_loss_noalloc(const gsfit_camera* cams, int32_t n_views, const float* rgb, const float* alpha,
+                       const float* target_rgb, const float* target_alpha, const float* bg, float lambda,
+                       float* dL_drgb, float* dL_dalpha, float* loss_out, cudaStream_t stream);
+
+/*
  * gsfit_render_bwd -- adjoint of gsfit_render_fwd and gsfit_project.
  *   Per pixel, back to front from n_contrib - 1, recovering T_i = T_{i+1} /
  *   (1 - alpha_i) from T_final (no per-(pixel, Gaussian) state is stored):

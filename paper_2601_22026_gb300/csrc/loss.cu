@@ -263,3 +263,65 @@ extern "C" int gsfit_loss(const gsfit_camera* cams, int32_t n_views, const float
     }
     return GSFIT_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant (no counterpart in the paper): the same kernels with
+// the per-view accumulators in a fixed device array of this library, for
+// callers that cannot allocate device memory (a real-time frame loop, a
+// plug-in whose host application owns all device allocations).
+// ---------------------------------------------------------------------------
+
+namespace gsfit {
+namespace {
+
+constexpr int kNoAllocMaxViews = GSFIT_MAX_VIEWS;
+
+// 3 accumulators per view: sum|x - y|, sum SSIM, sum|A - A*| (3 KB). Host code
+// must not use this name as a pointer: it is a host-side stand-in; the device
+// address comes from cudaGetSymbolAddress below.
+static __device__ __align__(256) float g_loss_noalloc_acc[3 * kNoAllocMaxViews];
+
+// Device address of g_loss_noalloc_acc, looked up once per device with that
+// device current.
+int noalloc_acc_address(int dev, float** out) {
+    static float* cached[64] = {nullptr};
+    if (dev < 0 || dev >= 64) return GSFIT_ERR_CUDA;
+    if (!cached[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_loss_noalloc_acc) != cudaSuccess || !p) return GSFIT_ERR_CUDA;
+        cached[dev] = static_cast<float*>(p);
+    }
+    *out = cached[dev];
+    return GSFIT_OK;
+}
+
+}  // namespace
+}  // namespace gsfit
+
+extern "C" int gsfit_loss_noalloc(const gsfit_camera* cams, int32_t n_views, const float* rgb, const float* alpha,
+                                  const float* target_rgb, const float* target_alpha, const float* bg,
+                                  float lambda, float* dL_drgb, float* dL_dalpha, float* loss_out,
+                                  cudaStream_t stream) {
+    if (!cams || n_views < 1 || n_views > kNoAllocMaxViews || !rgb || !alpha || !target_rgb || !target_alpha ||
+        !bg || !dL_drgb || !dL_dalpha)
+        return GSFIT_ERR_INVALID_ARG;
+    int dev = 0;
+    GSFIT_CUDA_CHECK(cudaGetDevice(&dev));
+    float* acc = nullptr;
+    const int rc = noalloc_acc_address(dev, &acc);
+    if (rc != GSFIT_OK) return rc;
+    const size_t smem = sizeof(LossSmem);
+    GSFIT_CUDA_CHECK(cudaFuncSetAttribute(loss_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int sms = 0;
+    GSFIT_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // the array keeps the previous call's sums: clear this call's part first
+    GSFIT_CUDA_CHECK(cudaMemsetAsync(acc, 0, sizeof(float) * 3 * n_views, stream));
+    loss_kernel<<<2 * sms, kLossThreads, smem, stream>>>(cams, n_views, rgb, alpha, target_rgb, target_alpha, bg,
+                                                         lambda, dL_drgb, dL_dalpha, acc);
+    GSFIT_LAUNCH_CHECK();
+    if (loss_out) {
+        loss_finalize_kernel<<<1, 32, 0, stream>>>(cams, n_views, lambda, acc, loss_out);
+        GSFIT_LAUNCH_CHECK();
+    }
+    return GSFIT_OK;
+}

@@ -58,6 +58,7 @@ SIGNATURES = {
     "gsfit_render_fwd": (ctypes.c_int, [_P, _P, _i32, _i32, _i32, _P, _P, _P, _P, _P, _P, _P, _P]),
     "gsfit_loss_workspace_size": (_size, [_i32]),
     "gsfit_loss": (ctypes.c_int, [_P, _i32, _P, _P, _P, _P, _P, _f32, _P, _P, _P, _P, _size, _P]),
+    "gsfit_loss_noalloc": (ctypes.c_int, [_P, _i32, _P, _P, _P, _P, _P, _f32, _P, _P, _P, _P]),
     "gsfit_render_bwd": (ctypes.c_int, [_P, _P, _P, _i32, _i32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "gsfit_adam_step": (ctypes.c_int, [_P, _P, _P, _P, _i32, _i32, _P, _f32, _f32, _f32, _P, _P]),
 }
@@ -264,6 +265,18 @@ def gsfit_loss(cams_dev, n_views, rgb, alpha, target_rgb, target_alpha, bg, lam,
                              _ptr(target_alpha), _ptr(bg), float(lam), _ptr(dL_drgb), _ptr(dL_dalpha),
                              _ptr(loss_out), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)),
            "gsfit_loss")
+
+
+def gsfit_loss_noalloc(cams_dev, n_views, rgb, alpha, target_rgb, target_alpha, bg, lam, dL_drgb, dL_dalpha,
+                       loss_out, stream=None):
+    """gsfit_loss without a workspace, for callers that cannot allocate device
+    memory; its accumulators live in a fixed array inside the library (make
+    the first call on a device before any stream capture; overlapping calls
+    race on the shared array)."""
+    _check(load().gsfit_loss_noalloc(_ptr(cams_dev), n_views, _ptr(rgb), _ptr(alpha), _ptr(target_rgb),
+                                     _ptr(target_alpha), _ptr(bg), float(lam), _ptr(dL_drgb), _ptr(dL_dalpha),
+                                     _ptr(loss_out), _stream(stream)),
+           "gsfit_loss_noalloc")
 
 
 def gsfit_render_bwd(params, n, sh_degree, proj: ProjBuffers, cams_dev, n_views, total_tiles, vals, ranges, bg,
