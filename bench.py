@@ -108,10 +108,10 @@ class ClockSampler:
 # workload
 # ---------------------------------------------------------------------------
 
-def build_state(seed: int = 0):
+def build_state(seed: int = 0, n: int = 1_000_000, crops: int = 14):
     import torch
     from paper_2601_22026_gb300.fit import FitState, boosted_lr
-    sc = scenes.batched_periphery_scene(seed)
+    sc = scenes.batched_periphery_scene(seed, n=n, n_crops=crops)
     cams = sc["cameras"]
     V = len(cams["width"])
     tgt = FitState(sc["target_gaussians"], cams, bg=np.zeros((V, 3), np.float32))
@@ -261,7 +261,7 @@ def run_reference(args) -> None:
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    sc = scenes.batched_periphery_scene(0)
+    sc = scenes.batched_periphery_scene(0, n=args.gaussians, n_crops=args.crops)
     vals = []
     for _ in range(max(1, args.warmup)):
         oracle_sample(sc)
@@ -288,6 +288,9 @@ def main() -> None:
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--no-plain", action="store_true", help="skip the single-view comparison")
+    ap.add_argument("--gaussians", type=int, default=1_000_000,
+                    help="smaller sets are for profiling captures only; the metric is quoted at 1M")
+    ap.add_argument("--crops", type=int, default=14, help="foveal crops per batch (profiling captures only)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -306,7 +309,7 @@ def main() -> None:
     import paper_2601_22026_gb300 as pkg
     pkg.build()
 
-    sc, st = build_state(0)
+    sc, st = build_state(0, args.gaussians, args.crops)
     V = st.V
     bg_table = torch.from_numpy(scenes.backgrounds(V, 3, n_steps=args.warmup + args.steps)).cuda()
     st.capture()
