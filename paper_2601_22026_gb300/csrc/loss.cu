@@ -17,17 +17,20 @@ namespace gsfit {
 namespace {
 
 constexpr int kOut = 32;             // output tile edge
-constexpr int kR1 = kOut + 10;       // moments / partials region (halo 5)
-constexpr int kR2 = kOut + 20;       // input region (halo 10)
+constexpr int kR1 = kOut + 10;       // moments / partials region (halo 5): 42
+constexpr int kR2 = kOut + 20;       // input region (halo 10): 52
+constexpr int kStrip = 4;            // outputs per thread along a pass (register blocking)
+constexpr int kR2p = 56;             // input rows / columns padded so strips never leave the array
+constexpr int kR1p = 44;             // moment rows / columns padded to whole strips
 constexpr int kLossThreads = 256;
 constexpr float kC1 = 0.01f * 0.01f;
 constexpr float kC2 = 0.03f * 0.03f;
 
 struct LossSmem {
-    float x[kR2][kR2];
-    float y[kR2][kR2];
-    float h[5][kR2][kR1];   // horizontal pass; later reused for the partials
-    float m[5][kR1][kR1];   // moments; later reused for the horizontal pass of the partials
+    float x[kR2][kR2p];         // render, input region (zero outside the image and in the padding)
+    float y[kR2][kR2p];         // target composited over the background
+    float h[5][kR2p][kR1p];     // horizontal pass of x, y, x^2, y^2, xy; later the SSIM partials
+    float m[5][kR1p][kR1];      // moments; later the horizontal pass of the partials
 };
 
 // Normalised 11-tap Gaussian, sigma = 1.5.
@@ -43,7 +46,23 @@ __device__ __forceinline__ void window(float w[11]) {
     for (int i = 0; i < 11; ++i) w[i] /= s;
 }
 
-__global__ void __launch_bounds__(kLossThreads) loss_kernel(
+// One pass of the 11-tap window over a strip of kStrip consecutive outputs:
+// the kStrip + 10 inputs are read once into registers.
+template <int STRIDE>
+__device__ __forceinline__ void strip11(const float* src, const float w[11], float out[kStrip]) {
+    float in[kStrip + 10];
+#pragma unroll
+    for (int k = 0; k < kStrip + 10; ++k) in[k] = src[k * STRIDE];
+#pragma unroll
+    for (int o = 0; o < kStrip; ++o) {
+        float a = 0.f;
+#pragma unroll
+        for (int j = 0; j < 11; ++j) a += w[j] * in[o + j];
+        out[o] = a;
+    }
+}
+
+__global__ void __launch_bounds__(kLossThreads, 2) loss_kernel(
     const gsfit_camera* __restrict__ cams_g, int n_views, const float* __restrict__ rgb,
     const float* __restrict__ alpha, const float* __restrict__ t_rgb, const float* __restrict__ t_alpha,
     const float* __restrict__ bg, float lambda, float* __restrict__ g_rgb, float* __restrict__ g_alpha,
@@ -61,6 +80,8 @@ __global__ void __launch_bounds__(kLossThreads) loss_kernel(
         }
         s_item_off[n_views] = o;
     }
+    // zero the padding once: rows / columns beyond the region stay zero
+    for (int k = threadIdx.x; k < 5 * kR2p * kR1p; k += kLossThreads) (&S.h[0][0][0])[k] = 0.f;
     float w[11];
     window(w);
     __syncthreads();
@@ -84,52 +105,69 @@ __global__ void __launch_bounds__(kLossThreads) loss_kernel(
         const float bgc = bg[3 * v + ch];
         const float inv3PV = 1.0f / (3.0f * (float)P * (float)n_views);
 
-        // 1. inputs over the 52 x 52 region, zero outside the image
-        for (int k = tid; k < kR2 * kR2; k += kLossThreads) {
-            const int r = k / kR2, cidx = k - r * kR2;
-            const int gy = oy - 10 + r, gx = ox - 10 + cidx;
-            float xv = 0.f, yv = 0.f;
-            if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
-                const long long q = (long long)gy * W + gx;
-                xv = X[q];
-                yv = Yt[q] + (1.0f - At[q]) * bgc;
-            }
-            S.x[r][cidx] = xv;
-            S.y[r][cidx] = yv;
-        }
-        __syncthreads();
-        // 2. horizontal pass of x, y, x^2, y^2, xy: rows 0..51, columns 0..41
-        for (int k = tid; k < kR2 * kR1; k += kLossThreads) {
-            const int r = k / kR1, cidx = k - r * kR1;
-            float a = 0.f, b = 0.f, c = 0.f, d = 0.f, e = 0.f;
-#pragma unroll
-            for (int j = 0; j < 11; ++j) {
-                const float xv = S.x[r][cidx + j], yv = S.y[r][cidx + j];
-                a += w[j] * xv;
-                b += w[j] * yv;
-                c += w[j] * xv * xv;
-                d += w[j] * yv * yv;
-                e += w[j] * xv * yv;
-            }
-            S.h[0][r][cidx] = a; S.h[1][r][cidx] = b; S.h[2][r][cidx] = c; S.h[3][r][cidx] = d; S.h[4][r][cidx] = e;
-        }
-        __syncthreads();
-        // 3. vertical pass: moments on the 42 x 42 region
-        for (int k = tid; k < kR1 * kR1; k += kLossThreads) {
-            const int r = k / kR1, cidx = k - r * kR1;
-#pragma unroll
-            for (int f = 0; f < 5; ++f) {
-                float a = 0.f;
-#pragma unroll
-                for (int j = 0; j < 11; ++j) a += w[j] * S.h[f][r + j][cidx];
-                S.m[f][r][cidx] = a;
+        // 1. inputs over the 52 x 52 region (56 columns with zero padding);
+        //    thread (column tid % 64, first row tid / 64) walks rows 4 apart
+        {
+            const int cidx = tid & 63, gx = ox - 10 + cidx;
+            const bool col_ok = cidx < kR2 && gx >= 0 && gx < W;
+            for (int r = tid >> 6; r < kR2; r += kLossThreads / 64) {
+                const int gy = oy - 10 + r;
+                float xv = 0.f, yv = 0.f;
+                if (col_ok && gy >= 0 && gy < H) {
+                    const long long q = (long long)gy * W + gx;
+                    xv = X[q];
+                    yv = Yt[q] + (1.0f - At[q]) * bgc;
+                }
+                if (cidx < kR2p) {
+                    S.x[r][cidx] = xv;
+                    S.y[r][cidx] = yv;
+                }
             }
         }
         __syncthreads();
-        // 4. SSIM and its partials w.r.t. (mu_x, E[x^2], E[xy]) on the region;
-        //    zero outside the image (those windows do not exist).
+        // 2. horizontal pass of x, y, x^2, y^2, xy: 52 rows x 44 columns in strips of 4
+        for (int k = tid; k < kR2 * (kR1p / kStrip); k += kLossThreads) {
+            const int r = k / (kR1p / kStrip), c0 = (k - r * (kR1p / kStrip)) * kStrip;
+            float xin[kStrip + 10], yin[kStrip + 10], xx[kStrip + 10], yy[kStrip + 10], xy[kStrip + 10];
+#pragma unroll
+            for (int j = 0; j < kStrip + 10; ++j) {
+                xin[j] = S.x[r][c0 + j];
+                yin[j] = S.y[r][c0 + j];
+                xx[j] = xin[j] * xin[j];
+                yy[j] = yin[j] * yin[j];
+                xy[j] = xin[j] * yin[j];
+            }
+#pragma unroll
+            for (int o = 0; o < kStrip; ++o) {
+                float a = 0.f, b = 0.f, c = 0.f, d = 0.f, e = 0.f;
+#pragma unroll
+                for (int j = 0; j < 11; ++j) {
+                    a += w[j] * xin[o + j];
+                    b += w[j] * yin[o + j];
+                    c += w[j] * xx[o + j];
+                    d += w[j] * yy[o + j];
+                    e += w[j] * xy[o + j];
+                }
+                S.h[0][r][c0 + o] = a; S.h[1][r][c0 + o] = b; S.h[2][r][c0 + o] = c;
+                S.h[3][r][c0 + o] = d; S.h[4][r][c0 + o] = e;
+            }
+        }
+        __syncthreads();
+        // 3. vertical pass: moments on 44 x 42 (rows 42, 43 are padding) in strips of 4
+        for (int k = tid; k < 5 * kR1 * (kR1p / kStrip); k += kLossThreads) {
+            const int f = k / (kR1 * (kR1p / kStrip));
+            const int rem = k - f * (kR1 * (kR1p / kStrip));
+            const int cidx = rem % kR1, r0 = (rem / kR1) * kStrip;
+            float out[kStrip];
+            strip11<kR1p>(&S.h[f][r0][cidx], w, out);
+#pragma unroll
+            for (int o = 0; o < kStrip; ++o) S.m[f][r0 + o][cidx] = out[o];
+        }
+        __syncthreads();
+        // 4. SSIM and its partials w.r.t. (mu_x, E[x^2], E[xy]) on the 42 x 42
+        //    region; zero outside the image (those windows do not exist).
         float ssim_sum = 0.f;
-        float (*part)[kR2][kR1] = S.h;  // reuse: part[0..2][r][c] for r, c < 42
+        float (*part)[kR2p][kR1p] = S.h;  // reuse: part[0..2][r][c], r, c < 42
         for (int k = tid; k < kR1 * kR1; k += kLossThreads) {
             const int r = k / kR1, cidx = k - r * kR1;
             const int gy = oy - 5 + r, gx = ox - 5 + cidx;
@@ -140,10 +178,11 @@ __global__ void __launch_bounds__(kLossThreads) loss_kernel(
                 const float sxy = S.m[4][r][cidx] - mx * my;
                 const float A1 = 2.f * mx * my + kC1, A2 = 2.f * sxy + kC2;
                 const float B1 = mx * mx + my * my + kC1, B2 = sx + sy + kC2;
-                const float iB = 1.0f / (B1 * B2);
+                const float iB1 = 1.0f / B1, iB2 = 1.0f / B2;
+                const float iB = iB1 * iB2;
                 const float ss = A1 * A2 * iB;
-                dmu = (2.f * my * A2 - 2.f * my * A1) * iB - ss * (2.f * mx / B1 - 2.f * mx / B2);
-                dxx = -ss / B2;
+                dmu = 2.f * my * (A2 - A1) * iB - 2.f * mx * ss * (iB1 - iB2);
+                dxx = -ss * iB2;
                 dxy = 2.f * A1 * iB;
                 if (r >= 5 && r < 5 + kOut && cidx >= 5 && cidx < 5 + kOut) ssim_sum += ss;
             }
@@ -152,44 +191,45 @@ __global__ void __launch_bounds__(kLossThreads) loss_kernel(
             part[2][r][cidx] = dxy;
         }
         __syncthreads();
-        // 5. horizontal pass of the partials: rows 0..41, columns 0..31
-        float (*hp)[kR1][kR1] = S.m;  // reuse: hp[0..2][r][c] for r < 42, c < 32
-        for (int k = tid; k < kR1 * kOut; k += kLossThreads) {
-            const int r = k / kOut, cidx = k - r * kOut;
+        // 5. horizontal pass of the partials: 42 rows x 32 columns in strips of 4
+        float (*hp)[kR1p][kR1] = S.m;  // reuse: hp[0..2][r][c], r < 42, c < 32
+        for (int k = tid; k < 3 * kR1 * (kOut / kStrip); k += kLossThreads) {
+            const int f = k / (kR1 * (kOut / kStrip));
+            const int rem = k - f * (kR1 * (kOut / kStrip));
+            const int r = rem / (kOut / kStrip), c0 = (rem % (kOut / kStrip)) * kStrip;
+            float out[kStrip];
+            strip11<1>(&part[f][r][c0], w, out);
 #pragma unroll
-            for (int f = 0; f < 3; ++f) {
-                float a = 0.f;
-#pragma unroll
-                for (int j = 0; j < 11; ++j) a += w[j] * part[f][r][cidx + j];
-                hp[f][r][cidx] = a;
-            }
+            for (int o = 0; o < kStrip; ++o) hp[f][r][c0 + o] = out[o];
         }
         __syncthreads();
-        // 6. vertical pass onto the tile and the gradient
+        // 6. vertical pass onto the tile (one 4-pixel column strip per thread) and
+        //    the gradient
         float l1 = 0.f, la = 0.f;
-        for (int k = tid; k < kOut * kOut; k += kLossThreads) {
-            const int r = k / kOut, cidx = k - r * kOut;
-            const int gy = oy + r, gx = ox + cidx;
-            if (gy >= H || gx >= W) continue;
-            float cm = 0.f, cxx = 0.f, cxy = 0.f;
+        {
+            const int cidx = tid % kOut, r0 = (tid / kOut) * kStrip;  // 32 columns x 8 strips = 256
+            float cm[kStrip], cxx[kStrip], cxy[kStrip];
+            strip11<kR1>(&hp[0][r0][cidx], w, cm);
+            strip11<kR1>(&hp[1][r0][cidx], w, cxx);
+            strip11<kR1>(&hp[2][r0][cidx], w, cxy);
 #pragma unroll
-            for (int j = 0; j < 11; ++j) {
-                cm += w[j] * hp[0][r + j][cidx];
-                cxx += w[j] * hp[1][r + j][cidx];
-                cxy += w[j] * hp[2][r + j][cidx];
-            }
-            const float xv = S.x[r + 10][cidx + 10], yv = S.y[r + 10][cidx + 10];
-            const float dssim = cm + 2.f * xv * cxx + yv * cxy;
-            const float diff = xv - yv;
-            const float sg = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
-            l1 += fabsf(diff);
-            const long long q = (long long)gy * W + gx;
-            g_rgb[3ll * cam.pixel_offset + ch * P + q] = ((1.0f - lambda) * sg - lambda * dssim) * inv3PV;
-            if (ch == 0) {
-                const float da = alpha[cam.pixel_offset + q] - At[q];
-                la += fabsf(da);
-                g_alpha[cam.pixel_offset + q] =
-                    (da > 0.f ? 1.f : (da < 0.f ? -1.f : 0.f)) / ((float)P * (float)n_views);
+            for (int o = 0; o < kStrip; ++o) {
+                const int r = r0 + o;
+                const int gy = oy + r, gx = ox + cidx;
+                if (gy >= H || gx >= W) continue;
+                const float xv = S.x[r + 10][cidx + 10], yv = S.y[r + 10][cidx + 10];
+                const float dssim = cm[o] + 2.f * xv * cxx[o] + yv * cxy[o];
+                const float diff = xv - yv;
+                const float sg = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
+                l1 += fabsf(diff);
+                const long long q = (long long)gy * W + gx;
+                g_rgb[3ll * cam.pixel_offset + ch * P + q] = ((1.0f - lambda) * sg - lambda * dssim) * inv3PV;
+                if (ch == 0) {
+                    const float da = alpha[cam.pixel_offset + q] - At[q];
+                    la += fabsf(da);
+                    g_alpha[cam.pixel_offset + q] =
+                        (da > 0.f ? 1.f : (da < 0.f ? -1.f : 0.f)) / ((float)P * (float)n_views);
+                }
             }
         }
         // block sums of the loss terms
@@ -203,10 +243,11 @@ __global__ void __launch_bounds__(kLossThreads) loss_kernel(
         }
         __syncthreads();
         if (tid < 3) {
-            float s = 0.f;
-            for (int k = 0; k < kLossThreads / 32; ++k) s += s_red[tid][k];
-            atomicAdd(&acc[3 * v + tid], s);
+            float sacc = 0.f;
+            for (int k = 0; k < kLossThreads / 32; ++k) sacc += s_red[tid][k];
+            atomicAdd(&acc[3 * v + tid], sacc);
         }
+        // (rows 52..55 of h, the only padding the passes read, are never written)
         __syncthreads();
     }
 }

@@ -282,38 +282,54 @@ __global__ void __launch_bounds__(256) project_kernel(const float4* __restrict__
 // reads the per-(view, Gaussian) 2D gradients accumulated by the blend
 // adjoint (and zeroes them for the next iteration), chains them through the
 // projection and writes the summed parameter gradients once.
+constexpr int kProjBwdThreads = 256;
+
+// Accumulator k of this thread's SH gradient; [k][thread] layout, so a warp's
+// accesses hit 32 different banks.
+__device__ __forceinline__ float& dsh_acc(float* s_dsh, int k) { return s_dsh[k * kProjBwdThreads + threadIdx.x]; }
+
 template <int DEG>
-__global__ void __launch_bounds__(256) project_bwd_kernel(const float4* __restrict__ P, int n,
-                                                          const gsfit_camera* __restrict__ cams_g, int n_views,
-                                                          const float4* __restrict__ xyd,
-                                                          const float4* __restrict__ conic,
-                                                          const float4* __restrict__ rgbm,
-                                                          float4* __restrict__ grad2d, float4* __restrict__ G) {
-    extern __shared__ gsfit_camera cams[];
+__global__ void __launch_bounds__(kProjBwdThreads, 2) project_bwd_kernel(
+    const float4* __restrict__ P, int n, const gsfit_camera* __restrict__ cams_g, int n_views,
+    const float4* __restrict__ xyd, const float4* __restrict__ conic, const float4* __restrict__ rgbm,
+    float4* __restrict__ grad2d, float4* __restrict__ G) {
+    // dynamic shared memory: the camera table, then 3K SH-gradient accumulators
+    // per thread (kept out of registers so two CTAs fit per SM)
+    extern __shared__ __align__(16) unsigned char smem_pb[];
+    gsfit_camera* cams = reinterpret_cast<gsfit_camera*>(smem_pb);
+    float* s_dsh = reinterpret_cast<float*>(smem_pb + sizeof(gsfit_camera) * n_views);
+    constexpr int K = SH<DEG>::K;
     load_cameras(cams, cams_g, n_views);
+#pragma unroll
+    for (int k = 0; k < 3 * K; ++k) dsh_acc(s_dsh, k) = 0.f;
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    constexpr int K = SH<DEG>::K;
     Gauss g;
     load_gauss(P, n, i, g);
-    float sh[3 * K];
-    load_sh<DEG>(P, n, i, sh);
     const float opacity = 1.0f / (1.0f + expf(-g.logit));
 
     float dmean[3] = {0.f, 0.f, 0.f};
     float dSig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // xx xy xz yy yz zz (symmetric, dL/dSigma_ij)
     float dlogit = 0.f;
-    float dsh[3 * K];
-#pragma unroll
-    for (int k = 0; k < 3 * K; ++k) dsh[k] = 0.f;
 
-    for (int v = 0; v < n_views; ++v) {
+    for (int v0 = 0; v0 < n_views; v0 += 32) {
+      // visibility of up to 32 views first: independent loads, one latency
+      uint32_t vis = 0;
+      const int vn = min(32, n_views - v0);
+#pragma unroll 8
+      for (int k = 0; k < vn; ++k)
+          if (__ldg(&xyd[(size_t)(v0 + k) * n + i].w) != 0.0f) vis |= 1u << k;
+      while (vis) {
+        const int v = v0 + __ffs(vis) - 1;
+        vis &= vis - 1;
         const size_t r = (size_t)v * n + i;
-        if (xyd[r].w == 0.0f) continue;  // culled in this view
+        // every load of this view issued together
         const float4 ga = grad2d[3 * r + 0];  // du, dv, dopacity
         const float4 gb = grad2d[3 * r + 1];  // da', db', dc'
         const float4 gc = grad2d[3 * r + 2];  // dr, dg, db
+        const float4 cq = __ldg(conic + r);
+        const float4 cm = __ldg(rgbm + r);
         const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
         grad2d[3 * r + 0] = zero;
         grad2d[3 * r + 1] = zero;
@@ -327,7 +343,6 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(const float4* __restri
         float dtz = -(ga.x * cam.fx * vg.tx + ga.y * cam.fy * vg.ty) * iz2;
 
         // conic Q = S^-1: dL/dS = -Q G Q with G = [[da', db'/2], [db'/2, dc']]
-        const float4 cq = conic[r];
         const float q00 = cq.x, q01 = cq.y, q11 = cq.z;
         const float g00 = gb.x, g01 = 0.5f * gb.y, g11 = gb.z;
         const float t00 = q00 * g00 + q01 * g01, t01 = q00 * g01 + q01 * g11;
@@ -385,7 +400,6 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(const float4* __restri
         dlogit += ga.z * opacity * (1.f - opacity);
 
         // colour: clamped channels pass no gradient
-        const float4 cm = rgbm[r];
         const int mask = (int)cm.w;
         const float gcol[3] = {(mask & 1) ? 0.f : gc.x, (mask & 2) ? 0.f : gc.y, (mask & 4) ? 0.f : gc.z};
         float dx = g.mx - cam.campos[0], dy = g.my - cam.campos[1], dz = g.mz - cam.campos[2];
@@ -394,12 +408,15 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(const float4* __restri
         dx *= idist; dy *= idist; dz *= idist;
         float Y[K];
         sh_basis<DEG>(dx, dy, dz, Y);
+        // coefficients re-read per view (L1-resident across the view loop)
+        float sh[3 * K];
+        load_sh<DEG>(P, n, i, sh);
         float wk[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            dsh[3 * k + 0] += Y[k] * gcol[0];
-            dsh[3 * k + 1] += Y[k] * gcol[1];
-            dsh[3 * k + 2] += Y[k] * gcol[2];
+            dsh_acc(s_dsh, 3 * k + 0) += Y[k] * gcol[0];
+            dsh_acc(s_dsh, 3 * k + 1) += Y[k] * gcol[1];
+            dsh_acc(s_dsh, 3 * k + 2) += Y[k] * gcol[2];
             wk[k] = sh[3 * k + 0] * gcol[0] + sh[3 * k + 1] * gcol[1] + sh[3 * k + 2] * gcol[2];
         }
         if (DEG > 0) {
@@ -409,6 +426,7 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(const float4* __restri
             dmean[1] += (dd.y - dy * proj) * idist;
             dmean[2] += (dd.z - dz * proj) * idist;
         }
+      }
     }
 
     // Sigma = Ms Ms^T, Ms = R diag(s): dMs = 2 dSigma Ms
@@ -447,10 +465,10 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(const float4* __restri
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
         float4 q;
-        q.x = (4 * p + 0 < K3) ? dsh[4 * p + 0] : 0.f;
-        q.y = (4 * p + 1 < K3) ? dsh[4 * p + 1] : 0.f;
-        q.z = (4 * p + 2 < K3) ? dsh[4 * p + 2] : 0.f;
-        q.w = (4 * p + 3 < K3) ? dsh[4 * p + 3] : 0.f;
+        q.x = (4 * p + 0 < K3) ? dsh_acc(s_dsh, 4 * p + 0) : 0.f;
+        q.y = (4 * p + 1 < K3) ? dsh_acc(s_dsh, 4 * p + 1) : 0.f;
+        q.z = (4 * p + 2 < K3) ? dsh_acc(s_dsh, 4 * p + 2) : 0.f;
+        q.w = (4 * p + 3 < K3) ? dsh_acc(s_dsh, 4 * p + 3) : 0.f;
         G[(size_t)(3 + p) * n + i] = q;
     }
 }
@@ -470,9 +488,19 @@ int launch_project(const gsfit_gaussians* g, const gsfit_camera* cams, int V, gs
 template <int DEG>
 int launch_project_bwd(const gsfit_gaussians* g, const gsfit_proj* proj, const gsfit_camera* cams, int V,
                        float* grad2d, float* grads, cudaStream_t s) {
-    const int threads = 256;
+    const int threads = kProjBwdThreads;
     const int blocks = (g->n + threads - 1) / threads;
-    const size_t smem = sizeof(gsfit_camera) * V;
+    const size_t smem = sizeof(gsfit_camera) * V + sizeof(float) * 3 * SH<DEG>::K * threads;
+    static bool attr_done[64] = {false};
+    int dev = 0;
+    GSFIT_CUDA_CHECK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return GSFIT_ERR_CUDA;
+    if (!attr_done[dev]) {
+        const size_t max_smem = sizeof(gsfit_camera) * GSFIT_MAX_VIEWS + sizeof(float) * 3 * SH<DEG>::K * threads;
+        GSFIT_CUDA_CHECK(cudaFuncSetAttribute(project_bwd_kernel<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)max_smem));
+        attr_done[dev] = true;
+    }
     project_bwd_kernel<DEG><<<blocks, threads, smem, s>>>(
         reinterpret_cast<const float4*>(g->params), g->n, cams, V, reinterpret_cast<const float4*>(proj->xyd),
         reinterpret_cast<const float4*>(proj->conic), reinterpret_cast<const float4*>(proj->rgb),
