@@ -40,6 +40,40 @@ WORKLOAD = ("batched periphery: 1M Gaussians SH3 from a 512x512x400 CT volume, 1
 HBM_FALLBACK_GBS = 6800.0
 
 
+# FP32 arithmetic per blended (pixel, Gaussian) pair, counted from the kernel
+# source (each +, -, *, /, exp one operation; skip tests not counted):
+# forward  dx, dy 2 + power 9 + exp 1 + o*G 1 + T (1 - a) 2 + weight 1 + colour 6
+# adjoint  power 9 + exp 1 + o*G 1 + 1-a 1 + 1/(1-a) 1 + T recovery 1 + weight 1
+#          + colour grads 3 + dL/dalpha 23 + behind-colour update 6 + 2D grads 18
+FLOP_PER_BLEND = {"render_fwd": 23, "blend_bwd": 65}
+# FP32 lanes per SM and SMs of GB300; the clock is the measured maximum.
+FP32_LANES_PER_SM = 128
+NUM_SMS = 152
+
+
+def alu_peak_tflops(sm_mhz: float) -> float:
+    """FP32 peak (FMA = 2 FLOP): SMs x lanes x 2 x clock."""
+    return NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def measured_traffic(kernel: str):
+    """Bytes per launch of `kernel` from the ncu summary under profiles/,
+    if the kernel source it was measured on is unchanged (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "dram_traffic.md")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        parts = [x.strip() for x in line.strip().strip("|").split("|")]
+        if len(parts) >= 4 and parts[0] == kernel:
+            src = os.path.join(ROOT, parts[2])
+            if not os.path.exists(src):
+                return None
+            sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+            return float(parts[1]) if sha == parts[3] else None
+    return None
+
+
 def measured_peaks() -> dict:
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -142,12 +176,15 @@ def stage_bytes(st, n_inst: int, n_vis: int, n_passes: int) -> dict:
     }
 
 
+TIMED_STAGES = ("project", "bin_sort", "render_fwd", "loss", "blend_bwd", "project_bwd", "adam")
+
+
 def time_stages(st, reps: int) -> dict:
     import torch
-    evs = {k: [] for k in st.STAGES}
+    evs = {k: [] for k in TIMED_STAGES}
     for _ in range(reps):
         marks = []
-        for name in st.STAGES:
+        for name in TIMED_STAGES:
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
             getattr(st, name)()
@@ -353,25 +390,37 @@ def main() -> None:
     n_inst = int(st.n_instances.item())
     n_vis = int((st.proj.tiles > 0).sum().item())
 
-    # per-stage durations (eager launches bracketed by events) and roofline
+    # per-stage durations (eager launches bracketed by events on the launch
+    # stream) and the roofline of the dominant kernel
     stage_ms = time_stages(st, reps=max(5, min(30, args.steps // 10)))
-    from paper_2601_22026_gb300.fit import FitState  # noqa: F401
+    blended = st.blended_pairs()
     n_passes = 4 + (int(np.ceil(np.log2(max(2, st.T)))) + 7) // 8
     sb = stage_bytes(st, n_inst, n_vis, n_passes)
     peaks = measured_peaks()
     hbm_stages = {k: sb[k] / (stage_ms[k] * 1e-3) / 1e9 for k in sb}
+    alu_peak = alu_peak_tflops(peaks["sm_max_mhz"])
+    alu_stages = {k: blended * f / (stage_ms[k] * 1e-3) / 1e12 for k, f in FLOP_PER_BLEND.items()}
     dominant = max(stage_ms, key=stage_ms.get)
+    # project 1; bin_sort reduce, scan, emit, hist, passes, ranges; render 1;
+    # loss (memset node excluded) 2; adjoint 2; adam 2
     launches_per_step = 1 + (5 + n_passes) + 1 + 2 + 2 + 2
+    kernel_of = {"blend_bwd": "render_bwd_kernel", "render_fwd": "render_fwd_kernel", "loss": "loss_kernel",
+                 "project": "project_kernel", "adam": "adam_kernel", "project_bwd": "project_bwd_kernel"}
+    traffic = measured_traffic(kernel_of.get(dominant, dominant))
     if dominant in sb:
         roof = {"kernel": dominant, "bound": "hbm", "achieved": hbm_stages[dominant], "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": hbm_stages[dominant] / peaks["hbm_gbs"], "traffic": None,
+                "unit": "GB/s", "frac": hbm_stages[dominant] / peaks["hbm_gbs"], "traffic": traffic,
                 "peak_source": peaks["source"]}
+    elif dominant in alu_stages:
+        roof = {"kernel": dominant, "bound": "alu", "achieved": alu_stages[dominant], "peak": alu_peak,
+                "unit": "TFLOP/s", "frac": alu_stages[dominant] / alu_peak, "traffic": traffic,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                "work": f"{blended} blended pairs x {FLOP_PER_BLEND[dominant]} FLOP"}
     else:
-        # ALU-bound compositing stages: report the HBM-bound stage fractions
-        # alongside (their FLOP accounting is in the profiles)
-        roof = {"kernel": dominant, "bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s",
-                "frac": None, "traffic": None}
+        roof = {"kernel": dominant, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
+                "traffic": traffic}
     roof["stages_hbm_frac"] = {k: round(hbm_stages[k] / peaks["hbm_gbs"], 4) for k in hbm_stages}
+    roof["stages_alu_frac"] = {k: round(alu_stages[k] / alu_peak, 4) for k in alu_stages}
 
     out = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -380,7 +429,7 @@ def main() -> None:
                       "pairs_per_step": n_inst, "parallelism": "replicas" if world > 1 else "single",
                       "l2": "working set > L2 (no flush)", "graph": True, "loss_last": loss_now},
            "gpu_launches": launches_per_step * args.steps,
-           "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+           "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()}, "blended_pairs": blended,
            "roofline": roof, "clocks": clk}
 
     if rank == 0 and not args.no_plain:

@@ -180,14 +180,18 @@ size_t gsfit_bin_sort_workspace_size(int64_t n_records, int64_t capacity, int32_
  *   2 * total_tiles entries; status: device int32, set to GSFIT_ERR_CAPACITY
  *   when the pairs exceed capacity (nothing is then emitted and every range
  *   is empty) and to GSFIT_ERR_TIMEOUT if a bounded wait of the sort ran out;
- *   it is not cleared by this call.
+ *   it is not cleared by this call. tile_order (device uint32, total_tiles
+ *   entries, may be null): a permutation of the tiles, longest lists first
+ *   (bucketed by log2 of the list length, any order within a bucket); the
+ *   compositing calls launch tiles in this order so the longest lists start
+ *   first and do not form the tail of the grid.
  * Errors: GSFIT_ERR_INVALID_ARG (null pointers, sizes, workspace too small,
  *   capacity >= 2^30), GSFIT_ERR_CUDA.
  */
 int gsfit_bin_sort(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_views, int32_t n,
                    int32_t total_tiles, void* ws, size_t ws_bytes, uint64_t* keys, uint32_t* vals,
-                   int64_t capacity, uint32_t* n_instances, uint32_t* ranges, int32_t* status,
-                   cudaStream_t stream);
+                   int64_t capacity, uint32_t* n_instances, uint32_t* ranges, uint32_t* tile_order,
+                   int32_t* status, cudaStream_t stream);
 
 /*
  * gsfit_render_fwd -- front-to-back compositing (3DGS, with the alpha output
@@ -199,12 +203,14 @@ int gsfit_bin_sort(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_v
  *   list position (within the tile's range) of the last blended Gaussian.
  * Arguments: bg: device float, 3 per view; rgb: 3 * total_pixels floats,
  *   alpha, T_final: total_pixels floats, n_contrib: total_pixels uint32
- *   (device). vals/ranges from gsfit_bin_sort.
+ *   (device). vals/ranges/tile_order from gsfit_bin_sort (tile_order may be
+ *   null: tiles in id order; the results do not depend on the order).
  * Errors: GSFIT_ERR_INVALID_ARG, GSFIT_ERR_CUDA.
  */
 int gsfit_render_fwd(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_views, int32_t n,
-                     int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges, const float* bg,
-                     float* rgb, float* alpha, float* T_final, uint32_t* n_contrib, cudaStream_t stream);
+                     int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges, const uint32_t* tile_order,
+                     const float* bg, float* rgb, float* alpha, float* T_final, uint32_t* n_contrib,
+                     cudaStream_t stream);
 
 /*
  * gsfit_loss -- photometric loss of a view batch and its gradient.
@@ -271,8 +277,36 @@ int gsfit_loss_noalloc(const gsfit_camera* cams, int32_t n_views, const float* r
  */
 int gsfit_render_bwd(const gsfit_gaussians* g, const gsfit_proj* proj, const gsfit_camera* cams,
                      int32_t n_views, int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges,
-                     const float* bg, const float* T_final, const uint32_t* n_contrib, const float* dL_drgb,
-                     const float* dL_dalpha, float* grad2d, float* grads, cudaStream_t stream);
+                     const uint32_t* tile_order, const float* bg, const float* T_final, const uint32_t* n_contrib,
+                     const float* dL_drgb, const float* dL_dalpha, float* grad2d, float* grads, cudaStream_t stream);
+
+/*
+ * gsfit_blend_bwd / gsfit_project_bwd -- the two halves of gsfit_render_bwd,
+ * for callers that schedule them separately (gsfit_render_bwd = blend, then
+ * project). gsfit_blend_bwd accumulates the per-(view, Gaussian) gradients of
+ * (u, v, conic, opacity, rgb) into grad2d (which must be zero on entry);
+ * gsfit_project_bwd chains them through the projection, sums them over views
+ * into `grads` (fully overwritten) and zeroes grad2d again. Arguments as for
+ * gsfit_render_bwd. Errors: GSFIT_ERR_INVALID_ARG, GSFIT_ERR_CUDA.
+ */
+int gsfit_blend_bwd(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_views, int32_t n,
+                    int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges, const uint32_t* tile_order,
+                    const float* bg, const float* T_final, const uint32_t* n_contrib, const float* dL_drgb,
+                    const float* dL_dalpha, float* grad2d, cudaStream_t stream);
+int gsfit_project_bwd(const gsfit_gaussians* g, const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_views,
+                      float* grad2d, float* grads, cudaStream_t stream);
+
+/*
+ * gsfit_render_count -- diagnostic: the number of blended (pixel, Gaussian)
+ * pairs of a forward pass (pairs with list position < n_contrib, power <= 0
+ * and alpha >= 1/255), i.e. the pairs whose adjoint gsfit_blend_bwd evaluates.
+ * Adds the count to *count (device uint64; the caller zeroes it). Not part of
+ * a fit iteration; used to state achieved arithmetic rates.
+ * Errors: GSFIT_ERR_INVALID_ARG, GSFIT_ERR_CUDA.
+ */
+int gsfit_render_count(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_views, int32_t n,
+                       int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges, const uint32_t* tile_order,
+                       const uint32_t* n_contrib, unsigned long long* count, cudaStream_t stream);
 
 /*
  * gsfit_adam_step -- Adam (Kingma & Ba) with bias correction over all

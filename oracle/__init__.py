@@ -69,7 +69,7 @@ def lib() -> ctypes.CDLL:
         L.oracle_project.argtypes = [i, i, P, i, P, i, i, P]
         L.oracle_bin.argtypes = [i, i, P, i, P, P, P, ll, P]
         L.oracle_bin.restype = ll
-        L.oracle_render_fwd.argtypes = [i, i, P, i, P, P, P, P, i, P, P, P, P, P]
+        L.oracle_render_fwd.argtypes = [i, i, P, i, P, P, P, P, i, P, P, P, P, P, P]
         L.oracle_render_bwd.argtypes = [i, i, P, i, P, i, P, P, P, P, i, P, P, P, P, P]
         L.oracle_loss.argtypes = [i, P, P, P, P, P, P, P, d, P, P, P]
         L.oracle_loss.restype = d
@@ -185,12 +185,13 @@ def render(gs: dict, cams: dict, bg: np.ndarray, tile: int = 16, smooth: bool = 
     T = np.zeros(P)
     nc = np.zeros(P, dtype=np.int32)
     amb = np.zeros(P, dtype=np.uint8)
+    nb = np.zeros(P, dtype=np.int32)
     bgd = np.ascontiguousarray(bg, dtype=np.float64).reshape(V, 3)
     vals_c = np.ascontiguousarray(vals) if vals.size else np.zeros(1, np.uint32)
     lib().oracle_render_fwd(n, V, _p(c), tile, _p(proj), _p(vals_c), _p(ranges), _p(bgd),
-                            SMOOTH if smooth else 0, _p(rgb), _p(alpha), _p(T), _p(nc), _p(amb))
+                            SMOOTH if smooth else 0, _p(rgb), _p(alpha), _p(T), _p(nc), _p(amb), _p(nb))
     return {"rgb": rgb, "alpha": alpha, "T_final": T, "n_contrib": nc, "ambiguous": amb.astype(bool),
-            "proj": proj, "keys": keys, "vals": vals, "ranges": ranges}
+            "n_blended": nb, "proj": proj, "keys": keys, "vals": vals, "ranges": ranges}
 
 
 def render_bwd(gs: dict, cams: dict, bg: np.ndarray, dL_drgb: np.ndarray, dL_dalpha: np.ndarray,

@@ -160,7 +160,7 @@ std::vector<WorkItem> work_items(const std::vector<Camera>& cams) {
 
 void render_fwd(int n, const std::vector<Camera>& cams, int tile, const double* proj, const uint32_t* vals,
                 const uint32_t* ranges, const double* bg, int flags, double* rgb, double* alpha, double* T_final,
-                int32_t* n_contrib, uint8_t* ambiguous) {
+                int32_t* n_contrib, uint8_t* ambiguous, int32_t* n_blended) {
     const int V = (int)cams.size();
     std::vector<std::vector<uint32_t>> sorted(V);
     if (flags & FLAG_SMOOTH)
@@ -194,6 +194,7 @@ void render_fwd(int n, const std::vector<Camera>& cams, int tile, const double* 
                 T_final[pix] = px.T;
                 n_contrib[pix] = px.n_contrib;
                 ambiguous[pix] = px.ambiguous ? 1 : 0;
+                if (n_blended) n_blended[pix] = (int32_t)px.blends.size();
             }
     }
 }

@@ -19,18 +19,26 @@ namespace {
 constexpr int kOut = 32;             // output tile edge
 constexpr int kR1 = kOut + 10;       // moments / partials region (halo 5): 42
 constexpr int kR2 = kOut + 20;       // input region (halo 10): 52
-constexpr int kStrip = 4;            // outputs per thread along a pass (register blocking)
-constexpr int kR2p = 56;             // input rows / columns padded so strips never leave the array
-constexpr int kR1p = 44;             // moment rows / columns padded to whole strips
 constexpr int kLossThreads = 256;
 constexpr float kC1 = 0.01f * 0.01f;
 constexpr float kC2 = 0.03f * 0.03f;
 
+// 74 KB: three CTAs per SM. The input region is reused for the SSIM partials
+// and the horizontal-pass buffer for the horizontal pass of the partials.
 struct LossSmem {
-    float x[kR2][kR2p];         // render, input region (zero outside the image and in the padding)
-    float y[kR2][kR2p];         // target composited over the background
-    float h[5][kR2p][kR1p];     // horizontal pass of x, y, x^2, y^2, xy; later the SSIM partials
-    float m[5][kR1p][kR1];      // moments; later the horizontal pass of the partials
+    union {
+        struct {
+            float x[kR2][kR2];       // render, input region (zero outside the image)
+            float y[kR2][kR2];       // target composited over the background
+        } in;
+        float part[3][kR1][kR1];     // dSSIM/d(mu_x, E[x^2], E[xy]) on the 42 x 42 region
+    } a;
+    union {
+        float h[5][kR2][kR1];        // horizontal pass of x, y, x^2, y^2, xy
+        float hp[3][kR1][kOut];      // horizontal pass of the partials
+    } b;
+    float xo[kOut][kOut];            // render and target at the output pixels
+    float yo[kOut][kOut];
 };
 
 // Normalised 11-tap Gaussian, sigma = 1.5.
@@ -46,55 +54,55 @@ __device__ __forceinline__ void window(float w[11]) {
     for (int i = 0; i < 11; ++i) w[i] /= s;
 }
 
-// One pass of the 11-tap window over a strip of kStrip consecutive outputs:
-// the kStrip + 10 inputs are read once into registers.
-template <int STRIDE>
-__device__ __forceinline__ void strip11(const float* src, const float w[11], float out[kStrip]) {
-    float in[kStrip + 10];
+// N outputs of the 11-tap window from N + 10 consecutive inputs read once
+// (stride STRIDE floats apart).
+template <int N, int STRIDE>
+__device__ __forceinline__ void strip11(const float* src, const float w[11], float out[N]) {
+    float in[N + 10];
 #pragma unroll
-    for (int k = 0; k < kStrip + 10; ++k) in[k] = src[k * STRIDE];
+    for (int k = 0; k < N + 10; ++k) in[k] = src[k * STRIDE];
 #pragma unroll
-    for (int o = 0; o < kStrip; ++o) {
-        float a = 0.f;
+    for (int o = 0; o < N; ++o) {
+        float acc = 0.f;
 #pragma unroll
-        for (int j = 0; j < 11; ++j) a += w[j] * in[o + j];
-        out[o] = a;
+        for (int j = 0; j < 11; ++j) acc += w[j] * in[o + j];
+        out[o] = acc;
     }
 }
 
-__global__ void __launch_bounds__(kLossThreads, 2) loss_kernel(
+__global__ void __launch_bounds__(kLossThreads, 3) loss_kernel(
     const gsfit_camera* __restrict__ cams_g, int n_views, const float* __restrict__ rgb,
     const float* __restrict__ alpha, const float* __restrict__ t_rgb, const float* __restrict__ t_alpha,
     const float* __restrict__ bg, float lambda, float* __restrict__ g_rgb, float* __restrict__ g_alpha,
     float* __restrict__ acc /* 3 per view: sum|x-y|, sum SSIM, sum|A-A*| */) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     LossSmem& S = *reinterpret_cast<LossSmem*>(smem_raw);
-    __shared__ int s_item_off[GSFIT_MAX_VIEWS + 1];
     __shared__ float s_red[3][kLossThreads / 32];
-    if (threadIdx.x == 0) {
-        int o = 0;
-        for (int v = 0; v < n_views; ++v) {
-            s_item_off[v] = o;
-            const int tx = (cams_g[v].width + kOut - 1) / kOut, ty = (cams_g[v].height + kOut - 1) / kOut;
-            o += 3 * tx * ty;
-        }
-        s_item_off[n_views] = o;
-    }
-    // zero the padding once: rows / columns beyond the region stay zero
-    for (int k = threadIdx.x; k < 5 * kR2p * kR1p; k += kLossThreads) (&S.h[0][0][0])[k] = 0.f;
+    __shared__ int s_view, s_first;
     float w[11];
     window(w);
-    __syncthreads();
-    const int n_items = s_item_off[n_views];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    int n_items = 0;
+    for (int v = 0; v < n_views; ++v)
+        n_items += 3 * ((cams_g[v].width + kOut - 1) / kOut) * ((cams_g[v].height + kOut - 1) / kOut);
 
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-        int v = 0;
-        while (s_item_off[v + 1] <= item) ++v;
+        if (tid == 0) {  // the view owning this item
+            int v = 0, first = 0;
+            for (;; ++v) {
+                const int k = 3 * ((cams_g[v].width + kOut - 1) / kOut) * ((cams_g[v].height + kOut - 1) / kOut);
+                if (item < first + k) break;
+                first += k;
+            }
+            s_view = v;
+            s_first = first;
+        }
+        __syncthreads();
+        const int v = s_view;
         const gsfit_camera& cam = cams_g[v];
         const int W = cam.width, H = cam.height;
         const int txn = (W + kOut - 1) / kOut;
-        const int local = item - s_item_off[v];
+        const int local = item - s_first;
         const int ch = local % 3;
         const int tile = local / 3;
         const int oy = (tile / txn) * kOut, ox = (tile % txn) * kOut;
@@ -105,40 +113,45 @@ __global__ void __launch_bounds__(kLossThreads, 2) loss_kernel(
         const float bgc = bg[3 * v + ch];
         const float inv3PV = 1.0f / (3.0f * (float)P * (float)n_views);
 
-        // 1. inputs over the 52 x 52 region (56 columns with zero padding);
-        //    thread (column tid % 64, first row tid / 64) walks rows 4 apart
+        // 1. inputs over the 52 x 52 region; thread (column tid % 64, first row
+        //    tid / 64) walks rows 4 apart
         {
             const int cidx = tid & 63, gx = ox - 10 + cidx;
-            const bool col_ok = cidx < kR2 && gx >= 0 && gx < W;
-            for (int r = tid >> 6; r < kR2; r += kLossThreads / 64) {
-                const int gy = oy - 10 + r;
-                float xv = 0.f, yv = 0.f;
-                if (col_ok && gy >= 0 && gy < H) {
-                    const long long q = (long long)gy * W + gx;
-                    xv = X[q];
-                    yv = Yt[q] + (1.0f - At[q]) * bgc;
-                }
-                if (cidx < kR2p) {
-                    S.x[r][cidx] = xv;
-                    S.y[r][cidx] = yv;
+            const bool col_ok = gx >= 0 && gx < W;
+            if (cidx < kR2) {
+                for (int r = tid >> 6; r < kR2; r += kLossThreads / 64) {
+                    const int gy = oy - 10 + r;
+                    float xv = 0.f, yv = 0.f;
+                    if (col_ok && gy >= 0 && gy < H) {
+                        const long long q = (long long)gy * W + gx;
+                        xv = X[q];
+                        yv = Yt[q] + (1.0f - At[q]) * bgc;
+                    }
+                    S.a.in.x[r][cidx] = xv;
+                    S.a.in.y[r][cidx] = yv;
                 }
             }
         }
         __syncthreads();
-        // 2. horizontal pass of x, y, x^2, y^2, xy: 52 rows x 44 columns in strips of 4
-        for (int k = tid; k < kR2 * (kR1p / kStrip); k += kLossThreads) {
-            const int r = k / (kR1p / kStrip), c0 = (k - r * (kR1p / kStrip)) * kStrip;
-            float xin[kStrip + 10], yin[kStrip + 10], xx[kStrip + 10], yy[kStrip + 10], xy[kStrip + 10];
+        // 2. horizontal pass of x, y, x^2, y^2, xy: 52 rows x 42 columns, strips of 6;
+        //    and a copy of the output pixels
+        for (int k = tid; k < kR2 * 7; k += kLossThreads) {
+            const int r = k / 7, c0 = (k - r * 7) * 6;
+            float xin[16], yin[16];
 #pragma unroll
-            for (int j = 0; j < kStrip + 10; ++j) {
-                xin[j] = S.x[r][c0 + j];
-                yin[j] = S.y[r][c0 + j];
+            for (int j = 0; j < 16; ++j) {
+                xin[j] = S.a.in.x[r][c0 + j];
+                yin[j] = S.a.in.y[r][c0 + j];
+            }
+            float xx[16], yy[16], xy[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
                 xx[j] = xin[j] * xin[j];
                 yy[j] = yin[j] * yin[j];
                 xy[j] = xin[j] * yin[j];
             }
 #pragma unroll
-            for (int o = 0; o < kStrip; ++o) {
+            for (int o = 0; o < 6; ++o) {
                 float a = 0.f, b = 0.f, c = 0.f, d = 0.f, e = 0.f;
 #pragma unroll
                 for (int j = 0; j < 11; ++j) {
@@ -148,76 +161,75 @@ __global__ void __launch_bounds__(kLossThreads, 2) loss_kernel(
                     d += w[j] * yy[o + j];
                     e += w[j] * xy[o + j];
                 }
-                S.h[0][r][c0 + o] = a; S.h[1][r][c0 + o] = b; S.h[2][r][c0 + o] = c;
-                S.h[3][r][c0 + o] = d; S.h[4][r][c0 + o] = e;
+                S.b.h[0][r][c0 + o] = a; S.b.h[1][r][c0 + o] = b; S.b.h[2][r][c0 + o] = c;
+                S.b.h[3][r][c0 + o] = d; S.b.h[4][r][c0 + o] = e;
             }
         }
-        __syncthreads();
-        // 3. vertical pass: moments on 44 x 42 (rows 42, 43 are padding) in strips of 4
-        for (int k = tid; k < 5 * kR1 * (kR1p / kStrip); k += kLossThreads) {
-            const int f = k / (kR1 * (kR1p / kStrip));
-            const int rem = k - f * (kR1 * (kR1p / kStrip));
-            const int cidx = rem % kR1, r0 = (rem / kR1) * kStrip;
-            float out[kStrip];
-            strip11<kR1p>(&S.h[f][r0][cidx], w, out);
-#pragma unroll
-            for (int o = 0; o < kStrip; ++o) S.m[f][r0 + o][cidx] = out[o];
+        for (int k = tid; k < kOut * kOut; k += kLossThreads) {
+            const int r = k / kOut, cidx = k - r * kOut;
+            S.xo[r][cidx] = S.a.in.x[r + 10][cidx + 10];
+            S.yo[r][cidx] = S.a.in.y[r + 10][cidx + 10];
         }
         __syncthreads();
-        // 4. SSIM and its partials w.r.t. (mu_x, E[x^2], E[xy]) on the 42 x 42
-        //    region; zero outside the image (those windows do not exist).
+        // 3. vertical pass (strips of 6 rows) straight into SSIM and its
+        //    partials w.r.t. (mu_x, E[x^2], E[xy]) on the 42 x 42 region; zero
+        //    outside the image (those windows do not exist)
         float ssim_sum = 0.f;
-        float (*part)[kR2p][kR1p] = S.h;  // reuse: part[0..2][r][c], r, c < 42
-        for (int k = tid; k < kR1 * kR1; k += kLossThreads) {
-            const int r = k / kR1, cidx = k - r * kR1;
-            const int gy = oy - 5 + r, gx = ox - 5 + cidx;
-            float dmu = 0.f, dxx = 0.f, dxy = 0.f;
-            if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
-                const float mx = S.m[0][r][cidx], my = S.m[1][r][cidx];
-                const float sx = S.m[2][r][cidx] - mx * mx, sy = S.m[3][r][cidx] - my * my;
-                const float sxy = S.m[4][r][cidx] - mx * my;
-                const float A1 = 2.f * mx * my + kC1, A2 = 2.f * sxy + kC2;
-                const float B1 = mx * mx + my * my + kC1, B2 = sx + sy + kC2;
-                const float iB1 = 1.0f / B1, iB2 = 1.0f / B2;
-                const float iB = iB1 * iB2;
-                const float ss = A1 * A2 * iB;
-                dmu = 2.f * my * (A2 - A1) * iB - 2.f * mx * ss * (iB1 - iB2);
-                dxx = -ss * iB2;
-                dxy = 2.f * A1 * iB;
-                if (r >= 5 && r < 5 + kOut && cidx >= 5 && cidx < 5 + kOut) ssim_sum += ss;
-            }
-            part[0][r][cidx] = dmu;
-            part[1][r][cidx] = dxx;
-            part[2][r][cidx] = dxy;
-        }
-        __syncthreads();
-        // 5. horizontal pass of the partials: 42 rows x 32 columns in strips of 4
-        float (*hp)[kR1p][kR1] = S.m;  // reuse: hp[0..2][r][c], r < 42, c < 32
-        for (int k = tid; k < 3 * kR1 * (kOut / kStrip); k += kLossThreads) {
-            const int f = k / (kR1 * (kOut / kStrip));
-            const int rem = k - f * (kR1 * (kOut / kStrip));
-            const int r = rem / (kOut / kStrip), c0 = (rem % (kOut / kStrip)) * kStrip;
-            float out[kStrip];
-            strip11<1>(&part[f][r][c0], w, out);
+        for (int k = tid; k < kR1 * 7; k += kLossThreads) {
+            const int cidx = k % kR1, r0 = (k / kR1) * 6;
+            float mom[5][6];
 #pragma unroll
-            for (int o = 0; o < kStrip; ++o) hp[f][r][c0 + o] = out[o];
+            for (int f = 0; f < 5; ++f) strip11<6, kR1>(&S.b.h[f][r0][cidx], w, mom[f]);
+            const int gx = ox - 5 + cidx;
+#pragma unroll
+            for (int o = 0; o < 6; ++o) {
+                const int r = r0 + o, gy = oy - 5 + r;
+                float dmu = 0.f, dxx = 0.f, dxy = 0.f;
+                if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
+                    const float mx = mom[0][o], my = mom[1][o];
+                    const float sx = mom[2][o] - mx * mx, sy = mom[3][o] - my * my;
+                    const float sxy = mom[4][o] - mx * my;
+                    const float A1 = 2.f * mx * my + kC1, A2 = 2.f * sxy + kC2;
+                    const float B1 = mx * mx + my * my + kC1, B2 = sx + sy + kC2;
+                    const float iB1 = 1.0f / B1, iB2 = 1.0f / B2;
+                    const float iB = iB1 * iB2;
+                    const float ss = A1 * A2 * iB;
+                    dmu = 2.f * my * (A2 - A1) * iB - 2.f * mx * ss * (iB1 - iB2);
+                    dxx = -ss * iB2;
+                    dxy = 2.f * A1 * iB;
+                    if (r >= 5 && r < 5 + kOut && cidx >= 5 && cidx < 5 + kOut) ssim_sum += ss;
+                }
+                S.a.part[0][r][cidx] = dmu;
+                S.a.part[1][r][cidx] = dxx;
+                S.a.part[2][r][cidx] = dxy;
+            }
         }
         __syncthreads();
-        // 6. vertical pass onto the tile (one 4-pixel column strip per thread) and
+        // 4. horizontal pass of the partials: 42 rows x 32 columns in strips of 8
+        for (int k = tid; k < 3 * kR1 * 4; k += kLossThreads) {
+            const int f = k / (kR1 * 4), rem = k - f * (kR1 * 4);
+            const int r = rem >> 2, c0 = (rem & 3) * 8;
+            float out[8];
+            strip11<8, 1>(&S.a.part[f][r][c0], w, out);
+#pragma unroll
+            for (int o = 0; o < 8; ++o) S.b.hp[f][r][c0 + o] = out[o];
+        }
+        __syncthreads();
+        // 5. vertical pass onto the tile (a 4-pixel column strip per thread) and
         //    the gradient
         float l1 = 0.f, la = 0.f;
         {
-            const int cidx = tid % kOut, r0 = (tid / kOut) * kStrip;  // 32 columns x 8 strips = 256
-            float cm[kStrip], cxx[kStrip], cxy[kStrip];
-            strip11<kR1>(&hp[0][r0][cidx], w, cm);
-            strip11<kR1>(&hp[1][r0][cidx], w, cxx);
-            strip11<kR1>(&hp[2][r0][cidx], w, cxy);
+            const int cidx = tid % kOut, r0 = (tid / kOut) * 4;  // 32 columns x 8 strips = 256
+            float cm[4], cxx[4], cxy[4];
+            strip11<4, kOut>(&S.b.hp[0][r0][cidx], w, cm);
+            strip11<4, kOut>(&S.b.hp[1][r0][cidx], w, cxx);
+            strip11<4, kOut>(&S.b.hp[2][r0][cidx], w, cxy);
 #pragma unroll
-            for (int o = 0; o < kStrip; ++o) {
+            for (int o = 0; o < 4; ++o) {
                 const int r = r0 + o;
                 const int gy = oy + r, gx = ox + cidx;
                 if (gy >= H || gx >= W) continue;
-                const float xv = S.x[r + 10][cidx + 10], yv = S.y[r + 10][cidx + 10];
+                const float xv = S.xo[r][cidx], yv = S.yo[r][cidx];
                 const float dssim = cm[o] + 2.f * xv * cxx[o] + yv * cxy[o];
                 const float diff = xv - yv;
                 const float sg = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
@@ -247,7 +259,6 @@ __global__ void __launch_bounds__(kLossThreads, 2) loss_kernel(
             for (int k = 0; k < kLossThreads / 32; ++k) sacc += s_red[tid][k];
             atomicAdd(&acc[3 * v + tid], sacc);
         }
-        // (rows 52..55 of h, the only padding the passes read, are never written)
         __syncthreads();
     }
 }
@@ -295,7 +306,7 @@ extern "C" int gsfit_loss(const gsfit_camera* cams, int32_t n_views, const float
     GSFIT_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     float* acc = static_cast<float*>(ws);
     GSFIT_CUDA_CHECK(cudaMemsetAsync(acc, 0, sizeof(float) * 3 * n_views, stream));
-    loss_kernel<<<2 * sms, kLossThreads, smem, stream>>>(cams, n_views, rgb, alpha, target_rgb, target_alpha, bg,
+    loss_kernel<<<3 * sms, kLossThreads, smem, stream>>>(cams, n_views, rgb, alpha, target_rgb, target_alpha, bg,
                                                          lambda, dL_drgb, dL_dalpha, acc);
     GSFIT_LAUNCH_CHECK();
     if (loss_out) {
@@ -357,7 +368,7 @@ extern "C" int gsfit_loss_noalloc(const gsfit_camera* cams, int32_t n_views, con
     GSFIT_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     // the array keeps the previous call's sums: clear this call's part first
     GSFIT_CUDA_CHECK(cudaMemsetAsync(acc, 0, sizeof(float) * 3 * n_views, stream));
-    loss_kernel<<<2 * sms, kLossThreads, smem, stream>>>(cams, n_views, rgb, alpha, target_rgb, target_alpha, bg,
+    loss_kernel<<<3 * sms, kLossThreads, smem, stream>>>(cams, n_views, rgb, alpha, target_rgb, target_alpha, bg,
                                                          lambda, dL_drgb, dL_dalpha, acc);
     GSFIT_LAUNCH_CHECK();
     if (loss_out) {

@@ -289,12 +289,12 @@ constexpr int kProjBwdThreads = 256;
 __device__ __forceinline__ float& dsh_acc(float* s_dsh, int k) { return s_dsh[k * kProjBwdThreads + threadIdx.x]; }
 
 template <int DEG>
-__global__ void __launch_bounds__(kProjBwdThreads, 2) project_bwd_kernel(
+__global__ void __launch_bounds__(kProjBwdThreads, 3) project_bwd_kernel(
     const float4* __restrict__ P, int n, const gsfit_camera* __restrict__ cams_g, int n_views,
     const float4* __restrict__ xyd, const float4* __restrict__ conic, const float4* __restrict__ rgbm,
     float4* __restrict__ grad2d, float4* __restrict__ G) {
     // dynamic shared memory: the camera table, then 3K SH-gradient accumulators
-    // per thread (kept out of registers so two CTAs fit per SM)
+    // per thread (kept out of registers so three CTAs fit per SM)
     extern __shared__ __align__(16) unsigned char smem_pb[];
     gsfit_camera* cams = reinterpret_cast<gsfit_camera*>(smem_pb);
     float* s_dsh = reinterpret_cast<float*>(smem_pb + sizeof(gsfit_camera) * n_views);

@@ -7,11 +7,13 @@
 // 1e-4, C = sum c alpha T + T_N bg, A = 1 - T_N.
 //
 // Design: one 256-thread CTA per 16 x 16 tile, one pixel per thread; warp w
-// owns the 16 x 2 pixel rows 2w, 2w + 1. The CTA stages the tile's records in
-// batches of 256 (one coalesced record per thread); each warp then compacts,
-// with a ballot, the batch entries whose opacity-aware extent can reach
-// alpha >= 1/255 somewhere in its 16 x 2 box (a conservative test: every pixel
-// of the box would skip the others anyway) and walks only those. The adjoint
+// owns an 8 x 4 pixel box (two boxes across, four down). Tiles are launched in
+// the heavy-first order gsfit_bin_sort produces, so the longest lists do not
+// form the tail of the grid. The CTA stages the tile's records in batches of
+// 256 (one coalesced record per thread); each warp then compacts, with a
+// ballot, the batch entries whose opacity-aware extent can reach alpha >=
+// 1/255 somewhere in its box (a conservative test: every pixel of the box
+// would skip the others anyway) and walks only those. The adjoint
 // keeps no per-(pixel, Gaussian) state: it restarts from the stored final
 // transmittance and contributor count and recovers T_i = T_{i+1} / (1 -
 // alpha_i) walking backwards, and sums the nine per-Gaussian gradient terms of
@@ -29,8 +31,8 @@ constexpr int kRenderWarps = kRenderThreads / 32;
 constexpr int kBatch = kRenderThreads;       // records staged per batch
 constexpr float kCullMargin = 0.02f;         // slack (units of the quadratic form) of the warp cull
 
-// This thread's pixel: warp w covers rows 2w, 2w + 1, lane l column l mod 16
-// of row 2w + l / 16. The warp's box of pixel centres is 16 x 2.
+// This thread's pixel: warp w covers the 8 x 4 box at (8 (w mod 2), 4 (w / 2))
+// of the tile, lane l its pixel (l mod 8, l / 8).
 struct TileCtx {
     int view, px, py;
     bool inside;
@@ -46,14 +48,15 @@ __device__ __forceinline__ TileCtx tile_ctx(const gsfit_camera* cams, int n_view
     const int txn = tiles_x_of(cam);
     const int ty = local / txn, tx = local - ty * txn;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    c.px = tx * kTile + (lane & 15);
-    c.py = ty * kTile + 2 * w + (lane >> 4);
+    const int bx = (w & 1) * 8, by = (w >> 1) * 4;
+    c.px = tx * kTile + bx + (lane & 7);
+    c.py = ty * kTile + by + (lane >> 3);
     c.inside = c.px < cam.width && c.py < cam.height;
     c.plane = (long long)cam.width * cam.height;
     c.pix = (long long)cam.pixel_offset + (long long)c.py * cam.width + c.px;
     c.rgb_base = 3ll * cam.pixel_offset + (long long)c.py * cam.width + c.px;
-    c.box_cx = (float)(tx * kTile) + 7.5f;
-    c.box_cy = (float)(ty * kTile + 2 * w) + 0.5f;
+    c.box_cx = (float)(tx * kTile + bx) + 3.5f;
+    c.box_cy = (float)(ty * kTile + by) + 1.5f;
     return c;
 }
 
@@ -107,20 +110,21 @@ __device__ __forceinline__ void stage(Batch& S, uint32_t idx, uint32_t end, cons
 __device__ __forceinline__ bool box_hit(const Batch& S, int j, const TileCtx& c) {
     const float2 p = S.xy[j];
     const float2 e = S.ext[j];
-    return e.x >= 0.0f && fabsf(p.x - c.box_cx) <= 7.5f + e.x && fabsf(p.y - c.box_cy) <= 0.5f + e.y;
+    return e.x >= 0.0f && fabsf(p.x - c.box_cx) <= 3.5f + e.x && fabsf(p.y - c.box_cy) <= 1.5f + e.y;
 }
 
 __global__ void __launch_bounds__(kRenderThreads) render_fwd_kernel(
     const float4* __restrict__ xyd, const float4* __restrict__ conic, const float4* __restrict__ rgb, int n,
     const gsfit_camera* __restrict__ cams_g, int n_views, const uint32_t* __restrict__ vals,
-    const uint2* __restrict__ ranges, const float* __restrict__ bg, float* __restrict__ out_rgb,
+    const uint2* __restrict__ ranges, const uint32_t* __restrict__ tile_order, const float* __restrict__ bg,
+    float* __restrict__ out_rgb,
     float* __restrict__ out_alpha, float* __restrict__ out_T, uint32_t* __restrict__ out_nc) {
     extern __shared__ gsfit_camera cams[];
     __shared__ Batch S;
     __shared__ uint8_t s_list[kRenderWarps][kBatch];
     load_cameras(cams, cams_g, n_views);
     __syncthreads();
-    const int t = blockIdx.x;
+    const int t = tile_order ? (int)tile_order[blockIdx.x] : (int)blockIdx.x;
     const TileCtx c = tile_ctx(cams, n_views, t);
     const uint2 range = ranges[t];
     const size_t rec0 = (size_t)c.view * n;
@@ -279,7 +283,8 @@ __device__ __forceinline__ bool pix_bwd_step(PixBwd& q, uint32_t pos, float4 co,
 __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(
     const float4* __restrict__ xyd, const float4* __restrict__ conic, const float4* __restrict__ rgb, int n,
     const gsfit_camera* __restrict__ cams_g, int n_views, const uint32_t* __restrict__ vals,
-    const uint2* __restrict__ ranges, const float* __restrict__ bg, const float* __restrict__ T_final,
+    const uint2* __restrict__ ranges, const uint32_t* __restrict__ tile_order, const float* __restrict__ bg,
+    const float* __restrict__ T_final,
     const uint32_t* __restrict__ n_contrib, const float* __restrict__ dL_drgb, const float* __restrict__ dL_dalpha,
     float* __restrict__ grad2d) {
     extern __shared__ gsfit_camera cams[];
@@ -289,7 +294,7 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(
     load_cameras(cams, cams_g, n_views);
     if (threadIdx.x == 0) s_max = 0u;
     __syncthreads();
-    const int t = blockIdx.x;
+    const int t = tile_order ? (int)tile_order[blockIdx.x] : (int)blockIdx.x;
     const TileCtx c = tile_ctx(cams, n_views, t);
     const uint2 range = ranges[t];
     const size_t rec0 = (size_t)c.view * n;
@@ -353,6 +358,39 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(
     }
 }
 
+// Diagnostic: blended pairs, with the forward's skip rules, up to each
+// pixel's contributor count (one pixel per thread, batches as above, no cull).
+__global__ void __launch_bounds__(kRenderThreads) render_count_kernel(
+    const float4* __restrict__ xyd, const float4* __restrict__ conic, const float4* __restrict__ rgb, int n,
+    const gsfit_camera* __restrict__ cams_g, int n_views, const uint32_t* __restrict__ vals,
+    const uint2* __restrict__ ranges, const uint32_t* __restrict__ tile_order, const uint32_t* __restrict__ n_contrib,
+    unsigned long long* __restrict__ count) {
+    extern __shared__ gsfit_camera cams[];
+    __shared__ Batch S;
+    load_cameras(cams, cams_g, n_views);
+    __syncthreads();
+    const int t = tile_order ? (int)tile_order[blockIdx.x] : (int)blockIdx.x;
+    const TileCtx c = tile_ctx(cams, n_views, t);
+    const uint2 range = ranges[t];
+    const size_t rec0 = (size_t)c.view * n;
+    const uint32_t last = c.inside ? n_contrib[c.pix] : 0u;
+    unsigned long long mine = 0;
+    for (uint32_t b0 = range.x; b0 < range.y; b0 += kBatch) {
+        __syncthreads();
+        stage(S, b0 + threadIdx.x, range.y, vals, xyd, conic, rgb, rec0, n);
+        __syncthreads();
+        const int cnt = (int)min((uint32_t)kBatch, range.y - b0);
+        for (int j = 0; j < cnt; ++j) {
+            if (S.g[j] == 0xffffffffu || b0 - range.x + (uint32_t)j >= last) continue;
+            const float power = splat_power(S.co[j], (float)c.px - S.xy[j].x, (float)c.py - S.xy[j].y);
+            if (power > 0.0f) continue;
+            if (fminf(kAlphaClamp, S.co[j].w * __expf(power)) >= kAlphaSkip) ++mine;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+    if ((threadIdx.x & 31) == 0 && mine) atomicAdd(count, mine);
+}
+
 }  // namespace
 
 bool valid_proj(const gsfit_proj* p);
@@ -365,34 +403,68 @@ int project_bwd(const gsfit_gaussians* g, const gsfit_proj* proj, const gsfit_ca
 using namespace gsfit;
 
 extern "C" int gsfit_render_fwd(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_views, int32_t n,
-                                int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges, const float* bg,
-                                float* rgb, float* alpha, float* T_final, uint32_t* n_contrib,
-                                cudaStream_t stream) {
+                                int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges,
+                                const uint32_t* tile_order, const float* bg, float* rgb, float* alpha,
+                                float* T_final, uint32_t* n_contrib, cudaStream_t stream) {
     if (!valid_proj(proj) || !cams || n_views < 1 || n_views > GSFIT_MAX_VIEWS || n < 1 || total_tiles < 1 ||
         !vals || !ranges || !bg || !rgb || !alpha || !T_final || !n_contrib)
         return GSFIT_ERR_INVALID_ARG;
     render_fwd_kernel<<<total_tiles, kRenderThreads, sizeof(gsfit_camera) * n_views, stream>>>(
         reinterpret_cast<const float4*>(proj->xyd), reinterpret_cast<const float4*>(proj->conic),
         reinterpret_cast<const float4*>(proj->rgb), n, cams, n_views, vals, reinterpret_cast<const uint2*>(ranges),
-        bg, rgb, alpha, T_final, n_contrib);
+        tile_order, bg, rgb, alpha, T_final, n_contrib);
     GSFIT_LAUNCH_CHECK();
     return GSFIT_OK;
 }
 
-extern "C" int gsfit_render_bwd(const gsfit_gaussians* g, const gsfit_proj* proj, const gsfit_camera* cams,
-                                int32_t n_views, int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges,
-                                const float* bg, const float* T_final, const uint32_t* n_contrib,
-                                const float* dL_drgb, const float* dL_dalpha, float* grad2d, float* grads,
-                                cudaStream_t stream) {
-    if (!valid_gaussians(g) || !valid_proj(proj) || !cams || n_views < 1 || n_views > GSFIT_MAX_VIEWS ||
-        total_tiles < 1 || !vals || !ranges || !bg || !T_final || !n_contrib || !dL_drgb || !dL_dalpha ||
-        !grad2d || !grads || (reinterpret_cast<uintptr_t>(grad2d) % 16) != 0 ||
-        (reinterpret_cast<uintptr_t>(grads) % 16) != 0)
+extern "C" int gsfit_blend_bwd(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_views, int32_t n,
+                               int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges,
+                               const uint32_t* tile_order, const float* bg, const float* T_final,
+                               const uint32_t* n_contrib, const float* dL_drgb, const float* dL_dalpha, float* grad2d,
+                               cudaStream_t stream) {
+    if (!valid_proj(proj) || !cams || n_views < 1 || n_views > GSFIT_MAX_VIEWS || n < 1 || total_tiles < 1 ||
+        !vals || !ranges || !bg || !T_final || !n_contrib || !dL_drgb || !dL_dalpha || !grad2d ||
+        (reinterpret_cast<uintptr_t>(grad2d) % 16) != 0)
         return GSFIT_ERR_INVALID_ARG;
     render_bwd_kernel<<<total_tiles, kRenderThreads, sizeof(gsfit_camera) * n_views, stream>>>(
         reinterpret_cast<const float4*>(proj->xyd), reinterpret_cast<const float4*>(proj->conic),
-        reinterpret_cast<const float4*>(proj->rgb), g->n, cams, n_views, vals,
-        reinterpret_cast<const uint2*>(ranges), bg, T_final, n_contrib, dL_drgb, dL_dalpha, grad2d);
+        reinterpret_cast<const float4*>(proj->rgb), n, cams, n_views, vals, reinterpret_cast<const uint2*>(ranges),
+        tile_order, bg, T_final, n_contrib, dL_drgb, dL_dalpha, grad2d);
     GSFIT_LAUNCH_CHECK();
+    return GSFIT_OK;
+}
+
+extern "C" int gsfit_project_bwd(const gsfit_gaussians* g, const gsfit_proj* proj, const gsfit_camera* cams,
+                                 int32_t n_views, float* grad2d, float* grads, cudaStream_t stream) {
+    if (!valid_gaussians(g) || !valid_proj(proj) || !cams || n_views < 1 || n_views > GSFIT_MAX_VIEWS || !grad2d ||
+        !grads || (reinterpret_cast<uintptr_t>(grad2d) % 16) != 0 || (reinterpret_cast<uintptr_t>(grads) % 16) != 0)
+        return GSFIT_ERR_INVALID_ARG;
     return project_bwd(g, proj, cams, n_views, grad2d, grads, stream);
+}
+
+extern "C" int gsfit_render_bwd(const gsfit_gaussians* g, const gsfit_proj* proj, const gsfit_camera* cams,
+                                int32_t n_views, int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges,
+                                const uint32_t* tile_order, const float* bg, const float* T_final,
+                                const uint32_t* n_contrib, const float* dL_drgb, const float* dL_dalpha, float* grad2d,
+                                float* grads, cudaStream_t stream) {
+    if (!valid_gaussians(g)) return GSFIT_ERR_INVALID_ARG;
+    const int rc = gsfit_blend_bwd(proj, cams, n_views, g->n, total_tiles, vals, ranges, tile_order, bg, T_final,
+                                   n_contrib, dL_drgb, dL_dalpha, grad2d, stream);
+    if (rc != GSFIT_OK) return rc;
+    return gsfit_project_bwd(g, proj, cams, n_views, grad2d, grads, stream);
+}
+
+extern "C" int gsfit_render_count(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_views, int32_t n,
+                                  int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges,
+                                  const uint32_t* tile_order, const uint32_t* n_contrib, unsigned long long* count,
+                                  cudaStream_t stream) {
+    if (!valid_proj(proj) || !cams || n_views < 1 || n_views > GSFIT_MAX_VIEWS || n < 1 || total_tiles < 1 ||
+        !vals || !ranges || !n_contrib || !count)
+        return GSFIT_ERR_INVALID_ARG;
+    render_count_kernel<<<total_tiles, kRenderThreads, sizeof(gsfit_camera) * n_views, stream>>>(
+        reinterpret_cast<const float4*>(proj->xyd), reinterpret_cast<const float4*>(proj->conic),
+        reinterpret_cast<const float4*>(proj->rgb), n, cams, n_views, vals, reinterpret_cast<const uint2*>(ranges),
+        tile_order, n_contrib, count);
+    GSFIT_LAUNCH_CHECK();
+    return GSFIT_OK;
 }

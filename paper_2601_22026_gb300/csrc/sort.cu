@@ -48,6 +48,8 @@ struct SortCtl {
     unsigned long long total;  // exact pair count
     uint32_t part_counter[kMaxPasses];
     uint32_t hist[kMaxPasses][kRadix];
+    uint32_t order_hist[32];  // tiles per log2(list length + 1) bucket
+    uint32_t order_fill[32];
 };
 
 // Block-wide exclusive scan of one value per thread (blockDim == 256).
@@ -99,6 +101,10 @@ __global__ void __launch_bounds__(1024) scan_kernel(uint32_t* __restrict__ block
     if (threadIdx.x == 0) s_carry = 0;
     for (int k = threadIdx.x; k < kMaxPasses * kRadix; k += blockDim.x) (&ctl->hist[0][0])[k] = 0u;
     if (threadIdx.x < kMaxPasses) ctl->part_counter[threadIdx.x] = 0u;
+    if (threadIdx.x < 32) {
+        ctl->order_hist[threadIdx.x] = 0u;
+        ctl->order_fill[threadIdx.x] = 0u;
+    }
     __syncthreads();
     for (int base = 0; base < n_blocks; base += 1024) {
         const int b = base + threadIdx.x;
@@ -205,6 +211,7 @@ __global__ void __launch_bounds__(256) hist_kernel(const unsigned long long* __r
 struct OnesweepSmem {
     unsigned long long keys[kPart];
     uint32_t vals[kPart];
+    uint32_t vals_in[kPart];  // this partition's values in input order
     uint32_t warp_hist[kSortWarps][kRadix + 1];  // bin kRadix collects padding keys
     uint32_t local_start[kRadix];
     uint32_t glob_off[kRadix];  // global position of local index j is glob_off[d] + j
@@ -212,7 +219,7 @@ struct OnesweepSmem {
     uint32_t part;
 };
 
-__global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const unsigned long long* __restrict__ keys_in,
+__global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(const unsigned long long* __restrict__ keys_in,
                                                                 const uint32_t* __restrict__ vals_in,
                                                                 unsigned long long* __restrict__ keys_out,
                                                                 uint32_t* __restrict__ vals_out,
@@ -233,23 +240,26 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const unsigned l
     const uint32_t base = part * kPart;
     const uint32_t valid = min((uint32_t)kPart, n - base);
 
-    // Load (warp-striped, coalesced) and rank within the warp per digit.
+    // Load (warp-striped, coalesced) and rank within the warp per digit. Keys
+    // stay in registers; values wait in shared memory in input order.
     unsigned long long k_reg[kSortItems];
-    uint32_t v_reg[kSortItems];
-    uint32_t d_reg[kSortItems];
     uint32_t r_reg[kSortItems];
     const uint32_t lt_mask = (1u << lane) - 1u;
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
         const uint32_t idx = (uint32_t)wid * (32 * kSortItems) + j * 32 + lane;
         const bool ok = idx < valid;
-        k_reg[j] = ok ? keys_in[base + idx] : 0ull;
-        v_reg[j] = ok ? vals_in[base + idx] : 0u;
-        d_reg[j] = ok ? (uint32_t)((k_reg[j] >> shift) & 0xff) : (uint32_t)kRadix;
+        k_reg[j] = ok ? keys_in[base + idx] : ~0ull;
+        if (ok) S.vals_in[idx] = vals_in[base + idx];
     }
+    // digit of item j; items past the end go to bin kRadix
+    auto digit = [&](int j) -> uint32_t {
+        const uint32_t idx = (uint32_t)wid * (32 * kSortItems) + j * 32 + lane;
+        return idx < valid ? (uint32_t)((k_reg[j] >> shift) & 0xff) : (uint32_t)kRadix;
+    };
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
-        const uint32_t d = d_reg[j];
+        const uint32_t d = digit(j);
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
         const uint32_t cnt = S.warp_hist[wid][d];
         __syncwarp();
@@ -312,11 +322,11 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const unsigned l
     // scatter into shared memory in digit order (stable: warp, item, lane order)
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
-        const uint32_t dd = d_reg[j];
+        const uint32_t dd = digit(j);
         if (dd < (uint32_t)kRadix) {
             const uint32_t pos = S.local_start[dd] + S.warp_hist[wid][dd] + r_reg[j];
             S.keys[pos] = k_reg[j];
-            S.vals[pos] = v_reg[j];
+            S.vals[pos] = S.vals_in[(uint32_t)wid * (32 * kSortItems) + j * 32 + lane];
         }
     }
     __syncthreads();
@@ -342,6 +352,42 @@ __global__ void __launch_bounds__(256) ranges_kernel(const unsigned long long* _
         if (t >= total_tiles) continue;  // only after a failed sort
         if (k == 0 || (uint32_t)(keys[k - 1] >> 32) != t) ranges[2 * (size_t)t] = (uint32_t)k;
         if (k + 1 == n || (uint32_t)(keys[k + 1] >> 32) != t) ranges[2 * (size_t)t + 1] = (uint32_t)(k + 1);
+    }
+}
+
+// Heavy-first tile order: tiles bucketed by floor(log2(list length + 1)),
+// buckets in decreasing order, tiles within a bucket in any order.
+__device__ __forceinline__ int length_bucket(const uint32_t* ranges, int t) {
+    const uint32_t len = ranges[2 * t + 1] - ranges[2 * t];
+    return 31 - __clz(len + 1u);
+}
+
+__global__ void __launch_bounds__(256) order_hist_kernel(const uint32_t* __restrict__ ranges, int total_tiles,
+                                                         SortCtl* __restrict__ ctl) {
+    __shared__ uint32_t h[32];
+    if (threadIdx.x < 32) h[threadIdx.x] = 0u;
+    __syncthreads();
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total_tiles; t += gridDim.x * blockDim.x)
+        atomicAdd(&h[length_bucket(ranges, t)], 1u);
+    __syncthreads();
+    if (threadIdx.x < 32 && h[threadIdx.x]) atomicAdd(&ctl->order_hist[threadIdx.x], h[threadIdx.x]);
+}
+
+__global__ void __launch_bounds__(256) order_scatter_kernel(const uint32_t* __restrict__ ranges, int total_tiles,
+                                                            SortCtl* __restrict__ ctl,
+                                                            uint32_t* __restrict__ tile_order) {
+    __shared__ uint32_t off[32];
+    if (threadIdx.x == 0) {
+        uint32_t o = 0;
+        for (int b = 31; b >= 0; --b) {
+            off[b] = o;
+            o += ctl->order_hist[b];
+        }
+    }
+    __syncthreads();
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total_tiles; t += gridDim.x * blockDim.x) {
+        const int b = length_bucket(ranges, t);
+        tile_order[off[b] + atomicAdd(&ctl->order_fill[b], 1u)] = (uint32_t)t;
     }
 }
 
@@ -402,8 +448,8 @@ extern "C" size_t gsfit_bin_sort_workspace_size(int64_t n_records, int64_t capac
 
 extern "C" int gsfit_bin_sort(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_views, int32_t n,
                               int32_t total_tiles, void* ws, size_t ws_bytes, uint64_t* keys, uint32_t* vals,
-                              int64_t capacity, uint32_t* n_instances, uint32_t* ranges, int32_t* status,
-                              cudaStream_t stream) {
+                              int64_t capacity, uint32_t* n_instances, uint32_t* ranges, uint32_t* tile_order,
+                              int32_t* status, cudaStream_t stream) {
     if (!valid_proj(proj) || !cams || n_views < 1 || n_views > GSFIT_MAX_VIEWS || n < 1 || total_tiles < 1 ||
         !ws || !keys || !vals || !n_instances || !ranges || !status || capacity < 1 ||
         capacity >= (int64_t)kFlagAgg)
@@ -450,5 +496,12 @@ extern "C" int gsfit_bin_sort(const gsfit_proj* proj, const gsfit_camera* cams, 
     }
     ranges_kernel<<<kHistBlocks, 256, 0, stream>>>(keys_out, ctl, ranges, (uint32_t)total_tiles);
     GSFIT_LAUNCH_CHECK();
+    if (tile_order) {
+        const int ob = min(152, (total_tiles + 255) / 256);
+        order_hist_kernel<<<ob, 256, 0, stream>>>(ranges, total_tiles, ctl);
+        GSFIT_LAUNCH_CHECK();
+        order_scatter_kernel<<<ob, 256, 0, stream>>>(ranges, total_tiles, ctl, tile_order);
+        GSFIT_LAUNCH_CHECK();
+    }
     return GSFIT_OK;
 }

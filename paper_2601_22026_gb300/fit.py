@@ -73,6 +73,7 @@ class FitState:
         self.target_rgb = torch.zeros(3 * self.P, dtype=f32, device=dev)
         self.target_alpha = torch.zeros(self.P, dtype=f32, device=dev)
         self.ranges = torch.zeros(2 * self.T, dtype=torch.int32, device=dev)
+        self.tile_order = torch.zeros(self.T, dtype=torch.int32, device=dev)
         self.grad2d = torch.zeros(self.V * self.n * 12, dtype=f32, device=dev)
         self.loss_ws = torch.zeros(G.gsfit_loss_workspace_size(self.V) // 4 + 1, dtype=f32, device=dev)
         bgv = np.zeros((self.V, 3), np.float32) if bg is None else np.asarray(bg, np.float32).reshape(self.V, 3)
@@ -117,11 +118,11 @@ class FitState:
 
     def bin_sort(self, stream=None):
         G.gsfit_bin_sort(self.proj, self.cams_dev, self.V, self.n, self.T, self.sort_ws, self.keys, self.vals,
-                         self.capacity, self.n_instances, self.ranges, self.status, stream)
+                         self.capacity, self.n_instances, self.ranges, self.status, stream, self.tile_order)
 
     def render_fwd(self, stream=None):
         G.gsfit_render_fwd(self.proj, self.cams_dev, self.V, self.n, self.T, self.vals, self.ranges, self.bg,
-                           self.rgb, self.alpha, self.T_final, self.n_contrib, stream)
+                           self.rgb, self.alpha, self.T_final, self.n_contrib, stream, self.tile_order)
 
     def loss(self, stream=None):
         G.gsfit_loss(self.cams_dev, self.V, self.rgb, self.alpha, self.target_rgb, self.target_alpha, self.bg,
@@ -130,7 +131,23 @@ class FitState:
     def render_bwd(self, stream=None):
         G.gsfit_render_bwd(self.params, self.n, self.sh_degree, self.proj, self.cams_dev, self.V, self.T,
                            self.vals, self.ranges, self.bg, self.T_final, self.n_contrib, self.dL_drgb,
-                           self.dL_dalpha, self.grad2d, self.grads, stream)
+                           self.dL_dalpha, self.grad2d, self.grads, stream, self.tile_order)
+
+    def blend_bwd(self, stream=None):
+        G.gsfit_blend_bwd(self.proj, self.cams_dev, self.V, self.n, self.T, self.vals, self.ranges, self.bg,
+                          self.T_final, self.n_contrib, self.dL_drgb, self.dL_dalpha, self.grad2d, stream,
+                          self.tile_order)
+
+    def project_bwd(self, stream=None):
+        G.gsfit_project_bwd(self.params, self.n, self.sh_degree, self.proj, self.cams_dev, self.V, self.grad2d,
+                            self.grads, stream)
+
+    def blended_pairs(self) -> int:
+        """Blended (pixel, Gaussian) pairs of the last forward pass (syncs)."""
+        cnt = torch.zeros(1, dtype=torch.int64, device=self.device)
+        G.gsfit_render_count(self.proj, self.cams_dev, self.V, self.n, self.T, self.vals, self.ranges,
+                             self.n_contrib, cnt, None, self.tile_order)
+        return int(cnt.item())
 
     def adam(self, stream=None):
         G.gsfit_adam_step(self.params, self.grads, self.m, self.v, self.n, self.n_planes, self.lr, 0.9, 0.999,

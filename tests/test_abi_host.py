@@ -90,11 +90,11 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.gsfit_project(ctypes.byref(g), fake, 257, ctypes.byref(p), None) == G.GSFIT_ERR_INVALID_ARG
     # capacity at or above 2^30 and undersized workspaces are refused before any launch
     assert lib.gsfit_bin_sort(ctypes.byref(p), fake, 1, 10, 4, fake, 1 << 40, fake, fake, 1 << 30, fake, fake,
-                              fake, None) == G.GSFIT_ERR_INVALID_ARG
+                              None, fake, None) == G.GSFIT_ERR_INVALID_ARG
     need = lib.gsfit_bin_sort_workspace_size(10, 1000, 4)
     assert need > 0
     assert lib.gsfit_bin_sort(ctypes.byref(p), fake, 1, 10, 4, fake, need - 1, fake, fake, 1000, fake, fake,
-                              fake, None) == G.GSFIT_ERR_INVALID_ARG
+                              None, fake, None) == G.GSFIT_ERR_INVALID_ARG
     assert lib.gsfit_adam_step(fake, fake, fake, fake, 10, 17, None, 0.9, 0.999, 1e-15, fake,
                                None) == G.GSFIT_ERR_INVALID_ARG
     assert lib.gsfit_loss_workspace_size(0) == 0

@@ -154,6 +154,12 @@ def test_keys_sort_ranges_bit_exact(name):
     assert len(rk) > 0
     np.testing.assert_array_equal(gk, ok_)
     np.testing.assert_array_equal(gv, ov)
+    # heavy-first launch order: a permutation with non-increasing log2 lengths
+    order = st.tile_order.cpu().numpy().view(np.uint32).astype(np.int64)
+    assert np.array_equal(np.sort(order), np.arange(len(ranges)))
+    lens = (ranges[:, 1].astype(np.int64) - ranges[:, 0].astype(np.int64))[order]
+    buckets = np.floor(np.log2(lens + 1)).astype(np.int64)
+    assert np.all(np.diff(buckets) <= 0)
     bad = np.array(sorted(bad_g | bad_o), dtype=np.int64)
     if not bad.size:
         assert n_inst == len(rk)
@@ -435,3 +441,19 @@ def test_single_gaussian_and_opaque_clamp():
     assert a[pix] == np.float32(1.0) - np.float32(0.01) or abs(a[pix] - 0.99) < 1e-7
     ref = oracle.render(gs, cams, bg)
     np.testing.assert_allclose(st.rgb.cpu().numpy(), ref["rgb"], atol=1e-6)
+
+
+def test_blended_pair_count_matches_oracle():
+    """The diagnostic pair counter behind the bench's arithmetic rate counts
+    what the oracle blends (differences only at flagged near-threshold
+    pixels)."""
+    sc = scenes.differentiation_scene(0)
+    gs, cams, bg = sc["gaussians"], sc["cameras"], sc["bg"]
+    st = _fit_state(gs, cams, bg)
+    st.forward()
+    got = st.blended_pairs()
+    ref = oracle.render(gs, cams, bg)
+    exact = int(ref["n_blended"][~ref["ambiguous"]].sum())
+    loose = int(ref["n_blended"][ref["ambiguous"]].sum())
+    assert exact > 0
+    assert abs(got - (exact + loose)) <= max(1, int(ref["ambiguous"].sum()))
