@@ -13,7 +13,9 @@
 // 256 (one coalesced record per thread); each warp then compacts, with a
 // ballot, the batch entries whose opacity-aware extent can reach alpha >=
 // 1/255 somewhere in its box (a conservative test: every pixel of the box
-// would skip the others anyway) and walks only those. The adjoint
+// would skip the others anyway) and walks only those. The adjoint copies the
+// next batch with cp.async while it works on the current one (the forward, which
+// often stops early, stages one batch at a time). The adjoint
 // keeps no per-(pixel, Gaussian) state: it restarts from the stored final
 // transmittance and contributor count and recovers T_i = T_{i+1} / (1 -
 // alpha_i) walking backwards, and sums the nine per-Gaussian gradient terms of
@@ -110,6 +112,59 @@ __device__ __forceinline__ void stage(Batch& S, uint32_t idx, uint32_t end, cons
 __device__ __forceinline__ bool box_hit(const Batch& S, int j, const TileCtx& c) {
     const float2 p = S.xy[j];
     const float2 e = S.ext[j];
+    return e.x >= 0.0f && fabsf(p.x - c.box_cx) <= 3.5f + e.x && fabsf(p.y - c.box_cy) <= 1.5f + e.y;
+}
+
+// Double-buffered staging (adjoint): while the warps work on one batch,
+// cp.async copies the next batch's 16-byte records (gathered by Gaussian index) into
+// the other buffer; only the index of the batch after that occupies a
+// register. Entries past the list end, or with an out-of-range index (which
+// only a failed sort produces), are never copied and are culled.
+struct Batch2 {
+    float4 xyd[2][kBatch];
+    float4 co[2][kBatch];
+    float4 col[2][kBatch];
+    float2 ext[2][kBatch];
+    uint32_t g[2][kBatch];
+};
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+__device__ __forceinline__ uint32_t load_index(uint32_t idx, uint32_t end, const uint32_t* __restrict__ vals, int n) {
+    if (idx >= end) return 0xffffffffu;
+    const uint32_t g = __ldg(vals + idx);
+    return g < (uint32_t)n ? g : 0xffffffffu;
+}
+
+// This thread's copies of record g into slot threadIdx.x of buffer b.
+__device__ __forceinline__ void issue_rec(Batch2& S, int b, uint32_t g, const float4* __restrict__ xyd,
+                                          const float4* __restrict__ conic, const float4* __restrict__ rgb,
+                                          size_t rec0) {
+    if (g != 0xffffffffu) {
+        const size_t k = rec0 + g;
+        const int t = threadIdx.x;
+        cp_async16(&S.xyd[b][t], xyd + k);
+        cp_async16(&S.co[b][t], conic + k);
+        cp_async16(&S.col[b][t], rgb + k);
+    }
+}
+
+// After this thread's copies into buffer b have landed: its slot's extents.
+__device__ __forceinline__ void finish_rec(Batch2& S, int b, uint32_t g) {
+    const int t = threadIdx.x;
+    S.ext[b][t] = g != 0xffffffffu ? alpha_extent(S.co[b][t]) : make_float2(-1.f, -1.f);
+    S.g[b][t] = g;
+}
+
+__device__ __forceinline__ bool box_hit2(const Batch2& S, int b, int j, const TileCtx& c) {
+    const float4 p = S.xyd[b][j];
+    const float2 e = S.ext[b][j];
     return e.x >= 0.0f && fabsf(p.x - c.box_cx) <= 3.5f + e.x && fabsf(p.y - c.box_cy) <= 1.5f + e.y;
 }
 
@@ -288,7 +343,7 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(
     const uint32_t* __restrict__ n_contrib, const float* __restrict__ dL_drgb, const float* __restrict__ dL_dalpha,
     float* __restrict__ grad2d) {
     extern __shared__ gsfit_camera cams[];
-    __shared__ Batch S;
+    __shared__ Batch2 S;
     __shared__ uint8_t s_list[kRenderWarps][kBatch];
     __shared__ uint32_t s_max;
     load_cameras(cams, cams_g, n_views);
@@ -325,17 +380,37 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(
     __syncthreads();
     const uint32_t end = range.x + min(s_max, range.y - range.x);
 
-    for (uint32_t b1 = end; b1 > range.x;) {
-        const uint32_t b0 = (b1 - range.x > (uint32_t)kBatch) ? b1 - kBatch : range.x;
-        __syncthreads();
-        stage(S, b0 + threadIdx.x, b1, vals, xyd, conic, rgb, rec0, n);
+    // batches walk backwards, [b0, b1) with b1 - b0 <= kBatch, the last first;
+    // the next one (towards the list start) is copied while this one runs
+    uint32_t b1 = end;
+    uint32_t b0 = (b1 - range.x > (uint32_t)kBatch) ? b1 - kBatch : range.x;
+    uint32_t g_cur = load_index(b0 + threadIdx.x, b1, vals, n);
+    issue_rec(S, 0, g_cur, xyd, conic, rgb, rec0);
+    cp_async_commit();
+    uint32_t pb1 = b0, pb0 = (pb1 - range.x > (uint32_t)kBatch) ? pb1 - kBatch : range.x;
+    uint32_t g_next = pb1 > range.x ? load_index(pb0 + threadIdx.x, pb1, vals, n) : 0xffffffffu;
+    int buf = 0;
+    while (b1 > range.x) {
+        __syncthreads();  // the other buffer is free again
+        uint32_t nb1 = pb1, nb0 = pb0, g_after = 0xffffffffu;
+        if (pb1 > range.x) {
+            issue_rec(S, buf ^ 1, g_next, xyd, conic, rgb, rec0);
+            cp_async_commit();
+            nb1 = pb0;
+            nb0 = (nb1 - range.x > (uint32_t)kBatch) ? nb1 - kBatch : range.x;
+            g_after = nb1 > range.x ? load_index(nb0 + threadIdx.x, nb1, vals, n) : 0xffffffffu;
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        finish_rec(S, buf, g_cur);
         __syncthreads();
         const int cnt = (int)(b1 - b0);
         int nw = 0;
 #pragma unroll
         for (int k = 0; k < kBatch / 32; ++k) {
             const int j = 32 * k + lane;
-            const bool hit = j < cnt && (b0 - range.x + (uint32_t)j) < wmax && box_hit(S, j, c);
+            const bool hit = j < cnt && (b0 - range.x + (uint32_t)j) < wmax && box_hit2(S, buf, j, c);
             const uint32_t m = __ballot_sync(0xffffffffu, hit);
             if (hit) s_list[w][nw + __popc(m & lt)] = (uint8_t)j;
             nw += __popc(m);
@@ -343,19 +418,26 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(
         __syncwarp();
         for (int i = nw - 1; i >= 0; --i) {
             const int j = s_list[w][i];
-            const float2 p = S.xy[j];
-            const float4 co = S.co[j];
-            const float4 col = S.col[j];
+            const float4 p = S.xyd[buf][j];
+            const float4 co = S.co[buf][j];
+            const float4 col = S.col[buf][j];
             float g9[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             const bool hit = pix_bwd_step(q, b0 + (uint32_t)j - range.x, co, col, bg0, bg1, bg2, fx - p.x,
                                           fy - p.y, g9);
             if (__any_sync(0xffffffffu, hit)) {
                 const float tot = reduce9(g9, lane);
-                if (slot >= 0) atomicAdd(grad2d + 12 * (rec0 + S.g[j]) + slot_off, tot);
+                if (slot >= 0) atomicAdd(grad2d + 12 * (rec0 + S.g[buf][j]) + slot_off, tot);
             }
         }
-        b1 = b0;
+        b1 = pb1;
+        b0 = pb0;
+        pb1 = nb1;
+        pb0 = nb0;
+        g_cur = g_next;
+        g_next = g_after;
+        buf ^= 1;
     }
+    cp_async_wait<0>();  // no copy may outlive the block
 }
 
 // Diagnostic: blended pairs, with the forward's skip rules, up to each
