@@ -75,6 +75,8 @@ def lib() -> ctypes.CDLL:
         L.oracle_loss.restype = d
         L.oracle_adam.argtypes = [ll, P, P, P, P, P, d, d, d, i]
         L.oracle_real_sh.argtypes = [i, P, P, P]
+        L.oracle_tiles_fwd.argtypes = [i, i, P, i, P, i, i, P, P, P, P, P, P, P, P, P, i]
+        L.oracle_gauss_bwd.argtypes = [i, i, P, i, P, i, P, P, P, i, P, P, P]
         L.oracle_set_threads.argtypes = [i]
         L.oracle_max_threads.restype = i
         assert L.oracle_proj_stride() == len(PROJ_FIELDS)
@@ -264,3 +266,42 @@ def grad_groups_flat(K: int) -> dict:
     """Column slices of the packed Gaussian record per parameter group."""
     return {"means": slice(0, 3), "log_scales": slice(3, 6), "quats": slice(6, 10),
             "opacity_logits": slice(10, 11), "sh": slice(11, 11 + 3 * K)}
+
+
+def render_tiles(gs: dict, cams: dict, bg: np.ndarray, items, tile: int = 16, max_list: int = 20000) -> dict:
+    """Composite only the given (view, local tile id) items, one view at a
+    time; per item B x B pixels (row-major in the tile) and its sorted
+    Gaussian list."""
+    g = pack_gaussians(gs)
+    c = pack_cameras(cams)
+    n, K, V = g.shape[0], gs["sh"].shape[1], c.shape[0]
+    it = np.ascontiguousarray(np.asarray(items, dtype=np.int32).reshape(-1, 2))
+    m, B2 = it.shape[0], tile * tile
+    rgb = np.zeros((m, 3, B2))
+    alpha = np.zeros((m, B2))
+    T = np.zeros((m, B2))
+    nc = np.zeros((m, B2), dtype=np.int32)
+    amb = np.zeros((m, B2), dtype=np.uint8)
+    ll = np.zeros(m, dtype=np.int32)
+    lists = np.zeros((m, max_list), dtype=np.uint32)
+    bgd = np.ascontiguousarray(bg, dtype=np.float64).reshape(V, 3)
+    lib().oracle_tiles_fwd(n, K, _p(g), V, _p(c), tile, m, _p(it), _p(bgd), _p(rgb), _p(alpha), _p(T), _p(nc),
+                           _p(amb), _p(ll), _p(lists), max_list)
+    return {"rgb": rgb, "alpha": alpha, "T_final": T, "n_contrib": nc, "ambiguous": amb.astype(bool),
+            "list_len": ll, "lists": [lists[k, :min(ll[k], max_list)].copy() for k in range(m)]}
+
+
+def gaussian_grads(gs: dict, cams: dict, bg: np.ndarray, dL_drgb, dL_dalpha, req, tile: int = 16):
+    """Complete parameter gradients (rows in the packed Gaussian layout) of
+    the requested Gaussians, and their ambiguity flags."""
+    g = pack_gaussians(gs)
+    c = pack_cameras(cams)
+    n, K, V = g.shape[0], gs["sh"].shape[1], c.shape[0]
+    r = np.ascontiguousarray(np.asarray(req, dtype=np.int32))
+    out = np.zeros((r.size, 11 + 3 * K))
+    amb = np.zeros(r.size, dtype=np.uint8)
+    bgd = np.ascontiguousarray(bg, dtype=np.float64).reshape(V, 3)
+    lib().oracle_gauss_bwd(n, K, _p(g), V, _p(c), tile, _p(bgd),
+                           _p(np.ascontiguousarray(dL_drgb, dtype=np.float64)),
+                           _p(np.ascontiguousarray(dL_dalpha, dtype=np.float64)), r.size, _p(r), _p(out), _p(amb))
+    return out, amb.astype(bool)

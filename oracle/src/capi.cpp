@@ -23,6 +23,12 @@ double loss_fwd_bwd(int V, const int* W, const int* H, const double* rgb, const 
                     double* dL_drgb, double* dL_dalpha, double* ssim_out);
 void adam(long long n, double* p, const double* g, double* m, double* v, const double* lr, double b1, double b2,
           double eps, int step);
+void tiles_fwd(int n, int K, const double* gauss, const std::vector<Camera>& cams, int tile, int n_items,
+               const int32_t* items, const double* bg, double* rgb, double* alpha, double* T_final, int32_t* nc,
+               uint8_t* amb, int32_t* list_len, uint32_t* lists, int max_list);
+void gauss_bwd(int n, int K, const double* gauss, const std::vector<Camera>& cams, int tile, const double* bg,
+               const double* dL_drgb, const double* dL_dalpha, int n_req, const int32_t* req, double* grads_out,
+               uint8_t* amb_out);
 }  // namespace oracle
 
 using namespace oracle;
@@ -107,5 +113,19 @@ void oracle_adam(long long n, double* p, const double* g, double* m, double* v, 
 }
 
 void oracle_real_sh(int deg, const double* dir, double* Y, double* dY) { real_sh(deg, dir, Y, dY); }
+
+void oracle_tiles_fwd(int n, int K, const double* gauss, int V, const double* cams, int tile, int n_items,
+                      const int32_t* items, const double* bg, double* rgb, double* alpha, double* T_final,
+                      int32_t* nc, uint8_t* amb, int32_t* list_len, uint32_t* lists, int max_list) {
+    const std::vector<Camera> c = unpack_cameras(V, cams, tile);
+    tiles_fwd(n, K, gauss, c, tile, n_items, items, bg, rgb, alpha, T_final, nc, amb, list_len, lists, max_list);
+}
+
+void oracle_gauss_bwd(int n, int K, const double* gauss, int V, const double* cams, int tile, const double* bg,
+                      const double* dL_drgb, const double* dL_dalpha, int n_req, const int32_t* req,
+                      double* grads_out, uint8_t* amb_out) {
+    const std::vector<Camera> c = unpack_cameras(V, cams, tile);
+    gauss_bwd(n, K, gauss, c, tile, bg, dL_drgb, dL_dalpha, n_req, req, grads_out, amb_out);
+}
 
 }  // extern "C"

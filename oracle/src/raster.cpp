@@ -293,3 +293,157 @@ void render_bwd(int n, int K, const double* gauss, const std::vector<Camera>& ca
 }
 
 }  // namespace oracle
+
+// ---------------------------------------------------------------------------
+// Sampled evaluation for workloads too large to render whole (the same
+// arithmetic as above, one view at a time, only where asked).
+// ---------------------------------------------------------------------------
+
+namespace oracle {
+
+namespace {
+
+// Projection and sorted tile lists of one view.
+struct ViewBins {
+    std::vector<double> proj;  // n * P_STRIDE
+    std::vector<uint64_t> keys;
+    std::vector<uint32_t> vals, ranges;
+};
+
+void bin_view(int n, int K, const double* gauss, const Camera& cam, int tile, ViewBins& vb) {
+    vb.proj.assign((size_t)n * P_STRIDE, 0.0);
+    const int stride = gauss_stride(K);
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < n; ++i) project_one(gauss + (size_t)i * stride, K, cam, tile, 0, vb.proj.data() + (size_t)i * P_STRIDE);
+    Camera c = cam;
+    c.tile_offset = 0;
+    c.pixel_offset = 0;
+    std::vector<Camera> one{c};
+    bin_tiles(n, one, vb.proj.data(), vb.keys, vb.vals, vb.ranges);
+}
+
+}  // namespace
+
+// items: n_items (view, local tile) pairs. Per item, B x B pixels (row-major
+// in the tile; pixels outside the view get n_contrib -1): colour (3 planes),
+// alpha, T_final, n_contrib, ambiguity; and the tile's sorted Gaussian list
+// (list_len[item] entries, at most max_list copied).
+void tiles_fwd(int n, int K, const double* gauss, const std::vector<Camera>& cams, int tile, int n_items,
+               const int32_t* items, const double* bg, double* rgb, double* alpha, double* T_final, int32_t* nc,
+               uint8_t* amb, int32_t* list_len, uint32_t* lists, int max_list) {
+    const int B2 = tile * tile;
+    for (int v = 0; v < (int)cams.size(); ++v) {
+        bool any = false;
+        for (int k = 0; k < n_items; ++k) any = any || items[2 * k] == v;
+        if (!any) continue;
+        ViewBins vb;
+        bin_view(n, K, gauss, cams[v], tile, vb);
+        const Camera& cam = cams[v];
+        for (int k = 0; k < n_items; ++k) {
+            if (items[2 * k] != v) continue;
+            const int t = items[2 * k + 1];
+            const int tx = t % cam.tiles_x, ty = t / cam.tiles_x;
+            const uint32_t* list = vb.vals.data() + vb.ranges[2 * t];
+            const int count = (int)(vb.ranges[2 * t + 1] - vb.ranges[2 * t]);
+            list_len[k] = count;
+            for (int j = 0; j < count && j < max_list; ++j) lists[(size_t)k * max_list + j] = list[j];
+            Pixel px;
+            for (int q = 0; q < B2; ++q) {
+                const int pxx = tx * tile + q % tile, py = ty * tile + q / tile;
+                const size_t o = (size_t)k * B2 + q;
+                if (pxx >= cam.W || py >= cam.H) {
+                    nc[o] = -1;
+                    continue;
+                }
+                composite_pixel(pxx, py, list, count, vb.proj.data(), 0, px);
+                for (int ch = 0; ch < 3; ++ch) rgb[3 * (size_t)k * B2 + ch * B2 + q] = px.C[ch] + px.T * bg[3 * v + ch];
+                alpha[o] = 1.0 - px.T;
+                T_final[o] = px.T;
+                nc[o] = px.n_contrib;
+                amb[o] = px.ambiguous ? 1 : 0;
+            }
+        }
+    }
+}
+
+// Complete parameter gradients of the requested Gaussians: every tile any of
+// them covers is composited and back-propagated in full; dL_drgb / dL_dalpha
+// are the packed full-batch upstream gradients. amb_out marks requested
+// Gaussians whose own decision was near a threshold somewhere (or whose radius
+// lies within rounding of an integer in some view).
+void gauss_bwd(int n, int K, const double* gauss, const std::vector<Camera>& cams, int tile, const double* bg,
+               const double* dL_drgb, const double* dL_dalpha, int n_req, const int32_t* req, double* grads_out,
+               uint8_t* amb_out) {
+    const int stride = gauss_stride(K);
+    std::memset(grads_out, 0, sizeof(double) * (size_t)n_req * stride);
+    std::memset(amb_out, 0, (size_t)n_req);
+    std::vector<int> slot(n, -1);
+    for (int r = 0; r < n_req; ++r) slot[req[r]] = r;
+    for (int v = 0; v < (int)cams.size(); ++v) {
+        const Camera& cam = cams[v];
+        ViewBins vb;
+        bin_view(n, K, gauss, cam, tile, vb);
+        std::vector<char> want((size_t)cam.tiles_x * cam.tiles_y, 0);
+        bool any = false;
+        for (int r = 0; r < n_req; ++r) {
+            const double* p = vb.proj.data() + (size_t)req[r] * P_STRIDE;
+            if (p[P_VISIBLE] == 0.0) continue;
+            if (p[P_NEAR_BOUNDARY] != 0.0) amb_out[r] = 1;
+            for (int ty = (int)p[P_RECT_Y0]; ty < (int)p[P_RECT_Y1]; ++ty)
+                for (int tx = (int)p[P_RECT_X0]; tx < (int)p[P_RECT_X1]; ++tx) want[(size_t)ty * cam.tiles_x + tx] = 1;
+            any = true;
+        }
+        if (!any) continue;
+        std::vector<double> g2((size_t)n_req * 9, 0.0);
+        const long long plane = (long long)cam.W * cam.H;
+        for (int t = 0; t < cam.tiles_x * cam.tiles_y; ++t) {
+            if (!want[t]) continue;
+            const int tx = t % cam.tiles_x, ty = t / cam.tiles_x;
+            const uint32_t* list = vb.vals.data() + vb.ranges[2 * t];
+            const int count = (int)(vb.ranges[2 * t + 1] - vb.ranges[2 * t]);
+            Pixel px;
+            for (int py = ty * tile; py < std::min((ty + 1) * tile, cam.H); ++py)
+                for (int pxx = tx * tile; pxx < std::min((tx + 1) * tile, cam.W); ++pxx) {
+                    composite_pixel(pxx, py, list, count, vb.proj.data(), 0, px);
+                    for (int gi : px.ambiguous_gauss)
+                        if (slot[gi] >= 0) amb_out[slot[gi]] = 1;
+                    const long long pix = cam.pixel_offset + (long long)py * cam.W + pxx;
+                    double dC[3];
+                    for (int ch = 0; ch < 3; ++ch)
+                        dC[ch] = dL_drgb[3 * cam.pixel_offset + ch * plane + (long long)py * cam.W + pxx];
+                    const double dA = dL_dalpha[pix];
+                    const double TN = px.T;
+                    double S[3] = {0.0, 0.0, 0.0};
+                    for (int b = (int)px.blends.size() - 1; b >= 0; --b) {
+                        const Blend& e = px.blends[b];
+                        const double* p = vb.proj.data() + (size_t)e.gauss * P_STRIDE;
+                        const int sl = slot[e.gauss];
+                        double dalpha = dA * TN / (1.0 - e.alpha);
+                        for (int ch = 0; ch < 3; ++ch) {
+                            const double c = p[P_R + ch];
+                            dalpha += dC[ch] * (e.T * c - (S[ch] + TN * bg[3 * v + ch]) / (1.0 - e.alpha));
+                            if (sl >= 0) g2[(size_t)sl * 9 + 6 + ch] += dC[ch] * e.alpha * e.T;
+                        }
+                        for (int ch = 0; ch < 3; ++ch) S[ch] += p[P_R + ch] * e.alpha * e.T;
+                        if (sl < 0 || e.clamped) continue;
+                        const double dpower = dalpha * e.alpha;
+                        double* out = g2.data() + (size_t)sl * 9;
+                        out[0] += dpower * (p[P_CONIC_A] * e.dx + p[P_CONIC_B] * e.dy);
+                        out[1] += dpower * (p[P_CONIC_C] * e.dy + p[P_CONIC_B] * e.dx);
+                        out[2] += dpower * (-0.5 * e.dx * e.dx);
+                        out[3] += dpower * (-e.dx * e.dy);
+                        out[4] += dpower * (-0.5 * e.dy * e.dy);
+                        out[5] += dalpha * e.G;
+                    }
+                }
+        }
+        for (int r = 0; r < n_req; ++r) {
+            const double* p = vb.proj.data() + (size_t)req[r] * P_STRIDE;
+            if (p[P_VISIBLE] == 0.0) continue;
+            project_bwd_one(gauss + (size_t)req[r] * stride, K, cam, g2.data() + (size_t)r * 9,
+                            grads_out + (size_t)r * stride);
+        }
+    }
+}
+
+}  // namespace oracle
