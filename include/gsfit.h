@@ -269,8 +269,8 @@ int gsfit_loss_noalloc(const gsfit_camera* cams, int32_t n_views, const float* r
  *   through the projection (zero derivative where the frustum guard or the
  *   colour clamp is active) and summed over views into `grads`.
  * Arguments: g: the Gaussians that were projected; dL_drgb/dL_dalpha in the
- *   image layout; grad2d: device workspace of 12 floats per record
- *   (n_views * n * 48 bytes) that must be zero before the first call; this
+ *   image layout; grad2d: device workspace of 16 floats per record
+ *   (n_views * n * 64 bytes) that must be zero before the first call; this
  *   call leaves it zero again. grads: device, same layout as the parameters,
  *   fully overwritten (no zeroing needed).
  * Errors: GSFIT_ERR_INVALID_ARG, GSFIT_ERR_CUDA.

@@ -278,10 +278,132 @@ __global__ void __launch_bounds__(256) project_kernel(const float4* __restrict__
     }
 }
 
-// Adjoint of project_kernel. One thread per Gaussian, looping over views:
-// reads the per-(view, Gaussian) 2D gradients accumulated by the blend
-// adjoint (and zeroes them for the next iteration), chains them through the
-// projection and writes the summed parameter gradients once.
+// Adjoint of project_kernel, in two kernels.
+//
+// project_bwd_rec_kernel, one thread per binned (view, Gaussian) record (a 2D
+// grid: x over views, so that consecutive blocks read the same Gaussians from
+// L2; y over Gaussian blocks): chains the record's accumulated 2D gradients
+// through the conic, the EWA covariance, the Jacobian and the camera
+// transform, adds the view-direction term of the SH colour, and overwrites its
+// 16-float grad2d record with what the per-Gaussian sum needs: (dmean,
+// dopacity), dL/dSigma (6 entries) and the colour gradient with the clamp mask
+// applied. Fully parallel, so memory latency is hidden by occupancy rather
+// than by one thread's view loop.
+//
+// project_bwd_gauss_kernel, one thread per Gaussian: sums those records over
+// the views where the Gaussian was binned (zeroing them for the next
+// iteration), accumulates the SH-coefficient gradient, and chains dL/dSigma to
+// scale and rotation once.
+
+template <int DEG>
+__global__ void __launch_bounds__(256) project_bwd_rec_kernel(const float4* __restrict__ P, int n,
+                                                              const gsfit_camera* __restrict__ cams_g,
+                                                              const float4* __restrict__ xyd,
+                                                              const float4* __restrict__ conic,
+                                                              const float4* __restrict__ rgbm,
+                                                              float4* __restrict__ grad2d) {
+    const int i = blockIdx.y * blockDim.x + threadIdx.x;
+    const int v = blockIdx.x;
+    if (i >= n) return;
+    const size_t r = (size_t)v * n + i;
+    if (__ldg(&xyd[r].w) == 0.0f) return;  // not binned in this view
+    const float4 ga = grad2d[4 * r + 0];  // du, dv, dopacity
+    const float4 gb = grad2d[4 * r + 1];  // da', db', dc'
+    const float4 gc = grad2d[4 * r + 2];  // dr, dg, db
+    const float4 cq = __ldg(conic + r);
+    const float4 cm = __ldg(rgbm + r);
+    const gsfit_camera& cam = cams_g[v];
+    Gauss g;
+    load_gauss(P, n, i, g);
+    ViewGeom vg;
+    view_geom(cam, g, vg);
+    const float iz = 1.0f / vg.tz, iz2 = iz * iz;
+    float dtx = ga.x * cam.fx * iz;
+    float dty = ga.y * cam.fy * iz;
+    float dtz = -(ga.x * cam.fx * vg.tx + ga.y * cam.fy * vg.ty) * iz2;
+
+    // conic Q = S^-1: dL/dS = -Q G Q with G = [[da', db'/2], [db'/2, dc']]
+    const float q00 = cq.x, q01 = cq.y, q11 = cq.z;
+    const float g00 = gb.x, g01 = 0.5f * gb.y, g11 = gb.z;
+    const float t00 = q00 * g00 + q01 * g01, t01 = q00 * g01 + q01 * g11;
+    const float t10 = q01 * g00 + q11 * g01, t11 = q01 * g01 + q11 * g11;
+    const float dS00 = -(t00 * q00 + t01 * q01);
+    const float dS01 = -(t00 * q01 + t01 * q11);
+    const float dS11 = -(t10 * q01 + t11 * q11);
+
+    // S = M Sigma M^T: dSigma = M^T dS M; dM = 2 dS M Sigma
+    const float* M0 = vg.M0;
+    const float* M1 = vg.M1;
+    float u0[3], u1[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        u0[j] = dS00 * M0[j] + dS01 * M1[j];
+        u1[j] = dS01 * M0[j] + dS11 * M1[j];
+    }
+    float dSig[6];
+    dSig[0] = M0[0] * u0[0] + M1[0] * u1[0];
+    dSig[1] = M0[0] * u0[1] + M1[0] * u1[1];
+    dSig[2] = M0[0] * u0[2] + M1[0] * u1[2];
+    dSig[3] = M0[1] * u0[1] + M1[1] * u1[1];
+    dSig[4] = M0[1] * u0[2] + M1[1] * u1[2];
+    dSig[5] = M0[2] * u0[2] + M1[2] * u1[2];
+    const float* S = g.Sig;
+    float dM0[3], dM1[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float sk0 = (k == 0) ? S[0] : (k == 1) ? S[1] : S[2];
+        const float sk1 = (k == 0) ? S[1] : (k == 1) ? S[3] : S[4];
+        const float sk2 = (k == 0) ? S[2] : (k == 1) ? S[4] : S[5];
+        dM0[k] = 2.f * (u0[0] * sk0 + u0[1] * sk1 + u0[2] * sk2);
+        dM1[k] = 2.f * (u1[0] * sk0 + u1[1] * sk1 + u1[2] * sk2);
+    }
+    // M = J W: dJ = dM W^T (only J00, J02, J11, J12 are non-zero)
+    const float* W = cam.viewmat;
+    const float dJ00 = dM0[0] * W[0] + dM0[1] * W[1] + dM0[2] * W[2];
+    const float dJ02 = dM0[0] * W[8] + dM0[1] * W[9] + dM0[2] * W[10];
+    const float dJ11 = dM1[0] * W[4] + dM1[1] * W[5] + dM1[2] * W[6];
+    const float dJ12 = dM1[0] * W[8] + dM1[1] * W[9] + dM1[2] * W[10];
+    dtz += -dJ00 * cam.fx * iz2 - dJ11 * cam.fy * iz2 + dJ02 * cam.fx * vg.rx * iz2 + dJ12 * cam.fy * vg.ry * iz2;
+    const float drx = -dJ02 * cam.fx * iz, dry = -dJ12 * cam.fy * iz;
+    if (!vg.gx) {
+        dtx += drx * iz;
+        dtz -= drx * vg.tx * iz2;
+    }
+    if (!vg.gy) {
+        dty += dry * iz;
+        dtz -= dry * vg.ty * iz2;
+    }
+    // t = W mu + t_w
+    float dmean[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) dmean[j] = W[j] * dtx + W[4 + j] * dty + W[8 + j] * dtz;
+    // colour: clamped channels pass no gradient
+    const int mask = (int)cm.w;
+    const float gcol[3] = {(mask & 1) ? 0.f : gc.x, (mask & 2) ? 0.f : gc.y, (mask & 4) ? 0.f : gc.z};
+    if (DEG > 0) {
+        // colour = sum_k c_k Y_k(d), d = (mu - campos) / |mu - campos|
+        constexpr int K = SH<DEG>::K;
+        float dx = g.mx - cam.campos[0], dy = g.my - cam.campos[1], dz = g.mz - cam.campos[2];
+        const float idist = rsqrtf(dx * dx + dy * dy + dz * dz);
+        dx *= idist; dy *= idist; dz *= idist;
+        float sh[3 * K];
+        load_sh<DEG>(P, n, i, sh);
+        float wk[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            wk[k] = sh[3 * k + 0] * gcol[0] + sh[3 * k + 1] * gcol[1] + sh[3 * k + 2] * gcol[2];
+        const float3 dd = sh_basis_vjp<DEG>(dx, dy, dz, wk);
+        const float proj = dx * dd.x + dy * dd.y + dz * dd.z;
+        dmean[0] += (dd.x - dx * proj) * idist;
+        dmean[1] += (dd.y - dy * proj) * idist;
+        dmean[2] += (dd.z - dz * proj) * idist;
+    }
+    grad2d[4 * r + 0] = make_float4(dmean[0], dmean[1], dmean[2], ga.z);
+    grad2d[4 * r + 1] = make_float4(dSig[0], dSig[1], dSig[2], dSig[3]);
+    grad2d[4 * r + 2] = make_float4(dSig[4], dSig[5], gcol[0], gcol[1]);
+    grad2d[4 * r + 3] = make_float4(gcol[2], 0.f, 0.f, 0.f);
+}
+
 constexpr int kProjBwdThreads = 256;
 
 // Accumulator k of this thread's SH gradient; [k][thread] layout, so a warp's
@@ -289,12 +411,11 @@ constexpr int kProjBwdThreads = 256;
 __device__ __forceinline__ float& dsh_acc(float* s_dsh, int k) { return s_dsh[k * kProjBwdThreads + threadIdx.x]; }
 
 template <int DEG>
-__global__ void __launch_bounds__(kProjBwdThreads, 3) project_bwd_kernel(
+__global__ void __launch_bounds__(kProjBwdThreads, 3) project_bwd_gauss_kernel(
     const float4* __restrict__ P, int n, const gsfit_camera* __restrict__ cams_g, int n_views,
-    const float4* __restrict__ xyd, const float4* __restrict__ conic, const float4* __restrict__ rgbm,
-    float4* __restrict__ grad2d, float4* __restrict__ G) {
+    const float4* __restrict__ xyd, float4* __restrict__ grad2d, float4* __restrict__ G) {
     // dynamic shared memory: the camera table, then 3K SH-gradient accumulators
-    // per thread (kept out of registers so three CTAs fit per SM)
+    // per thread (kept out of registers)
     extern __shared__ __align__(16) unsigned char smem_pb[];
     gsfit_camera* cams = reinterpret_cast<gsfit_camera*>(smem_pb);
     float* s_dsh = reinterpret_cast<float*>(smem_pb + sizeof(gsfit_camera) * n_views);
@@ -305,13 +426,12 @@ __global__ void __launch_bounds__(kProjBwdThreads, 3) project_bwd_kernel(
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    Gauss g;
-    load_gauss(P, n, i, g);
-    const float opacity = 1.0f / (1.0f + expf(-g.logit));
+    const float4 mean = P[i];  // the rest of the Gaussian is loaded after the view loop
 
     float dmean[3] = {0.f, 0.f, 0.f};
     float dSig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // xx xy xz yy yz zz (symmetric, dL/dSigma_ij)
-    float dlogit = 0.f;
+    float dop = 0.f;
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
 
     for (int v0 = 0; v0 < n_views; v0 += 32) {
       // visibility of up to 32 views first: independent loads, one latency
@@ -324,110 +444,36 @@ __global__ void __launch_bounds__(kProjBwdThreads, 3) project_bwd_kernel(
         const int v = v0 + __ffs(vis) - 1;
         vis &= vis - 1;
         const size_t r = (size_t)v * n + i;
-        // every load of this view issued together
-        const float4 ga = grad2d[3 * r + 0];  // du, dv, dopacity
-        const float4 gb = grad2d[3 * r + 1];  // da', db', dc'
-        const float4 gc = grad2d[3 * r + 2];  // dr, dg, db
-        const float4 cq = __ldg(conic + r);
-        const float4 cm = __ldg(rgbm + r);
-        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-        grad2d[3 * r + 0] = zero;
-        grad2d[3 * r + 1] = zero;
-        grad2d[3 * r + 2] = zero;
+        const float4 a = grad2d[4 * r + 0];
+        const float4 b = grad2d[4 * r + 1];
+        const float4 c = grad2d[4 * r + 2];
+        const float4 d = grad2d[4 * r + 3];
+        grad2d[4 * r + 0] = zero;
+        grad2d[4 * r + 1] = zero;
+        grad2d[4 * r + 2] = zero;
+        grad2d[4 * r + 3] = zero;
+        dmean[0] += a.x; dmean[1] += a.y; dmean[2] += a.z;
+        dop += a.w;
+        dSig[0] += b.x; dSig[1] += b.y; dSig[2] += b.z; dSig[3] += b.w; dSig[4] += c.x; dSig[5] += c.y;
+        const float gcol[3] = {c.z, c.w, d.x};
         const gsfit_camera& cam = cams[v];
-        ViewGeom vg;
-        view_geom(cam, g, vg);
-        const float iz = 1.0f / vg.tz, iz2 = iz * iz;
-        float dtx = ga.x * cam.fx * iz;
-        float dty = ga.y * cam.fy * iz;
-        float dtz = -(ga.x * cam.fx * vg.tx + ga.y * cam.fy * vg.ty) * iz2;
-
-        // conic Q = S^-1: dL/dS = -Q G Q with G = [[da', db'/2], [db'/2, dc']]
-        const float q00 = cq.x, q01 = cq.y, q11 = cq.z;
-        const float g00 = gb.x, g01 = 0.5f * gb.y, g11 = gb.z;
-        const float t00 = q00 * g00 + q01 * g01, t01 = q00 * g01 + q01 * g11;
-        const float t10 = q01 * g00 + q11 * g01, t11 = q01 * g01 + q11 * g11;
-        const float dS00 = -(t00 * q00 + t01 * q01);
-        const float dS01 = -(t00 * q01 + t01 * q11);
-        const float dS11 = -(t10 * q01 + t11 * q11);
-
-        // S = M Sigma M^T: dSigma += M^T dS M; dM = 2 dS M Sigma
-        const float* M0 = vg.M0;
-        const float* M1 = vg.M1;
-        float u0[3], u1[3];  // dS rows applied to M: u0 = dS00 M0 + dS01 M1, u1 = dS01 M0 + dS11 M1
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            u0[j] = dS00 * M0[j] + dS01 * M1[j];
-            u1[j] = dS01 * M0[j] + dS11 * M1[j];
-        }
-        dSig[0] += M0[0] * u0[0] + M1[0] * u1[0];
-        dSig[1] += M0[0] * u0[1] + M1[0] * u1[1];
-        dSig[2] += M0[0] * u0[2] + M1[0] * u1[2];
-        dSig[3] += M0[1] * u0[1] + M1[1] * u1[1];
-        dSig[4] += M0[1] * u0[2] + M1[1] * u1[2];
-        dSig[5] += M0[2] * u0[2] + M1[2] * u1[2];
-        const float* S = g.Sig;
-        float dM0[3], dM1[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const float sk0 = (k == 0) ? S[0] : (k == 1) ? S[1] : S[2];
-            const float sk1 = (k == 0) ? S[1] : (k == 1) ? S[3] : S[4];
-            const float sk2 = (k == 0) ? S[2] : (k == 1) ? S[4] : S[5];
-            dM0[k] = 2.f * (u0[0] * sk0 + u0[1] * sk1 + u0[2] * sk2);
-            dM1[k] = 2.f * (u1[0] * sk0 + u1[1] * sk1 + u1[2] * sk2);
-        }
-        // M = J W: dJ = dM W^T (only J00, J02, J11, J12 are non-zero)
-        const float* W = cam.viewmat;
-        const float dJ00 = dM0[0] * W[0] + dM0[1] * W[1] + dM0[2] * W[2];
-        const float dJ02 = dM0[0] * W[8] + dM0[1] * W[9] + dM0[2] * W[10];
-        const float dJ11 = dM1[0] * W[4] + dM1[1] * W[5] + dM1[2] * W[6];
-        const float dJ12 = dM1[0] * W[8] + dM1[1] * W[9] + dM1[2] * W[10];
-        dtz += -dJ00 * cam.fx * iz2 - dJ11 * cam.fy * iz2 + dJ02 * cam.fx * vg.rx * iz2 +
-               dJ12 * cam.fy * vg.ry * iz2;
-        const float drx = -dJ02 * cam.fx * iz, dry = -dJ12 * cam.fy * iz;
-        if (!vg.gx) {
-            dtx += drx * iz;
-            dtz -= drx * vg.tx * iz2;
-        }
-        if (!vg.gy) {
-            dty += dry * iz;
-            dtz -= dry * vg.ty * iz2;
-        }
-        // t = W mu + t_w
-#pragma unroll
-        for (int j = 0; j < 3; ++j) dmean[j] += W[j] * dtx + W[4 + j] * dty + W[8 + j] * dtz;
-
-        dlogit += ga.z * opacity * (1.f - opacity);
-
-        // colour: clamped channels pass no gradient
-        const int mask = (int)cm.w;
-        const float gcol[3] = {(mask & 1) ? 0.f : gc.x, (mask & 2) ? 0.f : gc.y, (mask & 4) ? 0.f : gc.z};
-        float dx = g.mx - cam.campos[0], dy = g.my - cam.campos[1], dz = g.mz - cam.campos[2];
-        const float dist = sqrtf(dx * dx + dy * dy + dz * dz);
-        const float idist = 1.0f / dist;
+        float dx = mean.x - cam.campos[0], dy = mean.y - cam.campos[1], dz = mean.z - cam.campos[2];
+        const float idist = rsqrtf(dx * dx + dy * dy + dz * dz);
         dx *= idist; dy *= idist; dz *= idist;
         float Y[K];
         sh_basis<DEG>(dx, dy, dz, Y);
-        // coefficients re-read per view (L1-resident across the view loop)
-        float sh[3 * K];
-        load_sh<DEG>(P, n, i, sh);
-        float wk[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             dsh_acc(s_dsh, 3 * k + 0) += Y[k] * gcol[0];
             dsh_acc(s_dsh, 3 * k + 1) += Y[k] * gcol[1];
             dsh_acc(s_dsh, 3 * k + 2) += Y[k] * gcol[2];
-            wk[k] = sh[3 * k + 0] * gcol[0] + sh[3 * k + 1] * gcol[1] + sh[3 * k + 2] * gcol[2];
-        }
-        if (DEG > 0) {
-            const float3 dd = sh_basis_vjp<DEG>(dx, dy, dz, wk);
-            const float proj = dx * dd.x + dy * dd.y + dz * dd.z;
-            dmean[0] += (dd.x - dx * proj) * idist;
-            dmean[1] += (dd.y - dy * proj) * idist;
-            dmean[2] += (dd.z - dz * proj) * idist;
         }
       }
     }
+    Gauss g;
+    load_gauss(P, n, i, g);
+    const float opacity = 1.0f / (1.0f + expf(-g.logit));
+    const float dlogit = dop * opacity * (1.f - opacity);
 
     // Sigma = Ms Ms^T, Ms = R diag(s): dMs = 2 dSigma Ms
     const float* R = g.R;
@@ -490,6 +536,12 @@ int launch_project_bwd(const gsfit_gaussians* g, const gsfit_proj* proj, const g
                        float* grad2d, float* grads, cudaStream_t s) {
     const int threads = kProjBwdThreads;
     const int blocks = (g->n + threads - 1) / threads;
+    dim3 grid_rec((unsigned)V, (unsigned)blocks);
+    project_bwd_rec_kernel<DEG><<<grid_rec, threads, 0, s>>>(
+        reinterpret_cast<const float4*>(g->params), g->n, cams, reinterpret_cast<const float4*>(proj->xyd),
+        reinterpret_cast<const float4*>(proj->conic), reinterpret_cast<const float4*>(proj->rgb),
+        reinterpret_cast<float4*>(grad2d));
+    GSFIT_LAUNCH_CHECK();
     const size_t smem = sizeof(gsfit_camera) * V + sizeof(float) * 3 * SH<DEG>::K * threads;
     static bool attr_done[64] = {false};
     int dev = 0;
@@ -497,13 +549,12 @@ int launch_project_bwd(const gsfit_gaussians* g, const gsfit_proj* proj, const g
     if (dev < 0 || dev >= 64) return GSFIT_ERR_CUDA;
     if (!attr_done[dev]) {
         const size_t max_smem = sizeof(gsfit_camera) * GSFIT_MAX_VIEWS + sizeof(float) * 3 * SH<DEG>::K * threads;
-        GSFIT_CUDA_CHECK(cudaFuncSetAttribute(project_bwd_kernel<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)max_smem));
+        GSFIT_CUDA_CHECK(cudaFuncSetAttribute(project_bwd_gauss_kernel<DEG>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem));
         attr_done[dev] = true;
     }
-    project_bwd_kernel<DEG><<<blocks, threads, smem, s>>>(
+    project_bwd_gauss_kernel<DEG><<<blocks, threads, smem, s>>>(
         reinterpret_cast<const float4*>(g->params), g->n, cams, V, reinterpret_cast<const float4*>(proj->xyd),
-        reinterpret_cast<const float4*>(proj->conic), reinterpret_cast<const float4*>(proj->rgb),
         reinterpret_cast<float4*>(grad2d), reinterpret_cast<float4*>(grads));
     GSFIT_LAUNCH_CHECK();
     return GSFIT_OK;

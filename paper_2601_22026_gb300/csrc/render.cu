@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(
     const uint32_t lt = (1u << lane) - 1u;
     const float bg0 = bg[3 * c.view], bg1 = bg[3 * c.view + 1], bg2 = bg[3 * c.view + 2];
     const int slot = reduce9_slot(lane);
-    const int slot_off = slot + slot / 3;  // floats (du dv do _ | da db dc _ | dr dg db _) per record
+    const int slot_off = slot + slot / 3;  // floats (du dv do _ | da db dc _ | dr dg db _ | ....) of a record
 
     PixBwd q;
     q.T = 1.f; q.last = 0; q.dC0 = q.dC1 = q.dC2 = q.dA = 0.f;
@@ -426,7 +426,7 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(
                                           fy - p.y, g9);
             if (__any_sync(0xffffffffu, hit)) {
                 const float tot = reduce9(g9, lane);
-                if (slot >= 0) atomicAdd(grad2d + 12 * (rec0 + S.g[buf][j]) + slot_off, tot);
+                if (slot >= 0) atomicAdd(grad2d + 16 * (rec0 + S.g[buf][j]) + slot_off, tot);
             }
         }
         b1 = pb1;
