@@ -205,12 +205,20 @@ int gsfit_bin_sort(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_v
  *   alpha, T_final: total_pixels floats, n_contrib: total_pixels uint32
  *   (device). vals/ranges/tile_order from gsfit_bin_sort (tile_order may be
  *   null: tiles in id order; the results do not depend on the order).
- * Errors: GSFIT_ERR_INVALID_ARG, GSFIT_ERR_CUDA.
+ *   status: device int32 or null. The kernel's warps hand records to each
+ *   other through shared-memory barriers whose waits are bounded (about a
+ *   second); if one runs out (which a correct launch never does) the kernel
+ *   writes GSFIT_ERR_TIMEOUT there, the affected tiles' outputs are
+ *   incomplete, and later tiles of this and the other compositing calls that
+ *   see that value skip their work. With a null status a timeout goes
+ *   unreported.
+ * Errors: GSFIT_ERR_INVALID_ARG, GSFIT_ERR_CUDA; GSFIT_ERR_TIMEOUT on the
+ *   device, through status.
  */
 int gsfit_render_fwd(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_views, int32_t n,
                      int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges, const uint32_t* tile_order,
                      const float* bg, float* rgb, float* alpha, float* T_final, uint32_t* n_contrib,
-                     cudaStream_t stream);
+                     int32_t* status, cudaStream_t stream);
 
 /*
  * gsfit_loss -- photometric loss of a view batch and its gradient.
@@ -272,13 +280,15 @@ int gsfit_loss_noalloc(const gsfit_camera* cams, int32_t n_views, const float* r
  *   image layout; grad2d: device workspace of 16 floats per record
  *   (n_views * n * 64 bytes) that must be zero before the first call; this
  *   call leaves it zero again. grads: device, same layout as the parameters,
- *   fully overwritten (no zeroing needed).
- * Errors: GSFIT_ERR_INVALID_ARG, GSFIT_ERR_CUDA.
+ *   fully overwritten (no zeroing needed). status: as for gsfit_render_fwd.
+ * Errors: GSFIT_ERR_INVALID_ARG, GSFIT_ERR_CUDA; GSFIT_ERR_TIMEOUT on the
+ *   device, through status.
  */
 int gsfit_render_bwd(const gsfit_gaussians* g, const gsfit_proj* proj, const gsfit_camera* cams,
                      int32_t n_views, int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges,
                      const uint32_t* tile_order, const float* bg, const float* T_final, const uint32_t* n_contrib,
-                     const float* dL_drgb, const float* dL_dalpha, float* grad2d, float* grads, cudaStream_t stream);
+                     const float* dL_drgb, const float* dL_dalpha, float* grad2d, float* grads, int32_t* status,
+                     cudaStream_t stream);
 
 /*
  * gsfit_blend_bwd / gsfit_project_bwd -- the two halves of gsfit_render_bwd,
@@ -287,12 +297,14 @@ int gsfit_render_bwd(const gsfit_gaussians* g, const gsfit_proj* proj, const gsf
  * (u, v, conic, opacity, rgb) into grad2d (which must be zero on entry);
  * gsfit_project_bwd chains them through the projection, sums them over views
  * into `grads` (fully overwritten) and zeroes grad2d again. Arguments as for
- * gsfit_render_bwd. Errors: GSFIT_ERR_INVALID_ARG, GSFIT_ERR_CUDA.
+ * gsfit_render_bwd (status only for gsfit_blend_bwd). Errors:
+ * GSFIT_ERR_INVALID_ARG, GSFIT_ERR_CUDA; GSFIT_ERR_TIMEOUT on the device,
+ * through status.
  */
 int gsfit_blend_bwd(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_views, int32_t n,
                     int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges, const uint32_t* tile_order,
                     const float* bg, const float* T_final, const uint32_t* n_contrib, const float* dL_drgb,
-                    const float* dL_dalpha, float* grad2d, cudaStream_t stream);
+                    const float* dL_dalpha, float* grad2d, int32_t* status, cudaStream_t stream);
 int gsfit_project_bwd(const gsfit_gaussians* g, const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_views,
                       float* grad2d, float* grads, cudaStream_t stream);
 

@@ -11,9 +11,10 @@
 // the heavy-first order gsfit_bin_sort produces, so the longest lists do not
 // form the tail of the grid. The CTA stages the tile's records in batches of
 // 256 (one coalesced record per thread); each warp then compacts, with a
-// ballot, the batch entries whose opacity-aware extent can reach alpha >=
-// 1/255 somewhere in its box (a conservative test: every pixel of the box
-// would skip the others anyway) and walks only those. The adjoint copies the
+// ballot, the batch entries that reach alpha >= 1/255 somewhere in its box
+// (the exact minimum of the splat's quadratic form over the box, with slack
+// for rounding: every pixel of the box would skip the others anyway) and
+// walks only those. The adjoint copies the
 // next batch with cp.async while it works on the current one (the forward, which
 // often stops early, stages one batch at a time). The adjoint
 // keeps no per-(pixel, Gaussian) state: it restarts from the stored final
@@ -28,9 +29,10 @@ namespace gsfit {
 
 namespace {
 
-constexpr int kRenderThreads = kTilePixels;  // one pixel per thread
-constexpr int kRenderWarps = kRenderThreads / 32;
-constexpr int kBatch = kRenderThreads;       // records staged per batch
+constexpr int kRenderWarps = kTilePixels / 32;       // pixel warps, one pixel per thread
+constexpr int kRenderThreads = kTilePixels + 32;     // + the producer warp
+constexpr int kCountThreads = kTilePixels;
+constexpr int kBatch = kCountThreads;                // records staged per batch (counter)
 constexpr float kCullMargin = 0.02f;         // slack (units of the quadratic form) of the warp cull
 
 // This thread's pixel: warp w covers the 8 x 4 box at (8 (w mod 2), 4 (w / 2))
@@ -39,7 +41,7 @@ struct TileCtx {
     int view, px, py;
     bool inside;
     long long pix, plane, rgb_base;
-    float box_cx, box_cy;  // centre of the warp's box of pixel centres
+    float box_x0, box_y0;  // first pixel centre of the warp's box
 };
 
 __device__ __forceinline__ TileCtx tile_ctx(const gsfit_camera* cams, int n_views, int t) {
@@ -57,28 +59,50 @@ __device__ __forceinline__ TileCtx tile_ctx(const gsfit_camera* cams, int n_view
     c.plane = (long long)cam.width * cam.height;
     c.pix = (long long)cam.pixel_offset + (long long)c.py * cam.width + c.px;
     c.rgb_base = 3ll * cam.pixel_offset + (long long)c.py * cam.width + c.px;
-    c.box_cx = (float)(tx * kTile + bx) + 3.5f;
-    c.box_cy = (float)(ty * kTile + by) + 1.5f;
+    c.box_x0 = (float)(tx * kTile + bx);
+    c.box_y0 = (float)(ty * kTile + by);
     return c;
 }
 
-// Half-extents of the region where a splat can reach alpha >= 1/255:
-// o exp(-q/2) >= 1/255  <=>  q <= 2 ln(255 o), q the conic's quadratic form;
-// the ellipse q <= t has half-widths sqrt(t Sigma'_xx), sqrt(t Sigma'_yy).
-// Negative extents mark a splat that cannot reach the threshold anywhere.
-__device__ __forceinline__ float2 alpha_extent(float4 co) {
+// Cull parameters of a splat: alpha >= 1/255 needs o exp(-q/2) >= 1/255, i.e.
+// q <= t = 2 ln(255 o), with q(d) = a' dx^2 + 2 b' dx dy + c' dy^2 the
+// conic's quadratic form; t < 0 marks a splat that reaches the threshold
+// nowhere. Also -b'/c' and -b'/a', the minimisers of q along a fixed dx or dy.
+// A degenerate conic (never produced by the projection) is never culled.
+__device__ __forceinline__ float4 cull_params(float4 co) {
     const float t = 2.0f * __logf(255.0f * co.w) + kCullMargin;
-    if (!(t > 0.0f)) return make_float2(-1.f, -1.f);
-    const float det = co.x * co.z - co.y * co.y;
-    if (!(det > 0.0f)) return make_float2(1e30f, 1e30f);  // degenerate conic: never cull
-    const float ex = sqrtf(t * co.z / det), ey = sqrtf(t * co.x / det);
-    return make_float2(ex * 1.001f + 0.05f, ey * 1.001f + 0.05f);
+    if (!(t > 0.0f)) return make_float4(-1.f, 0.f, 0.f, 0.f);
+    if (!(co.x > 0.0f && co.z > 0.0f && co.x * co.z - co.y * co.y > 0.0f)) return make_float4(1e30f, 0.f, 0.f, 0.f);
+    return make_float4(t, -co.y / co.z, -co.y / co.x, 0.f);
 }
 
-// One batch of staged records (shared memory).
+// Can a splat reach alpha >= 1/255 at some pixel centre of this warp's box?
+// Exact minimum of q over the rectangle of offsets d = pixel - centre: zero
+// if the centre lies inside; otherwise q is convex with its minimum outside,
+// so the constrained minimum lies on an edge facing the centre, x = xe or
+// y = ye (the rectangle's point nearest to the centre per axis), where the 1D
+// minimiser is clamped to the edge. Conservative against float rounding: the
+// slack 1e-5 (a' x^2 + c' y^2) bounds the rounding of both this evaluation
+// and the pixel's own (|2 b' x y| <= a' x^2 + c' y^2 for a positive form), and
+// the margin in t covers that of exp and log.
+// Entries without a record (past the list end, or an index only a failed
+// sort produces) carry t < 0 and are rejected before their (stale) record is
+// looked at.
+__device__ __forceinline__ bool box_reach(float ux, float uy, float4 co, float4 cp, float box_x0, float box_y0) {
+    if (!(cp.x > 0.0f)) return false;
+    const float X0 = box_x0 - ux, X1 = X0 + 7.0f, Y0 = box_y0 - uy, Y1 = Y0 + 3.0f;
+    const float xe = fminf(fmaxf(0.0f, X0), X1), ye = fminf(fmaxf(0.0f, Y0), Y1);
+    const float y1 = fminf(fmaxf(cp.y * xe, Y0), Y1);
+    const float x2 = fminf(fmaxf(cp.z * ye, X0), X1);
+    const float s1 = co.x * xe * xe + co.z * y1 * y1, s2 = co.x * x2 * x2 + co.z * ye * ye;
+    const float q1 = s1 + 2.0f * co.y * xe * y1, q2 = s2 + 2.0f * co.y * x2 * ye;
+    return fminf(q1 - 1e-5f * s1, q2 - 1e-5f * s2) <= cp.x;
+}
+
+// One batch of staged records (shared memory), for the diagnostic counter.
 struct Batch {
     float2 xy[kBatch];
-    float2 ext[kBatch];
+    float4 cp[kBatch];
     float4 co[kBatch];
     float4 col[kBatch];
     uint32_t g[kBatch];
@@ -101,141 +125,231 @@ __device__ __forceinline__ void stage(Batch& S, uint32_t idx, uint32_t end, cons
         S.xy[t] = make_float2(p.x, p.y);
         S.co[t] = co;
         S.col[t] = __ldg(rgb + k);
-        S.ext[t] = alpha_extent(co);
+        S.cp[t] = cull_params(co);
     } else {
-        S.ext[t] = make_float2(-1.f, -1.f);
+        S.cp[t] = make_float4(-1.f, 0.f, 0.f, 0.f);
     }
     S.g[t] = g;
 }
 
-// Can entry j reach alpha >= 1/255 at a pixel centre of this warp's box?
-__device__ __forceinline__ bool box_hit(const Batch& S, int j, const TileCtx& c) {
-    const float2 p = S.xy[j];
-    const float2 e = S.ext[j];
-    return e.x >= 0.0f && fabsf(p.x - c.box_cx) <= 3.5f + e.x && fabsf(p.y - c.box_cy) <= 1.5f + e.y;
-}
+// ---------------------------------------------------------------------------
+// Record ring of the compositing kernels. A producer warp gathers the tile's
+// records (by Gaussian index, 16-byte cp.async copies) into kRing slots of
+// kSlot entries and adds each entry's cull parameters; the eight pixel warps
+// consume the slots in order. Slot s has two mbarriers: full[s] (the
+// producer's 32 lanes arrive once the slot is written) and empty[s] (the 256
+// consumer threads arrive once they are done reading it). So a pixel warp
+// waits only for data, never for the other pixel warps, and can run up to
+// kRing - 1 slots ahead of the slowest. A slot with count 0 ends the list.
+// Every wait is bounded (kWaitCycles, about a second): on expiry the status
+// word gets GSFIT_ERR_TIMEOUT, the warp stops, and later tiles skip their work.
+constexpr int kSlot = 128;
+constexpr int kRing = 4;
+constexpr long long kWaitCycles = 1ll << 31;
 
-// Double-buffered staging (adjoint): while the warps work on one batch,
-// cp.async copies the next batch's 16-byte records (gathered by Gaussian index) into
-// the other buffer; only the index of the batch after that occupies a
-// register. Entries past the list end, or with an out-of-range index (which
-// only a failed sort produces), are never copied and are culled.
-struct Batch2 {
-    float4 xyd[2][kBatch];
-    float4 co[2][kBatch];
-    float4 col[2][kBatch];
-    float2 ext[2][kBatch];
-    uint32_t g[2][kBatch];
+struct Ring {
+    float4 xyd[kRing][kSlot];
+    float4 co[kRing][kSlot];
+    float4 col[kRing][kSlot];
+    float4 cp[kRing][kSlot];
+    uint32_t g[kRing][kSlot];
+    int cnt[kRing];
+    unsigned long long full[kRing];
+    unsigned long long empty[kRing];
 };
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Waits for the completion of the barrier phase of the given parity; false
+// (and the status word set) if it does not complete within kWaitCycles.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, uint32_t parity, int32_t* status) {
+    if (mbar_try_wait(b, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(b, parity)) {
+        if (clock64() - t0 > kWaitCycles) {
+            if (status) atomicExch(status, GSFIT_ERR_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t load_index(uint32_t idx, uint32_t end, const uint32_t* __restrict__ vals, int n) {
     if (idx >= end) return 0xffffffffu;
     const uint32_t g = __ldg(vals + idx);
-    return g < (uint32_t)n ? g : 0xffffffffu;
+    return g < (uint32_t)n ? g : 0xffffffffu;  // out of range only after a failed sort: never blended
 }
 
-// This thread's copies of record g into slot threadIdx.x of buffer b.
-__device__ __forceinline__ void issue_rec(Batch2& S, int b, uint32_t g, const float4* __restrict__ xyd,
-                                          const float4* __restrict__ conic, const float4* __restrict__ rgb,
-                                          size_t rec0) {
-    if (g != 0xffffffffu) {
-        const size_t k = rec0 + g;
-        const int t = threadIdx.x;
-        cp_async16(&S.xyd[b][t], xyd + k);
-        cp_async16(&S.co[b][t], conic + k);
-        cp_async16(&S.col[b][t], rgb + k);
+__device__ __forceinline__ void ring_init(Ring& R) {
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kRing; ++s) {
+            mbar_init(&R.full[s], 32);
+            mbar_init(&R.empty[s], 32 * kRenderWarps);
+        }
     }
 }
 
-// After this thread's copies into buffer b have landed: its slot's extents.
-__device__ __forceinline__ void finish_rec(Batch2& S, int b, uint32_t g) {
-    const int t = threadIdx.x;
-    S.ext[b][t] = g != 0xffffffffu ? alpha_extent(S.co[b][t]) : make_float2(-1.f, -1.f);
-    S.g[b][t] = g;
+__device__ __forceinline__ bool timed_out(const int32_t* status) {
+    return status && *reinterpret_cast<const volatile int32_t*>(status) == GSFIT_ERR_TIMEOUT;
 }
 
-__device__ __forceinline__ bool box_hit2(const Batch2& S, int b, int j, const TileCtx& c) {
-    const float4 p = S.xyd[b][j];
-    const float2 e = S.ext[b][j];
-    return e.x >= 0.0f && fabsf(p.x - c.box_cx) <= 3.5f + e.x && fabsf(p.y - c.box_cy) <= 1.5f + e.y;
+// Producer side: fills slot k % kRing with list positions [b0, b0 + cnt)
+// (cnt = 0 publishes the end of the list). Returns false on a timeout.
+__device__ __forceinline__ bool ring_produce(Ring& R, int k, uint32_t b0, int cnt, const uint32_t* __restrict__ vals,
+                                             const float4* __restrict__ xyd, const float4* __restrict__ conic,
+                                             const float4* __restrict__ rgb, size_t rec0, int n,
+                                             int32_t* status) {
+    const int s = k % kRing;
+    const int lane = threadIdx.x & 31;
+    if (k >= kRing && !mbar_wait(&R.empty[s], ((k / kRing) & 1) ^ 1, status)) return false;
+    uint32_t g[kSlot / 32];
+#pragma unroll
+    for (int q = 0; q < kSlot / 32; ++q) g[q] = load_index(b0 + 32 * q + lane, b0 + cnt, vals, n);
+#pragma unroll
+    for (int q = 0; q < kSlot / 32; ++q) {
+        if (g[q] != 0xffffffffu) {
+            const int e = 32 * q + lane;
+            const size_t r = rec0 + g[q];
+            cp_async16(&R.xyd[s][e], xyd + r);
+            cp_async16(&R.co[s][e], conic + r);
+            cp_async16(&R.col[s][e], rgb + r);
+        }
+    }
+    cp_async_commit();
+    cp_async_wait_all();
+#pragma unroll
+    for (int q = 0; q < kSlot / 32; ++q) {
+        const int e = 32 * q + lane;
+        R.cp[s][e] = g[q] != 0xffffffffu ? cull_params(R.co[s][e]) : make_float4(-1.f, 0.f, 0.f, 0.f);
+        R.g[s][e] = g[q];
+    }
+    if (lane == 0) R.cnt[s] = cnt;
+    mbar_arrive(&R.full[s]);
+    return true;
+}
+
+// This warp's entries of slot s that can blend in its box (list order).
+__device__ __forceinline__ int ring_compact(const Ring& R, int s, int cnt, uint32_t base, uint32_t wmax,
+                                            const TileCtx& c, uint8_t* list) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    int nw = 0;
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < kSlot / 32; ++q) {
+        const int j = 32 * q + lane;
+        const bool hit = j < cnt && base + (uint32_t)j < wmax &&
+                         box_reach(R.xyd[s][j].x, R.xyd[s][j].y, R.co[s][j], R.cp[s][j], c.box_x0, c.box_y0);
+        const uint32_t m = __ballot_sync(0xffffffffu, hit);
+        if (hit) list[nw + __popc(m & lt)] = (uint8_t)j;
+        nw += __popc(m);
+    }
+    __syncwarp();
+    return nw;
 }
 
 __global__ void __launch_bounds__(kRenderThreads) render_fwd_kernel(
     const float4* __restrict__ xyd, const float4* __restrict__ conic, const float4* __restrict__ rgb, int n,
     const gsfit_camera* __restrict__ cams_g, int n_views, const uint32_t* __restrict__ vals,
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ tile_order, const float* __restrict__ bg,
-    float* __restrict__ out_rgb,
-    float* __restrict__ out_alpha, float* __restrict__ out_T, uint32_t* __restrict__ out_nc) {
+    float* __restrict__ out_rgb, float* __restrict__ out_alpha, float* __restrict__ out_T,
+    uint32_t* __restrict__ out_nc, int32_t* __restrict__ status) {
     extern __shared__ gsfit_camera cams[];
-    __shared__ Batch S;
-    __shared__ uint8_t s_list[kRenderWarps][kBatch];
+    __shared__ Ring R;
+    __shared__ uint8_t s_list[kRenderWarps][kSlot];
+    __shared__ int s_done;  // pixel warps whose pixels have all stopped
     load_cameras(cams, cams_g, n_views);
+    ring_init(R);
+    if (threadIdx.x == 0) s_done = 0;
     __syncthreads();
     const int t = tile_order ? (int)tile_order[blockIdx.x] : (int)blockIdx.x;
-    const TileCtx c = tile_ctx(cams, n_views, t);
     const uint2 range = ranges[t];
-    const size_t rec0 = (size_t)c.view * n;
-    const float fx = (float)c.px, fy = (float)c.py;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const uint32_t lt = (1u << lane) - 1u;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool skip = timed_out(status);
 
+    if (w == kRenderWarps) {  // producer
+        const size_t rec0 = (size_t)view_of_tile(cams, n_views, t) * n;
+        for (int k = 0;; ++k) {
+            const uint32_t b0 = range.x + (uint32_t)k * kSlot;
+            const bool stop = skip || b0 >= range.y || *reinterpret_cast<volatile int*>(&s_done) == kRenderWarps;
+            const int cnt = stop ? 0 : (int)min((uint32_t)kSlot, range.y - b0);
+            if (!ring_produce(R, k, b0, cnt, vals, xyd, conic, rgb, rec0, n, status) || stop) break;
+        }
+        return;
+    }
+
+    const TileCtx c = tile_ctx(cams, n_views, t);
+    const float fx = (float)c.px, fy = (float)c.py;
     float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
     uint32_t last = 0;
     bool done = !c.inside;
-    for (uint32_t b0 = range.x; b0 < range.y; b0 += kBatch) {
-        if (__syncthreads_count(done) == kRenderThreads) break;
-        stage(S, b0 + threadIdx.x, range.y, vals, xyd, conic, rgb, rec0, n);
-        __syncthreads();
-        const int cnt = (int)min((uint32_t)kBatch, range.y - b0);
-        // this warp's entries of the batch, in list order
-        int nw = 0;
-        if (!__all_sync(0xffffffffu, done)) {
-#pragma unroll
-            for (int k = 0; k < kBatch / 32; ++k) {
-                const int j = 32 * k + lane;
-                const bool hit = j < cnt && box_hit(S, j, c);
-                const uint32_t m = __ballot_sync(0xffffffffu, hit);
-                if (hit) s_list[w][nw + __popc(m & lt)] = (uint8_t)j;
-                nw += __popc(m);
-            }
-        }
-        __syncwarp();
-        for (int i = 0; i < nw; ++i) {
-            const int j = s_list[w][i];
-            if (!done) {
-                const float2 p = S.xy[j];
-                const float4 co = S.co[j];
-                const float power = splat_power(co, fx - p.x, fy - p.y);
-                if (power <= 0.0f) {
-                    const float alpha = fminf(kAlphaClamp, co.w * __expf(power));
-                    if (alpha >= kAlphaSkip) {
-                        const float test_T = T * (1.0f - alpha);
-                        if (test_T < kTStop) {
-                            done = true;
-                        } else {
-                            const float4 col = S.col[j];
-                            const float wgt = alpha * T;
-                            C0 += col.x * wgt;
-                            C1 += col.y * wgt;
-                            C2 += col.z * wgt;
-                            T = test_T;
-                            last = b0 - range.x + (uint32_t)j + 1u;  // one past this list position
+    bool wdone = __all_sync(0xffffffffu, done);
+    if (wdone && lane == 0) atomicAdd(&s_done, 1);
+    for (int k = 0;; ++k) {
+        const int s = k % kRing;
+        // warp-uniform, so that no lane leaves while the others reach a warp collective
+        if (!__all_sync(0xffffffffu, mbar_wait(&R.full[s], (k / kRing) & 1, status))) break;
+        const int cnt = R.cnt[s];
+        if (cnt == 0) break;
+        if (!wdone) {
+            const uint32_t base = (uint32_t)k * kSlot;
+            const int nw = ring_compact(R, s, cnt, base, 0xffffffffu, c, s_list[w]);
+            for (int i = 0; i < nw; ++i) {
+                const int j = s_list[w][i];
+                if (!done) {
+                    const float4 p = R.xyd[s][j];
+                    const float4 co = R.co[s][j];
+                    const float power = splat_power(co, fx - p.x, fy - p.y);
+                    if (power <= 0.0f) {
+                        const float alpha = fminf(kAlphaClamp, co.w * __expf(power));
+                        if (alpha >= kAlphaSkip) {
+                            const float test_T = T * (1.0f - alpha);
+                            if (test_T < kTStop) {
+                                done = true;
+                            } else {
+                                const float4 col = R.col[s][j];
+                                const float wgt = alpha * T;
+                                C0 += col.x * wgt;
+                                C1 += col.y * wgt;
+                                C2 += col.z * wgt;
+                                T = test_T;
+                                last = base + (uint32_t)j + 1u;  // one past this list position
+                            }
                         }
                     }
                 }
+                if (__all_sync(0xffffffffu, done)) break;
             }
-            if (__all_sync(0xffffffffu, done)) break;
+            if (__all_sync(0xffffffffu, done)) {
+                wdone = true;
+                if (lane == 0) atomicAdd(&s_done, 1);
+            }
         }
+        mbar_arrive(&R.empty[s]);
     }
-    if (c.inside) {
+    if (c.inside && !skip) {
         const float* bgv = bg + 3 * c.view;
         out_rgb[c.rgb_base] = C0 + T * bgv[0];
         out_rgb[c.rgb_base + c.plane] = C1 + T * bgv[1];
@@ -341,108 +455,94 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ tile_order, const float* __restrict__ bg,
     const float* __restrict__ T_final,
     const uint32_t* __restrict__ n_contrib, const float* __restrict__ dL_drgb, const float* __restrict__ dL_dalpha,
-    float* __restrict__ grad2d) {
+    float* __restrict__ grad2d, int32_t* __restrict__ status) {
     extern __shared__ gsfit_camera cams[];
-    __shared__ Batch2 S;
-    __shared__ uint8_t s_list[kRenderWarps][kBatch];
+    __shared__ Ring R;
+    __shared__ uint8_t s_list[kRenderWarps][kSlot];
     __shared__ uint32_t s_max;
     load_cameras(cams, cams_g, n_views);
+    ring_init(R);
     if (threadIdx.x == 0) s_max = 0u;
     __syncthreads();
     const int t = tile_order ? (int)tile_order[blockIdx.x] : (int)blockIdx.x;
-    const TileCtx c = tile_ctx(cams, n_views, t);
     const uint2 range = ranges[t];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool skip = timed_out(status);
+
+    // the warp's furthest contributor bounds its walk; the block's bounds the list
+    PixBwd q;
+    TileCtx c;
+    uint32_t wmax = 0;
+    if (w < kRenderWarps) {
+        c = tile_ctx(cams, n_views, t);
+        q.T = 1.f; q.last = 0; q.dC0 = q.dC1 = q.dC2 = q.dA = 0.f;
+        if (c.inside) {
+            q.T = T_final[c.pix];
+            q.last = n_contrib[c.pix];
+            q.dC0 = dL_drgb[c.rgb_base];
+            q.dC1 = dL_drgb[c.rgb_base + c.plane];
+            q.dC2 = dL_drgb[c.rgb_base + 2 * c.plane];
+            q.dA = dL_dalpha[c.pix];
+        }
+        q.TN = q.T;
+        q.S0 = q.S1 = q.S2 = 0.f;
+        wmax = q.last;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+        if (lane == 0) atomicMax(&s_max, wmax);
+    }
+    __syncthreads();
+    const uint32_t len = skip ? 0u : min(s_max, range.y - range.x);
+
+    // slots walk the list backwards: slot k holds positions [b1 - kSlot, b1)
+    // (clipped at the list start), b1 = len - k kSlot, relative to range.x
+    if (w == kRenderWarps) {  // producer
+        const size_t rec0 = (size_t)view_of_tile(cams, n_views, t) * n;
+        for (int k = 0;; ++k) {
+            const uint32_t done_n = (uint32_t)k * kSlot;
+            const bool stop = done_n >= len;
+            const uint32_t b1 = stop ? 0u : len - done_n;
+            const uint32_t b0 = b1 > (uint32_t)kSlot ? b1 - kSlot : 0u;
+            const int cnt = stop ? 0 : (int)(b1 - b0);
+            if (!ring_produce(R, k, range.x + b0, cnt, vals, xyd, conic, rgb, rec0, n, status) || stop) break;
+        }
+        return;
+    }
+
     const size_t rec0 = (size_t)c.view * n;
     const float fx = (float)c.px, fy = (float)c.py;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const uint32_t lt = (1u << lane) - 1u;
     const float bg0 = bg[3 * c.view], bg1 = bg[3 * c.view + 1], bg2 = bg[3 * c.view + 2];
     const int slot = reduce9_slot(lane);
     const int slot_off = slot + slot / 3;  // floats (du dv do _ | da db dc _ | dr dg db _ | ....) of a record
-
-    PixBwd q;
-    q.T = 1.f; q.last = 0; q.dC0 = q.dC1 = q.dC2 = q.dA = 0.f;
-    if (c.inside) {
-        q.T = T_final[c.pix];
-        q.last = n_contrib[c.pix];
-        q.dC0 = dL_drgb[c.rgb_base];
-        q.dC1 = dL_drgb[c.rgb_base + c.plane];
-        q.dC2 = dL_drgb[c.rgb_base + 2 * c.plane];
-        q.dA = dL_dalpha[c.pix];
-    }
-    q.TN = q.T;
-    q.S0 = q.S1 = q.S2 = 0.f;
-    // the warp's furthest contributor bounds its walk; the block's bounds the batches
-    uint32_t wmax = q.last;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
-    if (lane == 0) atomicMax(&s_max, wmax);
-    __syncthreads();
-    const uint32_t end = range.x + min(s_max, range.y - range.x);
-
-    // batches walk backwards, [b0, b1) with b1 - b0 <= kBatch, the last first;
-    // the next one (towards the list start) is copied while this one runs
-    uint32_t b1 = end;
-    uint32_t b0 = (b1 - range.x > (uint32_t)kBatch) ? b1 - kBatch : range.x;
-    uint32_t g_cur = load_index(b0 + threadIdx.x, b1, vals, n);
-    issue_rec(S, 0, g_cur, xyd, conic, rgb, rec0);
-    cp_async_commit();
-    uint32_t pb1 = b0, pb0 = (pb1 - range.x > (uint32_t)kBatch) ? pb1 - kBatch : range.x;
-    uint32_t g_next = pb1 > range.x ? load_index(pb0 + threadIdx.x, pb1, vals, n) : 0xffffffffu;
-    int buf = 0;
-    while (b1 > range.x) {
-        __syncthreads();  // the other buffer is free again
-        uint32_t nb1 = pb1, nb0 = pb0, g_after = 0xffffffffu;
-        if (pb1 > range.x) {
-            issue_rec(S, buf ^ 1, g_next, xyd, conic, rgb, rec0);
-            cp_async_commit();
-            nb1 = pb0;
-            nb0 = (nb1 - range.x > (uint32_t)kBatch) ? nb1 - kBatch : range.x;
-            g_after = nb1 > range.x ? load_index(nb0 + threadIdx.x, nb1, vals, n) : 0xffffffffu;
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
-        finish_rec(S, buf, g_cur);
-        __syncthreads();
-        const int cnt = (int)(b1 - b0);
-        int nw = 0;
-#pragma unroll
-        for (int k = 0; k < kBatch / 32; ++k) {
-            const int j = 32 * k + lane;
-            const bool hit = j < cnt && (b0 - range.x + (uint32_t)j) < wmax && box_hit2(S, buf, j, c);
-            const uint32_t m = __ballot_sync(0xffffffffu, hit);
-            if (hit) s_list[w][nw + __popc(m & lt)] = (uint8_t)j;
-            nw += __popc(m);
-        }
-        __syncwarp();
-        for (int i = nw - 1; i >= 0; --i) {
-            const int j = s_list[w][i];
-            const float4 p = S.xyd[buf][j];
-            const float4 co = S.co[buf][j];
-            const float4 col = S.col[buf][j];
-            float g9[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            const bool hit = pix_bwd_step(q, b0 + (uint32_t)j - range.x, co, col, bg0, bg1, bg2, fx - p.x,
-                                          fy - p.y, g9);
-            if (__any_sync(0xffffffffu, hit)) {
-                const float tot = reduce9(g9, lane);
-                if (slot >= 0) atomicAdd(grad2d + 16 * (rec0 + S.g[buf][j]) + slot_off, tot);
+    for (int k = 0;; ++k) {
+        const int s = k % kRing;
+        // warp-uniform, so that no lane leaves while the others reach a warp collective
+        if (!__all_sync(0xffffffffu, mbar_wait(&R.full[s], (k / kRing) & 1, status))) break;
+        const int cnt = R.cnt[s];
+        if (cnt == 0) break;
+        const uint32_t b1 = len - (uint32_t)k * kSlot;
+        const uint32_t base = b1 - (uint32_t)cnt;  // list position of entry 0
+        if (base < wmax) {
+            const int nw = ring_compact(R, s, cnt, base, wmax, c, s_list[w]);
+            for (int i = nw - 1; i >= 0; --i) {
+                const int j = s_list[w][i];
+                const float4 p = R.xyd[s][j];
+                float g9[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                const bool hit = pix_bwd_step(q, base + (uint32_t)j, R.co[s][j], R.col[s][j], bg0, bg1, bg2,
+                                              fx - p.x, fy - p.y, g9);
+                if (__any_sync(0xffffffffu, hit)) {
+                    const float tot = reduce9(g9, lane);
+                    if (slot >= 0) atomicAdd(grad2d + 16 * (rec0 + R.g[s][j]) + slot_off, tot);
+                }
             }
         }
-        b1 = pb1;
-        b0 = pb0;
-        pb1 = nb1;
-        pb0 = nb0;
-        g_cur = g_next;
-        g_next = g_after;
-        buf ^= 1;
+        mbar_arrive(&R.empty[s]);
     }
-    cp_async_wait<0>();  // no copy may outlive the block
 }
 
 // Diagnostic: blended pairs, with the forward's skip rules, up to each
 // pixel's contributor count (one pixel per thread, batches as above, no cull).
-__global__ void __launch_bounds__(kRenderThreads) render_count_kernel(
+__global__ void __launch_bounds__(kCountThreads) render_count_kernel(
     const float4* __restrict__ xyd, const float4* __restrict__ conic, const float4* __restrict__ rgb, int n,
     const gsfit_camera* __restrict__ cams_g, int n_views, const uint32_t* __restrict__ vals,
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ tile_order, const uint32_t* __restrict__ n_contrib,
@@ -484,17 +584,39 @@ int project_bwd(const gsfit_gaussians* g, const gsfit_proj* proj, const gsfit_ca
 
 using namespace gsfit;
 
+namespace {
+// The camera table (up to GSFIT_MAX_VIEWS x 128 bytes) is dynamic shared
+// memory on top of the static ring: opt in to the larger size once per device.
+int ensure_render_smem() {
+    static bool done[64] = {false};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return GSFIT_ERR_CUDA;
+    if (!done[dev]) {
+        const int bytes = (int)(sizeof(gsfit_camera) * GSFIT_MAX_VIEWS);
+        if (cudaFuncSetAttribute(render_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) !=
+                cudaSuccess ||
+            cudaFuncSetAttribute(render_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) !=
+                cudaSuccess)
+            return GSFIT_ERR_CUDA;
+        done[dev] = true;
+    }
+    return GSFIT_OK;
+}
+}  // namespace
+
 extern "C" int gsfit_render_fwd(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_views, int32_t n,
                                 int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges,
                                 const uint32_t* tile_order, const float* bg, float* rgb, float* alpha,
-                                float* T_final, uint32_t* n_contrib, cudaStream_t stream) {
+                                float* T_final, uint32_t* n_contrib, int32_t* status, cudaStream_t stream) {
     if (!valid_proj(proj) || !cams || n_views < 1 || n_views > GSFIT_MAX_VIEWS || n < 1 || total_tiles < 1 ||
         !vals || !ranges || !bg || !rgb || !alpha || !T_final || !n_contrib)
         return GSFIT_ERR_INVALID_ARG;
+    const int rc = ensure_render_smem();
+    if (rc != GSFIT_OK) return rc;
     render_fwd_kernel<<<total_tiles, kRenderThreads, sizeof(gsfit_camera) * n_views, stream>>>(
         reinterpret_cast<const float4*>(proj->xyd), reinterpret_cast<const float4*>(proj->conic),
         reinterpret_cast<const float4*>(proj->rgb), n, cams, n_views, vals, reinterpret_cast<const uint2*>(ranges),
-        tile_order, bg, rgb, alpha, T_final, n_contrib);
+        tile_order, bg, rgb, alpha, T_final, n_contrib, status);
     GSFIT_LAUNCH_CHECK();
     return GSFIT_OK;
 }
@@ -503,15 +625,17 @@ extern "C" int gsfit_blend_bwd(const gsfit_proj* proj, const gsfit_camera* cams,
                                int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges,
                                const uint32_t* tile_order, const float* bg, const float* T_final,
                                const uint32_t* n_contrib, const float* dL_drgb, const float* dL_dalpha, float* grad2d,
-                               cudaStream_t stream) {
+                               int32_t* status, cudaStream_t stream) {
     if (!valid_proj(proj) || !cams || n_views < 1 || n_views > GSFIT_MAX_VIEWS || n < 1 || total_tiles < 1 ||
         !vals || !ranges || !bg || !T_final || !n_contrib || !dL_drgb || !dL_dalpha || !grad2d ||
         (reinterpret_cast<uintptr_t>(grad2d) % 16) != 0)
         return GSFIT_ERR_INVALID_ARG;
+    const int rc = ensure_render_smem();
+    if (rc != GSFIT_OK) return rc;
     render_bwd_kernel<<<total_tiles, kRenderThreads, sizeof(gsfit_camera) * n_views, stream>>>(
         reinterpret_cast<const float4*>(proj->xyd), reinterpret_cast<const float4*>(proj->conic),
         reinterpret_cast<const float4*>(proj->rgb), n, cams, n_views, vals, reinterpret_cast<const uint2*>(ranges),
-        tile_order, bg, T_final, n_contrib, dL_drgb, dL_dalpha, grad2d);
+        tile_order, bg, T_final, n_contrib, dL_drgb, dL_dalpha, grad2d, status);
     GSFIT_LAUNCH_CHECK();
     return GSFIT_OK;
 }
@@ -528,10 +652,10 @@ extern "C" int gsfit_render_bwd(const gsfit_gaussians* g, const gsfit_proj* proj
                                 int32_t n_views, int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges,
                                 const uint32_t* tile_order, const float* bg, const float* T_final,
                                 const uint32_t* n_contrib, const float* dL_drgb, const float* dL_dalpha, float* grad2d,
-                                float* grads, cudaStream_t stream) {
+                                float* grads, int32_t* status, cudaStream_t stream) {
     if (!valid_gaussians(g)) return GSFIT_ERR_INVALID_ARG;
     const int rc = gsfit_blend_bwd(proj, cams, n_views, g->n, total_tiles, vals, ranges, tile_order, bg, T_final,
-                                   n_contrib, dL_drgb, dL_dalpha, grad2d, stream);
+                                   n_contrib, dL_drgb, dL_dalpha, grad2d, status, stream);
     if (rc != GSFIT_OK) return rc;
     return gsfit_project_bwd(g, proj, cams, n_views, grad2d, grads, stream);
 }
@@ -543,7 +667,7 @@ extern "C" int gsfit_render_count(const gsfit_proj* proj, const gsfit_camera* ca
     if (!valid_proj(proj) || !cams || n_views < 1 || n_views > GSFIT_MAX_VIEWS || n < 1 || total_tiles < 1 ||
         !vals || !ranges || !n_contrib || !count)
         return GSFIT_ERR_INVALID_ARG;
-    render_count_kernel<<<total_tiles, kRenderThreads, sizeof(gsfit_camera) * n_views, stream>>>(
+    render_count_kernel<<<total_tiles, kCountThreads, sizeof(gsfit_camera) * n_views, stream>>>(
         reinterpret_cast<const float4*>(proj->xyd), reinterpret_cast<const float4*>(proj->conic),
         reinterpret_cast<const float4*>(proj->rgb), n, cams, n_views, vals, reinterpret_cast<const uint2*>(ranges),
         tile_order, n_contrib, count);

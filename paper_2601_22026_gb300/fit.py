@@ -122,7 +122,7 @@ class FitState:
 
     def render_fwd(self, stream=None):
         G.gsfit_render_fwd(self.proj, self.cams_dev, self.V, self.n, self.T, self.vals, self.ranges, self.bg,
-                           self.rgb, self.alpha, self.T_final, self.n_contrib, stream, self.tile_order)
+                           self.rgb, self.alpha, self.T_final, self.n_contrib, stream, self.tile_order, self.status)
 
     def loss(self, stream=None):
         G.gsfit_loss(self.cams_dev, self.V, self.rgb, self.alpha, self.target_rgb, self.target_alpha, self.bg,
@@ -131,12 +131,12 @@ class FitState:
     def render_bwd(self, stream=None):
         G.gsfit_render_bwd(self.params, self.n, self.sh_degree, self.proj, self.cams_dev, self.V, self.T,
                            self.vals, self.ranges, self.bg, self.T_final, self.n_contrib, self.dL_drgb,
-                           self.dL_dalpha, self.grad2d, self.grads, stream, self.tile_order)
+                           self.dL_dalpha, self.grad2d, self.grads, stream, self.tile_order, self.status)
 
     def blend_bwd(self, stream=None):
         G.gsfit_blend_bwd(self.proj, self.cams_dev, self.V, self.n, self.T, self.vals, self.ranges, self.bg,
                           self.T_final, self.n_contrib, self.dL_drgb, self.dL_dalpha, self.grad2d, stream,
-                          self.tile_order)
+                          self.tile_order, self.status)
 
     def project_bwd(self, stream=None):
         G.gsfit_project_bwd(self.params, self.n, self.sh_degree, self.proj, self.cams_dev, self.V, self.grad2d,

@@ -55,12 +55,12 @@ SIGNATURES = {
     "gsfit_project": (ctypes.c_int, [_P, _P, _i32, _P, _P]),
     "gsfit_bin_sort_workspace_size": (_size, [_i64, _i64, _i32]),
     "gsfit_bin_sort": (ctypes.c_int, [_P, _P, _i32, _i32, _i32, _P, _size, _P, _P, _i64, _P, _P, _P, _P, _P]),
-    "gsfit_render_fwd": (ctypes.c_int, [_P, _P, _i32, _i32, _i32, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "gsfit_render_fwd": (ctypes.c_int, [_P, _P, _i32, _i32, _i32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "gsfit_loss_workspace_size": (_size, [_i32]),
     "gsfit_loss": (ctypes.c_int, [_P, _i32, _P, _P, _P, _P, _P, _f32, _P, _P, _P, _P, _size, _P]),
     "gsfit_loss_noalloc": (ctypes.c_int, [_P, _i32, _P, _P, _P, _P, _P, _f32, _P, _P, _P, _P]),
-    "gsfit_render_bwd": (ctypes.c_int, [_P, _P, _P, _i32, _i32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
-    "gsfit_blend_bwd": (ctypes.c_int, [_P, _P, _i32, _i32, _i32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "gsfit_render_bwd": (ctypes.c_int, [_P, _P, _P, _i32, _i32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "gsfit_blend_bwd": (ctypes.c_int, [_P, _P, _i32, _i32, _i32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "gsfit_project_bwd": (ctypes.c_int, [_P, _P, _P, _i32, _P, _P, _P]),
     "gsfit_render_count": (ctypes.c_int, [_P, _P, _i32, _i32, _i32, _P, _P, _P, _P, _P, _P]),
     "gsfit_adam_step": (ctypes.c_int, [_P, _P, _P, _P, _i32, _i32, _P, _f32, _f32, _f32, _P, _P]),
@@ -250,11 +250,11 @@ def gsfit_bin_sort(proj: ProjBuffers, cams_dev, n_views, n, total_tiles, ws, key
 
 
 def gsfit_render_fwd(proj: ProjBuffers, cams_dev, n_views, n, total_tiles, vals, ranges, bg, rgb, alpha, T_final,
-                     n_contrib, stream=None, tile_order=None):
+                     n_contrib, stream=None, tile_order=None, status=None):
     p = proj.struct()
     _check(load().gsfit_render_fwd(ctypes.byref(p), _ptr(cams_dev), n_views, n, total_tiles, _ptr(vals),
                                    _ptr(ranges), _ptr(tile_order), _ptr(bg), _ptr(rgb), _ptr(alpha), _ptr(T_final),
-                                   _ptr(n_contrib), _stream(stream)),
+                                   _ptr(n_contrib), _ptr(status), _stream(stream)),
            "gsfit_render_fwd")
 
 
@@ -283,21 +283,23 @@ def gsfit_loss_noalloc(cams_dev, n_views, rgb, alpha, target_rgb, target_alpha, 
 
 
 def gsfit_render_bwd(params, n, sh_degree, proj: ProjBuffers, cams_dev, n_views, total_tiles, vals, ranges, bg,
-                     T_final, n_contrib, dL_drgb, dL_dalpha, grad2d, grads, stream=None, tile_order=None):
+                     T_final, n_contrib, dL_drgb, dL_dalpha, grad2d, grads, stream=None, tile_order=None,
+                     status=None):
     g = gaussians_struct(params, n, sh_degree)
     p = proj.struct()
     _check(load().gsfit_render_bwd(ctypes.byref(g), ctypes.byref(p), _ptr(cams_dev), n_views, total_tiles,
                                    _ptr(vals), _ptr(ranges), _ptr(tile_order), _ptr(bg), _ptr(T_final), _ptr(n_contrib),
-                                   _ptr(dL_drgb), _ptr(dL_dalpha), _ptr(grad2d), _ptr(grads), _stream(stream)),
+                                   _ptr(dL_drgb), _ptr(dL_dalpha), _ptr(grad2d), _ptr(grads), _ptr(status),
+                                   _stream(stream)),
            "gsfit_render_bwd")
 
 
 def gsfit_blend_bwd(proj: ProjBuffers, cams_dev, n_views, n, total_tiles, vals, ranges, bg, T_final, n_contrib,
-                    dL_drgb, dL_dalpha, grad2d, stream=None, tile_order=None):
+                    dL_drgb, dL_dalpha, grad2d, stream=None, tile_order=None, status=None):
     p = proj.struct()
     _check(load().gsfit_blend_bwd(ctypes.byref(p), _ptr(cams_dev), n_views, n, total_tiles, _ptr(vals), _ptr(ranges),
                                   _ptr(tile_order), _ptr(bg), _ptr(T_final), _ptr(n_contrib), _ptr(dL_drgb), _ptr(dL_dalpha),
-                                  _ptr(grad2d), _stream(stream)),
+                                  _ptr(grad2d), _ptr(status), _stream(stream)),
            "gsfit_blend_bwd")
 
 
