@@ -159,16 +159,19 @@ def build_state(seed: int = 0, n: int = 1_000_000, crops: int = 14):
     return sc, st
 
 
-def stage_bytes(st, n_inst: int, n_vis: int, n_passes: int) -> dict:
+def stage_bytes(st, n_inst: int, n_vis: int, tile_passes: int) -> dict:
     """Algorithmic HBM bytes per launch of the memory-bound stages."""
     n, V, P, npl = st.n, st.V, st.P, st.n_planes
     return {
         # read every parameter plane once; write a 20-byte centre record + tile
         # count per (view, Gaussian) and 32 more bytes for binned records
         "project": n * npl * 16 + V * n * 20 + n_vis * 32,
-        # tile counts read twice, binned centres once; pairs emitted (12 B),
-        # histogram read (8 B), n_passes x (read + write 12 B), range scan (8 B)
-        "bin_sort": V * n * 8 + n_vis * 16 + n_inst * (12 + 8 + 24 * n_passes + 8),
+        # tile counts read twice; per binned record: depth read (4 B), record
+        # key + index written (12 B), 4 depth passes x (read + write 12 B),
+        # sorted counts read (8 B), key + index + centre read for emission
+        # (28 B); per pair: emitted (12 B), tile passes x (read + write 12 B),
+        # range scan (8 B)
+        "bin_sort": V * n * 8 + n_vis * (4 + 12 + 4 * 24 + 8 + 28) + n_inst * (12 + 24 * tile_passes + 8),
         # render colour + alpha, target colour + alpha read; gradients written
         "loss": P * 4 * 12,
         # p, g, m, v read; p, m, v written: 28 bytes per parameter (float4 planes)
@@ -394,16 +397,17 @@ def main() -> None:
     # stream) and the roofline of the dominant kernel
     stage_ms = time_stages(st, reps=max(5, min(30, args.steps // 10)))
     blended = st.blended_pairs()
-    n_passes = 4 + (int(np.ceil(np.log2(max(2, st.T)))) + 7) // 8
-    sb = stage_bytes(st, n_inst, n_vis, n_passes)
+    tile_passes = max(1, (int(np.ceil(np.log2(max(2, st.T)))) + 7) // 8)
+    sb = stage_bytes(st, n_inst, n_vis, tile_passes)
     peaks = measured_peaks()
     hbm_stages = {k: sb[k] / (stage_ms[k] * 1e-3) / 1e9 for k in sb}
     alu_peak = alu_peak_tflops(peaks["sm_max_mhz"])
     alu_stages = {k: blended * f / (stage_ms[k] * 1e-3) / 1e12 for k, f in FLOP_PER_BLEND.items()}
     dominant = max(stage_ms, key=stage_ms.get)
-    # project 1; bin_sort reduce, scan, emit, hist, passes, ranges; render 1;
-    # loss (memset node excluded) 2; adjoint 2; adam 2
-    launches_per_step = 1 + (5 + n_passes) + 1 + 2 + 2 + 2
+    # project 1; bin_sort: reduce, scan, compact, 4 depth passes, sorted
+    # reduce + scan, emit, tile passes, ranges, 2 tile-order kernels; render 1;
+    # loss (memset node excluded) 2; adjoint: blend 1 + projection 2; adam 2
+    launches_per_step = 1 + (13 + tile_passes) + 1 + 2 + 3 + 2
     kernel_of = {"blend_bwd": "render_bwd_kernel", "render_fwd": "render_fwd_kernel", "loss": "loss_kernel",
                  "project": "project_kernel", "adam": "adam_kernel", "project_bwd": "project_bwd_kernel"}
     traffic = measured_traffic(kernel_of.get(dominant, dominant))

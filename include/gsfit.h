@@ -166,9 +166,11 @@ size_t gsfit_bin_sort_workspace_size(int64_t n_records, int64_t capacity, int32_
  * gsfit_bin_sort -- tile binning of the projected records (3DGS).
  *   Exclusive scan of tiles[]; for every record with tiles > 0 and every
  *   tile (row-major) of its rectangle, one pair key = (global tile id << 32)
- *   | float32 bits of depth, value = Gaussian index i, emitted in record
- *   order; a stable LSD radix sort of the pairs by key (the order is the
- *   unique order by (key, view, Gaussian index)); and per global tile t the
+ *   | float32 bits of depth, value = Gaussian index i; the pairs sorted by
+ *   key, stably with respect to record order (the result is the unique order
+ *   by (key, view, Gaussian index); computed as a stable radix sort of the
+ *   binned records by depth, emission of their pairs in that order, and a
+ *   stable radix sort of the pairs on the tile-id bits); and per global tile t the
  *   range ranges[2t], ranges[2t+1] = [first, last+1) of its pairs, [0, 0)
  *   if empty.
  * Arguments: proj/cams as for gsfit_project (n Gaussians, n_views views,
@@ -186,7 +188,7 @@ size_t gsfit_bin_sort_workspace_size(int64_t n_records, int64_t capacity, int32_
  *   compositing calls launch tiles in this order so the longest lists start
  *   first and do not form the tail of the grid.
  * Errors: GSFIT_ERR_INVALID_ARG (null pointers, sizes, workspace too small,
- *   capacity >= 2^30), GSFIT_ERR_CUDA.
+ *   capacity >= 2^30, n_views * n >= 2^32), GSFIT_ERR_CUDA.
  */
 int gsfit_bin_sort(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_views, int32_t n,
                    int32_t total_tiles, void* ws, size_t ws_bytes, uint64_t* keys, uint32_t* vals,

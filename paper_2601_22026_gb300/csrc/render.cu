@@ -414,8 +414,8 @@ struct PixBwd {
 // Adjoint of one blend at one pixel (list position pos < last), accumulating
 // the nine per-Gaussian terms g9 = dL/d(u, v, opacity, a', b', c', r, g, b);
 // returns whether the Gaussian was blended here.
-__device__ __forceinline__ bool pix_bwd_step(PixBwd& q, uint32_t pos, float4 co, float4 col, float bg0, float bg1,
-                                             float bg2, float dx, float dy, float* g9) {
+__device__ __forceinline__ bool pix_bwd_step(PixBwd& q, uint32_t pos, float4 co, const float4* colp, float bg0,
+                                             float bg1, float bg2, float dx, float dy, float* g9) {
     if (pos >= q.last) return false;
     const float power = splat_power(co, dx, dy);
     if (power > 0.0f) return false;
@@ -423,8 +423,11 @@ __device__ __forceinline__ bool pix_bwd_step(PixBwd& q, uint32_t pos, float4 co,
     const float a = co.w * G;
     const float alpha = fminf(kAlphaClamp, a);
     if (alpha < kAlphaSkip) return false;
+    const float4 col = *colp;
     const float one_m = 1.0f - alpha;
-    const float inv = 1.0f / one_m;
+    // 1 - alpha lies in [0.01, 1): the hardware reciprocal (within 2 ulp)
+    // suffices for recovering T
+    const float inv = __fdividef(1.0f, one_m);
     q.T *= inv;  // transmittance in front of this Gaussian
     const float wT = alpha * q.T;
     g9[6] = q.dC0 * wT;
@@ -528,7 +531,7 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(
                 const int j = s_list[w][i];
                 const float4 p = R.xyd[s][j];
                 float g9[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                const bool hit = pix_bwd_step(q, base + (uint32_t)j, R.co[s][j], R.col[s][j], bg0, bg1, bg2,
+                const bool hit = pix_bwd_step(q, base + (uint32_t)j, R.co[s][j], &R.col[s][j], bg0, bg1, bg2,
                                               fx - p.x, fy - p.y, g9);
                 if (__any_sync(0xffffffffu, hit)) {
                     const float tot = reduce9(g9, lane);

@@ -1,26 +1,34 @@
-// Tile binning: pair emission, LSD radix sort of 64-bit (tile | depth) keys,
-// per-tile ranges.
+// Tile binning: pair emission, stable sort by (tile id, depth), per-tile
+// ranges.
 //
 // 3DGS (which the fitted peripheral model is, Section 4.2) renders by sorting
 // every (Gaussian, covered tile) pair by (tile id, depth) once per image and
-// compositing each tile's range front to back. Here:
+// compositing each tile's range front to back. Every pair of one Gaussian
+// record carries the same depth, so the sort is done in two stages:
 //   1. reduce_kernel / scan_kernel: a spin-free reduce-then-scan over the
-//      per-record tile counts gives each record its output offset and the
-//      total pair count (kept on the device; checked against capacity).
-//   2. emit_kernel: rescans its block in record order and writes the pairs.
-//   3. hist_kernel: one read of the keys builds the digit histograms of every
-//      pass (8-bit digits over the 32 depth bits and the significant tile-id
-//      bits), and clears the look-back tables and tile ranges.
-//   4. onesweep_kernel, once per digit: a stable counting pass in the
-//      Onesweep style (Adinets & Merrill 2022): each CTA ranks a 4096-key
-//      partition in shared memory, publishes its digit counts, obtains its
-//      global digit offsets by decoupled look-back over earlier partitions
-//      (every wait bounded: on expiry the status word gets GSFIT_ERR_TIMEOUT),
-//      and writes its keys digit-run by digit-run so stores coalesce. One read
-//      and one write of (key, value) per pass: 24 bytes per pair.
-//   5. ranges_kernel: [first, last+1) of each tile from adjacent keys.
-// Pair counts never leave the device, so the sequence can be captured in a
-// CUDA graph; launches are sized by capacity and idle CTAs exit at once.
+//      per-record tile counts gives the total pair count (kept on the device;
+//      checked against capacity) and the number of binned records.
+//   2. compact_kernel: the binned records, in record order, as 64-bit keys
+//      (tile count << 32 | depth bits) with the record index as value; also
+//      the depth-digit histograms, and clears the look-back tables and ranges.
+//   3. onesweep_kernel x 4 over the depth bits: a stable counting pass per
+//      8-bit digit in the Onesweep style (Adinets & Merrill 2022): each CTA
+//      ranks a 4096-key partition in shared memory, publishes its digit
+//      counts, obtains its global digit offsets by decoupled look-back over
+//      earlier partitions (every wait bounded: on expiry the status word gets
+//      GSFIT_ERR_TIMEOUT), and writes its keys digit-run by digit-run so
+//      stores coalesce. Records are now in (depth, record index) order.
+//   4. reduce_sorted_kernel / scan_blocks_kernel / emit_kernel: pair offsets
+//      in that order, then the pairs (tile id << 32 | depth, Gaussian index),
+//      with the tile-digit histograms.
+//   5. onesweep_kernel over the significant tile-id bits only (two passes for
+//      up to 65536 tiles): being stable, it leaves equal tile ids in (depth,
+//      record index) order, the unique order by (key, view, index).
+//   6. ranges_kernel: [first, last+1) of each tile from adjacent keys.
+// Sorting records instead of pairs by depth moves 24 bytes per record per
+// depth pass instead of 24 bytes per pair (a record covers several tiles).
+// Counts never leave the device, so the sequence can be captured in a CUDA
+// graph; launches are sized by capacity and idle CTAs exit at once.
 #include "common.cuh"
 
 namespace gsfit {
@@ -42,12 +50,14 @@ constexpr uint32_t kValMask = kFlagAgg - 1u;
 constexpr int kSpinLimit = 1 << 20;  // x ~100 ns sleeps: about a tenth of a second
 constexpr int kHistBlocks = 1024;
 
+constexpr int kDepthPasses = 4;  // 8-bit digits over the 32 depth bits
+
 struct SortCtl {
     uint32_t n_sort;      // pairs to sort (0 when the capacity was exceeded)
-    uint32_t pad;
+    uint32_t n_rec;       // binned records to sort (0 when the capacity was exceeded)
     unsigned long long total;  // exact pair count
     uint32_t part_counter[kMaxPasses];
-    uint32_t hist[kMaxPasses][kRadix];
+    uint32_t hist[kMaxPasses][kRadix];  // depth passes, then tile passes
     uint32_t order_hist[32];  // tiles per log2(list length + 1) bucket
     uint32_t order_fill[32];
 };
@@ -75,40 +85,38 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t* s_warp
     return wpre + incl - x;
 }
 
+// Per block of kScanChunk records: pair count and binned-record count.
 __global__ void __launch_bounds__(kScanThreads) reduce_kernel(const uint32_t* __restrict__ tiles, long long n_rec,
-                                                              uint32_t* __restrict__ block_sums) {
+                                                              uint32_t* __restrict__ pair_sums,
+                                                              uint32_t* __restrict__ rec_sums) {
     __shared__ uint32_t s_warp[8];
     const long long base = (long long)blockIdx.x * kScanChunk;
-    uint32_t acc = 0;
+    uint32_t acc = 0, cnt = 0;
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
         const long long r = base + (long long)j * kScanThreads + threadIdx.x;
-        if (r < n_rec) acc += tiles[r];
+        const uint32_t t = r < n_rec ? tiles[r] : 0u;
+        acc += t;
+        cnt += t > 0u;
     }
     uint32_t total;
     block_excl_scan(acc, s_warp, total);
-    if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+    if (threadIdx.x == 0) pair_sums[blockIdx.x] = total;
+    block_excl_scan(cnt, s_warp, total);
+    if (threadIdx.x == 0) rec_sums[blockIdx.x] = total;
 }
 
-// Single block: exclusive scan of the block sums, total, capacity check, and
-// reset of the sort control block.
-__global__ void __launch_bounds__(1024) scan_kernel(uint32_t* __restrict__ block_sums, int n_blocks,
-                                                    SortCtl* __restrict__ ctl, uint32_t* __restrict__ n_instances,
-                                                    long long capacity, int32_t* __restrict__ status) {
+// In-place exclusive scan of n_blocks block sums by one 1024-thread block;
+// returns the total (to thread 0).
+__device__ unsigned long long scan_block_sums(uint32_t* __restrict__ sums, int n_blocks) {
     __shared__ unsigned long long s_warp[32];
     __shared__ unsigned long long s_carry;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (threadIdx.x == 0) s_carry = 0;
-    for (int k = threadIdx.x; k < kMaxPasses * kRadix; k += blockDim.x) (&ctl->hist[0][0])[k] = 0u;
-    if (threadIdx.x < kMaxPasses) ctl->part_counter[threadIdx.x] = 0u;
-    if (threadIdx.x < 32) {
-        ctl->order_hist[threadIdx.x] = 0u;
-        ctl->order_fill[threadIdx.x] = 0u;
-    }
     __syncthreads();
     for (int base = 0; base < n_blocks; base += 1024) {
         const int b = base + threadIdx.x;
-        const unsigned long long x = b < n_blocks ? block_sums[b] : 0ull;
+        const unsigned long long x = b < n_blocks ? sums[b] : 0ull;
         unsigned long long incl = x;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -123,88 +131,162 @@ __global__ void __launch_bounds__(1024) scan_kernel(uint32_t* __restrict__ block
             tot += s_warp[w];
         }
         const unsigned long long carry = s_carry;
-        if (b < n_blocks) block_sums[b] = (uint32_t)(carry + wpre + incl - x);
+        if (b < n_blocks) sums[b] = (uint32_t)(carry + wpre + incl - x);
         __syncthreads();
         if (threadIdx.x == 0) s_carry = carry + tot;
         __syncthreads();
     }
+    return s_carry;
+}
+
+// Single block: scans of both block-sum arrays, totals, capacity check, and
+// reset of the sort control block.
+__global__ void __launch_bounds__(1024) scan_kernel(uint32_t* __restrict__ pair_sums, uint32_t* __restrict__ rec_sums,
+                                                    int n_blocks, SortCtl* __restrict__ ctl,
+                                                    uint32_t* __restrict__ n_instances, long long capacity,
+                                                    int32_t* __restrict__ status) {
+    for (int k = threadIdx.x; k < kMaxPasses * kRadix; k += blockDim.x) (&ctl->hist[0][0])[k] = 0u;
+    if (threadIdx.x < kMaxPasses) ctl->part_counter[threadIdx.x] = 0u;
+    if (threadIdx.x < 32) {
+        ctl->order_hist[threadIdx.x] = 0u;
+        ctl->order_fill[threadIdx.x] = 0u;
+    }
+    const unsigned long long total = scan_block_sums(pair_sums, n_blocks);
+    const unsigned long long recs = scan_block_sums(rec_sums, n_blocks);
     if (threadIdx.x == 0) {
-        const unsigned long long total = s_carry;
         ctl->total = total;
         *n_instances = total > 0xffffffffull ? 0xffffffffu : (uint32_t)total;
         if (total > (unsigned long long)capacity) {
             ctl->n_sort = 0u;
+            ctl->n_rec = 0u;
             *status = GSFIT_ERR_CAPACITY;
         } else {
             ctl->n_sort = (uint32_t)total;
+            ctl->n_rec = (uint32_t)recs;
         }
     }
 }
 
-// Rescans each block's records in order and writes their pairs.
-__global__ void __launch_bounds__(kScanThreads) emit_kernel(const uint32_t* __restrict__ tiles,
-                                                            const float4* __restrict__ xyd, int n, int n_views,
-                                                            const gsfit_camera* __restrict__ cams_g,
-                                                            const uint32_t* __restrict__ block_sums,
-                                                            const SortCtl* __restrict__ ctl,
-                                                            unsigned long long* __restrict__ keys,
-                                                            uint32_t* __restrict__ vals) {
-    extern __shared__ gsfit_camera cams[];
+// Single block: in-place exclusive scan of the sorted records' block sums.
+__global__ void __launch_bounds__(1024) scan_blocks_kernel(uint32_t* __restrict__ sums, int n_blocks) {
+    scan_block_sums(sums, n_blocks);
+}
+
+// Binned records in record order as (tile count << 32 | depth bits, record
+// index), with the depth-digit histograms; clears the look-back tables and
+// the tile ranges for this sort.
+__global__ void __launch_bounds__(kScanThreads) compact_kernel(const uint32_t* __restrict__ tiles,
+                                                               const float4* __restrict__ xyd, long long n_rec,
+                                                               const uint32_t* __restrict__ rec_sums,
+                                                               SortCtl* __restrict__ ctl,
+                                                               unsigned long long* __restrict__ rkeys,
+                                                               uint32_t* __restrict__ rvals,
+                                                               uint32_t* __restrict__ lookback, long long lookback_words,
+                                                               uint32_t* __restrict__ ranges, long long range_words) {
     __shared__ uint32_t s_warp[8];
-    load_cameras(cams, cams_g, n_views);
-    __syncthreads();
-    if (ctl->total > (unsigned long long)ctl->n_sort) return;  // capacity exceeded: emit nothing
-    const long long n_rec = (long long)n * n_views;
-    const long long base = (long long)blockIdx.x * kScanChunk;
-    uint32_t offset = block_sums[blockIdx.x];
-    for (int j = 0; j < kScanItems; ++j) {
-        const long long r = base + (long long)j * kScanThreads + threadIdx.x;
-        const uint32_t t = r < n_rec ? tiles[r] : 0u;
-        uint32_t row_total;
-        const uint32_t ex = block_excl_scan(t, s_warp, row_total);
-        if (t > 0u) {
-            const int v = (int)(r / n);
-            const int i = (int)(r - (long long)v * n);
-            const gsfit_camera& cam = cams[v];
-            const float4 p = xyd[r];
-            const int txn = tiles_x_of(cam);
-            const Rect rc = tile_rect(p.x, p.y, p.w, txn, tiles_y_of(cam));
-            const unsigned long long depth = (unsigned long long)__float_as_uint(p.z);
-            uint32_t o = offset + ex;
-            for (int ty = rc.y0; ty < rc.y1; ++ty)
-                for (int tx = rc.x0; tx < rc.x1; ++tx) {
-                    const unsigned long long tile = (unsigned long long)(cam.tile_offset + ty * txn + tx);
-                    keys[o] = (tile << 32) | depth;
-                    vals[o] = (uint32_t)i;
-                    ++o;
-                }
-        }
-        offset += row_total;
-    }
-}
-
-// Digit histograms of every pass in one read of the keys; also clears the
-// look-back tables and the tile ranges for this sort.
-__global__ void __launch_bounds__(256) hist_kernel(const unsigned long long* __restrict__ keys,
-                                                   SortCtl* __restrict__ ctl, int n_passes,
-                                                   uint32_t* __restrict__ lookback, long long lookback_words,
-                                                   uint32_t* __restrict__ ranges, long long range_words) {
-    __shared__ uint32_t s_hist[kMaxPasses][kRadix];
-    for (int k = threadIdx.x; k < kMaxPasses * kRadix; k += blockDim.x) (&s_hist[0][0])[k] = 0u;
-    __syncthreads();
+    __shared__ uint32_t s_hist[kDepthPasses][kRadix];
+    for (int k = threadIdx.x; k < kDepthPasses * kRadix; k += blockDim.x) (&s_hist[0][0])[k] = 0u;
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     for (long long k = tid; k < lookback_words; k += stride) lookback[k] = 0u;
     for (long long k = tid; k < range_words; k += stride) ranges[k] = 0u;
-    const uint32_t n = ctl->n_sort;
-    for (long long k = tid; k < n; k += stride) {
-        const unsigned long long key = keys[k];
-        for (int p = 0; p < n_passes; ++p) atomicAdd(&s_hist[p][(key >> (8 * p)) & 0xff], 1u);
+    __syncthreads();
+    if (ctl->n_rec == 0u) return;  // nothing binned, or the capacity was exceeded
+    const long long base = (long long)blockIdx.x * kScanChunk;
+    uint32_t offset = rec_sums[blockIdx.x];
+    for (int j = 0; j < kScanItems; ++j) {
+        const long long r = base + (long long)j * kScanThreads + threadIdx.x;
+        const uint32_t t = r < n_rec ? tiles[r] : 0u;
+        uint32_t row_total;
+        const uint32_t ex = block_excl_scan(t > 0u ? 1u : 0u, s_warp, row_total);
+        if (t > 0u) {
+            const uint32_t depth = __float_as_uint(xyd[r].z);
+            rkeys[offset + ex] = ((unsigned long long)t << 32) | depth;
+            rvals[offset + ex] = (uint32_t)r;
+#pragma unroll
+            for (int p = 0; p < kDepthPasses; ++p) atomicAdd(&s_hist[p][(depth >> (8 * p)) & 0xff], 1u);
+        }
+        offset += row_total;
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < n_passes * kRadix; k += blockDim.x) {
+    for (int k = threadIdx.x; k < kDepthPasses * kRadix; k += blockDim.x) {
         const uint32_t c = (&s_hist[0][0])[k];
         if (c) atomicAdd(&ctl->hist[0][0] + k, c);
+    }
+}
+
+// Pair counts of the depth-sorted records, per block of kScanChunk.
+__global__ void __launch_bounds__(kScanThreads) reduce_sorted_kernel(const unsigned long long* __restrict__ rkeys,
+                                                                     const SortCtl* __restrict__ ctl,
+                                                                     uint32_t* __restrict__ sums) {
+    __shared__ uint32_t s_warp[8];
+    const uint32_t n = ctl->n_rec;
+    const long long base = (long long)blockIdx.x * kScanChunk;
+    uint32_t acc = 0;
+    if (base < n) {
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) {
+            const long long m = base + (long long)j * kScanThreads + threadIdx.x;
+            if (m < n) acc += (uint32_t)(rkeys[m] >> 32);
+        }
+    }
+    uint32_t total;
+    block_excl_scan(acc, s_warp, total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+// Pairs of the depth-sorted records, in that order, with the tile-digit
+// histograms of the n_tile_passes tile passes.
+__global__ void __launch_bounds__(kScanThreads) emit_kernel(const unsigned long long* __restrict__ rkeys,
+                                                            const uint32_t* __restrict__ rvals,
+                                                            const float4* __restrict__ xyd, int n, int n_views,
+                                                            const gsfit_camera* __restrict__ cams_g,
+                                                            const uint32_t* __restrict__ sums,
+                                                            SortCtl* __restrict__ ctl, int n_tile_passes,
+                                                            unsigned long long* __restrict__ keys,
+                                                            uint32_t* __restrict__ vals) {
+    extern __shared__ gsfit_camera cams[];
+    __shared__ uint32_t s_warp[8];
+    __shared__ uint32_t s_hist[kMaxPasses - kDepthPasses][kRadix];
+    load_cameras(cams, cams_g, n_views);
+    for (int k = threadIdx.x; k < n_tile_passes * kRadix; k += blockDim.x) (&s_hist[0][0])[k] = 0u;
+    __syncthreads();
+    const uint32_t n_recs = ctl->n_rec;
+    const long long base = (long long)blockIdx.x * kScanChunk;
+    if (base >= n_recs) return;
+    uint32_t offset = sums[blockIdx.x];
+    for (int j = 0; j < kScanItems; ++j) {
+        const long long m = base + (long long)j * kScanThreads + threadIdx.x;
+        const bool ok = m < n_recs;
+        const unsigned long long rk = ok ? rkeys[m] : 0ull;
+        const uint32_t t = (uint32_t)(rk >> 32);
+        uint32_t row_total;
+        const uint32_t ex = block_excl_scan(t, s_warp, row_total);
+        if (t > 0u) {
+            const uint32_t r = rvals[m];
+            const int v = (int)(r / (uint32_t)n);
+            const int i = (int)(r - (uint32_t)v * (uint32_t)n);
+            const gsfit_camera& cam = cams[v];
+            const float4 p = xyd[r];
+            const int txn = tiles_x_of(cam);
+            const Rect rc = tile_rect(p.x, p.y, p.w, txn, tiles_y_of(cam));
+            const unsigned long long depth = rk & 0xffffffffull;
+            uint32_t o = offset + ex;
+            for (int ty = rc.y0; ty < rc.y1; ++ty)
+                for (int tx = rc.x0; tx < rc.x1; ++tx) {
+                    const uint32_t tile = (uint32_t)(cam.tile_offset + ty * txn + tx);
+                    keys[o] = ((unsigned long long)tile << 32) | depth;
+                    vals[o] = (uint32_t)i;
+                    ++o;
+                    for (int q = 0; q < n_tile_passes; ++q) atomicAdd(&s_hist[q][(tile >> (8 * q)) & 0xff], 1u);
+                }
+        }
+        offset += row_total;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < n_tile_passes * kRadix; k += blockDim.x) {
+        const uint32_t c = (&s_hist[0][0])[k];
+        if (c) atomicAdd(&ctl->hist[kDepthPasses][0] + k, c);
     }
 }
 
@@ -219,24 +301,26 @@ struct OnesweepSmem {
     uint32_t part;
 };
 
+// One stable counting pass over the 8-bit digit at bit `shift` of *n_ptr keys;
+// `pass` indexes the histogram and partition counter of this launch.
 __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(const unsigned long long* __restrict__ keys_in,
                                                                 const uint32_t* __restrict__ vals_in,
                                                                 unsigned long long* __restrict__ keys_out,
                                                                 uint32_t* __restrict__ vals_out,
-                                                                SortCtl* __restrict__ ctl, int pass,
+                                                                SortCtl* __restrict__ ctl, int pass, int shift,
+                                                                const uint32_t* __restrict__ n_ptr,
                                                                 uint32_t* __restrict__ lookback,
                                                                 int32_t* __restrict__ status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     OnesweepSmem& S = *reinterpret_cast<OnesweepSmem*>(smem_raw);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const uint32_t n = ctl->n_sort;
+    const uint32_t n = *n_ptr;
     const uint32_t n_parts = (n + kPart - 1) / kPart;
     if (threadIdx.x == 0) S.part = atomicAdd(&ctl->part_counter[pass], 1u);
     for (int k = threadIdx.x; k < kSortWarps * (kRadix + 1); k += kSortThreads) (&S.warp_hist[0][0])[k] = 0u;
     __syncthreads();
     const uint32_t part = S.part;
     if (part >= n_parts) return;
-    const int shift = 8 * pass;
     const uint32_t base = part * kPart;
     const uint32_t valid = min((uint32_t)kPart, n - base);
 
@@ -394,28 +478,40 @@ __global__ void __launch_bounds__(256) order_scatter_kernel(const uint32_t* __re
 inline size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct SortLayout {
-    size_t block_sums, ctl, lookback, keys_alt, vals_alt, total;
-    int n_blocks, n_passes;
-    long long max_parts;
+    size_t pair_sums, rec_sums, sorted_sums, ctl, lookback, keys_alt, vals_alt, rkeys[2], rvals[2], total;
+    int n_blocks, tile_passes;
+    long long max_parts, max_rec_parts, lookback_words;
 };
 
-int passes_for(int total_tiles) {
+int tile_passes_for(int total_tiles) {
     int bits = 0;
     while ((1ll << bits) < (long long)total_tiles) ++bits;  // tile ids 0 .. total_tiles-1
-    return 4 + (bits + 7) / 8;
+    return bits == 0 ? 1 : (bits + 7) / 8;
 }
 
 SortLayout layout(long long n_rec, long long capacity, int total_tiles) {
     SortLayout L;
     L.n_blocks = (int)((n_rec + kScanChunk - 1) / kScanChunk);
-    L.n_passes = passes_for(total_tiles);
+    if (L.n_blocks < 1) L.n_blocks = 1;
+    L.tile_passes = tile_passes_for(total_tiles);
     L.max_parts = (capacity + kPart - 1) / kPart;
+    if (L.max_parts < 1) L.max_parts = 1;
+    L.max_rec_parts = (n_rec + kPart - 1) / kPart;
+    if (L.max_rec_parts < 1) L.max_rec_parts = 1;
+    L.lookback_words = ((long long)kDepthPasses * L.max_rec_parts + (long long)L.tile_passes * L.max_parts) * kRadix;
+    const size_t cap = (size_t)(capacity > 0 ? capacity : 1), nr = (size_t)(n_rec > 0 ? n_rec : 1);
     size_t o = 0;
-    L.block_sums = o; o = align_up(o + sizeof(uint32_t) * (size_t)(L.n_blocks > 0 ? L.n_blocks : 1));
+    L.pair_sums = o; o = align_up(o + sizeof(uint32_t) * (size_t)L.n_blocks);
+    L.rec_sums = o; o = align_up(o + sizeof(uint32_t) * (size_t)L.n_blocks);
+    L.sorted_sums = o; o = align_up(o + sizeof(uint32_t) * (size_t)L.n_blocks);
     L.ctl = o; o = align_up(o + sizeof(SortCtl));
-    L.lookback = o; o = align_up(o + sizeof(uint32_t) * (size_t)L.n_passes * (size_t)(L.max_parts > 0 ? L.max_parts : 1) * kRadix);
-    L.keys_alt = o; o = align_up(o + sizeof(unsigned long long) * (size_t)(capacity > 0 ? capacity : 1));
-    L.vals_alt = o; o = align_up(o + sizeof(uint32_t) * (size_t)(capacity > 0 ? capacity : 1));
+    L.lookback = o; o = align_up(o + sizeof(uint32_t) * (size_t)L.lookback_words);
+    L.keys_alt = o; o = align_up(o + sizeof(unsigned long long) * cap);
+    L.vals_alt = o; o = align_up(o + sizeof(uint32_t) * cap);
+    for (int b = 0; b < 2; ++b) {
+        L.rkeys[b] = o; o = align_up(o + sizeof(unsigned long long) * nr);
+        L.rvals[b] = o; o = align_up(o + sizeof(uint32_t) * nr);
+    }
     L.total = o;
     return L;
 }
@@ -455,42 +551,60 @@ extern "C" int gsfit_bin_sort(const gsfit_proj* proj, const gsfit_camera* cams, 
         capacity >= (int64_t)kFlagAgg)
         return GSFIT_ERR_INVALID_ARG;
     const long long n_rec = (long long)n * n_views;
+    if (n_rec >= (long long)0xffffffffll) return GSFIT_ERR_INVALID_ARG;  // record indices are 32-bit
     const SortLayout L = layout(n_rec, capacity, total_tiles);
     if (ws_bytes < L.total || (reinterpret_cast<uintptr_t>(ws) % 256) != 0) return GSFIT_ERR_INVALID_ARG;
     char* base = static_cast<char*>(ws);
-    uint32_t* block_sums = reinterpret_cast<uint32_t*>(base + L.block_sums);
+    uint32_t* pair_sums = reinterpret_cast<uint32_t*>(base + L.pair_sums);
+    uint32_t* rec_sums = reinterpret_cast<uint32_t*>(base + L.rec_sums);
+    uint32_t* sorted_sums = reinterpret_cast<uint32_t*>(base + L.sorted_sums);
     SortCtl* ctl = reinterpret_cast<SortCtl*>(base + L.ctl);
     uint32_t* lookback = reinterpret_cast<uint32_t*>(base + L.lookback);
     unsigned long long* keys_alt = reinterpret_cast<unsigned long long*>(base + L.keys_alt);
     uint32_t* vals_alt = reinterpret_cast<uint32_t*>(base + L.vals_alt);
+    unsigned long long* rk[2] = {reinterpret_cast<unsigned long long*>(base + L.rkeys[0]),
+                                 reinterpret_cast<unsigned long long*>(base + L.rkeys[1])};
+    uint32_t* rv[2] = {reinterpret_cast<uint32_t*>(base + L.rvals[0]), reinterpret_cast<uint32_t*>(base + L.rvals[1])};
     unsigned long long* keys_out = reinterpret_cast<unsigned long long*>(keys);
+    const size_t smem = sizeof(OnesweepSmem);
+    const int rc = enable_onesweep_smem(smem);
+    if (rc != GSFIT_OK) return rc;
 
-    // Pairs are emitted into the buffer that, after an odd or even number of
-    // ping-pong passes, leaves the sorted result in keys/vals.
-    const bool emit_to_alt = (L.n_passes % 2) == 1;
+    reduce_kernel<<<L.n_blocks, kScanThreads, 0, stream>>>(proj->tiles, n_rec, pair_sums, rec_sums);
+    GSFIT_LAUNCH_CHECK();
+    scan_kernel<<<1, 1024, 0, stream>>>(pair_sums, rec_sums, L.n_blocks, ctl, n_instances, capacity, status);
+    GSFIT_LAUNCH_CHECK();
+    compact_kernel<<<L.n_blocks, kScanThreads, 0, stream>>>(proj->tiles, reinterpret_cast<const float4*>(proj->xyd),
+                                                            n_rec, rec_sums, ctl, rk[0], rv[0], lookback,
+                                                            L.lookback_words, ranges, 2ll * total_tiles);
+    GSFIT_LAUNCH_CHECK();
+    // depth passes over the records (an even number: the result is back in buffer 0)
+    uint32_t* lb = lookback;
+    for (int p = 0; p < kDepthPasses; ++p) {
+        onesweep_kernel<<<(unsigned)L.max_rec_parts, kSortThreads, smem, stream>>>(
+            rk[p & 1], rv[p & 1], rk[(p + 1) & 1], rv[(p + 1) & 1], ctl, p, 8 * p, &ctl->n_rec, lb, status);
+        GSFIT_LAUNCH_CHECK();
+        lb += (size_t)L.max_rec_parts * kRadix;
+    }
+    reduce_sorted_kernel<<<L.n_blocks, kScanThreads, 0, stream>>>(rk[0], ctl, sorted_sums);
+    GSFIT_LAUNCH_CHECK();
+    scan_blocks_kernel<<<1, 1024, 0, stream>>>(sorted_sums, L.n_blocks);
+    GSFIT_LAUNCH_CHECK();
+    // pairs go to the buffer that, after the tile passes' ping-pong, leaves the result in keys/vals
+    const bool emit_to_alt = (L.tile_passes % 2) == 1;
     unsigned long long* k_cur = emit_to_alt ? keys_alt : keys_out;
     uint32_t* v_cur = emit_to_alt ? vals_alt : vals;
     unsigned long long* k_nxt = emit_to_alt ? keys_out : keys_alt;
     uint32_t* v_nxt = emit_to_alt ? vals : vals_alt;
-
-    reduce_kernel<<<L.n_blocks, kScanThreads, 0, stream>>>(proj->tiles, n_rec, block_sums);
-    GSFIT_LAUNCH_CHECK();
-    scan_kernel<<<1, 1024, 0, stream>>>(block_sums, L.n_blocks, ctl, n_instances, capacity, status);
-    GSFIT_LAUNCH_CHECK();
     emit_kernel<<<L.n_blocks, kScanThreads, sizeof(gsfit_camera) * n_views, stream>>>(
-        proj->tiles, reinterpret_cast<const float4*>(proj->xyd), n, n_views, cams, block_sums, ctl, k_cur, v_cur);
+        rk[0], rv[0], reinterpret_cast<const float4*>(proj->xyd), n, n_views, cams, sorted_sums, ctl, L.tile_passes,
+        k_cur, v_cur);
     GSFIT_LAUNCH_CHECK();
-    const long long lb_words = (long long)L.n_passes * L.max_parts * kRadix;
-    hist_kernel<<<kHistBlocks, 256, 0, stream>>>(k_cur, ctl, L.n_passes, lookback, lb_words, ranges,
-                                                 2ll * total_tiles);
-    GSFIT_LAUNCH_CHECK();
-    const size_t smem = sizeof(OnesweepSmem);
-    const int rc = enable_onesweep_smem(smem);
-    if (rc != GSFIT_OK) return rc;
-    for (int p = 0; p < L.n_passes; ++p) {
+    for (int q = 0; q < L.tile_passes; ++q) {
         onesweep_kernel<<<(unsigned)L.max_parts, kSortThreads, smem, stream>>>(
-            k_cur, v_cur, k_nxt, v_nxt, ctl, p, lookback + (size_t)p * L.max_parts * kRadix, status);
+            k_cur, v_cur, k_nxt, v_nxt, ctl, kDepthPasses + q, 32 + 8 * q, &ctl->n_sort, lb, status);
         GSFIT_LAUNCH_CHECK();
+        lb += (size_t)L.max_parts * kRadix;
         std::swap(k_cur, k_nxt);
         std::swap(v_cur, v_nxt);
     }
