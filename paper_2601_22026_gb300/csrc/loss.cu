@@ -20,6 +20,7 @@ constexpr int kOut = 32;             // output tile edge
 constexpr int kR1 = kOut + 10;       // moments / partials region (halo 5): 42
 constexpr int kR2 = kOut + 20;       // input region (halo 10): 52
 constexpr int kLossThreads = 256;
+static_assert(kR1 % 3 == 0 && kR1 % 7 == 0, "strip lengths of the stencil passes divide the region");
 constexpr float kC1 = 0.01f * 0.01f;
 constexpr float kC2 = 0.03f * 0.03f;
 
@@ -35,7 +36,10 @@ struct LossSmem {
     } a;
     union {
         float h[5][kR2][kR1];        // horizontal pass of x, y, x^2, y^2, xy
-        float hp[3][kR1][kOut];      // horizontal pass of the partials
+        struct {
+            float hp[3][kR1][kOut];  // horizontal pass of the partials
+            float at[kR2][kR2];      // next item's target alpha (prefetched during the last pass)
+        } st;
     } b;
     float xo[kOut][kOut];            // render and target at the output pixels
     float yo[kOut][kOut];
@@ -70,6 +74,50 @@ __device__ __forceinline__ void strip11(const float* src, const float w[11], flo
     }
 }
 
+// The view owning work item `item` and the index of that view's first item.
+__device__ __forceinline__ void locate_item(const gsfit_camera* __restrict__ cams, int item, int& v, int& first) {
+    v = 0;
+    first = 0;
+    for (;; ++v) {
+        const int k = 3 * ((cams[v].width + kOut - 1) / kOut) * ((cams[v].height + kOut - 1) / kOut);
+        if (item < first + k) break;
+        first += k;
+    }
+}
+
+__device__ __forceinline__ void cp_async4(float* smem, const float* gmem, bool ok) {
+    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    const int n = ok ? 4 : 0;  // source size 0: zero fill, nothing read
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(n) : "memory");
+}
+
+// Starts the copies of an item's render, target and target alpha over its
+// 52 x 52 input region (zero outside the image) into x, y and at.
+__device__ __forceinline__ void prefetch_item(LossSmem& S, const gsfit_camera* __restrict__ cams_g, int item, int v,
+                                              int first, const float* __restrict__ rgb,
+                                              const float* __restrict__ t_rgb, const float* __restrict__ t_alpha) {
+    const gsfit_camera& cam = cams_g[v];
+    const int W = cam.width, H = cam.height;
+    const int txn = (W + kOut - 1) / kOut;
+    const int local = item - first;
+    const int ch = local % 3, tile = local / 3;
+    const int oy = (tile / txn) * kOut, ox = (tile % txn) * kOut;
+    const long long P = (long long)W * H;
+    const float* X = rgb + 3ll * cam.pixel_offset + ch * P;
+    const float* Yt = t_rgb + 3ll * cam.pixel_offset + ch * P;
+    const float* At = t_alpha + cam.pixel_offset;
+    for (int k = threadIdx.x; k < kR2 * kR2; k += kLossThreads) {
+        const int r = k / kR2, c = k - r * kR2;
+        const int gx = ox - 10 + c, gy = oy - 10 + r;
+        const bool ok = gx >= 0 && gx < W && gy >= 0 && gy < H;
+        const long long q = ok ? (long long)gy * W + gx : 0;
+        cp_async4(&S.a.in.x[r][c], X + q, ok);
+        cp_async4(&S.a.in.y[r][c], Yt + q, ok);
+        cp_async4(&S.b.st.at[r][c], At + q, ok);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
 __global__ void __launch_bounds__(kLossThreads, 3) loss_kernel(
     const gsfit_camera* __restrict__ cams_g, int n_views, const float* __restrict__ rgb,
     const float* __restrict__ alpha, const float* __restrict__ t_rgb, const float* __restrict__ t_alpha,
@@ -86,72 +134,62 @@ __global__ void __launch_bounds__(kLossThreads, 3) loss_kernel(
     for (int v = 0; v < n_views; ++v)
         n_items += 3 * ((cams_g[v].width + kOut - 1) / kOut) * ((cams_g[v].height + kOut - 1) / kOut);
 
+    // The inputs of each item are copied asynchronously while the previous
+    // item finishes (its last pass leaves the input region and most of the
+    // horizontal-pass buffer free).
+    if (tid == 0 && (int)blockIdx.x < n_items) locate_item(cams_g, blockIdx.x, s_view, s_first);
+    __syncthreads();
+    if ((int)blockIdx.x < n_items) prefetch_item(S, cams_g, blockIdx.x, s_view, s_first, rgb, t_rgb, t_alpha);
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-        if (tid == 0) {  // the view owning this item
-            int v = 0, first = 0;
-            for (;; ++v) {
-                const int k = 3 * ((cams_g[v].width + kOut - 1) / kOut) * ((cams_g[v].height + kOut - 1) / kOut);
-                if (item < first + k) break;
-                first += k;
-            }
-            s_view = v;
-            s_first = first;
-        }
-        __syncthreads();
         const int v = s_view;
+        const int first = s_first;
+        const int next = item + gridDim.x;
+        __syncthreads();  // every thread has read this item's view
+        if (tid == 0 && next < n_items) locate_item(cams_g, next, s_view, s_first);
         const gsfit_camera& cam = cams_g[v];
         const int W = cam.width, H = cam.height;
         const int txn = (W + kOut - 1) / kOut;
-        const int local = item - s_first;
+        const int local = item - first;
         const int ch = local % 3;
         const int tile = local / 3;
         const int oy = (tile / txn) * kOut, ox = (tile % txn) * kOut;
         const long long P = (long long)W * H;
-        const float* X = rgb + 3ll * cam.pixel_offset + ch * P;
-        const float* Yt = t_rgb + 3ll * cam.pixel_offset + ch * P;
         const float* At = t_alpha + cam.pixel_offset;
         const float bgc = bg[3 * v + ch];
         const float inv3PV = 1.0f / (3.0f * (float)P * (float)n_views);
 
-        // 1. inputs over the 52 x 52 region; thread (column tid % 64, first row
-        //    tid / 64) walks rows 4 apart
-        {
-            const int cidx = tid & 63, gx = ox - 10 + cidx;
-            const bool col_ok = gx >= 0 && gx < W;
-            if (cidx < kR2) {
-                for (int r = tid >> 6; r < kR2; r += kLossThreads / 64) {
-                    const int gy = oy - 10 + r;
-                    float xv = 0.f, yv = 0.f;
-                    if (col_ok && gy >= 0 && gy < H) {
-                        const long long q = (long long)gy * W + gx;
-                        xv = X[q];
-                        yv = Yt[q] + (1.0f - At[q]) * bgc;
-                    }
-                    S.a.in.x[r][cidx] = xv;
-                    S.a.in.y[r][cidx] = yv;
-                }
-            }
+        // 1. the copied inputs: target composited over the background (zero
+        //    outside the image)
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        __syncthreads();
+        for (int k = tid; k < kR2 * kR2; k += kLossThreads) {
+            const int r = k / kR2, c = k - r * kR2;
+            const int gx = ox - 10 + c, gy = oy - 10 + r;
+            const bool ok = gx >= 0 && gx < W && gy >= 0 && gy < H;
+            S.a.in.y[r][c] = ok ? S.a.in.y[r][c] + (1.0f - S.b.st.at[r][c]) * bgc : 0.0f;
         }
         __syncthreads();
-        // 2. horizontal pass of x, y, x^2, y^2, xy: 52 rows x 42 columns, strips of 6;
-        //    and a copy of the output pixels
-        for (int k = tid; k < kR2 * 7; k += kLossThreads) {
-            const int r = k / 7, c0 = (k - r * 7) * 6;
-            float xin[16], yin[16];
+        // 2. horizontal pass of x, y, x^2, y^2, xy: 52 rows x 42 columns in
+        //    strips of 3 (728 strips: 95% of the threads busy over three
+        //    rounds); and a copy of the output pixels
+        constexpr int kHS = 3, kHN = kR1 / kHS;
+        for (int k = tid; k < kR2 * kHN; k += kLossThreads) {
+            const int r = k / kHN, c0 = (k - r * kHN) * kHS;
+            float xin[kHS + 10], yin[kHS + 10];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
+            for (int j = 0; j < kHS + 10; ++j) {
                 xin[j] = S.a.in.x[r][c0 + j];
                 yin[j] = S.a.in.y[r][c0 + j];
             }
-            float xx[16], yy[16], xy[16];
+            float xx[kHS + 10], yy[kHS + 10], xy[kHS + 10];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
+            for (int j = 0; j < kHS + 10; ++j) {
                 xx[j] = xin[j] * xin[j];
                 yy[j] = yin[j] * yin[j];
                 xy[j] = xin[j] * yin[j];
             }
 #pragma unroll
-            for (int o = 0; o < 6; ++o) {
+            for (int o = 0; o < kHS; ++o) {
                 float a = 0.f, b = 0.f, c = 0.f, d = 0.f, e = 0.f;
 #pragma unroll
                 for (int j = 0; j < 11; ++j) {
@@ -171,18 +209,19 @@ __global__ void __launch_bounds__(kLossThreads, 3) loss_kernel(
             S.yo[r][cidx] = S.a.in.y[r + 10][cidx + 10];
         }
         __syncthreads();
-        // 3. vertical pass (strips of 6 rows) straight into SSIM and its
-        //    partials w.r.t. (mu_x, E[x^2], E[xy]) on the 42 x 42 region; zero
-        //    outside the image (those windows do not exist)
+        // 3. vertical pass (strips of 7 rows: 252 strips, one round) straight
+        //    into SSIM and its partials w.r.t. (mu_x, E[x^2], E[xy]) on the
+        //    42 x 42 region; zero outside the image (those windows do not exist)
+        constexpr int kVS = 7, kVN = kR1 / kVS;
         float ssim_sum = 0.f;
-        for (int k = tid; k < kR1 * 7; k += kLossThreads) {
-            const int cidx = k % kR1, r0 = (k / kR1) * 6;
-            float mom[5][6];
+        for (int k = tid; k < kR1 * kVN; k += kLossThreads) {
+            const int cidx = k % kR1, r0 = (k / kR1) * kVS;
+            float mom[5][kVS];
 #pragma unroll
-            for (int f = 0; f < 5; ++f) strip11<6, kR1>(&S.b.h[f][r0][cidx], w, mom[f]);
+            for (int f = 0; f < 5; ++f) strip11<kVS, kR1>(&S.b.h[f][r0][cidx], w, mom[f]);
             const int gx = ox - 5 + cidx;
 #pragma unroll
-            for (int o = 0; o < 6; ++o) {
+            for (int o = 0; o < kVS; ++o) {
                 const int r = r0 + o, gy = oy - 5 + r;
                 float dmu = 0.f, dxx = 0.f, dxy = 0.f;
                 if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
@@ -191,7 +230,8 @@ __global__ void __launch_bounds__(kLossThreads, 3) loss_kernel(
                     const float sxy = mom[4][o] - mx * my;
                     const float A1 = 2.f * mx * my + kC1, A2 = 2.f * sxy + kC2;
                     const float B1 = mx * mx + my * my + kC1, B2 = sx + sy + kC2;
-                    const float iB1 = 1.0f / B1, iB2 = 1.0f / B2;
+                    // B1 >= C1 and B2 ~ >= C2: the hardware reciprocal (within 2 ulp)
+                    const float iB1 = __fdividef(1.0f, B1), iB2 = __fdividef(1.0f, B2);
                     const float iB = iB1 * iB2;
                     const float ss = A1 * A2 * iB;
                     dmu = 2.f * my * (A2 - A1) * iB - 2.f * mx * ss * (iB1 - iB2);
@@ -212,18 +252,20 @@ __global__ void __launch_bounds__(kLossThreads, 3) loss_kernel(
             float out[8];
             strip11<8, 1>(&S.a.part[f][r][c0], w, out);
 #pragma unroll
-            for (int o = 0; o < 8; ++o) S.b.hp[f][r][c0 + o] = out[o];
+            for (int o = 0; o < 8; ++o) S.b.st.hp[f][r][c0 + o] = out[o];
         }
         __syncthreads();
+        // the input region and the alpha buffer are free: copy the next item's inputs
+        if (next < n_items) prefetch_item(S, cams_g, next, s_view, s_first, rgb, t_rgb, t_alpha);
         // 5. vertical pass onto the tile (a 4-pixel column strip per thread) and
         //    the gradient
         float l1 = 0.f, la = 0.f;
         {
             const int cidx = tid % kOut, r0 = (tid / kOut) * 4;  // 32 columns x 8 strips = 256
             float cm[4], cxx[4], cxy[4];
-            strip11<4, kOut>(&S.b.hp[0][r0][cidx], w, cm);
-            strip11<4, kOut>(&S.b.hp[1][r0][cidx], w, cxx);
-            strip11<4, kOut>(&S.b.hp[2][r0][cidx], w, cxy);
+            strip11<4, kOut>(&S.b.st.hp[0][r0][cidx], w, cm);
+            strip11<4, kOut>(&S.b.st.hp[1][r0][cidx], w, cxx);
+            strip11<4, kOut>(&S.b.st.hp[2][r0][cidx], w, cxy);
 #pragma unroll
             for (int o = 0; o < 4; ++o) {
                 const int r = r0 + o;
