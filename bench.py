@@ -297,6 +297,38 @@ def oracle_sample(sc, seconds_cap: float = 30.0) -> dict:
             "sample_seconds": dt}
 
 
+def mixed_precision_rate(sc, st, bg_table, warmup: int, steps: int, features: str = "f16") -> dict:
+    """The same iteration in the mixed-precision form (16-bit rotation, scale
+    and SH storage read by the projection; everything computed in float32),
+    on a second state with the same scene, targets and backgrounds."""
+    import torch
+    from paper_2601_22026_gb300.fit import FitState, boosted_lr
+    mp = FitState(sc["gaussians"], sc["cameras"], bg=sc["bg"], lr=boosted_lr(), features=features)
+    mp.target_rgb.copy_(st.target_rgb)
+    mp.target_alpha.copy_(st.target_alpha)
+    mp.capture()
+    for k in range(warmup):
+        mp.bg.copy_(bg_table[k])
+        mp.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for k in range(steps):
+        mp.bg.copy_(bg_table[(warmup + k) % bg_table.shape[0]])
+        mp.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    if mp.check_status() != 0:
+        raise RuntimeError("device status set in the mixed-precision leg")
+    ms = e0.elapsed_time(e1) / steps
+    stage_ms = time_stages(mp, reps=10)
+    out = {"features": features, "value": 1000.0 / ms, "unit": "iters/s", "ms_per_step": ms, "steps": steps,
+           "loss_last": float(mp.loss_out.item()), "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()}}
+    del mp
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args) -> None:
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -328,6 +360,7 @@ def main() -> None:
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--no-plain", action="store_true", help="skip the single-view comparison")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision (16-bit features) leg")
     ap.add_argument("--gaussians", type=int, default=1_000_000,
                     help="smaller sets are for profiling captures only; the metric is quoted at 1M")
     ap.add_argument("--crops", type=int, default=14, help="foveal crops per batch (profiling captures only)")
@@ -436,10 +469,17 @@ def main() -> None:
            "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()}, "blended_pairs": blended,
            "roofline": roof, "clocks": clk}
 
+    plain = None
     if rank == 0 and not args.no_plain:
         plain = plain_single_view_rate(sc, st, steps=max(3, min(20, args.steps // 20)))
         out["plain_fp32_single_view"] = {"value": plain, "unit": "16-view batches/s",
                                          "speedup_of_batched": value / world / plain}
+    if rank == 0 and not args.no_mixed:
+        mp = mixed_precision_rate(sc, st, bg_table, args.warmup, max(10, min(200, args.steps)))
+        mp["vs_f32"] = mp["value"] / (value / world)
+        if plain is not None:
+            mp["speedup_vs_plain_fp32_single_view"] = mp["value"] / plain
+        out["mixed_precision"] = mp
     if rank == 0:
         host_rgb = st.target_rgb.cpu().pin_memory()
         host_alpha = st.target_alpha.cpu().pin_memory()

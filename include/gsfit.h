@@ -59,7 +59,7 @@
 extern "C" {
 #endif
 
-#define GSFIT_ABI_VERSION 1
+#define GSFIT_ABI_VERSION 2
 #define GSFIT_MAX_VIEWS 256
 #define GSFIT_TILE 16
 
@@ -91,11 +91,33 @@ typedef struct gsfit_camera {
     int32_t reserved[8];
 } gsfit_camera;
 
-/* A Gaussian set (device, float4 planes as described above). */
+/* Storage of the Gaussian features the projection reads (see gsfit_gaussians). */
+#define GSFIT_FEATURES_F32 0   /* planes 1.. read from params                   */
+#define GSFIT_FEATURES_F16 1   /* planes 1.. read from an IEEE half copy          */
+#define GSFIT_FEATURES_BF16 2  /* planes 1.. read from a bfloat16 copy            */
+
+/*
+ * A Gaussian set (device, float4 planes as described above).
+ * Mixed-precision form (the precision pattern of the fitting loop): with
+ * feature_dtype GSFIT_FEATURES_F16 or GSFIT_FEATURES_BF16 the projection and
+ * its adjoint read planes 1 .. num_planes-1 (rotation, scales, SH
+ * coefficients) from `features`, a 16-bit copy laid out as the planes with 4
+ * x 16 bits per entry (plane p of Gaussian i at 8-byte index (p - 1) * n +
+ * i, (num_planes - 1) * n * 8 bytes). The copy of plane 2 holds the
+ * activated scales (exp(log-scale) x3, 0), which 16 bits carry to 2^-12
+ * relative; the other planes hold the parameters. Plane 0 (means and
+ * opacity logit, one float4) is always read in float32 from params. Everything computed from the
+ * features (covariances, colour, transmittance, gradients) stays float32, and
+ * the gradients are those of the function of the 16-bit values. The copy is
+ * written by gsfit_features_refresh and kept current by gsfit_adam_step.
+ */
 typedef struct gsfit_gaussians {
-    const float* params;  /* gsfit_num_planes(sh_degree) * n float4 */
+    const float* params;    /* gsfit_num_planes(sh_degree) * n float4 (float32 master copy) */
     int32_t n;
-    int32_t sh_degree;    /* 0 .. 3 */
+    int32_t sh_degree;      /* 0 .. 3 */
+    const void* features;   /* 16-bit copy of planes 1.., or null with GSFIT_FEATURES_F32 */
+    int32_t feature_dtype;  /* GSFIT_FEATURES_* */
+    int32_t reserved;
 } gsfit_gaussians;
 
 /*
@@ -330,13 +352,32 @@ int gsfit_render_count(const gsfit_proj* proj, const gsfit_camera* cams, int32_t
  *   m = b1 m + (1 - b1) g; v = b2 v + (1 - b2) g^2;
  *   p -= lr * (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps),
  *   with t = *step + 1; *step is incremented on the device afterwards.
+ *   Parameters and moments are float32. With feature_dtype
+ *   GSFIT_FEATURES_F16 / GSFIT_FEATURES_BF16 the same pass also writes the
+ *   updated planes 1.. to `features`, rounded to nearest even (the layout and
+ *   contents of gsfit_gaussians.features: exp of the log-scales for plane 2).
  * Arguments: params, grads, m, v: n_planes * n float4 (device); lr: HOST
  *   array of 4 * n_planes floats, the rate of each component of each plane
- *   (0 freezes it); step: device int32 count of completed steps.
+ *   (0 freezes it); step: device int32 count of completed steps; features:
+ *   device, (n_planes - 1) * n * 8 bytes, or null with GSFIT_FEATURES_F32.
  * Errors: GSFIT_ERR_INVALID_ARG, GSFIT_ERR_CUDA.
  */
 int gsfit_adam_step(float* params, const float* grads, float* m, float* v, int32_t n, int32_t n_planes,
-                    const float* lr, float beta1, float beta2, float eps, int32_t* step, cudaStream_t stream);
+                    const float* lr, float beta1, float beta2, float eps, int32_t* step, void* features,
+                    int32_t feature_dtype, cudaStream_t stream);
+
+/*
+ * gsfit_features_refresh -- writes the 16-bit feature copy of
+ * gsfit_gaussians.features from the float32 parameters (planes 1 ..
+ * n_planes-1, exp of the log-scales for plane 2, rounded to nearest even):
+ * after the parameters were set or changed outside gsfit_adam_step.
+ * Arguments: params: n_planes * n float4 (device); features: device,
+ *   (n_planes - 1) * n * 8 bytes; feature_dtype GSFIT_FEATURES_F16 or
+ *   GSFIT_FEATURES_BF16.
+ * Errors: GSFIT_ERR_INVALID_ARG, GSFIT_ERR_CUDA.
+ */
+int gsfit_features_refresh(const float* params, int32_t n, int32_t n_planes, void* features, int32_t feature_dtype,
+                           cudaStream_t stream);
 
 #ifdef __cplusplus
 }

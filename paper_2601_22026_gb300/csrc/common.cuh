@@ -1,5 +1,7 @@
 // Internal helpers shared by the gsfit kernels (sm_103a).
 #pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -79,6 +81,51 @@ __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// 16-bit feature copies: one float4 plane entry as four halves / bfloat16s in
+// 8 bytes (round to nearest even; widening back is exact).
+template <int FT>
+__device__ __forceinline__ uint2 pack_features(float4 p) {
+    static_assert(FT == GSFIT_FEATURES_F16 || FT == GSFIT_FEATURES_BF16, "16-bit feature types only");
+    uint2 q;
+    if constexpr (FT == GSFIT_FEATURES_F16) {
+        const __half2 a = __floats2half2_rn(p.x, p.y), b = __floats2half2_rn(p.z, p.w);
+        q.x = *reinterpret_cast<const uint32_t*>(&a);
+        q.y = *reinterpret_cast<const uint32_t*>(&b);
+    } else {
+        const __nv_bfloat162 a = __floats2bfloat162_rn(p.x, p.y), b = __floats2bfloat162_rn(p.z, p.w);
+        q.x = *reinterpret_cast<const uint32_t*>(&a);
+        q.y = *reinterpret_cast<const uint32_t*>(&b);
+    }
+    return q;
+}
+
+template <int FT>
+__device__ __forceinline__ float4 unpack_features(uint2 q) {
+    static_assert(FT == GSFIT_FEATURES_F16 || FT == GSFIT_FEATURES_BF16, "16-bit feature types only");
+    float2 a, b;
+    if constexpr (FT == GSFIT_FEATURES_F16) {
+        a = __half22float2(*reinterpret_cast<const __half2*>(&q.x));
+        b = __half22float2(*reinterpret_cast<const __half2*>(&q.y));
+    } else {
+        a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.x));
+        b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.y));
+    }
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
+// Plane p of Gaussian i: plane 0 always from the float32 parameters, planes
+// 1.. from the 16-bit copy F when FT selects one.
+template <int FT>
+__device__ __forceinline__ float4 load_plane(const float4* __restrict__ P, const uint2* __restrict__ F, int n, int p,
+                                             int i) {
+    if constexpr (FT == GSFIT_FEATURES_F32) {
+        return P[(size_t)p * n + i];
+    } else {
+        if (p == 0) return P[i];
+        return unpack_features<FT>(F[(size_t)(p - 1) * n + i]);
+    }
 }
 
 }  // namespace gsfit

@@ -138,15 +138,21 @@ struct Gauss {
     float R[9];
 };
 
-__device__ __forceinline__ void load_gauss(const float4* __restrict__ P, int n, int i, Gauss& g) {
+template <int FT>
+__device__ __forceinline__ void load_gauss(const float4* __restrict__ P, const uint2* __restrict__ F, int n, int i,
+                                           Gauss& g) {
     const float4 p0 = P[i];
-    const float4 p1 = P[(size_t)n + i];
-    const float4 p2 = P[2 * (size_t)n + i];
+    const float4 p1 = load_plane<FT>(P, F, n, 1, i);
+    const float4 p2 = load_plane<FT>(P, F, n, 2, i);
     g.mx = p0.x; g.my = p0.y; g.mz = p0.z; g.logit = p0.w;
     g.qn = sqrtf(p1.x * p1.x + p1.y * p1.y + p1.z * p1.z + p1.w * p1.w);
     const float inv = 1.0f / g.qn;
     g.qw = p1.x * inv; g.qx = p1.y * inv; g.qy = p1.z * inv; g.qz = p1.w * inv;
-    g.s[0] = expf(p2.x); g.s[1] = expf(p2.y); g.s[2] = expf(p2.z);
+    if constexpr (FT == GSFIT_FEATURES_F32) {
+        g.s[0] = expf(p2.x); g.s[1] = expf(p2.y); g.s[2] = expf(p2.z);
+    } else {  // the 16-bit copy holds the activated scales
+        g.s[0] = p2.x; g.s[1] = p2.y; g.s[2] = p2.z;
+    }
     quat_rot(g.qw, g.qx, g.qy, g.qz, g.R);
     const float* R = g.R;
     const float s0 = g.s[0] * g.s[0], s1 = g.s[1] * g.s[1], s2 = g.s[2] * g.s[2];
@@ -159,13 +165,14 @@ __device__ __forceinline__ void load_gauss(const float4* __restrict__ P, int n, 
     g.Sig[5] = R[6] * R[6] * s0 + R[7] * R[7] * s1 + R[8] * R[8] * s2;
 }
 
-template <int DEG>
-__device__ __forceinline__ void load_sh(const float4* __restrict__ P, int n, int i, float* sh) {
+template <int DEG, int FT>
+__device__ __forceinline__ void load_sh(const float4* __restrict__ P, const uint2* __restrict__ F, int n, int i,
+                                        float* sh) {
     constexpr int K3 = 3 * SH<DEG>::K;
     constexpr int NP = (K3 + 3) / 4;
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-        const float4 q = P[(size_t)(3 + p) * n + i];
+        const float4 q = load_plane<FT>(P, F, n, 3 + p, i);
         if (4 * p + 0 < K3) sh[4 * p + 0] = q.x;
         if (4 * p + 1 < K3) sh[4 * p + 1] = q.y;
         if (4 * p + 2 < K3) sh[4 * p + 2] = q.z;
@@ -215,8 +222,8 @@ __device__ __forceinline__ void view_geom(const gsfit_camera& cam, const Gauss& 
     o.det = det2(o.a, o.b, o.c);
 }
 
-template <int DEG>
-__global__ void __launch_bounds__(256) project_kernel(const float4* __restrict__ P, int n,
+template <int DEG, int FT>
+__global__ void __launch_bounds__(256) project_kernel(const float4* __restrict__ P, const uint2* __restrict__ F, int n,
                                                       const gsfit_camera* __restrict__ cams_g, int n_views,
                                                       float4* __restrict__ xyd, float4* __restrict__ conic,
                                                       float4* __restrict__ rgb, uint32_t* __restrict__ tiles) {
@@ -227,9 +234,9 @@ __global__ void __launch_bounds__(256) project_kernel(const float4* __restrict__
     if (i >= n) return;
     constexpr int K = SH<DEG>::K;
     Gauss g;
-    load_gauss(P, n, i, g);
+    load_gauss<FT>(P, F, n, i, g);
     float sh[3 * K];
-    load_sh<DEG>(P, n, i, sh);
+    load_sh<DEG, FT>(P, F, n, i, sh);
     const float opacity = 1.0f / (1.0f + expf(-g.logit));
 
     for (int v = 0; v < n_views; ++v) {
@@ -295,8 +302,9 @@ __global__ void __launch_bounds__(256) project_kernel(const float4* __restrict__
 // iteration), accumulates the SH-coefficient gradient, and chains dL/dSigma to
 // scale and rotation once.
 
-template <int DEG>
-__global__ void __launch_bounds__(256) project_bwd_rec_kernel(const float4* __restrict__ P, int n,
+template <int DEG, int FT>
+__global__ void __launch_bounds__(256) project_bwd_rec_kernel(const float4* __restrict__ P,
+                                                              const uint2* __restrict__ F, int n,
                                                               const gsfit_camera* __restrict__ cams_g,
                                                               const float4* __restrict__ xyd,
                                                               const float4* __restrict__ conic,
@@ -314,7 +322,7 @@ __global__ void __launch_bounds__(256) project_bwd_rec_kernel(const float4* __re
     const float4 cm = __ldg(rgbm + r);
     const gsfit_camera& cam = cams_g[v];
     Gauss g;
-    load_gauss(P, n, i, g);
+    load_gauss<FT>(P, F, n, i, g);
     ViewGeom vg;
     view_geom(cam, g, vg);
     const float iz = 1.0f / vg.tz, iz2 = iz * iz;
@@ -387,7 +395,7 @@ __global__ void __launch_bounds__(256) project_bwd_rec_kernel(const float4* __re
         const float idist = rsqrtf(dx * dx + dy * dy + dz * dz);
         dx *= idist; dy *= idist; dz *= idist;
         float sh[3 * K];
-        load_sh<DEG>(P, n, i, sh);
+        load_sh<DEG, FT>(P, F, n, i, sh);
         float wk[K];
 #pragma unroll
         for (int k = 0; k < K; ++k)
@@ -410,9 +418,9 @@ constexpr int kProjBwdThreads = 256;
 // accesses hit 32 different banks.
 __device__ __forceinline__ float& dsh_acc(float* s_dsh, int k) { return s_dsh[k * kProjBwdThreads + threadIdx.x]; }
 
-template <int DEG>
+template <int DEG, int FT>
 __global__ void __launch_bounds__(kProjBwdThreads, 3) project_bwd_gauss_kernel(
-    const float4* __restrict__ P, int n, const gsfit_camera* __restrict__ cams_g, int n_views,
+    const float4* __restrict__ P, const uint2* __restrict__ F, int n, const gsfit_camera* __restrict__ cams_g, int n_views,
     const float4* __restrict__ xyd, float4* __restrict__ grad2d, float4* __restrict__ G) {
     // dynamic shared memory: the camera table, then 3K SH-gradient accumulators
     // per thread (kept out of registers)
@@ -471,7 +479,7 @@ __global__ void __launch_bounds__(kProjBwdThreads, 3) project_bwd_gauss_kernel(
       }
     }
     Gauss g;
-    load_gauss(P, n, i, g);
+    load_gauss<FT>(P, F, n, i, g);
     const float opacity = 1.0f / (1.0f + expf(-g.logit));
     const float dlogit = dop * opacity * (1.f - opacity);
 
@@ -519,28 +527,30 @@ __global__ void __launch_bounds__(kProjBwdThreads, 3) project_bwd_gauss_kernel(
     }
 }
 
-template <int DEG>
+template <int DEG, int FT>
 int launch_project(const gsfit_gaussians* g, const gsfit_camera* cams, int V, gsfit_proj* out, cudaStream_t s) {
     const int threads = 256;
     const int blocks = (g->n + threads - 1) / threads;
     const size_t smem = sizeof(gsfit_camera) * V;
-    project_kernel<DEG><<<blocks, threads, smem, s>>>(
-        reinterpret_cast<const float4*>(g->params), g->n, cams, V, reinterpret_cast<float4*>(out->xyd),
-        reinterpret_cast<float4*>(out->conic), reinterpret_cast<float4*>(out->rgb), out->tiles);
+    project_kernel<DEG, FT><<<blocks, threads, smem, s>>>(
+        reinterpret_cast<const float4*>(g->params), reinterpret_cast<const uint2*>(g->features), g->n, cams, V,
+        reinterpret_cast<float4*>(out->xyd), reinterpret_cast<float4*>(out->conic),
+        reinterpret_cast<float4*>(out->rgb), out->tiles);
     GSFIT_LAUNCH_CHECK();
     return GSFIT_OK;
 }
 
-template <int DEG>
+template <int DEG, int FT>
 int launch_project_bwd(const gsfit_gaussians* g, const gsfit_proj* proj, const gsfit_camera* cams, int V,
                        float* grad2d, float* grads, cudaStream_t s) {
     const int threads = kProjBwdThreads;
     const int blocks = (g->n + threads - 1) / threads;
+    const float4* P = reinterpret_cast<const float4*>(g->params);
+    const uint2* F = reinterpret_cast<const uint2*>(g->features);
     dim3 grid_rec((unsigned)V, (unsigned)blocks);
-    project_bwd_rec_kernel<DEG><<<grid_rec, threads, 0, s>>>(
-        reinterpret_cast<const float4*>(g->params), g->n, cams, reinterpret_cast<const float4*>(proj->xyd),
-        reinterpret_cast<const float4*>(proj->conic), reinterpret_cast<const float4*>(proj->rgb),
-        reinterpret_cast<float4*>(grad2d));
+    project_bwd_rec_kernel<DEG, FT><<<grid_rec, threads, 0, s>>>(
+        P, F, g->n, cams, reinterpret_cast<const float4*>(proj->xyd), reinterpret_cast<const float4*>(proj->conic),
+        reinterpret_cast<const float4*>(proj->rgb), reinterpret_cast<float4*>(grad2d));
     GSFIT_LAUNCH_CHECK();
     const size_t smem = sizeof(gsfit_camera) * V + sizeof(float) * 3 * SH<DEG>::K * threads;
     static bool attr_done[64] = {false};
@@ -549,22 +559,48 @@ int launch_project_bwd(const gsfit_gaussians* g, const gsfit_proj* proj, const g
     if (dev < 0 || dev >= 64) return GSFIT_ERR_CUDA;
     if (!attr_done[dev]) {
         const size_t max_smem = sizeof(gsfit_camera) * GSFIT_MAX_VIEWS + sizeof(float) * 3 * SH<DEG>::K * threads;
-        GSFIT_CUDA_CHECK(cudaFuncSetAttribute(project_bwd_gauss_kernel<DEG>,
+        GSFIT_CUDA_CHECK(cudaFuncSetAttribute(project_bwd_gauss_kernel<DEG, FT>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem));
         attr_done[dev] = true;
     }
-    project_bwd_gauss_kernel<DEG><<<blocks, threads, smem, s>>>(
-        reinterpret_cast<const float4*>(g->params), g->n, cams, V, reinterpret_cast<const float4*>(proj->xyd),
-        reinterpret_cast<float4*>(grad2d), reinterpret_cast<float4*>(grads));
+    project_bwd_gauss_kernel<DEG, FT><<<blocks, threads, smem, s>>>(
+        P, F, g->n, cams, V, reinterpret_cast<const float4*>(proj->xyd), reinterpret_cast<float4*>(grad2d),
+        reinterpret_cast<float4*>(grads));
     GSFIT_LAUNCH_CHECK();
     return GSFIT_OK;
+}
+
+// Dispatch over the feature storage type.
+template <int DEG>
+int project_ft(const gsfit_gaussians* g, const gsfit_camera* cams, int V, gsfit_proj* out, cudaStream_t s) {
+    switch (g->feature_dtype) {
+        case GSFIT_FEATURES_F16: return launch_project<DEG, GSFIT_FEATURES_F16>(g, cams, V, out, s);
+        case GSFIT_FEATURES_BF16: return launch_project<DEG, GSFIT_FEATURES_BF16>(g, cams, V, out, s);
+        default: return launch_project<DEG, GSFIT_FEATURES_F32>(g, cams, V, out, s);
+    }
+}
+
+template <int DEG>
+int project_bwd_ft(const gsfit_gaussians* g, const gsfit_proj* proj, const gsfit_camera* cams, int V, float* grad2d,
+                   float* grads, cudaStream_t s) {
+    switch (g->feature_dtype) {
+        case GSFIT_FEATURES_F16:
+            return launch_project_bwd<DEG, GSFIT_FEATURES_F16>(g, proj, cams, V, grad2d, grads, s);
+        case GSFIT_FEATURES_BF16:
+            return launch_project_bwd<DEG, GSFIT_FEATURES_BF16>(g, proj, cams, V, grad2d, grads, s);
+        default: return launch_project_bwd<DEG, GSFIT_FEATURES_F32>(g, proj, cams, V, grad2d, grads, s);
+    }
 }
 
 }  // namespace
 
 bool valid_gaussians(const gsfit_gaussians* g) {
-    return g && g->params && g->n > 0 && g->sh_degree >= 0 && g->sh_degree <= 3 &&
-           (reinterpret_cast<uintptr_t>(g->params) % 16) == 0;
+    if (!(g && g->params && g->n > 0 && g->sh_degree >= 0 && g->sh_degree <= 3 &&
+          (reinterpret_cast<uintptr_t>(g->params) % 16) == 0))
+        return false;
+    if (g->feature_dtype == GSFIT_FEATURES_F32) return true;
+    return (g->feature_dtype == GSFIT_FEATURES_F16 || g->feature_dtype == GSFIT_FEATURES_BF16) && g->features &&
+           (reinterpret_cast<uintptr_t>(g->features) % 8) == 0;
 }
 
 bool valid_proj(const gsfit_proj* p) {
@@ -575,10 +611,10 @@ bool valid_proj(const gsfit_proj* p) {
 int project_bwd(const gsfit_gaussians* g, const gsfit_proj* proj, const gsfit_camera* cams, int V, float* grad2d,
                 float* grads, cudaStream_t s) {
     switch (g->sh_degree) {
-        case 0: return launch_project_bwd<0>(g, proj, cams, V, grad2d, grads, s);
-        case 1: return launch_project_bwd<1>(g, proj, cams, V, grad2d, grads, s);
-        case 2: return launch_project_bwd<2>(g, proj, cams, V, grad2d, grads, s);
-        default: return launch_project_bwd<3>(g, proj, cams, V, grad2d, grads, s);
+        case 0: return project_bwd_ft<0>(g, proj, cams, V, grad2d, grads, s);
+        case 1: return project_bwd_ft<1>(g, proj, cams, V, grad2d, grads, s);
+        case 2: return project_bwd_ft<2>(g, proj, cams, V, grad2d, grads, s);
+        default: return project_bwd_ft<3>(g, proj, cams, V, grad2d, grads, s);
     }
 }
 
@@ -595,9 +631,9 @@ extern "C" int gsfit_project(const gsfit_gaussians* g, const gsfit_camera* cams,
         n_views > GSFIT_MAX_VIEWS)
         return GSFIT_ERR_INVALID_ARG;
     switch (g->sh_degree) {
-        case 0: return gsfit::launch_project<0>(g, cams, n_views, out, stream);
-        case 1: return gsfit::launch_project<1>(g, cams, n_views, out, stream);
-        case 2: return gsfit::launch_project<2>(g, cams, n_views, out, stream);
-        default: return gsfit::launch_project<3>(g, cams, n_views, out, stream);
+        case 0: return gsfit::project_ft<0>(g, cams, n_views, out, stream);
+        case 1: return gsfit::project_ft<1>(g, cams, n_views, out, stream);
+        case 2: return gsfit::project_ft<2>(g, cams, n_views, out, stream);
+        default: return gsfit::project_ft<3>(g, cams, n_views, out, stream);
     }
 }

@@ -32,12 +32,22 @@ class FitState:
 
     def __init__(self, gaussians: dict, cams: dict, *, target_rgb=None, target_alpha=None, bg=None,
                  capacity: int | None = None, lr: dict | None = None, eps: float = 1e-15,
-                 lam: float = 0.2, device: str = "cuda"):
+                 lam: float = 0.2, features: str = "f32", device: str = "cuda"):
+        """features: "f32", or "f16" / "bf16" for the mixed-precision form
+        (16-bit copy of rotation, scales and SH read by the projection, kept
+        current by Adam; float32 master parameters and moments)."""
         self.device = device
         self.n = int(gaussians["means"].shape[0])
         self.sh_degree = int(round(gaussians["sh"].shape[1] ** 0.5)) - 1
         self.n_planes = G.num_planes(self.sh_degree)
         self.params = torch.from_numpy(G.pack_params(gaussians)).to(device).contiguous()
+        self.feature_name = features
+        self.feature_dtype = G.FEATURES[features]
+        self.features = None
+        if self.feature_dtype != 0:
+            tdt = torch.float16 if features == "f16" else torch.bfloat16
+            self.features = torch.empty((self.n_planes - 1, self.n, 4), dtype=tdt, device=device)
+            self.refresh_features()
         self.grads = torch.zeros_like(self.params)
         self.m = torch.zeros_like(self.params)
         self.v = torch.zeros_like(self.params)
@@ -87,10 +97,15 @@ class FitState:
     def set_bg(self, bg) -> None:
         self.bg.copy_(torch.as_tensor(np.asarray(bg, np.float32)).reshape(self.V, 3))
 
+    def refresh_features(self, stream=None) -> None:
+        """Rewrites the 16-bit feature copy from the float32 parameters."""
+        if self.feature_dtype != 0:
+            G.gsfit_features_refresh(self.params, self.n, self.n_planes, self.features, self.feature_dtype, stream)
+
     # -- capacity -------------------------------------------------------
     def count_instances(self) -> int:
         """Pairs the current parameters produce (projects once; syncs)."""
-        G.gsfit_project(self.params, self.n, self.sh_degree, self.cams_dev, self.V, self.proj)
+        self.project()
         return int(self.proj.tiles.to(torch.int64).sum().item())
 
     def ensure_capacity(self, capacity: int | None = None, slack: float = 1.5) -> None:
@@ -114,7 +129,8 @@ class FitState:
 
     # -- stages ---------------------------------------------------------
     def project(self, stream=None):
-        G.gsfit_project(self.params, self.n, self.sh_degree, self.cams_dev, self.V, self.proj, stream)
+        G.gsfit_project(self.params, self.n, self.sh_degree, self.cams_dev, self.V, self.proj, stream,
+                        self.features, self.feature_dtype)
 
     def bin_sort(self, stream=None):
         G.gsfit_bin_sort(self.proj, self.cams_dev, self.V, self.n, self.T, self.sort_ws, self.keys, self.vals,
@@ -131,7 +147,8 @@ class FitState:
     def render_bwd(self, stream=None):
         G.gsfit_render_bwd(self.params, self.n, self.sh_degree, self.proj, self.cams_dev, self.V, self.T,
                            self.vals, self.ranges, self.bg, self.T_final, self.n_contrib, self.dL_drgb,
-                           self.dL_dalpha, self.grad2d, self.grads, stream, self.tile_order, self.status)
+                           self.dL_dalpha, self.grad2d, self.grads, stream, self.tile_order, self.status,
+                           self.features, self.feature_dtype)
 
     def blend_bwd(self, stream=None):
         G.gsfit_blend_bwd(self.proj, self.cams_dev, self.V, self.n, self.T, self.vals, self.ranges, self.bg,
@@ -140,7 +157,7 @@ class FitState:
 
     def project_bwd(self, stream=None):
         G.gsfit_project_bwd(self.params, self.n, self.sh_degree, self.proj, self.cams_dev, self.V, self.grad2d,
-                            self.grads, stream)
+                            self.grads, stream, self.features, self.feature_dtype)
 
     def blended_pairs(self) -> int:
         """Blended (pixel, Gaussian) pairs of the last forward pass (syncs)."""
@@ -151,7 +168,7 @@ class FitState:
 
     def adam(self, stream=None):
         G.gsfit_adam_step(self.params, self.grads, self.m, self.v, self.n, self.n_planes, self.lr, 0.9, 0.999,
-                          self.eps, self.step_count, stream)
+                          self.eps, self.step_count, stream, self.features, self.feature_dtype)
 
     def forward(self, stream=None):
         self.project(stream)
@@ -214,6 +231,7 @@ class GsfitRender(torch.autograd.Function):
     def forward(ctx, params, state: FitState):
         if params.data_ptr() != state.params.data_ptr():
             state.params.copy_(params.detach())
+            state.refresh_features()
         state.forward()
         ctx.state = state
         ctx.save_for_backward(state.T_final, state.n_contrib)

@@ -31,7 +31,14 @@ _size = ctypes.c_size_t
 
 
 class Gaussians(ctypes.Structure):
-    _fields_ = [("params", _P), ("n", _i32), ("sh_degree", _i32)]
+    _fields_ = [("params", _P), ("n", _i32), ("sh_degree", _i32), ("features", _P), ("feature_dtype", _i32),
+                ("reserved", _i32)]
+
+
+ABI_VERSION = 2  # GSFIT_ABI_VERSION of include/gsfit.h
+
+# gsfit_gaussians.feature_dtype values (GSFIT_FEATURES_*)
+FEATURES = {"f32": 0, "f16": 1, "bf16": 2}
 
 
 class Proj(ctypes.Structure):
@@ -63,7 +70,8 @@ SIGNATURES = {
     "gsfit_blend_bwd": (ctypes.c_int, [_P, _P, _i32, _i32, _i32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "gsfit_project_bwd": (ctypes.c_int, [_P, _P, _P, _i32, _P, _P, _P]),
     "gsfit_render_count": (ctypes.c_int, [_P, _P, _i32, _i32, _i32, _P, _P, _P, _P, _P, _P]),
-    "gsfit_adam_step": (ctypes.c_int, [_P, _P, _P, _P, _i32, _i32, _P, _f32, _f32, _f32, _P, _P]),
+    "gsfit_adam_step": (ctypes.c_int, [_P, _P, _P, _P, _i32, _i32, _P, _f32, _f32, _f32, _P, _P, _i32, _P]),
+    "gsfit_features_refresh": (ctypes.c_int, [_P, _i32, _i32, _P, _i32, _P]),
 }
 
 _lib = None
@@ -87,7 +95,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         fn = getattr(lib, name)
         fn.restype = res
         fn.argtypes = args
-    if lib.gsfit_abi_version() != 1:
+    if lib.gsfit_abi_version() != ABI_VERSION:
         raise RuntimeError("libgsfit.so ABI version mismatch")
     _lib = lib
     return lib
@@ -225,12 +233,13 @@ class ProjBuffers:
         return ProjBuffers(f(), f(), f(), torch.empty(n_records, dtype=torch.int32, device=device))
 
 
-def gaussians_struct(params, n: int, sh_degree: int) -> Gaussians:
-    return Gaussians(_ptr(params), n, sh_degree)
+def gaussians_struct(params, n: int, sh_degree: int, features=None, feature_dtype: int = 0) -> Gaussians:
+    return Gaussians(_ptr(params), n, sh_degree, _ptr(features), int(feature_dtype), 0)
 
 
-def gsfit_project(params, n, sh_degree, cams_dev, n_views, proj: ProjBuffers, stream=None):
-    g = gaussians_struct(params, n, sh_degree)
+def gsfit_project(params, n, sh_degree, cams_dev, n_views, proj: ProjBuffers, stream=None, features=None,
+                  feature_dtype=0):
+    g = gaussians_struct(params, n, sh_degree, features, feature_dtype)
     p = proj.struct()
     _check(load().gsfit_project(ctypes.byref(g), _ptr(cams_dev), n_views, ctypes.byref(p), _stream(stream)),
            "gsfit_project")
@@ -284,8 +293,8 @@ def gsfit_loss_noalloc(cams_dev, n_views, rgb, alpha, target_rgb, target_alpha, 
 
 def gsfit_render_bwd(params, n, sh_degree, proj: ProjBuffers, cams_dev, n_views, total_tiles, vals, ranges, bg,
                      T_final, n_contrib, dL_drgb, dL_dalpha, grad2d, grads, stream=None, tile_order=None,
-                     status=None):
-    g = gaussians_struct(params, n, sh_degree)
+                     status=None, features=None, feature_dtype=0):
+    g = gaussians_struct(params, n, sh_degree, features, feature_dtype)
     p = proj.struct()
     _check(load().gsfit_render_bwd(ctypes.byref(g), ctypes.byref(p), _ptr(cams_dev), n_views, total_tiles,
                                    _ptr(vals), _ptr(ranges), _ptr(tile_order), _ptr(bg), _ptr(T_final), _ptr(n_contrib),
@@ -303,8 +312,9 @@ def gsfit_blend_bwd(proj: ProjBuffers, cams_dev, n_views, n, total_tiles, vals, 
            "gsfit_blend_bwd")
 
 
-def gsfit_project_bwd(params, n, sh_degree, proj: ProjBuffers, cams_dev, n_views, grad2d, grads, stream=None):
-    g = gaussians_struct(params, n, sh_degree)
+def gsfit_project_bwd(params, n, sh_degree, proj: ProjBuffers, cams_dev, n_views, grad2d, grads, stream=None,
+                      features=None, feature_dtype=0):
+    g = gaussians_struct(params, n, sh_degree, features, feature_dtype)
     p = proj.struct()
     _check(load().gsfit_project_bwd(ctypes.byref(g), ctypes.byref(p), _ptr(cams_dev), n_views, _ptr(grad2d),
                                     _ptr(grads), _stream(stream)),
@@ -319,10 +329,17 @@ def gsfit_render_count(proj: ProjBuffers, cams_dev, n_views, n, total_tiles, val
            "gsfit_render_count")
 
 
-def gsfit_adam_step(params, grads, m, v, n, n_planes, lr: np.ndarray, beta1, beta2, eps, step, stream=None):
+def gsfit_adam_step(params, grads, m, v, n, n_planes, lr: np.ndarray, beta1, beta2, eps, step, stream=None,
+                    features=None, feature_dtype=0):
     lr = np.ascontiguousarray(lr, dtype=np.float32).reshape(-1)
     assert lr.size == 4 * n_planes
     _check(load().gsfit_adam_step(_ptr(params), _ptr(grads), _ptr(m), _ptr(v), n, n_planes,
                                   lr.ctypes.data_as(_P), float(beta1), float(beta2), float(eps), _ptr(step),
-                                  _stream(stream)),
+                                  _ptr(features), int(feature_dtype), _stream(stream)),
            "gsfit_adam_step")
+
+
+def gsfit_features_refresh(params, n, n_planes, features, feature_dtype, stream=None):
+    _check(load().gsfit_features_refresh(_ptr(params), n, n_planes, _ptr(features), int(feature_dtype),
+                                         _stream(stream)),
+           "gsfit_features_refresh")

@@ -37,7 +37,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version_and_status_strings(lib):
-    assert lib.gsfit_abi_version() == 1
+    assert lib.gsfit_abi_version() == 2
     assert lib.gsfit_status_string(G.GSFIT_ERR_CAPACITY) == b"instance capacity exceeded"
     assert lib.gsfit_status_string(G.GSFIT_ERR_TIMEOUT) == b"bounded device wait ran out"
 
@@ -95,7 +95,7 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert need > 0
     assert lib.gsfit_bin_sort(ctypes.byref(p), fake, 1, 10, 4, fake, need - 1, fake, fake, 1000, fake, fake,
                               None, fake, None) == G.GSFIT_ERR_INVALID_ARG
-    assert lib.gsfit_adam_step(fake, fake, fake, fake, 10, 17, None, 0.9, 0.999, 1e-15, fake,
+    assert lib.gsfit_adam_step(fake, fake, fake, fake, 10, 17, None, 0.9, 0.999, 1e-15, fake, None, 0,
                                None) == G.GSFIT_ERR_INVALID_ARG
     assert lib.gsfit_loss_workspace_size(0) == 0
 
@@ -106,3 +106,19 @@ def test_workspace_size_grows_with_capacity(lib):
     c = lib.gsfit_bin_sort_workspace_size(1000, 20_000, 70_000)  # more tile bits: one more pass
     assert 0 < a < b < c
     assert b - a >= 10_000 * 12
+
+
+def test_feature_storage_arguments_rejected_on_host(lib):
+    fake = 256
+    p = G.Proj(fake, fake, fake, fake)
+    # unknown storage type, and a 16-bit type without its copy
+    for dtype, feats in [(7, fake), (G.FEATURES["f16"], None), (G.FEATURES["bf16"], None), (G.FEATURES["f16"], 260)]:
+        g = G.Gaussians(fake, 10, 0, feats, dtype, 0)
+        assert lib.gsfit_project(ctypes.byref(g), fake, 1, ctypes.byref(p), None) == G.GSFIT_ERR_INVALID_ARG
+    lr = (ctypes.c_float * 16)()
+    assert lib.gsfit_adam_step(fake, fake, fake, fake, 10, 4, lr, 0.9, 0.999, 1e-15, fake, None,
+                               G.FEATURES["f16"], None) == G.GSFIT_ERR_INVALID_ARG
+    assert lib.gsfit_adam_step(fake, fake, fake, fake, 10, 4, lr, 0.9, 0.999, 1e-15, fake, fake, 5,
+                               None) == G.GSFIT_ERR_INVALID_ARG
+    assert lib.gsfit_features_refresh(fake, 10, 4, fake, G.FEATURES["f32"], None) == G.GSFIT_ERR_INVALID_ARG
+    assert lib.gsfit_features_refresh(fake, 10, 1, fake, G.FEATURES["f16"], None) == G.GSFIT_ERR_INVALID_ARG
