@@ -303,7 +303,8 @@ def mixed_precision_rate(sc, st, bg_table, warmup: int, steps: int, features: st
     on a second state with the same scene, targets and backgrounds."""
     import torch
     from paper_2601_22026_gb300.fit import FitState, boosted_lr
-    mp = FitState(sc["gaussians"], sc["cameras"], bg=sc["bg"], lr=boosted_lr(), features=features)
+    mp = FitState(sc["gaussians"], sc["cameras"], bg=sc["bg"], lr=boosted_lr(), features=features,
+                  tile=st.tile, batch=int(st.opts.batch))
     mp.target_rgb.copy_(st.target_rgb)
     mp.target_alpha.copy_(st.target_alpha)
     mp.capture()
@@ -361,6 +362,7 @@ def main() -> None:
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--no-plain", action="store_true", help="skip the single-view comparison")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision (16-bit features) leg")
+    ap.add_argument("--no-tune", action="store_true", help="default tile 16 / batch 128 instead of the autotuner")
     ap.add_argument("--gaussians", type=int, default=1_000_000,
                     help="smaller sets are for profiling captures only; the metric is quoted at 1M")
     ap.add_argument("--crops", type=int, default=14, help="foveal crops per batch (profiling captures only)")
@@ -383,6 +385,26 @@ def main() -> None:
     pkg.build()
 
     sc, st = build_state(0, args.gaussians, args.crops)
+    tuned = None
+    if not args.no_tune:
+        # the batched launch's tunables (tile edge, batch depth), chosen on this
+        # workload before anything is timed; cached per device and workload
+        from paper_2601_22026_gb300 import tune
+        from paper_2601_22026_gb300.fit import FitState, boosted_lr
+
+        def make_state(tile, batch, features="f32"):
+            s2 = FitState(sc["gaussians"], sc["cameras"], bg=sc["bg"], lr=boosted_lr(), tile=tile, batch=batch,
+                          features=features)
+            s2.target_rgb.copy_(st.target_rgb)
+            s2.target_alpha.copy_(st.target_alpha)
+            return s2
+
+        tuned = tune.autotune(make_state, tune.signature(st.n, st.sh_degree, sc["cameras"]))
+        if (tuned["tile"], tuned["batch"]) != (st.tile, st.opts.batch):
+            best = make_state(tuned["tile"], tuned["batch"])
+            del st
+            torch.cuda.empty_cache()
+            st = best
     V = st.V
     bg_table = torch.from_numpy(scenes.backgrounds(V, 3, n_steps=args.warmup + args.steps)).cuda()
     st.capture()
@@ -464,7 +486,10 @@ def main() -> None:
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": WORKLOAD, "gaussians": st.n, "views": V, "pixels": st.P, "tiles": st.T,
                       "pairs_per_step": n_inst, "parallelism": "replicas" if world > 1 else "single",
-                      "l2": "working set > L2 (no flush)", "graph": True, "loss_last": loss_now},
+                      "l2": "working set > L2 (no flush)", "graph": True, "loss_last": loss_now,
+                      "tile": st.tile, "batch": int(st.opts.batch),
+                      "autotune": None if tuned is None else
+                      {"cached": tuned["cached"], "candidates": tuned["candidates"]}},
            "gpu_launches": launches_per_step * args.steps,
            "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()}, "blended_pairs": blended,
            "roofline": roof, "clocks": clk}

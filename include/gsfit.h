@@ -29,7 +29,8 @@
  *     device (instance capacity exceeded, a bounded wait that ran out) are
  *     written to the caller's int32 status word, read after a synchronise.
  *   - Sizes: n Gaussians (n < 2^31), V views (1 <= V <= GSFIT_MAX_VIEWS),
- *     tile size B = 16 pixels.
+ *     tile size B = 8 or 16 pixels (GSFIT_TILE = 16 is the default; see
+ *     gsfit_camera and gsfit_render_opts).
  *
  * Data layouts
  *   Gaussian parameters (and their gradients, and the Adam moments) are
@@ -77,8 +78,11 @@ extern "C" {
  * camera centre in world space (-R^T t), used for the SH view direction.
  * A Gaussian is culled in a view when its float32 depth is <= near_plane
  * (3DGS uses 0.2). tile_offset is the global id of the view's first tile and
- * pixel_offset its first pixel in the packed images; gsfit_camera_layout
- * fills both for a batch.
+ * pixel_offset its first pixel in the packed images; tile is the tile edge
+ * B the batch is laid out for (8 or 16, the same in every view of a batch);
+ * gsfit_camera_layout fills all three. The projection's tile rectangles and
+ * the binning use B; the compositing calls are told B by their options and
+ * check it against the cameras.
  */
 typedef struct gsfit_camera {
     float viewmat[12];
@@ -88,7 +92,8 @@ typedef struct gsfit_camera {
     int32_t width, height;
     int32_t tile_offset;
     int32_t pixel_offset;
-    int32_t reserved[8];
+    int32_t tile;         /* tile edge in pixels, 8 or 16 (any other value reads as 16) */
+    int32_t reserved[7];
 } gsfit_camera;
 
 /* Storage of the Gaussian features the projection reads (see gsfit_gaussians). */
@@ -148,9 +153,10 @@ int gsfit_abi_version(void);
 const char* gsfit_status_string(int code);
 
 /*
- * Host helper: fills tile_offset and pixel_offset of V HOST cameras for tile
- * size `tile`, laying views out in order, and returns the batch totals.
- * Returns GSFIT_ERR_INVALID_ARG for a non-positive size or V out of range.
+ * Host helper: fills tile_offset, pixel_offset and tile of V HOST cameras for
+ * tile size `tile` (8 or 16), laying views out in order, and returns the batch
+ * totals. Returns GSFIT_ERR_INVALID_ARG for another tile size, a
+ * non-positive image size or V out of range.
  */
 int gsfit_camera_layout(gsfit_camera* cams_host, int n_views, int tile, int32_t* total_tiles,
                         int64_t* total_pixels);
@@ -218,6 +224,22 @@ int gsfit_bin_sort(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_v
                    int32_t* status, cudaStream_t stream);
 
 /*
+ * Options of the compositing calls: the tunables of the batched launch.
+ *   tile:  the tile edge the cameras were laid out for by gsfit_camera_layout
+ *          (8 or 16); a launch whose cameras say otherwise writes
+ *          GSFIT_ERR_INVALID_ARG to the status word and does nothing.
+ *   batch: records per shared-memory slot of the producer ring (the number of
+ *          Gaussians staged per batch): 64, 128 or 256.
+ * A null pointer or a 0 field selects the default (tile 16, batch 128).
+ * gsfit_render_autotune measures the batch depths on a caller's workload.
+ */
+typedef struct gsfit_render_opts {
+    int32_t tile;
+    int32_t batch;
+    int32_t reserved[2];
+} gsfit_render_opts;
+
+/*
  * gsfit_render_fwd -- front-to-back compositing (3DGS, with the alpha output
  * used for alpha supervision, Section 4.2).
  *   For each pixel, over its tile's sorted pairs: power as in gsfit_proj,
@@ -235,14 +257,15 @@ int gsfit_bin_sort(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_v
  *   writes GSFIT_ERR_TIMEOUT there, the affected tiles' outputs are
  *   incomplete, and later tiles of this and the other compositing calls that
  *   see that value skip their work. With a null status a timeout goes
- *   unreported.
- * Errors: GSFIT_ERR_INVALID_ARG, GSFIT_ERR_CUDA; GSFIT_ERR_TIMEOUT on the
+ *   unreported. opts: see gsfit_render_opts (may be null).
+ * Errors: GSFIT_ERR_INVALID_ARG (also for unsupported options), GSFIT_ERR_CUDA;
+ *   GSFIT_ERR_TIMEOUT, or GSFIT_ERR_INVALID_ARG for a tile mismatch, on the
  *   device, through status.
  */
 int gsfit_render_fwd(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_views, int32_t n,
                      int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges, const uint32_t* tile_order,
                      const float* bg, float* rgb, float* alpha, float* T_final, uint32_t* n_contrib,
-                     int32_t* status, cudaStream_t stream);
+                     const gsfit_render_opts* opts, int32_t* status, cudaStream_t stream);
 
 /*
  * gsfit_loss -- photometric loss of a view batch and its gradient.
@@ -304,15 +327,16 @@ int gsfit_loss_noalloc(const gsfit_camera* cams, int32_t n_views, const float* r
  *   image layout; grad2d: device workspace of 16 floats per record
  *   (n_views * n * 64 bytes) that must be zero before the first call; this
  *   call leaves it zero again. grads: device, same layout as the parameters,
- *   fully overwritten (no zeroing needed). status: as for gsfit_render_fwd.
+ *   fully overwritten (no zeroing needed). opts, status: as for
+ *   gsfit_render_fwd.
  * Errors: GSFIT_ERR_INVALID_ARG, GSFIT_ERR_CUDA; GSFIT_ERR_TIMEOUT on the
  *   device, through status.
  */
 int gsfit_render_bwd(const gsfit_gaussians* g, const gsfit_proj* proj, const gsfit_camera* cams,
                      int32_t n_views, int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges,
                      const uint32_t* tile_order, const float* bg, const float* T_final, const uint32_t* n_contrib,
-                     const float* dL_drgb, const float* dL_dalpha, float* grad2d, float* grads, int32_t* status,
-                     cudaStream_t stream);
+                     const float* dL_drgb, const float* dL_dalpha, float* grad2d, float* grads,
+                     const gsfit_render_opts* opts, int32_t* status, cudaStream_t stream);
 
 /*
  * gsfit_blend_bwd / gsfit_project_bwd -- the two halves of gsfit_render_bwd,
@@ -321,14 +345,15 @@ int gsfit_render_bwd(const gsfit_gaussians* g, const gsfit_proj* proj, const gsf
  * (u, v, conic, opacity, rgb) into grad2d (which must be zero on entry);
  * gsfit_project_bwd chains them through the projection, sums them over views
  * into `grads` (fully overwritten) and zeroes grad2d again. Arguments as for
- * gsfit_render_bwd (status only for gsfit_blend_bwd). Errors:
+ * gsfit_render_bwd (opts and status only for gsfit_blend_bwd). Errors:
  * GSFIT_ERR_INVALID_ARG, GSFIT_ERR_CUDA; GSFIT_ERR_TIMEOUT on the device,
  * through status.
  */
 int gsfit_blend_bwd(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_views, int32_t n,
                     int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges, const uint32_t* tile_order,
                     const float* bg, const float* T_final, const uint32_t* n_contrib, const float* dL_drgb,
-                    const float* dL_dalpha, float* grad2d, int32_t* status, cudaStream_t stream);
+                    const float* dL_dalpha, float* grad2d, const gsfit_render_opts* opts, int32_t* status,
+                    cudaStream_t stream);
 int gsfit_project_bwd(const gsfit_gaussians* g, const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_views,
                       float* grad2d, float* grads, cudaStream_t stream);
 
@@ -342,7 +367,31 @@ int gsfit_project_bwd(const gsfit_gaussians* g, const gsfit_proj* proj, const gs
  */
 int gsfit_render_count(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_views, int32_t n,
                        int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges, const uint32_t* tile_order,
-                       const uint32_t* n_contrib, unsigned long long* count, cudaStream_t stream);
+                       const uint32_t* n_contrib, unsigned long long* count,
+                       const gsfit_render_opts* opts, cudaStream_t stream);
+
+/*
+ * gsfit_render_autotune -- the batching pattern's tuner: picks the batch
+ * depth of the compositing kernels for one laid-out view batch by measuring
+ * each supported depth (64, 128, 256) on the caller's buffers: `reps`
+ * forward launches and `reps` adjoint launches each, timed with CUDA events on
+ * `stream`. The adjoint accumulates into grad2d, which this call zeroes again
+ * at the end. Unlike the other calls it synchronises the stream (it measures)
+ * and must not be captured in a graph. Writes the options with the smallest
+ * forward + adjoint time to *best (tile = `tile`), and, if times_ms (host) is
+ * not null, the mean times per depth: 2 floats per depth (forward, adjoint),
+ * depths in increasing order. The tile size itself changes the projection
+ * and the binning too; callers compare tile sizes on the whole iteration.
+ * Arguments as for gsfit_render_fwd and gsfit_blend_bwd; tile 8 or 16; reps
+ * >= 1.
+ * Errors: GSFIT_ERR_INVALID_ARG, GSFIT_ERR_CUDA.
+ */
+int gsfit_render_autotune(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_views, int32_t n,
+                          int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges,
+                          const uint32_t* tile_order, const float* bg, float* rgb, float* alpha, float* T_final,
+                          uint32_t* n_contrib, const float* dL_drgb, const float* dL_dalpha, float* grad2d,
+                          int32_t tile, int32_t reps, gsfit_render_opts* best, float* times_ms, int32_t* status,
+                          cudaStream_t stream);
 
 /*
  * gsfit_adam_step -- Adam (Kingma & Ba) with bias correction over all

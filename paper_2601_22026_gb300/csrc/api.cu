@@ -16,7 +16,7 @@ extern "C" const char* gsfit_status_string(int code) {
 
 extern "C" int gsfit_camera_layout(gsfit_camera* cams, int n_views, int tile, int32_t* total_tiles,
                                    int64_t* total_pixels) {
-    if (!cams || n_views < 1 || n_views > GSFIT_MAX_VIEWS || tile != GSFIT_TILE) return GSFIT_ERR_INVALID_ARG;
+    if (!cams || n_views < 1 || n_views > GSFIT_MAX_VIEWS || (tile != 8 && tile != 16)) return GSFIT_ERR_INVALID_ARG;
     long long toff = 0, poff = 0;
     for (int v = 0; v < n_views; ++v) {
         if (cams[v].width < 1 || cams[v].height < 1) return GSFIT_ERR_INVALID_ARG;
@@ -24,6 +24,7 @@ extern "C" int gsfit_camera_layout(gsfit_camera* cams, int n_views, int tile, in
         if (toff > 0x7fffffffll || poff > 0x7fffffffll) return GSFIT_ERR_INVALID_ARG;
         cams[v].tile_offset = (int32_t)toff;
         cams[v].pixel_offset = (int32_t)poff;
+        cams[v].tile = tile;
         toff += tx * ty;
         poff += (long long)cams[v].width * cams[v].height;
     }

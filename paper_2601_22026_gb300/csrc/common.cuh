@@ -49,8 +49,16 @@ __device__ __forceinline__ void load_cameras(gsfit_camera* dst, const gsfit_came
     for (int k = threadIdx.x; k < words; k += blockDim.x) d[k] = s[k];
 }
 
-__device__ __forceinline__ int tiles_x_of(const gsfit_camera& c) { return (c.width + kTile - 1) / kTile; }
-__device__ __forceinline__ int tiles_y_of(const gsfit_camera& c) { return (c.height + kTile - 1) / kTile; }
+// Tile edge of a camera's batch layout: 8 or 16 (16 for any other value).
+__device__ __forceinline__ int tile_of(const gsfit_camera& c) { return c.tile == 8 ? 8 : 16; }
+__device__ __forceinline__ int tiles_x_of(const gsfit_camera& c) {
+    const int B = tile_of(c);
+    return (c.width + B - 1) / B;
+}
+__device__ __forceinline__ int tiles_y_of(const gsfit_camera& c) {
+    const int B = tile_of(c);
+    return (c.height + B - 1) / B;
+}
 
 // Tile rectangle [x0, x1) x [y0, y1) of a splat with centre (u, w) and
 // integer radius r (3DGS): x0 = floor((u - r) / B), x1 = floor(((u + r) + (B -
@@ -60,8 +68,8 @@ struct Rect {
     int x0, y0, x1, y1;
 };
 
-__device__ __forceinline__ Rect tile_rect(float u, float w, float radius, int tiles_x, int tiles_y) {
-    const float Bf = (float)kTile, Bm1 = (float)(kTile - 1);
+__device__ __forceinline__ Rect tile_rect(float u, float w, float radius, int tiles_x, int tiles_y, int B) {
+    const float Bf = (float)B, Bm1 = (float)(B - 1);
     Rect t;
     t.x0 = min(tiles_x, max(0, (int)floorf(__fdiv_rn(__fsub_rn(u, radius), Bf))));
     t.x1 = min(tiles_x, max(0, (int)floorf(__fdiv_rn(__fadd_rn(__fadd_rn(u, radius), Bm1), Bf))));

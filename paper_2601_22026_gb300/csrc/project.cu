@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(256) project_kernel(const float4* __restrict__
         // centre, correctly rounded in a fixed order: (fx * t_x) / t_z + cx
         const float u = __fadd_rn(__fdiv_rn(__fmul_rn(cam.fx, vg.tx), vg.tz), cam.cx);
         const float w = __fadd_rn(__fdiv_rn(__fmul_rn(cam.fy, vg.ty), vg.tz), cam.cy);
-        const Rect rc = tile_rect(u, w, radius, tiles_x_of(cam), tiles_y_of(cam));
+        const Rect rc = tile_rect(u, w, radius, tiles_x_of(cam), tiles_y_of(cam), tile_of(cam));
         const uint32_t nt = (uint32_t)((rc.x1 - rc.x0) * (rc.y1 - rc.y0));
         if (nt == 0u) {
             xyd[r] = make_float4(u, w, vg.tz, 0.f);

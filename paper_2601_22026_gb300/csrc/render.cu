@@ -29,14 +29,21 @@ namespace gsfit {
 
 namespace {
 
-constexpr int kRenderWarps = kTilePixels / 32;       // pixel warps, one pixel per thread
-constexpr int kRenderThreads = kTilePixels + 32;     // + the producer warp
-constexpr int kCountThreads = kTilePixels;
-constexpr int kBatch = kCountThreads;                // records staged per batch (counter)
-constexpr float kCullMargin = 0.02f;         // slack (units of the quadratic form) of the warp cull
+constexpr float kCullMargin = 0.02f;  // slack (units of the quadratic form) of the warp cull
 
-// This thread's pixel: warp w covers the 8 x 4 box at (8 (w mod 2), 4 (w / 2))
-// of the tile, lane l its pixel (l mod 8, l / 8).
+// A CTA composites one TILE x TILE tile (TILE = 8 or 16): one pixel per thread
+// in 8 x 4 warp boxes, plus one producer warp.
+template <int TILE>
+struct TileShape {
+    static_assert(TILE == 8 || TILE == 16, "tile edge 8 or 16");
+    static constexpr int kPixels = TILE * TILE;
+    static constexpr int kWarps = kPixels / 32;     // pixel warps
+    static constexpr int kThreads = kPixels + 32;   // + the producer warp
+    static constexpr int kBoxesX = TILE / 8;        // 8 x 4 boxes across the tile
+};
+
+// This thread's pixel: warp w covers the 8 x 4 box at (8 (w mod B/8),
+// 4 (w div B/8)) of the tile, lane l its pixel (l mod 8, l / 8).
 struct TileCtx {
     int view, px, py;
     bool inside;
@@ -44,6 +51,7 @@ struct TileCtx {
     float box_x0, box_y0;  // first pixel centre of the warp's box
 };
 
+template <int TILE>
 __device__ __forceinline__ TileCtx tile_ctx(const gsfit_camera* cams, int n_views, int t) {
     TileCtx c;
     c.view = view_of_tile(cams, n_views, t);
@@ -52,15 +60,15 @@ __device__ __forceinline__ TileCtx tile_ctx(const gsfit_camera* cams, int n_view
     const int txn = tiles_x_of(cam);
     const int ty = local / txn, tx = local - ty * txn;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int bx = (w & 1) * 8, by = (w >> 1) * 4;
-    c.px = tx * kTile + bx + (lane & 7);
-    c.py = ty * kTile + by + (lane >> 3);
+    const int bx = (w % TileShape<TILE>::kBoxesX) * 8, by = (w / TileShape<TILE>::kBoxesX) * 4;
+    c.px = tx * TILE + bx + (lane & 7);
+    c.py = ty * TILE + by + (lane >> 3);
     c.inside = c.px < cam.width && c.py < cam.height;
     c.plane = (long long)cam.width * cam.height;
     c.pix = (long long)cam.pixel_offset + (long long)c.py * cam.width + c.px;
     c.rgb_base = 3ll * cam.pixel_offset + (long long)c.py * cam.width + c.px;
-    c.box_x0 = (float)(tx * kTile + bx);
-    c.box_y0 = (float)(ty * kTile + by);
+    c.box_x0 = (float)(tx * TILE + bx);
+    c.box_y0 = (float)(ty * TILE + by);
     return c;
 }
 
@@ -99,17 +107,19 @@ __device__ __forceinline__ bool box_reach(float ux, float uy, float4 co, float4 
     return fminf(q1 - 1e-5f * s1, q2 - 1e-5f * s2) <= cp.x;
 }
 
-// One batch of staged records (shared memory), for the diagnostic counter.
+// One batch of N staged records (shared memory), for the diagnostic counter.
+template <int N>
 struct Batch {
-    float2 xy[kBatch];
-    float4 cp[kBatch];
-    float4 co[kBatch];
-    float4 col[kBatch];
-    uint32_t g[kBatch];
+    float2 xy[N];
+    float4 cp[N];
+    float4 co[N];
+    float4 col[N];
+    uint32_t g[N];
 };
 
 // This thread stages list entry idx (if < end) into slot threadIdx.x.
-__device__ __forceinline__ void stage(Batch& S, uint32_t idx, uint32_t end, const uint32_t* __restrict__ vals,
+template <int N>
+__device__ __forceinline__ void stage(Batch<N>& S, uint32_t idx, uint32_t end, const uint32_t* __restrict__ vals,
                                       const float4* __restrict__ xyd, const float4* __restrict__ conic,
                                       const float4* __restrict__ rgb, size_t rec0, int n) {
     const int t = threadIdx.x;
@@ -135,7 +145,8 @@ __device__ __forceinline__ void stage(Batch& S, uint32_t idx, uint32_t end, cons
 // ---------------------------------------------------------------------------
 // Record ring of the compositing kernels. A producer warp gathers the tile's
 // records (by Gaussian index, 16-byte cp.async copies) into kRing slots of
-// kSlot entries and adds each entry's cull parameters; the eight pixel warps
+// SLOT entries (the batch depth: 64, 128 or 256) and adds each entry's cull
+// parameters; the pixel warps
 // consume the slots in order. Slot s has two mbarriers: full[s] (the
 // producer's 32 lanes arrive once the slot is written) and empty[s] (the 256
 // consumer threads arrive once they are done reading it). So a pixel warp
@@ -143,20 +154,29 @@ __device__ __forceinline__ void stage(Batch& S, uint32_t idx, uint32_t end, cons
 // kRing - 1 slots ahead of the slowest. A slot with count 0 ends the list.
 // Every wait is bounded (kWaitCycles, about a second): on expiry the status
 // word gets GSFIT_ERR_TIMEOUT, the warp stops, and later tiles skip their work.
-constexpr int kSlot = 128;
 constexpr int kRing = 4;
 constexpr long long kWaitCycles = 1ll << 31;
 
+template <int SLOT>
 struct Ring {
-    float4 xyd[kRing][kSlot];
-    float4 co[kRing][kSlot];
-    float4 col[kRing][kSlot];
-    float4 cp[kRing][kSlot];
-    uint32_t g[kRing][kSlot];
+    float4 xyd[kRing][SLOT];
+    float4 co[kRing][SLOT];
+    float4 col[kRing][SLOT];
+    float4 cp[kRing][SLOT];
+    uint32_t g[kRing][SLOT];
     int cnt[kRing];
     unsigned long long full[kRing];
     unsigned long long empty[kRing];
 };
+
+// Dynamic shared memory of a compositing CTA: the camera table, then the ring.
+__host__ __device__ constexpr size_t ring_offset(int n_views) {
+    return ((size_t)n_views * sizeof(gsfit_camera) + 127) & ~(size_t)127;
+}
+template <int SLOT>
+__host__ __device__ constexpr size_t render_smem(int n_views) {
+    return ring_offset(n_views) + sizeof(Ring<SLOT>);
+}
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
     return static_cast<unsigned>(__cvta_generic_to_shared(p));
@@ -202,11 +222,12 @@ __device__ __forceinline__ uint32_t load_index(uint32_t idx, uint32_t end, const
     return g < (uint32_t)n ? g : 0xffffffffu;  // out of range only after a failed sort: never blended
 }
 
-__device__ __forceinline__ void ring_init(Ring& R) {
+template <int SLOT>
+__device__ __forceinline__ void ring_init(Ring<SLOT>& R, int pixel_warps) {
     if (threadIdx.x == 0) {
         for (int s = 0; s < kRing; ++s) {
             mbar_init(&R.full[s], 32);
-            mbar_init(&R.empty[s], 32 * kRenderWarps);
+            mbar_init(&R.empty[s], 32 * pixel_warps);
         }
     }
 }
@@ -217,18 +238,19 @@ __device__ __forceinline__ bool timed_out(const int32_t* status) {
 
 // Producer side: fills slot k % kRing with list positions [b0, b0 + cnt)
 // (cnt = 0 publishes the end of the list). Returns false on a timeout.
-__device__ __forceinline__ bool ring_produce(Ring& R, int k, uint32_t b0, int cnt, const uint32_t* __restrict__ vals,
+template <int SLOT>
+__device__ __forceinline__ bool ring_produce(Ring<SLOT>& R, int k, uint32_t b0, int cnt, const uint32_t* __restrict__ vals,
                                              const float4* __restrict__ xyd, const float4* __restrict__ conic,
                                              const float4* __restrict__ rgb, size_t rec0, int n,
                                              int32_t* status) {
     const int s = k % kRing;
     const int lane = threadIdx.x & 31;
     if (k >= kRing && !mbar_wait(&R.empty[s], ((k / kRing) & 1) ^ 1, status)) return false;
-    uint32_t g[kSlot / 32];
+    uint32_t g[SLOT / 32];
 #pragma unroll
-    for (int q = 0; q < kSlot / 32; ++q) g[q] = load_index(b0 + 32 * q + lane, b0 + cnt, vals, n);
+    for (int q = 0; q < SLOT / 32; ++q) g[q] = load_index(b0 + 32 * q + lane, b0 + cnt, vals, n);
 #pragma unroll
-    for (int q = 0; q < kSlot / 32; ++q) {
+    for (int q = 0; q < SLOT / 32; ++q) {
         if (g[q] != 0xffffffffu) {
             const int e = 32 * q + lane;
             const size_t r = rec0 + g[q];
@@ -240,7 +262,7 @@ __device__ __forceinline__ bool ring_produce(Ring& R, int k, uint32_t b0, int cn
     cp_async_commit();
     cp_async_wait_all();
 #pragma unroll
-    for (int q = 0; q < kSlot / 32; ++q) {
+    for (int q = 0; q < SLOT / 32; ++q) {
         const int e = 32 * q + lane;
         R.cp[s][e] = g[q] != 0xffffffffu ? cull_params(R.co[s][e]) : make_float4(-1.f, 0.f, 0.f, 0.f);
         R.g[s][e] = g[q];
@@ -251,14 +273,15 @@ __device__ __forceinline__ bool ring_produce(Ring& R, int k, uint32_t b0, int cn
 }
 
 // This warp's entries of slot s that can blend in its box (list order).
-__device__ __forceinline__ int ring_compact(const Ring& R, int s, int cnt, uint32_t base, uint32_t wmax,
+template <int SLOT>
+__device__ __forceinline__ int ring_compact(const Ring<SLOT>& R, int s, int cnt, uint32_t base, uint32_t wmax,
                                             const TileCtx& c, uint8_t* list) {
     const int lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
     int nw = 0;
     __syncwarp();
 #pragma unroll
-    for (int q = 0; q < kSlot / 32; ++q) {
+    for (int q = 0; q < SLOT / 32; ++q) {
         const int j = 32 * q + lane;
         const bool hit = j < cnt && base + (uint32_t)j < wmax &&
                          box_reach(R.xyd[s][j].x, R.xyd[s][j].y, R.co[s][j], R.cp[s][j], c.box_x0, c.box_y0);
@@ -270,37 +293,50 @@ __device__ __forceinline__ int ring_compact(const Ring& R, int s, int cnt, uint3
     return nw;
 }
 
-__global__ void __launch_bounds__(kRenderThreads) render_fwd_kernel(
+// The cameras must be laid out for this kernel's tile edge; a mismatch is
+// reported as GSFIT_ERR_INVALID_ARG in the status word and the launch does nothing.
+template <int TILE>
+__device__ __forceinline__ bool tile_mismatch(const gsfit_camera* cams, int32_t* status) {
+    if (tile_of(cams[0]) == TILE) return false;
+    if (status && threadIdx.x == 0) atomicExch(status, GSFIT_ERR_INVALID_ARG);
+    return true;
+}
+
+template <int TILE, int SLOT>
+__global__ void __launch_bounds__(TileShape<TILE>::kThreads) render_fwd_kernel(
     const float4* __restrict__ xyd, const float4* __restrict__ conic, const float4* __restrict__ rgb, int n,
     const gsfit_camera* __restrict__ cams_g, int n_views, const uint32_t* __restrict__ vals,
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ tile_order, const float* __restrict__ bg,
     float* __restrict__ out_rgb, float* __restrict__ out_alpha, float* __restrict__ out_T,
     uint32_t* __restrict__ out_nc, int32_t* __restrict__ status) {
-    extern __shared__ gsfit_camera cams[];
-    __shared__ Ring R;
-    __shared__ uint8_t s_list[kRenderWarps][kSlot];
+    constexpr int kWarps = TileShape<TILE>::kWarps;
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    gsfit_camera* cams = reinterpret_cast<gsfit_camera*>(smem_dyn);
+    Ring<SLOT>& R = *reinterpret_cast<Ring<SLOT>*>(smem_dyn + ring_offset(n_views));
+    __shared__ uint8_t s_list[kWarps][SLOT];
     __shared__ int s_done;  // pixel warps whose pixels have all stopped
     load_cameras(cams, cams_g, n_views);
-    ring_init(R);
+    ring_init(R, kWarps);
     if (threadIdx.x == 0) s_done = 0;
     __syncthreads();
+    if (tile_mismatch<TILE>(cams, status)) return;
     const int t = tile_order ? (int)tile_order[blockIdx.x] : (int)blockIdx.x;
     const uint2 range = ranges[t];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool skip = timed_out(status);
 
-    if (w == kRenderWarps) {  // producer
+    if (w == kWarps) {  // producer
         const size_t rec0 = (size_t)view_of_tile(cams, n_views, t) * n;
         for (int k = 0;; ++k) {
-            const uint32_t b0 = range.x + (uint32_t)k * kSlot;
-            const bool stop = skip || b0 >= range.y || *reinterpret_cast<volatile int*>(&s_done) == kRenderWarps;
-            const int cnt = stop ? 0 : (int)min((uint32_t)kSlot, range.y - b0);
+            const uint32_t b0 = range.x + (uint32_t)k * SLOT;
+            const bool stop = skip || b0 >= range.y || *reinterpret_cast<volatile int*>(&s_done) == kWarps;
+            const int cnt = stop ? 0 : (int)min((uint32_t)SLOT, range.y - b0);
             if (!ring_produce(R, k, b0, cnt, vals, xyd, conic, rgb, rec0, n, status) || stop) break;
         }
         return;
     }
 
-    const TileCtx c = tile_ctx(cams, n_views, t);
+    const TileCtx c = tile_ctx<TILE>(cams, n_views, t);
     const float fx = (float)c.px, fy = (float)c.py;
     float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
     uint32_t last = 0;
@@ -314,7 +350,7 @@ __global__ void __launch_bounds__(kRenderThreads) render_fwd_kernel(
         const int cnt = R.cnt[s];
         if (cnt == 0) break;
         if (!wdone) {
-            const uint32_t base = (uint32_t)k * kSlot;
+            const uint32_t base = (uint32_t)k * SLOT;
             const int nw = ring_compact(R, s, cnt, base, 0xffffffffu, c, s_list[w]);
             for (int i = 0; i < nw; ++i) {
                 const int j = s_list[w][i];
@@ -452,21 +488,25 @@ __device__ __forceinline__ bool pix_bwd_step(PixBwd& q, uint32_t pos, float4 co,
     return true;
 }
 
-__global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(
+template <int TILE, int SLOT>
+__global__ void __launch_bounds__(TileShape<TILE>::kThreads) render_bwd_kernel(
     const float4* __restrict__ xyd, const float4* __restrict__ conic, const float4* __restrict__ rgb, int n,
     const gsfit_camera* __restrict__ cams_g, int n_views, const uint32_t* __restrict__ vals,
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ tile_order, const float* __restrict__ bg,
     const float* __restrict__ T_final,
     const uint32_t* __restrict__ n_contrib, const float* __restrict__ dL_drgb, const float* __restrict__ dL_dalpha,
     float* __restrict__ grad2d, int32_t* __restrict__ status) {
-    extern __shared__ gsfit_camera cams[];
-    __shared__ Ring R;
-    __shared__ uint8_t s_list[kRenderWarps][kSlot];
+    constexpr int kWarps = TileShape<TILE>::kWarps;
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    gsfit_camera* cams = reinterpret_cast<gsfit_camera*>(smem_dyn);
+    Ring<SLOT>& R = *reinterpret_cast<Ring<SLOT>*>(smem_dyn + ring_offset(n_views));
+    __shared__ uint8_t s_list[kWarps][SLOT];
     __shared__ uint32_t s_max;
     load_cameras(cams, cams_g, n_views);
-    ring_init(R);
+    ring_init(R, kWarps);
     if (threadIdx.x == 0) s_max = 0u;
     __syncthreads();
+    if (tile_mismatch<TILE>(cams, status)) return;
     const int t = tile_order ? (int)tile_order[blockIdx.x] : (int)blockIdx.x;
     const uint2 range = ranges[t];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -476,8 +516,8 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(
     PixBwd q;
     TileCtx c;
     uint32_t wmax = 0;
-    if (w < kRenderWarps) {
-        c = tile_ctx(cams, n_views, t);
+    if (w < kWarps) {
+        c = tile_ctx<TILE>(cams, n_views, t);
         q.T = 1.f; q.last = 0; q.dC0 = q.dC1 = q.dC2 = q.dA = 0.f;
         if (c.inside) {
             q.T = T_final[c.pix];
@@ -497,15 +537,15 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(
     __syncthreads();
     const uint32_t len = skip ? 0u : min(s_max, range.y - range.x);
 
-    // slots walk the list backwards: slot k holds positions [b1 - kSlot, b1)
-    // (clipped at the list start), b1 = len - k kSlot, relative to range.x
-    if (w == kRenderWarps) {  // producer
+    // slots walk the list backwards: slot k holds positions [b1 - SLOT, b1)
+    // (clipped at the list start), b1 = len - k SLOT, relative to range.x
+    if (w == kWarps) {  // producer
         const size_t rec0 = (size_t)view_of_tile(cams, n_views, t) * n;
         for (int k = 0;; ++k) {
-            const uint32_t done_n = (uint32_t)k * kSlot;
+            const uint32_t done_n = (uint32_t)k * SLOT;
             const bool stop = done_n >= len;
             const uint32_t b1 = stop ? 0u : len - done_n;
-            const uint32_t b0 = b1 > (uint32_t)kSlot ? b1 - kSlot : 0u;
+            const uint32_t b0 = b1 > (uint32_t)SLOT ? b1 - SLOT : 0u;
             const int cnt = stop ? 0 : (int)(b1 - b0);
             if (!ring_produce(R, k, range.x + b0, cnt, vals, xyd, conic, rgb, rec0, n, status) || stop) break;
         }
@@ -523,7 +563,7 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(
         if (!__all_sync(0xffffffffu, mbar_wait(&R.full[s], (k / kRing) & 1, status))) break;
         const int cnt = R.cnt[s];
         if (cnt == 0) break;
-        const uint32_t b1 = len - (uint32_t)k * kSlot;
+        const uint32_t b1 = len - (uint32_t)k * SLOT;
         const uint32_t base = b1 - (uint32_t)cnt;  // list position of entry 0
         if (base < wmax) {
             const int nw = ring_compact(R, s, cnt, base, wmax, c, s_list[w]);
@@ -545,17 +585,19 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(
 
 // Diagnostic: blended pairs, with the forward's skip rules, up to each
 // pixel's contributor count (one pixel per thread, batches as above, no cull).
-__global__ void __launch_bounds__(kCountThreads) render_count_kernel(
+template <int TILE>
+__global__ void __launch_bounds__(TILE * TILE) render_count_kernel(
     const float4* __restrict__ xyd, const float4* __restrict__ conic, const float4* __restrict__ rgb, int n,
     const gsfit_camera* __restrict__ cams_g, int n_views, const uint32_t* __restrict__ vals,
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ tile_order, const uint32_t* __restrict__ n_contrib,
     unsigned long long* __restrict__ count) {
     extern __shared__ gsfit_camera cams[];
-    __shared__ Batch S;
+    constexpr int kBatch = TILE * TILE;
+    __shared__ Batch<kBatch> S;
     load_cameras(cams, cams_g, n_views);
     __syncthreads();
     const int t = tile_order ? (int)tile_order[blockIdx.x] : (int)blockIdx.x;
-    const TileCtx c = tile_ctx(cams, n_views, t);
+    const TileCtx c = tile_ctx<TILE>(cams, n_views, t);
     const uint2 range = ranges[t];
     const size_t rec0 = (size_t)c.view * n;
     const uint32_t last = c.inside ? n_contrib[c.pix] : 0u;
@@ -588,59 +630,173 @@ int project_bwd(const gsfit_gaussians* g, const gsfit_proj* proj, const gsfit_ca
 using namespace gsfit;
 
 namespace {
-// The camera table (up to GSFIT_MAX_VIEWS x 128 bytes) is dynamic shared
-// memory on top of the static ring: opt in to the larger size once per device.
-int ensure_render_smem() {
-    static bool done[64] = {false};
+
+struct RenderCfg {
+    int tile, batch;
+};
+
+// Options -> a supported (tile, batch); false for unsupported values.
+bool resolve(const gsfit_render_opts* o, RenderCfg& c) {
+    c.tile = (o && o->tile) ? o->tile : GSFIT_TILE;
+    c.batch = (o && o->batch) ? o->batch : 128;
+    return (c.tile == 8 || c.tile == 16) && (c.batch == 64 || c.batch == 128 || c.batch == 256);
+}
+
+struct FwdArgs {
+    const float4 *xyd, *conic, *rgb;
+    int n;
+    const gsfit_camera* cams;
+    int n_views;
+    const uint32_t* vals;
+    const uint2* ranges;
+    const uint32_t* tile_order;
+    const float* bg;
+    float *out_rgb, *out_alpha, *out_T;
+    uint32_t* out_nc;
+    int32_t* status;
+};
+
+struct BwdArgs {
+    const float4 *xyd, *conic, *rgb;
+    int n;
+    const gsfit_camera* cams;
+    int n_views;
+    const uint32_t* vals;
+    const uint2* ranges;
+    const uint32_t* tile_order;
+    const float *bg, *T_final;
+    const uint32_t* n_contrib;
+    const float *dL_drgb, *dL_dalpha;
+    float* grad2d;
+    int32_t* status;
+};
+
+// The ring and the camera table (up to GSFIT_MAX_VIEWS x 128 bytes) are
+// dynamic shared memory: opt each kernel in to its largest size once per device.
+template <typename K>
+int opt_in(K kernel, size_t bytes, bool* done) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return GSFIT_ERR_CUDA;
     if (!done[dev]) {
-        const int bytes = (int)(sizeof(gsfit_camera) * GSFIT_MAX_VIEWS);
-        if (cudaFuncSetAttribute(render_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) !=
-                cudaSuccess ||
-            cudaFuncSetAttribute(render_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) !=
-                cudaSuccess)
+        if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
             return GSFIT_ERR_CUDA;
         done[dev] = true;
     }
     return GSFIT_OK;
 }
+
+template <int TILE, int SLOT>
+int launch_fwd(const FwdArgs& a, int total_tiles, cudaStream_t s) {
+    static bool done[64] = {false};
+    const int rc = opt_in(render_fwd_kernel<TILE, SLOT>, render_smem<SLOT>(GSFIT_MAX_VIEWS), done);
+    if (rc != GSFIT_OK) return rc;
+    render_fwd_kernel<TILE, SLOT><<<total_tiles, TileShape<TILE>::kThreads, render_smem<SLOT>(a.n_views), s>>>(
+        a.xyd, a.conic, a.rgb, a.n, a.cams, a.n_views, a.vals, a.ranges, a.tile_order, a.bg, a.out_rgb, a.out_alpha,
+        a.out_T, a.out_nc, a.status);
+    GSFIT_LAUNCH_CHECK();
+    return GSFIT_OK;
+}
+
+template <int TILE, int SLOT>
+int launch_bwd(const BwdArgs& a, int total_tiles, cudaStream_t s) {
+    static bool done[64] = {false};
+    const int rc = opt_in(render_bwd_kernel<TILE, SLOT>, render_smem<SLOT>(GSFIT_MAX_VIEWS), done);
+    if (rc != GSFIT_OK) return rc;
+    render_bwd_kernel<TILE, SLOT><<<total_tiles, TileShape<TILE>::kThreads, render_smem<SLOT>(a.n_views), s>>>(
+        a.xyd, a.conic, a.rgb, a.n, a.cams, a.n_views, a.vals, a.ranges, a.tile_order, a.bg, a.T_final, a.n_contrib,
+        a.dL_drgb, a.dL_dalpha, a.grad2d, a.status);
+    GSFIT_LAUNCH_CHECK();
+    return GSFIT_OK;
+}
+
+template <int TILE>
+int dispatch_fwd(const FwdArgs& a, int batch, int total_tiles, cudaStream_t s) {
+    switch (batch) {
+        case 64: return launch_fwd<TILE, 64>(a, total_tiles, s);
+        case 256: return launch_fwd<TILE, 256>(a, total_tiles, s);
+        default: return launch_fwd<TILE, 128>(a, total_tiles, s);
+    }
+}
+
+template <int TILE>
+int dispatch_bwd(const BwdArgs& a, int batch, int total_tiles, cudaStream_t s) {
+    switch (batch) {
+        case 64: return launch_bwd<TILE, 64>(a, total_tiles, s);
+        case 256: return launch_bwd<TILE, 256>(a, total_tiles, s);
+        default: return launch_bwd<TILE, 128>(a, total_tiles, s);
+    }
+}
+
+int run_fwd(const FwdArgs& a, const RenderCfg& c, int total_tiles, cudaStream_t s) {
+    return c.tile == 8 ? dispatch_fwd<8>(a, c.batch, total_tiles, s) : dispatch_fwd<16>(a, c.batch, total_tiles, s);
+}
+
+int run_bwd(const BwdArgs& a, const RenderCfg& c, int total_tiles, cudaStream_t s) {
+    return c.tile == 8 ? dispatch_bwd<8>(a, c.batch, total_tiles, s) : dispatch_bwd<16>(a, c.batch, total_tiles, s);
+}
+
+FwdArgs fwd_args(const gsfit_proj* proj, const gsfit_camera* cams, int n_views, int n, const uint32_t* vals,
+                 const uint32_t* ranges, const uint32_t* tile_order, const float* bg, float* rgb, float* alpha,
+                 float* T_final, uint32_t* n_contrib, int32_t* status) {
+    return FwdArgs{reinterpret_cast<const float4*>(proj->xyd), reinterpret_cast<const float4*>(proj->conic),
+                   reinterpret_cast<const float4*>(proj->rgb), n, cams, n_views, vals,
+                   reinterpret_cast<const uint2*>(ranges), tile_order, bg, rgb, alpha, T_final, n_contrib, status};
+}
+
+BwdArgs bwd_args(const gsfit_proj* proj, const gsfit_camera* cams, int n_views, int n, const uint32_t* vals,
+                 const uint32_t* ranges, const uint32_t* tile_order, const float* bg, const float* T_final,
+                 const uint32_t* n_contrib, const float* dL_drgb, const float* dL_dalpha, float* grad2d,
+                 int32_t* status) {
+    return BwdArgs{reinterpret_cast<const float4*>(proj->xyd), reinterpret_cast<const float4*>(proj->conic),
+                   reinterpret_cast<const float4*>(proj->rgb), n, cams, n_views, vals,
+                   reinterpret_cast<const uint2*>(ranges), tile_order, bg, T_final, n_contrib, dL_drgb, dL_dalpha,
+                   grad2d, status};
+}
+
+bool fwd_ok(const gsfit_proj* proj, const gsfit_camera* cams, int n_views, int n, int total_tiles,
+            const uint32_t* vals, const uint32_t* ranges, const float* bg, const float* rgb, const float* alpha,
+            const float* T_final, const uint32_t* n_contrib) {
+    return valid_proj(proj) && cams && n_views >= 1 && n_views <= GSFIT_MAX_VIEWS && n >= 1 && total_tiles >= 1 &&
+           vals && ranges && bg && rgb && alpha && T_final && n_contrib;
+}
+
+bool bwd_ok(const gsfit_proj* proj, const gsfit_camera* cams, int n_views, int n, int total_tiles,
+            const uint32_t* vals, const uint32_t* ranges, const float* bg, const float* T_final,
+            const uint32_t* n_contrib, const float* dL_drgb, const float* dL_dalpha, const float* grad2d) {
+    return valid_proj(proj) && cams && n_views >= 1 && n_views <= GSFIT_MAX_VIEWS && n >= 1 && total_tiles >= 1 &&
+           vals && ranges && bg && T_final && n_contrib && dL_drgb && dL_dalpha && grad2d &&
+           (reinterpret_cast<uintptr_t>(grad2d) % 16) == 0;
+}
+
 }  // namespace
 
 extern "C" int gsfit_render_fwd(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_views, int32_t n,
                                 int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges,
                                 const uint32_t* tile_order, const float* bg, float* rgb, float* alpha,
-                                float* T_final, uint32_t* n_contrib, int32_t* status, cudaStream_t stream) {
-    if (!valid_proj(proj) || !cams || n_views < 1 || n_views > GSFIT_MAX_VIEWS || n < 1 || total_tiles < 1 ||
-        !vals || !ranges || !bg || !rgb || !alpha || !T_final || !n_contrib)
+                                float* T_final, uint32_t* n_contrib, const gsfit_render_opts* opts, int32_t* status,
+                                cudaStream_t stream) {
+    RenderCfg c;
+    if (!fwd_ok(proj, cams, n_views, n, total_tiles, vals, ranges, bg, rgb, alpha, T_final, n_contrib) ||
+        !resolve(opts, c))
         return GSFIT_ERR_INVALID_ARG;
-    const int rc = ensure_render_smem();
-    if (rc != GSFIT_OK) return rc;
-    render_fwd_kernel<<<total_tiles, kRenderThreads, sizeof(gsfit_camera) * n_views, stream>>>(
-        reinterpret_cast<const float4*>(proj->xyd), reinterpret_cast<const float4*>(proj->conic),
-        reinterpret_cast<const float4*>(proj->rgb), n, cams, n_views, vals, reinterpret_cast<const uint2*>(ranges),
-        tile_order, bg, rgb, alpha, T_final, n_contrib, status);
-    GSFIT_LAUNCH_CHECK();
-    return GSFIT_OK;
+    return run_fwd(fwd_args(proj, cams, n_views, n, vals, ranges, tile_order, bg, rgb, alpha, T_final, n_contrib,
+                            status),
+                   c, total_tiles, stream);
 }
 
 extern "C" int gsfit_blend_bwd(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_views, int32_t n,
                                int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges,
                                const uint32_t* tile_order, const float* bg, const float* T_final,
                                const uint32_t* n_contrib, const float* dL_drgb, const float* dL_dalpha, float* grad2d,
-                               int32_t* status, cudaStream_t stream) {
-    if (!valid_proj(proj) || !cams || n_views < 1 || n_views > GSFIT_MAX_VIEWS || n < 1 || total_tiles < 1 ||
-        !vals || !ranges || !bg || !T_final || !n_contrib || !dL_drgb || !dL_dalpha || !grad2d ||
-        (reinterpret_cast<uintptr_t>(grad2d) % 16) != 0)
+                               const gsfit_render_opts* opts, int32_t* status, cudaStream_t stream) {
+    RenderCfg c;
+    if (!bwd_ok(proj, cams, n_views, n, total_tiles, vals, ranges, bg, T_final, n_contrib, dL_drgb, dL_dalpha,
+                grad2d) ||
+        !resolve(opts, c))
         return GSFIT_ERR_INVALID_ARG;
-    const int rc = ensure_render_smem();
-    if (rc != GSFIT_OK) return rc;
-    render_bwd_kernel<<<total_tiles, kRenderThreads, sizeof(gsfit_camera) * n_views, stream>>>(
-        reinterpret_cast<const float4*>(proj->xyd), reinterpret_cast<const float4*>(proj->conic),
-        reinterpret_cast<const float4*>(proj->rgb), n, cams, n_views, vals, reinterpret_cast<const uint2*>(ranges),
-        tile_order, bg, T_final, n_contrib, dL_drgb, dL_dalpha, grad2d, status);
-    GSFIT_LAUNCH_CHECK();
-    return GSFIT_OK;
+    return run_bwd(bwd_args(proj, cams, n_views, n, vals, ranges, tile_order, bg, T_final, n_contrib, dL_drgb,
+                            dL_dalpha, grad2d, status),
+                   c, total_tiles, stream);
 }
 
 extern "C" int gsfit_project_bwd(const gsfit_gaussians* g, const gsfit_proj* proj, const gsfit_camera* cams,
@@ -655,10 +811,10 @@ extern "C" int gsfit_render_bwd(const gsfit_gaussians* g, const gsfit_proj* proj
                                 int32_t n_views, int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges,
                                 const uint32_t* tile_order, const float* bg, const float* T_final,
                                 const uint32_t* n_contrib, const float* dL_drgb, const float* dL_dalpha, float* grad2d,
-                                float* grads, int32_t* status, cudaStream_t stream) {
+                                float* grads, const gsfit_render_opts* opts, int32_t* status, cudaStream_t stream) {
     if (!valid_gaussians(g)) return GSFIT_ERR_INVALID_ARG;
     const int rc = gsfit_blend_bwd(proj, cams, n_views, g->n, total_tiles, vals, ranges, tile_order, bg, T_final,
-                                   n_contrib, dL_drgb, dL_dalpha, grad2d, status, stream);
+                                   n_contrib, dL_drgb, dL_dalpha, grad2d, opts, status, stream);
     if (rc != GSFIT_OK) return rc;
     return gsfit_project_bwd(g, proj, cams, n_views, grad2d, grads, stream);
 }
@@ -666,14 +822,92 @@ extern "C" int gsfit_render_bwd(const gsfit_gaussians* g, const gsfit_proj* proj
 extern "C" int gsfit_render_count(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_views, int32_t n,
                                   int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges,
                                   const uint32_t* tile_order, const uint32_t* n_contrib, unsigned long long* count,
-                                  cudaStream_t stream) {
+                                  const gsfit_render_opts* opts, cudaStream_t stream) {
+    RenderCfg c;
     if (!valid_proj(proj) || !cams || n_views < 1 || n_views > GSFIT_MAX_VIEWS || n < 1 || total_tiles < 1 ||
-        !vals || !ranges || !n_contrib || !count)
+        !vals || !ranges || !n_contrib || !count || !resolve(opts, c))
         return GSFIT_ERR_INVALID_ARG;
-    render_count_kernel<<<total_tiles, kCountThreads, sizeof(gsfit_camera) * n_views, stream>>>(
-        reinterpret_cast<const float4*>(proj->xyd), reinterpret_cast<const float4*>(proj->conic),
-        reinterpret_cast<const float4*>(proj->rgb), n, cams, n_views, vals, reinterpret_cast<const uint2*>(ranges),
-        tile_order, n_contrib, count);
+    const float4* xyd = reinterpret_cast<const float4*>(proj->xyd);
+    const float4* conic = reinterpret_cast<const float4*>(proj->conic);
+    const float4* rgb = reinterpret_cast<const float4*>(proj->rgb);
+    const uint2* rg = reinterpret_cast<const uint2*>(ranges);
+    const size_t smem = sizeof(gsfit_camera) * n_views;
+    if (c.tile == 8)
+        render_count_kernel<8><<<total_tiles, 64, smem, stream>>>(xyd, conic, rgb, n, cams, n_views, vals, rg,
+                                                                 tile_order, n_contrib, count);
+    else
+        render_count_kernel<16><<<total_tiles, 256, smem, stream>>>(xyd, conic, rgb, n, cams, n_views, vals, rg,
+                                                                   tile_order, n_contrib, count);
     GSFIT_LAUNCH_CHECK();
+    return GSFIT_OK;
+}
+
+namespace {
+struct Events {
+    cudaEvent_t e[3] = {nullptr, nullptr, nullptr};
+    bool ok = true;
+    Events() {
+        for (auto& x : e) ok = ok && cudaEventCreate(&x) == cudaSuccess;
+    }
+    ~Events() {
+        for (auto& x : e)
+            if (x) cudaEventDestroy(x);
+    }
+};
+}  // namespace
+
+extern "C" int gsfit_render_autotune(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_views, int32_t n,
+                                     int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges,
+                                     const uint32_t* tile_order, const float* bg, float* rgb, float* alpha,
+                                     float* T_final, uint32_t* n_contrib, const float* dL_drgb,
+                                     const float* dL_dalpha, float* grad2d, int32_t tile, int32_t reps,
+                                     gsfit_render_opts* best, float* times_ms, int32_t* status,
+                                     cudaStream_t stream) {
+    if (!fwd_ok(proj, cams, n_views, n, total_tiles, vals, ranges, bg, rgb, alpha, T_final, n_contrib) ||
+        !bwd_ok(proj, cams, n_views, n, total_tiles, vals, ranges, bg, T_final, n_contrib, dL_drgb, dL_dalpha,
+                grad2d) ||
+        (tile != 8 && tile != 16) || reps < 1 || !best)
+        return GSFIT_ERR_INVALID_ARG;
+    const FwdArgs fa =
+        fwd_args(proj, cams, n_views, n, vals, ranges, tile_order, bg, rgb, alpha, T_final, n_contrib, status);
+    const BwdArgs ba = bwd_args(proj, cams, n_views, n, vals, ranges, tile_order, bg, T_final, n_contrib, dL_drgb,
+                                dL_dalpha, grad2d, status);
+    Events ev;
+    if (!ev.ok) return GSFIT_ERR_CUDA;
+    const int depths[3] = {64, 128, 256};
+    float best_ms = 3.4e38f;
+    int best_depth = 128;
+    for (int d = 0; d < 3; ++d) {
+        const RenderCfg c{tile, depths[d]};
+        int rc = run_fwd(fa, c, total_tiles, stream);  // warm-up (and shared-memory opt-in)
+        if (rc == GSFIT_OK) rc = run_bwd(ba, c, total_tiles, stream);
+        if (rc != GSFIT_OK) return rc;
+        GSFIT_CUDA_CHECK(cudaEventRecord(ev.e[0], stream));
+        for (int r = 0; r < reps && rc == GSFIT_OK; ++r) rc = run_fwd(fa, c, total_tiles, stream);
+        GSFIT_CUDA_CHECK(cudaEventRecord(ev.e[1], stream));
+        for (int r = 0; r < reps && rc == GSFIT_OK; ++r) rc = run_bwd(ba, c, total_tiles, stream);
+        GSFIT_CUDA_CHECK(cudaEventRecord(ev.e[2], stream));
+        GSFIT_CUDA_CHECK(cudaEventSynchronize(ev.e[2]));
+        if (rc != GSFIT_OK) return rc;
+        float tf = 0.f, tb = 0.f;
+        GSFIT_CUDA_CHECK(cudaEventElapsedTime(&tf, ev.e[0], ev.e[1]));
+        GSFIT_CUDA_CHECK(cudaEventElapsedTime(&tb, ev.e[1], ev.e[2]));
+        tf /= (float)reps;
+        tb /= (float)reps;
+        if (times_ms) {
+            times_ms[2 * d] = tf;
+            times_ms[2 * d + 1] = tb;
+        }
+        if (tf + tb < best_ms) {
+            best_ms = tf + tb;
+            best_depth = depths[d];
+        }
+    }
+    // the adjoint launches accumulated into grad2d: leave it zero, as the calls require
+    GSFIT_CUDA_CHECK(cudaMemsetAsync(grad2d, 0, sizeof(float) * 16 * (size_t)n_views * (size_t)n, stream));
+    GSFIT_CUDA_CHECK(cudaStreamSynchronize(stream));
+    best->tile = tile;
+    best->batch = best_depth;
+    best->reserved[0] = best->reserved[1] = 0;
     return GSFIT_OK;
 }

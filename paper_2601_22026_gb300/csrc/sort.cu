@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(kScanThreads) emit_kernel(const unsigned long 
             const gsfit_camera& cam = cams[v];
             const float4 p = xyd[r];
             const int txn = tiles_x_of(cam);
-            const Rect rc = tile_rect(p.x, p.y, p.w, txn, tiles_y_of(cam));
+            const Rect rc = tile_rect(p.x, p.y, p.w, txn, tiles_y_of(cam), tile_of(cam));
             const unsigned long long depth = rk & 0xffffffffull;
             uint32_t o = offset + ex;
             for (int ty = rc.y0; ty < rc.y1; ++ty)

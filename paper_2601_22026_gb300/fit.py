@@ -32,11 +32,16 @@ class FitState:
 
     def __init__(self, gaussians: dict, cams: dict, *, target_rgb=None, target_alpha=None, bg=None,
                  capacity: int | None = None, lr: dict | None = None, eps: float = 1e-15,
-                 lam: float = 0.2, features: str = "f32", device: str = "cuda"):
+                 lam: float = 0.2, features: str = "f32", tile: int = 16, batch: int = 128,
+                 device: str = "cuda"):
         """features: "f32", or "f16" / "bf16" for the mixed-precision form
         (16-bit copy of rotation, scales and SH read by the projection, kept
-        current by Adam; float32 master parameters and moments)."""
+        current by Adam; float32 master parameters and moments).
+        tile (8 or 16) and batch (64, 128, 256 records per shared-memory
+        slot): the compositing options; see tune.py for choosing them."""
         self.device = device
+        self.tile = int(tile)
+        self.opts = G.RenderOpts(self.tile, int(batch))
         self.n = int(gaussians["means"].shape[0])
         self.sh_degree = int(round(gaussians["sh"].shape[1] ** 0.5)) - 1
         self.n_planes = G.num_planes(self.sh_degree)
@@ -67,7 +72,7 @@ class FitState:
 
     # -- view batch -----------------------------------------------------
     def set_cameras(self, cams: dict, bg=None) -> None:
-        self.table = G.camera_table(cams)
+        self.table = G.camera_table(cams, self.tile)
         self.V = self.table.n_views
         self.T = self.table.total_tiles
         self.P = self.table.total_pixels
@@ -138,7 +143,8 @@ class FitState:
 
     def render_fwd(self, stream=None):
         G.gsfit_render_fwd(self.proj, self.cams_dev, self.V, self.n, self.T, self.vals, self.ranges, self.bg,
-                           self.rgb, self.alpha, self.T_final, self.n_contrib, stream, self.tile_order, self.status)
+                           self.rgb, self.alpha, self.T_final, self.n_contrib, stream, self.tile_order, self.status,
+                           self.opts)
 
     def loss(self, stream=None):
         G.gsfit_loss(self.cams_dev, self.V, self.rgb, self.alpha, self.target_rgb, self.target_alpha, self.bg,
@@ -148,12 +154,12 @@ class FitState:
         G.gsfit_render_bwd(self.params, self.n, self.sh_degree, self.proj, self.cams_dev, self.V, self.T,
                            self.vals, self.ranges, self.bg, self.T_final, self.n_contrib, self.dL_drgb,
                            self.dL_dalpha, self.grad2d, self.grads, stream, self.tile_order, self.status,
-                           self.features, self.feature_dtype)
+                           self.features, self.feature_dtype, self.opts)
 
     def blend_bwd(self, stream=None):
         G.gsfit_blend_bwd(self.proj, self.cams_dev, self.V, self.n, self.T, self.vals, self.ranges, self.bg,
                           self.T_final, self.n_contrib, self.dL_drgb, self.dL_dalpha, self.grad2d, stream,
-                          self.tile_order, self.status)
+                          self.tile_order, self.status, self.opts)
 
     def project_bwd(self, stream=None):
         G.gsfit_project_bwd(self.params, self.n, self.sh_degree, self.proj, self.cams_dev, self.V, self.grad2d,
@@ -163,8 +169,23 @@ class FitState:
         """Blended (pixel, Gaussian) pairs of the last forward pass (syncs)."""
         cnt = torch.zeros(1, dtype=torch.int64, device=self.device)
         G.gsfit_render_count(self.proj, self.cams_dev, self.V, self.n, self.T, self.vals, self.ranges,
-                             self.n_contrib, cnt, None, self.tile_order)
+                             self.n_contrib, cnt, None, self.tile_order, self.opts)
         return int(cnt.item())
+
+    def tune_batch(self, reps: int = 3) -> dict:
+        """Measures the compositing batch depths on this state's current view
+        batch (one forward and loss first, for realistic lists and
+        cotangents), keeps the fastest in self.opts and drops any captured
+        graph. Returns {depth: (forward ms, adjoint ms)}; synchronises."""
+        self.forward()
+        self.loss()
+        best, times = G.gsfit_render_autotune(self.proj, self.cams_dev, self.V, self.n, self.T, self.vals,
+                                              self.ranges, self.tile_order, self.bg, self.rgb, self.alpha,
+                                              self.T_final, self.n_contrib, self.dL_drgb, self.dL_dalpha,
+                                              self.grad2d, self.tile, reps, None, self.status)
+        self.opts = best
+        self.graph = None
+        return times
 
     def adam(self, stream=None):
         G.gsfit_adam_step(self.params, self.grads, self.m, self.v, self.n, self.n_planes, self.lr, 0.9, 0.999,

@@ -48,7 +48,12 @@ class Proj(ctypes.Structure):
 class Camera(ctypes.Structure):
     _fields_ = [("viewmat", _f32 * 12), ("campos", _f32 * 3), ("fx", _f32), ("fy", _f32), ("cx", _f32),
                 ("cy", _f32), ("near_plane", _f32), ("width", _i32), ("height", _i32), ("tile_offset", _i32),
-                ("pixel_offset", _i32), ("reserved", _i32 * 8)]
+                ("pixel_offset", _i32), ("tile", _i32), ("reserved", _i32 * 7)]
+
+
+class RenderOpts(ctypes.Structure):
+    """gsfit_render_opts: tile edge (8 or 16) and batch depth (64, 128, 256)."""
+    _fields_ = [("tile", _i32), ("batch", _i32), ("reserved", _i32 * 2)]
 
 
 assert ctypes.sizeof(Camera) == 128
@@ -62,14 +67,17 @@ SIGNATURES = {
     "gsfit_project": (ctypes.c_int, [_P, _P, _i32, _P, _P]),
     "gsfit_bin_sort_workspace_size": (_size, [_i64, _i64, _i32]),
     "gsfit_bin_sort": (ctypes.c_int, [_P, _P, _i32, _i32, _i32, _P, _size, _P, _P, _i64, _P, _P, _P, _P, _P]),
-    "gsfit_render_fwd": (ctypes.c_int, [_P, _P, _i32, _i32, _i32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "gsfit_render_fwd": (ctypes.c_int, [_P, _P, _i32, _i32, _i32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "gsfit_loss_workspace_size": (_size, [_i32]),
     "gsfit_loss": (ctypes.c_int, [_P, _i32, _P, _P, _P, _P, _P, _f32, _P, _P, _P, _P, _size, _P]),
     "gsfit_loss_noalloc": (ctypes.c_int, [_P, _i32, _P, _P, _P, _P, _P, _f32, _P, _P, _P, _P]),
-    "gsfit_render_bwd": (ctypes.c_int, [_P, _P, _P, _i32, _i32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
-    "gsfit_blend_bwd": (ctypes.c_int, [_P, _P, _i32, _i32, _i32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "gsfit_render_bwd": (ctypes.c_int, [_P, _P, _P, _i32, _i32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
+                                        _P]),
+    "gsfit_blend_bwd": (ctypes.c_int, [_P, _P, _i32, _i32, _i32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "gsfit_project_bwd": (ctypes.c_int, [_P, _P, _P, _i32, _P, _P, _P]),
-    "gsfit_render_count": (ctypes.c_int, [_P, _P, _i32, _i32, _i32, _P, _P, _P, _P, _P, _P]),
+    "gsfit_render_count": (ctypes.c_int, [_P, _P, _i32, _i32, _i32, _P, _P, _P, _P, _P, _P, _P]),
+    "gsfit_render_autotune": (ctypes.c_int, [_P, _P, _i32, _i32, _i32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
+                                             _i32, _i32, _P, _P, _P, _P]),
     "gsfit_adam_step": (ctypes.c_int, [_P, _P, _P, _P, _i32, _i32, _P, _f32, _f32, _f32, _P, _P, _i32, _P]),
     "gsfit_features_refresh": (ctypes.c_int, [_P, _i32, _i32, _P, _i32, _P]),
 }
@@ -186,8 +194,8 @@ class CameraTable:
         return ctypes.string_at(ctypes.addressof(self.host), ctypes.sizeof(self.host))
 
 
-def camera_table(cams: dict) -> CameraTable:
-    """Scene camera dict -> laid-out gsfit_camera records (host)."""
+def camera_table(cams: dict, tile: int = GSFIT_TILE) -> CameraTable:
+    """Scene camera dict -> gsfit_camera records laid out for tile edge `tile` (host)."""
     V = len(cams["width"])
     arr = (Camera * V)()
     for v in range(V):
@@ -202,7 +210,7 @@ def camera_table(cams: dict) -> CameraTable:
         c.width, c.height = int(cams["width"][v]), int(cams["height"][v])
     tt = ctypes.c_int32()
     tp = ctypes.c_int64()
-    _check(load().gsfit_camera_layout(arr, V, GSFIT_TILE, ctypes.byref(tt), ctypes.byref(tp)), "gsfit_camera_layout")
+    _check(load().gsfit_camera_layout(arr, V, int(tile), ctypes.byref(tt), ctypes.byref(tp)), "gsfit_camera_layout")
     return CameraTable(arr, V, int(tt.value), int(tp.value))
 
 
@@ -258,12 +266,21 @@ def gsfit_bin_sort(proj: ProjBuffers, cams_dev, n_views, n, total_tiles, ws, key
            "gsfit_bin_sort")
 
 
+def _opts(opts):
+    """None, a RenderOpts, or a (tile, batch) pair -> a pointer argument."""
+    if opts is None:
+        return None
+    if not isinstance(opts, RenderOpts):
+        opts = RenderOpts(int(opts[0]), int(opts[1]))
+    return ctypes.byref(opts)
+
+
 def gsfit_render_fwd(proj: ProjBuffers, cams_dev, n_views, n, total_tiles, vals, ranges, bg, rgb, alpha, T_final,
-                     n_contrib, stream=None, tile_order=None, status=None):
+                     n_contrib, stream=None, tile_order=None, status=None, opts=None):
     p = proj.struct()
     _check(load().gsfit_render_fwd(ctypes.byref(p), _ptr(cams_dev), n_views, n, total_tiles, _ptr(vals),
                                    _ptr(ranges), _ptr(tile_order), _ptr(bg), _ptr(rgb), _ptr(alpha), _ptr(T_final),
-                                   _ptr(n_contrib), _ptr(status), _stream(stream)),
+                                   _ptr(n_contrib), _opts(opts), _ptr(status), _stream(stream)),
            "gsfit_render_fwd")
 
 
@@ -293,22 +310,22 @@ def gsfit_loss_noalloc(cams_dev, n_views, rgb, alpha, target_rgb, target_alpha, 
 
 def gsfit_render_bwd(params, n, sh_degree, proj: ProjBuffers, cams_dev, n_views, total_tiles, vals, ranges, bg,
                      T_final, n_contrib, dL_drgb, dL_dalpha, grad2d, grads, stream=None, tile_order=None,
-                     status=None, features=None, feature_dtype=0):
+                     status=None, features=None, feature_dtype=0, opts=None):
     g = gaussians_struct(params, n, sh_degree, features, feature_dtype)
     p = proj.struct()
     _check(load().gsfit_render_bwd(ctypes.byref(g), ctypes.byref(p), _ptr(cams_dev), n_views, total_tiles,
                                    _ptr(vals), _ptr(ranges), _ptr(tile_order), _ptr(bg), _ptr(T_final), _ptr(n_contrib),
-                                   _ptr(dL_drgb), _ptr(dL_dalpha), _ptr(grad2d), _ptr(grads), _ptr(status),
-                                   _stream(stream)),
+                                   _ptr(dL_drgb), _ptr(dL_dalpha), _ptr(grad2d), _ptr(grads), _opts(opts),
+                                   _ptr(status), _stream(stream)),
            "gsfit_render_bwd")
 
 
 def gsfit_blend_bwd(proj: ProjBuffers, cams_dev, n_views, n, total_tiles, vals, ranges, bg, T_final, n_contrib,
-                    dL_drgb, dL_dalpha, grad2d, stream=None, tile_order=None, status=None):
+                    dL_drgb, dL_dalpha, grad2d, stream=None, tile_order=None, status=None, opts=None):
     p = proj.struct()
     _check(load().gsfit_blend_bwd(ctypes.byref(p), _ptr(cams_dev), n_views, n, total_tiles, _ptr(vals), _ptr(ranges),
                                   _ptr(tile_order), _ptr(bg), _ptr(T_final), _ptr(n_contrib), _ptr(dL_drgb), _ptr(dL_dalpha),
-                                  _ptr(grad2d), _ptr(status), _stream(stream)),
+                                  _ptr(grad2d), _opts(opts), _ptr(status), _stream(stream)),
            "gsfit_blend_bwd")
 
 
@@ -322,11 +339,32 @@ def gsfit_project_bwd(params, n, sh_degree, proj: ProjBuffers, cams_dev, n_views
 
 
 def gsfit_render_count(proj: ProjBuffers, cams_dev, n_views, n, total_tiles, vals, ranges, n_contrib, count,
-                       stream=None, tile_order=None):
+                       stream=None, tile_order=None, opts=None):
     p = proj.struct()
     _check(load().gsfit_render_count(ctypes.byref(p), _ptr(cams_dev), n_views, n, total_tiles, _ptr(vals),
-                                     _ptr(ranges), _ptr(tile_order), _ptr(n_contrib), _ptr(count), _stream(stream)),
+                                     _ptr(ranges), _ptr(tile_order), _ptr(n_contrib), _ptr(count), _opts(opts),
+                                     _stream(stream)),
            "gsfit_render_count")
+
+
+BATCH_DEPTHS = (64, 128, 256)  # the depths gsfit_render_autotune measures, in its order
+
+
+def gsfit_render_autotune(proj: ProjBuffers, cams_dev, n_views, n, total_tiles, vals, ranges, tile_order, bg, rgb,
+                          alpha, T_final, n_contrib, dL_drgb, dL_dalpha, grad2d, tile, reps=3, stream=None,
+                          status=None):
+    """Measures every batch depth for this tile edge; returns (best RenderOpts,
+    {depth: (forward ms, adjoint ms)}). Synchronises the stream."""
+    p = proj.struct()
+    best = RenderOpts()
+    times = (ctypes.c_float * (2 * len(BATCH_DEPTHS)))()
+    _check(load().gsfit_render_autotune(ctypes.byref(p), _ptr(cams_dev), n_views, n, total_tiles, _ptr(vals),
+                                        _ptr(ranges), _ptr(tile_order), _ptr(bg), _ptr(rgb), _ptr(alpha),
+                                        _ptr(T_final), _ptr(n_contrib), _ptr(dL_drgb), _ptr(dL_dalpha), _ptr(grad2d),
+                                        int(tile), int(reps), ctypes.byref(best), times, _ptr(status),
+                                        _stream(stream)),
+           "gsfit_render_autotune")
+    return best, {d: (times[2 * k], times[2 * k + 1]) for k, d in enumerate(BATCH_DEPTHS)}
 
 
 def gsfit_adam_step(params, grads, m, v, n, n_planes, lr: np.ndarray, beta1, beta2, eps, step, stream=None,

@@ -122,3 +122,27 @@ def test_feature_storage_arguments_rejected_on_host(lib):
                                None) == G.GSFIT_ERR_INVALID_ARG
     assert lib.gsfit_features_refresh(fake, 10, 4, fake, G.FEATURES["f32"], None) == G.GSFIT_ERR_INVALID_ARG
     assert lib.gsfit_features_refresh(fake, 10, 1, fake, G.FEATURES["f16"], None) == G.GSFIT_ERR_INVALID_ARG
+
+
+def test_camera_layout_tile_edges(lib):
+    cams = scenes.periphery_batch_cameras(7)
+    for tile in (8, 16):
+        table = G.camera_table(cams, tile)
+        assert table.total_tiles == oracle.total_tiles(cams, tile)
+        assert all(table.host[v].tile == tile for v in range(table.n_views))
+    with pytest.raises(RuntimeError):
+        G.camera_table(cams, 12)
+
+
+def test_render_options_rejected_on_host(lib):
+    fake = 256
+    p = G.Proj(fake, fake, fake, fake)
+    for opts in [G.RenderOpts(8, 100), G.RenderOpts(32, 128), G.RenderOpts(12, 64)]:
+        assert lib.gsfit_render_fwd(ctypes.byref(p), fake, 1, 10, 4, fake, fake, None, fake, fake, fake, fake, fake,
+                                    ctypes.byref(opts), None, None) == G.GSFIT_ERR_INVALID_ARG
+        assert lib.gsfit_blend_bwd(ctypes.byref(p), fake, 1, 10, 4, fake, fake, None, fake, fake, fake, fake, fake,
+                                   fake, ctypes.byref(opts), None, None) == G.GSFIT_ERR_INVALID_ARG
+    best = G.RenderOpts()
+    assert lib.gsfit_render_autotune(ctypes.byref(p), fake, 1, 10, 4, fake, fake, None, fake, fake, fake, fake, fake,
+                                     fake, fake, fake, 12, 3, ctypes.byref(best), None, None,
+                                     None) == G.GSFIT_ERR_INVALID_ARG
