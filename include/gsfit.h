@@ -162,6 +162,20 @@ int gsfit_camera_layout(gsfit_camera* cams_host, int n_views, int tile, int32_t*
                         int64_t* total_pixels);
 
 /*
+ * Host helper, view selection for continual refinement (Section 4.2, Eq. 1):
+ * a new view joins the training set only if, for every view i already in
+ * it, ||pos_new - pos_i|| > delta_pos or view_new . view_i < cos(theta_view)
+ * (the paper uses delta_pos = 0.05 and theta_view = 5 degrees). pos: camera
+ * centres, 3 floats each; dir: viewing directions, 3 floats each, normalised
+ * here (a zero direction is invalid). HOST pointers; n_set may be 0 (an
+ * empty set accepts any view).
+ * Returns 1 (novel: add the view), 0 (redundant), GSFIT_ERR_INVALID_ARG for
+ * null pointers with n_set > 0, a zero direction or a negative n_set.
+ */
+int gsfit_view_is_novel(const float* pos_new, const float* dir_new, const float* pos_set, const float* dir_set,
+                        int32_t n_set, float delta_pos, float cos_theta);
+
+/*
  * gsfit_project -- EWA projection with SH colour (3DGS forward projection).
  *   Per (view v, Gaussian i): s = exp(log_scale), q normalised, opacity =
  *   sigmoid(logit), Sigma = R(q) diag(s^2) R(q)^T; t = R_v mu + t_v; culled

@@ -305,3 +305,19 @@ def gaussian_grads(gs: dict, cams: dict, bg: np.ndarray, dL_drgb, dL_dalpha, req
                            _p(np.ascontiguousarray(dL_drgb, dtype=np.float64)),
                            _p(np.ascontiguousarray(dL_dalpha, dtype=np.float64)), r.size, _p(r), _p(out), _p(amb))
     return out, amb.astype(bool)
+
+
+def view_is_novel(pos_new, dir_new, pos_set, dir_set, delta_pos: float = 0.05, theta_deg: float = 5.0) -> bool:
+    """Section 4.2, Eq. 1: a new view is added to the training set only if for
+    every view C_i already in it, ||pos_new - pos_i|| > delta_pos or
+    view_new . view_i < cos(theta_view) (view directions as unit vectors).
+    The definition written out, in float64; an empty set accepts the view."""
+    p = np.asarray(pos_new, np.float64)
+    d = np.asarray(dir_new, np.float64)
+    d = d / np.linalg.norm(d)
+    c = np.cos(np.deg2rad(theta_deg))
+    for pi, di in zip(np.asarray(pos_set, np.float64).reshape(-1, 3), np.asarray(dir_set, np.float64).reshape(-1, 3)):
+        di = di / np.linalg.norm(di)
+        if not (np.linalg.norm(p - pi) > delta_pos or float(d @ di) < c):
+            return False
+    return True

@@ -80,6 +80,7 @@ SIGNATURES = {
                                              _i32, _i32, _P, _P, _P, _P]),
     "gsfit_adam_step": (ctypes.c_int, [_P, _P, _P, _P, _i32, _i32, _P, _f32, _f32, _f32, _P, _P, _i32, _P]),
     "gsfit_features_refresh": (ctypes.c_int, [_P, _i32, _i32, _P, _i32, _P]),
+    "gsfit_view_is_novel": (ctypes.c_int, [_P, _P, _P, _P, _i32, _f32, _f32]),
 }
 
 _lib = None
@@ -381,3 +382,15 @@ def gsfit_features_refresh(params, n, n_planes, features, feature_dtype, stream=
     _check(load().gsfit_features_refresh(_ptr(params), n, n_planes, _ptr(features), int(feature_dtype),
                                          _stream(stream)),
            "gsfit_features_refresh")
+
+
+def gsfit_view_is_novel(pos_new, dir_new, pos_set, dir_set, delta_pos=0.05, theta_deg=5.0) -> bool:
+    """Eq. 1 view selection (host): True if the new view is novel w.r.t. every view of the set."""
+    f = lambda a: np.ascontiguousarray(a, dtype=np.float32).reshape(-1)
+    pn, dn, ps, ds = f(pos_new), f(dir_new), f(pos_set), f(dir_set)
+    n = ps.size // 3
+    rc = load().gsfit_view_is_novel(pn.ctypes.data_as(_P), dn.ctypes.data_as(_P), ps.ctypes.data_as(_P) if n else None,
+                                    ds.ctypes.data_as(_P) if n else None, n, float(delta_pos),
+                                    float(np.cos(np.deg2rad(theta_deg))))
+    _check(min(rc, 0), "gsfit_view_is_novel")
+    return rc == 1
