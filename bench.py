@@ -330,6 +330,91 @@ def mixed_precision_rate(sc, st, bg_table, warmup: int, steps: int, features: st
     return out
 
 
+def refinement_leg(sc, st, iters: int, replace_every: int = 10, n_replace: int = 4, every: int = 25,
+                   features: str = "f16") -> dict:
+    """The continuous-refinement loop of the mixed-precision form (16-bit
+    features): every `replace_every` iterations `n_replace` foveal crops are
+    replaced by newly streamed views that pass Eq. 1 (targets rendered from
+    the target set, the iteration captured again). PSNR on the starting
+    16-view batch (zero background) every `every` iterations; wall time
+    excludes the PSNR evaluations. Beside it the plain float32 single-view
+    form (one view per launch sequence and Adam step, no graph) from the same
+    start, for the same number of 16-view passes; reports when the refinement
+    loop first reaches the PSNR the plain form ends at."""
+    import itertools
+    import torch
+    from paper_2601_22026_gb300 import refine
+    from paper_2601_22026_gb300.fit import FitState, boosted_lr
+    cams = sc["cameras"]
+    V = len(cams["width"])
+    zeros = np.zeros((V, 3), np.float32)
+    tgt = FitState(sc["target_gaussians"], cams, bg=zeros, tile=st.tile, batch=int(st.opts.batch))
+    tgt.forward()
+    t_rgb, t_alpha = tgt.rgb.clone(), tgt.alpha.clone()
+
+    def with_targets(s, rgb, alpha):
+        s.target_rgb.copy_(rgb)
+        s.target_alpha.copy_(alpha)
+        return s
+
+    def run(step_fn, ev, n_blocks):
+        curve = [[0, 0.0, refine.psnr(ev)]]
+        wall = 0.0
+        for _ in range(n_blocks):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            for _ in range(every):
+                step_fn()
+            torch.cuda.synchronize()
+            wall += time.perf_counter() - t
+            curve.append([curve[-1][0] + every, wall, refine.psnr(ev)])
+        return curve
+
+    n_blocks = max(1, iters // every)
+    # refinement loop, mixed precision
+    tr = with_targets(FitState(sc["gaussians"], cams, bg=zeros, lr=boosted_lr(), features=features, tile=st.tile,
+                               batch=int(st.opts.batch)), t_rgb, t_alpha)
+    ev = with_targets(refine.view_state(tr, cams, bg=zeros), t_rgb, t_alpha)
+    stream = (scenes.foveal_crops(0, 1, 10_000 + k) for k in itertools.count())
+    loop = refine.ContinuousRefinement(tr, tgt, cams, stream, scenes.backgrounds(V, 21, n_steps=iters),
+                                       replace_every=replace_every, n_replace=n_replace)
+    curve = run(loop.step, ev, n_blocks)
+    if tr.check_status() != 0:
+        raise RuntimeError("device status set in the refinement leg")
+    out = {"features": features, "iterations": loop.it, "replace_every": replace_every, "n_replace": n_replace,
+           "crops_offered": loop.offered, "crops_accepted": loop.accepted, "training_views": len(loop.views),
+           "wall_s": curve[-1][1], "iters_per_s": loop.it / curve[-1][1],
+           "psnr_db": [[c[0], round(c[1], 4), round(c[2], 3)] for c in curve]}
+    del loop, ev, tr
+    torch.cuda.empty_cache()
+    # plain float32 single-view form from the same start on the fixed batch
+    pl = FitState(sc["gaussians"], cams, bg=zeros, lr=boosted_lr())
+    per_view, off = [], 0
+    for v in range(V):
+        c1 = scenes.camera_subset(cams, [v])
+        P = int(cams["width"][v]) * int(cams["height"][v])
+        s1 = refine.view_state(pl, c1, bg=sc["bg"][v:v + 1])
+        with_targets(s1, t_rgb[3 * off:3 * (off + P)], t_alpha[off:off + P])
+        per_view.append(s1)
+        off += P
+    ev_pl = with_targets(refine.view_state(pl, cams, bg=zeros), t_rgb, t_alpha)
+
+    def plain_pass():
+        for s1 in per_view:
+            s1.step()
+
+    curve_pl = run(plain_pass, ev_pl, n_blocks)
+    target = curve_pl[-1][2]
+    reach = next((c for c in curve if c[2] >= target), None)
+    out["plain_fp32_single_view"] = {"passes": n_blocks * every, "wall_s": curve_pl[-1][1],
+                                     "psnr_db": [[c[0], round(c[1], 4), round(c[2], 3)] for c in curve_pl]}
+    out["time_to_plain_final_psnr"] = None if reach is None else {
+        "iterations": reach[0], "wall_s": reach[1], "speedup_vs_plain": curve_pl[-1][1] / max(reach[1], 1e-9)}
+    del per_view, ev_pl, pl, tgt
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args) -> None:
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -363,6 +448,8 @@ def main() -> None:
     ap.add_argument("--no-plain", action="store_true", help="skip the single-view comparison")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision (16-bit features) leg")
     ap.add_argument("--no-tune", action="store_true", help="default tile 16 / batch 128 instead of the autotuner")
+    ap.add_argument("--refine-iters", type=int, default=300,
+                    help="iterations of the continuous-refinement leg (0 skips it)")
     ap.add_argument("--gaussians", type=int, default=1_000_000,
                     help="smaller sets are for profiling captures only; the metric is quoted at 1M")
     ap.add_argument("--crops", type=int, default=14, help="foveal crops per batch (profiling captures only)")
@@ -505,6 +592,8 @@ def main() -> None:
         if plain is not None:
             mp["speedup_vs_plain_fp32_single_view"] = mp["value"] / plain
         out["mixed_precision"] = mp
+    if rank == 0 and args.refine_iters > 0:
+        out["continuous_refinement"] = refinement_leg(sc, st, args.refine_iters)
     if rank == 0:
         host_rgb = st.target_rgb.cpu().pin_memory()
         host_alpha = st.target_alpha.cpu().pin_memory()

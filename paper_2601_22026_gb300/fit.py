@@ -235,6 +235,10 @@ class FitState:
     def gaussians(self) -> dict:
         return G.unpack_params(self.params.cpu().numpy(), self.sh_degree)
 
+    def gaussians_first(self) -> dict:
+        """The first Gaussian only (a placeholder for states that share these parameters)."""
+        return G.unpack_params(self.params[:, :1].cpu().numpy(), self.sh_degree)
+
     def gradients(self) -> dict:
         return G.unpack_params(self.grads.cpu().numpy(), self.sh_degree)
 

@@ -1,0 +1,156 @@
+"""Continuous refinement during viewing (Section 4.2).
+
+After the initial model, the fit keeps running on the foveal views the
+viewer streams in. A new view joins the training set only when Eq. 1 calls
+it novel (gsfit_view_is_novel: farther than delta_pos = 0.05 from, or turned
+more than 5 degrees against, every view already in the set). The paper
+simplifies continual training to periodic restarts that reload the current
+Gaussians and discard the optimiser state (ContinuousRefinement.restart).
+
+The driver keeps a fixed-size batch of V views (the periphery frames plus
+foveal crops); every `replace_every` iterations the oldest `n_replace` crops
+are replaced by newly streamed views that pass Eq. 1, their targets are
+rendered from the target set, and the iteration is captured again as a CUDA
+graph. Every arithmetic step runs in the library's kernels; this module only
+moves views and buffers around.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import gsfit as G
+
+
+def camera_forward(cams: dict, v: int) -> np.ndarray:
+    """World-space viewing direction of view v (third row of the rotation)."""
+    return np.asarray(cams["viewmat"][v], np.float64).reshape(3, 4)[2, :3].copy()
+
+
+class ViewSet:
+    """The training views of continual refinement, grown by Eq. 1."""
+
+    def __init__(self, delta_pos: float = 0.05, theta_deg: float = 5.0):
+        self.delta_pos = float(delta_pos)
+        self.theta_deg = float(theta_deg)
+        self.pos: list[np.ndarray] = []
+        self.dir: list[np.ndarray] = []
+
+    def __len__(self) -> int:
+        return len(self.pos)
+
+    def add(self, pos, direction) -> None:
+        self.pos.append(np.asarray(pos, np.float64))
+        self.dir.append(np.asarray(direction, np.float64))
+
+    def offer(self, pos, direction) -> bool:
+        """Adds the view if it is novel w.r.t. every view of the set (Eq. 1)."""
+        ps = np.array(self.pos).reshape(-1, 3)
+        ds = np.array(self.dir).reshape(-1, 3)
+        novel = G.gsfit_view_is_novel(pos, direction, ps, ds, self.delta_pos, self.theta_deg)
+        if novel:
+            self.add(pos, direction)
+        return novel
+
+
+def share_parameters(dst, src) -> None:
+    """Makes FitState dst render src's Gaussians (parameters, 16-bit copy,
+    optimiser state) on its own views."""
+    dst.params, dst.grads, dst.m, dst.v = src.params, src.grads, src.m, src.v
+    dst.step_count, dst.lr = src.step_count, src.lr
+    dst.features, dst.feature_dtype = src.features, src.feature_dtype
+    dst.graph = None
+
+
+def view_state(src, cams: dict, bg=None, **kw):
+    """A FitState on other views that renders (and, if stepped, fits) src's
+    Gaussians: built around a one-Gaussian placeholder, then sharing src's
+    parameters, 16-bit copy and optimiser state."""
+    from .fit import FitState
+    st = FitState(src.gaussians_first(), cams, bg=bg, capacity=16, tile=src.tile, batch=int(src.opts.batch), **kw)
+    st.n = src.n
+    share_parameters(st, src)
+    st.set_cameras(cams, bg=bg)
+    st.capacity = 0
+    st.ensure_capacity()
+    return st
+
+
+def psnr(eval_state) -> float:
+    """PSNR (dB) of eval_state's render against its targets, over all colour
+    pixels of its view batch (a measurement; not part of the fit step)."""
+    import torch
+    eval_state.forward()
+    mse = torch.mean((eval_state.rgb - eval_state.target_rgb) ** 2).item()
+    return float(10.0 * np.log10(1.0 / max(mse, 1e-20)))
+
+
+class ContinuousRefinement:
+    """Streams foveal views into a FitState's batch.
+
+    state: the FitState being fitted (its batch: n_fixed periphery frames,
+    then crops); target_state: a FitState of the target Gaussians used to
+    render the targets of new views (over a zero background, premultiplied);
+    crop_stream: an iterator of single-view camera dicts; backgrounds:
+    (steps, V, 3) random per-view backgrounds, one row per iteration."""
+
+    def __init__(self, state, target_state, cams: dict, crop_stream, backgrounds: np.ndarray, *, n_fixed: int = 2,
+                 replace_every: int = 10, n_replace: int = 4, view_set: ViewSet | None = None):
+        import torch
+        self.st, self.tgt = state, target_state
+        self.cams = {k: np.array(v) for k, v in cams.items()}
+        self.V = len(self.cams["width"])
+        self.crops = crop_stream
+        self.bg = torch.as_tensor(np.asarray(backgrounds, np.float32)).to(state.device)
+        self.n_fixed, self.replace_every, self.n_replace = int(n_fixed), int(replace_every), int(n_replace)
+        self.views = view_set if view_set is not None else ViewSet()
+        for v in range(self.V):  # the starting batch is the starting training set
+            self.views.add(self.cams["campos"][v], camera_forward(self.cams, v))
+        self.next_slot = self.n_fixed
+        self.it = 0
+        self.offered = 0
+        self.accepted = 0
+        self.replacements = 0
+
+    def _render_targets(self) -> None:
+        self.tgt.set_cameras(self.cams, bg=np.zeros((self.V, 3), np.float32))
+        self.tgt.ensure_capacity()
+        self.tgt.forward()
+        self.st.target_rgb.copy_(self.tgt.rgb)
+        self.st.target_alpha.copy_(self.tgt.alpha)
+
+    def replace_crops(self, max_offers: int = 64) -> int:
+        """Replaces up to n_replace of the oldest crops by streamed views that
+        pass Eq. 1; returns how many were replaced."""
+        new = []
+        while len(new) < self.n_replace and self.offered < 10**9 and max_offers > 0:
+            c = next(self.crops)
+            self.offered += 1
+            max_offers -= 1
+            if self.views.offer(c["campos"][0], camera_forward(c, 0)):
+                self.accepted += 1
+                new.append(c)
+        for c in new:
+            slot = self.next_slot
+            for k in self.cams:
+                self.cams[k][slot] = c[k][0]
+            self.next_slot = self.n_fixed + (slot - self.n_fixed + 1) % (self.V - self.n_fixed)
+        if new:
+            self.st.set_cameras(self.cams, bg=np.zeros((self.V, 3), np.float32))
+            self.st.ensure_capacity()
+            self._render_targets()
+            self.replacements += 1
+        return len(new)
+
+    def step(self) -> None:
+        """One fit iteration (no host synchronisation unless views change)."""
+        if self.it > 0 and self.it % self.replace_every == 0:
+            self.replace_crops()
+        self.st.bg.copy_(self.bg[self.it % self.bg.shape[0]])
+        if self.st.graph is None:
+            self.st.capture(warmup=0)
+        self.st.replay()
+        self.it += 1
+
+    def restart(self) -> None:
+        """Periodic restart: keep the Gaussians, discard the optimiser state."""
+        self.st.reset_optimizer()

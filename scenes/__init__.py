@@ -186,6 +186,36 @@ def periphery_batch_cameras(seed: int, *, n_crops: int = 14, periphery_size: int
     return stack_cameras(cams)
 
 
+def foveal_crops(seed: int, n: int, stream_seed: int, *, periphery_size: int = 1920,
+                 periphery_fov_deg: float = 100.0, baseline: float = 0.064, distance: float = 3.0,
+                 crop_min: int = 256, crop_max: int = 768, px_per_20deg: float = 512.0,
+                 max_gaze_deg: float = 20.0, near: float = 0.2) -> dict:
+    """n further foveal crops for the head of periphery_batch_cameras(seed)
+    (same eyes and angular density, new gaze directions and sizes), drawn
+    from a stream seeded by stream_seed: the views a viewer keeps sending
+    during continual refinement."""
+    g = rng(stream_seed)
+    head = unit_sphere_points(1, seed)[0] * distance
+    fwd = -head / np.linalg.norm(head)
+    R = _look_rotation(fwd, np.array([0.0, 0.0, 1.0]))
+    right, down = R[0], R[1]
+    eyes = [head - right * baseline / 2, head + right * baseline / 2]
+    fxf = (px_per_20deg / 2.0) / math.tan(math.radians(10.0))
+    cams = []
+    for k in range(n):
+        w = int(g.integers(crop_min, crop_max + 1))
+        h = int(g.integers(crop_min, crop_max + 1))
+        yaw = math.radians(g.uniform(-max_gaze_deg, max_gaze_deg))
+        pitch = math.radians(g.uniform(-max_gaze_deg, max_gaze_deg))
+        gaze = _rotate(_rotate(fwd, down, yaw), right, pitch)
+        cams.append(make_camera(eyes[int(g.integers(0, 2))], None, w, h, fx=fxf, forward=gaze, up=-down, near=near))
+    return stack_cameras(cams)
+
+
+def concat_cameras(a: dict, b: dict) -> dict:
+    return {k: np.concatenate([a[k], b[k]]) for k in a}
+
+
 def camera_subset(cams: dict, idx) -> dict:
     return {k: v[idx] for k, v in cams.items()}
 

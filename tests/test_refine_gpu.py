@@ -1,0 +1,78 @@
+"""Continuous refinement (Section 4.2): streamed foveal views enter the batch
+through Eq. 1, their targets are rendered from the target set, the fit keeps
+improving, and a restart keeps the Gaussians but discards the optimiser
+state. Small scene (20k Gaussians, 256^2 periphery frames, 64..128 px crops)."""
+import itertools
+
+import numpy as np
+import pytest
+
+import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+KW = dict(periphery_size=256, crop_min=64, crop_max=128)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import paper_2601_22026_gb300 as pkg
+    pkg.build()
+
+
+def _setup(features="f32"):
+    from paper_2601_22026_gb300 import refine
+    from paper_2601_22026_gb300.fit import FitState, boosted_lr
+    cams = scenes.periphery_batch_cameras(0, n_crops=6, **KW)
+    V = len(cams["width"])
+    zeros = np.zeros((V, 3), np.float32)
+    gs = scenes.random_gaussians(20000, 3, 61, log_scale_mean=-4.0)
+    tg = scenes.random_gaussians(20000, 3, 62, log_scale_mean=-4.0)
+    tgt = FitState(tg, cams, bg=zeros)
+    tgt.forward()
+    st = FitState(gs, cams, bg=zeros, lr=boosted_lr(), features=features)
+    st.target_rgb.copy_(tgt.rgb)
+    st.target_alpha.copy_(tgt.alpha)
+    ev = refine.view_state(st, cams, bg=zeros)
+    ev.target_rgb.copy_(tgt.rgb)
+    ev.target_alpha.copy_(tgt.alpha)
+    stream = (scenes.foveal_crops(0, 1, 5000 + k, **KW) for k in itertools.count())
+    loop = refine.ContinuousRefinement(st, tgt, cams, stream, scenes.backgrounds(V, 63, n_steps=64),
+                                       replace_every=10, n_replace=2)
+    return st, tgt, ev, loop
+
+
+@pytest.mark.parametrize("features", ["f32", "f16"])
+def test_refinement_streams_views_and_improves(features):
+    from paper_2601_22026_gb300 import refine
+    st, tgt, ev, loop = _setup(features)
+    p0 = refine.psnr(ev)
+    n0 = len(loop.views)
+    for _ in range(40):
+        loop.step()
+    torch.cuda.synchronize()
+    assert st.check_status() == 0
+    assert loop.replacements == 3  # at iterations 10, 20, 30
+    assert 0 < loop.accepted <= loop.offered
+    assert len(loop.views) == n0 + loop.accepted
+    # the replaced views' targets are the target set's render of the current batch
+    tgt.forward()
+    assert torch.equal(st.target_rgb, tgt.rgb)
+    p1 = refine.psnr(ev)
+    assert p1 > p0 + 0.5, (p0, p1)
+
+
+def test_restart_keeps_gaussians_and_discards_optimizer_state():
+    st, _, _, loop = _setup()
+    for _ in range(5):
+        loop.step()
+    torch.cuda.synchronize()
+    params = st.params.clone()
+    loop.restart()
+    torch.cuda.synchronize()
+    assert torch.equal(st.params, params)
+    assert float(st.m.abs().max()) == 0.0 and float(st.v.abs().max()) == 0.0
+    assert int(st.step_count.item()) == 0
