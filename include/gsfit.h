@@ -442,6 +442,36 @@ int gsfit_adam_step(float* params, const float* grads, float* m, float* v, int32
 int gsfit_features_refresh(const float* params, int32_t n, int32_t n_planes, void* features, int32_t feature_dtype,
                            cudaStream_t stream);
 
+/*
+ * gsfit_reproject -- depth-guided reprojection of a foveal image to a newer
+ * head pose (Section 4.3, Eqs. 2-4), as a headless kernel writing device
+ * buffers instead of deforming a mesh in a viewer shader.
+ *   Per source pixel (x, y), uv = ((x + 0.5) / W, (y + 0.5) / H) (v grows
+ *   with the row index) and its linear depth d (world distance along the ray):
+ *     p_far   = (P_old V_old)^-1 (2uv - 1, 1, 1)^T / w   (the far plane, z_ndc = 1)
+ *     p_world = pos_old + d (p_far - pos_old) / |p_far - pos_old|
+ *     p'_clip = P_new V_new p_world                      (written to clip)
+ *   The image is then carried to the new view point by point: the source
+ *   pixel lands on the output pixel nearest to its projected centre
+ *   ((ndc + 1) / 2 * size - 0.5 rounded half up) if p'_clip.w > 0 and that pixel
+ *   exists; among sources landing on one output pixel the smallest w (nearest
+ *   to the new camera) wins, ties to the lower source index. Output pixels no
+ *   source reaches (disocclusions, which the viewer fills from the Gaussian
+ *   model) get covered = 0 and colour 0. Pixels with depth <= 0 or not
+ *   finite are skipped (clip = 0).
+ * Arguments: rgb: 3 planes of W*H floats; depth: W*H floats (device);
+ *   inv_pv_old (the inverse of P_old V_old), pv_new: HOST row-major 4x4
+ *   float matrices acting on column vectors; pos_old: HOST 3 floats; clip:
+ *   device 4*W*H floats or null; zbuf: device workspace of out_w*out_h
+ *   uint64 (contents need not be initialised); out_rgb: 3 planes of
+ *   out_w*out_h floats; covered: out_w*out_h bytes (device).
+ * Errors: GSFIT_ERR_INVALID_ARG (null pointers, non-positive sizes),
+ *   GSFIT_ERR_CUDA.
+ */
+int gsfit_reproject(const float* rgb, const float* depth, int32_t width, int32_t height, const float* inv_pv_old,
+                    const float* pos_old, const float* pv_new, int32_t out_w, int32_t out_h, float* clip,
+                    unsigned long long* zbuf, float* out_rgb, uint8_t* covered, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

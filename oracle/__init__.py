@@ -321,3 +321,66 @@ def view_is_novel(pos_new, dir_new, pos_set, dir_set, delta_pos: float = 0.05, t
         if not (np.linalg.norm(p - pi) > delta_pos or float(d @ di) < c):
             return False
     return True
+
+
+def reproject(rgb, depth, W: int, H: int, inv_pv_old, pos_old, pv_new, out_w: int, out_h: int) -> dict:
+    """Section 4.3, Eqs. 2-4, in float64: per source pixel (x, y) with
+    uv = ((x + 0.5) / W, (y + 0.5) / H) and linear depth d,
+      p_far = (P_old V_old)^-1 (2uv - 1, 1, 1) / w,
+      p_world = pos_old + d (p_far - pos_old) / |p_far - pos_old|,
+      p'_clip = P_new V_new p_world;
+    then each source pixel is carried to the output pixel nearest its
+    projected centre (w > 0), the smallest w winning, ties to the lower index.
+    Returns clip (W*H, 4), out_rgb (3, out_w*out_h), covered, and `ambiguous`
+    output pixels whose winner could differ in float32: a source landing within
+    1e-3 px of a rounding boundary next to them, or a runner-up w within 1e-5."""
+    rgb = np.asarray(rgb, np.float64).reshape(3, -1)
+    d = np.asarray(depth, np.float64).reshape(-1)
+    n = W * H
+    y, x = np.divmod(np.arange(n), W)
+    ndc = np.stack([2 * (x + 0.5) / W - 1, 2 * (y + 0.5) / H - 1, np.ones(n), np.ones(n)])
+    h = np.asarray(inv_pv_old, np.float64) @ ndc
+    p_far = h[:3] / h[3]
+    pos = np.asarray(pos_old, np.float64).reshape(3, 1)
+    ray = p_far - pos
+    p_world = pos + ray / np.linalg.norm(ray, axis=0) * d
+    clip = np.asarray(pv_new, np.float64) @ np.vstack([p_world, np.ones(n)])
+    ok = (d > 0) & np.isfinite(d)
+    clip[:, ~ok] = 0.0
+    out_rgb = np.zeros((3, out_w * out_h))
+    covered = np.zeros(out_w * out_h, bool)
+    ambiguous = np.zeros(out_w * out_h, bool)
+    best_w = np.full(out_w * out_h, np.inf)
+    second_w = np.full(out_w * out_h, np.inf)
+    best_src = np.full(out_w * out_h, -1)
+    for k in range(n):  # plain per-source loop (small images only)
+        c = clip[:, k]
+        if not ok[k] or not c[3] > 0:
+            continue
+        px = (c[0] / c[3] + 1) * 0.5 * out_w - 0.5
+        py = (c[1] / c[3] + 1) * 0.5 * out_h - 0.5
+        rx, ry = np.floor(px + 0.5), np.floor(py + 0.5)
+        near_x = abs((px + 0.5) - np.round(px + 0.5)) < 1e-3
+        near_y = abs((py + 0.5) - np.round(py + 0.5)) < 1e-3
+        if near_x or near_y:  # flag every output pixel it could land on
+            for ax in ([rx - 1, rx] if near_x else [rx]):
+                for ay in ([ry - 1, ry] if near_y else [ry]):
+                    if 0 <= ax < out_w and 0 <= ay < out_h:
+                        ambiguous[int(ay) * out_w + int(ax)] = True
+        if not (0 <= rx < out_w and 0 <= ry < out_h):
+            continue
+        t = int(ry) * out_w + int(rx)
+        w = c[3]
+        if w < best_w[t] or (w == best_w[t] and k < best_src[t]):
+            second_w[t] = best_w[t]
+            best_w[t], best_src[t] = w, k
+        elif w < second_w[t]:
+            second_w[t] = w
+    has = best_src >= 0
+    covered[has] = True
+    out_rgb[:, has] = rgb[:, best_src[has]]
+    with np.errstate(invalid="ignore"):  # inf - inf where a pixel has no runner-up
+        close = has & np.isfinite(second_w) & (np.abs(second_w - best_w) <= 1e-5 * np.abs(best_w))
+    ambiguous |= close
+    return {"clip": clip.T.copy(), "out_rgb": out_rgb, "covered": covered, "ambiguous": ambiguous,
+            "p_world": p_world.T.copy()}

@@ -81,6 +81,7 @@ SIGNATURES = {
     "gsfit_adam_step": (ctypes.c_int, [_P, _P, _P, _P, _i32, _i32, _P, _f32, _f32, _f32, _P, _P, _i32, _P]),
     "gsfit_features_refresh": (ctypes.c_int, [_P, _i32, _i32, _P, _i32, _P]),
     "gsfit_view_is_novel": (ctypes.c_int, [_P, _P, _P, _P, _i32, _f32, _f32]),
+    "gsfit_reproject": (ctypes.c_int, [_P, _P, _i32, _i32, _P, _P, _P, _i32, _i32, _P, _P, _P, _P, _P]),
 }
 
 _lib = None
@@ -394,3 +395,15 @@ def gsfit_view_is_novel(pos_new, dir_new, pos_set, dir_set, delta_pos=0.05, thet
                                     float(np.cos(np.deg2rad(theta_deg))))
     _check(min(rc, 0), "gsfit_view_is_novel")
     return rc == 1
+
+
+def gsfit_reproject(rgb, depth, width, height, inv_pv_old, pos_old, pv_new, out_w, out_h, clip, zbuf, out_rgb,
+                    covered, stream=None):
+    """Depth-guided reprojection (Eqs. 2-4); matrices and pos_old are host arrays."""
+    m0 = np.ascontiguousarray(inv_pv_old, dtype=np.float32).reshape(16)
+    m1 = np.ascontiguousarray(pv_new, dtype=np.float32).reshape(16)
+    p0 = np.ascontiguousarray(pos_old, dtype=np.float32).reshape(3)
+    _check(load().gsfit_reproject(_ptr(rgb), _ptr(depth), int(width), int(height), m0.ctypes.data_as(_P),
+                                  p0.ctypes.data_as(_P), m1.ctypes.data_as(_P), int(out_w), int(out_h), _ptr(clip),
+                                  _ptr(zbuf), _ptr(out_rgb), _ptr(covered), _stream(stream)),
+           "gsfit_reproject")

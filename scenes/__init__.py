@@ -212,6 +212,23 @@ def foveal_crops(seed: int, n: int, stream_seed: int, *, periphery_size: int = 1
     return stack_cameras(cams)
 
 
+def projection_view(cams: dict, v: int, near: float = 0.2, far: float = 100.0) -> np.ndarray:
+    """4x4 projection-view matrix (float64, acting on column vectors) of view
+    v for the pixel convention of the cameras: a world point maps to
+    ndc = ((u + 0.5) / W * 2 - 1, (v + 0.5) / H * 2 - 1) with u = fx x/z + cx,
+    v = fy y/z + cy in camera space, and depth to [0, 1] with the far plane at
+    z_ndc = 1."""
+    W, H = float(cams["width"][v]), float(cams["height"][v])
+    fx, fy, cx, cy = (float(cams[k][v]) for k in ("fx", "fy", "cx", "cy"))
+    P = np.array([[2 * fx / W, 0.0, 2 * (cx + 0.5) / W - 1.0, 0.0],
+                  [0.0, 2 * fy / H, 2 * (cy + 0.5) / H - 1.0, 0.0],
+                  [0.0, 0.0, far / (far - near), -far * near / (far - near)],
+                  [0.0, 0.0, 1.0, 0.0]])
+    Vm = np.eye(4)
+    Vm[:3, :] = np.asarray(cams["viewmat"][v], np.float64).reshape(3, 4)
+    return P @ Vm
+
+
 def concat_cameras(a: dict, b: dict) -> dict:
     return {k: np.concatenate([a[k], b[k]]) for k in a}
 
