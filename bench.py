@@ -453,6 +453,39 @@ def reprojection_rate(reps: int = 50) -> dict:
             "covered": float(cov.float().mean().item())}
 
 
+def regeneration_leg(iters: int = 700, simplify_at: int = 95, keep: int = 10_000, n_init: int = 50_000,
+                     n_views: int = 16, size: int = 512) -> dict:
+    """The abbreviated initial regeneration (Section 4.2) end to end: Gaussians
+    seeded from the 256^3 CT procedure, fitted to a batch of orbit views
+    rendered from a denser target set, simplified by importance after 95 steps,
+    700 steps in all; wall time from the first step to the last."""
+    import torch
+    from paper_2601_22026_gb300 import refine
+    from paper_2601_22026_gb300.fit import FitState
+    vol, vox = scenes.ct_volume((256, 256, 256), 0)
+    init = scenes.gaussians_from_volume(vol, vox, n_init, 0)
+    target = scenes.gaussians_from_volume(vol, vox, 4 * n_init, 1)
+    cams = scenes.orbit_cameras(n_views, size, size, 60.0, 3.0, 2)
+    zeros = np.zeros((n_views, 3), np.float32)
+    tgt = FitState(target, cams, bg=zeros)
+    tgt.forward()
+    ev = FitState(init, cams, bg=zeros)
+    ev.target_rgb.copy_(tgt.rgb)
+    p0 = refine.psnr(ev)
+    del ev
+    st, info = refine.regenerate(init, cams, tgt.rgb, tgt.alpha, scenes.backgrounds(n_views, 4, n_steps=iters),
+                                 iters=iters, simplify_at=simplify_at, keep=keep)
+    st.bg.zero_()
+    p1 = refine.psnr(st)
+    out = dict(info, iterations=iters, simplify_at=simplify_at, keep=keep, views_per_iteration=n_views,
+               view_size=size, psnr_db_before=p0, psnr_db_after=p1,
+               context="the paper regenerates ~10k Gaussians in ~700 steps in about a second on an RTX 4090 "
+                       "(Section 5.2.1; other hardware, one view per step)")
+    del st, tgt
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args) -> None:
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -486,6 +519,7 @@ def main() -> None:
     ap.add_argument("--no-plain", action="store_true", help="skip the single-view comparison")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision (16-bit features) leg")
     ap.add_argument("--no-tune", action="store_true", help="default tile 16 / batch 128 instead of the autotuner")
+    ap.add_argument("--no-regen", action="store_true", help="skip the abbreviated-regeneration leg")
     ap.add_argument("--refine-iters", type=int, default=300,
                     help="iterations of the continuous-refinement leg (0 skips it)")
     ap.add_argument("--gaussians", type=int, default=1_000_000,
@@ -634,6 +668,8 @@ def main() -> None:
         out["reprojection_768"] = reprojection_rate()
     if rank == 0 and args.refine_iters > 0:
         out["continuous_refinement"] = refinement_leg(sc, st, args.refine_iters)
+    if rank == 0 and not args.no_regen:
+        out["regeneration"] = regeneration_leg()
     if rank == 0:
         host_rgb = st.target_rgb.cpu().pin_memory()
         host_alpha = st.target_alpha.cpu().pin_memory()

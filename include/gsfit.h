@@ -443,6 +443,40 @@ int gsfit_features_refresh(const float* params, int32_t n, int32_t n_planes, voi
                            cudaStream_t stream);
 
 /*
+ * gsfit_render_importance -- gsfit_render_fwd that also accumulates each
+ * Gaussian's importance: the sum over the batch's pixels of its blend weight
+ * alpha_i T_i (the weight its colour gets in C). Per pixel these weights sum
+ * to 1 - T_N, so the importances of a batch sum to its total alpha. Used for
+ * the simplification step of the abbreviated regeneration (Section 4.2).
+ * Arguments as for gsfit_render_fwd; importance: device, n floats, added to
+ * (the caller zeroes it before the first batch).
+ * Errors: as for gsfit_render_fwd.
+ */
+int gsfit_render_importance(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_views, int32_t n,
+                            int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges,
+                            const uint32_t* tile_order, const float* bg, float* rgb, float* alpha, float* T_final,
+                            uint32_t* n_contrib, float* importance, const gsfit_render_opts* opts, int32_t* status,
+                            cudaStream_t stream);
+
+/*
+ * gsfit_simplify -- keeps the `keep` most important Gaussians (the
+ * simplification of the abbreviated regeneration, Section 4.2; importance as
+ * gsfit_render_importance accumulates it). The threshold is the keep-th
+ * largest importance; every Gaussian at or above it is kept, so ties at the
+ * threshold may keep a few more; with n <= keep every Gaussian is kept.
+ * Kept Gaussians are written in index order: plane p of the m-th kept one at
+ * float4 index p * n + m of params_out (the input's plane stride n); the count
+ * goes to *n_out (device). Negative or NaN importance counts as 0.
+ * Arguments: params: n_planes * n float4 (device); importance: n floats;
+ *   params_out: n_planes * n float4, distinct from params; ws: device workspace
+ *   of gsfit_simplify_workspace_size(n) bytes, 16-byte aligned.
+ * Errors: GSFIT_ERR_INVALID_ARG, GSFIT_ERR_CUDA.
+ */
+size_t gsfit_simplify_workspace_size(int32_t n);
+int gsfit_simplify(const float* params, int32_t n, int32_t n_planes, const float* importance, int32_t keep,
+                   float* params_out, uint32_t* n_out, void* ws, size_t ws_bytes, cudaStream_t stream);
+
+/*
  * gsfit_reproject -- depth-guided reprojection of a foveal image to a newer
  * head pose (Section 4.3, Eqs. 2-4), as a headless kernel writing device
  * buffers instead of deforming a mesh in a viewer shader.

@@ -69,7 +69,7 @@ def lib() -> ctypes.CDLL:
         L.oracle_project.argtypes = [i, i, P, i, P, i, i, P]
         L.oracle_bin.argtypes = [i, i, P, i, P, P, P, ll, P]
         L.oracle_bin.restype = ll
-        L.oracle_render_fwd.argtypes = [i, i, P, i, P, P, P, P, i, P, P, P, P, P, P]
+        L.oracle_render_fwd.argtypes = [i, i, P, i, P, P, P, P, i, P, P, P, P, P, P, P]
         L.oracle_render_bwd.argtypes = [i, i, P, i, P, i, P, P, P, P, i, P, P, P, P, P]
         L.oracle_loss.argtypes = [i, P, P, P, P, P, P, P, d, P, P, P]
         L.oracle_loss.restype = d
@@ -190,10 +190,11 @@ def render(gs: dict, cams: dict, bg: np.ndarray, tile: int = 16, smooth: bool = 
     nb = np.zeros(P, dtype=np.int32)
     bgd = np.ascontiguousarray(bg, dtype=np.float64).reshape(V, 3)
     vals_c = np.ascontiguousarray(vals) if vals.size else np.zeros(1, np.uint32)
+    imp = np.zeros(n)
     lib().oracle_render_fwd(n, V, _p(c), tile, _p(proj), _p(vals_c), _p(ranges), _p(bgd),
-                            SMOOTH if smooth else 0, _p(rgb), _p(alpha), _p(T), _p(nc), _p(amb), _p(nb))
+                            SMOOTH if smooth else 0, _p(rgb), _p(alpha), _p(T), _p(nc), _p(amb), _p(nb), _p(imp))
     return {"rgb": rgb, "alpha": alpha, "T_final": T, "n_contrib": nc, "ambiguous": amb.astype(bool),
-            "n_blended": nb, "proj": proj, "keys": keys, "vals": vals, "ranges": ranges}
+            "n_blended": nb, "proj": proj, "keys": keys, "vals": vals, "ranges": ranges, "importance": imp}
 
 
 def render_bwd(gs: dict, cams: dict, bg: np.ndarray, dL_drgb: np.ndarray, dL_dalpha: np.ndarray,
@@ -384,3 +385,18 @@ def reproject(rgb, depth, W: int, H: int, inv_pv_old, pos_old, pv_new, out_w: in
     ambiguous |= close
     return {"clip": clip.T.copy(), "out_rgb": out_rgb, "covered": covered, "ambiguous": ambiguous,
             "p_world": p_world.T.copy()}
+
+
+def simplify(gs: dict, importance, keep: int) -> tuple[dict, np.ndarray]:
+    """Simplification by importance: keep the Gaussians whose importance is at
+    least the keep-th largest (all of them when there are at most keep; ties
+    at the threshold all kept), in index order. Importance compared as float32
+    values, as stored on the GPU. Returns (kept set, kept indices)."""
+    imp = np.asarray(importance, np.float32)
+    imp = np.where(np.isfinite(imp) & (imp > 0), imp, np.float32(0.0))
+    if imp.size <= keep:
+        idx = np.arange(imp.size)
+    else:
+        thr = np.sort(imp)[::-1][keep - 1]
+        idx = np.flatnonzero(imp >= thr)
+    return {k: np.asarray(v)[idx] for k, v in gs.items()}, idx

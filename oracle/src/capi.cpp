@@ -14,7 +14,7 @@ long long bin_tiles(int n, const std::vector<Camera>& cams, const double* proj, 
                     std::vector<uint32_t>& vals, std::vector<uint32_t>& ranges);
 void render_fwd(int n, const std::vector<Camera>& cams, int tile, const double* proj, const uint32_t* vals,
                 const uint32_t* ranges, const double* bg, int flags, double* rgb, double* alpha, double* T_final,
-                int32_t* n_contrib, uint8_t* ambiguous, int32_t* n_blended);
+                int32_t* n_contrib, uint8_t* ambiguous, int32_t* n_blended, double* importance);
 void render_bwd(int n, int K, const double* gauss, const std::vector<Camera>& cams, int tile, const double* proj,
                 const uint32_t* vals, const uint32_t* ranges, const double* bg, int flags, const double* dL_drgb,
                 const double* dL_dalpha, double* grad2d, double* grads, uint8_t* gauss_ambiguous);
@@ -87,9 +87,11 @@ long long oracle_bin(int n, int V, const double* cams, int tile, const double* p
 
 void oracle_render_fwd(int n, int V, const double* cams, int tile, const double* proj, const uint32_t* vals,
                        const uint32_t* ranges, const double* bg, int flags, double* rgb, double* alpha,
-                       double* T_final, int32_t* n_contrib, uint8_t* ambiguous, int32_t* n_blended) {
+                       double* T_final, int32_t* n_contrib, uint8_t* ambiguous, int32_t* n_blended,
+                       double* importance) {
     const std::vector<Camera> c = unpack_cameras(V, cams, tile);
-    render_fwd(n, c, tile, proj, vals, ranges, bg, flags, rgb, alpha, T_final, n_contrib, ambiguous, n_blended);
+    render_fwd(n, c, tile, proj, vals, ranges, bg, flags, rgb, alpha, T_final, n_contrib, ambiguous, n_blended,
+               importance);
 }
 
 void oracle_render_bwd(int n, int K, const double* gauss, int V, const double* cams, int tile, const double* proj,

@@ -158,9 +158,11 @@ std::vector<WorkItem> work_items(const std::vector<Camera>& cams) {
 
 }  // namespace
 
+// importance (optional, n entries, added to): per Gaussian the sum over the
+// pixels of its blend weight alpha T, the weight its colour receives in C.
 void render_fwd(int n, const std::vector<Camera>& cams, int tile, const double* proj, const uint32_t* vals,
                 const uint32_t* ranges, const double* bg, int flags, double* rgb, double* alpha, double* T_final,
-                int32_t* n_contrib, uint8_t* ambiguous, int32_t* n_blended) {
+                int32_t* n_contrib, uint8_t* ambiguous, int32_t* n_blended, double* importance) {
     const int V = (int)cams.size();
     std::vector<std::vector<uint32_t>> sorted(V);
     if (flags & FLAG_SMOOTH)
@@ -195,6 +197,11 @@ void render_fwd(int n, const std::vector<Camera>& cams, int tile, const double* 
                 n_contrib[pix] = px.n_contrib;
                 ambiguous[pix] = px.ambiguous ? 1 : 0;
                 if (n_blended) n_blended[pix] = (int32_t)px.blends.size();
+                if (importance)
+                    for (const Blend& e : px.blends) {
+#pragma omp atomic
+                        importance[e.gauss] += e.alpha * e.T;
+                    }
             }
     }
 }

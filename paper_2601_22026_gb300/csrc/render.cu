@@ -302,13 +302,15 @@ __device__ __forceinline__ bool tile_mismatch(const gsfit_camera* cams, int32_t*
     return true;
 }
 
-template <int TILE, int SLOT>
+// IMP: also accumulate each Gaussian's blend weight alpha T over the batch
+// into importance[g] (a warp sum per (warp, Gaussian), then one atomic).
+template <int TILE, int SLOT, bool IMP>
 __global__ void __launch_bounds__(TileShape<TILE>::kThreads) render_fwd_kernel(
     const float4* __restrict__ xyd, const float4* __restrict__ conic, const float4* __restrict__ rgb, int n,
     const gsfit_camera* __restrict__ cams_g, int n_views, const uint32_t* __restrict__ vals,
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ tile_order, const float* __restrict__ bg,
     float* __restrict__ out_rgb, float* __restrict__ out_alpha, float* __restrict__ out_T,
-    uint32_t* __restrict__ out_nc, int32_t* __restrict__ status) {
+    uint32_t* __restrict__ out_nc, int32_t* __restrict__ status, float* __restrict__ importance) {
     constexpr int kWarps = TileShape<TILE>::kWarps;
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     gsfit_camera* cams = reinterpret_cast<gsfit_camera*>(smem_dyn);
@@ -354,6 +356,7 @@ __global__ void __launch_bounds__(TileShape<TILE>::kThreads) render_fwd_kernel(
             const int nw = ring_compact(R, s, cnt, base, 0xffffffffu, c, s_list[w]);
             for (int i = 0; i < nw; ++i) {
                 const int j = s_list[w][i];
+                float my_w = 0.0f;  // this pixel's blend weight of entry j (importance pass)
                 if (!done) {
                     const float4 p = R.xyd[s][j];
                     const float4 co = R.co[s][j];
@@ -372,9 +375,14 @@ __global__ void __launch_bounds__(TileShape<TILE>::kThreads) render_fwd_kernel(
                                 C2 += col.z * wgt;
                                 T = test_T;
                                 last = base + (uint32_t)j + 1u;  // one past this list position
+                                if constexpr (IMP) my_w = wgt;
                             }
                         }
                     }
+                }
+                if constexpr (IMP) {
+                    const float sum = warp_sum(my_w);
+                    if (lane == 0 && sum != 0.0f) atomicAdd(importance + R.g[s][j], sum);
                 }
                 if (__all_sync(0xffffffffu, done)) break;
             }
@@ -654,6 +662,7 @@ struct FwdArgs {
     float *out_rgb, *out_alpha, *out_T;
     uint32_t* out_nc;
     int32_t* status;
+    float* importance;  // non-null: the importance variant
 };
 
 struct BwdArgs {
@@ -685,16 +694,22 @@ int opt_in(K kernel, size_t bytes, bool* done) {
     return GSFIT_OK;
 }
 
-template <int TILE, int SLOT>
-int launch_fwd(const FwdArgs& a, int total_tiles, cudaStream_t s) {
+template <int TILE, int SLOT, bool IMP>
+int launch_fwd_v(const FwdArgs& a, int total_tiles, cudaStream_t s) {
     static bool done[64] = {false};
-    const int rc = opt_in(render_fwd_kernel<TILE, SLOT>, render_smem<SLOT>(GSFIT_MAX_VIEWS), done);
+    const int rc = opt_in(render_fwd_kernel<TILE, SLOT, IMP>, render_smem<SLOT>(GSFIT_MAX_VIEWS), done);
     if (rc != GSFIT_OK) return rc;
-    render_fwd_kernel<TILE, SLOT><<<total_tiles, TileShape<TILE>::kThreads, render_smem<SLOT>(a.n_views), s>>>(
+    render_fwd_kernel<TILE, SLOT, IMP><<<total_tiles, TileShape<TILE>::kThreads, render_smem<SLOT>(a.n_views), s>>>(
         a.xyd, a.conic, a.rgb, a.n, a.cams, a.n_views, a.vals, a.ranges, a.tile_order, a.bg, a.out_rgb, a.out_alpha,
-        a.out_T, a.out_nc, a.status);
+        a.out_T, a.out_nc, a.status, a.importance);
     GSFIT_LAUNCH_CHECK();
     return GSFIT_OK;
+}
+
+template <int TILE, int SLOT>
+int launch_fwd(const FwdArgs& a, int total_tiles, cudaStream_t s) {
+    return a.importance ? launch_fwd_v<TILE, SLOT, true>(a, total_tiles, s)
+                        : launch_fwd_v<TILE, SLOT, false>(a, total_tiles, s);
 }
 
 template <int TILE, int SLOT>
@@ -740,7 +755,8 @@ FwdArgs fwd_args(const gsfit_proj* proj, const gsfit_camera* cams, int n_views, 
                  float* T_final, uint32_t* n_contrib, int32_t* status) {
     return FwdArgs{reinterpret_cast<const float4*>(proj->xyd), reinterpret_cast<const float4*>(proj->conic),
                    reinterpret_cast<const float4*>(proj->rgb), n, cams, n_views, vals,
-                   reinterpret_cast<const uint2*>(ranges), tile_order, bg, rgb, alpha, T_final, n_contrib, status};
+                   reinterpret_cast<const uint2*>(ranges), tile_order, bg, rgb, alpha, T_final, n_contrib, status,
+                   nullptr};
 }
 
 BwdArgs bwd_args(const gsfit_proj* proj, const gsfit_camera* cams, int n_views, int n, const uint32_t* vals,
@@ -782,6 +798,21 @@ extern "C" int gsfit_render_fwd(const gsfit_proj* proj, const gsfit_camera* cams
     return run_fwd(fwd_args(proj, cams, n_views, n, vals, ranges, tile_order, bg, rgb, alpha, T_final, n_contrib,
                             status),
                    c, total_tiles, stream);
+}
+
+extern "C" int gsfit_render_importance(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_views, int32_t n,
+                                       int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges,
+                                       const uint32_t* tile_order, const float* bg, float* rgb, float* alpha,
+                                       float* T_final, uint32_t* n_contrib, float* importance,
+                                       const gsfit_render_opts* opts, int32_t* status, cudaStream_t stream) {
+    RenderCfg c;
+    if (!fwd_ok(proj, cams, n_views, n, total_tiles, vals, ranges, bg, rgb, alpha, T_final, n_contrib) ||
+        !importance || !resolve(opts, c))
+        return GSFIT_ERR_INVALID_ARG;
+    FwdArgs a = fwd_args(proj, cams, n_views, n, vals, ranges, tile_order, bg, rgb, alpha, T_final, n_contrib,
+                         status);
+    a.importance = importance;
+    return run_fwd(a, c, total_tiles, stream);
 }
 
 extern "C" int gsfit_blend_bwd(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_views, int32_t n,

@@ -70,6 +70,50 @@ class FitState:
         self.ensure_capacity(capacity)
         self.graph = None
 
+    @classmethod
+    def from_params(cls, params, sh_degree: int, cams: dict, **kw):
+        """A state around device parameters (n_planes, n, 4) float32 (e.g. a
+        simplified set): fresh gradients and optimiser state."""
+        import torch
+        first = G.unpack_params(params[:, :1].cpu().numpy(), sh_degree)
+        st = cls(first, cams, capacity=16, **{k: v for k, v in kw.items() if k != "capacity"})
+        st.n = int(params.shape[1])
+        st.params = params.contiguous()
+        st.grads = torch.zeros_like(st.params)
+        st.m = torch.zeros_like(st.params)
+        st.v = torch.zeros_like(st.params)
+        if st.feature_dtype != 0:
+            st.features = torch.empty((st.n_planes - 1, st.n, 4), dtype=st.features.dtype, device=st.device)
+            st.refresh_features()
+        st.set_cameras(cams, bg=kw.get("bg"))
+        st.capacity = 0
+        st.ensure_capacity(kw.get("capacity"))
+        return st
+
+    def importance(self):
+        """Per-Gaussian blend-weight importance over the current view batch
+        (one forward pass with gsfit_render_importance; no synchronisation)."""
+        import torch
+        imp = torch.zeros(self.n, dtype=torch.float32, device=self.device)
+        self.project()
+        self.bin_sort()
+        G.gsfit_render_importance(self.proj, self.cams_dev, self.V, self.n, self.T, self.vals, self.ranges, self.bg,
+                                  self.rgb, self.alpha, self.T_final, self.n_contrib, imp, None, self.tile_order,
+                                  self.status, self.opts)
+        return imp
+
+    def simplified_params(self, keep: int):
+        """The `keep` most important Gaussians' parameters (gsfit_simplify over
+        this batch's importance); synchronises to read the count."""
+        import torch
+        imp = self.importance()
+        out = torch.empty_like(self.params)
+        n_out = torch.zeros(1, dtype=torch.int32, device=self.device)
+        ws = torch.empty(G.gsfit_simplify_workspace_size(self.n), dtype=torch.uint8, device=self.device)
+        G.gsfit_simplify(self.params, self.n, self.n_planes, imp, int(keep), out, n_out, ws)
+        m = int(n_out.item())
+        return out[:, :m].contiguous()
+
     # -- view batch -----------------------------------------------------
     def set_cameras(self, cams: dict, bg=None) -> None:
         self.table = G.camera_table(cams, self.tile)

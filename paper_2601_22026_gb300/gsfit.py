@@ -81,6 +81,10 @@ SIGNATURES = {
     "gsfit_adam_step": (ctypes.c_int, [_P, _P, _P, _P, _i32, _i32, _P, _f32, _f32, _f32, _P, _P, _i32, _P]),
     "gsfit_features_refresh": (ctypes.c_int, [_P, _i32, _i32, _P, _i32, _P]),
     "gsfit_view_is_novel": (ctypes.c_int, [_P, _P, _P, _P, _i32, _f32, _f32]),
+    "gsfit_render_importance": (ctypes.c_int, [_P, _P, _i32, _i32, _i32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
+                                               _P, _P]),
+    "gsfit_simplify_workspace_size": (_size, [_i32]),
+    "gsfit_simplify": (ctypes.c_int, [_P, _i32, _i32, _P, _i32, _P, _P, _P, _size, _P]),
     "gsfit_reproject": (ctypes.c_int, [_P, _P, _i32, _i32, _P, _P, _P, _i32, _i32, _P, _P, _P, _P, _P]),
 }
 
@@ -407,3 +411,23 @@ def gsfit_reproject(rgb, depth, width, height, inv_pv_old, pos_old, pv_new, out_
                                   p0.ctypes.data_as(_P), m1.ctypes.data_as(_P), int(out_w), int(out_h), _ptr(clip),
                                   _ptr(zbuf), _ptr(out_rgb), _ptr(covered), _stream(stream)),
            "gsfit_reproject")
+
+
+def gsfit_render_importance(proj: ProjBuffers, cams_dev, n_views, n, total_tiles, vals, ranges, bg, rgb, alpha,
+                            T_final, n_contrib, importance, stream=None, tile_order=None, status=None, opts=None):
+    p = proj.struct()
+    _check(load().gsfit_render_importance(ctypes.byref(p), _ptr(cams_dev), n_views, n, total_tiles, _ptr(vals),
+                                          _ptr(ranges), _ptr(tile_order), _ptr(bg), _ptr(rgb), _ptr(alpha),
+                                          _ptr(T_final), _ptr(n_contrib), _ptr(importance), _opts(opts),
+                                          _ptr(status), _stream(stream)),
+           "gsfit_render_importance")
+
+
+def gsfit_simplify_workspace_size(n) -> int:
+    return int(load().gsfit_simplify_workspace_size(n))
+
+
+def gsfit_simplify(params, n, n_planes, importance, keep, params_out, n_out, ws, stream=None):
+    _check(load().gsfit_simplify(_ptr(params), n, n_planes, _ptr(importance), int(keep), _ptr(params_out),
+                                 _ptr(n_out), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)),
+           "gsfit_simplify")

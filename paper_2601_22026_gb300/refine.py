@@ -154,3 +154,69 @@ class ContinuousRefinement:
     def restart(self) -> None:
         """Periodic restart: keep the Gaussians, discard the optimiser state."""
         self.st.reset_optimizer()
+
+
+def regenerate(gaussians: dict, cams: dict, target_rgb, target_alpha, backgrounds: np.ndarray, *, iters: int = 700,
+               simplify_at: int = 95, keep: int = 10_000, lr: dict | None = None, **state_kw) -> tuple:
+    """The abbreviated initial regeneration of Section 4.2: fit the seeded
+    Gaussians to the view batch with the raised learning rates, no
+    densification, simplify to the `keep` most important Gaussians after
+    `simplify_at` steps, and continue (fresh optimiser state) to `iters`
+    steps. backgrounds: (steps, V, 3) random per-view backgrounds. Returns
+    (final FitState, {"wall_s", "simplify_s", "n_before", "n_after"});
+    wall time from the first step to the last one's completion, including the
+    simplification and the rebuilt state's first capture."""
+    import time
+    import torch
+    from .fit import FitState, boosted_lr
+    lr = lr if lr is not None else boosted_lr()
+    bgt = torch.as_tensor(np.asarray(backgrounds, np.float32)).cuda()
+    V = len(cams["width"])
+    regrown = 0
+
+    def run(st, first, last):
+        # splats grow at the raised rates: the pair capacity starts at 4x the
+        # initial count and is checked every `check_every` steps; a step that
+        # overflowed it (its sort emits nothing, so it renders the background)
+        # is followed by a regrow to the counted need and a new capture
+        nonlocal regrown
+        for it in range(first, last):
+            st.bg.copy_(bgt[it % bgt.shape[0]])
+            st.replay()
+            if (it + 1 - first) % check_every == 0 or it + 1 == last:
+                s = st.check_status()
+                if s == G.GSFIT_ERR_CAPACITY:
+                    st.ensure_capacity(int(int(st.n_instances.item()) * 1.5) + 1024)
+                    st.capture(warmup=0)
+                    regrown += 1
+                elif s != 0:
+                    raise RuntimeError(f"device status {s} during the regeneration")
+
+    check_every = 50
+    st = FitState(gaussians, cams, bg=np.zeros((V, 3), np.float32), lr=lr, **state_kw)
+    st.ensure_capacity(4 * st.count_instances())
+    st.target_rgb.copy_(torch.as_tensor(target_rgb).reshape(-1))
+    st.target_alpha.copy_(torch.as_tensor(target_alpha).reshape(-1))
+    n_before = st.n
+    st.capture(warmup=0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    run(st, 0, min(simplify_at, iters))
+    t1 = time.perf_counter()
+    if iters > simplify_at:
+        kept = st.simplified_params(keep)
+        st2 = FitState.from_params(kept, st.sh_degree, cams, bg=np.zeros((V, 3), np.float32), lr=lr, **state_kw)
+        st2.ensure_capacity(4 * st2.count_instances())
+        st2.target_rgb.copy_(st.target_rgb)
+        st2.target_alpha.copy_(st.target_alpha)
+        del st
+        st = st2
+        st.capture(warmup=0)
+        t2 = time.perf_counter()
+        run(st, simplify_at, iters)
+    else:
+        t2 = t1
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    return st, {"wall_s": t3 - t0, "simplify_s": t2 - t1, "n_before": n_before, "n_after": st.n,
+                "capacity_regrows": regrown}

@@ -76,3 +76,24 @@ def test_restart_keeps_gaussians_and_discards_optimizer_state():
     assert torch.equal(st.params, params)
     assert float(st.m.abs().max()) == 0.0 and float(st.v.abs().max()) == 0.0
     assert int(st.step_count.item()) == 0
+
+
+def test_regeneration_schedule_simplifies_and_keeps_fitting():
+    from paper_2601_22026_gb300 import refine
+    from paper_2601_22026_gb300.fit import FitState
+    cams = scenes.periphery_batch_cameras(1, n_crops=4, **KW)
+    V = len(cams["width"])
+    zeros = np.zeros((V, 3), np.float32)
+    gs = scenes.random_gaussians(12000, 3, 71, log_scale_mean=-4.0)
+    tgt = FitState(scenes.random_gaussians(12000, 3, 72, log_scale_mean=-4.0), cams, bg=zeros)
+    tgt.forward()
+    before = FitState(gs, cams, bg=zeros)
+    before.target_rgb.copy_(tgt.rgb)
+    p0 = refine.psnr(before)
+    del before
+    st, info = refine.regenerate(gs, cams, tgt.rgb, tgt.alpha, scenes.backgrounds(V, 73, n_steps=64), iters=60,
+                                 simplify_at=20, keep=3000)
+    assert info["n_before"] == 12000 and 3000 <= info["n_after"] <= 3100
+    assert st.n == info["n_after"] and info["wall_s"] > 0
+    st.bg.zero_()
+    assert refine.psnr(st) > p0 + 0.5
