@@ -477,6 +477,35 @@ int gsfit_simplify(const float* params, int32_t n, int32_t n_planes, const float
                    float* params_out, uint32_t* n_out, void* ws, size_t ws_bytes, cudaStream_t stream);
 
 /*
+ * gsfit_first_hit -- first-hit point-cloud seeding (Section 4.1): rays cast
+ * toward the CT volume from the given viewpoints; each ray keeps its first
+ * significant hit, the first point where the transfer function's opacity of
+ * the (trilinearly interpolated) volume reaches alpha_min.
+ *   Volume: int16 HU values hu[z][y][x], nx * ny * nz voxels of edge `voxel`,
+ *   corner at `origin` (HOST 3 floats); voxel centres at origin + (i + 0.5)
+ *   voxel; samples between centres interpolate trilinearly, clamped at the
+ *   faces. Transfer function: n_knots (<= 8) HOST rows (HU, r, g, b, alpha),
+ *   HU increasing; linear between knots, clamped outside.
+ *   Rays: per view, a rays_x x rays_y grid over the image (ray (i, j) through
+ *   pixel ((i + 0.5) W / rays_x - 0.5, (j + 0.5) H / rays_y - 0.5) of the
+ *   pinhole camera), from the camera centre, clipped to the volume's box and
+ *   sampled every `step` (world units) from the entry point; at the first
+ *   sample whose opacity reaches alpha_min the crossing is refined by 12
+ *   bisection steps between it and the previous sample (or the entry point).
+ *   Ray r = (v * rays_y + j) * rays_x + i writes points[r] = (x, y, z, 1) at
+ *   the hit, (0, 0, 0, 0) for a miss, and colour[r] = the transfer function's
+ *   (r, g, b, alpha) there (0 for a miss). The paper colours the points by
+ *   path tracing; that is not part of this library.
+ * Arguments: hu, cams (n_views cameras), points, colour: device; points and
+ *   colour 4 * n_views * rays_x * rays_y floats, 16-byte aligned; step > 0.
+ * Errors: GSFIT_ERR_INVALID_ARG, GSFIT_ERR_CUDA.
+ */
+int gsfit_first_hit(const int16_t* hu, int32_t nx, int32_t ny, int32_t nz, const float* origin, float voxel,
+                    const float* tf_knots, int32_t n_knots, const gsfit_camera* cams, int32_t n_views,
+                    int32_t rays_x, int32_t rays_y, float step, float alpha_min, float* points, float* colour,
+                    cudaStream_t stream);
+
+/*
  * gsfit_reproject -- depth-guided reprojection of a foveal image to a newer
  * head pose (Section 4.3, Eqs. 2-4), as a headless kernel writing device
  * buffers instead of deforming a mesh in a viewer shader.

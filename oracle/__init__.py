@@ -400,3 +400,99 @@ def simplify(gs: dict, importance, keep: int) -> tuple[dict, np.ndarray]:
         thr = np.sort(imp)[::-1][keep - 1]
         idx = np.flatnonzero(imp >= thr)
     return {k: np.asarray(v)[idx] for k, v in gs.items()}, idx
+
+
+def first_hit(vol, origin, voxel: float, knots, cams: dict, rays_x: int, rays_y: int, step: float,
+              alpha_min: float) -> dict:
+    """Section 4.1 first-hit seeding, in float64: per view a rays_x x rays_y
+    grid of rays from the camera centre through pixel ((i + 0.5) W / rays_x -
+    0.5, (j + 0.5) H / rays_y - 0.5); clipped to the volume's box; samples at
+    t0 + k step (k = 0 .. floor((t1 - t0) / step)); the first sample whose
+    transfer-function opacity of the trilinear HU field (voxel centres at
+    origin + (i + 0.5) voxel, indices clamped at the faces) reaches alpha_min
+    is refined by bisection against the previous sample (or the entry point).
+    Returns points (R, 4: x, y, z, hit), colour (R, 4) and `ambiguous` rays
+    whose float32 march could decide differently (a sample's opacity within
+    1e-4 of alpha_min, or a sample count within rounding of the exit)."""
+    vol = np.asarray(vol)
+    nz, ny, nx = vol.shape
+    kn = np.asarray(knots, np.float64)
+    org = np.asarray(origin, np.float64)
+    lo, hi = org, org + voxel * np.array([nx, ny, nz], np.float64)
+
+    def hu_at(p):  # p (R, 3) -> trilinear HU
+        c = (p - org) / voxel - 0.5
+        f = np.floor(c)
+        t = c - f
+        i0 = f.astype(np.int64)
+        out = np.zeros(len(p))
+        for dz in (0, 1):
+            for dy in (0, 1):
+                for dx in (0, 1):
+                    w = (t[:, 0] if dx else 1 - t[:, 0]) * (t[:, 1] if dy else 1 - t[:, 1]) * \
+                        (t[:, 2] if dz else 1 - t[:, 2])
+                    ix = np.clip(i0[:, 0] + dx, 0, nx - 1)
+                    iy = np.clip(i0[:, 1] + dy, 0, ny - 1)
+                    iz = np.clip(i0[:, 2] + dz, 0, nz - 1)
+                    out += w * vol[iz, iy, ix]
+        return out
+
+    def tf(hu, c):
+        return np.interp(hu, kn[:, 0], kn[:, c])
+
+    pts, cols, amb = [], [], []
+    for v in range(len(cams["width"])):
+        W, H = float(cams["width"][v]), float(cams["height"][v])
+        R = np.asarray(cams["viewmat"][v], np.float64).reshape(3, 4)[:, :3]
+        j, i = np.divmod(np.arange(rays_x * rays_y), rays_x)
+        u = (i + 0.5) * W / rays_x - 0.5
+        w = (j + 0.5) * H / rays_y - 0.5
+        dc = np.stack([(u - float(cams["cx"][v])) / float(cams["fx"][v]),
+                       (w - float(cams["cy"][v])) / float(cams["fy"][v]), np.ones_like(u)], 1)
+        d = dc @ R
+        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        o = np.asarray(cams["campos"][v], np.float64)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            ta = (lo - o) / d
+            tb = (hi - o) / d
+        t0 = np.maximum(np.nanmax(np.where(d != 0, np.minimum(ta, tb), -np.inf), axis=1), 0.0)
+        t1 = np.nanmin(np.where(d != 0, np.maximum(ta, tb), np.inf), axis=1)
+        inside_par = np.all(np.where(d == 0, (o >= lo) & (o <= hi), True), axis=1)
+        live = inside_par & (t0 <= t1)
+        n_s = np.where(live, np.floor((t1 - t0) / step) + 1, 0).astype(np.int64)
+        frac = (t1 - t0) / step
+        a_flag = live & (np.abs(frac - np.round(frac)) < 1e-4)
+        n = len(u)
+        hit_t = np.full(n, np.nan)
+        prev_t = t0.copy()
+        done = ~live
+        for k in range(int(n_s.max()) if n > 0 else 0):
+            act = ~done & (k < n_s)
+            if not act.any():
+                break
+            t = t0 + k * step
+            a = tf(hu_at(o + t[act, None] * d[act]), 4)
+            a_flag[np.flatnonzero(act)[np.abs(a - alpha_min) < 1e-4]] = True
+            idx = np.flatnonzero(act)
+            got = idx[a >= alpha_min]
+            hit_t[got] = t[got]
+            done[got] = True
+            prev_t[idx[a < alpha_min]] = t[idx[a < alpha_min]]
+            done |= ~done & (k + 1 >= n_s)
+        hit = ~np.isnan(hit_t)
+        a_lo, b_hi = prev_t[hit], hit_t[hit]
+        for _ in range(50):
+            m = 0.5 * (a_lo + b_hi)
+            up = tf(hu_at(o + m[:, None] * d[hit]), 4) >= alpha_min
+            b_hi = np.where(up, m, b_hi)
+            a_lo = np.where(up, a_lo, m)
+        p = np.zeros((n, 4))
+        c = np.zeros((n, 4))
+        hp = o + b_hi[:, None] * d[hit]
+        p[hit, :3], p[hit, 3] = hp, 1.0
+        hu_h = hu_at(hp)
+        c[hit] = np.stack([tf(hu_h, 1), tf(hu_h, 2), tf(hu_h, 3), tf(hu_h, 4)], 1)
+        pts.append(p)
+        cols.append(c)
+        amb.append(a_flag)
+    return {"points": np.concatenate(pts), "colour": np.concatenate(cols), "ambiguous": np.concatenate(amb)}

@@ -85,6 +85,8 @@ SIGNATURES = {
                                                _P, _P]),
     "gsfit_simplify_workspace_size": (_size, [_i32]),
     "gsfit_simplify": (ctypes.c_int, [_P, _i32, _i32, _P, _i32, _P, _P, _P, _size, _P]),
+    "gsfit_first_hit": (ctypes.c_int, [_P, _i32, _i32, _i32, _P, _f32, _P, _i32, _P, _i32, _i32, _i32, _f32, _f32,
+                                       _P, _P, _P]),
     "gsfit_reproject": (ctypes.c_int, [_P, _P, _i32, _i32, _P, _P, _P, _i32, _i32, _P, _P, _P, _P, _P]),
 }
 
@@ -431,3 +433,15 @@ def gsfit_simplify(params, n, n_planes, importance, keep, params_out, n_out, ws,
     _check(load().gsfit_simplify(_ptr(params), n, n_planes, _ptr(importance), int(keep), _ptr(params_out),
                                  _ptr(n_out), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)),
            "gsfit_simplify")
+
+
+def gsfit_first_hit(hu, nx, ny, nz, origin, voxel, tf_knots, cams_dev, n_views, rays_x, rays_y, step, alpha_min,
+                    points, colour, stream=None):
+    """First-hit seeding rays (Section 4.1); origin and tf_knots are host arrays."""
+    o = np.ascontiguousarray(origin, dtype=np.float32).reshape(3)
+    k = np.ascontiguousarray(tf_knots, dtype=np.float32).reshape(-1, 5)
+    _check(load().gsfit_first_hit(_ptr(hu), int(nx), int(ny), int(nz), o.ctypes.data_as(_P), float(voxel),
+                                  k.ctypes.data_as(_P), int(k.shape[0]), _ptr(cams_dev), int(n_views), int(rays_x),
+                                  int(rays_y), float(step), float(alpha_min), _ptr(points), _ptr(colour),
+                                  _stream(stream)),
+           "gsfit_first_hit")

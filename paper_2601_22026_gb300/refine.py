@@ -21,6 +21,51 @@ import numpy as np
 from . import gsfit as G
 
 
+SH_Y00 = 0.28209479177387814  # 1 / (2 sqrt(pi)), the constant SH basis function
+
+
+def first_hit_points(vol: np.ndarray, origin, voxel: float, tf_knots, cams: dict, rays_x: int, rays_y: int,
+                     step: float | None = None, alpha_min: float = 0.3):
+    """First-hit seeding rays (Section 4.1) through gsfit_first_hit: the
+    volume vol[z][y][x] (int16 HU) seen from the given cameras. Returns host
+    (points (R, 4), colour (R, 4)) and the kernel's time in ms."""
+    import torch
+    nz, ny, nx = vol.shape
+    table = G.camera_table(cams)
+    cams_dev = G.cameras_to_device(table)
+    hu = torch.from_numpy(np.ascontiguousarray(vol, dtype=np.int16).reshape(-1)).cuda()
+    n = table.n_views * rays_x * rays_y
+    pts = torch.empty(4 * n, device="cuda")
+    col = torch.empty(4 * n, device="cuda")
+    step = 0.5 * voxel if step is None else step
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    G.gsfit_first_hit(hu, nx, ny, nz, origin, voxel, tf_knots, cams_dev, table.n_views, rays_x, rays_y, step,
+                      alpha_min, pts, col)
+    b.record()
+    torch.cuda.synchronize()
+    return pts.cpu().numpy().reshape(-1, 4), col.cpu().numpy().reshape(-1, 4), a.elapsed_time(b)
+
+
+def gaussians_from_hits(points: np.ndarray, colour: np.ndarray, voxel: float, sh_degree: int = 3) -> dict:
+    """One Gaussian per hit: mean at the hit, isotropic scale of one voxel,
+    identity rotation, opacity and base colour from the transfer function at
+    the hit (opacity logit = logit(clamp(alpha, 0.01, 0.99))), higher SH bands
+    zero -- the starting point the optimisation refines."""
+    hit = points[:, 3] > 0
+    n = int(hit.sum())
+    rgba = colour[hit].astype(np.float64)
+    a = np.clip(rgba[:, 3], 0.01, 0.99)
+    K = (sh_degree + 1) ** 2
+    sh = np.zeros((n, K, 3), np.float32)
+    sh[:, 0, :] = (rgba[:, :3] - 0.5) / SH_Y00
+    return {"means": points[hit, :3].astype(np.float32),
+            "quats": np.tile(np.array([1.0, 0.0, 0.0, 0.0], np.float32), (n, 1)),
+            "log_scales": np.full((n, 3), np.log(voxel), np.float32),
+            "opacity_logits": np.log(a / (1.0 - a)).astype(np.float32),
+            "sh": sh}
+
+
 def camera_forward(cams: dict, v: int) -> np.ndarray:
     """World-space viewing direction of view v (third row of the rotation)."""
     return np.asarray(cams["viewmat"][v], np.float64).reshape(3, 4)[2, :3].copy()
