@@ -182,6 +182,19 @@ def stage_bytes(st, n_inst: int, n_vis: int, tile_passes: int) -> dict:
 TIMED_STAGES = ("project", "bin_sort", "render_fwd", "loss", "blend_bwd", "project_bwd", "adam")
 
 
+def aggregate(ms_total: float, steps: int, world: int, device: str = "cuda") -> tuple:
+    """Replicas: every rank timed the same number of steps on its own GPU; the
+    job's time is the slowest rank's, its throughput all ranks' iterations over
+    that time. Returns (ms per step, iterations per second of the job)."""
+    if world > 1:
+        import torch
+        t = torch.tensor([ms_total], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_per_step = ms_total / steps
+    return ms_per_step, world * 1000.0 / ms_per_step
+
+
 def time_stages(st, reps: int) -> dict:
     import torch
     evs = {k: [] for k in TIMED_STAGES}
@@ -603,12 +616,7 @@ def main() -> None:
     barrier()
     ms_total = e0.elapsed_time(e1)
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms_total], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
-    ms_per_step = ms_total / args.steps
-    value = world * 1000.0 / ms_per_step
+    ms_per_step, value = aggregate(ms_total, args.steps, world, "cuda")
     status = st.check_status()
     if status != 0:
         raise RuntimeError(f"device status {status} after the timed steps")
