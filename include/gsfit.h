@@ -189,7 +189,10 @@ int gsfit_view_is_novel(const float* pos_new, const float* dir_new, const float*
  *   campos), real SH with Condon-Shortley phase, m = -l..l per band.
  *   Depth, centre and rectangle are computed with a fixed order of correctly
  *   rounded float32 operations (no contraction) so that keys are
- *   reproducible.
+ *   reproducible. A Gaussian with non-finite parameters is culled in every
+ *   view (a NaN position, scale or rotation fails the depth or determinant
+ *   test; a non-finite opacity or colour is culled explicitly), so it neither
+ *   renders nor receives gradients and the rest of the set is unaffected.
  * Arguments: g (device params), cams (device, n_views records laid out by
  *   gsfit_camera_layout), out (device arrays of n_views * n records each).
  * Errors: GSFIT_ERR_INVALID_ARG for null pointers, n <= 0, bad degree or V;
@@ -534,6 +537,21 @@ int gsfit_first_hit(const int16_t* hu, int32_t nx, int32_t ny, int32_t nz, const
 int gsfit_reproject(const float* rgb, const float* depth, int32_t width, int32_t height, const float* inv_pv_old,
                     const float* pos_old, const float* pv_new, int32_t out_w, int32_t out_h, float* clip,
                     unsigned long long* zbuf, float* out_rgb, uint8_t* covered, cudaStream_t stream);
+
+/*
+ * Diagnostics of the bounded device waits (failure detection without a GPU
+ * fault). gsfit_selftest_wait_timeout launches threads that wait, as the
+ * compositing kernels' pixel and producer warps do, on a shared-memory
+ * mbarrier phase that never completes, giving up after limit_cycles clock
+ * cycles; gsfit_selftest_lookback_timeout polls, as the radix pass's
+ * decoupled look-back does, a device word (a zeroed uint32 the caller
+ * provides) that nothing sets, giving up after `polls` polls of ~100 ns.
+ * Both write GSFIT_ERR_TIMEOUT to *status (device int32) and return; the
+ * context stays usable.
+ * Errors: GSFIT_ERR_INVALID_ARG, GSFIT_ERR_CUDA.
+ */
+int gsfit_selftest_wait_timeout(int64_t limit_cycles, int32_t* status, cudaStream_t stream);
+int gsfit_selftest_lookback_timeout(uint32_t* word, int32_t polls, int32_t* status, cudaStream_t stream);
 
 #ifdef __cplusplus
 }

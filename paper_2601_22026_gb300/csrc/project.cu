@@ -277,6 +277,11 @@ __global__ void __launch_bounds__(256) project_kernel(const float4* __restrict__
             for (int k = 0; k < K; ++k) acc += Y[k] * sh[3 * k + ch];
             col[ch] = acc + 0.5f;
         }
+        if (!(opacity >= 0.0f) || !isfinite(col[0] + col[1] + col[2])) {  // non-finite parameters: culled
+            xyd[r] = make_float4(u, w, vg.tz, 0.f);
+            tiles[r] = 0u;
+            continue;
+        }
         const float mask = (col[0] < 0.f ? 1.f : 0.f) + (col[1] < 0.f ? 2.f : 0.f) + (col[2] < 0.f ? 4.f : 0.f);
         xyd[r] = make_float4(u, w, vg.tz, radius);
         conic[r] = make_float4(vg.c * inv_det, -vg.b * inv_det, vg.a * inv_det, opacity);

@@ -198,16 +198,26 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* b, uint32_t pa
 }
 // Waits for the completion of the barrier phase of the given parity; false
 // (and the status word set) if it does not complete within kWaitCycles.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* b, uint32_t parity, int32_t* status) {
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, uint32_t parity, int32_t* status,
+                                          long long limit = kWaitCycles) {
     if (mbar_try_wait(b, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(b, parity)) {
-        if (clock64() - t0 > kWaitCycles) {
+        if (clock64() - t0 > limit) {
             if (status) atomicExch(status, GSFIT_ERR_TIMEOUT);
             return false;
         }
     }
     return true;
+}
+
+// Diagnostic: each thread waits on an mbarrier that expects one arrival no
+// one makes, with a limit of `limit` clock cycles.
+__global__ void wait_selftest_kernel(long long limit, int32_t* status) {
+    __shared__ unsigned long long bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    mbar_wait(&bar, 0, status, limit);
 }
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -940,5 +950,12 @@ extern "C" int gsfit_render_autotune(const gsfit_proj* proj, const gsfit_camera*
     best->tile = tile;
     best->batch = best_depth;
     best->reserved[0] = best->reserved[1] = 0;
+    return GSFIT_OK;
+}
+
+extern "C" int gsfit_selftest_wait_timeout(int64_t limit_cycles, int32_t* status, cudaStream_t stream) {
+    if (!status || limit_cycles < 1) return GSFIT_ERR_INVALID_ARG;
+    wait_selftest_kernel<<<1, 64, 0, stream>>>((long long)limit_cycles, status);
+    GSFIT_LAUNCH_CHECK();
     return GSFIT_OK;
 }

@@ -290,6 +290,27 @@ __global__ void __launch_bounds__(kScanThreads) emit_kernel(const unsigned long 
     }
 }
 
+// Waits until a look-back word carries a flag (aggregate or inclusive prefix)
+// and returns it in f; false, with GSFIT_ERR_TIMEOUT in the status word, after
+// `limit` polls of ~100 ns.
+__device__ __forceinline__ bool lookback_poll(const uint32_t* word, uint32_t& f, int32_t* status, int limit) {
+    for (int spins = 0;; ++spins) {
+        f = *reinterpret_cast<const volatile uint32_t*>(word);
+        if (f & (kFlagInc | kFlagAgg)) return true;
+        if (spins >= limit) {
+            if (status) atomicExch(status, GSFIT_ERR_TIMEOUT);
+            return false;
+        }
+        __nanosleep(100);
+    }
+}
+
+// Diagnostic: polls a look-back word nothing will ever set.
+__global__ void lookback_selftest_kernel(const uint32_t* word, int limit, int32_t* status) {
+    uint32_t f;
+    lookback_poll(word, f, status, limit);
+}
+
 struct OnesweepSmem {
     unsigned long long keys[kPart];
     uint32_t vals[kPart];
@@ -377,23 +398,12 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(const unsigne
     uint32_t excl = 0;
     if (part > 0) {
         int p = (int)part - 1;
-        int spins = 0;
         while (p >= 0) {
-            const uint32_t f = *((volatile uint32_t*)&lb[(size_t)p * kRadix + d]);
-            if (f & kFlagInc) {
-                excl += f & kValMask;
-                break;
-            }
-            if (f & kFlagAgg) {
-                excl += f & kValMask;
-                --p;
-                continue;
-            }
-            if (++spins > kSpinLimit) {
-                atomicExch(status, GSFIT_ERR_TIMEOUT);
-                break;
-            }
-            __nanosleep(100);
+            uint32_t f;
+            if (!lookback_poll(&lb[(size_t)p * kRadix + d], f, status, kSpinLimit)) break;  // timed out
+            excl += f & kValMask;
+            if (f & kFlagInc) break;
+            --p;  // an aggregate: keep looking back
         }
         atomicExch(&lb[(size_t)part * kRadix + d], kFlagInc | (excl + dcount));
     }
@@ -617,5 +627,12 @@ extern "C" int gsfit_bin_sort(const gsfit_proj* proj, const gsfit_camera* cams, 
         order_scatter_kernel<<<ob, 256, 0, stream>>>(ranges, total_tiles, ctl, tile_order);
         GSFIT_LAUNCH_CHECK();
     }
+    return GSFIT_OK;
+}
+
+extern "C" int gsfit_selftest_lookback_timeout(uint32_t* word, int32_t polls, int32_t* status, cudaStream_t stream) {
+    if (!word || !status || polls < 1) return GSFIT_ERR_INVALID_ARG;
+    lookback_selftest_kernel<<<1, 32, 0, stream>>>(word, polls, status);
+    GSFIT_LAUNCH_CHECK();
     return GSFIT_OK;
 }

@@ -90,6 +90,27 @@ class FitState:
         st.ensure_capacity(kw.get("capacity"))
         return st
 
+    def save(self, path) -> None:
+        """Checkpoint: parameters, Adam moments and step count as raw arrays
+        (numpy .npz; syncs)."""
+        np.savez(path, params=self.params.cpu().numpy(), m=self.m.cpu().numpy(), v=self.v.cpu().numpy(),
+                 step=self.step_count.cpu().numpy(), sh_degree=np.int32(self.sh_degree))
+
+    @classmethod
+    def resume(cls, path, cams: dict, *, reset_optimizer: bool = False, **kw):
+        """A state from a checkpoint on the given views. reset_optimizer:
+        reload the Gaussians but discard the optimiser state, as the paper's
+        periodic restarts do (Section 4.2)."""
+        import torch
+        d = np.load(path)
+        st = cls.from_params(torch.from_numpy(d["params"]).to(kw.get("device", "cuda")), int(d["sh_degree"]), cams,
+                             **kw)
+        if not reset_optimizer:
+            st.m.copy_(torch.from_numpy(d["m"]))
+            st.v.copy_(torch.from_numpy(d["v"]))
+            st.step_count.copy_(torch.from_numpy(d["step"]))
+        return st
+
     def importance(self):
         """Per-Gaussian blend-weight importance over the current view batch
         (one forward pass with gsfit_render_importance; no synchronisation)."""

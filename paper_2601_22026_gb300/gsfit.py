@@ -87,6 +87,8 @@ SIGNATURES = {
     "gsfit_simplify": (ctypes.c_int, [_P, _i32, _i32, _P, _i32, _P, _P, _P, _size, _P]),
     "gsfit_first_hit": (ctypes.c_int, [_P, _i32, _i32, _i32, _P, _f32, _P, _i32, _P, _i32, _i32, _i32, _f32, _f32,
                                        _P, _P, _P]),
+    "gsfit_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_int64, _P, _P]),
+    "gsfit_selftest_lookback_timeout": (ctypes.c_int, [_P, _i32, _P, _P]),
     "gsfit_reproject": (ctypes.c_int, [_P, _P, _i32, _i32, _P, _P, _P, _i32, _i32, _P, _P, _P, _P, _P]),
 }
 
@@ -445,3 +447,13 @@ def gsfit_first_hit(hu, nx, ny, nz, origin, voxel, tf_knots, cams_dev, n_views, 
                                   int(rays_y), float(step), float(alpha_min), _ptr(points), _ptr(colour),
                                   _stream(stream)),
            "gsfit_first_hit")
+
+
+def gsfit_selftest_wait_timeout(limit_cycles, status, stream=None):
+    _check(load().gsfit_selftest_wait_timeout(int(limit_cycles), _ptr(status), _stream(stream)),
+           "gsfit_selftest_wait_timeout")
+
+
+def gsfit_selftest_lookback_timeout(word, polls, status, stream=None):
+    _check(load().gsfit_selftest_lookback_timeout(_ptr(word), int(polls), _ptr(status), _stream(stream)),
+           "gsfit_selftest_lookback_timeout")

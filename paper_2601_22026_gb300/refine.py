@@ -120,13 +120,27 @@ def view_state(src, cams: dict, bg=None, **kw):
     return st
 
 
-def psnr(eval_state) -> float:
-    """PSNR (dB) of eval_state's render against its targets, over all colour
-    pixels of its view batch (a measurement; not part of the fit step)."""
+def psnr(eval_state, masked: bool = True) -> float:
+    """PSNR (dB) of eval_state's render against its targets over its view
+    batch (a measurement; not part of the fit step). masked: the paper's
+    masked PSNR (Section 5), only pixels whose alpha is non-zero in the target
+    or the render; otherwise every pixel."""
     import torch
     eval_state.forward()
-    mse = torch.mean((eval_state.rgb - eval_state.target_rgb) ** 2).item()
-    return float(10.0 * np.log10(1.0 / max(mse, 1e-20)))
+    if not masked:
+        mse = torch.mean((eval_state.rgb - eval_state.target_rgb) ** 2).item()
+        return float(10.0 * np.log10(1.0 / max(mse, 1e-20)))
+    se, count = 0.0, 0
+    off = 0
+    for v in range(eval_state.V):
+        c = eval_state.table.host[v]
+        P = int(c.width) * int(c.height)
+        m = (eval_state.alpha[off:off + P] > 0) | (eval_state.target_alpha[off:off + P] > 0)
+        d = (eval_state.rgb[3 * off:3 * (off + P)] - eval_state.target_rgb[3 * off:3 * (off + P)]).view(3, P)
+        se += float((d[:, m] ** 2).sum().item())
+        count += 3 * int(m.sum().item())
+        off += P
+    return float(10.0 * np.log10(count / max(se, 1e-20))) if count else float("inf")
 
 
 class ContinuousRefinement:

@@ -97,3 +97,35 @@ def test_regeneration_schedule_simplifies_and_keeps_fitting():
     assert st.n == info["n_after"] and info["wall_s"] > 0
     st.bg.zero_()
     assert refine.psnr(st) > p0 + 0.5
+
+
+@pytest.mark.parametrize("reset", [False, True])
+def test_checkpoint_resume(tmp_path, reset):
+    from paper_2601_22026_gb300.fit import FitState, boosted_lr
+    cams = scenes.periphery_batch_cameras(2, n_crops=3, **KW)
+    V = len(cams["width"])
+    zeros = np.zeros((V, 3), np.float32)
+    tgt = FitState(scenes.random_gaussians(5000, 3, 82, log_scale_mean=-4.0), cams, bg=zeros)
+    tgt.forward()
+    a = FitState(scenes.random_gaussians(5000, 3, 81, log_scale_mean=-4.0), cams, bg=zeros, lr=boosted_lr())
+    a.target_rgb.copy_(tgt.rgb)
+    a.target_alpha.copy_(tgt.alpha)
+    for _ in range(3):
+        a.step()
+    path = tmp_path / "ckpt.npz"
+    a.save(path)
+    b = FitState.resume(path, cams, reset_optimizer=reset, bg=zeros, lr=boosted_lr())
+    b.target_rgb.copy_(tgt.rgb)
+    b.target_alpha.copy_(tgt.alpha)
+    torch.cuda.synchronize()
+    assert torch.equal(a.params, b.params)
+    if reset:
+        assert float(b.m.abs().max()) == 0.0 and int(b.step_count.item()) == 0
+    else:
+        assert torch.equal(a.m, b.m) and torch.equal(a.v, b.v) and int(b.step_count.item()) == 3
+        for _ in range(2):
+            a.step()
+            b.step()
+        torch.cuda.synchronize()
+        # the same updates (up to the order of the adjoint's float atomics)
+        torch.testing.assert_close(b.params, a.params, rtol=1e-4, atol=1e-6)
