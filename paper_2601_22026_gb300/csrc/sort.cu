@@ -20,15 +20,19 @@
 //      stores coalesce. Records are now in (depth, record index) order.
 //   4. reduce_sorted_kernel / scan_blocks_kernel / emit_kernel: pair offsets
 //      in that order, then the pairs (tile id << 32 | depth, Gaussian index),
-//      with the tile-digit histograms.
+//      with the tile-digit histograms; each warp deals its records' pairs out
+//      to its lanes 32 at a time, so stores coalesce whatever the splat sizes.
 //   5. onesweep_kernel over the significant tile-id bits only (two passes for
 //      up to 65536 tiles): being stable, it leaves equal tile ids in (depth,
 //      record index) order, the unique order by (key, view, index).
-//   6. ranges_kernel: [first, last+1) of each tile from adjacent keys.
+//   6. ranges_kernel: [first, last+1) of each tile from adjacent keys, and
+//      the heavy-first tile order for the compositing kernels.
 // Sorting records instead of pairs by depth moves 24 bytes per record per
 // depth pass instead of 24 bytes per pair (a record covers several tiles).
 // Counts never leave the device, so the sequence can be captured in a CUDA
 // graph; launches are sized by capacity and idle CTAs exit at once.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace gsfit {
@@ -174,7 +178,10 @@ __global__ void __launch_bounds__(1024) scan_blocks_kernel(uint32_t* __restrict_
 
 // Binned records in record order as (tile count << 32 | depth bits, record
 // index), with the depth-digit histograms; clears the look-back tables and
-// the tile ranges for this sort.
+// the tile ranges for this sort. Warp w of a block takes the block's records
+// [32 kScanItems w, 32 kScanItems (w + 1)) as kScanItems rows of 32 and
+// places each row's binned records with a ballot; one block-wide step orders
+// the warps.
 __global__ void __launch_bounds__(kScanThreads) compact_kernel(const uint32_t* __restrict__ tiles,
                                                                const float4* __restrict__ xyd, long long n_rec,
                                                                const uint32_t* __restrict__ rec_sums,
@@ -183,7 +190,7 @@ __global__ void __launch_bounds__(kScanThreads) compact_kernel(const uint32_t* _
                                                                uint32_t* __restrict__ rvals,
                                                                uint32_t* __restrict__ lookback, long long lookback_words,
                                                                uint32_t* __restrict__ ranges, long long range_words) {
-    __shared__ uint32_t s_warp[8];
+    __shared__ uint32_t s_wtot[kScanThreads / 32];
     __shared__ uint32_t s_hist[kDepthPasses][kRadix];
     for (int k = threadIdx.x; k < kDepthPasses * kRadix; k += blockDim.x) (&s_hist[0][0])[k] = 0u;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -192,21 +199,41 @@ __global__ void __launch_bounds__(kScanThreads) compact_kernel(const uint32_t* _
     for (long long k = tid; k < range_words; k += stride) ranges[k] = 0u;
     __syncthreads();
     if (ctl->n_rec == 0u) return;  // nothing binned, or the capacity was exceeded
-    const long long base = (long long)blockIdx.x * kScanChunk;
-    uint32_t offset = rec_sums[blockIdx.x];
-    for (int j = 0; j < kScanItems; ++j) {
-        const long long r = base + (long long)j * kScanThreads + threadIdx.x;
-        const uint32_t t = r < n_rec ? tiles[r] : 0u;
-        uint32_t row_total;
-        const uint32_t ex = block_excl_scan(t > 0u ? 1u : 0u, s_warp, row_total);
-        if (t > 0u) {
-            const uint32_t depth = __float_as_uint(xyd[r].z);
-            rkeys[offset + ex] = ((unsigned long long)t << 32) | depth;
-            rvals[offset + ex] = (uint32_t)r;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const long long wbase = (long long)blockIdx.x * kScanChunk + (long long)wid * (32 * kScanItems);
+    const float* depth_of = reinterpret_cast<const float*>(xyd) + 2;  // .z of record r at 4 r
+    bool bin[kScanItems];
+    uint32_t depth[kScanItems];
+    uint32_t mine = 0;
 #pragma unroll
-            for (int p = 0; p < kDepthPasses; ++p) atomicAdd(&s_hist[p][(depth >> (8 * p)) & 0xff], 1u);
+    for (int j = 0; j < kScanItems; ++j) {
+        const long long r = wbase + 32 * j + lane;
+        bin[j] = r < n_rec && __ldg(tiles + r) > 0u;
+        mine += bin[j];
+    }
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        const long long r = wbase + 32 * j + lane;
+        depth[j] = bin[j] ? __float_as_uint(__ldg(depth_of + 4 * r)) : 0u;
+    }
+    const uint32_t wtot = __reduce_add_sync(0xffffffffu, mine);
+    if (lane == 0) s_wtot[wid] = wtot;
+    __syncthreads();
+    uint32_t offset = rec_sums[blockIdx.x];
+    for (int w = 0; w < wid; ++w) offset += s_wtot[w];
+    const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        const uint32_t m = __ballot_sync(0xffffffffu, bin[j]);
+        if (bin[j]) {
+            const long long r = wbase + 32 * j + lane;
+            const uint32_t o = offset + __popc(m & lt);
+            rkeys[o] = ((unsigned long long)__ldg(tiles + r) << 32) | depth[j];
+            rvals[o] = (uint32_t)r;
+#pragma unroll
+            for (int p = 0; p < kDepthPasses; ++p) atomicAdd(&s_hist[p][(depth[j] >> (8 * p)) & 0xff], 1u);
         }
-        offset += row_total;
+        offset += __popc(m);
     }
     __syncthreads();
     for (int k = threadIdx.x; k < kDepthPasses * kRadix; k += blockDim.x) {
@@ -236,7 +263,13 @@ __global__ void __launch_bounds__(kScanThreads) reduce_sorted_kernel(const unsig
 }
 
 // Pairs of the depth-sorted records, in that order, with the tile-digit
-// histograms of the n_tile_passes tile passes.
+// histograms of the n_tile_passes tile passes. Warp w of a block takes the
+// block's sorted records [32 kScanItems w, 32 kScanItems (w + 1)) as rows of
+// 32 (one per lane); a row's pairs are dealt out to the lanes 32 at a time
+// (pair k goes to lane k mod 32, which finds the record owning it by binary
+// search over the row's inclusive counts), so every store is coalesced and a
+// large splat does not hold up the other lanes. The next row's record gather
+// is issued before the current row is dealt out.
 __global__ void __launch_bounds__(kScanThreads) emit_kernel(const unsigned long long* __restrict__ rkeys,
                                                             const uint32_t* __restrict__ rvals,
                                                             const float4* __restrict__ xyd, int n, int n_views,
@@ -246,42 +279,85 @@ __global__ void __launch_bounds__(kScanThreads) emit_kernel(const unsigned long 
                                                             unsigned long long* __restrict__ keys,
                                                             uint32_t* __restrict__ vals) {
     extern __shared__ gsfit_camera cams[];
-    __shared__ uint32_t s_warp[8];
+    __shared__ uint32_t s_wtot[kScanThreads / 32];
     __shared__ uint32_t s_hist[kMaxPasses - kDepthPasses][kRadix];
     load_cameras(cams, cams_g, n_views);
     for (int k = threadIdx.x; k < n_tile_passes * kRadix; k += blockDim.x) (&s_hist[0][0])[k] = 0u;
     __syncthreads();
     const uint32_t n_recs = ctl->n_rec;
-    const long long base = (long long)blockIdx.x * kScanChunk;
-    if (base >= n_recs) return;
-    uint32_t offset = sums[blockIdx.x];
+    if ((long long)blockIdx.x * kScanChunk >= (long long)n_recs) return;  // block-uniform
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const long long wbase = (long long)blockIdx.x * kScanChunk + (long long)wid * (32 * kScanItems);
+    uint32_t cnt[kScanItems], rec[kScanItems];
+    uint32_t mine = 0;
+#pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
-        const long long m = base + (long long)j * kScanThreads + threadIdx.x;
-        const bool ok = m < n_recs;
-        const unsigned long long rk = ok ? rkeys[m] : 0ull;
-        const uint32_t t = (uint32_t)(rk >> 32);
-        uint32_t row_total;
-        const uint32_t ex = block_excl_scan(t, s_warp, row_total);
-        if (t > 0u) {
-            const uint32_t r = rvals[m];
-            const int v = (int)(r / (uint32_t)n);
-            const int i = (int)(r - (uint32_t)v * (uint32_t)n);
-            const gsfit_camera& cam = cams[v];
-            const float4 p = xyd[r];
-            const int txn = tiles_x_of(cam);
-            const Rect rc = tile_rect(p.x, p.y, p.w, txn, tiles_y_of(cam), tile_of(cam));
-            const unsigned long long depth = rk & 0xffffffffull;
-            uint32_t o = offset + ex;
-            for (int ty = rc.y0; ty < rc.y1; ++ty)
-                for (int tx = rc.x0; tx < rc.x1; ++tx) {
-                    const uint32_t tile = (uint32_t)(cam.tile_offset + ty * txn + tx);
-                    keys[o] = ((unsigned long long)tile << 32) | depth;
-                    vals[o] = (uint32_t)i;
-                    ++o;
-                    for (int q = 0; q < n_tile_passes; ++q) atomicAdd(&s_hist[q][(tile >> (8 * q)) & 0xff], 1u);
-                }
+        const long long m = wbase + 32 * j + lane;
+        const bool ok = m < (long long)n_recs;
+        cnt[j] = ok ? (uint32_t)(__ldg(rkeys + m) >> 32) : 0u;
+        rec[j] = ok ? __ldg(rvals + m) : 0u;
+        mine += cnt[j];
+    }
+    const uint32_t wtot = __reduce_add_sync(0xffffffffu, mine);
+    if (lane == 0) s_wtot[wid] = wtot;
+    __syncthreads();
+    uint32_t offset = sums[blockIdx.x];
+    for (int w = 0; w < wid; ++w) offset += s_wtot[w];
+    float4 p_next = cnt[0] > 0u ? __ldg(xyd + rec[0]) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        const uint32_t c = cnt[j];
+        uint32_t inc = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
         }
-        offset += row_total;
+        const uint32_t row = __shfl_sync(0xffffffffu, inc, 31);
+        const float4 p = p_next;
+        if (j + 1 < kScanItems && cnt[j + 1] > 0u) p_next = __ldg(xyd + rec[j + 1]);
+        if (row == 0u) continue;  // warp-uniform
+        // this lane's record: first tile id, tiles across the camera, rect width, depth, Gaussian index
+        uint32_t t0 = 0u, txn = 0u, rw = 1u, depth = 0u, gi = 0u;
+        if (c > 0u) {
+            const uint32_t r = rec[j];
+            const uint32_t v = r / (uint32_t)n;
+            gi = r - v * (uint32_t)n;
+            const gsfit_camera& cam = cams[v];
+            const int tx = tiles_x_of(cam);
+            const Rect rc = tile_rect(p.x, p.y, p.w, tx, tiles_y_of(cam), tile_of(cam));
+            txn = (uint32_t)tx;
+            rw = (uint32_t)max(rc.x1 - rc.x0, 1);
+            t0 = (uint32_t)(cam.tile_offset + rc.y0 * tx + rc.x0);
+            depth = (uint32_t)__ldg(rkeys + wbase + 32 * j + lane);
+        }
+        const uint32_t excl = inc - c;
+        for (uint32_t k0 = 0; k0 < row; k0 += 32) {
+            const uint32_t k = k0 + (uint32_t)lane;
+            int owner = 0;  // lanes whose inclusive count is <= k
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const uint32_t x = __shfl_sync(0xffffffffu, inc, owner + step - 1);
+                if (x <= k) owner += step;
+            }
+            const uint32_t o_t0 = __shfl_sync(0xffffffffu, t0, owner);
+            const uint32_t o_txn = __shfl_sync(0xffffffffu, txn, owner);
+            const uint32_t o_rw = __shfl_sync(0xffffffffu, rw, owner);
+            const uint32_t o_depth = __shfl_sync(0xffffffffu, depth, owner);
+            const uint32_t o_gi = __shfl_sync(0xffffffffu, gi, owner);
+            const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, owner);
+            if (k < row) {
+                const uint32_t q = k - o_excl;  // row-major position in the owner's rect
+                uint32_t dy = (uint32_t)((float)q * __frcp_rn((float)o_rw));
+                if (dy * o_rw > q) --dy;  // exact floor(q / rw) after the float estimate
+                else if ((dy + 1u) * o_rw <= q) ++dy;
+                const uint32_t tile = o_t0 + dy * o_txn + (q - dy * o_rw);
+                keys[offset + k] = ((unsigned long long)tile << 32) | o_depth;
+                vals[offset + k] = o_gi;
+                for (int p = 0; p < n_tile_passes; ++p) atomicAdd(&s_hist[p][(tile >> (8 * p)) & 0xff], 1u);
+            }
+        }
+        offset += row;
     }
     __syncthreads();
     for (int k = threadIdx.x; k < n_tile_passes * kRadix; k += blockDim.x) {
@@ -302,6 +378,45 @@ __device__ __forceinline__ bool lookback_poll(const uint32_t* word, uint32_t& f,
             return false;
         }
         __nanosleep(100);
+    }
+}
+
+// Exclusive prefix of digit d over partitions [0, p], looked up kLookWindow
+// partitions per round trip: the window's words are read together and
+// consumed newest first while they carry a flag, up to the first inclusive
+// prefix. A window whose newest word carries no flag is polled again after
+// ~100 ns, at most kSpinLimit times in a row (then GSFIT_ERR_TIMEOUT).
+constexpr int kLookWindow = 8;
+__device__ __forceinline__ void lookback_window(const uint32_t* lb, int p, int d, uint32_t& excl,
+                                                int32_t* status) {
+    int idle = 0;
+    while (p >= 0) {
+        uint32_t f[kLookWindow];
+#pragma unroll
+        for (int w = 0; w < kLookWindow; ++w)
+            f[w] = p - w >= 0 ? *reinterpret_cast<const volatile uint32_t*>(&lb[(size_t)(p - w) * kRadix + d])
+                              : 0u;
+        int used = 0;
+        bool inc = false;
+#pragma unroll
+        for (int w = 0; w < kLookWindow; ++w) {
+            if (used == w && p - w >= 0 && (f[w] & (kFlagInc | kFlagAgg))) {
+                excl += f[w] & kValMask;
+                inc = (f[w] & kFlagInc) != 0u;
+                used = inc ? kLookWindow + 1 : w + 1;  // stop consuming after an inclusive prefix
+            }
+        }
+        if (inc) return;
+        if (used == 0) {
+            if (++idle > kSpinLimit) {
+                if (status) atomicExch(status, GSFIT_ERR_TIMEOUT);
+                return;
+            }
+            __nanosleep(100);
+        } else {
+            idle = 0;
+            p -= used;
+        }
     }
 }
 
@@ -337,6 +452,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(const unsigne
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t n = *n_ptr;
     const uint32_t n_parts = (n + kPart - 1) / kPart;
+    const uint32_t hist_d = ctl->hist[pass][threadIdx.x];  // this pass's count of digit threadIdx.x
     if (threadIdx.x == 0) S.part = atomicAdd(&ctl->part_counter[pass], 1u);
     for (int k = threadIdx.x; k < kSortWarps * (kRadix + 1); k += kSortThreads) (&S.warp_hist[0][0])[k] = 0u;
     __syncthreads();
@@ -357,6 +473,10 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(const unsigne
         k_reg[j] = ok ? keys_in[base + idx] : ~0ull;
         if (ok) S.vals_in[idx] = vals_in[base + idx];
     }
+    // global exclusive offset of digit threadIdx.x over all keys of this pass
+    // (while the loads are in flight)
+    uint32_t htot;
+    S.glob_off[threadIdx.x] = block_excl_scan(hist_d, S.scan_warp, htot);
     // digit of item j; items past the end go to bin kRadix
     auto digit = [&](int j) -> uint32_t {
         const uint32_t idx = (uint32_t)wid * (32 * kSortItems) + j * 32 + lane;
@@ -365,7 +485,15 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(const unsigne
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
         const uint32_t d = digit(j);
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        // lanes holding the same digit: one ballot per digit bit (bit 8 marks
+        // padding), a constant cost where match.any grows with the number of
+        // distinct digits in the warp
+        uint32_t peers = 0xffffffffu;
+#pragma unroll
+        for (int b = 0; b < 9; ++b) {
+            const uint32_t vote = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+            peers &= ((d >> b) & 1u) ? vote : ~vote;
+        }
         const uint32_t cnt = S.warp_hist[wid][d];
         __syncwarp();
         const int leader = 31 - __clz(peers);
@@ -397,20 +525,10 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(const unsigne
     // decoupled look-back over earlier partitions for digit d
     uint32_t excl = 0;
     if (part > 0) {
-        int p = (int)part - 1;
-        while (p >= 0) {
-            uint32_t f;
-            if (!lookback_poll(&lb[(size_t)p * kRadix + d], f, status, kSpinLimit)) break;  // timed out
-            excl += f & kValMask;
-            if (f & kFlagInc) break;
-            --p;  // an aggregate: keep looking back
-        }
+        lookback_window(lb, (int)part - 1, d, excl, status);
         atomicExch(&lb[(size_t)part * kRadix + d], kFlagInc | (excl + dcount));
     }
-    // global exclusive offset of digit d over all keys of this pass
-    uint32_t htot;
-    const uint32_t gexcl = block_excl_scan(ctl->hist[pass][d], S.scan_warp, htot);
-    S.glob_off[d] = gexcl + excl - lstart;
+    S.glob_off[d] += excl - lstart;
     __syncthreads();
 
     // scatter into shared memory in digit order (stable: warp, item, lane order)
@@ -436,16 +554,33 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(const unsigne
     }
 }
 
+// [first, last + 1) of each tile from adjacent sorted keys. A resident grid
+// strides over chunks of 256 kRangeItems keys, kRangeItems per thread
+// (block-striped), with all of a chunk's loads issued before any compare.
+constexpr int kRangeItems = 4;
+constexpr int kRangeBlocksPerSm = 8;
 __global__ void __launch_bounds__(256) ranges_kernel(const unsigned long long* __restrict__ keys,
                                                      const SortCtl* __restrict__ ctl,
                                                      uint32_t* __restrict__ ranges, uint32_t total_tiles) {
     const uint32_t n = ctl->n_sort;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
-        const uint32_t t = (uint32_t)(keys[k] >> 32);
-        if (t >= total_tiles) continue;  // only after a failed sort
-        if (k == 0 || (uint32_t)(keys[k - 1] >> 32) != t) ranges[2 * (size_t)t] = (uint32_t)k;
-        if (k + 1 == n || (uint32_t)(keys[k + 1] >> 32) != t) ranges[2 * (size_t)t + 1] = (uint32_t)(k + 1);
+    const uint32_t* hi = reinterpret_cast<const uint32_t*>(keys) + 1;  // tile id: the upper word of each key
+    for (long long base = (long long)blockIdx.x * (256 * kRangeItems) + threadIdx.x; base < n;
+         base += (long long)gridDim.x * (256 * kRangeItems)) {
+        uint32_t t[kRangeItems], prev[kRangeItems], next[kRangeItems];
+#pragma unroll
+        for (int i = 0; i < kRangeItems; ++i) {
+            const long long k = base + 256 * i;
+            t[i] = k < n ? __ldg(hi + 2 * k) : 0xffffffffu;
+            prev[i] = k < n && k > 0 ? __ldg(hi + 2 * (k - 1)) : 0xffffffffu;
+            next[i] = k + 1 < n ? __ldg(hi + 2 * (k + 1)) : 0xffffffffu;
+        }
+#pragma unroll
+        for (int i = 0; i < kRangeItems; ++i) {
+            const long long k = base + 256 * i;
+            if (k >= n || t[i] >= total_tiles) continue;  // past the end, or only after a failed sort
+            if (k == 0 || prev[i] != t[i]) ranges[2 * (size_t)t[i]] = (uint32_t)k;
+            if (k + 1 == n || next[i] != t[i]) ranges[2 * (size_t)t[i] + 1] = (uint32_t)(k + 1);
+        }
     }
 }
 
@@ -478,10 +613,21 @@ __global__ void __launch_bounds__(256) order_scatter_kernel(const uint32_t* __re
             o += ctl->order_hist[b];
         }
     }
-    __syncthreads();
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total_tiles; t += gridDim.x * blockDim.x) {
-        const int b = length_bucket(ranges, t);
-        tile_order[off[b] + atomicAdd(&ctl->order_fill[b], 1u)] = (uint32_t)t;
+    // per 256 tiles: bucket counts in shared memory, then one global
+    // reservation per (block, bucket)
+    __shared__ uint32_t cnt[32], res[32];
+    for (int t0 = blockIdx.x * blockDim.x; t0 < total_tiles; t0 += gridDim.x * blockDim.x) {
+        if (threadIdx.x < 32) cnt[threadIdx.x] = 0u;
+        __syncthreads();
+        const int t = t0 + threadIdx.x;
+        const int b = t < total_tiles ? length_bucket(ranges, t) : 0;
+        const uint32_t local = t < total_tiles ? atomicAdd(&cnt[b], 1u) : 0u;
+        __syncthreads();
+        if (threadIdx.x < 32 && cnt[threadIdx.x])
+            res[threadIdx.x] = atomicAdd(&ctl->order_fill[threadIdx.x], cnt[threadIdx.x]);
+        __syncthreads();
+        if (t < total_tiles) tile_order[off[b] + res[b] + local] = (uint32_t)t;
+        __syncthreads();
     }
 }
 
@@ -618,7 +764,12 @@ extern "C" int gsfit_bin_sort(const gsfit_proj* proj, const gsfit_camera* cams, 
         std::swap(k_cur, k_nxt);
         std::swap(v_cur, v_nxt);
     }
-    ranges_kernel<<<kHistBlocks, 256, 0, stream>>>(keys_out, ctl, ranges, (uint32_t)total_tiles);
+    int dev = 0, sms = 0;
+    GSFIT_CUDA_CHECK(cudaGetDevice(&dev));
+    GSFIT_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    ranges_kernel<<<(unsigned)std::min<long long>((long long)kRangeBlocksPerSm * sms,
+                                                 (capacity + 256 * kRangeItems - 1) / (256 * kRangeItems)),
+                    256, 0, stream>>>(keys_out, ctl, ranges, (uint32_t)total_tiles);
     GSFIT_LAUNCH_CHECK();
     if (tile_order) {
         const int ob = min(152, (total_tiles + 255) / 256);
