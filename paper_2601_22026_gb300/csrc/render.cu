@@ -459,17 +459,19 @@ __device__ __forceinline__ int reduce9_slot(int lane) {
     return (lane & 1) ? -1 : idx;
 }
 
-// Back-to-front state of one pixel.
+// Back-to-front state of one pixel: T = transmittance behind the current
+// list position; DS = sum_c dL/dC_c (S_c + T_N bg_c) with S_c the colour
+// blended behind it; dAT = dL/dA T_N.
 struct PixBwd {
-    float T, TN, S0, S1, S2, dC0, dC1, dC2, dA;
+    float T, DS, dAT, dC0, dC1, dC2;
     uint32_t last;
 };
 
 // Adjoint of one blend at one pixel (list position pos < last), accumulating
 // the nine per-Gaussian terms g9 = dL/d(u, v, opacity, a', b', c', r, g, b);
 // returns whether the Gaussian was blended here.
-__device__ __forceinline__ bool pix_bwd_step(PixBwd& q, uint32_t pos, float4 co, const float4* colp, float bg0,
-                                             float bg1, float bg2, float dx, float dy, float* g9) {
+__device__ __forceinline__ bool pix_bwd_step(PixBwd& q, uint32_t pos, float4 co, const float4* colp, float dx,
+                                             float dy, float* g9) {
     if (pos >= q.last) return false;
     const float power = splat_power(co, dx, dy);
     if (power > 0.0f) return false;
@@ -482,18 +484,18 @@ __device__ __forceinline__ bool pix_bwd_step(PixBwd& q, uint32_t pos, float4 co,
     // 1 - alpha lies in [0.01, 1): the hardware reciprocal (within 2 ulp)
     // suffices for recovering T
     const float inv = __fdividef(1.0f, one_m);
-    q.T *= inv;  // transmittance in front of this Gaussian
+    const float T_behind = q.T;  // T_{i+1} = T_i (1 - alpha_i)
+    q.T = T_behind * inv;        // T_i, the transmittance in front of this Gaussian
     const float wT = alpha * q.T;
     g9[6] = q.dC0 * wT;
     g9[7] = q.dC1 * wT;
     g9[8] = q.dC2 * wT;
-    // dC/dalpha = T c - (S + T_N bg) / (1 - alpha); dA/dalpha = T_N / (1 - alpha)
-    const float dalpha = (q.dA * q.TN + q.dC0 * (q.T * col.x * one_m - (q.S0 + q.TN * bg0)) +
-                          q.dC1 * (q.T * col.y * one_m - (q.S1 + q.TN * bg1)) +
-                          q.dC2 * (q.T * col.z * one_m - (q.S2 + q.TN * bg2))) * inv;
-    q.S0 += col.x * wT;
-    q.S1 += col.y * wT;
-    q.S2 += col.z * wT;
+    // dC_c/dalpha = T_i c_c - (S_c + T_N bg_c) / (1 - alpha), dA/dalpha =
+    // T_N / (1 - alpha); with T_i (1 - alpha) = T_{i+1} the channel sum is
+    // (T_{i+1} dC.c - DS) / (1 - alpha)
+    const float dCc = q.dC0 * col.x + q.dC1 * col.y + q.dC2 * col.z;
+    const float dalpha = (q.dAT + T_behind * dCc - q.DS) * inv;
+    q.DS += wT * dCc;
     if (a <= kAlphaClamp) {  // the clamped alpha depends on neither opacity nor power
         const float dpow = dalpha * alpha;
         g9[2] = dalpha * G;
@@ -506,8 +508,12 @@ __device__ __forceinline__ bool pix_bwd_step(PixBwd& q, uint32_t pos, float4 co,
     return true;
 }
 
+// Five resident CTAs per SM (45 warps; registers capped at 40 per thread):
+// the adjoint is issue-bound on dependent shared-memory, shuffle and MUFU
+// latencies, and the extra warps hide more of them than the few spilled
+// registers cost.
 template <int TILE, int SLOT>
-__global__ void __launch_bounds__(TileShape<TILE>::kThreads) render_bwd_kernel(
+__global__ void __launch_bounds__(TileShape<TILE>::kThreads, 5) render_bwd_kernel(
     const float4* __restrict__ xyd, const float4* __restrict__ conic, const float4* __restrict__ rgb, int n,
     const gsfit_camera* __restrict__ cams_g, int n_views, const uint32_t* __restrict__ vals,
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ tile_order, const float* __restrict__ bg,
@@ -536,17 +542,19 @@ __global__ void __launch_bounds__(TileShape<TILE>::kThreads) render_bwd_kernel(
     uint32_t wmax = 0;
     if (w < kWarps) {
         c = tile_ctx<TILE>(cams, n_views, t);
-        q.T = 1.f; q.last = 0; q.dC0 = q.dC1 = q.dC2 = q.dA = 0.f;
+        q.T = 1.f; q.last = 0; q.dC0 = q.dC1 = q.dC2 = 0.f;
+        float dA = 0.f;
         if (c.inside) {
             q.T = T_final[c.pix];
             q.last = n_contrib[c.pix];
             q.dC0 = dL_drgb[c.rgb_base];
             q.dC1 = dL_drgb[c.rgb_base + c.plane];
             q.dC2 = dL_drgb[c.rgb_base + 2 * c.plane];
-            q.dA = dL_dalpha[c.pix];
+            dA = dL_dalpha[c.pix];
         }
-        q.TN = q.T;
-        q.S0 = q.S1 = q.S2 = 0.f;
+        const float* bgv = bg + 3 * c.view;
+        q.dAT = dA * q.T;
+        q.DS = q.T * (q.dC0 * bgv[0] + q.dC1 * bgv[1] + q.dC2 * bgv[2]);
         wmax = q.last;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
@@ -572,7 +580,6 @@ __global__ void __launch_bounds__(TileShape<TILE>::kThreads) render_bwd_kernel(
 
     const size_t rec0 = (size_t)c.view * n;
     const float fx = (float)c.px, fy = (float)c.py;
-    const float bg0 = bg[3 * c.view], bg1 = bg[3 * c.view + 1], bg2 = bg[3 * c.view + 2];
     const int slot = reduce9_slot(lane);
     const int slot_off = slot + slot / 3;  // floats (du dv do _ | da db dc _ | dr dg db _ | ....) of a record
     for (int k = 0;; ++k) {
@@ -589,8 +596,7 @@ __global__ void __launch_bounds__(TileShape<TILE>::kThreads) render_bwd_kernel(
                 const int j = s_list[w][i];
                 const float4 p = R.xyd[s][j];
                 float g9[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                const bool hit = pix_bwd_step(q, base + (uint32_t)j, R.co[s][j], &R.col[s][j], bg0, bg1, bg2,
-                                              fx - p.x, fy - p.y, g9);
+                const bool hit = pix_bwd_step(q, base + (uint32_t)j, R.co[s][j], &R.col[s][j], fx - p.x, fy - p.y, g9);
                 if (__any_sync(0xffffffffu, hit)) {
                     const float tot = reduce9(g9, lane);
                     if (slot >= 0) atomicAdd(grad2d + 16 * (rec0 + R.g[s][j]) + slot_off, tot);
