@@ -366,30 +366,26 @@ __global__ void __launch_bounds__(TileShape<TILE>::kThreads) render_fwd_kernel(
             const int nw = ring_compact(R, s, cnt, base, 0xffffffffu, c, s_list[w]);
             for (int i = 0; i < nw; ++i) {
                 const int j = s_list[w][i];
-                float my_w = 0.0f;  // this pixel's blend weight of entry j (importance pass)
-                if (!done) {
-                    const float4 p = R.xyd[s][j];
-                    const float4 co = R.co[s][j];
-                    const float power = splat_power(co, fx - p.x, fy - p.y);
-                    if (power <= 0.0f) {
-                        const float alpha = fminf(kAlphaClamp, co.w * __expf(power));
-                        if (alpha >= kAlphaSkip) {
-                            const float test_T = T * (1.0f - alpha);
-                            if (test_T < kTStop) {
-                                done = true;
-                            } else {
-                                const float4 col = R.col[s][j];
-                                const float wgt = alpha * T;
-                                C0 += col.x * wgt;
-                                C1 += col.y * wgt;
-                                C2 += col.z * wgt;
-                                T = test_T;
-                                last = base + (uint32_t)j + 1u;  // one past this list position
-                                if constexpr (IMP) my_w = wgt;
-                            }
-                        }
-                    }
-                }
+                // branch-free: a lane that is done, or skips this entry
+                // (power > 0, alpha < 1/255), or stops at it (T would drop
+                // below 1e-4) adds a zero weight and keeps its T
+                const float4 p = R.xyd[s][j];
+                const float4 co = R.co[s][j];
+                const float4 col = R.col[s][j];
+                const float power = splat_power(co, fx - p.x, fy - p.y);
+                const float alpha = fminf(kAlphaClamp, co.w * __expf(power));
+                const bool hit = !done && power <= 0.0f && alpha >= kAlphaSkip;
+                const float test_T = T * (1.0f - alpha);
+                const bool stop = hit && test_T < kTStop;
+                const bool blend = hit && !stop;
+                const float wgt = blend ? alpha * T : 0.0f;  // this pixel's blend weight of entry j
+                C0 += col.x * wgt;
+                C1 += col.y * wgt;
+                C2 += col.z * wgt;
+                T = blend ? test_T : T;
+                last = blend ? base + (uint32_t)j + 1u : last;  // one past this list position
+                done = done || stop;
+                [[maybe_unused]] const float my_w = wgt;
                 if constexpr (IMP) {
                     const float sum = warp_sum(my_w);
                     if (lane == 0 && sum != 0.0f) atomicAdd(importance + R.g[s][j], sum);
@@ -467,25 +463,26 @@ struct PixBwd {
     uint32_t last;
 };
 
-// Adjoint of one blend at one pixel (list position pos < last), accumulating
-// the nine per-Gaussian terms g9 = dL/d(u, v, opacity, a', b', c', r, g, b);
-// returns whether the Gaussian was blended here.
+// Adjoint of one blend at one pixel (list position pos < last): writes the
+// nine per-Gaussian terms g9 = dL/d(u, v, opacity, a', b', c', r, g, b) and
+// returns whether the Gaussian was blended here. Branch-free: a lane that
+// does not blend it (past its contributor count, power > 0 or alpha < 1/255,
+// the forward's own tests on the same values) takes alpha = 0, which leaves
+// T and the behind-colour sum unchanged and makes all nine terms zero.
 __device__ __forceinline__ bool pix_bwd_step(PixBwd& q, uint32_t pos, float4 co, const float4* colp, float dx,
                                              float dy, float* g9) {
-    if (pos >= q.last) return false;
     const float power = splat_power(co, dx, dy);
-    if (power > 0.0f) return false;
     const float G = __expf(power);
     const float a = co.w * G;
-    const float alpha = fminf(kAlphaClamp, a);
-    if (alpha < kAlphaSkip) return false;
+    const float alpha_f = fminf(kAlphaClamp, a);
+    const bool hit = pos < q.last && power <= 0.0f && alpha_f >= kAlphaSkip;
+    const float alpha = hit ? alpha_f : 0.0f;
     const float4 col = *colp;
-    const float one_m = 1.0f - alpha;
-    // 1 - alpha lies in [0.01, 1): the hardware reciprocal (within 2 ulp)
+    // 1 - alpha lies in [0.01, 1]: the hardware reciprocal (within 2 ulp)
     // suffices for recovering T
-    const float inv = __fdividef(1.0f, one_m);
-    const float T_behind = q.T;  // T_{i+1} = T_i (1 - alpha_i)
-    q.T = T_behind * inv;        // T_i, the transmittance in front of this Gaussian
+    const float inv = __fdividef(1.0f, 1.0f - alpha);
+    const float T_behind = q.T;               // T_{i+1} = T_i (1 - alpha_i)
+    q.T = hit ? T_behind * inv : T_behind;    // T_i, the transmittance in front of this Gaussian
     const float wT = alpha * q.T;
     g9[6] = q.dC0 * wT;
     g9[7] = q.dC1 * wT;
@@ -494,18 +491,18 @@ __device__ __forceinline__ bool pix_bwd_step(PixBwd& q, uint32_t pos, float4 co,
     // T_N / (1 - alpha); with T_i (1 - alpha) = T_{i+1} the channel sum is
     // (T_{i+1} dC.c - DS) / (1 - alpha)
     const float dCc = q.dC0 * col.x + q.dC1 * col.y + q.dC2 * col.z;
-    const float dalpha = (q.dAT + T_behind * dCc - q.DS) * inv;
+    const float dalpha_f = (q.dAT + T_behind * dCc - q.DS) * inv;
     q.DS += wT * dCc;
-    if (a <= kAlphaClamp) {  // the clamped alpha depends on neither opacity nor power
-        const float dpow = dalpha * alpha;
-        g9[2] = dalpha * G;
-        g9[0] = dpow * (co.x * dx + co.y * dy);
-        g9[1] = dpow * (co.z * dy + co.y * dx);
-        g9[3] = -0.5f * dpow * dx * dx;
-        g9[4] = -dpow * dx * dy;
-        g9[5] = -0.5f * dpow * dy * dy;
-    }
-    return true;
+    // the clamped alpha depends on neither opacity nor power
+    const float dalpha = hit && a <= kAlphaClamp ? dalpha_f : 0.0f;
+    const float dpow = dalpha * alpha;
+    g9[2] = dalpha * G;
+    g9[0] = dpow * (co.x * dx + co.y * dy);
+    g9[1] = dpow * (co.z * dy + co.y * dx);
+    g9[3] = -0.5f * dpow * dx * dx;
+    g9[4] = -dpow * dx * dy;
+    g9[5] = -0.5f * dpow * dy * dy;
+    return hit;
 }
 
 // Five resident CTAs per SM (45 warps; registers capped at 40 per thread):
@@ -595,7 +592,7 @@ __global__ void __launch_bounds__(TileShape<TILE>::kThreads, 5) render_bwd_kerne
             for (int i = nw - 1; i >= 0; --i) {
                 const int j = s_list[w][i];
                 const float4 p = R.xyd[s][j];
-                float g9[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                float g9[9];
                 const bool hit = pix_bwd_step(q, base + (uint32_t)j, R.co[s][j], &R.col[s][j], fx - p.x, fy - p.y, g9);
                 if (__any_sync(0xffffffffu, hit)) {
                     const float tot = reduce9(g9, lane);
