@@ -4,8 +4,10 @@
 //
 // Design: one work item is a 32 x 32 output tile of one colour channel of one
 // view. The item loads render and target over the tile plus a 10-pixel halo
-// into shared memory, forms the five windowed moments on the tile plus a
-// 5-pixel halo with two separable 11-tap passes, evaluates the SSIM map and
+// into shared memory, forms the four windowed moments mu_x, mu_y, E[x^2 +
+// y^2], E[xy] on the tile plus a 5-pixel halo with two separable 11-tap
+// passes (SSIM uses the two variances only through their sum, so one moment
+// of x^2 + y^2 serves both), evaluates the SSIM map and
 // its partials there, and convolves the partials back onto the tile: the
 // gradient of the windowed SSIM never leaves shared memory, so the kernel
 // reads each input pixel once and writes each gradient once. Channel-0 items
@@ -24,7 +26,7 @@ static_assert(kR1 % 3 == 0 && kR1 % 7 == 0, "strip lengths of the stencil passes
 constexpr float kC1 = 0.01f * 0.01f;
 constexpr float kC2 = 0.03f * 0.03f;
 
-// 74 KB: three CTAs per SM. The input region is reused for the SSIM partials
+// 65 KB: three CTAs per SM. The input region is reused for the SSIM partials
 // and the horizontal-pass buffer for the horizontal pass of the partials.
 struct LossSmem {
     union {
@@ -35,7 +37,7 @@ struct LossSmem {
         float part[3][kR1][kR1];     // dSSIM/d(mu_x, E[x^2], E[xy]) on the 42 x 42 region
     } a;
     union {
-        float h[5][kR2][kR1];        // horizontal pass of x, y, x^2, y^2, xy
+        float h[4][kR2][kR1];        // horizontal pass of x, y, x^2 + y^2, xy
         struct {
             float hp[3][kR1][kOut];  // horizontal pass of the partials
             float at[kR2][kR2];      // next item's target alpha (prefetched during the last pass)
@@ -106,14 +108,19 @@ __device__ __forceinline__ void prefetch_item(LossSmem& S, const gsfit_camera* _
     const float* X = rgb + 3ll * cam.pixel_offset + ch * P;
     const float* Yt = t_rgb + 3ll * cam.pixel_offset + ch * P;
     const float* At = t_alpha + cam.pixel_offset;
-    for (int k = threadIdx.x; k < kR2 * kR2; k += kLossThreads) {
-        const int r = k / kR2, c = k - r * kR2;
-        const int gx = ox - 10 + c, gy = oy - 10 + r;
-        const bool ok = gx >= 0 && gx < W && gy >= 0 && gy < H;
-        const long long q = ok ? (long long)gy * W + gx : 0;
-        cp_async4(&S.a.in.x[r][c], X + q, ok);
-        cp_async4(&S.a.in.y[r][c], Yt + q, ok);
-        cp_async4(&S.b.st.at[r][c], At + q, ok);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const bool interior = ox >= 10 && oy >= 10 && ox + kOut + 10 <= W && oy + kOut + 10 <= H;
+    // warp w copies rows w, w + 8, ...; lane l columns l and l + 32
+    for (int r = wid; r < kR2; r += kLossThreads / 32) {
+        const int gy = oy - 10 + r;
+        for (int c = lane; c < kR2; c += 32) {
+            const int gx = ox - 10 + c;
+            const bool ok = interior || (gx >= 0 && gx < W && gy >= 0 && gy < H);
+            const long long q = ok ? (long long)gy * W + gx : 0;
+            cp_async4(&S.a.in.x[r][c], X + q, ok);
+            cp_async4(&S.a.in.y[r][c], Yt + q, ok);
+            cp_async4(&S.b.st.at[r][c], At + q, ok);
+        }
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
@@ -162,14 +169,22 @@ __global__ void __launch_bounds__(kLossThreads, 3) loss_kernel(
         //    outside the image)
         asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         __syncthreads();
-        for (int k = tid; k < kR2 * kR2; k += kLossThreads) {
-            const int r = k / kR2, c = k - r * kR2;
-            const int gx = ox - 10 + c, gy = oy - 10 + r;
-            const bool ok = gx >= 0 && gx < W && gy >= 0 && gy < H;
-            S.a.in.y[r][c] = ok ? S.a.in.y[r][c] + (1.0f - S.b.st.at[r][c]) * bgc : 0.0f;
+        if (ox >= 10 && oy >= 10 && ox + kOut + 10 <= W && oy + kOut + 10 <= H) {  // the region lies inside
+            float* yf = &S.a.in.y[0][0];
+            const float* af = &S.b.st.at[0][0];
+            for (int k = tid; k < kR2 * kR2; k += kLossThreads) yf[k] += (1.0f - af[k]) * bgc;
+        } else {
+            for (int r = wid; r < kR2; r += kLossThreads / 32) {
+                const int gy = oy - 10 + r;
+                for (int c = lane; c < kR2; c += 32) {
+                    const int gx = ox - 10 + c;
+                    const bool ok = gx >= 0 && gx < W && gy >= 0 && gy < H;
+                    S.a.in.y[r][c] = ok ? S.a.in.y[r][c] + (1.0f - S.b.st.at[r][c]) * bgc : 0.0f;
+                }
+            }
         }
         __syncthreads();
-        // 2. horizontal pass of x, y, x^2, y^2, xy: 52 rows x 42 columns in
+        // 2. horizontal pass of x, y, x^2 + y^2, xy: 52 rows x 42 columns in
         //    strips of 3 (728 strips: 95% of the threads busy over three
         //    rounds); and a copy of the output pixels
         constexpr int kHS = 3, kHN = kR1 / kHS;
@@ -181,32 +196,29 @@ __global__ void __launch_bounds__(kLossThreads, 3) loss_kernel(
                 xin[j] = S.a.in.x[r][c0 + j];
                 yin[j] = S.a.in.y[r][c0 + j];
             }
-            float xx[kHS + 10], yy[kHS + 10], xy[kHS + 10];
+            float sq[kHS + 10], xy[kHS + 10];
 #pragma unroll
             for (int j = 0; j < kHS + 10; ++j) {
-                xx[j] = xin[j] * xin[j];
-                yy[j] = yin[j] * yin[j];
+                sq[j] = xin[j] * xin[j] + yin[j] * yin[j];
                 xy[j] = xin[j] * yin[j];
             }
 #pragma unroll
             for (int o = 0; o < kHS; ++o) {
-                float a = 0.f, b = 0.f, c = 0.f, d = 0.f, e = 0.f;
+                float a = 0.f, b = 0.f, c = 0.f, e = 0.f;
 #pragma unroll
                 for (int j = 0; j < 11; ++j) {
                     a += w[j] * xin[o + j];
                     b += w[j] * yin[o + j];
-                    c += w[j] * xx[o + j];
-                    d += w[j] * yy[o + j];
+                    c += w[j] * sq[o + j];
                     e += w[j] * xy[o + j];
                 }
                 S.b.h[0][r][c0 + o] = a; S.b.h[1][r][c0 + o] = b; S.b.h[2][r][c0 + o] = c;
-                S.b.h[3][r][c0 + o] = d; S.b.h[4][r][c0 + o] = e;
+                S.b.h[3][r][c0 + o] = e;
             }
         }
-        for (int k = tid; k < kOut * kOut; k += kLossThreads) {
-            const int r = k / kOut, cidx = k - r * kOut;
-            S.xo[r][cidx] = S.a.in.x[r + 10][cidx + 10];
-            S.yo[r][cidx] = S.a.in.y[r + 10][cidx + 10];
+        for (int r = wid; r < kOut; r += kLossThreads / 32) {
+            S.xo[r][lane] = S.a.in.x[r + 10][lane + 10];
+            S.yo[r][lane] = S.a.in.y[r + 10][lane + 10];
         }
         __syncthreads();
         // 3. vertical pass (strips of 7 rows: 252 strips, one round) straight
@@ -216,9 +228,9 @@ __global__ void __launch_bounds__(kLossThreads, 3) loss_kernel(
         float ssim_sum = 0.f;
         for (int k = tid; k < kR1 * kVN; k += kLossThreads) {
             const int cidx = k % kR1, r0 = (k / kR1) * kVS;
-            float mom[5][kVS];
+            float mom[4][kVS];
 #pragma unroll
-            for (int f = 0; f < 5; ++f) strip11<kVS, kR1>(&S.b.h[f][r0][cidx], w, mom[f]);
+            for (int f = 0; f < 4; ++f) strip11<kVS, kR1>(&S.b.h[f][r0][cidx], w, mom[f]);
             const int gx = ox - 5 + cidx;
 #pragma unroll
             for (int o = 0; o < kVS; ++o) {
@@ -226,10 +238,11 @@ __global__ void __launch_bounds__(kLossThreads, 3) loss_kernel(
                 float dmu = 0.f, dxx = 0.f, dxy = 0.f;
                 if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
                     const float mx = mom[0][o], my = mom[1][o];
-                    const float sx = mom[2][o] - mx * mx, sy = mom[3][o] - my * my;
-                    const float sxy = mom[4][o] - mx * my;
+                    const float m2 = mx * mx + my * my;
+                    const float sxy = mom[3][o] - mx * my;
                     const float A1 = 2.f * mx * my + kC1, A2 = 2.f * sxy + kC2;
-                    const float B1 = mx * mx + my * my + kC1, B2 = sx + sy + kC2;
+                    // B2 = var x + var y + C2 = E[x^2 + y^2] - mu_x^2 - mu_y^2 + C2
+                    const float B1 = m2 + kC1, B2 = mom[2][o] - m2 + kC2;
                     // B1 >= C1 and B2 ~ >= C2: the hardware reciprocal (within 2 ulp)
                     const float iB1 = __fdividef(1.0f, B1), iB2 = __fdividef(1.0f, B2);
                     const float iB = iB1 * iB2;
