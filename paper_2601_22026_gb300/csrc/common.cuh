@@ -68,13 +68,15 @@ struct Rect {
     int x0, y0, x1, y1;
 };
 
+// B is 8 or 16: x / B and x * (1 / B) are the same real number, so the
+// correctly rounded product equals the correctly rounded quotient.
 __device__ __forceinline__ Rect tile_rect(float u, float w, float radius, int tiles_x, int tiles_y, int B) {
-    const float Bf = (float)B, Bm1 = (float)(B - 1);
+    const float iB = B == 8 ? 0.125f : 0.0625f, Bm1 = (float)(B - 1);
     Rect t;
-    t.x0 = min(tiles_x, max(0, (int)floorf(__fdiv_rn(__fsub_rn(u, radius), Bf))));
-    t.x1 = min(tiles_x, max(0, (int)floorf(__fdiv_rn(__fadd_rn(__fadd_rn(u, radius), Bm1), Bf))));
-    t.y0 = min(tiles_y, max(0, (int)floorf(__fdiv_rn(__fsub_rn(w, radius), Bf))));
-    t.y1 = min(tiles_y, max(0, (int)floorf(__fdiv_rn(__fadd_rn(__fadd_rn(w, radius), Bm1), Bf))));
+    t.x0 = min(tiles_x, max(0, (int)floorf(__fmul_rn(__fsub_rn(u, radius), iB))));
+    t.x1 = min(tiles_x, max(0, (int)floorf(__fmul_rn(__fadd_rn(__fadd_rn(u, radius), Bm1), iB))));
+    t.y0 = min(tiles_y, max(0, (int)floorf(__fmul_rn(__fsub_rn(w, radius), iB))));
+    t.y1 = min(tiles_y, max(0, (int)floorf(__fmul_rn(__fadd_rn(__fadd_rn(w, radius), Bm1), iB))));
     return t;
 }
 

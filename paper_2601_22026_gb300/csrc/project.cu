@@ -223,7 +223,7 @@ __device__ __forceinline__ void view_geom(const gsfit_camera& cam, const Gauss& 
 }
 
 template <int DEG, int FT>
-__global__ void __launch_bounds__(256) project_kernel(const float4* __restrict__ P, const uint2* __restrict__ F, int n,
+__global__ void __launch_bounds__(256, 3) project_kernel(const float4* __restrict__ P, const uint2* __restrict__ F, int n,
                                                       const gsfit_camera* __restrict__ cams_g, int n_views,
                                                       float4* __restrict__ xyd, float4* __restrict__ conic,
                                                       float4* __restrict__ rgb, uint32_t* __restrict__ tiles) {
