@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(256, 3) project_kernel(const float4* __restric
 // scale and rotation once.
 
 template <int DEG, int FT>
-__global__ void __launch_bounds__(256) project_bwd_rec_kernel(const float4* __restrict__ P,
+__global__ void __launch_bounds__(256, 4) project_bwd_rec_kernel(const float4* __restrict__ P,
                                                               const uint2* __restrict__ F, int n,
                                                               const gsfit_camera* __restrict__ cams_g,
                                                               const float4* __restrict__ xyd,
