@@ -84,7 +84,8 @@ __device__ __forceinline__ float4 cull_params(float4 co) {
     return make_float4(t, -co.y / co.z, -co.y / co.x, 0.f);
 }
 
-// Can a splat reach alpha >= 1/255 at some pixel centre of this warp's box?
+// Can a splat reach alpha >= 1/255 at some pixel centre of the rectangle
+// [b.x, b.z] x [b.y, b.w] (pixel coordinates)?
 // Exact minimum of q over the rectangle of offsets d = pixel - centre: zero
 // if the centre lies inside; otherwise q is convex with its minimum outside,
 // so the constrained minimum lies on an edge facing the centre, x = xe or
@@ -96,9 +97,9 @@ __device__ __forceinline__ float4 cull_params(float4 co) {
 // Entries without a record (past the list end, or an index only a failed
 // sort produces) carry t < 0 and are rejected before their (stale) record is
 // looked at.
-__device__ __forceinline__ bool box_reach(float ux, float uy, float4 co, float4 cp, float box_x0, float box_y0) {
+__device__ __forceinline__ bool box_reach(float ux, float uy, float4 co, float4 cp, float4 b) {
     if (!(cp.x > 0.0f)) return false;
-    const float X0 = box_x0 - ux, X1 = X0 + 7.0f, Y0 = box_y0 - uy, Y1 = Y0 + 3.0f;
+    const float X0 = b.x - ux, X1 = b.z - ux, Y0 = b.y - uy, Y1 = b.w - uy;
     const float xe = fminf(fmaxf(0.0f, X0), X1), ye = fminf(fmaxf(0.0f, Y0), Y1);
     const float y1 = fminf(fmaxf(cp.y * xe, Y0), Y1);
     const float x2 = fminf(fmaxf(cp.z * ye, X0), X1);
@@ -282,10 +283,19 @@ __device__ __forceinline__ bool ring_produce(Ring<SLOT>& R, int k, uint32_t b0, 
     return true;
 }
 
-// This warp's entries of slot s that can blend in its box (list order).
+// The bounding rectangle (pixel coordinates, x0 y0 x1 y1) of the lanes of
+// mask m (nonzero) in this warp's 8 x 4 box: lane l is pixel (l mod 8, l / 8).
+__device__ __forceinline__ float4 active_rect(uint32_t m, const TileCtx& c) {
+    const uint32_t cols = (m | (m >> 8) | (m >> 16) | (m >> 24)) & 0xffu;
+    return make_float4(c.box_x0 + (float)(__ffs(cols) - 1), c.box_y0 + (float)((__ffs(m) - 1) >> 3),
+                       c.box_x0 + (float)(31 - __clz(cols)), c.box_y0 + (float)((31 - __clz(m)) >> 3));
+}
+
+// This warp's entries of slot s that can blend at a pixel of rectangle b
+// (the bounding rectangle of its pixels still in play), in list order.
 template <int SLOT>
 __device__ __forceinline__ int ring_compact(const Ring<SLOT>& R, int s, int cnt, uint32_t base, uint32_t wmax,
-                                            const TileCtx& c, uint8_t* list) {
+                                            float4 b, uint8_t* list) {
     const int lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
     int nw = 0;
@@ -294,7 +304,7 @@ __device__ __forceinline__ int ring_compact(const Ring<SLOT>& R, int s, int cnt,
     for (int q = 0; q < SLOT / 32; ++q) {
         const int j = 32 * q + lane;
         const bool hit = j < cnt && base + (uint32_t)j < wmax &&
-                         box_reach(R.xyd[s][j].x, R.xyd[s][j].y, R.co[s][j], R.cp[s][j], c.box_x0, c.box_y0);
+                         box_reach(R.xyd[s][j].x, R.xyd[s][j].y, R.co[s][j], R.cp[s][j], b);
         const uint32_t m = __ballot_sync(0xffffffffu, hit);
         if (hit) list[nw + __popc(m & lt)] = (uint8_t)j;
         nw += __popc(m);
@@ -363,7 +373,9 @@ __global__ void __launch_bounds__(TileShape<TILE>::kThreads) render_fwd_kernel(
         if (cnt == 0) break;
         if (!wdone) {
             const uint32_t base = (uint32_t)k * SLOT;
-            const int nw = ring_compact(R, s, cnt, base, 0xffffffffu, c, s_list[w]);
+            // cull against the pixels that have not stopped (a nonzero set: the warp is not done)
+            const float4 b = active_rect(__ballot_sync(0xffffffffu, !done), c);
+            const int nw = ring_compact(R, s, cnt, base, 0xffffffffu, b, s_list[w]);
             for (int i = 0; i < nw; ++i) {
                 const int j = s_list[w][i];
                 // branch-free: a lane that is done, or skips this entry
@@ -587,8 +599,10 @@ __global__ void __launch_bounds__(TileShape<TILE>::kThreads, 5) render_bwd_kerne
         if (cnt == 0) break;
         const uint32_t b1 = len - (uint32_t)k * SLOT;
         const uint32_t base = b1 - (uint32_t)cnt;  // list position of entry 0
-        if (base < wmax) {
-            const int nw = ring_compact(R, s, cnt, base, wmax, c, s_list[w]);
+        // pixels whose contributors reach into this slot; the others need none of its entries
+        const uint32_t am = __ballot_sync(0xffffffffu, q.last > base);
+        if (am != 0u) {
+            const int nw = ring_compact(R, s, cnt, base, wmax, active_rect(am, c), s_list[w]);
             for (int i = nw - 1; i >= 0; --i) {
                 const int j = s_list[w][i];
                 const float4 p = R.xyd[s][j];
