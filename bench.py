@@ -310,14 +310,16 @@ def oracle_sample(sc, seconds_cap: float = 30.0) -> dict:
             "sample_seconds": dt}
 
 
-def mixed_precision_rate(sc, st, bg_table, warmup: int, steps: int, features: str = "f16") -> dict:
+def mixed_precision_rate(sc, st, bg_table, warmup: int, steps: int, features: str = "f16",
+                         exp_half2: bool = False) -> dict:
     """The same iteration in the mixed-precision form (16-bit rotation, scale
-    and SH storage read by the projection; everything computed in float32),
+    and SH storage read by the projection; everything computed in float32;
+    with exp_half2 also the compositing exponent in packed half precision),
     on a second state with the same scene, targets and backgrounds."""
     import torch
     from paper_2601_22026_gb300.fit import FitState, boosted_lr
     mp = FitState(sc["gaussians"], sc["cameras"], bg=sc["bg"], lr=boosted_lr(), features=features,
-                  tile=st.tile, batch=int(st.opts.batch))
+                  tile=st.tile, batch=int(st.opts.batch), exp_half2=exp_half2)
     mp.target_rgb.copy_(st.target_rgb)
     mp.target_alpha.copy_(st.target_alpha)
     mp.capture()
@@ -336,7 +338,8 @@ def mixed_precision_rate(sc, st, bg_table, warmup: int, steps: int, features: st
         raise RuntimeError("device status set in the mixed-precision leg")
     ms = e0.elapsed_time(e1) / steps
     stage_ms = time_stages(mp, reps=10)
-    out = {"features": features, "value": 1000.0 / ms, "unit": "iters/s", "ms_per_step": ms, "steps": steps,
+    out = {"features": features, "exp_half2": bool(exp_half2), "value": 1000.0 / ms, "unit": "iters/s",
+           "ms_per_step": ms, "steps": steps,
            "loss_last": float(mp.loss_out.item()), "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()}}
     del mp
     torch.cuda.empty_cache()
@@ -680,6 +683,11 @@ def main() -> None:
         mp["vs_f32"] = mp["value"] / (value / world)
         if plain is not None:
             mp["speedup_vs_plain_fp32_single_view"] = mp["value"] / plain
+        mp2 = mixed_precision_rate(sc, st, bg_table, args.warmup, max(10, min(200, args.steps)), exp_half2=True)
+        mp2["vs_f32"] = mp2["value"] / (value / world)
+        if plain is not None:
+            mp2["speedup_vs_plain_fp32_single_view"] = mp2["value"] / plain
+        mp["half2_exponent"] = mp2
         out["mixed_precision"] = mp
     if rank == 0:
         out["reprojection_768"] = reprojection_rate()

@@ -60,7 +60,7 @@
 extern "C" {
 #endif
 
-#define GSFIT_ABI_VERSION 2
+#define GSFIT_ABI_VERSION 3
 #define GSFIT_MAX_VIEWS 256
 #define GSFIT_TILE 16
 
@@ -247,13 +247,27 @@ int gsfit_bin_sort(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_v
  *          GSFIT_ERR_INVALID_ARG to the status word and does nothing.
  *   batch: records per shared-memory slot of the producer ring (the number of
  *          Gaussians staged per batch): 64, 128 or 256.
- * A null pointer or a 0 field selects the default (tile 16, batch 128).
+ *   exp_half2: 1 evaluates exp(power) of each (pixel, Gaussian) pair in
+ *          packed half precision (f16x2: the forward pass takes two Gaussians
+ *          of a pixel per instruction), the half2-exponent option of the
+ *          mixed-precision form; 0 (default) in float32. The quadratic form,
+ *          alpha, T, colours and gradients stay float32. Each pair's value
+ *          depends on its own power only, so the adjoint, which must be called
+ *          with the same setting as the forward pass it follows, takes the
+ *          same skip and stop decisions. Against the float32 form the result
+ *          moves by the half-precision rounding of power and exp (up to about
+ *          2^-10 relative in the weight) and by the threshold decisions that
+ *          rounding moves.
+ *   reserved: must be 0.
+ * A null pointer or a 0 field selects the default (tile 16, batch 128, float32
+ * exponent).
  * gsfit_render_autotune measures the batch depths on a caller's workload.
  */
 typedef struct gsfit_render_opts {
     int32_t tile;
     int32_t batch;
-    int32_t reserved[2];
+    int32_t exp_half2;
+    int32_t reserved;
 } gsfit_render_opts;
 
 /*

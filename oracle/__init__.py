@@ -63,6 +63,8 @@ def lib() -> ctypes.CDLL:
         L = ctypes.CDLL(str(LIB))
         P = ctypes.c_void_p
         i, d, ll = ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+        L.oracle_set_threshold_margin.argtypes = [d]
+        L.oracle_threshold_margin.restype = d
         L.oracle_proj_stride.restype = i
         L.oracle_total_tiles.argtypes = [i, P, i]
         L.oracle_total_tiles.restype = i
@@ -172,6 +174,24 @@ def bin_tiles(proj: np.ndarray, cams: dict, tile: int = 16):
     cnt = lib().oracle_bin(n, V, _p(c), tile, _p(np.ascontiguousarray(proj)), _p(keys), _p(vals), cap, _p(ranges))
     assert cnt == cap
     return keys[:cnt], vals[:cnt], ranges
+
+
+class threshold_margin:
+    """Context manager: widen (or narrow) the relative margin within which
+    render / render_bwd flag a pixel or Gaussian as ambiguous (its alpha near
+    1/255 or 0.99, or its T near 1e-4). Flags only; no value changes."""
+
+    def __init__(self, margin: float):
+        self.margin = float(margin)
+
+    def __enter__(self):
+        self.prev = lib().oracle_threshold_margin()
+        lib().oracle_set_threshold_margin(self.margin)
+        return self
+
+    def __exit__(self, *exc):
+        lib().oracle_set_threshold_margin(self.prev)
+        return False
 
 
 def render(gs: dict, cams: dict, bg: np.ndarray, tile: int = 16, smooth: bool = False) -> dict:

@@ -36,6 +36,10 @@ using namespace oracle;
 extern "C" {
 
 int oracle_proj_stride(void) { return P_STRIDE; }
+
+// Relative margin of the near-threshold flags of the compositing (see raster.cpp).
+void oracle_set_threshold_margin(double m) { oracle::g_threshold_margin = m; }
+double oracle_threshold_margin(void) { return oracle::g_threshold_margin; }
 int oracle_cam_doubles(void) { return CAM_DOUBLES; }
 
 void oracle_set_threads(int n) {

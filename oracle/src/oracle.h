@@ -21,6 +21,10 @@
 
 namespace oracle {
 
+// Relative margin of the compositing's near-threshold flags (raster.cpp).
+extern double g_threshold_margin;
+
+
 // One pinhole camera. viewmat rows are the camera's right, down and forward
 // axes; p_cam = R p_world + t. campos is the camera centre in world space.
 struct Camera {

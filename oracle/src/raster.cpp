@@ -64,6 +64,11 @@ long long bin_tiles(int n, const std::vector<Camera>& cams, const double* proj, 
     return (long long)keys.size();
 }
 
+// Relative margin of the near-threshold flags (2e-4 by default; a test of a
+// lower-precision form widens it with oracle_set_threshold_margin). It only
+// flags pixels and Gaussians; it changes no computed value.
+double g_threshold_margin = 2e-4;
+
 namespace {
 
 struct Blend {
@@ -81,8 +86,8 @@ struct Pixel {
 };
 
 // |x - thr| within a relative margin: float32 rounding on the GPU side could
-// take the other branch of this comparison.
-inline bool near_threshold(double x, double thr) { return std::fabs(x - thr) <= 2e-4 * thr; }
+// take the other branch of this comparison (g_threshold_margin).
+inline bool near_threshold(double x, double thr) { return std::fabs(x - thr) <= g_threshold_margin * thr; }
 
 void composite_pixel(int px, int py, const uint32_t* list, int count, const double* proj_v, int flags, Pixel& out) {
     const bool smooth = flags & FLAG_SMOOTH;

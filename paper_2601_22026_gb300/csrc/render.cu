@@ -322,9 +322,17 @@ __device__ __forceinline__ bool tile_mismatch(const gsfit_camera* cams, int32_t*
     return true;
 }
 
+// exp of two powers in one packed half-precision instruction (f16x2), for the
+// half2-exponent option: each half's result depends on its own power only, so
+// a pair evaluated alone (the adjoint) or next to any other gives the same value.
+__device__ __forceinline__ float2 exp_half2(float a, float b) {
+    return __half22float2(h2exp(__floats2half2_rn(a, b)));
+}
+
 // IMP: also accumulate each Gaussian's blend weight alpha T over the batch
 // into importance[g] (a warp sum per (warp, Gaussian), then one atomic).
-template <int TILE, int SLOT, bool IMP>
+// E16: the half2-exponent option (two Gaussians of a pixel per exp instruction).
+template <int TILE, int SLOT, bool IMP, bool E16>
 __global__ void __launch_bounds__(TileShape<TILE>::kThreads) render_fwd_kernel(
     const float4* __restrict__ xyd, const float4* __restrict__ conic, const float4* __restrict__ rgb, int n,
     const gsfit_camera* __restrict__ cams_g, int n_views, const uint32_t* __restrict__ vals,
@@ -376,16 +384,11 @@ __global__ void __launch_bounds__(TileShape<TILE>::kThreads) render_fwd_kernel(
             // cull against the pixels that have not stopped (a nonzero set: the warp is not done)
             const float4 b = active_rect(__ballot_sync(0xffffffffu, !done), c);
             const int nw = ring_compact(R, s, cnt, base, 0xffffffffu, b, s_list[w]);
-            for (int i = 0; i < nw; ++i) {
-                const int j = s_list[w][i];
-                // branch-free: a lane that is done, or skips this entry
-                // (power > 0, alpha < 1/255), or stops at it (T would drop
-                // below 1e-4) adds a zero weight and keeps its T
-                const float4 p = R.xyd[s][j];
-                const float4 co = R.co[s][j];
-                const float4 col = R.col[s][j];
-                const float power = splat_power(co, fx - p.x, fy - p.y);
-                const float alpha = fminf(kAlphaClamp, co.w * __expf(power));
+            // branch-free: a lane that is done, or skips an entry (power > 0,
+            // alpha < 1/255), or stops at it (T would drop below 1e-4) adds a
+            // zero weight and keeps its T
+            auto blend_entry = [&](int j, const float4& co, const float4& col, float power, float G) {
+                const float alpha = fminf(kAlphaClamp, co.w * G);
                 const bool hit = !done && power <= 0.0f && alpha >= kAlphaSkip;
                 const float test_T = T * (1.0f - alpha);
                 const bool stop = hit && test_T < kTStop;
@@ -397,12 +400,32 @@ __global__ void __launch_bounds__(TileShape<TILE>::kThreads) render_fwd_kernel(
                 T = blend ? test_T : T;
                 last = blend ? base + (uint32_t)j + 1u : last;  // one past this list position
                 done = done || stop;
-                [[maybe_unused]] const float my_w = wgt;
                 if constexpr (IMP) {
-                    const float sum = warp_sum(my_w);
+                    const float sum = warp_sum(wgt);
                     if (lane == 0 && sum != 0.0f) atomicAdd(importance + R.g[s][j], sum);
                 }
-                if (__all_sync(0xffffffffu, done)) break;
+            };
+            if constexpr (E16) {
+                for (int i = 0; i < nw; i += 2) {  // entries in pairs: one exp instruction for both
+                    const int j0 = s_list[w][i], j1 = s_list[w][min(i + 1, nw - 1)];
+                    const float4 p0 = R.xyd[s][j0], co0 = R.co[s][j0], col0 = R.col[s][j0];
+                    const float4 p1 = R.xyd[s][j1], co1 = R.co[s][j1], col1 = R.col[s][j1];
+                    const float pw0 = splat_power(co0, fx - p0.x, fy - p0.y);
+                    const float pw1 = splat_power(co1, fx - p1.x, fy - p1.y);
+                    const float2 G = exp_half2(pw0, pw1);
+                    blend_entry(j0, co0, col0, pw0, G.x);
+                    if (i + 1 < nw) blend_entry(j1, co1, col1, pw1, G.y);
+                    if (__all_sync(0xffffffffu, done)) break;
+                }
+            } else {
+                for (int i = 0; i < nw; ++i) {
+                    const int j = s_list[w][i];
+                    const float4 p = R.xyd[s][j];
+                    const float4 co = R.co[s][j];
+                    const float power = splat_power(co, fx - p.x, fy - p.y);
+                    blend_entry(j, co, R.col[s][j], power, __expf(power));
+                    if (__all_sync(0xffffffffu, done)) break;
+                }
             }
             if (__all_sync(0xffffffffu, done)) {
                 wdone = true;
@@ -481,10 +504,11 @@ struct PixBwd {
 // does not blend it (past its contributor count, power > 0 or alpha < 1/255,
 // the forward's own tests on the same values) takes alpha = 0, which leaves
 // T and the behind-colour sum unchanged and makes all nine terms zero.
+template <bool E16>
 __device__ __forceinline__ bool pix_bwd_step(PixBwd& q, uint32_t pos, float4 co, const float4* colp, float dx,
                                              float dy, float* g9) {
     const float power = splat_power(co, dx, dy);
-    const float G = __expf(power);
+    const float G = E16 ? exp_half2(power, power).x : __expf(power);
     const float a = co.w * G;
     const float alpha_f = fminf(kAlphaClamp, a);
     const bool hit = pos < q.last && power <= 0.0f && alpha_f >= kAlphaSkip;
@@ -521,7 +545,7 @@ __device__ __forceinline__ bool pix_bwd_step(PixBwd& q, uint32_t pos, float4 co,
 // the adjoint is issue-bound on dependent shared-memory, shuffle and MUFU
 // latencies, and the extra warps hide more of them than the few spilled
 // registers cost.
-template <int TILE, int SLOT>
+template <int TILE, int SLOT, bool E16>
 __global__ void __launch_bounds__(TileShape<TILE>::kThreads, 5) render_bwd_kernel(
     const float4* __restrict__ xyd, const float4* __restrict__ conic, const float4* __restrict__ rgb, int n,
     const gsfit_camera* __restrict__ cams_g, int n_views, const uint32_t* __restrict__ vals,
@@ -607,7 +631,7 @@ __global__ void __launch_bounds__(TileShape<TILE>::kThreads, 5) render_bwd_kerne
                 const int j = s_list[w][i];
                 const float4 p = R.xyd[s][j];
                 float g9[9];
-                const bool hit = pix_bwd_step(q, base + (uint32_t)j, R.co[s][j], &R.col[s][j], fx - p.x, fy - p.y, g9);
+                const bool hit = pix_bwd_step<E16>(q, base + (uint32_t)j, R.co[s][j], &R.col[s][j], fx - p.x, fy - p.y, g9);
                 if (__any_sync(0xffffffffu, hit)) {
                     const float tot = reduce9(g9, lane);
                     if (slot >= 0) atomicAdd(grad2d + 16 * (rec0 + R.g[s][j]) + slot_off, tot);
@@ -668,13 +692,16 @@ namespace {
 
 struct RenderCfg {
     int tile, batch;
+    bool e16 = false;  // half2 exponent
 };
 
-// Options -> a supported (tile, batch); false for unsupported values.
+// Options -> a supported (tile, batch, exponent precision); false for unsupported values.
 bool resolve(const gsfit_render_opts* o, RenderCfg& c) {
     c.tile = (o && o->tile) ? o->tile : GSFIT_TILE;
     c.batch = (o && o->batch) ? o->batch : 128;
-    return (c.tile == 8 || c.tile == 16) && (c.batch == 64 || c.batch == 128 || c.batch == 256);
+    c.e16 = o && o->exp_half2 == 1;
+    return (c.tile == 8 || c.tile == 16) && (c.batch == 64 || c.batch == 128 || c.batch == 256) &&
+           (!o || ((o->exp_half2 == 0 || o->exp_half2 == 1) && o->reserved == 0));
 }
 
 struct FwdArgs {
@@ -721,60 +748,68 @@ int opt_in(K kernel, size_t bytes, bool* done) {
     return GSFIT_OK;
 }
 
-template <int TILE, int SLOT, bool IMP>
+template <int TILE, int SLOT, bool IMP, bool E16>
 int launch_fwd_v(const FwdArgs& a, int total_tiles, cudaStream_t s) {
     static bool done[64] = {false};
-    const int rc = opt_in(render_fwd_kernel<TILE, SLOT, IMP>, render_smem<SLOT>(GSFIT_MAX_VIEWS), done);
+    const int rc = opt_in(render_fwd_kernel<TILE, SLOT, IMP, E16>, render_smem<SLOT>(GSFIT_MAX_VIEWS), done);
     if (rc != GSFIT_OK) return rc;
-    render_fwd_kernel<TILE, SLOT, IMP><<<total_tiles, TileShape<TILE>::kThreads, render_smem<SLOT>(a.n_views), s>>>(
+    render_fwd_kernel<TILE, SLOT, IMP, E16><<<total_tiles, TileShape<TILE>::kThreads, render_smem<SLOT>(a.n_views), s>>>(
         a.xyd, a.conic, a.rgb, a.n, a.cams, a.n_views, a.vals, a.ranges, a.tile_order, a.bg, a.out_rgb, a.out_alpha,
         a.out_T, a.out_nc, a.status, a.importance);
     GSFIT_LAUNCH_CHECK();
     return GSFIT_OK;
 }
 
-template <int TILE, int SLOT>
+template <int TILE, int SLOT, bool E16>
 int launch_fwd(const FwdArgs& a, int total_tiles, cudaStream_t s) {
-    return a.importance ? launch_fwd_v<TILE, SLOT, true>(a, total_tiles, s)
-                        : launch_fwd_v<TILE, SLOT, false>(a, total_tiles, s);
+    return a.importance ? launch_fwd_v<TILE, SLOT, true, E16>(a, total_tiles, s)
+                        : launch_fwd_v<TILE, SLOT, false, E16>(a, total_tiles, s);
 }
 
-template <int TILE, int SLOT>
+template <int TILE, int SLOT, bool E16>
 int launch_bwd(const BwdArgs& a, int total_tiles, cudaStream_t s) {
     static bool done[64] = {false};
-    const int rc = opt_in(render_bwd_kernel<TILE, SLOT>, render_smem<SLOT>(GSFIT_MAX_VIEWS), done);
+    const int rc = opt_in(render_bwd_kernel<TILE, SLOT, E16>, render_smem<SLOT>(GSFIT_MAX_VIEWS), done);
     if (rc != GSFIT_OK) return rc;
-    render_bwd_kernel<TILE, SLOT><<<total_tiles, TileShape<TILE>::kThreads, render_smem<SLOT>(a.n_views), s>>>(
+    render_bwd_kernel<TILE, SLOT, E16><<<total_tiles, TileShape<TILE>::kThreads, render_smem<SLOT>(a.n_views), s>>>(
         a.xyd, a.conic, a.rgb, a.n, a.cams, a.n_views, a.vals, a.ranges, a.tile_order, a.bg, a.T_final, a.n_contrib,
         a.dL_drgb, a.dL_dalpha, a.grad2d, a.status);
     GSFIT_LAUNCH_CHECK();
     return GSFIT_OK;
 }
 
-template <int TILE>
+template <int TILE, bool E16>
 int dispatch_fwd(const FwdArgs& a, int batch, int total_tiles, cudaStream_t s) {
     switch (batch) {
-        case 64: return launch_fwd<TILE, 64>(a, total_tiles, s);
-        case 256: return launch_fwd<TILE, 256>(a, total_tiles, s);
-        default: return launch_fwd<TILE, 128>(a, total_tiles, s);
+        case 64: return launch_fwd<TILE, 64, E16>(a, total_tiles, s);
+        case 256: return launch_fwd<TILE, 256, E16>(a, total_tiles, s);
+        default: return launch_fwd<TILE, 128, E16>(a, total_tiles, s);
     }
 }
 
-template <int TILE>
+template <int TILE, bool E16>
 int dispatch_bwd(const BwdArgs& a, int batch, int total_tiles, cudaStream_t s) {
     switch (batch) {
-        case 64: return launch_bwd<TILE, 64>(a, total_tiles, s);
-        case 256: return launch_bwd<TILE, 256>(a, total_tiles, s);
-        default: return launch_bwd<TILE, 128>(a, total_tiles, s);
+        case 64: return launch_bwd<TILE, 64, E16>(a, total_tiles, s);
+        case 256: return launch_bwd<TILE, 256, E16>(a, total_tiles, s);
+        default: return launch_bwd<TILE, 128, E16>(a, total_tiles, s);
     }
 }
 
 int run_fwd(const FwdArgs& a, const RenderCfg& c, int total_tiles, cudaStream_t s) {
-    return c.tile == 8 ? dispatch_fwd<8>(a, c.batch, total_tiles, s) : dispatch_fwd<16>(a, c.batch, total_tiles, s);
+    if (c.e16)
+        return c.tile == 8 ? dispatch_fwd<8, true>(a, c.batch, total_tiles, s)
+                           : dispatch_fwd<16, true>(a, c.batch, total_tiles, s);
+    return c.tile == 8 ? dispatch_fwd<8, false>(a, c.batch, total_tiles, s)
+                       : dispatch_fwd<16, false>(a, c.batch, total_tiles, s);
 }
 
 int run_bwd(const BwdArgs& a, const RenderCfg& c, int total_tiles, cudaStream_t s) {
-    return c.tile == 8 ? dispatch_bwd<8>(a, c.batch, total_tiles, s) : dispatch_bwd<16>(a, c.batch, total_tiles, s);
+    if (c.e16)
+        return c.tile == 8 ? dispatch_bwd<8, true>(a, c.batch, total_tiles, s)
+                           : dispatch_bwd<16, true>(a, c.batch, total_tiles, s);
+    return c.tile == 8 ? dispatch_bwd<8, false>(a, c.batch, total_tiles, s)
+                       : dispatch_bwd<16, false>(a, c.batch, total_tiles, s);
 }
 
 FwdArgs fwd_args(const gsfit_proj* proj, const gsfit_camera* cams, int n_views, int n, const uint32_t* vals,
@@ -936,7 +971,9 @@ extern "C" int gsfit_render_autotune(const gsfit_proj* proj, const gsfit_camera*
     float best_ms = 3.4e38f;
     int best_depth = 128;
     for (int d = 0; d < 3; ++d) {
-        const RenderCfg c{tile, depths[d]};
+        RenderCfg c;
+        c.tile = tile;
+        c.batch = depths[d];
         int rc = run_fwd(fa, c, total_tiles, stream);  // warm-up (and shared-memory opt-in)
         if (rc == GSFIT_OK) rc = run_bwd(ba, c, total_tiles, stream);
         if (rc != GSFIT_OK) return rc;
@@ -966,7 +1003,8 @@ extern "C" int gsfit_render_autotune(const gsfit_proj* proj, const gsfit_camera*
     GSFIT_CUDA_CHECK(cudaStreamSynchronize(stream));
     best->tile = tile;
     best->batch = best_depth;
-    best->reserved[0] = best->reserved[1] = 0;
+    best->exp_half2 = 0;
+    best->reserved = 0;
     return GSFIT_OK;
 }
 

@@ -33,15 +33,18 @@ class FitState:
     def __init__(self, gaussians: dict, cams: dict, *, target_rgb=None, target_alpha=None, bg=None,
                  capacity: int | None = None, lr: dict | None = None, eps: float = 1e-15,
                  lam: float = 0.2, features: str = "f32", tile: int = 16, batch: int = 128,
-                 device: str = "cuda"):
+                 exp_half2: bool = False, device: str = "cuda"):
         """features: "f32", or "f16" / "bf16" for the mixed-precision form
         (16-bit copy of rotation, scales and SH read by the projection, kept
         current by Adam; float32 master parameters and moments).
         tile (8 or 16) and batch (64, 128, 256 records per shared-memory
-        slot): the compositing options; see tune.py for choosing them."""
+        slot): the compositing options; see tune.py for choosing them.
+        exp_half2: evaluate the compositing exponent in packed half precision
+        (the half2 option of the mixed-precision form)."""
         self.device = device
         self.tile = int(tile)
-        self.opts = G.RenderOpts(self.tile, int(batch))
+        self.exp_half2 = bool(exp_half2)
+        self.opts = G.RenderOpts(self.tile, int(batch), int(self.exp_half2))
         self.n = int(gaussians["means"].shape[0])
         self.sh_degree = int(round(gaussians["sh"].shape[1] ** 0.5)) - 1
         self.n_planes = G.num_planes(self.sh_degree)
@@ -249,6 +252,7 @@ class FitState:
                                               self.T_final, self.n_contrib, self.dL_drgb, self.dL_dalpha,
                                               self.grad2d, self.tile, reps, None, self.status)
         self.opts = best
+        self.opts.exp_half2 = int(self.exp_half2)
         self.graph = None
         return times
 

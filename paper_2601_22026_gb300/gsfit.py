@@ -35,7 +35,7 @@ class Gaussians(ctypes.Structure):
                 ("reserved", _i32)]
 
 
-ABI_VERSION = 2  # GSFIT_ABI_VERSION of include/gsfit.h
+ABI_VERSION = 3  # GSFIT_ABI_VERSION of include/gsfit.h
 
 # gsfit_gaussians.feature_dtype values (GSFIT_FEATURES_*)
 FEATURES = {"f32": 0, "f16": 1, "bf16": 2}
@@ -52,8 +52,9 @@ class Camera(ctypes.Structure):
 
 
 class RenderOpts(ctypes.Structure):
-    """gsfit_render_opts: tile edge (8 or 16) and batch depth (64, 128, 256)."""
-    _fields_ = [("tile", _i32), ("batch", _i32), ("reserved", _i32 * 2)]
+    """gsfit_render_opts: tile edge (8 or 16), batch depth (64, 128, 256) and
+    the half2-exponent switch (0 or 1)."""
+    _fields_ = [("tile", _i32), ("batch", _i32), ("exp_half2", _i32), ("reserved", _i32)]
 
 
 assert ctypes.sizeof(Camera) == 128
@@ -277,11 +278,11 @@ def gsfit_bin_sort(proj: ProjBuffers, cams_dev, n_views, n, total_tiles, ws, key
 
 
 def _opts(opts):
-    """None, a RenderOpts, or a (tile, batch) pair -> a pointer argument."""
+    """None, a RenderOpts, or a (tile, batch[, exp_half2]) tuple -> a pointer argument."""
     if opts is None:
         return None
     if not isinstance(opts, RenderOpts):
-        opts = RenderOpts(int(opts[0]), int(opts[1]))
+        opts = RenderOpts(*[int(x) for x in opts])
     return ctypes.byref(opts)
 
 

@@ -211,6 +211,97 @@ def test_error_of_the_16bit_form_against_full_precision(kind):
             assert rows[f"grad {k}, rel. norm"] <= 3e-2, k
 
 
+def test_error_of_the_half2_exponent_option():
+    """The half2-exponent option of the half form: 16-bit features and
+    exp(power) of every (pixel, Gaussian) pair in packed half precision (the
+    forward pass takes two Gaussians per instruction). Error against the FP64
+    oracle on the unrounded float32 features, per output. Besides the feature
+    rounding, half precision rounds power (at most 2^-9 absolute for
+    |power| <= 5.6, the range that passes the alpha test) and exp (2^-11
+    relative): the weight moves by at most about 3e-3 relative, so pixels where
+    a decision could move are found with the oracle's threshold flags widened
+    to 5e-3 relative; the 2e-3 image bound applies to the others."""
+    from paper_2601_22026_gb300.fit import FitState
+    from test_parity_gpu import _rgb_to_pixels
+    gs, cams, bg = _scene("differentiation_512")
+    P = scenes.num_pixels(cams)
+    w_rgb = scenes.cotangents(3 * P, 711, 1e-3)
+    w_a = scenes.cotangents(P, 712, 1e-3)
+    st = FitState(gs, cams, bg=bg, features="f16", exp_half2=True)
+    assert st.opts.exp_half2 == 1
+    st.forward()
+    st.dL_drgb.copy_(torch.from_numpy(w_rgb))
+    st.dL_dalpha.copy_(torch.from_numpy(w_a))
+    rgb = _rgb_to_pixels(st.rgb.cpu().numpy().astype(np.float64), cams)
+    alpha = st.alpha.cpu().numpy().astype(np.float64)
+    st.render_bwd()
+    torch.cuda.synchronize()
+    assert st.check_status() == 0
+    with oracle.threshold_margin(5e-3):
+        ref = oracle.render(gs, cams, bg)
+        ref16 = oracle.render(_snapped(gs, "f16"), cams, bg)
+    refg = oracle.render_bwd(gs, cams, bg, w_rgb.astype(np.float64), w_a.astype(np.float64))
+    same = ((ref["n_contrib"] == ref16["n_contrib"]) & (ref["n_blended"] == ref16["n_blended"]) &
+            ~ref["ambiguous"] & ~ref16["ambiguous"])
+    err = np.abs(rgb - _rgb_to_pixels(ref["rgb"], cams))
+    aerr = np.abs(alpha - ref["alpha"])
+    rows = {"image, max abs (same decisions)": float(err[same].max()),
+            "image, max abs (all pixels)": float(err.max()),
+            "image, mean abs (all pixels)": float(err.mean()),
+            "alpha, max abs (same decisions)": float(aerr[same].max()),
+            "pixels with a changed or near decision": float(1.0 - same.mean())}
+    grads = st.gradients()
+    for k in ["means", "log_scales", "quats", "opacity_logits", "sh"]:
+        a = np.asarray(grads[k], np.float64).reshape(-1)
+        b = np.asarray(refg["grads"][k], np.float64).reshape(-1)
+        rows[f"grad {k}, rel. norm"] = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    print("\nhalf form with the half2 exponent vs FP64 oracle on float32 features, 50k Gaussians SH3, 512x512:")
+    for k, v in rows.items():
+        print(f"  {k:40s} {v:.3e}")
+    assert rows["pixels with a changed or near decision"] <= 0.5
+    assert rows["image, max abs (all pixels)"] <= 2.0 / 255.0
+    assert rows["image, mean abs (all pixels)"] <= 3e-4
+    assert rows["image, max abs (same decisions)"] <= 2e-3
+    assert rows["alpha, max abs (same decisions)"] <= 2e-3
+    for k in ["means", "log_scales", "quats", "opacity_logits", "sh"]:
+        assert rows[f"grad {k}, rel. norm"] <= 3e-2, k
+
+
+def test_half2_exponent_pairs_do_not_matter():
+    """exp(power) of a pair is evaluated in one f16x2 instruction next to
+    whichever Gaussian shares it: the forward pairs list entries two by two,
+    the adjoint evaluates one at a time. With identical values either way the
+    adjoint takes the forward's decisions: its T recovery ends at T = 1 in
+    front of the first Gaussian, which the gradients of the opacity would
+    otherwise betray. Checked here as: the half2 form's image and gradients
+    against the float32-exponent form on the same half features, closer than
+    the threshold jumps allow for a mismatch."""
+    from paper_2601_22026_gb300.fit import FitState
+    gs, cams, bg = _scene("differentiation_512")
+    P = scenes.num_pixels(cams)
+    w_rgb = torch.from_numpy(scenes.cotangents(3 * P, 721, 1e-3))
+    w_a = torch.from_numpy(scenes.cotangents(P, 722, 1e-3))
+    out = {}
+    for e16 in (False, True):
+        st = FitState(gs, cams, bg=bg, features="f16", exp_half2=e16)
+        st.forward()
+        st.dL_drgb.copy_(w_rgb)
+        st.dL_dalpha.copy_(w_a)
+        st.render_bwd()
+        torch.cuda.synchronize()
+        assert st.check_status() == 0
+        out[e16] = (st.rgb.cpu().numpy().astype(np.float64), st.gradients())
+    # half precision moves each weight by at most about 3e-3 relative: a
+    # typical pixel moves by well under 1e-4; a pixel whose decision moves by
+    # at most one threshold jump
+    d = np.abs(out[True][0] - out[False][0])
+    assert np.median(d) <= 1e-4 and d.mean() <= 1e-4 and d.max() <= 2.0 / 255.0
+    for k in ["means", "opacity_logits", "sh"]:
+        a = np.asarray(out[True][1][k], np.float64).reshape(-1)
+        b = np.asarray(out[False][1][k], np.float64).reshape(-1)
+        assert np.linalg.norm(a - b) <= 3e-2 * np.linalg.norm(b), k
+
+
 @pytest.mark.parametrize("kind", KINDS)
 def test_adam_writes_the_rounded_features(kind):
     from paper_2601_22026_gb300 import gsfit as G

@@ -521,3 +521,17 @@ def test_adam_first_step_moves_by_lr_sign():
     p, m, v = np.zeros(4), np.zeros(4), np.zeros(4)
     oracle.adam(p, g, m, v, 1e-3, 0.9, 0.999, 1e-15, 1)
     np.testing.assert_allclose(p, -1e-3 * g / (np.abs(g) + 1e-15), rtol=1e-12, atol=0)
+
+
+def test_threshold_margin_changes_flags_only():
+    """Widening the near-threshold margin flags more pixels and changes no
+    rendered value (it is a test aid for lower-precision forms)."""
+    sc = scenes.plain_single_view(0)
+    gs, cams, bg = sc["gaussians"], sc["cameras"], sc["bg"]
+    a = oracle.render(gs, cams, bg)
+    with oracle.threshold_margin(1e-2):
+        b = oracle.render(gs, cams, bg)
+    for k in ("rgb", "alpha", "T_final", "n_contrib", "n_blended"):
+        np.testing.assert_array_equal(a[k], b[k])
+    assert (b["ambiguous"] | ~a["ambiguous"]).all() and b["ambiguous"].sum() > a["ambiguous"].sum()
+    assert oracle.lib().oracle_threshold_margin() == 2e-4
