@@ -47,23 +47,16 @@ struct LossSmem {
     float yo[kOut][kOut];
 };
 
-// Normalised 11-tap Gaussian, sigma = 1.5.
-__device__ __forceinline__ void window(float w[11]) {
-    float s = 0.f;
-#pragma unroll
-    for (int i = 0; i < 11; ++i) {
-        const float d = (float)(i - 5);
-        w[i] = expf(-d * d / (2.0f * 1.5f * 1.5f));
-        s += w[i];
-    }
-#pragma unroll
-    for (int i = 0; i < 11; ++i) w[i] /= s;
-}
+// The SSIM window: 11-tap Gaussian, sigma = 1.5, normalised
+// (exp(-(i - 5)^2 / 4.5) / sum, evaluated in double, rounded to float).
+__device__ constexpr float kWin[11] = {0x1.0d956cp-10f, 0x1.f1fe02p-8f, 0x1.26eb18p-5f, 0x1.bff0fep-4f,
+                                       0x1.b43c40p-3f,  0x1.106560p-2f, 0x1.b43c40p-3f, 0x1.bff0fep-4f,
+                                       0x1.26eb18p-5f,  0x1.f1fe02p-8f, 0x1.0d956cp-10f};
 
 // N outputs of the 11-tap window from N + 10 consecutive inputs read once
 // (stride STRIDE floats apart).
 template <int N, int STRIDE>
-__device__ __forceinline__ void strip11(const float* src, const float w[11], float out[N]) {
+__device__ __forceinline__ void strip11(const float* src, float out[N]) {
     float in[N + 10];
 #pragma unroll
     for (int k = 0; k < N + 10; ++k) in[k] = src[k * STRIDE];
@@ -71,7 +64,24 @@ __device__ __forceinline__ void strip11(const float* src, const float w[11], flo
     for (int o = 0; o < N; ++o) {
         float acc = 0.f;
 #pragma unroll
-        for (int j = 0; j < 11; ++j) acc += w[j] * in[o + j];
+        for (int j = 0; j < 11; ++j) acc += kWin[j] * in[o + j];
+        out[o] = acc;
+    }
+}
+
+// The same for two maps at once (a and b, same layout): each tap is one packed
+// two-lane FMA (fma.rn.f32x2, each lane rounded as a scalar FMA), so the
+// results equal two strip11 calls.
+template <int N, int STRIDE>
+__device__ __forceinline__ void strip11x2(const float* a, const float* b, float2 out[N]) {
+    float2 in[N + 10];
+#pragma unroll
+    for (int k = 0; k < N + 10; ++k) in[k] = make_float2(a[k * STRIDE], b[k * STRIDE]);
+#pragma unroll
+    for (int o = 0; o < N; ++o) {
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < 11; ++j) acc = __ffma2_rn(make_float2(kWin[j], kWin[j]), in[o + j], acc);
         out[o] = acc;
     }
 }
@@ -134,8 +144,6 @@ __global__ void __launch_bounds__(kLossThreads, 3) loss_kernel(
     LossSmem& S = *reinterpret_cast<LossSmem*>(smem_raw);
     __shared__ float s_red[3][kLossThreads / 32];
     __shared__ int s_view, s_first;
-    float w[11];
-    window(w);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     int n_items = 0;
     for (int v = 0; v < n_views; ++v)
@@ -190,30 +198,24 @@ __global__ void __launch_bounds__(kLossThreads, 3) loss_kernel(
         constexpr int kHS = 3, kHN = kR1 / kHS;
         for (int k = tid; k < kR2 * kHN; k += kLossThreads) {
             const int r = k / kHN, c0 = (k - r * kHN) * kHS;
-            float xin[kHS + 10], yin[kHS + 10];
+            // packed pairs: (x, y) and (x^2 + y^2, xy), one two-lane FMA per tap and pair
+            float2 xy2[kHS + 10], qp[kHS + 10];
 #pragma unroll
             for (int j = 0; j < kHS + 10; ++j) {
-                xin[j] = S.a.in.x[r][c0 + j];
-                yin[j] = S.a.in.y[r][c0 + j];
-            }
-            float sq[kHS + 10], xy[kHS + 10];
-#pragma unroll
-            for (int j = 0; j < kHS + 10; ++j) {
-                sq[j] = xin[j] * xin[j] + yin[j] * yin[j];
-                xy[j] = xin[j] * yin[j];
+                xy2[j] = make_float2(S.a.in.x[r][c0 + j], S.a.in.y[r][c0 + j]);
+                qp[j] = make_float2(xy2[j].x * xy2[j].x + xy2[j].y * xy2[j].y, xy2[j].x * xy2[j].y);
             }
 #pragma unroll
             for (int o = 0; o < kHS; ++o) {
-                float a = 0.f, b = 0.f, c = 0.f, e = 0.f;
+                float2 ab = make_float2(0.f, 0.f), ce = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int j = 0; j < 11; ++j) {
-                    a += w[j] * xin[o + j];
-                    b += w[j] * yin[o + j];
-                    c += w[j] * sq[o + j];
-                    e += w[j] * xy[o + j];
+                    const float2 wj = make_float2(kWin[j], kWin[j]);
+                    ab = __ffma2_rn(wj, xy2[o + j], ab);
+                    ce = __ffma2_rn(wj, qp[o + j], ce);
                 }
-                S.b.h[0][r][c0 + o] = a; S.b.h[1][r][c0 + o] = b; S.b.h[2][r][c0 + o] = c;
-                S.b.h[3][r][c0 + o] = e;
+                S.b.h[0][r][c0 + o] = ab.x; S.b.h[1][r][c0 + o] = ab.y; S.b.h[2][r][c0 + o] = ce.x;
+                S.b.h[3][r][c0 + o] = ce.y;
             }
         }
         for (int r = wid; r < kOut; r += kLossThreads / 32) {
@@ -228,21 +230,21 @@ __global__ void __launch_bounds__(kLossThreads, 3) loss_kernel(
         float ssim_sum = 0.f;
         for (int k = tid; k < kR1 * kVN; k += kLossThreads) {
             const int cidx = k % kR1, r0 = (k / kR1) * kVS;
-            float mom[4][kVS];
-#pragma unroll
-            for (int f = 0; f < 4; ++f) strip11<kVS, kR1>(&S.b.h[f][r0][cidx], w, mom[f]);
+            float2 m01[kVS], m23[kVS];  // (mu_x, mu_y), (E[x^2 + y^2], E[xy])
+            strip11x2<kVS, kR1>(&S.b.h[0][r0][cidx], &S.b.h[1][r0][cidx], m01);
+            strip11x2<kVS, kR1>(&S.b.h[2][r0][cidx], &S.b.h[3][r0][cidx], m23);
             const int gx = ox - 5 + cidx;
 #pragma unroll
             for (int o = 0; o < kVS; ++o) {
                 const int r = r0 + o, gy = oy - 5 + r;
                 float dmu = 0.f, dxx = 0.f, dxy = 0.f;
                 if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
-                    const float mx = mom[0][o], my = mom[1][o];
+                    const float mx = m01[o].x, my = m01[o].y;
                     const float m2 = mx * mx + my * my;
-                    const float sxy = mom[3][o] - mx * my;
+                    const float sxy = m23[o].y - mx * my;
                     const float A1 = 2.f * mx * my + kC1, A2 = 2.f * sxy + kC2;
                     // B2 = var x + var y + C2 = E[x^2 + y^2] - mu_x^2 - mu_y^2 + C2
-                    const float B1 = m2 + kC1, B2 = mom[2][o] - m2 + kC2;
+                    const float B1 = m2 + kC1, B2 = m23[o].x - m2 + kC2;
                     // B1 >= C1 and B2 ~ >= C2: the hardware reciprocal (within 2 ulp)
                     const float iB1 = __fdividef(1.0f, B1), iB2 = __fdividef(1.0f, B2);
                     const float iB = iB1 * iB2;
@@ -258,14 +260,25 @@ __global__ void __launch_bounds__(kLossThreads, 3) loss_kernel(
             }
         }
         __syncthreads();
-        // 4. horizontal pass of the partials: 42 rows x 32 columns in strips of 8
-        for (int k = tid; k < 3 * kR1 * 4; k += kLossThreads) {
-            const int f = k / (kR1 * 4), rem = k - f * (kR1 * 4);
+        // 4. horizontal pass of the partials: 42 rows x 32 columns in strips of 8,
+        //    the first two partials packed (168 strips), the third alone (168)
+        for (int k = tid; k < 2 * kR1 * 4; k += kLossThreads) {
+            const int rem = k < kR1 * 4 ? k : k - kR1 * 4;
             const int r = rem >> 2, c0 = (rem & 3) * 8;
-            float out[8];
-            strip11<8, 1>(&S.a.part[f][r][c0], w, out);
+            if (k < kR1 * 4) {
+                float2 out[8];
+                strip11x2<8, 1>(&S.a.part[0][r][c0], &S.a.part[1][r][c0], out);
 #pragma unroll
-            for (int o = 0; o < 8; ++o) S.b.st.hp[f][r][c0 + o] = out[o];
+                for (int o = 0; o < 8; ++o) {
+                    S.b.st.hp[0][r][c0 + o] = out[o].x;
+                    S.b.st.hp[1][r][c0 + o] = out[o].y;
+                }
+            } else {
+                float out[8];
+                strip11<8, 1>(&S.a.part[2][r][c0], out);
+#pragma unroll
+                for (int o = 0; o < 8; ++o) S.b.st.hp[2][r][c0 + o] = out[o];
+            }
         }
         __syncthreads();
         // the input region and the alpha buffer are free: copy the next item's inputs
@@ -275,17 +288,17 @@ __global__ void __launch_bounds__(kLossThreads, 3) loss_kernel(
         float l1 = 0.f, la = 0.f;
         {
             const int cidx = tid % kOut, r0 = (tid / kOut) * 4;  // 32 columns x 8 strips = 256
-            float cm[4], cxx[4], cxy[4];
-            strip11<4, kOut>(&S.b.st.hp[0][r0][cidx], w, cm);
-            strip11<4, kOut>(&S.b.st.hp[1][r0][cidx], w, cxx);
-            strip11<4, kOut>(&S.b.st.hp[2][r0][cidx], w, cxy);
+            float2 cmx[4];  // (dSSIM/dmu_x, dSSIM/dE[x^2]) convolved back
+            float cxy[4];
+            strip11x2<4, kOut>(&S.b.st.hp[0][r0][cidx], &S.b.st.hp[1][r0][cidx], cmx);
+            strip11<4, kOut>(&S.b.st.hp[2][r0][cidx], cxy);
 #pragma unroll
             for (int o = 0; o < 4; ++o) {
                 const int r = r0 + o;
                 const int gy = oy + r, gx = ox + cidx;
                 if (gy >= H || gx >= W) continue;
                 const float xv = S.xo[r][cidx], yv = S.yo[r][cidx];
-                const float dssim = cm[o] + 2.f * xv * cxx[o] + yv * cxy[o];
+                const float dssim = cmx[o].x + 2.f * xv * cmx[o].y + yv * cxy[o];
                 const float diff = xv - yv;
                 const float sg = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
                 l1 += fabsf(diff);
