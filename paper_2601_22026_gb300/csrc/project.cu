@@ -290,44 +290,17 @@ __global__ void __launch_bounds__(256, 3) project_kernel(const float4* __restric
     }
 }
 
-// Adjoint of project_kernel, in two kernels.
-//
-// project_bwd_rec_kernel, one thread per binned (view, Gaussian) record (a 2D
-// grid: x over views, so that consecutive blocks read the same Gaussians from
-// L2; y over Gaussian blocks): chains the record's accumulated 2D gradients
-// through the conic, the EWA covariance, the Jacobian and the camera
-// transform, adds the view-direction term of the SH colour, and overwrites its
-// 16-float grad2d record with what the per-Gaussian sum needs: (dmean,
-// dopacity), dL/dSigma (6 entries) and the colour gradient with the clamp mask
-// applied. Fully parallel, so memory latency is hidden by occupancy rather
-// than by one thread's view loop.
-//
-// project_bwd_gauss_kernel, one thread per Gaussian: sums those records over
-// the views where the Gaussian was binned (zeroing them for the next
-// iteration), accumulates the SH-coefficient gradient, and chains dL/dSigma to
-// scale and rotation once.
-
+// The adjoint of one binned (view, Gaussian) record: from the accumulated 2D
+// gradients (ga: du, dv, dopacity; gb: da', db', dc'; gc: dr, dg, db) through
+// the conic, the EWA covariance, the Jacobian and the camera transform, plus
+// the view-direction term of the SH colour. Returns dL/dmean (this view's
+// part), dL/dSigma (xx xy xz yy yz zz) and the colour gradient with the clamp
+// mask (cm.w) applied.
 template <int DEG, int FT>
-__global__ void __launch_bounds__(256, 4) project_bwd_rec_kernel(const float4* __restrict__ P,
-                                                              const uint2* __restrict__ F, int n,
-                                                              const gsfit_camera* __restrict__ cams_g,
-                                                              const float4* __restrict__ xyd,
-                                                              const float4* __restrict__ conic,
-                                                              const float4* __restrict__ rgbm,
-                                                              float4* __restrict__ grad2d) {
-    const int i = blockIdx.y * blockDim.x + threadIdx.x;
-    const int v = blockIdx.x;
-    if (i >= n) return;
-    const size_t r = (size_t)v * n + i;
-    if (__ldg(&xyd[r].w) == 0.0f) return;  // not binned in this view
-    const float4 ga = grad2d[4 * r + 0];  // du, dv, dopacity
-    const float4 gb = grad2d[4 * r + 1];  // da', db', dc'
-    const float4 gc = grad2d[4 * r + 2];  // dr, dg, db
-    const float4 cq = __ldg(conic + r);
-    const float4 cm = __ldg(rgbm + r);
-    const gsfit_camera& cam = cams_g[v];
-    Gauss g;
-    load_gauss<FT>(P, F, n, i, g);
+__device__ __forceinline__ void record_bwd(const gsfit_camera& cam, const Gauss& g, float4 ga, float4 gb, float4 gc,
+                                           float4 cq, float4 cm, const float4* __restrict__ P,
+                                           const uint2* __restrict__ F, int n, int i, float (&dmean)[3],
+                                           float (&dSig)[6], float (&gcol)[3]) {
     ViewGeom vg;
     view_geom(cam, g, vg);
     const float iz = 1.0f / vg.tz, iz2 = iz * iz;
@@ -353,7 +326,6 @@ __global__ void __launch_bounds__(256, 4) project_bwd_rec_kernel(const float4* _
         u0[j] = dS00 * M0[j] + dS01 * M1[j];
         u1[j] = dS01 * M0[j] + dS11 * M1[j];
     }
-    float dSig[6];
     dSig[0] = M0[0] * u0[0] + M1[0] * u1[0];
     dSig[1] = M0[0] * u0[1] + M1[0] * u1[1];
     dSig[2] = M0[0] * u0[2] + M1[0] * u1[2];
@@ -387,12 +359,13 @@ __global__ void __launch_bounds__(256, 4) project_bwd_rec_kernel(const float4* _
         dtz -= dry * vg.ty * iz2;
     }
     // t = W mu + t_w
-    float dmean[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) dmean[j] = W[j] * dtx + W[4 + j] * dty + W[8 + j] * dtz;
     // colour: clamped channels pass no gradient
     const int mask = (int)cm.w;
-    const float gcol[3] = {(mask & 1) ? 0.f : gc.x, (mask & 2) ? 0.f : gc.y, (mask & 4) ? 0.f : gc.z};
+    gcol[0] = (mask & 1) ? 0.f : gc.x;
+    gcol[1] = (mask & 2) ? 0.f : gc.y;
+    gcol[2] = (mask & 4) ? 0.f : gc.z;
     if (DEG > 0) {
         // colour = sum_k c_k Y_k(d), d = (mu - campos) / |mu - campos|
         constexpr int K = SH<DEG>::K;
@@ -411,22 +384,40 @@ __global__ void __launch_bounds__(256, 4) project_bwd_rec_kernel(const float4* _
         dmean[1] += (dd.y - dy * proj) * idist;
         dmean[2] += (dd.z - dz * proj) * idist;
     }
-    grad2d[4 * r + 0] = make_float4(dmean[0], dmean[1], dmean[2], ga.z);
-    grad2d[4 * r + 1] = make_float4(dSig[0], dSig[1], dSig[2], dSig[3]);
-    grad2d[4 * r + 2] = make_float4(dSig[4], dSig[5], gcol[0], gcol[1]);
-    grad2d[4 * r + 3] = make_float4(gcol[2], 0.f, 0.f, 0.f);
 }
 
+// Adjoint of project_kernel: one thread per Gaussian walks the views where the
+// Gaussian was binned. Per view it reads the record's accumulated 2D
+// gradients (zeroing them for the next iteration) and chains them back
+// (record_bwd) while the next binned view's record loads are in flight; the
+// sums over views then go through the opacity sigmoid, the SH coefficients
+// (accumulators in shared memory) and dL/dSigma to scale and rotation once.
 constexpr int kProjBwdThreads = 256;
 
 // Accumulator k of this thread's SH gradient; [k][thread] layout, so a warp's
 // accesses hit 32 different banks.
 __device__ __forceinline__ float& dsh_acc(float* s_dsh, int k) { return s_dsh[k * kProjBwdThreads + threadIdx.x]; }
 
+// The loads of one binned record: 2D gradients and the record's conic and colour mask.
+struct RecIn {
+    float4 ga, gb, gc, cq, cm;
+};
+__device__ __forceinline__ RecIn load_rec(const float4* __restrict__ grad2d, const float4* __restrict__ conic,
+                                          const float4* __restrict__ rgbm, size_t r) {
+    RecIn x;
+    x.ga = grad2d[4 * r + 0];
+    x.gb = grad2d[4 * r + 1];
+    x.gc = grad2d[4 * r + 2];
+    x.cq = __ldg(conic + r);
+    x.cm = __ldg(rgbm + r);
+    return x;
+}
+
 template <int DEG, int FT>
-__global__ void __launch_bounds__(kProjBwdThreads, 3) project_bwd_gauss_kernel(
-    const float4* __restrict__ P, const uint2* __restrict__ F, int n, const gsfit_camera* __restrict__ cams_g, int n_views,
-    const float4* __restrict__ xyd, float4* __restrict__ grad2d, float4* __restrict__ G) {
+__global__ void __launch_bounds__(kProjBwdThreads, 2) project_bwd_kernel(
+    const float4* __restrict__ P, const uint2* __restrict__ F, int n, const gsfit_camera* __restrict__ cams_g,
+    int n_views, const float4* __restrict__ xyd, const float4* __restrict__ conic, const float4* __restrict__ rgbm,
+    float4* __restrict__ grad2d, float4* __restrict__ G) {
     // dynamic shared memory: the camera table, then 3K SH-gradient accumulators
     // per thread (kept out of registers)
     extern __shared__ __align__(16) unsigned char smem_pb[];
@@ -439,7 +430,8 @@ __global__ void __launch_bounds__(kProjBwdThreads, 3) project_bwd_gauss_kernel(
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const float4 mean = P[i];  // the rest of the Gaussian is loaded after the view loop
+    Gauss g;
+    load_gauss<FT>(P, F, n, i, g);
 
     float dmean[3] = {0.f, 0.f, 0.f};
     float dSig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // xx xy xz yy yz zz (symmetric, dL/dSigma_ij)
@@ -447,44 +439,49 @@ __global__ void __launch_bounds__(kProjBwdThreads, 3) project_bwd_gauss_kernel(
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
 
     for (int v0 = 0; v0 < n_views; v0 += 32) {
-      // visibility of up to 32 views first: independent loads, one latency
-      uint32_t vis = 0;
-      const int vn = min(32, n_views - v0);
+        // visibility of up to 32 views first: independent loads, one latency
+        uint32_t vis = 0;
+        const int vn = min(32, n_views - v0);
 #pragma unroll 8
-      for (int k = 0; k < vn; ++k)
-          if (__ldg(&xyd[(size_t)(v0 + k) * n + i].w) != 0.0f) vis |= 1u << k;
-      while (vis) {
-        const int v = v0 + __ffs(vis) - 1;
+        for (int k = 0; k < vn; ++k)
+            if (__ldg(&xyd[(size_t)(v0 + k) * n + i].w) != 0.0f) vis |= 1u << k;
+        if (!vis) continue;
+        int v = v0 + __ffs(vis) - 1;
         vis &= vis - 1;
-        const size_t r = (size_t)v * n + i;
-        const float4 a = grad2d[4 * r + 0];
-        const float4 b = grad2d[4 * r + 1];
-        const float4 c = grad2d[4 * r + 2];
-        const float4 d = grad2d[4 * r + 3];
-        grad2d[4 * r + 0] = zero;
-        grad2d[4 * r + 1] = zero;
-        grad2d[4 * r + 2] = zero;
-        grad2d[4 * r + 3] = zero;
-        dmean[0] += a.x; dmean[1] += a.y; dmean[2] += a.z;
-        dop += a.w;
-        dSig[0] += b.x; dSig[1] += b.y; dSig[2] += b.z; dSig[3] += b.w; dSig[4] += c.x; dSig[5] += c.y;
-        const float gcol[3] = {c.z, c.w, d.x};
-        const gsfit_camera& cam = cams[v];
-        float dx = mean.x - cam.campos[0], dy = mean.y - cam.campos[1], dz = mean.z - cam.campos[2];
-        const float idist = rsqrtf(dx * dx + dy * dy + dz * dz);
-        dx *= idist; dy *= idist; dz *= idist;
-        float Y[K];
-        sh_basis<DEG>(dx, dy, dz, Y);
+        RecIn cur = load_rec(grad2d, conic, rgbm, (size_t)v * n + i);
+        for (;;) {
+            // the next binned view's loads go out before this view's chain
+            const int vnext = vis ? v0 + __ffs(vis) - 1 : -1;
+            vis &= vis - 1;
+            RecIn nxt;
+            if (vnext >= 0) nxt = load_rec(grad2d, conic, rgbm, (size_t)vnext * n + i);
+            const size_t r = (size_t)v * n + i;
+            grad2d[4 * r + 0] = zero;  // the adjoint's atomics fill these three
+            grad2d[4 * r + 1] = zero;
+            grad2d[4 * r + 2] = zero;
+            const gsfit_camera& cam = cams[v];
+            float dm[3], dS[6], gcol[3];
+            record_bwd<DEG, FT>(cam, g, cur.ga, cur.gb, cur.gc, cur.cq, cur.cm, P, F, n, i, dm, dS, gcol);
+            dmean[0] += dm[0]; dmean[1] += dm[1]; dmean[2] += dm[2];
+            dop += cur.ga.z;
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            dsh_acc(s_dsh, 3 * k + 0) += Y[k] * gcol[0];
-            dsh_acc(s_dsh, 3 * k + 1) += Y[k] * gcol[1];
-            dsh_acc(s_dsh, 3 * k + 2) += Y[k] * gcol[2];
+            for (int k = 0; k < 6; ++k) dSig[k] += dS[k];
+            float dx = g.mx - cam.campos[0], dy = g.my - cam.campos[1], dz = g.mz - cam.campos[2];
+            const float idist = rsqrtf(dx * dx + dy * dy + dz * dz);
+            dx *= idist; dy *= idist; dz *= idist;
+            float Y[K];
+            sh_basis<DEG>(dx, dy, dz, Y);
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                dsh_acc(s_dsh, 3 * k + 0) += Y[k] * gcol[0];
+                dsh_acc(s_dsh, 3 * k + 1) += Y[k] * gcol[1];
+                dsh_acc(s_dsh, 3 * k + 2) += Y[k] * gcol[2];
+            }
+            if (vnext < 0) break;
+            v = vnext;
+            cur = nxt;
         }
-      }
     }
-    Gauss g;
-    load_gauss<FT>(P, F, n, i, g);
     const float opacity = 1.0f / (1.0f + expf(-g.logit));
     const float dlogit = dop * opacity * (1.f - opacity);
 
@@ -552,11 +549,6 @@ int launch_project_bwd(const gsfit_gaussians* g, const gsfit_proj* proj, const g
     const int blocks = (g->n + threads - 1) / threads;
     const float4* P = reinterpret_cast<const float4*>(g->params);
     const uint2* F = reinterpret_cast<const uint2*>(g->features);
-    dim3 grid_rec((unsigned)V, (unsigned)blocks);
-    project_bwd_rec_kernel<DEG, FT><<<grid_rec, threads, 0, s>>>(
-        P, F, g->n, cams, reinterpret_cast<const float4*>(proj->xyd), reinterpret_cast<const float4*>(proj->conic),
-        reinterpret_cast<const float4*>(proj->rgb), reinterpret_cast<float4*>(grad2d));
-    GSFIT_LAUNCH_CHECK();
     const size_t smem = sizeof(gsfit_camera) * V + sizeof(float) * 3 * SH<DEG>::K * threads;
     static bool attr_done[64] = {false};
     int dev = 0;
@@ -564,12 +556,13 @@ int launch_project_bwd(const gsfit_gaussians* g, const gsfit_proj* proj, const g
     if (dev < 0 || dev >= 64) return GSFIT_ERR_CUDA;
     if (!attr_done[dev]) {
         const size_t max_smem = sizeof(gsfit_camera) * GSFIT_MAX_VIEWS + sizeof(float) * 3 * SH<DEG>::K * threads;
-        GSFIT_CUDA_CHECK(cudaFuncSetAttribute(project_bwd_gauss_kernel<DEG, FT>,
+        GSFIT_CUDA_CHECK(cudaFuncSetAttribute(project_bwd_kernel<DEG, FT>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem));
         attr_done[dev] = true;
     }
-    project_bwd_gauss_kernel<DEG, FT><<<blocks, threads, smem, s>>>(
-        P, F, g->n, cams, V, reinterpret_cast<const float4*>(proj->xyd), reinterpret_cast<float4*>(grad2d),
+    project_bwd_kernel<DEG, FT><<<blocks, threads, smem, s>>>(
+        P, F, g->n, cams, V, reinterpret_cast<const float4*>(proj->xyd), reinterpret_cast<const float4*>(proj->conic),
+        reinterpret_cast<const float4*>(proj->rgb), reinterpret_cast<float4*>(grad2d),
         reinterpret_cast<float4*>(grads));
     GSFIT_LAUNCH_CHECK();
     return GSFIT_OK;
