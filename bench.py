@@ -640,8 +640,8 @@ def main() -> None:
     dominant = max(stage_ms, key=stage_ms.get)
     # project 1; bin_sort: reduce, scan, compact, 4 depth passes, sorted
     # reduce + scan, emit, tile passes, ranges, 2 tile-order kernels; render 1;
-    # loss (memset node excluded) 2; adjoint: blend 1 + projection 2; adam 2
-    launches_per_step = 1 + (13 + tile_passes) + 1 + 2 + 3 + 2
+    # loss (memset node excluded) 2; adjoint: blend 1 + projection 1; adam 2
+    launches_per_step = 1 + (13 + tile_passes) + 1 + 2 + 2 + 2
     kernel_of = {"blend_bwd": "render_bwd_kernel", "render_fwd": "render_fwd_kernel", "loss": "loss_kernel",
                  "project": "project_kernel", "adam": "adam_kernel", "project_bwd": "project_bwd_kernel"}
     traffic = measured_traffic(kernel_of.get(dominant, dominant))
