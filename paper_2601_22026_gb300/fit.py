@@ -342,3 +342,69 @@ class GsfitRender(torch.autograd.Function):
 
 def render(params, state: FitState):
     return GsfitRender.apply(params, state)
+
+
+class HostFeed:
+    """Feeds a FitState new per-step inputs (target images and backgrounds)
+    from pinned host memory, as a frame source (the path tracer's views) does
+    on every step, without stalling the GPU.
+
+    prefetch(k) starts copying step k's inputs into one of two staging
+    buffers on a copy stream; step() moves the staged inputs into the state
+    with a device-to-device copy (tens of microseconds instead of the
+    host-to-device transfer), replays the captured iteration and starts the
+    device-to-host copy of its loss; loss(handle) waits for that copy only.
+    So the transfer of step k + 1 overlaps step k, and reading step k's loss
+    while step k + 1 runs keeps the GPU busy. Staging buffer k % 2 is reused
+    by prefetch(k + 2) only after step k has consumed it."""
+
+    def __init__(self, state: FitState):
+        self.st = state
+        self.copy_stream = torch.cuda.Stream()
+        self.stage = [(torch.empty_like(state.target_rgb), torch.empty_like(state.target_alpha),
+                       torch.empty_like(state.bg)) for _ in range(2)]
+        self.staged = [torch.cuda.Event() for _ in range(2)]
+        self.consumed = [torch.cuda.Event() for _ in range(2)]
+        self.loss_host = [torch.empty(1, dtype=torch.float32).pin_memory() for _ in range(2)]
+        self.loss_done = [torch.cuda.Event() for _ in range(2)]
+        self.issued = 0  # prefetches issued
+        self.stepped = 0  # steps issued
+        self.h2d_bytes = state.target_rgb.numel() * 4 + state.target_alpha.numel() * 4 + state.bg.numel() * 4
+
+    def prefetch(self, host_rgb, host_alpha, host_bg) -> None:
+        """Copies the next step's inputs (pinned host tensors) to the device."""
+        b = self.issued % 2
+        rgb, alpha, bg = self.stage[b]
+        with torch.cuda.stream(self.copy_stream):
+            if self.issued >= 2:
+                self.copy_stream.wait_event(self.consumed[b])
+            rgb.copy_(host_rgb, non_blocking=True)
+            alpha.copy_(host_alpha, non_blocking=True)
+            bg.copy_(host_bg, non_blocking=True)
+            self.staged[b].record(self.copy_stream)
+        self.issued += 1
+
+    def step(self) -> int:
+        """One fit iteration on the oldest staged inputs; returns a handle for loss()."""
+        if self.stepped >= self.issued:
+            raise RuntimeError("HostFeed.step without a prefetched input")
+        b = self.stepped % 2
+        st = self.st
+        cur = torch.cuda.current_stream()
+        cur.wait_event(self.staged[b])
+        rgb, alpha, bg = self.stage[b]
+        st.target_rgb.copy_(rgb)
+        st.target_alpha.copy_(alpha)
+        st.bg.copy_(bg)
+        self.consumed[b].record(cur)
+        st.replay()
+        self.loss_host[b].copy_(st.loss_out, non_blocking=True)
+        self.loss_done[b].record(cur)
+        self.stepped += 1
+        return b
+
+    def loss(self, handle: int) -> float:
+        """The loss of the step with this handle (waits for that step only);
+        read it before issuing two more steps."""
+        self.loss_done[handle].synchronize()
+        return float(self.loss_host[handle].item())

@@ -129,3 +129,46 @@ def test_checkpoint_resume(tmp_path, reset):
         torch.cuda.synchronize()
         # the same updates (up to the order of the adjoint's float atomics)
         torch.testing.assert_close(b.params, a.params, rtol=1e-4, atol=1e-6)
+
+
+def test_host_feed_matches_synchronous_steps():
+    """HostFeed (inputs streamed from pinned host memory, the next step's copy
+    overlapping the current step, losses read one step behind) gives the same
+    loss sequence as copying the inputs and stepping synchronously."""
+    from paper_2601_22026_gb300.fit import FitState, HostFeed, boosted_lr
+    cams = scenes.periphery_batch_cameras(3, n_crops=3, **KW)
+    V = len(cams["width"])
+    tgt = FitState(scenes.random_gaussians(5000, 3, 92, log_scale_mean=-4.0), cams, bg=np.zeros((V, 3), np.float32))
+    tgt.forward()
+    host_rgb = tgt.rgb.cpu().pin_memory()
+    host_alpha = tgt.alpha.cpu().pin_memory()
+    bgs = torch.from_numpy(scenes.backgrounds(V, 93, n_steps=6)).pin_memory()
+    runs = []
+    for streamed in (False, True):
+        st = FitState(scenes.random_gaussians(5000, 3, 91, log_scale_mean=-4.0), cams, bg=bgs[0].numpy(),
+                      lr=boosted_lr())
+        st.capture()
+        losses = []
+        if streamed:
+            feed = HostFeed(st)
+            feed.prefetch(host_rgb, host_alpha, bgs[0])
+            prev = None
+            for k in range(6):
+                if k + 1 < 6:
+                    feed.prefetch(host_rgb, host_alpha, bgs[k + 1])
+                h = feed.step()
+                if prev is not None:
+                    losses.append(feed.loss(prev))
+                prev = h
+            losses.append(feed.loss(prev))
+        else:
+            for k in range(6):
+                st.target_rgb.copy_(host_rgb)
+                st.target_alpha.copy_(host_alpha)
+                st.bg.copy_(bgs[k])
+                st.replay()
+                losses.append(float(st.loss_out.item()))
+        assert st.check_status() == 0
+        runs.append(np.array(losses))
+    assert runs[0][0] > runs[0][-1]  # the fit progresses
+    np.testing.assert_allclose(runs[1], runs[0], rtol=1e-4)
