@@ -6,22 +6,21 @@
 // min(0.99, o exp(power)) (skip if < 1/255), stop before T would drop below
 // 1e-4, C = sum c alpha T + T_N bg, A = 1 - T_N.
 //
-// Design: one 256-thread CTA per 16 x 16 tile, one pixel per thread; warp w
-// owns an 8 x 4 pixel box (two boxes across, four down). Tiles are launched in
-// the heavy-first order gsfit_bin_sort produces, so the longest lists do not
-// form the tail of the grid. The CTA stages the tile's records in batches of
-// 256 (one coalesced record per thread); each warp then compacts, with a
-// ballot, the batch entries that reach alpha >= 1/255 somewhere in its box
-// (the exact minimum of the splat's quadratic form over the box, with slack
-// for rounding: every pixel of the box would skip the others anyway) and
-// walks only those. The adjoint copies the
-// next batch with cp.async while it works on the current one (the forward, which
-// often stops early, stages one batch at a time). The adjoint
-// keeps no per-(pixel, Gaussian) state: it restarts from the stored final
-// transmittance and contributor count and recovers T_i = T_{i+1} / (1 -
-// alpha_i) walking backwards, and sums the nine per-Gaussian gradient terms of
-// the warp with a transposed butterfly (12 shuffles instead of 45) that
-// leaves each total in its own lane, so one predicated scalar-atomic
+// Design: one CTA per tile (TILE = 16: eight pixel warps; 8: two), one pixel
+// per thread, warp w owning an 8 x 4 pixel box, plus one producer warp. Tiles
+// are launched in the heavy-first order gsfit_bin_sort produces, so the
+// longest lists do not form the tail of the grid. The producer gathers the
+// tile's records into a ring of shared-memory slots (cp.async, mbarrier
+// hand-over, bounded waits); each pixel warp compacts, with a ballot, the slot
+// entries that can reach alpha >= 1/255 at one of its pixels still in play
+// (the exact minimum of the splat's quadratic form over the bounding
+// rectangle of those pixel centres, with slack for rounding, so the cull
+// never changes a result) and walks only those, one branch-free step per
+// entry. The adjoint keeps no per-(pixel, Gaussian) state: it restarts from
+// the stored final transmittance and contributor count and recovers T_i =
+// T_{i+1} / (1 - alpha_i) walking backwards, and sums the nine per-Gaussian
+// gradient terms of the warp with a transposed butterfly (12 shuffles instead
+// of 45) that leaves each total in its own lane, so one scalar-atomic
 // instruction of nine lanes accumulates them.
 #include "common.cuh"
 
