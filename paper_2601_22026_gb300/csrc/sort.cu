@@ -52,7 +52,6 @@ constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagInc = 1u << 31;
 constexpr uint32_t kValMask = kFlagAgg - 1u;
 constexpr int kSpinLimit = 1 << 20;  // x ~100 ns sleeps: about a tenth of a second
-constexpr int kHistBlocks = 1024;
 
 constexpr int kDepthPasses = 4;  // 8-bit digits over the 32 depth bits
 
@@ -366,29 +365,15 @@ __global__ void __launch_bounds__(kScanThreads) emit_kernel(const unsigned long 
     }
 }
 
-// Waits until a look-back word carries a flag (aggregate or inclusive prefix)
-// and returns it in f; false, with GSFIT_ERR_TIMEOUT in the status word, after
-// `limit` polls of ~100 ns.
-__device__ __forceinline__ bool lookback_poll(const uint32_t* word, uint32_t& f, int32_t* status, int limit) {
-    for (int spins = 0;; ++spins) {
-        f = *reinterpret_cast<const volatile uint32_t*>(word);
-        if (f & (kFlagInc | kFlagAgg)) return true;
-        if (spins >= limit) {
-            if (status) atomicExch(status, GSFIT_ERR_TIMEOUT);
-            return false;
-        }
-        __nanosleep(100);
-    }
-}
-
 // Exclusive prefix of digit d over partitions [0, p], looked up kLookWindow
 // partitions per round trip: the window's words are read together and
 // consumed newest first while they carry a flag, up to the first inclusive
 // prefix. A window whose newest word carries no flag is polled again after
-// ~100 ns, at most kSpinLimit times in a row (then GSFIT_ERR_TIMEOUT).
+// ~100 ns, at most `limit` times in a row (then GSFIT_ERR_TIMEOUT). With
+// p = 0 only lb[d] is read.
 constexpr int kLookWindow = 8;
 __device__ __forceinline__ void lookback_window(const uint32_t* lb, int p, int d, uint32_t& excl,
-                                                int32_t* status) {
+                                                int32_t* status, int limit = kSpinLimit) {
     int idle = 0;
     while (p >= 0) {
         uint32_t f[kLookWindow];
@@ -408,7 +393,7 @@ __device__ __forceinline__ void lookback_window(const uint32_t* lb, int p, int d
         }
         if (inc) return;
         if (used == 0) {
-            if (++idle > kSpinLimit) {
+            if (++idle > limit) {
                 if (status) atomicExch(status, GSFIT_ERR_TIMEOUT);
                 return;
             }
@@ -422,8 +407,8 @@ __device__ __forceinline__ void lookback_window(const uint32_t* lb, int p, int d
 
 // Diagnostic: polls a look-back word nothing will ever set.
 __global__ void lookback_selftest_kernel(const uint32_t* word, int limit, int32_t* status) {
-    uint32_t f;
-    lookback_poll(word, f, status, limit);
+    uint32_t excl = 0;
+    lookback_window(word, 0, 0, excl, status, limit);  // partition 0's word of digit 0: word[0] only
 }
 
 struct OnesweepSmem {
