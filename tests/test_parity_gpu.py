@@ -44,6 +44,10 @@ CASES = {
                            scenes.stack_cameras([scenes.make_camera((0, 0, 3), (0, 0, 0), 45, 29, fx=40.0)])),
     # splats of tens to hundreds of tiles each: rows of records with more pairs than a warp has lanes, and
     # tile lists spanning several shared-memory slots
+    # the largest view batch the calls accept (GSFIT_MAX_VIEWS): the camera table at its largest in shared
+    # memory, the longest view search per tile, ragged 24 x 17 views
+    "max_views": lambda: (scenes.random_gaussians(500, 1, 15, log_scale_mean=-2.8),
+                          scenes.orbit_cameras(256, 24, 17, 60.0, 3.0, 16)),
     "big_splats": lambda: (scenes.random_gaussians(300, 2, 14, log_scale_mean=-1.3),
                            scenes.stack_cameras([scenes.make_camera((0.3, -0.2, 3), (0, 0, 0), 250, 190, fx=220.0),
                                                  scenes.make_camera((-2, 1, 2), (0, 0, 0), 130, 97, fx=120.0)])),
@@ -267,9 +271,10 @@ def test_render_bwd_matches_oracle(name):
     torch.cuda.synchronize()
     ref = oracle.render_bwd(gs, cams, bg, w_rgb.astype(np.float64), w_a.astype(np.float64))
     amb = ref["gauss_ambiguous"].any(axis=0) | (oracle.project(gs, cams)[:, :, F["near_boundary"]] > 0).any(axis=0)
-    # a splat covering thousands of pixels almost always has some pixel of its alpha = 1/255 edge ring within
-    # the float32 margin of the threshold: such Gaussians are excluded, and for the big splats most are
-    assert amb.mean() < (0.6 if name == "big_splats" else 0.05)
+    # a Gaussian is excluded if some pixel of its alpha = 1/255 edge ring (or a clamp or stop decision) lies
+    # within the float32 margin of the threshold; the more pixels it touches, the likelier: thousands per
+    # splat in big_splats, up to 256 views per Gaussian in max_views
+    assert amb.mean() < {"big_splats": 0.6, "max_views": 0.4}.get(name, 0.05)
     _grad_check(st.gradients(), ref["grads"], amb)
     # grad2d workspace is left zeroed for the next iteration
     assert float(st.grad2d.abs().max().item()) == 0.0
