@@ -299,9 +299,11 @@ def test_autograd_function_matches_oracle():
 
 
 def test_loss_matches_oracle():
+    # ragged views; the 128 x 96 view has tiles whose 52 x 52 input region lies inside the image (the
+    # kernel's path without per-element bounds tests), the others only border tiles
     cams = scenes.stack_cameras([scenes.make_camera((0, 0, 3), (0, 0, 0), w, h, fx=50.0)
-                                 for w, h in [(45, 37), (64, 64), (100, 33), (7, 5)]])
-    V = 4
+                                 for w, h in [(45, 37), (64, 64), (100, 33), (7, 5), (128, 96)]])
+    V = 5
     g = scenes.rng(31)
     img = scenes.smooth_images(cams, 32, channels=4)
     tgt = scenes.smooth_images(cams, 33, channels=4)
