@@ -367,7 +367,8 @@ __global__ void __launch_bounds__(TileShape<TILE>::kThreads) render_fwd_kernel(
 
     const TileCtx c = tile_ctx<TILE>(cams, n_views, t);
     const float fx = (float)c.px, fy = (float)c.py;
-    float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+    float T = 1.0f, C2 = 0.f;
+    float2 C01 = make_float2(0.f, 0.f);  // red and green, accumulated by one packed FMA
     uint32_t last = 0;
     bool done = !c.inside;
     bool wdone = __all_sync(0xffffffffu, done);
@@ -393,8 +394,7 @@ __global__ void __launch_bounds__(TileShape<TILE>::kThreads) render_fwd_kernel(
                 const bool stop = hit && test_T < kTStop;
                 const bool blend = hit && !stop;
                 const float wgt = blend ? alpha * T : 0.0f;  // this pixel's blend weight of entry j
-                C0 += col.x * wgt;
-                C1 += col.y * wgt;
+                C01 = __ffma2_rn(make_float2(col.x, col.y), make_float2(wgt, wgt), C01);
                 C2 += col.z * wgt;
                 T = blend ? test_T : T;
                 last = blend ? base + (uint32_t)j + 1u : last;  // one past this list position
@@ -435,8 +435,8 @@ __global__ void __launch_bounds__(TileShape<TILE>::kThreads) render_fwd_kernel(
     }
     if (c.inside && !skip) {
         const float* bgv = bg + 3 * c.view;
-        out_rgb[c.rgb_base] = C0 + T * bgv[0];
-        out_rgb[c.rgb_base + c.plane] = C1 + T * bgv[1];
+        out_rgb[c.rgb_base] = C01.x + T * bgv[0];
+        out_rgb[c.rgb_base + c.plane] = C01.y + T * bgv[1];
         out_rgb[c.rgb_base + 2 * c.plane] = C2 + T * bgv[2];
         out_alpha[c.pix] = 1.0f - T;
         out_T[c.pix] = T;
@@ -450,29 +450,37 @@ __global__ void __launch_bounds__(TileShape<TILE>::kThreads) render_fwd_kernel(
 // pair (l, l ^ 1) holds the warp total of value reduce9_slot(l).
 __device__ __forceinline__ float reduce9(const float* v, int lane) {
     const bool b1 = lane & 16, b2 = lane & 8, b3 = lane & 4, b4 = lane & 2;
-    float w1[5];
+    // each level: send one half of every value pair, keep the other, and add
+    // the received halves two at a time (add.rn.f32x2)
+    float k1[6], r1[6];
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
         const float lo = v[k], hi = (k < 4) ? v[5 + k] : 0.f;
-        const float r = __shfl_xor_sync(0xffffffffu, b1 ? lo : hi, 16);
-        w1[k] = (b1 ? hi : lo) + r;
+        r1[k] = __shfl_xor_sync(0xffffffffu, b1 ? lo : hi, 16);
+        k1[k] = b1 ? hi : lo;
     }
-    float w2[3];
+    const float2 w01 = __fadd2_rn(make_float2(k1[0], k1[1]), make_float2(r1[0], r1[1]));
+    const float2 w23 = __fadd2_rn(make_float2(k1[2], k1[3]), make_float2(r1[2], r1[3]));
+    const float w1[5] = {w01.x, w01.y, w23.x, w23.y, k1[4] + r1[4]};
+    float k2[3], r2[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const float lo = w1[k], hi = (k < 2) ? w1[3 + k] : 0.f;
-        const float r = __shfl_xor_sync(0xffffffffu, b2 ? lo : hi, 8);
-        w2[k] = (b2 ? hi : lo) + r;
+        r2[k] = __shfl_xor_sync(0xffffffffu, b2 ? lo : hi, 8);
+        k2[k] = b2 ? hi : lo;
     }
-    float w3[2];
+    const float2 w2p = __fadd2_rn(make_float2(k2[0], k2[1]), make_float2(r2[0], r2[1]));
+    const float w2[3] = {w2p.x, w2p.y, k2[2] + r2[2]};
+    float k3[2], r3[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const float lo = w2[k], hi = (k < 1) ? w2[2 + k] : 0.f;
-        const float r = __shfl_xor_sync(0xffffffffu, b3 ? lo : hi, 4);
-        w3[k] = (b3 ? hi : lo) + r;
+        r3[k] = __shfl_xor_sync(0xffffffffu, b3 ? lo : hi, 4);
+        k3[k] = b3 ? hi : lo;
     }
-    const float r4 = __shfl_xor_sync(0xffffffffu, b4 ? w3[0] : w3[1], 2);
-    const float w4 = (b4 ? w3[1] : w3[0]) + r4;
+    const float2 w3 = __fadd2_rn(make_float2(k3[0], k3[1]), make_float2(r3[0], r3[1]));
+    const float r4 = __shfl_xor_sync(0xffffffffu, b4 ? w3.x : w3.y, 2);
+    const float w4 = (b4 ? w3.y : w3.x) + r4;
     return w4 + __shfl_xor_sync(0xffffffffu, w4, 1);
 }
 
@@ -519,8 +527,11 @@ __device__ __forceinline__ bool pix_bwd_step(PixBwd& q, uint32_t pos, float4 co,
     const float T_behind = q.T;               // T_{i+1} = T_i (1 - alpha_i)
     q.T = hit ? T_behind * inv : T_behind;    // T_i, the transmittance in front of this Gaussian
     const float wT = alpha * q.T;
-    g9[6] = q.dC0 * wT;
-    g9[7] = q.dC1 * wT;
+    // pairs of independent products go through the packed two-lane FMA unit
+    // (fma.rn.f32x2 / mul.rn.f32x2: each half rounds like its scalar form)
+    const float2 c01 = __fmul2_rn(make_float2(q.dC0, q.dC1), make_float2(wT, wT));
+    g9[6] = c01.x;
+    g9[7] = c01.y;
     g9[8] = q.dC2 * wT;
     // dC_c/dalpha = T_i c_c - (S_c + T_N bg_c) / (1 - alpha), dA/dalpha =
     // T_N / (1 - alpha); with T_i (1 - alpha) = T_{i+1} the channel sum is
@@ -532,11 +543,17 @@ __device__ __forceinline__ bool pix_bwd_step(PixBwd& q, uint32_t pos, float4 co,
     const float dalpha = hit && a <= kAlphaClamp ? dalpha_f : 0.0f;
     const float dpow = dalpha * alpha;
     g9[2] = dalpha * G;
-    g9[0] = dpow * (co.x * dx + co.y * dy);
-    g9[1] = dpow * (co.z * dy + co.y * dx);
-    g9[3] = -0.5f * dpow * dx * dx;
+    // d(power)/d(u, v) = (a' dx + b' dy, c' dy + b' dx)
+    const float2 lin = __ffma2_rn(make_float2(co.x, co.z), make_float2(dx, dy),
+                                  __fmul2_rn(make_float2(co.y, co.y), make_float2(dy, dx)));
+    const float2 duv = __fmul2_rn(lin, make_float2(dpow, dpow));
+    g9[0] = duv.x;
+    g9[1] = duv.y;
+    const float hd = -0.5f * dpow;
+    const float2 dac = __fmul2_rn(make_float2(hd, hd), __fmul2_rn(make_float2(dx, dy), make_float2(dx, dy)));
+    g9[3] = dac.x;
     g9[4] = -dpow * dx * dy;
-    g9[5] = -0.5f * dpow * dy * dy;
+    g9[5] = dac.y;
     return hit;
 }
 

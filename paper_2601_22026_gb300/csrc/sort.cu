@@ -17,7 +17,11 @@
 //      counts, obtains its global digit offsets by decoupled look-back over
 //      earlier partitions (every wait bounded: on expiry the status word gets
 //      GSFIT_ERR_TIMEOUT), and writes its keys digit-run by digit-run so
-//      stores coalesce. Records are now in (depth, record index) order.
+//      stores coalesce. A pass whose digit is the same for every key (the
+//      histogram has one bucket holding them all, as the top depth byte is
+//      when all depths share a binary exponent) is the identity permutation:
+//      its CTAs copy their partitions instead. Records are now in (depth,
+//      record index) order.
 //   4. reduce_sorted_kernel / scan_blocks_kernel / emit_kernel: pair offsets
 //      in that order, then the pairs (tile id << 32 | depth, Gaussian index),
 //      with the tile-digit histograms; each warp deals its records' pairs out
@@ -241,122 +245,147 @@ __global__ void __launch_bounds__(kScanThreads) compact_kernel(const uint32_t* _
     }
 }
 
-// Pair counts of the depth-sorted records, per block of kScanChunk.
+// The emit kernel's unit of work: kEmitSeg consecutive depth-sorted records,
+// taken by one warp as rows of 32.
+constexpr int kEmitSeg = 128;
+constexpr int kSegsPerChunk = kScanChunk / kEmitSeg;
+static_assert(kSegsPerChunk == 32 && kScanItems * 2 == kSegsPerChunk, "one segment per half row of a chunk load");
+constexpr int kEmitBlocksPerSm = 5;
+
+// Pair counts of the depth-sorted records: per block of kScanChunk (the
+// total, scanned over blocks afterwards) and the exclusive offset of each
+// kEmitSeg-record segment within its block. Records are loaded block-striped,
+// so row j of the load holds segments 2j (warps 0-3) and 2j + 1 (warps 4-7).
 __global__ void __launch_bounds__(kScanThreads) reduce_sorted_kernel(const unsigned long long* __restrict__ rkeys,
                                                                      const SortCtl* __restrict__ ctl,
-                                                                     uint32_t* __restrict__ sums) {
-    __shared__ uint32_t s_warp[8];
+                                                                     uint32_t* __restrict__ sums,
+                                                                     uint32_t* __restrict__ seg_off) {
+    __shared__ uint32_t s_part[kScanItems][kScanThreads / 32];
     const uint32_t n = ctl->n_rec;
     const long long base = (long long)blockIdx.x * kScanChunk;
-    uint32_t acc = 0;
-    if (base < n) {
-#pragma unroll
-        for (int j = 0; j < kScanItems; ++j) {
-            const long long m = base + (long long)j * kScanThreads + threadIdx.x;
-            if (m < n) acc += (uint32_t)(rkeys[m] >> 32);
-        }
+    if (base >= n) {  // block-uniform: an empty block's sum is still scanned
+        if (threadIdx.x == 0) sums[blockIdx.x] = 0u;
+        return;
     }
-    uint32_t total;
-    block_excl_scan(acc, s_warp, total);
-    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        const long long m = base + (long long)j * kScanThreads + threadIdx.x;
+        const uint32_t c = m < n ? (uint32_t)(rkeys[m] >> 32) : 0u;
+        const uint32_t w = __reduce_add_sync(0xffffffffu, c);
+        if (lane == 0) s_part[j][wid] = w;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        const int j = lane >> 1, h = 4 * (lane & 1);  // segment `lane` = half h / 4 of load row j
+        const uint32_t seg = s_part[j][h] + s_part[j][h + 1] + s_part[j][h + 2] + s_part[j][h + 3];
+        uint32_t incl = seg;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        seg_off[(size_t)blockIdx.x * kSegsPerChunk + lane] = incl - seg;
+        if (lane == 31) sums[blockIdx.x] = incl;
+    }
 }
 
 // Pairs of the depth-sorted records, in that order, with the tile-digit
-// histograms of the n_tile_passes tile passes. Warp w of a block takes the
-// block's sorted records [32 kScanItems w, 32 kScanItems (w + 1)) as rows of
-// 32 (one per lane); a row's pairs are dealt out to the lanes 32 at a time
-// (pair k goes to lane k mod 32, which finds the record owning it by binary
-// search over the row's inclusive counts), so every store is coalesced and a
-// large splat does not hold up the other lanes. The next row's record gather
-// is issued before the current row is dealt out.
-__global__ void __launch_bounds__(kScanThreads) emit_kernel(const unsigned long long* __restrict__ rkeys,
-                                                            const uint32_t* __restrict__ rvals,
-                                                            const float4* __restrict__ xyd, int n, int n_views,
-                                                            const gsfit_camera* __restrict__ cams_g,
-                                                            const uint32_t* __restrict__ sums,
-                                                            SortCtl* __restrict__ ctl, int n_tile_passes,
-                                                            unsigned long long* __restrict__ keys,
-                                                            uint32_t* __restrict__ vals) {
+// histograms of the n_tile_passes tile passes. A resident grid: every warp
+// takes kEmitSeg-record segments in turn (global warp index, then strided by
+// the grid's warp count), so the work has no wave tail whatever the record
+// count, and each block adds its histograms to the global ones once. A
+// segment is taken as 4 rows of 32 records (one per lane); a row's pairs are
+// dealt out to the lanes 32 at a time (pair k goes to lane k mod 32, which
+// finds the record owning it by binary search over the row's inclusive
+// counts), so every store is coalesced and a large splat does not hold up the
+// other lanes. The next row's record gather is issued before the current row
+// is dealt out.
+__global__ void __launch_bounds__(kScanThreads, kEmitBlocksPerSm) emit_kernel(
+    const unsigned long long* __restrict__ rkeys, const uint32_t* __restrict__ rvals,
+    const float4* __restrict__ xyd, int n, int n_views, const gsfit_camera* __restrict__ cams_g,
+    const uint32_t* __restrict__ sums, const uint32_t* __restrict__ seg_off, SortCtl* __restrict__ ctl,
+    int n_tile_passes, unsigned long long* __restrict__ keys, uint32_t* __restrict__ vals) {
+    constexpr int kRows = kEmitSeg / 32;
     extern __shared__ gsfit_camera cams[];
-    __shared__ uint32_t s_wtot[kScanThreads / 32];
     __shared__ uint32_t s_hist[kMaxPasses - kDepthPasses][kRadix];
+    const uint32_t n_recs = ctl->n_rec;
+    const long long n_segs = ((long long)n_recs + kEmitSeg - 1) / kEmitSeg;
+    const long long warps = (long long)gridDim.x * (kScanThreads / 32);
+    if ((long long)blockIdx.x * (kScanThreads / 32) >= n_segs) return;  // block-uniform
     load_cameras(cams, cams_g, n_views);
     for (int k = threadIdx.x; k < n_tile_passes * kRadix; k += blockDim.x) (&s_hist[0][0])[k] = 0u;
     __syncthreads();
-    const uint32_t n_recs = ctl->n_rec;
-    if ((long long)blockIdx.x * kScanChunk >= (long long)n_recs) return;  // block-uniform
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const long long wbase = (long long)blockIdx.x * kScanChunk + (long long)wid * (32 * kScanItems);
-    uint32_t cnt[kScanItems], rec[kScanItems];
-    uint32_t mine = 0;
+    const int lane = threadIdx.x & 31;
+    for (long long seg = (long long)blockIdx.x * (kScanThreads / 32) + (threadIdx.x >> 5); seg < n_segs;
+         seg += warps) {
+        const long long sbase = seg * kEmitSeg;
+        uint32_t offset = __ldg(sums + seg / kSegsPerChunk) + __ldg(seg_off + seg);
+        unsigned long long key[kRows];
+        uint32_t rec[kRows];
 #pragma unroll
-    for (int j = 0; j < kScanItems; ++j) {
-        const long long m = wbase + 32 * j + lane;
-        const bool ok = m < (long long)n_recs;
-        cnt[j] = ok ? (uint32_t)(__ldg(rkeys + m) >> 32) : 0u;
-        rec[j] = ok ? __ldg(rvals + m) : 0u;
-        mine += cnt[j];
-    }
-    const uint32_t wtot = __reduce_add_sync(0xffffffffu, mine);
-    if (lane == 0) s_wtot[wid] = wtot;
-    __syncthreads();
-    uint32_t offset = sums[blockIdx.x];
-    for (int w = 0; w < wid; ++w) offset += s_wtot[w];
-    float4 p_next = cnt[0] > 0u ? __ldg(xyd + rec[0]) : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-    for (int j = 0; j < kScanItems; ++j) {
-        const uint32_t c = cnt[j];
-        uint32_t inc = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += y;
+        for (int j = 0; j < kRows; ++j) {
+            const long long m = sbase + 32 * j + lane;
+            const bool ok = m < (long long)n_recs;
+            key[j] = ok ? __ldg(rkeys + m) : 0ull;
+            rec[j] = ok ? __ldg(rvals + m) : 0u;
         }
-        const uint32_t row = __shfl_sync(0xffffffffu, inc, 31);
-        const float4 p = p_next;
-        if (j + 1 < kScanItems && cnt[j + 1] > 0u) p_next = __ldg(xyd + rec[j + 1]);
-        if (row == 0u) continue;  // warp-uniform
-        // this lane's record: first tile id, tiles across the camera, rect width, depth, Gaussian index
-        uint32_t t0 = 0u, txn = 0u, rw = 1u, depth = 0u, gi = 0u;
-        if (c > 0u) {
-            const uint32_t r = rec[j];
-            const uint32_t v = r / (uint32_t)n;
-            gi = r - v * (uint32_t)n;
-            const gsfit_camera& cam = cams[v];
-            const int tx = tiles_x_of(cam);
-            const Rect rc = tile_rect(p.x, p.y, p.w, tx, tiles_y_of(cam), tile_of(cam));
-            txn = (uint32_t)tx;
-            rw = (uint32_t)max(rc.x1 - rc.x0, 1);
-            t0 = (uint32_t)(cam.tile_offset + rc.y0 * tx + rc.x0);
-            depth = (uint32_t)__ldg(rkeys + wbase + 32 * j + lane);
-        }
-        const uint32_t excl = inc - c;
-        for (uint32_t k0 = 0; k0 < row; k0 += 32) {
-            const uint32_t k = k0 + (uint32_t)lane;
-            int owner = 0;  // lanes whose inclusive count is <= k
+        float4 p_next = (key[0] >> 32) > 0ull ? __ldg(xyd + rec[0]) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                const uint32_t x = __shfl_sync(0xffffffffu, inc, owner + step - 1);
-                if (x <= k) owner += step;
+        for (int j = 0; j < kRows; ++j) {
+            const uint32_t c = (uint32_t)(key[j] >> 32);
+            uint32_t inc = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
             }
-            const uint32_t o_t0 = __shfl_sync(0xffffffffu, t0, owner);
-            const uint32_t o_txn = __shfl_sync(0xffffffffu, txn, owner);
-            const uint32_t o_rw = __shfl_sync(0xffffffffu, rw, owner);
-            const uint32_t o_depth = __shfl_sync(0xffffffffu, depth, owner);
-            const uint32_t o_gi = __shfl_sync(0xffffffffu, gi, owner);
-            const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, owner);
-            if (k < row) {
-                const uint32_t q = k - o_excl;  // row-major position in the owner's rect
-                uint32_t dy = (uint32_t)((float)q * __frcp_rn((float)o_rw));
-                if (dy * o_rw > q) --dy;  // exact floor(q / rw) after the float estimate
-                else if ((dy + 1u) * o_rw <= q) ++dy;
-                const uint32_t tile = o_t0 + dy * o_txn + (q - dy * o_rw);
-                keys[offset + k] = ((unsigned long long)tile << 32) | o_depth;
-                vals[offset + k] = o_gi;
-                for (int p = 0; p < n_tile_passes; ++p) atomicAdd(&s_hist[p][(tile >> (8 * p)) & 0xff], 1u);
+            const uint32_t row = __shfl_sync(0xffffffffu, inc, 31);
+            const float4 p = p_next;
+            if (j + 1 < kRows && (key[j + 1] >> 32) > 0ull) p_next = __ldg(xyd + rec[j + 1]);
+            if (row == 0u) continue;  // warp-uniform
+            // this lane's record: first tile id, tiles across the camera, rect width, depth, Gaussian index
+            uint32_t t0 = 0u, txn = 0u, rw = 1u, depth = 0u, gi = 0u;
+            if (c > 0u) {
+                const uint32_t r = rec[j];
+                const uint32_t v = r / (uint32_t)n;
+                gi = r - v * (uint32_t)n;
+                const gsfit_camera& cam = cams[v];
+                const int tx = tiles_x_of(cam);
+                const Rect rc = tile_rect(p.x, p.y, p.w, tx, tiles_y_of(cam), tile_of(cam));
+                txn = (uint32_t)tx;
+                rw = (uint32_t)max(rc.x1 - rc.x0, 1);
+                t0 = (uint32_t)(cam.tile_offset + rc.y0 * tx + rc.x0);
+                depth = (uint32_t)key[j];
             }
+            const uint32_t excl = inc - c;
+            for (uint32_t k0 = 0; k0 < row; k0 += 32) {
+                const uint32_t k = k0 + (uint32_t)lane;
+                int owner = 0;  // lanes whose inclusive count is <= k
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const uint32_t x = __shfl_sync(0xffffffffu, inc, owner + step - 1);
+                    if (x <= k) owner += step;
+                }
+                const uint32_t o_t0 = __shfl_sync(0xffffffffu, t0, owner);
+                const uint32_t o_txn = __shfl_sync(0xffffffffu, txn, owner);
+                const uint32_t o_rw = __shfl_sync(0xffffffffu, rw, owner);
+                const uint32_t o_depth = __shfl_sync(0xffffffffu, depth, owner);
+                const uint32_t o_gi = __shfl_sync(0xffffffffu, gi, owner);
+                const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, owner);
+                if (k < row) {
+                    const uint32_t q = k - o_excl;  // row-major position in the owner's rect
+                    uint32_t dy = (uint32_t)((float)q * __frcp_rn((float)o_rw));
+                    if (dy * o_rw > q) --dy;  // exact floor(q / rw) after the float estimate
+                    else if ((dy + 1u) * o_rw <= q) ++dy;
+                    const uint32_t tile = o_t0 + dy * o_txn + (q - dy * o_rw);
+                    keys[offset + k] = ((unsigned long long)tile << 32) | o_depth;
+                    vals[offset + k] = o_gi;
+                    for (int p = 0; p < n_tile_passes; ++p) atomicAdd(&s_hist[p][(tile >> (8 * p)) & 0xff], 1u);
+                }
+            }
+            offset += row;
         }
-        offset += row;
     }
     __syncthreads();
     for (int k = threadIdx.x; k < n_tile_passes * kRadix; k += blockDim.x) {
@@ -440,11 +469,33 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(const unsigne
     const uint32_t hist_d = ctl->hist[pass][threadIdx.x];  // this pass's count of digit threadIdx.x
     if (threadIdx.x == 0) S.part = atomicAdd(&ctl->part_counter[pass], 1u);
     for (int k = threadIdx.x; k < kSortWarps * (kRadix + 1); k += kSortThreads) (&S.warp_hist[0][0])[k] = 0u;
-    __syncthreads();
+    // one digit value holding every key: the stable pass is the identity permutation
+    const bool identity = __syncthreads_or(hist_d == n) != 0;
     const uint32_t part = S.part;
     if (part >= n_parts) return;
     const uint32_t base = part * kPart;
     const uint32_t valid = min((uint32_t)kPart, n - base);
+    if (identity) {  // block-uniform: copy the partition in place of ranking it
+        unsigned long long kc[kSortItems];
+        uint32_t vc[kSortItems];
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j) {
+            const uint32_t idx = (uint32_t)j * kSortThreads + threadIdx.x;
+            if (idx < valid) {
+                kc[j] = keys_in[base + idx];
+                vc[j] = vals_in[base + idx];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j) {
+            const uint32_t idx = (uint32_t)j * kSortThreads + threadIdx.x;
+            if (idx < valid) {
+                keys_out[base + idx] = kc[j];
+                vals_out[base + idx] = vc[j];
+            }
+        }
+        return;
+    }
 
     // Load (warp-striped, coalesced) and rank within the warp per digit. Keys
     // stay in registers; values wait in shared memory in input order.
@@ -619,7 +670,7 @@ __global__ void __launch_bounds__(256) order_scatter_kernel(const uint32_t* __re
 inline size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct SortLayout {
-    size_t pair_sums, rec_sums, sorted_sums, ctl, lookback, keys_alt, vals_alt, rkeys[2], rvals[2], total;
+    size_t pair_sums, rec_sums, sorted_sums, seg_off, ctl, lookback, keys_alt, vals_alt, rkeys[2], rvals[2], total;
     int n_blocks, tile_passes;
     long long max_parts, max_rec_parts, lookback_words;
 };
@@ -645,6 +696,7 @@ SortLayout layout(long long n_rec, long long capacity, int total_tiles) {
     L.pair_sums = o; o = align_up(o + sizeof(uint32_t) * (size_t)L.n_blocks);
     L.rec_sums = o; o = align_up(o + sizeof(uint32_t) * (size_t)L.n_blocks);
     L.sorted_sums = o; o = align_up(o + sizeof(uint32_t) * (size_t)L.n_blocks);
+    L.seg_off = o; o = align_up(o + sizeof(uint32_t) * (size_t)L.n_blocks * kSegsPerChunk);
     L.ctl = o; o = align_up(o + sizeof(SortCtl));
     L.lookback = o; o = align_up(o + sizeof(uint32_t) * (size_t)L.lookback_words);
     L.keys_alt = o; o = align_up(o + sizeof(unsigned long long) * cap);
@@ -727,7 +779,8 @@ extern "C" int gsfit_bin_sort(const gsfit_proj* proj, const gsfit_camera* cams, 
         GSFIT_LAUNCH_CHECK();
         lb += (size_t)L.max_rec_parts * kRadix;
     }
-    reduce_sorted_kernel<<<L.n_blocks, kScanThreads, 0, stream>>>(rk[0], ctl, sorted_sums);
+    uint32_t* seg_off = reinterpret_cast<uint32_t*>(base + L.seg_off);
+    reduce_sorted_kernel<<<L.n_blocks, kScanThreads, 0, stream>>>(rk[0], ctl, sorted_sums, seg_off);
     GSFIT_LAUNCH_CHECK();
     scan_blocks_kernel<<<1, 1024, 0, stream>>>(sorted_sums, L.n_blocks);
     GSFIT_LAUNCH_CHECK();
@@ -737,9 +790,14 @@ extern "C" int gsfit_bin_sort(const gsfit_proj* proj, const gsfit_camera* cams, 
     uint32_t* v_cur = emit_to_alt ? vals_alt : vals;
     unsigned long long* k_nxt = emit_to_alt ? keys_out : keys_alt;
     uint32_t* v_nxt = emit_to_alt ? vals : vals_alt;
-    emit_kernel<<<L.n_blocks, kScanThreads, sizeof(gsfit_camera) * n_views, stream>>>(
-        rk[0], rv[0], reinterpret_cast<const float4*>(proj->xyd), n, n_views, cams, sorted_sums, ctl, L.tile_passes,
-        k_cur, v_cur);
+    int dev = 0, sms = 0;
+    GSFIT_CUDA_CHECK(cudaGetDevice(&dev));
+    GSFIT_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const long long segs = (long long)L.n_blocks * kSegsPerChunk;
+    emit_kernel<<<(unsigned)std::min<long long>((long long)kEmitBlocksPerSm * sms, (segs + 7) / 8), kScanThreads,
+                  sizeof(gsfit_camera) * n_views, stream>>>(rk[0], rv[0], reinterpret_cast<const float4*>(proj->xyd),
+                                                            n, n_views, cams, sorted_sums, seg_off, ctl,
+                                                            L.tile_passes, k_cur, v_cur);
     GSFIT_LAUNCH_CHECK();
     for (int q = 0; q < L.tile_passes; ++q) {
         onesweep_kernel<<<(unsigned)L.max_parts, kSortThreads, smem, stream>>>(
@@ -749,9 +807,6 @@ extern "C" int gsfit_bin_sort(const gsfit_proj* proj, const gsfit_camera* cams, 
         std::swap(k_cur, k_nxt);
         std::swap(v_cur, v_nxt);
     }
-    int dev = 0, sms = 0;
-    GSFIT_CUDA_CHECK(cudaGetDevice(&dev));
-    GSFIT_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     ranges_kernel<<<(unsigned)std::min<long long>((long long)kRangeBlocksPerSm * sms,
                                                  (capacity + 256 * kRangeItems - 1) / (256 * kRangeItems)),
                     256, 0, stream>>>(keys_out, ctl, ranges, (uint32_t)total_tiles);

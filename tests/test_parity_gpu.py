@@ -180,6 +180,65 @@ def test_keys_sort_ranges_bit_exact(name):
                                       (ref["ranges"][:, 1] - ref["ranges"][:, 0])[good])
 
 
+def _plane_facing_camera():
+    """Splats on the plane z = 0 seen along -z from (0, 0, 3): the view matrix
+    is exactly axis-aligned, so every depth is exactly 3.0f and every depth
+    digit is the same for all records (ties resolved by record index)."""
+    gs = scenes.random_gaussians(10000, 1, 21)
+    gs["means"][:, 2] = 0.0
+    return gs, scenes.stack_cameras([scenes.make_camera((0, 0, 3), (0, 0, 0), 150, 113, fx=120.0)])
+
+
+def _far_camera():
+    """The uniform cube seen from distance 6: depths within (4, 8), one
+    binary exponent, so the top depth digit is the same for all records."""
+    gs = scenes.random_gaussians(6000, 2, 22, log_scale_mean=-2.8)
+    return gs, scenes.stack_cameras([scenes.make_camera((0.4, -0.3, 6.0), (0, 0, 0), 210, 160, fx=300.0),
+                                     scenes.make_camera((-6.0, 0.5, 0.2), (0, 0, 0), 96, 80, fx=140.0)])
+
+
+# scene, number of depth digits (of four) that are the same for every binned record
+CONSTANT_DIGIT_CASES = {"equal_depths": (_plane_facing_camera, 4), "one_binade": (_far_camera, 1)}
+
+
+def _constant_depth_digits(proj):
+    vis = proj[:, :, F["tiles"]] > 0
+    bits = proj[:, :, F["depth32"]][vis].astype(np.float32).view(np.uint32)
+    return sum(len(np.unique((bits >> np.uint32(8 * p)) & np.uint32(0xff))) == 1 for p in range(4)), int(vis.sum())
+
+
+@pytest.mark.parametrize("name", list(CONSTANT_DIGIT_CASES))
+def test_sort_with_constant_digits_bit_exact(name):
+    """A counting pass whose digit is the same for every key is the identity
+    permutation (the kernel copies instead of ranking); keys, values and
+    ranges must still be the oracle's (tile, depth, record) order, over
+    several 4096-key partitions."""
+    make, n_const = CONSTANT_DIGIT_CASES[name]
+    gs, cams = make()
+    bg = scenes.backgrounds(len(cams["width"]), 78)
+    ref = oracle.render(gs, cams, bg)
+    proj = ref["proj"]
+    const, n_binned = _constant_depth_digits(proj)
+    assert const == n_const and n_binned > 2 * 4096  # the case's precondition
+    st = _fit_state(gs, cams, bg)
+    st.forward()
+    torch.cuda.synchronize()
+    assert st.check_status() == 0
+    n_inst = int(st.n_instances.item())
+    keys = st.keys[:n_inst].cpu().numpy().view(np.uint64)
+    vals = st.vals[:n_inst].cpu().numpy().view(np.uint32)
+    ranges = st.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2)
+    flips = _radius_flips(st, proj)
+    gk, gv, bad_g = _pairs_excluding(keys, vals, proj, cams, st.n, flips)
+    ok_, ov, bad_o = _pairs_excluding(ref["keys"], ref["vals"], proj, cams, st.n, flips)
+    assert len(ok_) > 4096
+    np.testing.assert_array_equal(gk, ok_)
+    np.testing.assert_array_equal(gv, ov)
+    if not (bad_g | bad_o):
+        assert n_inst == len(ref["keys"])
+        np.testing.assert_array_equal(ranges, ref["ranges"])
+
+
 def _pixel_tile_mask(cams, bad_tiles):
     """Per-pixel mask of pixels lying in the given global tiles."""
     out = []
