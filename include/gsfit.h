@@ -567,6 +567,21 @@ int gsfit_reproject(const float* rgb, const float* depth, int32_t width, int32_t
 int gsfit_selftest_wait_timeout(int64_t limit_cycles, int32_t* status, cudaStream_t stream);
 int gsfit_selftest_lookback_timeout(uint32_t* word, int32_t polls, int32_t* status, cudaStream_t stream);
 
+/*
+ * Diagnostic of the compositing kernels' shared exponent (Section 4.2, the
+ * 3DGS splat power -1/2 d^T Sigma'^-1 d). The forward pass evaluates it with
+ * scalar operations on records as stored; the adjoint with packed two-lane
+ * operations on records rearranged in shared memory. Both must round
+ * identically, or the adjoint would not replay the forward's skip and stop
+ * decisions. For each i < n: conic[4i..4i+3] = (a', b', c', opacity) and
+ * pix[4i..4i+3] = (px, py, u, v); out[2i] is the forward's power and
+ * out[2i+1] the adjoint's. All pointers are device float arrays owned by
+ * the caller; n >= 0.
+ * Errors: GSFIT_ERR_INVALID_ARG (null pointers with n > 0, n < 0),
+ *   GSFIT_ERR_CUDA.
+ */
+int gsfit_selftest_splat_power(const float* conic, const float* pix, int32_t n, float* out, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -80,11 +80,24 @@ __device__ __forceinline__ Rect tile_rect(float u, float w, float radius, int ti
     return t;
 }
 
-// Exponent of a splat at pixel offset (dx, dy) = pixel - centre:
-// power = -1/2 (a' dx^2 + c' dy^2) - b' dx dy. The forward pass and the
-// adjoint both call this, so they take identical skip decisions.
+// Exponent of a splat at pixel offset (dx, dy) = pixel - centre, from the
+// conic as (a', b', b', c') and the offsets as pairs dxx = (dx, dx),
+// dyy = (dy, dy): lin = (a' dx + b' dy, b' dx + c' dy) by packed two-lane
+// operations (also the adjoint's d(-power)/d(dx, dy)), then
+// power = -1/2 (dx lin.x + dy lin.y) = -1/2 (a' dx^2 + c' dy^2) - b' dx dy.
+// Every rounding is explicit, and the forward pass and the adjoint both call
+// this, so they take identical skip decisions.
+__device__ __forceinline__ float splat_power(float4 cq, float2 dxx, float2 dyy, float2& lin) {
+    lin = __ffma2_rn(make_float2(cq.x, cq.y), dxx, __fmul2_rn(make_float2(cq.z, cq.w), dyy));
+    return -0.5f * __fmaf_rn(dxx.x, lin.x, __fmul_rn(dyy.x, lin.y));
+}
+
+// The same exponent from the conic as stored, (a', b', c', opacity), and the
+// offsets as scalars: the same operations in the same order (a packed lane
+// rounds like its scalar form, and fx - u = fx + (-u)), hence bit-identical.
 __device__ __forceinline__ float splat_power(float4 co, float dx, float dy) {
-    return -0.5f * (co.x * dx * dx + co.z * dy * dy) - co.y * dx * dy;
+    const float lx = __fmaf_rn(co.x, dx, __fmul_rn(co.y, dy)), ly = __fmaf_rn(co.y, dx, __fmul_rn(co.z, dy));
+    return -0.5f * __fmaf_rn(dx, lx, __fmul_rn(dy, ly));
 }
 
 __device__ __forceinline__ float warp_sum(float v) {

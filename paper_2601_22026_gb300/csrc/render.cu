@@ -96,14 +96,14 @@ __device__ __forceinline__ float4 cull_params(float4 co) {
 // Entries without a record (past the list end, or an index only a failed
 // sort produces) carry t < 0 and are rejected before their (stale) record is
 // looked at.
-__device__ __forceinline__ bool box_reach(float ux, float uy, float4 co, float4 cp, float4 b) {
+__device__ __forceinline__ bool box_reach(float ux, float uy, float ca, float cb, float cc, float4 cp, float4 b) {
     if (!(cp.x > 0.0f)) return false;
     const float X0 = b.x - ux, X1 = b.z - ux, Y0 = b.y - uy, Y1 = b.w - uy;
     const float xe = fminf(fmaxf(0.0f, X0), X1), ye = fminf(fmaxf(0.0f, Y0), Y1);
     const float y1 = fminf(fmaxf(cp.y * xe, Y0), Y1);
     const float x2 = fminf(fmaxf(cp.z * ye, X0), X1);
-    const float s1 = co.x * xe * xe + co.z * y1 * y1, s2 = co.x * x2 * x2 + co.z * ye * ye;
-    const float q1 = s1 + 2.0f * co.y * xe * y1, q2 = s2 + 2.0f * co.y * x2 * ye;
+    const float s1 = ca * xe * xe + cc * y1 * y1, s2 = ca * x2 * x2 + cc * ye * ye;
+    const float q1 = s1 + 2.0f * cb * xe * y1, q2 = s2 + 2.0f * cb * x2 * ye;
     return fminf(q1 - 1e-5f * s1, q2 - 1e-5f * s2) <= cp.x;
 }
 
@@ -159,6 +159,10 @@ constexpr long long kWaitCycles = 1ll << 31;
 
 template <int SLOT>
 struct Ring {
+    // records as stored (u, v, depth, radius | a', b', c', opacity | r, g, b,
+    // clamp mask), or, staged PAIRED for the adjoint, rearranged so that each
+    // operand pair of its packed two-lane arithmetic is one aligned half of a
+    // float4: (-u, -u, -v, -v | a', b', b', c' | r, g, b, opacity)
     float4 xyd[kRing][SLOT];
     float4 co[kRing][SLOT];
     float4 col[kRing][SLOT];
@@ -248,7 +252,7 @@ __device__ __forceinline__ bool timed_out(const int32_t* status) {
 
 // Producer side: fills slot k % kRing with list positions [b0, b0 + cnt)
 // (cnt = 0 publishes the end of the list). Returns false on a timeout.
-template <int SLOT>
+template <bool PAIRED, int SLOT>
 __device__ __forceinline__ bool ring_produce(Ring<SLOT>& R, int k, uint32_t b0, int cnt, const uint32_t* __restrict__ vals,
                                              const float4* __restrict__ xyd, const float4* __restrict__ conic,
                                              const float4* __restrict__ rgb, size_t rec0, int n,
@@ -274,7 +278,18 @@ __device__ __forceinline__ bool ring_produce(Ring<SLOT>& R, int k, uint32_t b0, 
 #pragma unroll
     for (int q = 0; q < SLOT / 32; ++q) {
         const int e = 32 * q + lane;
-        R.cp[s][e] = g[q] != 0xffffffffu ? cull_params(R.co[s][e]) : make_float4(-1.f, 0.f, 0.f, 0.f);
+        if (g[q] != 0xffffffffu) {
+            const float4 co = R.co[s][e];
+            R.cp[s][e] = cull_params(co);
+            if constexpr (PAIRED) {  // this lane's own copies, complete: rearrange in place
+                const float4 p = R.xyd[s][e];
+                R.xyd[s][e] = make_float4(-p.x, -p.x, -p.y, -p.y);
+                R.co[s][e] = make_float4(co.x, co.y, co.y, co.z);
+                R.col[s][e].w = co.w;
+            }
+        } else {
+            R.cp[s][e] = make_float4(-1.f, 0.f, 0.f, 0.f);
+        }
         R.g[s][e] = g[q];
     }
     if (lane == 0) R.cnt[s] = cnt;
@@ -292,7 +307,7 @@ __device__ __forceinline__ float4 active_rect(uint32_t m, const TileCtx& c) {
 
 // This warp's entries of slot s that can blend at a pixel of rectangle b
 // (the bounding rectangle of its pixels still in play), in list order.
-template <int SLOT>
+template <bool PAIRED, int SLOT>
 __device__ __forceinline__ int ring_compact(const Ring<SLOT>& R, int s, int cnt, uint32_t base, uint32_t wmax,
                                             float4 b, uint8_t* list) {
     const int lane = threadIdx.x & 31;
@@ -302,8 +317,13 @@ __device__ __forceinline__ int ring_compact(const Ring<SLOT>& R, int s, int cnt,
 #pragma unroll
     for (int q = 0; q < SLOT / 32; ++q) {
         const int j = 32 * q + lane;
-        const bool hit = j < cnt && base + (uint32_t)j < wmax &&
-                         box_reach(R.xyd[s][j].x, R.xyd[s][j].y, R.co[s][j], R.cp[s][j], b);
+        bool hit = j < cnt && base + (uint32_t)j < wmax;
+        if constexpr (PAIRED)
+            hit = hit && box_reach(-R.xyd[s][j].x, -R.xyd[s][j].z, R.co[s][j].x, R.co[s][j].y, R.co[s][j].w,
+                                   R.cp[s][j], b);
+        else
+            hit = hit && box_reach(R.xyd[s][j].x, R.xyd[s][j].y, R.co[s][j].x, R.co[s][j].y, R.co[s][j].z,
+                                   R.cp[s][j], b);
         const uint32_t m = __ballot_sync(0xffffffffu, hit);
         if (hit) list[nw + __popc(m & lt)] = (uint8_t)j;
         nw += __popc(m);
@@ -360,13 +380,14 @@ __global__ void __launch_bounds__(TileShape<TILE>::kThreads) render_fwd_kernel(
             const uint32_t b0 = range.x + (uint32_t)k * SLOT;
             const bool stop = skip || b0 >= range.y || *reinterpret_cast<volatile int*>(&s_done) == kWarps;
             const int cnt = stop ? 0 : (int)min((uint32_t)SLOT, range.y - b0);
-            if (!ring_produce(R, k, b0, cnt, vals, xyd, conic, rgb, rec0, n, status) || stop) break;
+            if (!ring_produce<false>(R, k, b0, cnt, vals, xyd, conic, rgb, rec0, n, status) || stop) break;
         }
         return;
     }
 
     const TileCtx c = tile_ctx<TILE>(cams, n_views, t);
     const float fx = (float)c.px, fy = (float)c.py;
+
     float T = 1.0f, C2 = 0.f;
     float2 C01 = make_float2(0.f, 0.f);  // red and green, accumulated by one packed FMA
     uint32_t last = 0;
@@ -383,12 +404,12 @@ __global__ void __launch_bounds__(TileShape<TILE>::kThreads) render_fwd_kernel(
             const uint32_t base = (uint32_t)k * SLOT;
             // cull against the pixels that have not stopped (a nonzero set: the warp is not done)
             const float4 b = active_rect(__ballot_sync(0xffffffffu, !done), c);
-            const int nw = ring_compact(R, s, cnt, base, 0xffffffffu, b, s_list[w]);
+            const int nw = ring_compact<false>(R, s, cnt, base, 0xffffffffu, b, s_list[w]);
             // branch-free: a lane that is done, or skips an entry (power > 0,
             // alpha < 1/255), or stops at it (T would drop below 1e-4) adds a
             // zero weight and keeps its T
-            auto blend_entry = [&](int j, const float4& co, const float4& col, float power, float G) {
-                const float alpha = fminf(kAlphaClamp, co.w * G);
+            auto blend_entry = [&](int j, float opacity, const float4& col, float power, float G) {
+                const float alpha = fminf(kAlphaClamp, opacity * G);
                 const bool hit = !done && power <= 0.0f && alpha >= kAlphaSkip;
                 const float test_T = T * (1.0f - alpha);
                 const bool stop = hit && test_T < kTStop;
@@ -409,20 +430,25 @@ __global__ void __launch_bounds__(TileShape<TILE>::kThreads) render_fwd_kernel(
                     const int j0 = s_list[w][i], j1 = s_list[w][min(i + 1, nw - 1)];
                     const float4 p0 = R.xyd[s][j0], co0 = R.co[s][j0], col0 = R.col[s][j0];
                     const float4 p1 = R.xyd[s][j1], co1 = R.co[s][j1], col1 = R.col[s][j1];
-                    const float pw0 = splat_power(co0, fx - p0.x, fy - p0.y);
-                    const float pw1 = splat_power(co1, fx - p1.x, fy - p1.y);
+                    const float pw0 = splat_power(co0, __fsub_rn(fx, p0.x), __fsub_rn(fy, p0.y));
+                    const float pw1 = splat_power(co1, __fsub_rn(fx, p1.x), __fsub_rn(fy, p1.y));
                     const float2 G = exp_half2(pw0, pw1);
-                    blend_entry(j0, co0, col0, pw0, G.x);
-                    if (i + 1 < nw) blend_entry(j1, co1, col1, pw1, G.y);
+                    blend_entry(j0, co0.w, col0, pw0, G.x);
+                    if (i + 1 < nw) blend_entry(j1, co1.w, col1, pw1, G.y);
                     if (__all_sync(0xffffffffu, done)) break;
                 }
             } else {
-                for (int i = 0; i < nw; ++i) {
-                    const int j = s_list[w][i];
+                // two entries per warp vote: an entry after the one that ends every
+                // pixel changes nothing (a done pixel blends no further)
+                auto one = [&](int j) {
                     const float4 p = R.xyd[s][j];
                     const float4 co = R.co[s][j];
-                    const float power = splat_power(co, fx - p.x, fy - p.y);
-                    blend_entry(j, co, R.col[s][j], power, __expf(power));
+                    const float power = splat_power(co, __fsub_rn(fx, p.x), __fsub_rn(fy, p.y));
+                    blend_entry(j, co.w, R.col[s][j], power, __expf(power));
+                };
+                for (int i = 0; i < nw; i += 2) {
+                    one(s_list[w][i]);
+                    if (i + 1 < nw) one(s_list[w][i + 1]);
                     if (__all_sync(0xffffffffu, done)) break;
                 }
             }
@@ -512,15 +538,16 @@ struct PixBwd {
 // the forward's own tests on the same values) takes alpha = 0, which leaves
 // T and the behind-colour sum unchanged and makes all nine terms zero.
 template <bool E16>
-__device__ __forceinline__ bool pix_bwd_step(PixBwd& q, uint32_t pos, float4 co, const float4* colp, float dx,
-                                             float dy, float* g9) {
-    const float power = splat_power(co, dx, dy);
+__device__ __forceinline__ bool pix_bwd_step(PixBwd& q, uint32_t pos, float4 cq, const float4* colp, float2 dxx,
+                                             float2 dyy, float* g9) {
+    float2 lin;  // (a' dx + b' dy, b' dx + c' dy)
+    const float power = splat_power(cq, dxx, dyy, lin);
     const float G = E16 ? exp_half2(power, power).x : __expf(power);
-    const float a = co.w * G;
+    const float4 col = *colp;
+    const float a = col.w * G;
     const float alpha_f = fminf(kAlphaClamp, a);
     const bool hit = pos < q.last && power <= 0.0f && alpha_f >= kAlphaSkip;
     const float alpha = hit ? alpha_f : 0.0f;
-    const float4 col = *colp;
     // 1 - alpha lies in [0.01, 1]: the hardware reciprocal (within 2 ulp)
     // suffices for recovering T
     const float inv = __fdividef(1.0f, 1.0f - alpha);
@@ -543,17 +570,14 @@ __device__ __forceinline__ bool pix_bwd_step(PixBwd& q, uint32_t pos, float4 co,
     const float dalpha = hit && a <= kAlphaClamp ? dalpha_f : 0.0f;
     const float dpow = dalpha * alpha;
     g9[2] = dalpha * G;
-    // d(power)/d(u, v) = (a' dx + b' dy, c' dy + b' dx)
-    const float2 lin = __ffma2_rn(make_float2(co.x, co.z), make_float2(dx, dy),
-                                  __fmul2_rn(make_float2(co.y, co.y), make_float2(dy, dx)));
+    // d(power)/d(u, v) = lin, from the exponent's own evaluation
     const float2 duv = __fmul2_rn(lin, make_float2(dpow, dpow));
     g9[0] = duv.x;
     g9[1] = duv.y;
-    const float hd = -0.5f * dpow;
-    const float2 dac = __fmul2_rn(make_float2(hd, hd), __fmul2_rn(make_float2(dx, dy), make_float2(dx, dy)));
-    g9[3] = dac.x;
+    const float dx = dxx.x, dy = dyy.x, hd = -0.5f * dpow;
+    g9[3] = hd * dx * dx;
     g9[4] = -dpow * dx * dy;
-    g9[5] = dac.y;
+    g9[5] = hd * dy * dy;
     return hit;
 }
 
@@ -622,13 +646,14 @@ __global__ void __launch_bounds__(TileShape<TILE>::kThreads, 5) render_bwd_kerne
             const uint32_t b1 = stop ? 0u : len - done_n;
             const uint32_t b0 = b1 > (uint32_t)SLOT ? b1 - SLOT : 0u;
             const int cnt = stop ? 0 : (int)(b1 - b0);
-            if (!ring_produce(R, k, range.x + b0, cnt, vals, xyd, conic, rgb, rec0, n, status) || stop) break;
+            if (!ring_produce<true>(R, k, range.x + b0, cnt, vals, xyd, conic, rgb, rec0, n, status) || stop) break;
         }
         return;
     }
 
     const size_t rec0 = (size_t)c.view * n;
     const float fx = (float)c.px, fy = (float)c.py;
+    const float2 fxx = make_float2(fx, fx), fyy = make_float2(fy, fy);
     const int slot = reduce9_slot(lane);
     const int slot_off = slot + slot / 3;  // floats (du dv do _ | da db dc _ | dr dg db _ | ....) of a record
     for (int k = 0;; ++k) {
@@ -642,12 +667,14 @@ __global__ void __launch_bounds__(TileShape<TILE>::kThreads, 5) render_bwd_kerne
         // pixels whose contributors reach into this slot; the others need none of its entries
         const uint32_t am = __ballot_sync(0xffffffffu, q.last > base);
         if (am != 0u) {
-            const int nw = ring_compact(R, s, cnt, base, wmax, active_rect(am, c), s_list[w]);
+            const int nw = ring_compact<true>(R, s, cnt, base, wmax, active_rect(am, c), s_list[w]);
             for (int i = nw - 1; i >= 0; --i) {
                 const int j = s_list[w][i];
                 const float4 p = R.xyd[s][j];
                 float g9[9];
-                const bool hit = pix_bwd_step<E16>(q, base + (uint32_t)j, R.co[s][j], &R.col[s][j], fx - p.x, fy - p.y, g9);
+                const bool hit = pix_bwd_step<E16>(q, base + (uint32_t)j, R.co[s][j], &R.col[s][j],
+                                                   __fadd2_rn(fxx, make_float2(p.x, p.y)),
+                                                   __fadd2_rn(fyy, make_float2(p.z, p.w)), g9);
                 if (__any_sync(0xffffffffu, hit)) {
                     const float tot = reduce9(g9, lane);
                     if (slot >= 0) atomicAdd(grad2d + 16 * (rec0 + R.g[s][j]) + slot_off, tot);
@@ -656,6 +683,20 @@ __global__ void __launch_bounds__(TileShape<TILE>::kThreads, 5) render_bwd_kerne
         }
         mbar_arrive(&R.empty[s]);
     }
+}
+
+// Diagnostic: the exponent as the forward evaluates it (scalar, stored
+// layout) and as the adjoint does (packed, rearranged layout).
+__global__ void splat_power_selftest_kernel(const float4* __restrict__ conic, const float4* __restrict__ pix, int n,
+                                            float2* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 co = conic[i], p = pix[i];
+    const float fwd = splat_power(co, __fsub_rn(p.x, p.z), __fsub_rn(p.y, p.w));
+    float2 lin;
+    const float bwd = splat_power(make_float4(co.x, co.y, co.y, co.z), __fadd2_rn(make_float2(p.x, p.x), make_float2(-p.z, -p.z)),
+                                  __fadd2_rn(make_float2(p.y, p.y), make_float2(-p.w, -p.w)), lin);
+    out[i] = make_float2(fwd, bwd);
 }
 
 // Diagnostic: blended pairs, with the forward's skip rules, up to each
@@ -684,7 +725,7 @@ __global__ void __launch_bounds__(TILE * TILE) render_count_kernel(
         const int cnt = (int)min((uint32_t)kBatch, range.y - b0);
         for (int j = 0; j < cnt; ++j) {
             if (S.g[j] == 0xffffffffu || b0 - range.x + (uint32_t)j >= last) continue;
-            const float power = splat_power(S.co[j], (float)c.px - S.xy[j].x, (float)c.py - S.xy[j].y);
+            const float power = splat_power(S.co[j], __fsub_rn((float)c.px, S.xy[j].x), __fsub_rn((float)c.py, S.xy[j].y));
             if (power > 0.0f) continue;
             if (fminf(kAlphaClamp, S.co[j].w * __expf(power)) >= kAlphaSkip) ++mine;
         }
@@ -1027,6 +1068,16 @@ extern "C" int gsfit_render_autotune(const gsfit_proj* proj, const gsfit_camera*
 extern "C" int gsfit_selftest_wait_timeout(int64_t limit_cycles, int32_t* status, cudaStream_t stream) {
     if (!status || limit_cycles < 1) return GSFIT_ERR_INVALID_ARG;
     wait_selftest_kernel<<<1, 64, 0, stream>>>((long long)limit_cycles, status);
+    GSFIT_LAUNCH_CHECK();
+    return GSFIT_OK;
+}
+
+extern "C" int gsfit_selftest_splat_power(const float* conic, const float* pix, int32_t n, float* out,
+                                          cudaStream_t stream) {
+    if (n < 0 || (n > 0 && (!conic || !pix || !out))) return GSFIT_ERR_INVALID_ARG;
+    if (n == 0) return GSFIT_OK;
+    splat_power_selftest_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(
+        reinterpret_cast<const float4*>(conic), reinterpret_cast<const float4*>(pix), n, reinterpret_cast<float2*>(out));
     GSFIT_LAUNCH_CHECK();
     return GSFIT_OK;
 }

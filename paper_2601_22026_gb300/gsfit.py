@@ -90,6 +90,7 @@ SIGNATURES = {
                                        _P, _P, _P]),
     "gsfit_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_int64, _P, _P]),
     "gsfit_selftest_lookback_timeout": (ctypes.c_int, [_P, _i32, _P, _P]),
+    "gsfit_selftest_splat_power": (ctypes.c_int, [_P, _P, _i32, _P, _P]),
     "gsfit_reproject": (ctypes.c_int, [_P, _P, _i32, _i32, _P, _P, _P, _i32, _i32, _P, _P, _P, _P, _P]),
 }
 
@@ -458,3 +459,8 @@ def gsfit_selftest_wait_timeout(limit_cycles, status, stream=None):
 def gsfit_selftest_lookback_timeout(word, polls, status, stream=None):
     _check(load().gsfit_selftest_lookback_timeout(_ptr(word), int(polls), _ptr(status), _stream(stream)),
            "gsfit_selftest_lookback_timeout")
+
+
+def gsfit_selftest_splat_power(conic, pix, n, out, stream=None):
+    _check(load().gsfit_selftest_splat_power(_ptr(conic), _ptr(pix), int(n), _ptr(out), _stream(stream)),
+           "gsfit_selftest_splat_power")
