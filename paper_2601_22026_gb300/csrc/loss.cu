@@ -28,22 +28,28 @@ constexpr float kC2 = 0.03f * 0.03f;
 
 // 65 KB: three CTAs per SM. The input region is reused for the SSIM partials
 // and the horizontal-pass buffer for the horizontal pass of the partials.
+// Maps that the packed two-lane FMAs take together are interleaved as float2,
+// so one 8-byte shared-memory access moves an operand pair.
 struct LossSmem {
     union {
+        float2 xy[kR2][kR2];           // (render, target over the background), input region; zero outside the image
         struct {
-            float x[kR2][kR2];       // render, input region (zero outside the image)
-            float y[kR2][kR2];       // target composited over the background
-        } in;
-        float part[3][kR1][kR1];     // dSSIM/d(mu_x, E[x^2], E[xy]) on the 42 x 42 region
+            float2 p01[kR1][kR1];      // dSSIM/d(mu_x, E[x^2 + y^2]) on the 42 x 42 region
+            float p2[kR1][kR1];        // dSSIM/dE[xy]
+        } part;
     } a;
     union {
-        float h[4][kR2][kR1];        // horizontal pass of x, y, x^2 + y^2, xy
         struct {
-            float hp[3][kR1][kOut];  // horizontal pass of the partials
-            float at[kR2][kR2];      // next item's target alpha (prefetched during the last pass)
+            float2 h01[kR2][kR1];      // horizontal pass of (x, y)
+            float2 h23[kR2][kR1];      // horizontal pass of (x^2 + y^2, xy)
+        } h;
+        struct {
+            float2 hp01[kR1][kOut];    // horizontal pass of the first two partials
+            float hp2[kR1][kOut];      // and of the third
+            float at[kR2][kR2];        // next item's target alpha (prefetched during the last pass)
         } st;
     } b;
-    float xo[kOut][kOut];            // render and target at the output pixels
+    float xo[kOut][kOut];              // render and target at the output pixels
     float yo[kOut][kOut];
 };
 
@@ -69,14 +75,14 @@ __device__ __forceinline__ void strip11(const float* src, float out[N]) {
     }
 }
 
-// The same for two maps at once (a and b, same layout): each tap is one packed
-// two-lane FMA (fma.rn.f32x2, each lane rounded as a scalar FMA), so the
-// results equal two strip11 calls.
+// The same for two interleaved maps at once (STRIDE in float2): each tap is
+// one packed two-lane FMA (fma.rn.f32x2, each lane rounded as a scalar FMA),
+// so the results equal two strip11 calls.
 template <int N, int STRIDE>
-__device__ __forceinline__ void strip11x2(const float* a, const float* b, float2 out[N]) {
+__device__ __forceinline__ void strip11x2(const float2* src, float2 out[N]) {
     float2 in[N + 10];
 #pragma unroll
-    for (int k = 0; k < N + 10; ++k) in[k] = make_float2(a[k * STRIDE], b[k * STRIDE]);
+    for (int k = 0; k < N + 10; ++k) in[k] = src[k * STRIDE];
 #pragma unroll
     for (int o = 0; o < N; ++o) {
         float2 acc = make_float2(0.f, 0.f);
@@ -127,8 +133,8 @@ __device__ __forceinline__ void prefetch_item(LossSmem& S, const gsfit_camera* _
             const int gx = ox - 10 + c;
             const bool ok = interior || (gx >= 0 && gx < W && gy >= 0 && gy < H);
             const long long q = ok ? (long long)gy * W + gx : 0;
-            cp_async4(&S.a.in.x[r][c], X + q, ok);
-            cp_async4(&S.a.in.y[r][c], Yt + q, ok);
+            cp_async4(&S.a.xy[r][c].x, X + q, ok);
+            cp_async4(&S.a.xy[r][c].y, Yt + q, ok);
             cp_async4(&S.b.st.at[r][c], At + q, ok);
         }
     }
@@ -178,16 +184,16 @@ __global__ void __launch_bounds__(kLossThreads, 3) loss_kernel(
         asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         __syncthreads();
         if (ox >= 10 && oy >= 10 && ox + kOut + 10 <= W && oy + kOut + 10 <= H) {  // the region lies inside
-            float* yf = &S.a.in.y[0][0];
+            float2* xyf = &S.a.xy[0][0];
             const float* af = &S.b.st.at[0][0];
-            for (int k = tid; k < kR2 * kR2; k += kLossThreads) yf[k] += (1.0f - af[k]) * bgc;
+            for (int k = tid; k < kR2 * kR2; k += kLossThreads) xyf[k].y += (1.0f - af[k]) * bgc;
         } else {
             for (int r = wid; r < kR2; r += kLossThreads / 32) {
                 const int gy = oy - 10 + r;
                 for (int c = lane; c < kR2; c += 32) {
                     const int gx = ox - 10 + c;
                     const bool ok = gx >= 0 && gx < W && gy >= 0 && gy < H;
-                    S.a.in.y[r][c] = ok ? S.a.in.y[r][c] + (1.0f - S.b.st.at[r][c]) * bgc : 0.0f;
+                    S.a.xy[r][c].y = ok ? S.a.xy[r][c].y + (1.0f - S.b.st.at[r][c]) * bgc : 0.0f;
                 }
             }
         }
@@ -202,7 +208,7 @@ __global__ void __launch_bounds__(kLossThreads, 3) loss_kernel(
             float2 xy2[kHS + 10], qp[kHS + 10];
 #pragma unroll
             for (int j = 0; j < kHS + 10; ++j) {
-                xy2[j] = make_float2(S.a.in.x[r][c0 + j], S.a.in.y[r][c0 + j]);
+                xy2[j] = S.a.xy[r][c0 + j];
                 qp[j] = make_float2(xy2[j].x * xy2[j].x + xy2[j].y * xy2[j].y, xy2[j].x * xy2[j].y);
             }
 #pragma unroll
@@ -214,13 +220,14 @@ __global__ void __launch_bounds__(kLossThreads, 3) loss_kernel(
                     ab = __ffma2_rn(wj, xy2[o + j], ab);
                     ce = __ffma2_rn(wj, qp[o + j], ce);
                 }
-                S.b.h[0][r][c0 + o] = ab.x; S.b.h[1][r][c0 + o] = ab.y; S.b.h[2][r][c0 + o] = ce.x;
-                S.b.h[3][r][c0 + o] = ce.y;
+                S.b.h.h01[r][c0 + o] = ab;
+                S.b.h.h23[r][c0 + o] = ce;
             }
         }
         for (int r = wid; r < kOut; r += kLossThreads / 32) {
-            S.xo[r][lane] = S.a.in.x[r + 10][lane + 10];
-            S.yo[r][lane] = S.a.in.y[r + 10][lane + 10];
+            const float2 v = S.a.xy[r + 10][lane + 10];
+            S.xo[r][lane] = v.x;
+            S.yo[r][lane] = v.y;
         }
         __syncthreads();
         // 3. vertical pass (strips of 7 rows: 252 strips, one round) straight
@@ -231,8 +238,8 @@ __global__ void __launch_bounds__(kLossThreads, 3) loss_kernel(
         for (int k = tid; k < kR1 * kVN; k += kLossThreads) {
             const int cidx = k % kR1, r0 = (k / kR1) * kVS;
             float2 m01[kVS], m23[kVS];  // (mu_x, mu_y), (E[x^2 + y^2], E[xy])
-            strip11x2<kVS, kR1>(&S.b.h[0][r0][cidx], &S.b.h[1][r0][cidx], m01);
-            strip11x2<kVS, kR1>(&S.b.h[2][r0][cidx], &S.b.h[3][r0][cidx], m23);
+            strip11x2<kVS, kR1>(&S.b.h.h01[r0][cidx], m01);
+            strip11x2<kVS, kR1>(&S.b.h.h23[r0][cidx], m23);
             const int gx = ox - 5 + cidx;
 #pragma unroll
             for (int o = 0; o < kVS; ++o) {
@@ -254,9 +261,8 @@ __global__ void __launch_bounds__(kLossThreads, 3) loss_kernel(
                     dxy = 2.f * A1 * iB;
                     if (r >= 5 && r < 5 + kOut && cidx >= 5 && cidx < 5 + kOut) ssim_sum += ss;
                 }
-                S.a.part[0][r][cidx] = dmu;
-                S.a.part[1][r][cidx] = dxx;
-                S.a.part[2][r][cidx] = dxy;
+                S.a.part.p01[r][cidx] = make_float2(dmu, dxx);
+                S.a.part.p2[r][cidx] = dxy;
             }
         }
         __syncthreads();
@@ -267,17 +273,14 @@ __global__ void __launch_bounds__(kLossThreads, 3) loss_kernel(
             const int r = rem >> 2, c0 = (rem & 3) * 8;
             if (k < kR1 * 4) {
                 float2 out[8];
-                strip11x2<8, 1>(&S.a.part[0][r][c0], &S.a.part[1][r][c0], out);
+                strip11x2<8, 1>(&S.a.part.p01[r][c0], out);
 #pragma unroll
-                for (int o = 0; o < 8; ++o) {
-                    S.b.st.hp[0][r][c0 + o] = out[o].x;
-                    S.b.st.hp[1][r][c0 + o] = out[o].y;
-                }
+                for (int o = 0; o < 8; ++o) S.b.st.hp01[r][c0 + o] = out[o];
             } else {
                 float out[8];
-                strip11<8, 1>(&S.a.part[2][r][c0], out);
+                strip11<8, 1>(&S.a.part.p2[r][c0], out);
 #pragma unroll
-                for (int o = 0; o < 8; ++o) S.b.st.hp[2][r][c0 + o] = out[o];
+                for (int o = 0; o < 8; ++o) S.b.st.hp2[r][c0 + o] = out[o];
             }
         }
         __syncthreads();
@@ -290,8 +293,8 @@ __global__ void __launch_bounds__(kLossThreads, 3) loss_kernel(
             const int cidx = tid % kOut, r0 = (tid / kOut) * 4;  // 32 columns x 8 strips = 256
             float2 cmx[4];  // (dSSIM/dmu_x, dSSIM/dE[x^2]) convolved back
             float cxy[4];
-            strip11x2<4, kOut>(&S.b.st.hp[0][r0][cidx], &S.b.st.hp[1][r0][cidx], cmx);
-            strip11<4, kOut>(&S.b.st.hp[2][r0][cidx], cxy);
+            strip11x2<4, kOut>(&S.b.st.hp01[r0][cidx], cmx);
+            strip11<4, kOut>(&S.b.st.hp2[r0][cidx], cxy);
 #pragma unroll
             for (int o = 0; o < 4; ++o) {
                 const int r = r0 + o;
