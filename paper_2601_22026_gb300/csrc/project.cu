@@ -239,6 +239,7 @@ __global__ void __launch_bounds__(256, 3) project_kernel(const float4* __restric
     load_sh<DEG, FT>(P, F, n, i, sh);
     const float opacity = 1.0f / (1.0f + expf(-g.logit));
 
+#pragma unroll 2
     for (int v = 0; v < n_views; ++v) {
         const gsfit_camera& cam = cams[v];
         const size_t r = (size_t)v * n + i;
