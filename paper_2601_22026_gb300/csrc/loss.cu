@@ -9,8 +9,9 @@
 // passes (SSIM uses the two variances only through their sum, so one moment
 // of x^2 + y^2 serves both), evaluates the SSIM map and
 // its partials there, and convolves the partials back onto the tile: the
-// gradient of the windowed SSIM never leaves shared memory, so the kernel
-// reads each input pixel once and writes each gradient once. Channel-0 items
+// gradient of the windowed SSIM never leaves shared memory: the kernel reads
+// each input region once from DRAM (the output pixels' own values a second
+// time, from L2, for the gradient) and writes each gradient once. Channel-0 items
 // also handle the alpha term. Persistent CTAs stride over the items.
 #include "common.cuh"
 
@@ -22,11 +23,12 @@ constexpr int kOut = 32;             // output tile edge
 constexpr int kR1 = kOut + 10;       // moments / partials region (halo 5): 42
 constexpr int kR2 = kOut + 20;       // input region (halo 10): 52
 constexpr int kLossThreads = 256;
+constexpr int kLossCtasPerSm = 4;    // 64 registers, 56.6 KB of shared memory each
 static_assert(kR1 % 3 == 0 && kR1 % 7 == 0, "strip lengths of the stencil passes divide the region");
 constexpr float kC1 = 0.01f * 0.01f;
 constexpr float kC2 = 0.03f * 0.03f;
 
-// 65 KB: three CTAs per SM. The input region is reused for the SSIM partials
+// 56.6 KB: four CTAs per SM. The input region is reused for the SSIM partials
 // and the horizontal-pass buffer for the horizontal pass of the partials.
 // Maps that the packed two-lane FMAs take together are interleaved as float2,
 // so one 8-byte shared-memory access moves an operand pair.
@@ -49,8 +51,6 @@ struct LossSmem {
             float at[kR2][kR2];        // next item's target alpha (prefetched during the last pass)
         } st;
     } b;
-    float xo[kOut][kOut];              // render and target at the output pixels
-    float yo[kOut][kOut];
 };
 
 // The SSIM window: 11-tap Gaussian, sigma = 1.5, normalised
@@ -141,7 +141,7 @@ __device__ __forceinline__ void prefetch_item(LossSmem& S, const gsfit_camera* _
     asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
 
-__global__ void __launch_bounds__(kLossThreads, 3) loss_kernel(
+__global__ void __launch_bounds__(kLossThreads, kLossCtasPerSm) loss_kernel(
     const gsfit_camera* __restrict__ cams_g, int n_views, const float* __restrict__ rgb,
     const float* __restrict__ alpha, const float* __restrict__ t_rgb, const float* __restrict__ t_alpha,
     const float* __restrict__ bg, float lambda, float* __restrict__ g_rgb, float* __restrict__ g_alpha,
@@ -224,11 +224,6 @@ __global__ void __launch_bounds__(kLossThreads, 3) loss_kernel(
                 S.b.h.h23[r][c0 + o] = ce;
             }
         }
-        for (int r = wid; r < kOut; r += kLossThreads / 32) {
-            const float2 v = S.a.xy[r + 10][lane + 10];
-            S.xo[r][lane] = v.x;
-            S.yo[r][lane] = v.y;
-        }
         __syncthreads();
         // 3. vertical pass (strips of 7 rows: 252 strips, one round) straight
         //    into SSIM and its partials w.r.t. (mu_x, E[x^2], E[xy]) on the
@@ -300,7 +295,11 @@ __global__ void __launch_bounds__(kLossThreads, 3) loss_kernel(
                 const int r = r0 + o;
                 const int gy = oy + r, gx = ox + cidx;
                 if (gy >= H || gx >= W) continue;
-                const float xv = S.xo[r][cidx], yv = S.yo[r][cidx];
+                // the output pixel's render and composited target, again from global memory
+                // (the same operations as step 1, so bit-identical; the item's region is in L2)
+                const long long q0 = (long long)gy * W + gx;
+                const float xv = __ldg(rgb + 3ll * cam.pixel_offset + ch * P + q0);
+                const float yv = __ldg(t_rgb + 3ll * cam.pixel_offset + ch * P + q0) + (1.0f - __ldg(At + q0)) * bgc;
                 const float dssim = cmx[o].x + 2.f * xv * cmx[o].y + yv * cxy[o];
                 const float diff = xv - yv;
                 const float sg = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
@@ -377,7 +376,7 @@ extern "C" int gsfit_loss(const gsfit_camera* cams, int32_t n_views, const float
     GSFIT_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     float* acc = static_cast<float*>(ws);
     GSFIT_CUDA_CHECK(cudaMemsetAsync(acc, 0, sizeof(float) * 3 * n_views, stream));
-    loss_kernel<<<3 * sms, kLossThreads, smem, stream>>>(cams, n_views, rgb, alpha, target_rgb, target_alpha, bg,
+    loss_kernel<<<kLossCtasPerSm * sms, kLossThreads, smem, stream>>>(cams, n_views, rgb, alpha, target_rgb, target_alpha, bg,
                                                          lambda, dL_drgb, dL_dalpha, acc);
     GSFIT_LAUNCH_CHECK();
     if (loss_out) {
@@ -439,7 +438,7 @@ extern "C" int gsfit_loss_noalloc(const gsfit_camera* cams, int32_t n_views, con
     GSFIT_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     // the array keeps the previous call's sums: clear this call's part first
     GSFIT_CUDA_CHECK(cudaMemsetAsync(acc, 0, sizeof(float) * 3 * n_views, stream));
-    loss_kernel<<<3 * sms, kLossThreads, smem, stream>>>(cams, n_views, rgb, alpha, target_rgb, target_alpha, bg,
+    loss_kernel<<<kLossCtasPerSm * sms, kLossThreads, smem, stream>>>(cams, n_views, rgb, alpha, target_rgb, target_alpha, bg,
                                                          lambda, dL_drgb, dL_dalpha, acc);
     GSFIT_LAUNCH_CHECK();
     if (loss_out) {
