@@ -23,9 +23,11 @@
 //      its CTAs copy their partitions instead. Records are now in (depth,
 //      record index) order.
 //   4. reduce_sorted_kernel / scan_blocks_kernel / emit_kernel: pair offsets
-//      in that order, then the pairs (tile id << 32 | depth, Gaussian index),
-//      with the tile-digit histograms; each warp deals its records' pairs out
-//      to its lanes 32 at a time, so stores coalesce whatever the splat sizes.
+//      in that order (per block of records, and per 128-record segment within
+//      it), then the pairs (tile id << 32 | depth, Gaussian index), with the
+//      tile-digit histograms; a resident grid of warps takes the segments in
+//      turn and deals each row's pairs out to its lanes 32 at a time, so
+//      stores coalesce whatever the splat sizes.
 //   5. onesweep_kernel over the significant tile-id bits only (two passes for
 //      up to 65536 tiles): being stable, it leaves equal tile ids in (depth,
 //      record index) order, the unique order by (key, view, index).
@@ -34,7 +36,8 @@
 // Sorting records instead of pairs by depth moves 24 bytes per record per
 // depth pass instead of 24 bytes per pair (a record covers several tiles).
 // Counts never leave the device, so the sequence can be captured in a CUDA
-// graph; launches are sized by capacity and idle CTAs exit at once.
+// graph; launches are sized by capacity (or, for the emission, by the SM
+// count) and idle CTAs exit at once.
 #include <algorithm>
 
 #include "common.cuh"
