@@ -92,6 +92,21 @@ __device__ __forceinline__ void strip11x2(const float2* src, float2 out[N]) {
     }
 }
 
+// The same for two maps at separate addresses (two rows of one map).
+template <int N, int STRIDE>
+__device__ __forceinline__ void strip11x2(const float* a, const float* b, float2 out[N]) {
+    float2 in[N + 10];
+#pragma unroll
+    for (int k = 0; k < N + 10; ++k) in[k] = make_float2(a[k * STRIDE], b[k * STRIDE]);
+#pragma unroll
+    for (int o = 0; o < N; ++o) {
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < 11; ++j) acc = __ffma2_rn(make_float2(kWin[j], kWin[j]), in[o + j], acc);
+        out[o] = acc;
+    }
+}
+
 // The view owning work item `item` and the index of that view's first item.
 __device__ __forceinline__ void locate_item(const gsfit_camera* __restrict__ cams, int item, int& v, int& first) {
     v = 0;
@@ -262,20 +277,24 @@ __global__ void __launch_bounds__(kLossThreads, kLossCtasPerSm) loss_kernel(
         }
         __syncthreads();
         // 4. horizontal pass of the partials: 42 rows x 32 columns in strips of 8,
-        //    the first two partials packed (168 strips), the third alone (168)
-        for (int k = tid; k < 2 * kR1 * 4; k += kLossThreads) {
-            const int rem = k < kR1 * 4 ? k : k - kR1 * 4;
-            const int r = rem >> 2, c0 = (rem & 3) * 8;
-            if (k < kR1 * 4) {
-                float2 out[8];
-                strip11x2<8, 1>(&S.a.part.p01[r][c0], out);
+        //    the first two partials packed (168 strips), the third two rows at a
+        //    time (84 strips): 252 strips, one round of the block
+        static_assert(kR1 % 2 == 0 && kR1 * 4 + (kR1 / 2) * 4 <= kLossThreads, "one strip per thread");
+        if (tid < kR1 * 4) {
+            const int r = tid >> 2, c0 = (tid & 3) * 8;
+            float2 out[8];
+            strip11x2<8, 1>(&S.a.part.p01[r][c0], out);
 #pragma unroll
-                for (int o = 0; o < 8; ++o) S.b.st.hp01[r][c0 + o] = out[o];
-            } else {
-                float out[8];
-                strip11<8, 1>(&S.a.part.p2[r][c0], out);
+            for (int o = 0; o < 8; ++o) S.b.st.hp01[r][c0 + o] = out[o];
+        } else if (tid < kR1 * 4 + (kR1 / 2) * 4) {
+            const int rem = tid - kR1 * 4;
+            const int r = (rem >> 2) * 2, c0 = (rem & 3) * 8;
+            float2 out[8];
+            strip11x2<8, 1>(&S.a.part.p2[r][c0], &S.a.part.p2[r + 1][c0], out);
 #pragma unroll
-                for (int o = 0; o < 8; ++o) S.b.st.hp2[r][c0 + o] = out[o];
+            for (int o = 0; o < 8; ++o) {
+                S.b.st.hp2[r][c0 + o] = out[o].x;
+                S.b.st.hp2[r + 1][c0 + o] = out[o].y;
             }
         }
         __syncthreads();
