@@ -147,3 +147,11 @@ def test_render_options_rejected_on_host(lib):
     assert lib.gsfit_render_autotune(ctypes.byref(p), fake, 1, 10, 4, fake, fake, None, fake, fake, fake, fake, fake,
                                      fake, fake, fake, 12, 3, ctypes.byref(best), None, None,
                                      None) == G.GSFIT_ERR_INVALID_ARG
+
+
+def test_splat_power_selftest_arguments_rejected_on_host(lib):
+    fake = 256
+    assert lib.gsfit_selftest_splat_power(None, None, 1, None, None) == G.GSFIT_ERR_INVALID_ARG
+    assert lib.gsfit_selftest_splat_power(fake, None, 1, fake, None) == G.GSFIT_ERR_INVALID_ARG
+    assert lib.gsfit_selftest_splat_power(fake, fake, -1, fake, None) == G.GSFIT_ERR_INVALID_ARG
+    assert lib.gsfit_selftest_splat_power(None, None, 0, None, None) == G.GSFIT_OK  # empty: nothing launched
