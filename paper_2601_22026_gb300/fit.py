@@ -350,13 +350,14 @@ class HostFeed:
     on every step, without stalling the GPU.
 
     prefetch(k) starts copying step k's inputs into one of two staging
-    buffers on a copy stream; step() moves the staged inputs into the state
-    with a device-to-device copy (tens of microseconds instead of the
-    host-to-device transfer), replays the captured iteration and starts the
+    buffers on a copy stream; step() replays an iteration captured against
+    that staging buffer (one CUDA graph per buffer, so the inputs are read
+    where the copy put them, with no device-to-device copy) and starts the
     device-to-host copy of its loss; loss(handle) waits for that copy only.
     So the transfer of step k + 1 overlaps step k, and reading step k's loss
     while step k + 1 runs keeps the GPU busy. Staging buffer k % 2 is reused
-    by prefetch(k + 2) only after step k has consumed it."""
+    by prefetch(k + 2) only after step k has finished with it. The state's
+    own target and background buffers are not used by these steps."""
 
     def __init__(self, state: FitState):
         self.st = state
@@ -370,6 +371,20 @@ class HostFeed:
         self.issued = 0  # prefetches issued
         self.stepped = 0  # steps issued
         self.h2d_bytes = state.target_rgb.numel() * 4 + state.target_alpha.numel() * 4 + state.bg.numel() * 4
+        self.graphs = [self._capture(b) for b in range(2)]
+
+    def _capture(self, b: int):
+        """One iteration captured with staging buffer b as its inputs."""
+        st = self.st
+        saved = (st.target_rgb, st.target_alpha, st.bg)
+        st.target_rgb, st.target_alpha, st.bg = self.stage[b]
+        try:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                st.step()
+        finally:
+            st.target_rgb, st.target_alpha, st.bg = saved
+        return g
 
     def prefetch(self, host_rgb, host_alpha, host_bg) -> None:
         """Copies the next step's inputs (pinned host tensors) to the device."""
@@ -392,12 +407,8 @@ class HostFeed:
         st = self.st
         cur = torch.cuda.current_stream()
         cur.wait_event(self.staged[b])
-        rgb, alpha, bg = self.stage[b]
-        st.target_rgb.copy_(rgb)
-        st.target_alpha.copy_(alpha)
-        st.bg.copy_(bg)
+        self.graphs[b].replay()
         self.consumed[b].record(cur)
-        st.replay()
         self.loss_host[b].copy_(st.loss_out, non_blocking=True)
         self.loss_done[b].record(cur)
         self.stepped += 1
