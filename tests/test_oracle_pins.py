@@ -404,6 +404,203 @@ def test_adjoint_matches_central_differences_smooth_mode():
     assert checked > 300
 
 
+def _clamp_and_stop_scene(seed=123):
+    """One 48 x 40 view (tile 8) with: a wide, nearly opaque Gaussian in
+    front (o = 0.9999) whose o G exceeds the 0.99 clamp at about ten pixels
+    around its centre; six wide layers (o ~ 0.86 - 0.92) behind it at well
+    separated depths, under which about ninety pixels stop early (the next
+    blend would take T below 1e-4); ten small Gaussians spread across the
+    view at depths in between. SH degree 1."""
+    cams = scenes.stack_cameras([scenes.make_camera((0, 0, 3), (0, 0, 0), 48, 40, fx=60.0)])
+    g = scenes.rng(seed)
+    means = [(0.2, 0.08, 0.8)]
+    ls = [(math.log(0.5), math.log(0.42), math.log(0.46))]
+    logit = [9.2]
+    for k in range(6):
+        means.append((g.uniform(-0.08, 0.08), g.uniform(-0.08, 0.08), 0.5 - 0.15 * k))
+        ls.append(tuple(np.log(g.uniform(0.28, 0.4, 3))))
+        logit.append(g.uniform(1.8, 2.4))
+    n_small = 10
+    means += [tuple(x) for x in np.c_[g.uniform(-0.55, 0.55, (n_small, 2)), np.linspace(0.65, -0.6, n_small) + 0.01]]
+    ls += [tuple(x) for x in g.normal(-2.6, 0.25, (n_small, 3))]
+    logit += list(g.normal(-0.5, 0.8, n_small))
+    n, K = len(means), 4
+    q = g.normal(size=(n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    sh = np.zeros((n, K, 3))
+    sh[:, 0, :] = (g.uniform(0.25, 0.75, (n, 3)) - 0.5) / scenes.SH_C0
+    sh[:, 1:, :] = g.normal(0, 0.05, (n, K - 1, 3))
+    gs = {"means": np.array(means, np.float64), "log_scales": np.array(ls, np.float64), "quats": q,
+          "opacity_logits": np.array(logit, np.float64), "sh": sh}
+    return gs, cams
+
+
+def _splat_alpha_unclamped(proj_i, W, H):
+    """o G at every pixel centre of a W x H view, from a projected record
+    (the normal-mode float32 centre)."""
+    yy, xx = np.mgrid[0:H, 0:W]
+    dx, dy = xx - proj_i[F["u32"]], yy - proj_i[F["v32"]]
+    pw = -0.5 * (proj_i[F["conic_a"]] * dx * dx + proj_i[F["conic_c"]] * dy * dy) - proj_i[F["conic_b"]] * dx * dy
+    return (proj_i[F["opacity"]] * np.exp(pw)).reshape(-1)
+
+
+def _stopped_pixels(r, W, H, tile):
+    """Pixels whose front-to-back walk ended at the T stop (a later Gaussian
+    would blend but take T below 1e-4), walked here from the oracle's own
+    lists and records."""
+    proj = r["proj"][0]
+    tx_n = -(-W // tile)
+    out = np.zeros(W * H, bool)
+    for py in range(H):
+        for px in range(W):
+            t = (py // tile) * tx_n + px // tile
+            s, e = r["ranges"][t]
+            T = 1.0
+            for gi in r["vals"][s:e]:
+                p = proj[gi]
+                dx, dy = px - p[F["u32"]], py - p[F["v32"]]
+                pw = -0.5 * (p[F["conic_a"]] * dx * dx + p[F["conic_c"]] * dy * dy) - p[F["conic_b"]] * dx * dy
+                if pw > 0:
+                    continue
+                a = min(0.99, p[F["opacity"]] * math.exp(pw))
+                if a < 1 / 255:
+                    continue
+                if T * (1 - a) < 1e-4:
+                    out[py * W + px] = True
+                    break
+                T *= 1 - a
+    return out
+
+
+def test_adjoint_matches_central_differences_normal_mode():
+    """The analytic adjoint of the normal-mode render (1/255 skip, 0.99 clamp,
+    T stop, tile lists) against central differences, h = 1e-4 in FP64, on a
+    scene where the clamp is active at pixels of a Gaussian and pixels stop
+    early. A parameter is compared wherever no decision of the render moves
+    between theta - h and theta + h (same tile lists, contributor counts and
+    blend counts; Gaussians with a near-threshold decision excluded): there
+    the render is smooth, and the clamped alpha has zero derivative in o and
+    in the exponent. Passing the gradient through the clamp (as 3DGS does)
+    misses this check by a factor of about 50 in every geometric group."""
+    gs, cams = _clamp_and_stop_scene()
+    W, H, tile = 48, 40, 8
+    bg = np.array([[0.2, 0.6, 0.4]])
+    P = W * H
+    g = scenes.rng(7)
+    w_rgb, w_a = g.normal(size=3 * P), g.normal(size=P)
+
+    def evaluate():
+        r = oracle.render(gs, cams, bg, tile=tile)
+        sig = (r["vals"].tobytes(), r["ranges"].tobytes(), r["n_contrib"].tobytes(), r["n_blended"].tobytes())
+        return float(w_rgb @ r["rgb"] + w_a @ r["alpha"]), sig, r
+
+    _, sig0, r0 = evaluate()
+    # the scene exercises both branches
+    clamped = _splat_alpha_unclamped(r0["proj"][0, 0], W, H) > 0.99
+    assert clamped.sum() >= 5
+    assert _stopped_pixels(r0, W, H, tile).sum() >= 50
+    b = oracle.render_bwd(gs, cams, bg, w_rgb, w_a, tile=tile, fwd=r0)
+    amb = b["gauss_ambiguous"].any(axis=0) | (r0["proj"][:, :, F["near_boundary"]] > 0).any(axis=0)
+    assert not amb[0]
+    h = 1e-4
+    # The normal mode composites at the float32 splat centre, a staircase in
+    # the mean with steps of about 2e-6 px against the 2.4e-3 px that h moves
+    # the centre: the means' differences carry about 1e-3 relative noise.
+    tol = {"means": 1e-3, "log_scales": 1e-6, "quats": 1e-6, "opacity_logits": 1e-6, "sh": 1e-6}
+    total = checked = 0
+    clamped_checked = 0
+    for name in ["means", "log_scales", "quats", "opacity_logits", "sh"]:
+        arr = gs[name]
+        n = arr.shape[0]
+        rows = arr.reshape(n, -1)
+        fd, an = [], []
+        for i in range(n):
+            if amb[i]:
+                continue
+            for j in range(rows.shape[1]):
+                total += 1
+                old = rows[i, j]
+                rows[i, j] = old + h
+                fp, sp, _ = evaluate()
+                rows[i, j] = old - h
+                fm, sm, _ = evaluate()
+                rows[i, j] = old
+                if sp != sig0 or sm != sig0:
+                    continue
+                fd.append((fp - fm) / (2 * h))
+                an.append(b["grads"][name].reshape(n, -1)[i, j])
+                checked += 1
+                clamped_checked += i == 0
+        fd, an = np.array(fd), np.array(an)
+        err = np.linalg.norm(an - fd) / np.linalg.norm(fd)
+        assert err < tol[name], (name, err)
+    assert checked >= 0.9 * total, (checked, total)
+    assert clamped_checked >= 20  # most of the clamped Gaussian's 23 parameters
+
+
+def _three_uneven_views():
+    return scenes.stack_cameras([
+        scenes.make_camera((0.2, 0.3, 3), (0, 0, 0), 53, 41, fx=45.0),
+        scenes.make_camera((-2.0, 1.0, 2.0), (0, 0, 0), 37, 66, fx=40.0),
+        scenes.make_camera((1.5, -1.5, 2.0), (0.05, 0, 0), 70, 29, fx=60.0)])
+
+
+def test_sampled_entry_points_equal_full_render():
+    """render_tiles (tiles composited on demand, one view at a time) and
+    gaussian_grads (complete gradients of chosen Gaussians) give what the
+    whole-batch render and adjoint give for the same tiles and Gaussians:
+    three uneven views, tiles of the second and third view by their
+    view-local ids (ragged edge tiles included), Gaussians seen in one, two
+    or three views."""
+    gs = scenes.random_gaussians(400, 2, 21, log_scale_mean=-2.6, extent=2.0)
+    cams = _three_uneven_views()
+    V, tile, B2 = 3, 16, 256
+    bg = scenes.backgrounds(V, 22)
+    full = oracle.render(gs, cams, bg, tile=tile)
+    off = oracle.pixel_offsets(cams)
+    Ws, Hs = [int(x) for x in cams["width"]], [int(x) for x in cams["height"]]
+    txn = [-(-w // tile) for w in Ws]
+    tyn = [-(-h // tile) for h in Hs]
+    toff = np.concatenate([[0], np.cumsum([a * b for a, b in zip(txn, tyn)])])
+    items = [(1, 0), (1, txn[1] * tyn[1] - 1), (1, txn[1] + 1), (2, 3), (2, txn[2] * tyn[2] - 1), (2, txn[2]),
+             (0, 5)]
+    got = oracle.render_tiles(gs, cams, bg, items, tile=tile)
+    for k, (v, t) in enumerate(items):
+        tx, ty = t % txn[v], t // txn[v]
+        s, e = full["ranges"][toff[v] + t]
+        np.testing.assert_array_equal(got["lists"][k], full["vals"][s:e])
+        assert got["list_len"][k] == e - s
+        plane = Ws[v] * Hs[v]
+        for q in range(B2):
+            px, py = tx * tile + q % tile, ty * tile + q // tile
+            if px >= Ws[v] or py >= Hs[v]:
+                assert got["n_contrib"][k, q] == -1
+                continue
+            pix = off[v] + py * Ws[v] + px
+            for ch in range(3):
+                ref = full["rgb"][3 * off[v] + ch * plane + py * Ws[v] + px]
+                assert abs(got["rgb"][k, ch, q] - ref) <= 1e-12
+            assert abs(got["alpha"][k, q] - full["alpha"][pix]) <= 1e-12
+            assert abs(got["T_final"][k, q] - full["T_final"][pix]) <= 1e-12
+            assert got["n_contrib"][k, q] == full["n_contrib"][pix]
+            assert got["ambiguous"][k, q] == full["ambiguous"][pix]
+    # gradients of chosen Gaussians
+    P = int(off[-1])
+    w_rgb = scenes.cotangents(3 * P, 23, 1.0).astype(np.float64)
+    w_a = scenes.cotangents(P, 24, 1.0).astype(np.float64)
+    b = oracle.render_bwd(gs, cams, bg, w_rgb, w_a, tile=tile, fwd=full)
+    seen = (full["proj"][:, :, F["tiles"]] > 0).sum(axis=0)
+    req = np.concatenate([np.flatnonzero(seen == c)[:4] for c in (0, 1, 2, 3)])
+    assert {int(c) for c in seen[req]} == {0, 1, 2, 3}
+    rows, amb = oracle.gaussian_grads(gs, cams, bg, w_rgb, w_a, req, tile=tile)
+    ref = b["grads_flat"][req]
+    scale = np.abs(b["grads_flat"]).max(axis=0)
+    assert np.all(np.abs(rows - ref) <= 1e-12 * (np.abs(ref) + 1e-3 * scale))
+    assert np.all(rows[seen[req] == 0] == 0)
+    ref_amb = b["gauss_ambiguous"].any(axis=0) | (full["proj"][:, :, F["near_boundary"]] > 0).any(axis=0)
+    np.testing.assert_array_equal(amb, ref_amb[req])
+
+
 def test_adjoint_sums_over_views():
     gs, cams = _fd_scene(seed=8)
     bg = np.array([[0.1, 0.5, 0.9], [0.7, 0.2, 0.4]])
