@@ -545,8 +545,8 @@ int gsfit_first_hit(const int16_t* hu, int32_t nx, int32_t ny, int32_t nz, const
  *   device 4*W*H floats or null; zbuf: device workspace of out_w*out_h
  *   uint64 (contents need not be initialised); out_rgb: 3 planes of
  *   out_w*out_h floats; covered: out_w*out_h bytes (device).
- * Errors: GSFIT_ERR_INVALID_ARG (null pointers, non-positive sizes),
- *   GSFIT_ERR_CUDA.
+ * Errors: GSFIT_ERR_INVALID_ARG (null pointers, non-positive sizes, clip
+ *   not 16-byte aligned, zbuf not 8-byte aligned), GSFIT_ERR_CUDA.
  */
 int gsfit_reproject(const float* rgb, const float* depth, int32_t width, int32_t height, const float* inv_pv_old,
                     const float* pos_old, const float* pv_new, int32_t out_w, int32_t out_h, float* clip,

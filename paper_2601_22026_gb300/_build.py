@@ -60,7 +60,11 @@ def build(force: bool = False, verbose: bool = False) -> Path:
     with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
         objs = list(ex.map(compile_one, sources()))
     tmp = LIB.with_suffix(f".{os.getpid()}.tmp")
-    cmd = [nvcc(), "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", str(tmp), *map(str, objs)]
+    cuda = Path(nvcc()).parent.parent
+    # the CUDA runtime as a shared library: one runtime instance with the host
+    # process (PyTorch's, when it is loaded first: same soname)
+    cmd = [nvcc(), "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-cudart", "shared",
+           f"-Xlinker=-rpath={cuda / 'lib64'}", "-o", str(tmp), *map(str, objs)]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

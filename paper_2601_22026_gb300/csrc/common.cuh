@@ -1,9 +1,12 @@
 // Internal helpers shared by the gsfit kernels (sm_103a).
 #pragma once
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <mutex>
 
 #include "gsfit.h"
 
@@ -16,6 +19,80 @@
 #define GSFIT_LAUNCH_CHECK() GSFIT_CUDA_CHECK(cudaGetLastError())
 
 namespace gsfit {
+
+// Host-side set-up that must run once per device and CUDA context (a kernel
+// attribute, a device symbol's address): a context reset (cudaDeviceReset, a
+// released and recreated primary context) reloads the library's module, and
+// the set-up has to run again. Identifies the context by its process-unique
+// id (cuCtxGetId), not its handle, which a new context may reuse. Thread-safe.
+struct ContextOnce {
+    std::mutex m;
+    unsigned long long ctx_id[64] = {};  // 0: not yet run on this device
+};
+
+// Two driver-API calls, resolved through the runtime's entry-point query so
+// that the library needs no link against the driver (it loads on machines
+// without one; the calls only run where a device exists).
+struct DriverCtxApi {
+    CUresult (*get_current)(CUcontext*) = nullptr;
+    CUresult (*get_id)(CUcontext, unsigned long long*) = nullptr;
+    bool ok = false;
+};
+inline const DriverCtxApi& driver_ctx_api() {
+    static DriverCtxApi api;
+    static std::once_flag flag;
+    std::call_once(flag, [] {
+        void *a = nullptr, *b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) == cudaSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) == cudaSuccess &&
+            qa == cudaDriverEntryPointSuccess && qb == cudaDriverEntryPointSuccess && a && b) {
+            api.get_current = reinterpret_cast<CUresult (*)(CUcontext*)>(a);
+            api.get_id = reinterpret_cast<CUresult (*)(CUcontext, unsigned long long*)>(b);
+            api.ok = true;
+        }
+    });
+    return api;
+}
+
+// The id of the calling thread's current context on device `dev` (created
+// and made current by cudaSetDevice if there is none yet).
+inline int current_context_id(int dev, unsigned long long* id) {
+    const DriverCtxApi& api = driver_ctx_api();
+    if (!api.ok) return GSFIT_ERR_CUDA;
+    CUcontext ctx = nullptr;
+    if (api.get_current(&ctx) != CUDA_SUCCESS) return GSFIT_ERR_CUDA;
+    if (!ctx) {
+        if (cudaSetDevice(dev) != cudaSuccess || api.get_current(&ctx) != CUDA_SUCCESS || !ctx) return GSFIT_ERR_CUDA;
+    }
+    return api.get_id(ctx, id) == CUDA_SUCCESS && *id != 0 ? GSFIT_OK : GSFIT_ERR_CUDA;
+}
+
+// Runs fn() (returning a GSFIT status) unless it already succeeded on the
+// current device in the current context.
+template <typename Fn>
+int run_once_per_context(ContextOnce& once, Fn fn) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return GSFIT_ERR_CUDA;
+    unsigned long long id = 0;
+    const int rc = current_context_id(dev, &id);
+    if (rc != GSFIT_OK) return rc;
+    std::lock_guard<std::mutex> lock(once.m);
+    if (once.ctx_id[dev] == id) return GSFIT_OK;
+    const int r = fn();
+    if (r == GSFIT_OK) once.ctx_id[dev] = id;
+    return r;
+}
+
+// Opts `kernel` in to `bytes` of dynamic shared memory, once per device and context.
+template <typename K>
+int opt_in_smem(ContextOnce& once, K kernel, size_t bytes) {
+    return run_once_per_context(once, [&] {
+        return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess
+                   ? GSFIT_OK
+                   : GSFIT_ERR_CUDA;
+    });
+}
 
 constexpr int kTile = GSFIT_TILE;
 constexpr int kTilePixels = kTile * kTile;

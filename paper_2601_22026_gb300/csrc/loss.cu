@@ -364,6 +364,11 @@ __global__ void loss_finalize_kernel(const gsfit_camera* __restrict__ cams, int 
     *loss_out = L / (float)n_views;
 }
 
+// The loss kernel's dynamic shared memory opt-in, shared by both entry
+// points: once per device and context.
+ContextOnce g_loss_smem_once;
+int enable_loss_smem() { return opt_in_smem(g_loss_smem_once, loss_kernel, sizeof(LossSmem)); }
+
 }  // namespace
 
 }  // namespace gsfit
@@ -382,16 +387,11 @@ extern "C" int gsfit_loss(const gsfit_camera* cams, int32_t n_views, const float
     if (!cams || n_views < 1 || n_views > GSFIT_MAX_VIEWS || !rgb || !alpha || !target_rgb || !target_alpha ||
         !bg || !dL_drgb || !dL_dalpha || !ws || ws_bytes < gsfit_loss_workspace_size(n_views))
         return GSFIT_ERR_INVALID_ARG;
-    static bool attr_done[64] = {false};
-    int dev = 0;
-    GSFIT_CUDA_CHECK(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return GSFIT_ERR_CUDA;
     const size_t smem = sizeof(LossSmem);
-    if (!attr_done[dev]) {
-        GSFIT_CUDA_CHECK(cudaFuncSetAttribute(loss_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_done[dev] = true;
-    }
-    int sms = 0;
+    const int rc = enable_loss_smem();
+    if (rc != GSFIT_OK) return rc;
+    int dev = 0, sms = 0;
+    GSFIT_CUDA_CHECK(cudaGetDevice(&dev));
     GSFIT_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     float* acc = static_cast<float*>(ws);
     GSFIT_CUDA_CHECK(cudaMemsetAsync(acc, 0, sizeof(float) * 3 * n_views, stream));
@@ -422,18 +422,31 @@ constexpr int kNoAllocMaxViews = GSFIT_MAX_VIEWS;
 // address comes from cudaGetSymbolAddress below.
 static __device__ __align__(256) float g_loss_noalloc_acc[3 * kNoAllocMaxViews];
 
-// Device address of g_loss_noalloc_acc, looked up once per device with that
-// device current.
-int noalloc_acc_address(int dev, float** out) {
-    static float* cached[64] = {nullptr};
+// Device address of g_loss_noalloc_acc in the current device's current
+// context. Looked up (cudaGetSymbolAddress, with that device current) on the
+// first call in each context and cached under the context's id: a context
+// reset reloads the library's module, and the next call looks the address up
+// again instead of writing through a stale one.
+struct NoAllocAddress {
+    ContextOnce once;
+    float* addr[64] = {};
+};
+NoAllocAddress g_noalloc;
+
+int noalloc_acc_address(float** out) {
+    int dev = 0;
+    GSFIT_CUDA_CHECK(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return GSFIT_ERR_CUDA;
-    if (!cached[dev]) {
+    const int rc = run_once_per_context(g_noalloc.once, [&] {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_loss_noalloc_acc) != cudaSuccess || !p) return GSFIT_ERR_CUDA;
-        cached[dev] = static_cast<float*>(p);
-    }
-    *out = cached[dev];
-    return GSFIT_OK;
+        g_noalloc.addr[dev] = static_cast<float*>(p);
+        return GSFIT_OK;
+    });
+    if (rc != GSFIT_OK) return rc;
+    std::lock_guard<std::mutex> lock(g_noalloc.once.m);
+    *out = g_noalloc.addr[dev];
+    return *out ? GSFIT_OK : GSFIT_ERR_CUDA;
 }
 
 }  // namespace
@@ -446,14 +459,14 @@ extern "C" int gsfit_loss_noalloc(const gsfit_camera* cams, int32_t n_views, con
     if (!cams || n_views < 1 || n_views > kNoAllocMaxViews || !rgb || !alpha || !target_rgb || !target_alpha ||
         !bg || !dL_drgb || !dL_dalpha)
         return GSFIT_ERR_INVALID_ARG;
-    int dev = 0;
-    GSFIT_CUDA_CHECK(cudaGetDevice(&dev));
     float* acc = nullptr;
-    const int rc = noalloc_acc_address(dev, &acc);
+    int rc = noalloc_acc_address(&acc);
     if (rc != GSFIT_OK) return rc;
     const size_t smem = sizeof(LossSmem);
-    GSFIT_CUDA_CHECK(cudaFuncSetAttribute(loss_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int sms = 0;
+    rc = enable_loss_smem();
+    if (rc != GSFIT_OK) return rc;
+    int dev = 0, sms = 0;
+    GSFIT_CUDA_CHECK(cudaGetDevice(&dev));
     GSFIT_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     // the array keeps the previous call's sums: clear this call's part first
     GSFIT_CUDA_CHECK(cudaMemsetAsync(acc, 0, sizeof(float) * 3 * n_views, stream));

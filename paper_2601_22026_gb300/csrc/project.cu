@@ -551,16 +551,10 @@ int launch_project_bwd(const gsfit_gaussians* g, const gsfit_proj* proj, const g
     const float4* P = reinterpret_cast<const float4*>(g->params);
     const uint2* F = reinterpret_cast<const uint2*>(g->features);
     const size_t smem = sizeof(gsfit_camera) * V + sizeof(float) * 3 * SH<DEG>::K * threads;
-    static bool attr_done[64] = {false};
-    int dev = 0;
-    GSFIT_CUDA_CHECK(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return GSFIT_ERR_CUDA;
-    if (!attr_done[dev]) {
-        const size_t max_smem = sizeof(gsfit_camera) * GSFIT_MAX_VIEWS + sizeof(float) * 3 * SH<DEG>::K * threads;
-        GSFIT_CUDA_CHECK(cudaFuncSetAttribute(project_bwd_kernel<DEG, FT>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem));
-        attr_done[dev] = true;
-    }
+    static ContextOnce once;
+    const size_t max_smem = sizeof(gsfit_camera) * GSFIT_MAX_VIEWS + sizeof(float) * 3 * SH<DEG>::K * threads;
+    const int rc = opt_in_smem(once, project_bwd_kernel<DEG, FT>, max_smem);
+    if (rc != GSFIT_OK) return rc;
     project_bwd_kernel<DEG, FT><<<blocks, threads, smem, s>>>(
         P, F, g->n, cams, V, reinterpret_cast<const float4*>(proj->xyd), reinterpret_cast<const float4*>(proj->conic),
         reinterpret_cast<const float4*>(proj->rgb), reinterpret_cast<float4*>(grad2d),

@@ -792,23 +792,12 @@ struct BwdArgs {
 };
 
 // The ring and the camera table (up to GSFIT_MAX_VIEWS x 128 bytes) are
-// dynamic shared memory: opt each kernel in to its largest size once per device.
-template <typename K>
-int opt_in(K kernel, size_t bytes, bool* done) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return GSFIT_ERR_CUDA;
-    if (!done[dev]) {
-        if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
-            return GSFIT_ERR_CUDA;
-        done[dev] = true;
-    }
-    return GSFIT_OK;
-}
-
+// dynamic shared memory: each kernel is opted in to its largest size once per
+// device and context.
 template <int TILE, int SLOT, bool IMP, bool E16>
 int launch_fwd_v(const FwdArgs& a, int total_tiles, cudaStream_t s) {
-    static bool done[64] = {false};
-    const int rc = opt_in(render_fwd_kernel<TILE, SLOT, IMP, E16>, render_smem<SLOT>(GSFIT_MAX_VIEWS), done);
+    static ContextOnce once;
+    const int rc = opt_in_smem(once, render_fwd_kernel<TILE, SLOT, IMP, E16>, render_smem<SLOT>(GSFIT_MAX_VIEWS));
     if (rc != GSFIT_OK) return rc;
     render_fwd_kernel<TILE, SLOT, IMP, E16><<<total_tiles, TileShape<TILE>::kThreads, render_smem<SLOT>(a.n_views), s>>>(
         a.xyd, a.conic, a.rgb, a.n, a.cams, a.n_views, a.vals, a.ranges, a.tile_order, a.bg, a.out_rgb, a.out_alpha,
@@ -825,8 +814,8 @@ int launch_fwd(const FwdArgs& a, int total_tiles, cudaStream_t s) {
 
 template <int TILE, int SLOT, bool E16>
 int launch_bwd(const BwdArgs& a, int total_tiles, cudaStream_t s) {
-    static bool done[64] = {false};
-    const int rc = opt_in(render_bwd_kernel<TILE, SLOT, E16>, render_smem<SLOT>(GSFIT_MAX_VIEWS), done);
+    static ContextOnce once;
+    const int rc = opt_in_smem(once, render_bwd_kernel<TILE, SLOT, E16>, render_smem<SLOT>(GSFIT_MAX_VIEWS));
     if (rc != GSFIT_OK) return rc;
     render_bwd_kernel<TILE, SLOT, E16><<<total_tiles, TileShape<TILE>::kThreads, render_smem<SLOT>(a.n_views), s>>>(
         a.xyd, a.conic, a.rgb, a.n, a.cams, a.n_views, a.vals, a.ranges, a.tile_order, a.bg, a.T_final, a.n_contrib,

@@ -102,7 +102,7 @@ extern "C" int gsfit_reproject(const float* rgb, const float* depth, int32_t wid
                                uint8_t* covered, cudaStream_t stream) {
     if (!rgb || !depth || !inv_pv_old || !pos_old || !pv_new || !zbuf || !out_rgb || !covered || width < 1 ||
         height < 1 || out_w < 1 || out_h < 1 || (long long)width * height >= (1ll << 32) ||
-        (clip && (reinterpret_cast<uintptr_t>(clip) % 16) != 0))
+        (clip && (reinterpret_cast<uintptr_t>(clip) % 16) != 0) || (reinterpret_cast<uintptr_t>(zbuf) % 8) != 0)
         return GSFIT_ERR_INVALID_ARG;
     Mat4 a, b;
     for (int i = 0; i < 16; ++i) {

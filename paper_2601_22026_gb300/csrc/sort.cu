@@ -712,17 +712,10 @@ SortLayout layout(long long n_rec, long long capacity, int total_tiles) {
     return L;
 }
 
-// Opt-in to more than 48 KB of dynamic shared memory, once per device.
+// Opt-in to more than 48 KB of dynamic shared memory, once per device and context.
 int enable_onesweep_smem(size_t smem) {
-    static bool done[64] = {false};
-    int dev = 0;
-    GSFIT_CUDA_CHECK(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return GSFIT_ERR_CUDA;
-    if (!done[dev]) {
-        GSFIT_CUDA_CHECK(cudaFuncSetAttribute(onesweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        done[dev] = true;
-    }
-    return GSFIT_OK;
+    static ContextOnce once;
+    return opt_in_smem(once, onesweep_kernel, smem);
 }
 
 }  // namespace

@@ -100,6 +100,18 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.gsfit_loss_workspace_size(0) == 0
 
 
+def test_reproject_alignment_rejected_on_host(lib):
+    """zbuf takes 64-bit atomics and clip 16-byte stores: misaligned pointers
+    are refused before any launch."""
+    fake = 256
+    m = (ctypes.c_float * 16)(*np.eye(4, dtype=np.float32).reshape(-1))
+    pos = (ctypes.c_float * 3)(0, 0, 0)
+    args = lambda clip, zbuf: (fake, fake, 8, 8, m, pos, m, 8, 8, clip, zbuf, fake, fake, None)
+    assert lib.gsfit_reproject(*args(None, fake + 4)) == G.GSFIT_ERR_INVALID_ARG
+    assert lib.gsfit_reproject(*args(fake + 8, fake)) == G.GSFIT_ERR_INVALID_ARG
+    assert lib.gsfit_reproject(*args(None, None)) == G.GSFIT_ERR_INVALID_ARG
+
+
 def test_workspace_size_grows_with_capacity(lib):
     a = lib.gsfit_bin_sort_workspace_size(1000, 10_000, 64)
     b = lib.gsfit_bin_sort_workspace_size(1000, 20_000, 64)
