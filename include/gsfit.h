@@ -60,7 +60,7 @@
 extern "C" {
 #endif
 
-#define GSFIT_ABI_VERSION 3
+#define GSFIT_ABI_VERSION 4
 #define GSFIT_MAX_VIEWS 256
 #define GSFIT_TILE 16
 
@@ -97,30 +97,32 @@ typedef struct gsfit_camera {
 } gsfit_camera;
 
 /* Storage of the Gaussian features the projection reads (see gsfit_gaussians). */
-#define GSFIT_FEATURES_F32 0   /* planes 1.. read from params                   */
-#define GSFIT_FEATURES_F16 1   /* planes 1.. read from an IEEE half copy          */
-#define GSFIT_FEATURES_BF16 2  /* planes 1.. read from a bfloat16 copy            */
+#define GSFIT_FEATURES_F32 0   /* every plane read from params                    */
+#define GSFIT_FEATURES_F16 1   /* SH planes 3.. read from an IEEE half copy         */
+#define GSFIT_FEATURES_BF16 2  /* SH planes 3.. read from a bfloat16 copy           */
 
 /*
  * A Gaussian set (device, float4 planes as described above).
- * Mixed-precision form (the precision pattern of the fitting loop): with
- * feature_dtype GSFIT_FEATURES_F16 or GSFIT_FEATURES_BF16 the projection and
- * its adjoint read planes 1 .. num_planes-1 (rotation, scales, SH
- * coefficients) from `features`, a 16-bit copy laid out as the planes with 4
- * x 16 bits per entry (plane p of Gaussian i at 8-byte index (p - 1) * n +
- * i, (num_planes - 1) * n * 8 bytes). The copy of plane 2 holds the
- * activated scales (exp(log-scale) x3, 0), which 16 bits carry to 2^-12
- * relative; the other planes hold the parameters. Plane 0 (means and
- * opacity logit, one float4) is always read in float32 from params. Everything computed from the
- * features (covariances, colour, transmittance, gradients) stays float32, and
- * the gradients are those of the function of the 16-bit values. The copy is
- * written by gsfit_features_refresh and kept current by gsfit_adam_step.
+ * Mixed-precision form (the precision pattern of the fitting loop, Section
+ * 4.2's fitted 3DGS model with 16-bit colour storage): with feature_dtype
+ * GSFIT_FEATURES_F16 or GSFIT_FEATURES_BF16 the projection and its adjoint
+ * read the SH coefficient planes 3 .. num_planes-1 from `features`, a 16-bit
+ * copy laid out as those planes with 4 x 16 bits per entry (plane p of
+ * Gaussian i at 8-byte index (p - 3) * n + i, (num_planes - 3) * n * 8
+ * bytes). Planes 0-2 (means and opacity logit, rotation, log-scales) are
+ * always read in float32 from params: rounding them would move splat
+ * footprints and with them the compositing's skip / clamp / stop decisions,
+ * while the SH coefficients (48 of the 59 values of a degree-3 Gaussian) only
+ * tint colours. Everything computed from the features (colour, transmittance,
+ * gradients) stays float32, and the gradients are those of the function of
+ * the 16-bit values. The copy is written by gsfit_features_refresh and kept
+ * current by gsfit_adam_step.
  */
 typedef struct gsfit_gaussians {
     const float* params;    /* gsfit_num_planes(sh_degree) * n float4 (float32 master copy) */
     int32_t n;
     int32_t sh_degree;      /* 0 .. 3 */
-    const void* features;   /* 16-bit copy of planes 1.., or null with GSFIT_FEATURES_F32 */
+    const void* features;   /* 16-bit copy of the SH planes 3.., or null with GSFIT_FEATURES_F32 */
     int32_t feature_dtype;  /* GSFIT_FEATURES_* */
     int32_t reserved;
 } gsfit_gaussians;
@@ -434,12 +436,12 @@ int gsfit_render_autotune(const gsfit_proj* proj, const gsfit_camera* cams, int3
  *   with t = *step + 1; *step is incremented on the device afterwards.
  *   Parameters and moments are float32. With feature_dtype
  *   GSFIT_FEATURES_F16 / GSFIT_FEATURES_BF16 the same pass also writes the
- *   updated planes 1.. to `features`, rounded to nearest even (the layout and
- *   contents of gsfit_gaussians.features: exp of the log-scales for plane 2).
+ *   updated SH planes 3.. to `features`, rounded to nearest even (the layout
+ *   of gsfit_gaussians.features).
  * Arguments: params, grads, m, v: n_planes * n float4 (device); lr: HOST
  *   array of 4 * n_planes floats, the rate of each component of each plane
  *   (0 freezes it); step: device int32 count of completed steps; features:
- *   device, (n_planes - 1) * n * 8 bytes, or null with GSFIT_FEATURES_F32.
+ *   device, (n_planes - 3) * n * 8 bytes, or null with GSFIT_FEATURES_F32.
  * Errors: GSFIT_ERR_INVALID_ARG, GSFIT_ERR_CUDA.
  */
 int gsfit_adam_step(float* params, const float* grads, float* m, float* v, int32_t n, int32_t n_planes,
@@ -448,11 +450,11 @@ int gsfit_adam_step(float* params, const float* grads, float* m, float* v, int32
 
 /*
  * gsfit_features_refresh -- writes the 16-bit feature copy of
- * gsfit_gaussians.features from the float32 parameters (planes 1 ..
- * n_planes-1, exp of the log-scales for plane 2, rounded to nearest even):
- * after the parameters were set or changed outside gsfit_adam_step.
+ * gsfit_gaussians.features from the float32 parameters (the SH planes 3 ..
+ * n_planes-1, rounded to nearest even): after the parameters were set or
+ * changed outside gsfit_adam_step.
  * Arguments: params: n_planes * n float4 (device); features: device,
- *   (n_planes - 1) * n * 8 bytes; feature_dtype GSFIT_FEATURES_F16 or
+ *   (n_planes - 3) * n * 8 bytes; feature_dtype GSFIT_FEATURES_F16 or
  *   GSFIT_FEATURES_BF16.
  * Errors: GSFIT_ERR_INVALID_ARG, GSFIT_ERR_CUDA.
  */
@@ -581,6 +583,20 @@ int gsfit_selftest_lookback_timeout(uint32_t* word, int32_t polls, int32_t* stat
  *   GSFIT_ERR_CUDA.
  */
 int gsfit_selftest_splat_power(const float* conic, const float* pix, int32_t n, float* out, cudaStream_t stream);
+
+/*
+ * gsfit_selftest_alu_rate -- diagnostic with no counterpart in the paper: the
+ * arithmetic-rate microbenchmark behind the compositing kernels' roofline.
+ * Launches `blocks` CTAs of 256 threads; each thread runs 8 independent
+ * chains of `iters` operations of one kind: 0 = fma.rn.f32 (2 FLOP), 1 =
+ * fma.rn.f32x2 (two FMAs, 4 FLOP), 2 = ex2.approx.f32 (one MUFU operation).
+ * The caller times the launch (CUDA events on `stream`) and divides
+ * blocks * 256 * 8 * iters operations by the time.
+ * Arguments: sink: device, blocks * 256 floats (written, meaningless).
+ * Errors: GSFIT_ERR_INVALID_ARG (kind not 0-2, blocks or iters < 1, null
+ *   sink), GSFIT_ERR_CUDA.
+ */
+int gsfit_selftest_alu_rate(int32_t kind, int32_t blocks, int32_t iters, float* sink, cudaStream_t stream);
 
 #ifdef __cplusplus
 }

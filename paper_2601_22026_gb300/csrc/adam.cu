@@ -8,8 +8,8 @@
 // m, v (64 bytes) and write p, m, v (48 bytes); grid.y selects the plane and
 // with it the four per-component learning rates. The step count lives on the
 // device so a captured graph can be replayed without host updates. In the
-// mixed-precision form the same pass writes the 16-bit feature copy of planes
-// 1.. (8 more bytes per float4).
+// mixed-precision form the same pass writes the 16-bit copy of the SH planes
+// (8 more bytes per float4 of those planes).
 #include "common.cuh"
 
 namespace gsfit {
@@ -21,15 +21,6 @@ constexpr int kMaxPlanes = 16;
 struct LrTable {
     float4 lr[kMaxPlanes];
 };
-
-// The value the 16-bit copy stores for parameter plane `plane`: the
-// activated scales exp(log-scale) for plane 2 (the projection's s; 16-bit
-// floats then carry the scale to 2^-12 relative instead of the log-scale to
-// 2^-11 of its magnitude), the parameters themselves otherwise.
-__device__ __forceinline__ float4 feature_value(int plane, float4 p) {
-    if (plane == 2) return make_float4(expf(p.x), expf(p.y), expf(p.z), 0.0f);
-    return p;
-}
 
 template <int FT>
 __global__ void __launch_bounds__(256) adam_kernel(float4* __restrict__ p, const float4* __restrict__ g,
@@ -61,7 +52,7 @@ __global__ void __launch_bounds__(256) adam_kernel(float4* __restrict__ p, const
         v[k] = vv;
         p[k] = pp;
         if constexpr (FT != GSFIT_FEATURES_F32) {
-            if (plane > 0) feat[(size_t)(plane - 1) * n + i] = pack_features<FT>(feature_value(plane, pp));
+            if (plane >= kFeaturePlane0) feat[(size_t)(plane - kFeaturePlane0) * n + i] = pack_features<FT>(pp);
         }
     }
 }
@@ -69,9 +60,9 @@ __global__ void __launch_bounds__(256) adam_kernel(float4* __restrict__ p, const
 template <int FT>
 __global__ void __launch_bounds__(256) refresh_kernel(const float4* __restrict__ p, int n, int n_planes,
                                                       uint2* __restrict__ feat) {
-    const size_t total = (size_t)(n_planes - 1) * n;
+    const size_t total = (size_t)(n_planes - kFeaturePlane0) * n;
     for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (size_t)gridDim.x * blockDim.x)
-        feat[k] = pack_features<FT>(feature_value(1 + (int)(k / (size_t)n), p[(size_t)n + k]));
+        feat[k] = pack_features<FT>(p[(size_t)kFeaturePlane0 * n + k]);
 }
 
 __global__ void step_increment_kernel(int32_t* step) { *step += 1; }
@@ -124,14 +115,14 @@ extern "C" int gsfit_adam_step(float* params, const float* grads, float* m, floa
 
 extern "C" int gsfit_features_refresh(const float* params, int32_t n, int32_t n_planes, void* features,
                                       int32_t feature_dtype, cudaStream_t stream) {
-    if (!params || !features || n < 1 || n_planes < 2 || n_planes > kMaxPlanes ||
+    if (!params || !features || n < 1 || n_planes <= kFeaturePlane0 || n_planes > kMaxPlanes ||
         (reinterpret_cast<uintptr_t>(params) % 16) != 0 || (reinterpret_cast<uintptr_t>(features) % 8) != 0 ||
         (feature_dtype != GSFIT_FEATURES_F16 && feature_dtype != GSFIT_FEATURES_BF16))
         return GSFIT_ERR_INVALID_ARG;
     int dev = 0, sms = 0;
     GSFIT_CUDA_CHECK(cudaGetDevice(&dev));
     GSFIT_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const long long total = (long long)(n_planes - 1) * n;
+    const long long total = (long long)(n_planes - kFeaturePlane0) * n;
     const long long want = (total + 255) / 256;
     const int blocks = (int)(want < 8ll * sms ? want : 8ll * sms);
     const float4* p4 = reinterpret_cast<const float4*>(params);

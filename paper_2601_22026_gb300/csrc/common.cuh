@@ -215,16 +215,20 @@ __device__ __forceinline__ float4 unpack_features(uint2 q) {
     return make_float4(a.x, a.y, b.x, b.y);
 }
 
-// Plane p of Gaussian i: plane 0 always from the float32 parameters, planes
-// 1.. from the 16-bit copy F when FT selects one.
+// First parameter plane of the 16-bit feature copy: the SH coefficient planes
+// 3.. (means, opacity, rotation and scales are always read in float32).
+constexpr int kFeaturePlane0 = 3;
+
+// Plane p of Gaussian i: planes 0-2 always from the float32 parameters, the
+// SH planes 3.. from the 16-bit copy F when FT selects one.
 template <int FT>
 __device__ __forceinline__ float4 load_plane(const float4* __restrict__ P, const uint2* __restrict__ F, int n, int p,
                                              int i) {
     if constexpr (FT == GSFIT_FEATURES_F32) {
         return P[(size_t)p * n + i];
     } else {
-        if (p == 0) return P[i];
-        return unpack_features<FT>(F[(size_t)(p - 1) * n + i]);
+        if (p < kFeaturePlane0) return P[(size_t)p * n + i];
+        return unpack_features<FT>(F[(size_t)(p - kFeaturePlane0) * n + i]);
     }
 }
 

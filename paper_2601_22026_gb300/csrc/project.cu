@@ -148,11 +148,7 @@ __device__ __forceinline__ void load_gauss(const float4* __restrict__ P, const u
     g.qn = sqrtf(p1.x * p1.x + p1.y * p1.y + p1.z * p1.z + p1.w * p1.w);
     const float inv = 1.0f / g.qn;
     g.qw = p1.x * inv; g.qx = p1.y * inv; g.qy = p1.z * inv; g.qz = p1.w * inv;
-    if constexpr (FT == GSFIT_FEATURES_F32) {
-        g.s[0] = expf(p2.x); g.s[1] = expf(p2.y); g.s[2] = expf(p2.z);
-    } else {  // the 16-bit copy holds the activated scales
-        g.s[0] = p2.x; g.s[1] = p2.y; g.s[2] = p2.z;
-    }
+    g.s[0] = expf(p2.x); g.s[1] = expf(p2.y); g.s[2] = expf(p2.z);
     quat_rot(g.qw, g.qx, g.qy, g.qz, g.R);
     const float* R = g.R;
     const float s0 = g.s[0] * g.s[0], s1 = g.s[1] * g.s[1], s2 = g.s[2] * g.s[2];

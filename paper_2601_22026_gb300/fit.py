@@ -35,7 +35,7 @@ class FitState:
                  lam: float = 0.2, features: str = "f32", tile: int = 16, batch: int = 128,
                  exp_half2: bool = False, device: str = "cuda"):
         """features: "f32", or "f16" / "bf16" for the mixed-precision form
-        (16-bit copy of rotation, scales and SH read by the projection, kept
+        (16-bit copy of the SH coefficients read by the projection, kept
         current by Adam; float32 master parameters and moments).
         tile (8 or 16) and batch (64, 128, 256 records per shared-memory
         slot): the compositing options; see tune.py for choosing them.
@@ -54,7 +54,7 @@ class FitState:
         self.features = None
         if self.feature_dtype != 0:
             tdt = torch.float16 if features == "f16" else torch.bfloat16
-            self.features = torch.empty((self.n_planes - 1, self.n, 4), dtype=tdt, device=device)
+            self.features = torch.empty((self.n_planes - 3, self.n, 4), dtype=tdt, device=device)
             self.refresh_features()
         self.grads = torch.zeros_like(self.params)
         self.m = torch.zeros_like(self.params)
@@ -86,7 +86,7 @@ class FitState:
         st.m = torch.zeros_like(st.params)
         st.v = torch.zeros_like(st.params)
         if st.feature_dtype != 0:
-            st.features = torch.empty((st.n_planes - 1, st.n, 4), dtype=st.features.dtype, device=st.device)
+            st.features = torch.empty((st.n_planes - 3, st.n, 4), dtype=st.features.dtype, device=st.device)
             st.refresh_features()
         st.set_cameras(cams, bg=kw.get("bg"))
         st.capacity = 0

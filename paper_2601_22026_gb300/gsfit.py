@@ -35,7 +35,7 @@ class Gaussians(ctypes.Structure):
                 ("reserved", _i32)]
 
 
-ABI_VERSION = 3  # GSFIT_ABI_VERSION of include/gsfit.h
+ABI_VERSION = 4  # GSFIT_ABI_VERSION of include/gsfit.h
 
 # gsfit_gaussians.feature_dtype values (GSFIT_FEATURES_*)
 FEATURES = {"f32": 0, "f16": 1, "bf16": 2}
@@ -91,6 +91,7 @@ SIGNATURES = {
     "gsfit_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_int64, _P, _P]),
     "gsfit_selftest_lookback_timeout": (ctypes.c_int, [_P, _i32, _P, _P]),
     "gsfit_selftest_splat_power": (ctypes.c_int, [_P, _P, _i32, _P, _P]),
+    "gsfit_selftest_alu_rate": (ctypes.c_int, [_i32, _i32, _i32, _P, _P]),
     "gsfit_reproject": (ctypes.c_int, [_P, _P, _i32, _i32, _P, _P, _P, _i32, _i32, _P, _P, _P, _P, _P]),
 }
 
@@ -464,3 +465,8 @@ def gsfit_selftest_lookback_timeout(word, polls, status, stream=None):
 def gsfit_selftest_splat_power(conic, pix, n, out, stream=None):
     _check(load().gsfit_selftest_splat_power(_ptr(conic), _ptr(pix), int(n), _ptr(out), _stream(stream)),
            "gsfit_selftest_splat_power")
+
+
+def gsfit_selftest_alu_rate(kind: int, blocks: int, iters: int, sink, stream=None) -> None:
+    _check(load().gsfit_selftest_alu_rate(int(kind), int(blocks), int(iters), _ptr(sink), _stream(stream)),
+           "gsfit_selftest_alu_rate")

@@ -37,7 +37,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version_and_status_strings(lib):
-    assert lib.gsfit_abi_version() == 3
+    assert lib.gsfit_abi_version() == 4
     assert lib.gsfit_status_string(G.GSFIT_ERR_CAPACITY) == b"instance capacity exceeded"
     assert lib.gsfit_status_string(G.GSFIT_ERR_TIMEOUT) == b"bounded device wait ran out"
 
@@ -133,7 +133,7 @@ def test_feature_storage_arguments_rejected_on_host(lib):
     assert lib.gsfit_adam_step(fake, fake, fake, fake, 10, 4, lr, 0.9, 0.999, 1e-15, fake, fake, 5,
                                None) == G.GSFIT_ERR_INVALID_ARG
     assert lib.gsfit_features_refresh(fake, 10, 4, fake, G.FEATURES["f32"], None) == G.GSFIT_ERR_INVALID_ARG
-    assert lib.gsfit_features_refresh(fake, 10, 1, fake, G.FEATURES["f16"], None) == G.GSFIT_ERR_INVALID_ARG
+    assert lib.gsfit_features_refresh(fake, 10, 3, fake, G.FEATURES["f16"], None) == G.GSFIT_ERR_INVALID_ARG
 
 
 def test_camera_layout_tile_edges(lib):
