@@ -18,10 +18,11 @@
 // never changes a result) and walks only those, one branch-free step per
 // entry. The adjoint keeps no per-(pixel, Gaussian) state: it restarts from
 // the stored final transmittance and contributor count and recovers T_i =
-// T_{i+1} / (1 - alpha_i) walking backwards, and sums the nine per-Gaussian
-// gradient terms of the warp with a transposed butterfly (12 shuffles instead
-// of 45) that leaves each total in its own lane, so one scalar-atomic
-// instruction of nine lanes accumulates them.
+// T_{i+1} / (1 - alpha_i) walking backwards. Where at most 16 lanes blend a
+// Gaussian, each adds its nine gradient terms with three 16-byte vector
+// atomics; otherwise the warp sums them with a transposed butterfly (12
+// shuffles instead of 45) that leaves each total in its own lane, so one
+// scalar-atomic instruction of nine lanes accumulates them.
 #include "common.cuh"
 
 namespace gsfit {
@@ -470,6 +471,21 @@ __global__ void __launch_bounds__(TileShape<TILE>::kThreads) render_fwd_kernel(
     }
 }
 
+// Adjoint visits where at most this many lanes blend the Gaussian skip the
+// warp reduction: each blending lane adds its nine terms to the record's
+// grad2d entry itself with three 16-byte vector atomics (no more L2 atomic
+// operations than the nine-lane scalar atomic after the butterfly for up to
+// three lanes; measured fastest at 16 on the bench workload: fewer lanes
+// leave more visits to the 42-instruction butterfly, more flood the L2 with
+// atomics).
+constexpr int kDirectLanes = 16;
+
+// Adds (a, b, c, 0) to the 16-byte-aligned float4 at addr (one vector atomic).
+__device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float c) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(0.0f)
+                 : "memory");
+}
+
 // Transposed butterfly sum of nine values over the warp (12 shuffles): at each
 // level the two partner lanes split their remaining values in halves, each
 // keeping one half and adding its partner's copy of it. Afterwards the lane
@@ -675,9 +691,20 @@ __global__ void __launch_bounds__(TileShape<TILE>::kThreads, 5) render_bwd_kerne
                 const bool hit = pix_bwd_step<E16>(q, base + (uint32_t)j, R.co[s][j], &R.col[s][j],
                                                    __fadd2_rn(fxx, make_float2(p.x, p.y)),
                                                    __fadd2_rn(fyy, make_float2(p.z, p.w)), g9);
-                if (__any_sync(0xffffffffu, hit)) {
-                    const float tot = reduce9(g9, lane);
-                    if (slot >= 0) atomicAdd(grad2d + 16 * (rec0 + R.g[s][j]) + slot_off, tot);
+                const uint32_t hm = __ballot_sync(0xffffffffu, hit);
+                if (hm != 0u) {
+                    float* gp = grad2d + 16 * (rec0 + R.g[s][j]);
+                    if (__popc(hm) <= kDirectLanes) {
+                        // few blending lanes: each adds its own nine terms
+                        if (hit) {
+                            red_add_v4(gp, g9[0], g9[1], g9[2]);
+                            red_add_v4(gp + 4, g9[3], g9[4], g9[5]);
+                            red_add_v4(gp + 8, g9[6], g9[7], g9[8]);
+                        }
+                    } else {
+                        const float tot = reduce9(g9, lane);
+                        if (slot >= 0) atomicAdd(gp + slot_off, tot);
+                    }
                 }
             }
         }
