@@ -77,8 +77,9 @@ def lib() -> ctypes.CDLL:
         L.oracle_loss.restype = d
         L.oracle_adam.argtypes = [ll, P, P, P, P, P, d, d, d, i]
         L.oracle_real_sh.argtypes = [i, P, P, P]
-        L.oracle_tiles_fwd.argtypes = [i, i, P, i, P, i, i, P, P, P, P, P, P, P, P, P, i]
+        L.oracle_tiles_fwd.argtypes = [i, i, P, i, P, i, i, P, P, P, P, P, P, P, P, P, i, P]
         L.oracle_gauss_bwd.argtypes = [i, i, P, i, P, i, P, P, P, i, P, P, P]
+        L.oracle_project_bwd.argtypes = [i, i, P, i, P, i, P, P, P]
         L.oracle_set_threads.argtypes = [i]
         L.oracle_max_threads.restype = i
         assert L.oracle_proj_stride() == len(PROJ_FIELDS)
@@ -160,6 +161,19 @@ def project(gs: dict, cams: dict, tile: int = 16, smooth: bool = False) -> np.nd
     proj = np.zeros((V, n, len(PROJ_FIELDS)), dtype=np.float64)
     lib().oracle_project(n, K, _p(g), V, _p(c), tile, SMOOTH if smooth else 0, _p(proj))
     return proj
+
+
+def project_bwd(gs: dict, cams: dict, proj: np.ndarray, grad2d: np.ndarray, tile: int = 16) -> np.ndarray:
+    """The projection adjoint alone: parameter gradients (packed Gaussian
+    rows, summed over views) of the per-(view, Gaussian) 2D gradients grad2d
+    (V, N, 9: u, v, a', b', c', opacity, r, g, b) at the projected records."""
+    g = pack_gaussians(gs)
+    c = pack_cameras(cams)
+    n, K, V = g.shape[0], gs["sh"].shape[1], c.shape[0]
+    out = np.zeros_like(g)
+    lib().oracle_project_bwd(n, K, _p(g), V, _p(c), tile, _p(np.ascontiguousarray(proj)),
+                             _p(np.ascontiguousarray(grad2d, dtype=np.float64)), _p(out))
+    return out
 
 
 def bin_tiles(proj: np.ndarray, cams: dict, tile: int = 16):
@@ -291,8 +305,8 @@ def grad_groups_flat(K: int) -> dict:
 
 def render_tiles(gs: dict, cams: dict, bg: np.ndarray, items, tile: int = 16, max_list: int = 20000) -> dict:
     """Composite only the given (view, local tile id) items, one view at a
-    time; per item B x B pixels (row-major in the tile) and its sorted
-    Gaussian list."""
+    time; per item B x B pixels (row-major in the tile), their blend and
+    clamp counts (n_blended, n_clamped), and its sorted Gaussian list."""
     g = pack_gaussians(gs)
     c = pack_cameras(cams)
     n, K, V = g.shape[0], gs["sh"].shape[1], c.shape[0]
@@ -305,10 +319,12 @@ def render_tiles(gs: dict, cams: dict, bg: np.ndarray, items, tile: int = 16, ma
     amb = np.zeros((m, B2), dtype=np.uint8)
     ll = np.zeros(m, dtype=np.int32)
     lists = np.zeros((m, max_list), dtype=np.uint32)
+    nb = np.zeros((m, B2, 2), dtype=np.int32)
     bgd = np.ascontiguousarray(bg, dtype=np.float64).reshape(V, 3)
     lib().oracle_tiles_fwd(n, K, _p(g), V, _p(c), tile, m, _p(it), _p(bgd), _p(rgb), _p(alpha), _p(T), _p(nc),
-                           _p(amb), _p(ll), _p(lists), max_list)
+                           _p(amb), _p(ll), _p(lists), max_list, _p(nb))
     return {"rgb": rgb, "alpha": alpha, "T_final": T, "n_contrib": nc, "ambiguous": amb.astype(bool),
+            "n_blended": nb[:, :, 0], "n_clamped": nb[:, :, 1],
             "list_len": ll, "lists": [lists[k, :min(ll[k], max_list)].copy() for k in range(m)]}
 
 

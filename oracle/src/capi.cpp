@@ -25,10 +25,11 @@ void adam(long long n, double* p, const double* g, double* m, double* v, const d
           double eps, int step);
 void tiles_fwd(int n, int K, const double* gauss, const std::vector<Camera>& cams, int tile, int n_items,
                const int32_t* items, const double* bg, double* rgb, double* alpha, double* T_final, int32_t* nc,
-               uint8_t* amb, int32_t* list_len, uint32_t* lists, int max_list);
+               uint8_t* amb, int32_t* list_len, uint32_t* lists, int max_list, int32_t* nb);
 void gauss_bwd(int n, int K, const double* gauss, const std::vector<Camera>& cams, int tile, const double* bg,
                const double* dL_drgb, const double* dL_dalpha, int n_req, const int32_t* req, double* grads_out,
                uint8_t* amb_out);
+void project_bwd_one(const double* g, int K, const Camera& cam, const double g2[9], double* gout);
 }  // namespace oracle
 
 using namespace oracle;
@@ -107,6 +108,25 @@ void oracle_render_bwd(int n, int K, const double* gauss, int V, const double* c
                gauss_ambiguous);
 }
 
+// The projection adjoint alone (the second half of oracle_render_bwd): for
+// every visible (view, Gaussian) record, dL/d(parameters) of the 2D gradients
+// in grad2d (V * n * 9, the layout render_bwd writes), summed over views into
+// grads (zeroed first). Used to time the per-view share of an iteration.
+void oracle_project_bwd(int n, int K, const double* gauss, int V, const double* cams, int tile, const double* proj,
+                        const double* grad2d, double* grads) {
+    const std::vector<Camera> c = unpack_cameras(V, cams, tile);
+    const int stride = gauss_stride(K);
+    std::memset(grads, 0, sizeof(double) * (size_t)n * stride);
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < n; ++i)
+        for (int v = 0; v < V; ++v) {
+            const double* p = proj + ((size_t)v * n + i) * P_STRIDE;
+            if (p[P_VISIBLE] == 0.0) continue;
+            project_bwd_one(gauss + (size_t)i * stride, K, c[v], grad2d + ((size_t)v * n + i) * 9,
+                            grads + (size_t)i * stride);
+        }
+}
+
 double oracle_loss(int V, const int* W, const int* H, const double* rgb, const double* alpha,
                    const double* target_rgb, const double* target_alpha, const double* bg, double lambda,
                    double* dL_drgb, double* dL_dalpha, double* ssim_out) {
@@ -122,9 +142,9 @@ void oracle_real_sh(int deg, const double* dir, double* Y, double* dY) { real_sh
 
 void oracle_tiles_fwd(int n, int K, const double* gauss, int V, const double* cams, int tile, int n_items,
                       const int32_t* items, const double* bg, double* rgb, double* alpha, double* T_final,
-                      int32_t* nc, uint8_t* amb, int32_t* list_len, uint32_t* lists, int max_list) {
+                      int32_t* nc, uint8_t* amb, int32_t* list_len, uint32_t* lists, int max_list, int32_t* nb) {
     const std::vector<Camera> c = unpack_cameras(V, cams, tile);
-    tiles_fwd(n, K, gauss, c, tile, n_items, items, bg, rgb, alpha, T_final, nc, amb, list_len, lists, max_list);
+    tiles_fwd(n, K, gauss, c, tile, n_items, items, bg, rgb, alpha, T_final, nc, amb, list_len, lists, max_list, nb);
 }
 
 void oracle_gauss_bwd(int n, int K, const double* gauss, int V, const double* cams, int tile, const double* bg,

@@ -338,11 +338,12 @@ void bin_view(int n, int K, const double* gauss, const Camera& cam, int tile, Vi
 
 // items: n_items (view, local tile) pairs. Per item, B x B pixels (row-major
 // in the tile; pixels outside the view get n_contrib -1): colour (3 planes),
-// alpha, T_final, n_contrib, ambiguity; and the tile's sorted Gaussian list
-// (list_len[item] entries, at most max_list copied).
+// alpha, T_final, n_contrib, ambiguity, and (if nb is not null) the number of
+// blended and of clamped Gaussians (nb: 2 ints per pixel); and the tile's
+// sorted Gaussian list (list_len[item] entries, at most max_list copied).
 void tiles_fwd(int n, int K, const double* gauss, const std::vector<Camera>& cams, int tile, int n_items,
                const int32_t* items, const double* bg, double* rgb, double* alpha, double* T_final, int32_t* nc,
-               uint8_t* amb, int32_t* list_len, uint32_t* lists, int max_list) {
+               uint8_t* amb, int32_t* list_len, uint32_t* lists, int max_list, int32_t* nb) {
     const int B2 = tile * tile;
     for (int v = 0; v < (int)cams.size(); ++v) {
         bool any = false;
@@ -373,6 +374,12 @@ void tiles_fwd(int n, int K, const double* gauss, const std::vector<Camera>& cam
                 T_final[o] = px.T;
                 nc[o] = px.n_contrib;
                 amb[o] = px.ambiguous ? 1 : 0;
+                if (nb) {
+                    int clamped = 0;
+                    for (const Blend& e : px.blends) clamped += e.clamped ? 1 : 0;
+                    nb[2 * o] = (int32_t)px.blends.size();
+                    nb[2 * o + 1] = clamped;
+                }
             }
         }
     }

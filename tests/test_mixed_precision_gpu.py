@@ -141,15 +141,16 @@ def test_gradients_match_oracle_on_the_16bit_features(kind):
 @pytest.mark.parametrize("kind", KINDS)
 def test_error_of_the_16bit_form_against_full_precision(kind):
     """Per-output error of the 16-bit form against the FP64 oracle on the
-    unrounded float32 features (SH 3, 50k Gaussians, one 512^2 view).
+    unrounded float32 features (SH 3, 50k Gaussians, one 512^2 view), and the
+    bounds of the mixed-precision target for the half form: images within
+    2e-3, gradients within 1e-3 relative.
 
-    Compositing is discontinuous at its thresholds (skip below alpha = 1/255,
-    clamp at 0.99, stop before T < 1e-4): where rounding a feature to 16 bits
-    moves some Gaussian across one of them at a pixel, that pixel's colour
-    jumps by about one Gaussian's weight (up to ~1/255). Such pixels are found
-    by rendering the oracle on both feature sets and comparing its per-pixel
-    blend counts; the 2e-3 image bound applies to the others, and the share of
-    pixels with a changed decision is stated and bounded."""
+    Only colours are stored in 16 bits, and the compositing's skip, clamp and
+    stop decisions depend on the splat geometry and opacity alone: the oracle
+    takes the same decision at every pixel on both feature sets (checked).
+    Pixels the oracle flags as near a threshold (where the float32 GPU and the
+    FP64 oracle may legitimately decide differently, as in the float32 form)
+    are left out of the image bounds and counted."""
     from test_parity_gpu import _rgb_to_pixels
     gs, cams, bg = _scene("differentiation_512")
     P = scenes.num_pixels(cams)
@@ -166,16 +167,18 @@ def test_error_of_the_16bit_form_against_full_precision(kind):
     ref = oracle.render(gs, cams, bg)
     ref16 = oracle.render(_snapped(gs, kind), cams, bg)
     refg = oracle.render_bwd(gs, cams, bg, w_rgb.astype(np.float64), w_a.astype(np.float64))
-    same = ((ref["n_contrib"] == ref16["n_contrib"]) & (ref["n_blended"] == ref16["n_blended"]) &
-            ~ref["ambiguous"] & ~ref16["ambiguous"])
+    # rounding colours moves no decision
+    np.testing.assert_array_equal(ref["n_contrib"], ref16["n_contrib"])
+    np.testing.assert_array_equal(ref["n_blended"], ref16["n_blended"])
+    same = ~ref["ambiguous"] & ~ref16["ambiguous"]
     err = np.abs(rgb - _rgb_to_pixels(ref["rgb"], cams))
     aerr = np.abs(alpha - ref["alpha"])
-    rows = {"image, max abs (same decisions)": float(err[same].max()),
+    rows = {"image, max abs (unflagged pixels)": float(err[same].max()),
             "image, max abs (all pixels)": float(err.max()),
             "image, mean abs (all pixels)": float(err.mean()),
-            "alpha, max abs (same decisions)": float(aerr[same].max()),
+            "alpha, max abs (unflagged pixels)": float(aerr[same].max()),
             "alpha, max abs (all pixels)": float(aerr.max()),
-            "pixels with a changed decision": float(1.0 - same.mean())}
+            "pixels flagged near a threshold": float(1.0 - same.mean())}
     grads = st.gradients()
     for k in ["means", "log_scales", "quats", "opacity_logits", "sh"]:
         a = np.asarray(grads[k], np.float64).reshape(-1)
@@ -184,15 +187,18 @@ def test_error_of_the_16bit_form_against_full_precision(kind):
     print(f"\n16-bit form ({kind}) vs FP64 oracle on float32 features, 50k Gaussians SH3, 512x512:")
     for k, v in rows.items():
         print(f"  {k:36s} {v:.3e}")
-    # bfloat16 keeps 8 significant bits (half: 11): only sanity bounds for it
-    assert rows["pixels with a changed decision"] <= (0.3 if kind == "f16" else 0.6)
+    assert rows["pixels flagged near a threshold"] <= 0.02
     assert rows["image, max abs (all pixels)"] <= 2.0 / 255.0  # at most about one threshold jump
-    assert rows["image, mean abs (all pixels)"] <= (2e-4 if kind == "f16" else 1e-3)
     if kind == "f16":
-        assert rows["image, max abs (same decisions)"] <= 2e-3
-        assert rows["alpha, max abs (same decisions)"] <= 2e-3
+        assert rows["image, max abs (unflagged pixels)"] <= 2e-3
+        assert rows["alpha, max abs (unflagged pixels)"] <= 2e-3
         for k in ["means", "log_scales", "quats", "opacity_logits", "sh"]:
-            assert rows[f"grad {k}, rel. norm"] <= 3e-2, k
+            assert rows[f"grad {k}, rel. norm"] <= 1e-3, k
+    else:
+        # bfloat16 keeps 8 significant bits (half: 11): sanity bounds only
+        assert rows["image, max abs (unflagged pixels)"] <= 4e-3
+        for k in ["means", "log_scales", "quats", "opacity_logits", "sh"]:
+            assert rows[f"grad {k}, rel. norm"] <= 5e-3, k
 
 
 def test_error_of_the_half2_exponent_option():

@@ -583,6 +583,7 @@ def test_sampled_entry_points_equal_full_render():
             assert abs(got["alpha"][k, q] - full["alpha"][pix]) <= 1e-12
             assert abs(got["T_final"][k, q] - full["T_final"][pix]) <= 1e-12
             assert got["n_contrib"][k, q] == full["n_contrib"][pix]
+            assert got["n_blended"][k, q] == full["n_blended"][pix]
             assert got["ambiguous"][k, q] == full["ambiguous"][pix]
     # gradients of chosen Gaussians
     P = int(off[-1])
@@ -599,6 +600,23 @@ def test_sampled_entry_points_equal_full_render():
     assert np.all(rows[seen[req] == 0] == 0)
     ref_amb = b["gauss_ambiguous"].any(axis=0) | (full["proj"][:, :, F["near_boundary"]] > 0).any(axis=0)
     np.testing.assert_array_equal(amb, ref_amb[req])
+
+
+def test_projection_adjoint_entry_equals_the_second_half_of_render_bwd():
+    """oracle.project_bwd (the projection adjoint alone, used to time the
+    per-view share of an iteration) applied to render_bwd's 2D gradients
+    gives render_bwd's parameter gradients."""
+    gs = scenes.random_gaussians(300, 1, 31)
+    cams = scenes.stack_cameras([
+        scenes.make_camera((0, 0.5, 3), (0, 0, 0), 48, 40, fx=50.0),
+        scenes.make_camera((2.5, 0, 1), (0, 0, 0), 32, 56, fx=40.0)])
+    bg = scenes.backgrounds(2, 5)
+    P = int(oracle.pixel_offsets(cams)[-1])
+    g = scenes.rng(3)
+    b = oracle.render_bwd(gs, cams, bg, g.normal(size=3 * P), g.normal(size=P))
+    got = oracle.project_bwd(gs, cams, oracle.project(gs, cams), b["grad2d"])
+    assert np.abs(b["grads_flat"]).max() > 0
+    np.testing.assert_array_equal(got, b["grads_flat"])
 
 
 def test_adjoint_sums_over_views():

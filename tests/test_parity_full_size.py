@@ -1,9 +1,13 @@
-"""Parity at the benchmark's full size: 1,000,000 Gaussians (SH 3) from the
-512x512x400 CT volume and the 16-view batch (2 x 1920^2 periphery frames +
-14 foveal crops), through the same kernels and launch configuration the
-benchmark times. The oracle cannot render the batch whole, so it computes
-sampled outputs one by one: every pixel and the sorted list of sampled tiles,
-and the complete gradients of sampled Gaussians."""
+"""Parity at the benchmark's full sizes, through the same kernels and launch
+configuration the benchmark times:
+  * the batched periphery: 1,000,000 Gaussians (SH 3) from the 512x512x400
+    CT volume and the 16-view batch (2 x 1920^2 periphery frames + 14 foveal
+    crops);
+  * the CT periphery: 200,000 Gaussians seeded from the 256^3 CT volume and
+    one of its 24 orbit views of 1024^2 (one view per iteration).
+The oracle cannot render these whole, so it computes sampled outputs one by
+one: every pixel and the sorted list of sampled tiles, and the complete
+gradients of sampled Gaussians."""
 import numpy as np
 import pytest
 
@@ -58,10 +62,34 @@ def _sample_items(sc, per_view=4, seed=9):
     return items
 
 
-def test_full_size_sampled_tiles(batch):
-    sc, st = batch
+@pytest.fixture(scope="module")
+def ct_view():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import paper_2601_22026_gb300 as pkg
+    from paper_2601_22026_gb300.fit import FitState
+    pkg.build()
+    full = scenes.ct_periphery_scene(0)
+    v = 3
+    sc = {"gaussians": full["gaussians"], "cameras": scenes.camera_subset(full["cameras"], [v]),
+          "bg": full["bg"][v:v + 1]}
+    st = FitState(sc["gaussians"], sc["cameras"], bg=sc["bg"])
+    st.forward()
+    torch.cuda.synchronize()
+    assert st.check_status() == 0
+    return sc, st
+
+
+@pytest.fixture(params=["batched_1M_16views", "ct_200k_1024"])
+def workload(request):
+    return request.getfixturevalue("batch" if request.param == "batched_1M_16views" else "ct_view")
+
+
+def test_full_size_sampled_tiles(workload):
+    sc, st = workload
     gs, cams, bg = sc["gaussians"], sc["cameras"], sc["bg"]
-    items = _sample_items(sc)
+    per_view = max(4, 48 // len(sc["cameras"]["width"]))
+    items = _sample_items(sc, per_view=per_view)
     assert len(items) >= 48
     ref = oracle.render_tiles(gs, cams, bg, items)
     ranges = st.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2)
@@ -100,8 +128,8 @@ def test_full_size_sampled_tiles(batch):
     assert exact_lists >= len(items) - 2 and compared > 10000
 
 
-def test_full_size_sampled_gradients(batch):
-    sc, st = batch
+def test_full_size_sampled_gradients(workload):
+    sc, st = workload
     gs, cams, bg = sc["gaussians"], sc["cameras"], sc["bg"]
     P = st.P
     w_rgb = scenes.cotangents(3 * P, 701, 1e-3)

@@ -287,13 +287,17 @@ def test_render_fwd_matches_oracle(name):
     np.testing.assert_array_equal(st.n_contrib.cpu().numpy()[ok], ref["n_contrib"][ok])
 
 
-def _grad_check(gpu: dict, ref: dict, amb_gauss: np.ndarray, rtol=1e-3, floor=2e-2):
+def _grad_check(gpu: dict, ref: dict, amb_gauss: np.ndarray, rtol=1e-3, floor=1e-2):
     """Per parameter group: ||g_gpu - g_ref|| / ||g_ref|| <= rtol, and per
     element |g_gpu - g_ref| <= rtol (|g_ref| + floor * max|g_ref|) for all but
-    one element in 10^4 (none beyond five times the bound). The
-    absolute floor (rtol * 2e-2 of the group's largest element) covers
-    elements that are small sums of large cancelling per-pixel terms, where
-    float32 accumulation cannot reach rtol relative."""
+    one element in 10^4 (none beyond five times the bound). The absolute
+    floor (rtol * 1e-2 of the group's largest element) covers elements that
+    are small sums of large cancelling per-pixel terms, where float32
+    accumulation cannot reach rtol relative. Measured on GB300 (the GRADSTAT
+    lines this prints): only the 50k-Gaussian 512^2 case has elements over
+    the bound, 4 of 146,217 means (at most 1.65 x), 1 log-scale (2.31 x) and
+    8 of 2,339,472 SH coefficients (1.77 x); every other case is within
+    0.25 x of it."""
     import os
     label = os.environ.get("PYTEST_CURRENT_TEST", "").split(" ")[0]
     keep = ~amb_gauss
@@ -437,8 +441,7 @@ def test_full_step_plain_single_view():
     assert float(st.loss_out.item()) == pytest.approx(L, rel=1e-4)
     b = oracle.render_bwd(gs, cams, bg, g_rgb, g_a, fwd=fwd)
     amb = b["gauss_ambiguous"].any(axis=0) | (fwd["proj"][:, :, F["near_boundary"]] > 0).any(axis=0)
-    # pixels whose L1 sign the float32 render may flip
-    _grad_check(st.gradients(), b["grads"], amb, rtol=2e-3)
+    _grad_check(st.gradients(), b["grads"], amb)
     # Adam step 1 with eps 1e-15 moves each parameter by lr * sign(g)
     from paper_2601_22026_gb300 import gsfit as G
     after = st.gaussians()
