@@ -56,6 +56,33 @@ def alu_peak_tflops(sm_mhz: float) -> float:
     return NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
 
 
+def measure_alu_peaks(reps: int = 5) -> dict:
+    """FP32 FMA (scalar and packed two-lane) and MUFU exp2 rates of this GPU,
+    from gsfit_selftest_alu_rate: eight CTAs of 256 threads per SM, eight
+    independent chains per thread, best of `reps` event-timed launches."""
+    import torch
+    from paper_2601_22026_gb300 import gsfit as G
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    blocks, iters = 8 * sms, 4096
+    sink = torch.empty(blocks * 256, device="cuda")
+    ops = blocks * 256 * 8 * iters
+    out = {}
+    for kind, name, per_op in ((0, "fma_tflops", 2), (1, "fma2_tflops", 4), (2, "ex2_tops", 1)):
+        G.gsfit_selftest_alu_rate(kind, blocks, iters, sink)
+        best = float("inf")
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            G.gsfit_selftest_alu_rate(kind, blocks, iters, sink)
+            b.record()
+            torch.cuda.synchronize()
+            best = min(best, a.elapsed_time(b))
+        out[name] = ops * per_op / (best * 1e-3) / 1e12
+    out["how"] = (f"gsfit_selftest_alu_rate: {blocks} CTAs x 256 threads x 8 chains x {iters} ops, "
+                  "best of 5 event-timed launches; fma counts 2 FLOP, fma.f32x2 4, ex2 one op")
+    return out
+
+
 def measured_traffic(kernel: str):
     """Bytes per launch of `kernel` from the ncu summary under profiles/,
     if the kernel source it was measured on is unchanged (else None)."""
@@ -286,37 +313,106 @@ def e2e_rate(st, host_rgb, host_alpha, host_bg, steps: int) -> dict:
 # ---------------------------------------------------------------------------
 
 SAMPLE_VIEWS = [2, 3, 4, 5]  # four foveal crops of the 16-view batch
+VIEW_SUBSET = 16  # the per-view part is timed on a seeded 1/16 of the Gaussians
 
 
-def oracle_sample(sc, seconds_cap: float = 30.0) -> dict:
-    """One full fit iteration of the FP64 oracle (project, bin, composite,
-    loss, adjoint, Adam) over all 1M Gaussians and a subset of the views;
-    extrapolated to the whole batch by pixel count."""
+def oracle_sample(sc) -> dict:
+    """One FP64 oracle fit iteration on the host cores, timed in parts that
+    scale with different things:
+      per-view work: the projection and its adjoint of every (view, Gaussian)
+        record, over all views of the batch for a seeded 1/VIEW_SUBSET of the
+        Gaussians, scaled by VIEW_SUBSET (linear in the Gaussian count);
+      per-pixel work: tile lists, compositing, loss and blend adjoint over four
+        foveal crops with all Gaussians, scaled by the batch's pixel count;
+      Adam over all parameters, once.
+    The per-pixel part is the iteration on the crops less its own
+    projection and projection adjoint, timed separately."""
     import oracle
     oracle.build()
     cams = sc["cameras"]
+    gs = sc["gaussians"]
+    N = scenes.num_gaussians(gs)
     sub = scenes.camera_subset(cams, SAMPLE_VIEWS)
     bg = sc["bg"][SAMPLE_VIEWS]
-    gs = sc["gaussians"]
     P_sub = scenes.num_pixels(sub)
     P_all = scenes.num_pixels(cams)
     g = scenes.rng(5)
     tr = g.uniform(0, 1, 3 * P_sub)
     ta = g.uniform(0, 1, P_sub)
-    t0 = time.perf_counter()
+    clock = time.perf_counter
+    # per-view work on a subset of the Gaussians, all views
+    idx = np.sort(g.choice(N, N // VIEW_SUBSET, replace=False))
+    gsub = {k: v[idx] for k, v in gs.items()}
+    t0 = clock()
+    proj_all = oracle.project(gsub, cams)
+    t_proj_all = clock() - t0
+    g2 = g.normal(size=(proj_all.shape[0], proj_all.shape[1], 9))
+    t0 = clock()
+    oracle.project_bwd(gsub, cams, proj_all, g2)
+    t_pbwd_all = clock() - t0
+    del proj_all, g2
+    # the iteration on four crops, all Gaussians
+    t0 = clock()
     fwd = oracle.render(gs, sub, bg)
+    t_render = clock() - t0
+    t0 = clock()
     L, grgb, ga, _ = oracle.loss(fwd["rgb"], fwd["alpha"], tr, ta, bg, sub)
+    t_loss = clock() - t0
+    t0 = clock()
     b = oracle.render_bwd(gs, sub, bg, grgb, ga, fwd=fwd)
+    t_bwd = clock() - t0
     flat = oracle.pack_gaussians(gs)
     m = np.zeros_like(flat)
     v = np.zeros_like(flat)
+    t0 = clock()
     oracle.adam(flat, b["grads_flat"], m, v, 1e-3)
-    dt = time.perf_counter() - t0
-    est = dt * P_all / P_sub
+    t_adam = clock() - t0
+    # the crops' own per-view share, subtracted from the per-pixel part
+    t0 = clock()
+    proj_sub = oracle.project(gs, sub)
+    t_proj_sub = clock() - t0
+    t0 = clock()
+    oracle.project_bwd(gs, sub, proj_sub, b["grad2d"])
+    t_pbwd_sub = clock() - t0
+    per_view = (t_proj_all + t_pbwd_all) * VIEW_SUBSET
+    per_pixel = max(0.0, t_render - t_proj_sub) + t_loss + max(0.0, t_bwd - t_pbwd_sub)
+    est = per_view + per_pixel * P_all / P_sub + t_adam
+    spent = t_proj_all + t_pbwd_all + t_render + t_loss + t_bwd + t_adam + t_proj_sub + t_pbwd_sub
     return {"value": 1.0 / est, "unit": "iters/s", "cores": oracle.max_threads(), "kind": "oracle",
-            "sample": (f"one full FP64 iteration over all {scenes.num_gaussians(gs)} Gaussians and views "
-                       f"{SAMPLE_VIEWS} ({P_sub} px of {P_all}); {dt:.1f} s, scaled by pixel count"),
-            "sample_seconds": dt}
+            "sample": (f"FP64 oracle iteration in parts: projection + projection adjoint of all {len(cams['width'])} "
+                       f"views for {len(idx)} of {N} Gaussians (x{VIEW_SUBSET}); lists, compositing, loss and "
+                       f"blend adjoint of views {SAMPLE_VIEWS} with all Gaussians ({P_sub} of {P_all} px, scaled "
+                       f"by pixel count); Adam once; {spent:.1f} s of CPU work"),
+            "seconds_per_iteration": {"per_view": per_view, "per_pixel": per_pixel * P_all / P_sub,
+                                      "adam": t_adam, "total": est},
+            "sample_seconds": spent}
+
+
+def oracle_threads_compare() -> dict:
+    """The plain single-view step (2,000 Gaussians, one 128^2 view: forward,
+    loss, adjoint, Adam) of the FP64 oracle at one thread and at every host
+    thread."""
+    import oracle
+    sc = scenes.plain_single_view(0)
+    gs, cams, bg = sc["gaussians"], sc["cameras"], sc["bg"]
+    tgt = oracle.render(sc["target_gaussians"], cams, np.zeros((1, 3)))
+    out = {"workload": "plain single view: 2,000 Gaussians SH0, one 128x128 view, one full step"}
+    n_all = oracle.max_threads()
+    for n in (1, n_all):
+        oracle.set_threads(n)
+        best = float("inf")
+        for _ in range(3):
+            t0 = time.perf_counter()
+            fwd = oracle.render(gs, cams, bg)
+            L, grgb, ga, _ = oracle.loss(fwd["rgb"], fwd["alpha"], tgt["rgb"], tgt["alpha"], bg, cams)
+            b = oracle.render_bwd(gs, cams, bg, grgb, ga, fwd=fwd)
+            flat = oracle.pack_gaussians(gs)
+            oracle.adam(flat, b["grads_flat"], np.zeros_like(flat), np.zeros_like(flat), 1e-3)
+            best = min(best, time.perf_counter() - t0)
+        out[f"s_per_step_{n}_threads"] = best
+    oracle.set_threads(n_all)
+    out["threads"] = n_all
+    return out
 
 
 def mixed_precision_rate(sc, st, bg_table, warmup: int, steps: int, features: str = "f16",
@@ -356,7 +452,7 @@ def mixed_precision_rate(sc, st, bg_table, warmup: int, steps: int, features: st
 
 
 def refinement_leg(sc, st, iters: int, replace_every: int = 10, n_replace: int = 4, every: int = 25,
-                   features: str = "f16") -> dict:
+                   features: str = "f16", plain_passes: int = 300) -> dict:
     """The continuous-refinement loop of the mixed-precision form (16-bit
     features): every `replace_every` iterations `n_replace` foveal crops are
     replaced by newly streamed views that pass Eq. 1 (targets rendered from
@@ -364,8 +460,9 @@ def refinement_leg(sc, st, iters: int, replace_every: int = 10, n_replace: int =
     16-view batch (zero background) every `every` iterations; wall time
     excludes the PSNR evaluations. Beside it the plain float32 single-view
     form (one view per launch sequence and Adam step, no graph) from the same
-    start, for the same number of 16-view passes; reports when the refinement
-    loop first reaches the PSNR the plain form ends at."""
+    start, for plain_passes 16-view passes (its PSNR has levelled off well
+    before); reports when the refinement loop first reaches the PSNR the
+    plain form ends at."""
     import itertools
     import torch
     from paper_2601_22026_gb300 import refine
@@ -428,14 +525,145 @@ def refinement_leg(sc, st, iters: int, replace_every: int = 10, n_replace: int =
         for s1 in per_view:
             s1.step()
 
-    curve_pl = run(plain_pass, ev_pl, n_blocks)
+    curve_pl = run(plain_pass, ev_pl, max(1, min(iters, plain_passes) // every))
     target = curve_pl[-1][2]
     reach = next((c for c in curve if c[2] >= target), None)
-    out["plain_fp32_single_view"] = {"passes": n_blocks * every, "wall_s": curve_pl[-1][1],
+    out["plain_fp32_single_view"] = {"passes": curve_pl[-1][0], "wall_s": curve_pl[-1][1],
                                      "psnr_db": [[c[0], round(c[1], 4), round(c[2], 3)] for c in curve_pl]}
     out["time_to_plain_final_psnr"] = None if reach is None else {
         "iterations": reach[0], "wall_s": reach[1], "speedup_vs_plain": curve_pl[-1][1] / max(reach[1], 1e-9)}
     del per_view, ev_pl, pl, tgt
+    torch.cuda.empty_cache()
+    return out
+
+
+def differentiation_fit_leg(iters: int = 300, every: int = 10) -> dict:
+    """The differentiation workload (50,000 Gaussians, SH degree 3, one 512^2
+    view) fitted for `iters` iterations against the render of a second seeded
+    set (the ground truth), with a random background per iteration: the
+    photometric loss curve L1 + 0.2 (1 - SSIM) of the colour channels, read
+    every `every` iterations from the loss kernel's per-view sums (and the
+    full objective, which adds the alpha L1)."""
+    import torch
+    from paper_2601_22026_gb300.fit import FitState, boosted_lr
+    sc = scenes.differentiation_scene(0)
+    cams = sc["cameras"]
+    tgt = FitState(sc["target_gaussians"], cams, bg=np.zeros((1, 3), np.float32))
+    tgt.forward()
+    st = FitState(sc["gaussians"], cams, bg=sc["bg"], lr=boosted_lr())
+    st.target_rgb.copy_(tgt.rgb)
+    st.target_alpha.copy_(tgt.alpha)
+    del tgt
+    bgs = torch.from_numpy(scenes.backgrounds(1, 9, n_steps=iters)).cuda()
+    st.capture(warmup=0)
+    P = st.P
+    curve = []
+    t0 = time.perf_counter()
+    for k in range(iters):
+        st.bg.copy_(bgs[k])
+        st.replay()
+        if (k + 1) % every == 0 or k == 0:
+            acc = st.loss_ws[:3].cpu().numpy().astype(np.float64)
+            l1, ssim = acc[0] / (3 * P), acc[1] / (3 * P)
+            curve.append([k + 1, round(l1 + 0.2 * (1.0 - ssim), 6), round(float(st.loss_out.item()), 6)])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if st.check_status() != 0:
+        raise RuntimeError("device status set in the differentiation fit leg")
+    del st
+    torch.cuda.empty_cache()
+    return {"workload": "differentiation: 50k Gaussians SH3, one 512x512 view, targets from a second seeded set",
+            "iterations": iters, "wall_s_with_reads": wall,
+            "curve": curve, "curve_columns": ["iteration", "L1 + 0.2 (1 - SSIM)", "objective (+ alpha L1)"]}
+
+
+def ct_periphery_leg(iters: int = 240, warmup: int = 10) -> dict:
+    """The CT-derived periphery (200,000 Gaussians seeded from the 256^3 CT
+    volume through the transfer function) fitted against 24 orbit views of
+    1024^2 rendered from the ground-truth set, one view per iteration in a
+    seeded order: one captured iteration whose camera record, target images
+    and background are swapped in (device-to-device copies, timed) before
+    each replay. Reports iterations/s, per-stage times and arithmetic and
+    bandwidth fractions of one such iteration, and the loss and masked PSNR
+    over all 24 views before and after."""
+    import torch
+    from paper_2601_22026_gb300 import gsfit as G
+    from paper_2601_22026_gb300 import refine
+    from paper_2601_22026_gb300.fit import FitState, boosted_lr
+    sc = scenes.ct_periphery_scene(0)
+    cams = sc["cameras"]
+    V = len(cams["width"])
+    P1 = int(cams["width"][0]) * int(cams["height"][0])
+    zeros = np.zeros((V, 3), np.float32)
+    tgt = FitState(sc["target_gaussians"], cams, bg=zeros)
+    tgt.forward()
+    t_rgb, t_alpha = tgt.rgb.view(V, 3 * P1).clone(), tgt.alpha.view(V, P1).clone()
+    del tgt
+    tables = torch.stack([G.cameras_to_device(G.camera_table(scenes.camera_subset(cams, [v]))) for v in range(V)])
+    st = FitState(sc["gaussians"], scenes.camera_subset(cams, [0]), bg=zeros[:1], lr=boosted_lr())
+    need = 0
+    for v in range(V):
+        st.cams_dev.copy_(tables[v])
+        need = max(need, st.count_instances())
+    st.ensure_capacity(int(need * 1.5))
+    order = scenes.rng(5).permutation(V)
+    bgs = torch.from_numpy(scenes.backgrounds(1, 6, n_steps=warmup + iters)).cuda()
+
+    def load(k):
+        v = int(order[k % V])
+        st.cams_dev.copy_(tables[v])
+        st.target_rgb.copy_(t_rgb[v])
+        st.target_alpha.copy_(t_alpha[v])
+        st.bg.copy_(bgs[k])
+
+    def eval_all():
+        ev = FitState.from_params(st.params, st.sh_degree, cams, bg=zeros)
+        ev.target_rgb.copy_(t_rgb.reshape(-1))
+        ev.target_alpha.copy_(t_alpha.reshape(-1))
+        ev.forward()
+        ev.loss()
+        out = (float(ev.loss_out.item()), refine.psnr(ev))
+        del ev
+        torch.cuda.empty_cache()
+        return out
+
+    loss0, psnr0 = eval_all()
+    load(0)
+    st.capture()
+    for k in range(warmup):
+        load(k)
+        st.replay()
+    torch.cuda.synchronize()
+    curve = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for k in range(iters):
+        load(warmup + k)
+        st.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / iters
+    if st.check_status() != 0:
+        raise RuntimeError("device status set in the CT periphery leg")
+    loss1, psnr1 = eval_all()
+    # one iteration's stages on the last view
+    stage_ms = time_stages(st, reps=10)
+    blended = st.blended_pairs()
+    n_inst = int(st.n_instances.item())
+    n_vis = int((st.proj.tiles > 0).sum().item())
+    tile_passes = max(1, (int(np.ceil(np.log2(max(2, st.T)))) + 7) // 8)
+    sb = stage_bytes(st, n_inst, n_vis, tile_passes)
+    peaks = measured_peaks()
+    out = {"workload": "CT periphery: 200k Gaussians SH3 from a 256^3 CT volume, 24 orbit views 1024^2, "
+                       "one view per iteration",
+           "iters_per_s": 1000.0 / ms, "ms_per_iter": ms, "iterations": iters,
+           "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()}, "pairs_per_iter": n_inst,
+           "blended_pairs": blended,
+           "hbm_frac": {k: round(sb[k] / (stage_ms[k] * 1e-3) / 1e9 / peaks["hbm_gbs"], 4) for k in sb},
+           "alu_tflops": {k: round(blended * f / (stage_ms[k] * 1e-3) / 1e12, 3) for k, f in FLOP_PER_BLEND.items()},
+           "all_24_views_before": {"loss": loss0, "psnr_db": psnr0},
+           "all_24_views_after": {"loss": loss1, "psnr_db": psnr1}}
+    del st, t_rgb, t_alpha, tables
     torch.cuda.empty_cache()
     return out
 
@@ -502,6 +730,7 @@ def regeneration_leg(iters: int = 700, simplify_at: int = 95, keep: int = 10_000
     tgt.forward()
     ev = FitState(init, cams, bg=zeros)
     ev.target_rgb.copy_(tgt.rgb)
+    ev.target_alpha.copy_(tgt.alpha)
     p0 = refine.psnr(ev)
     del ev
     st, info = refine.regenerate(init, cams, tgt.rgb, tgt.alpha, scenes.backgrounds(n_views, 4, n_steps=iters),
@@ -554,7 +783,8 @@ def main() -> None:
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision (16-bit features) leg")
     ap.add_argument("--no-tune", action="store_true", help="default tile 16 / batch 128 instead of the autotuner")
     ap.add_argument("--no-regen", action="store_true", help="skip the abbreviated-regeneration leg")
-    ap.add_argument("--refine-iters", type=int, default=300,
+    ap.add_argument("--no-ct", action="store_true", help="skip the CT periphery (24 x 1024^2 views) leg")
+    ap.add_argument("--refine-iters", type=int, default=1000,
                     help="iterations of the continuous-refinement leg (0 skips it)")
     ap.add_argument("--gaussians", type=int, default=1_000_000,
                     help="smaller sets are for profiling captures only; the metric is quoted at 1M")
@@ -644,7 +874,10 @@ def main() -> None:
     sb = stage_bytes(st, n_inst, n_vis, tile_passes)
     peaks = measured_peaks()
     hbm_stages = {k: sb[k] / (stage_ms[k] * 1e-3) / 1e9 for k in sb}
-    alu_peak = alu_peak_tflops(peaks["sm_max_mhz"])
+    alu = measure_alu_peaks()
+    # the FP32 denominator: the measured packed-FMA rate if higher (the
+    # compositing kernels issue packed two-lane FMAs), else the scalar one
+    alu_peak = max(alu["fma_tflops"], alu["fma2_tflops"])
     alu_stages = {k: blended * f / (stage_ms[k] * 1e-3) / 1e12 for k, f in FLOP_PER_BLEND.items()}
     dominant = max(stage_ms, key=stage_ms.get)
     # project 1; bin_sort: reduce, scan, compact, 4 depth passes, sorted
@@ -661,7 +894,7 @@ def main() -> None:
     elif dominant in alu_stages:
         roof = {"kernel": dominant, "bound": "alu", "achieved": alu_stages[dominant], "peak": alu_peak,
                 "unit": "TFLOP/s", "frac": alu_stages[dominant] / alu_peak, "traffic": traffic,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                "peak_source": "measured: " + alu["how"],
                 "work": f"{blended} blended pairs x {FLOP_PER_BLEND[dominant]} FLOP"}
     else:
         roof = {"kernel": dominant, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
@@ -680,7 +913,8 @@ def main() -> None:
                       {"cached": tuned["cached"], "candidates": tuned["candidates"]}},
            "gpu_launches": launches_per_step * args.steps,
            "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()}, "blended_pairs": blended,
-           "roofline": roof, "clocks": clk}
+           "roofline": roof, "clocks": clk,
+           "alu_peaks": dict(alu, derived_fp32_tflops=alu_peak_tflops(peaks["sm_max_mhz"]))}
 
     plain = None
     if rank == 0 and not args.no_plain:
@@ -701,9 +935,14 @@ def main() -> None:
     if rank == 0:
         out["reprojection_768"] = reprojection_rate()
     if rank == 0 and args.refine_iters > 0:
-        out["continuous_refinement"] = refinement_leg(sc, st, args.refine_iters)
+        cr = refinement_leg(sc, st, args.refine_iters)
+        cr["vs_batched_fp32"] = cr["iters_per_s"] / (value / world)
+        out["continuous_refinement"] = cr
     if rank == 0 and not args.no_regen:
         out["regeneration"] = regeneration_leg()
+    if rank == 0 and not args.no_ct:
+        out["ct_periphery_1024"] = ct_periphery_leg()
+        out["differentiation_fit_512"] = differentiation_fit_leg()
     if rank == 0:
         host_rgb = st.target_rgb.cpu().pin_memory()
         host_alpha = st.target_alpha.cpu().pin_memory()
@@ -712,6 +951,7 @@ def main() -> None:
         out["e2e"]["value"] *= world
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = oracle_sample(sc)
+        out["cpu_baseline"]["threads_compare"] = oracle_threads_compare()
     if rank == 0:
         print(json.dumps(out))
     if world > 1:

@@ -178,7 +178,10 @@ int gsfit_view_is_novel(const float* pos_new, const float* dir_new, const float*
                         int32_t n_set, float delta_pos, float cos_theta);
 
 /*
- * gsfit_project -- EWA projection with SH colour (3DGS forward projection).
+ * gsfit_project -- EWA projection with SH colour: the first stage of
+ * rendering the peripheral 3DGS model that Section 4.2 fits to the
+ * path-traced views (alpha training, randomised backgrounds); the splatting
+ * conventions are those of 3DGS, which the paper inherits.
  *   Per (view v, Gaussian i): s = exp(log_scale), q normalised, opacity =
  *   sigmoid(logit), Sigma = R(q) diag(s^2) R(q)^T; t = R_v mu + t_v; culled
  *   if t_z <= near. Sigma' = J R_v Sigma R_v^T J^T + 0.3 I with the EWA
@@ -210,7 +213,9 @@ int gsfit_project(const gsfit_gaussians* g, const gsfit_camera* cams, int32_t n_
 size_t gsfit_bin_sort_workspace_size(int64_t n_records, int64_t capacity, int32_t total_tiles);
 
 /*
- * gsfit_bin_sort -- tile binning of the projected records (3DGS).
+ * gsfit_bin_sort -- tile binning of the projected records: the depth-ordered
+ * per-tile lists from which the peripheral 3DGS model of Section 4.2 is
+ * composited (3DGS's tile rasteriser ordering).
  *   Exclusive scan of tiles[]; for every record with tiles > 0 and every
  *   tile (row-major) of its rectangle, one pair key = (global tile id << 32)
  *   | float32 bits of depth, value = Gaussian index i; the pairs sorted by
@@ -346,7 +351,10 @@ int gsfit_loss_noalloc(const gsfit_camera* cams, int32_t n_views, const float* r
                        float* dL_drgb, float* dL_dalpha, float* loss_out, cudaStream_t stream);
 
 /*
- * gsfit_render_bwd -- adjoint of gsfit_render_fwd and gsfit_project.
+ * gsfit_render_bwd -- adjoint of gsfit_render_fwd and gsfit_project: the
+ * gradient step of fitting the peripheral 3DGS model to the training views
+ * (Section 4.2: alpha training against the views' alpha, randomised
+ * backgrounds).
  *   Per pixel, back to front from n_contrib - 1, recovering T_i = T_{i+1} /
  *   (1 - alpha_i) from T_final (no per-(pixel, Gaussian) state is stored):
  *   dC/dc_i = alpha_i T_i; dC/dalpha_i = T_i c_i - (S_i + T_N bg) / (1 -
