@@ -20,8 +20,9 @@
 //      stores coalesce. A pass whose digit is the same for every key (the
 //      histogram has one bucket holding them all, as the top depth byte is
 //      when all depths share a binary exponent) is the identity permutation:
-//      its CTAs copy their partitions instead. Records are now in (depth,
-//      record index) order.
+//      its CTAs exit at once and the records stay in their buffer (each later
+//      kernel derives the buffer from the histograms). Records are now in
+//      (depth, record index) order.
 //   4. reduce_sorted_kernel / scan_blocks_kernel / emit_kernel: pair offsets
 //      in that order (per block of records, and per 128-record segment within
 //      it), then the pairs (tile id << 32 | depth, Gaussian index), with the
@@ -70,7 +71,18 @@ struct SortCtl {
     uint32_t hist[kMaxPasses][kRadix];  // depth passes, then tile passes
     uint32_t order_hist[32];  // tiles per log2(list length + 1) bucket
     uint32_t order_fill[32];
+    uint32_t depth_buf;  // buffer of the depth-sorted records (set by reduce_sorted_kernel)
 };
+
+// The buffer (0 or 1) holding the depth-sorted records after depth passes
+// [0, p) (blockDim == kRadix, called by the whole block): a pass whose digit
+// is the same for all n keys is the identity permutation and is skipped; every
+// other pass moves the records to the other buffer.
+__device__ __forceinline__ int depth_buffer(const SortCtl* ctl, int p, uint32_t n) {
+    int b = 0;
+    for (int q = 0; q < p; ++q) b ^= __syncthreads_or(ctl->hist[q][threadIdx.x] == n) ? 0 : 1;
+    return b;
+}
 
 // Block-wide exclusive scan of one value per thread (blockDim == 256).
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t* s_warp, uint32_t& total) {
@@ -259,12 +271,16 @@ constexpr int kEmitBlocksPerSm = 5;
 // total, scanned over blocks afterwards) and the exclusive offset of each
 // kEmitSeg-record segment within its block. Records are loaded block-striped,
 // so row j of the load holds segments 2j (warps 0-3) and 2j + 1 (warps 4-7).
-__global__ void __launch_bounds__(kScanThreads) reduce_sorted_kernel(const unsigned long long* __restrict__ rkeys,
+__global__ void __launch_bounds__(kScanThreads) reduce_sorted_kernel(const unsigned long long* __restrict__ rkeys0,
+                                                                     const unsigned long long* __restrict__ rkeys1,
                                                                      const SortCtl* __restrict__ ctl,
                                                                      uint32_t* __restrict__ sums,
                                                                      uint32_t* __restrict__ seg_off) {
     __shared__ uint32_t s_part[kScanItems][kScanThreads / 32];
     const uint32_t n = ctl->n_rec;
+    const int buf = depth_buffer(ctl, kDepthPasses, n);
+    const unsigned long long* rkeys = buf ? rkeys1 : rkeys0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) const_cast<SortCtl*>(ctl)->depth_buf = (uint32_t)buf;
     const long long base = (long long)blockIdx.x * kScanChunk;
     if (base >= n) {  // block-uniform: an empty block's sum is still scanned
         if (threadIdx.x == 0) sums[blockIdx.x] = 0u;
@@ -305,7 +321,8 @@ __global__ void __launch_bounds__(kScanThreads) reduce_sorted_kernel(const unsig
 // other lanes. The next row's record gather is issued before the current row
 // is dealt out.
 __global__ void __launch_bounds__(kScanThreads, kEmitBlocksPerSm) emit_kernel(
-    const unsigned long long* __restrict__ rkeys, const uint32_t* __restrict__ rvals,
+    const unsigned long long* __restrict__ rkeys0, const uint32_t* __restrict__ rvals0,
+    const unsigned long long* __restrict__ rkeys1, const uint32_t* __restrict__ rvals1,
     const float4* __restrict__ xyd, int n, int n_views, const gsfit_camera* __restrict__ cams_g,
     const uint32_t* __restrict__ sums, const uint32_t* __restrict__ seg_off, SortCtl* __restrict__ ctl,
     int n_tile_passes, unsigned long long* __restrict__ keys, uint32_t* __restrict__ vals) {
@@ -315,6 +332,9 @@ __global__ void __launch_bounds__(kScanThreads, kEmitBlocksPerSm) emit_kernel(
     const uint32_t n_recs = ctl->n_rec;
     const long long n_segs = ((long long)n_recs + kEmitSeg - 1) / kEmitSeg;
     const long long warps = (long long)gridDim.x * (kScanThreads / 32);
+    const bool second = ctl->depth_buf != 0u;
+    const unsigned long long* rkeys = second ? rkeys1 : rkeys0;
+    const uint32_t* rvals = second ? rvals1 : rvals0;
     if ((long long)blockIdx.x * (kScanThreads / 32) >= n_segs) return;  // block-uniform
     load_cameras(cams, cams_g, n_views);
     for (int k = threadIdx.x; k < n_tile_passes * kRadix; k += blockDim.x) (&s_hist[0][0])[k] = 0u;
@@ -456,14 +476,12 @@ struct OnesweepSmem {
 
 // One stable counting pass over the 8-bit digit at bit `shift` of *n_ptr keys;
 // `pass` indexes the histogram and partition counter of this launch.
-__global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(const unsigned long long* __restrict__ keys_in,
-                                                                const uint32_t* __restrict__ vals_in,
-                                                                unsigned long long* __restrict__ keys_out,
-                                                                uint32_t* __restrict__ vals_out,
+__global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(unsigned long long* keys_a, uint32_t* vals_a,
+                                                                unsigned long long* keys_b, uint32_t* vals_b,
                                                                 SortCtl* __restrict__ ctl, int pass, int shift,
                                                                 const uint32_t* __restrict__ n_ptr,
                                                                 uint32_t* __restrict__ lookback,
-                                                                int32_t* __restrict__ status) {
+                                                                int32_t* __restrict__ status, int depth_pass) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     OnesweepSmem& S = *reinterpret_cast<OnesweepSmem*>(smem_raw);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -474,6 +492,17 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(const unsigne
     for (int k = threadIdx.x; k < kSortWarps * (kRadix + 1); k += kSortThreads) (&S.warp_hist[0][0])[k] = 0u;
     // one digit value holding every key: the stable pass is the identity permutation
     const bool identity = __syncthreads_or(hist_d == n) != 0;
+    // input a, output b; a depth pass reads where the last pass that moved the
+    // records left them (buffer a or b), and an identity depth pass leaves them there
+    bool swap = false;
+    if (depth_pass) {
+        if (identity) return;
+        swap = depth_buffer(ctl, pass, n) != 0;
+    }
+    const unsigned long long* __restrict__ keys_in = swap ? keys_b : keys_a;
+    const uint32_t* __restrict__ vals_in = swap ? vals_b : vals_a;
+    unsigned long long* __restrict__ keys_out = swap ? keys_a : keys_b;
+    uint32_t* __restrict__ vals_out = swap ? vals_a : vals_b;
     const uint32_t part = S.part;
     if (part >= n_parts) return;
     const uint32_t base = part * kPart;
@@ -767,16 +796,17 @@ extern "C" int gsfit_bin_sort(const gsfit_proj* proj, const gsfit_camera* cams, 
                                                             n_rec, rec_sums, ctl, rk[0], rv[0], lookback,
                                                             L.lookback_words, ranges, 2ll * total_tiles);
     GSFIT_LAUNCH_CHECK();
-    // depth passes over the records (an even number: the result is back in buffer 0)
+    // depth passes over the records, between buffers 0 and 1 (which one holds the
+    // result depends on how many passes were identities; the kernels after them check)
     uint32_t* lb = lookback;
     for (int p = 0; p < kDepthPasses; ++p) {
-        onesweep_kernel<<<(unsigned)L.max_rec_parts, kSortThreads, smem, stream>>>(
-            rk[p & 1], rv[p & 1], rk[(p + 1) & 1], rv[(p + 1) & 1], ctl, p, 8 * p, &ctl->n_rec, lb, status);
+        onesweep_kernel<<<(unsigned)L.max_rec_parts, kSortThreads, smem, stream>>>(rk[0], rv[0], rk[1], rv[1], ctl, p,
+                                                                                    8 * p, &ctl->n_rec, lb, status, 1);
         GSFIT_LAUNCH_CHECK();
         lb += (size_t)L.max_rec_parts * kRadix;
     }
     uint32_t* seg_off = reinterpret_cast<uint32_t*>(base + L.seg_off);
-    reduce_sorted_kernel<<<L.n_blocks, kScanThreads, 0, stream>>>(rk[0], ctl, sorted_sums, seg_off);
+    reduce_sorted_kernel<<<L.n_blocks, kScanThreads, 0, stream>>>(rk[0], rk[1], ctl, sorted_sums, seg_off);
     GSFIT_LAUNCH_CHECK();
     scan_blocks_kernel<<<1, 1024, 0, stream>>>(sorted_sums, L.n_blocks);
     GSFIT_LAUNCH_CHECK();
@@ -791,13 +821,14 @@ extern "C" int gsfit_bin_sort(const gsfit_proj* proj, const gsfit_camera* cams, 
     GSFIT_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const long long segs = (long long)L.n_blocks * kSegsPerChunk;
     emit_kernel<<<(unsigned)std::min<long long>((long long)kEmitBlocksPerSm * sms, (segs + 7) / 8), kScanThreads,
-                  sizeof(gsfit_camera) * n_views, stream>>>(rk[0], rv[0], reinterpret_cast<const float4*>(proj->xyd),
+                  sizeof(gsfit_camera) * n_views, stream>>>(rk[0], rv[0], rk[1], rv[1],
+                                                            reinterpret_cast<const float4*>(proj->xyd),
                                                             n, n_views, cams, sorted_sums, seg_off, ctl,
                                                             L.tile_passes, k_cur, v_cur);
     GSFIT_LAUNCH_CHECK();
     for (int q = 0; q < L.tile_passes; ++q) {
         onesweep_kernel<<<(unsigned)L.max_parts, kSortThreads, smem, stream>>>(
-            k_cur, v_cur, k_nxt, v_nxt, ctl, kDepthPasses + q, 32 + 8 * q, &ctl->n_sort, lb, status);
+            k_cur, v_cur, k_nxt, v_nxt, ctl, kDepthPasses + q, 32 + 8 * q, &ctl->n_sort, lb, status, 0);
         GSFIT_LAUNCH_CHECK();
         lb += (size_t)L.max_parts * kRadix;
         std::swap(k_cur, k_nxt);
