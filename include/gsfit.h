@@ -70,6 +70,7 @@ extern "C" {
 #define GSFIT_ERR_CAPACITY (-2)  /* more (Gaussian, tile) pairs than capacity  */
 #define GSFIT_ERR_CUDA (-3)      /* a CUDA launch or runtime call failed        */
 #define GSFIT_ERR_TIMEOUT (-4)   /* a bounded device-side wait ran out          */
+#define GSFIT_ERR_NONFINITE (-5) /* a non-finite parameter gradient was produced */
 
 /*
  * One pinhole camera: 128 bytes, identical on host and device.
@@ -361,7 +362,8 @@ int gsfit_loss_noalloc(const gsfit_camera* cams, int32_t n_views, const float* r
  *   alpha_i) with S_i the colour composited behind i; dA/dalpha_i = T_N /
  *   (1 - alpha_i); dalpha/d(opacity, power) = 0 where the 0.99 clamp is
  *   active. Per-(view, Gaussian) gradients of (u, v, conic, opacity, rgb) are
- *   reduced per warp and accumulated with atomics in grad2d, then chained
+ *   accumulated with atomics in grad2d (per lane where few lanes of a warp
+ *   blend the Gaussian, else reduced over the warp first), then chained
  *   through the projection (zero derivative where the frustum guard or the
  *   colour clamp is active) and summed over views into `grads`.
  * Arguments: g: the Gaussians that were projected; dL_drgb/dL_dalpha in the
@@ -370,8 +372,11 @@ int gsfit_loss_noalloc(const gsfit_camera* cams, int32_t n_views, const float* r
  *   call leaves it zero again. grads: device, same layout as the parameters,
  *   fully overwritten (no zeroing needed). opts, status: as for
  *   gsfit_render_fwd.
- * Errors: GSFIT_ERR_INVALID_ARG, GSFIT_ERR_CUDA; GSFIT_ERR_TIMEOUT on the
- *   device, through status.
+ * Errors: GSFIT_ERR_INVALID_ARG, GSFIT_ERR_CUDA; on the device, through
+ *   status: GSFIT_ERR_TIMEOUT, and GSFIT_ERR_NONFINITE when a parameter
+ *   gradient written to `grads` is not finite (a non-finite image,
+ *   cotangent or 2D gradient upstream; the gradients are still written, and
+ *   an earlier error in status is kept).
  */
 int gsfit_render_bwd(const gsfit_gaussians* g, const gsfit_proj* proj, const gsfit_camera* cams,
                      int32_t n_views, int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges,

@@ -13,6 +13,7 @@ extern "C" const char* gsfit_status_string(int code) {
         case GSFIT_ERR_CAPACITY: return "instance capacity exceeded";
         case GSFIT_ERR_CUDA: return "CUDA error";
         case GSFIT_ERR_TIMEOUT: return "bounded device wait ran out";
+        case GSFIT_ERR_NONFINITE: return "non-finite gradient";
         default: return "unknown status";
     }
 }

@@ -410,11 +410,15 @@ __device__ __forceinline__ RecIn load_rec(const float4* __restrict__ grad2d, con
     return x;
 }
 
+__device__ __forceinline__ bool finite4(float4 q) {
+    return isfinite(q.x) && isfinite(q.y) && isfinite(q.z) && isfinite(q.w);
+}
+
 template <int DEG, int FT>
 __global__ void __launch_bounds__(kProjBwdThreads, 2) project_bwd_kernel(
     const float4* __restrict__ P, const uint2* __restrict__ F, int n, const gsfit_camera* __restrict__ cams_g,
     int n_views, const float4* __restrict__ xyd, const float4* __restrict__ conic, const float4* __restrict__ rgbm,
-    float4* __restrict__ grad2d, float4* __restrict__ G) {
+    float4* __restrict__ grad2d, float4* __restrict__ G, int32_t* __restrict__ status) {
     // dynamic shared memory: the camera table, then 3K SH-gradient accumulators
     // per thread (kept out of registers)
     extern __shared__ __align__(16) unsigned char smem_pb[];
@@ -434,6 +438,7 @@ __global__ void __launch_bounds__(kProjBwdThreads, 2) project_bwd_kernel(
     float dSig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // xx xy xz yy yz zz (symmetric, dL/dSigma_ij)
     float dop = 0.f;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    bool binned = false;  // some view binned this Gaussian
 
     for (int v0 = 0; v0 < n_views; v0 += 32) {
         // visibility of up to 32 views first: independent loads, one latency
@@ -443,6 +448,7 @@ __global__ void __launch_bounds__(kProjBwdThreads, 2) project_bwd_kernel(
         for (int k = 0; k < vn; ++k)
             if (__ldg(&xyd[(size_t)(v0 + k) * n + i].w) != 0.0f) vis |= 1u << k;
         if (!vis) continue;
+        binned = true;
         int v = v0 + __ffs(vis) - 1;
         vis &= vis - 1;
         RecIn cur = load_rec(grad2d, conic, rgbm, (size_t)v * n + i);
@@ -479,6 +485,15 @@ __global__ void __launch_bounds__(kProjBwdThreads, 2) project_bwd_kernel(
             cur = nxt;
         }
     }
+    if (!binned) {
+        // a Gaussian no view binned contributes to no pixel: its gradient is
+        // zero (written as such, also where its parameters are not finite and
+        // the chain below would give 0 x NaN)
+        constexpr int NPL = 3 + (3 * K + 3) / 4;
+#pragma unroll
+        for (int p = 0; p < NPL; ++p) G[(size_t)p * n + i] = zero;
+        return;
+    }
     const float opacity = 1.0f / (1.0f + expf(-g.logit));
     const float dlogit = dop * opacity * (1.f - opacity);
 
@@ -509,10 +524,14 @@ __global__ void __launch_bounds__(kProjBwdThreads, 2) project_bwd_kernel(
     const float qd = w * dq[0] + x * dq[1] + y * dq[2] + z * dq[3];
     const float iq = 1.0f / g.qn;
 
-    G[i] = make_float4(dmean[0], dmean[1], dmean[2], dlogit);
-    G[(size_t)n + i] = make_float4((dq[0] - w * qd) * iq, (dq[1] - x * qd) * iq, (dq[2] - y * qd) * iq,
-                                   (dq[3] - z * qd) * iq);
-    G[2 * (size_t)n + i] = make_float4(dls[0], dls[1], dls[2], 0.f);
+    const float4 g0 = make_float4(dmean[0], dmean[1], dmean[2], dlogit);
+    const float4 g1 = make_float4((dq[0] - w * qd) * iq, (dq[1] - x * qd) * iq, (dq[2] - y * qd) * iq,
+                                  (dq[3] - z * qd) * iq);
+    const float4 g2 = make_float4(dls[0], dls[1], dls[2], 0.f);
+    G[i] = g0;
+    G[(size_t)n + i] = g1;
+    G[2 * (size_t)n + i] = g2;
+    bool finite = finite4(g0) && finite4(g1) && finite4(g2);
     constexpr int K3 = 3 * K;
     constexpr int NP = (K3 + 3) / 4;
 #pragma unroll
@@ -523,7 +542,12 @@ __global__ void __launch_bounds__(kProjBwdThreads, 2) project_bwd_kernel(
         q.z = (4 * p + 2 < K3) ? dsh_acc(s_dsh, 4 * p + 2) : 0.f;
         q.w = (4 * p + 3 < K3) ? dsh_acc(s_dsh, 4 * p + 3) : 0.f;
         G[(size_t)(3 + p) * n + i] = q;
+        finite = finite && finite4(q);
     }
+    // a non-finite gradient (from a non-finite image, cotangent or 2D
+    // gradient upstream) is reported, not hidden: the first such Gaussian sets
+    // the status word unless an earlier error already has
+    if (!finite && status) atomicCAS(status, GSFIT_OK, GSFIT_ERR_NONFINITE);
 }
 
 template <int DEG, int FT>
@@ -541,7 +565,7 @@ int launch_project(const gsfit_gaussians* g, const gsfit_camera* cams, int V, gs
 
 template <int DEG, int FT>
 int launch_project_bwd(const gsfit_gaussians* g, const gsfit_proj* proj, const gsfit_camera* cams, int V,
-                       float* grad2d, float* grads, cudaStream_t s) {
+                       float* grad2d, float* grads, int32_t* status, cudaStream_t s) {
     const int threads = kProjBwdThreads;
     const int blocks = (g->n + threads - 1) / threads;
     const float4* P = reinterpret_cast<const float4*>(g->params);
@@ -554,7 +578,7 @@ int launch_project_bwd(const gsfit_gaussians* g, const gsfit_proj* proj, const g
     project_bwd_kernel<DEG, FT><<<blocks, threads, smem, s>>>(
         P, F, g->n, cams, V, reinterpret_cast<const float4*>(proj->xyd), reinterpret_cast<const float4*>(proj->conic),
         reinterpret_cast<const float4*>(proj->rgb), reinterpret_cast<float4*>(grad2d),
-        reinterpret_cast<float4*>(grads));
+        reinterpret_cast<float4*>(grads), status);
     GSFIT_LAUNCH_CHECK();
     return GSFIT_OK;
 }
@@ -571,13 +595,13 @@ int project_ft(const gsfit_gaussians* g, const gsfit_camera* cams, int V, gsfit_
 
 template <int DEG>
 int project_bwd_ft(const gsfit_gaussians* g, const gsfit_proj* proj, const gsfit_camera* cams, int V, float* grad2d,
-                   float* grads, cudaStream_t s) {
+                   float* grads, int32_t* status, cudaStream_t s) {
     switch (g->feature_dtype) {
         case GSFIT_FEATURES_F16:
-            return launch_project_bwd<DEG, GSFIT_FEATURES_F16>(g, proj, cams, V, grad2d, grads, s);
+            return launch_project_bwd<DEG, GSFIT_FEATURES_F16>(g, proj, cams, V, grad2d, grads, status, s);
         case GSFIT_FEATURES_BF16:
-            return launch_project_bwd<DEG, GSFIT_FEATURES_BF16>(g, proj, cams, V, grad2d, grads, s);
-        default: return launch_project_bwd<DEG, GSFIT_FEATURES_F32>(g, proj, cams, V, grad2d, grads, s);
+            return launch_project_bwd<DEG, GSFIT_FEATURES_BF16>(g, proj, cams, V, grad2d, grads, status, s);
+        default: return launch_project_bwd<DEG, GSFIT_FEATURES_F32>(g, proj, cams, V, grad2d, grads, status, s);
     }
 }
 
@@ -598,12 +622,12 @@ bool valid_proj(const gsfit_proj* p) {
 }
 
 int project_bwd(const gsfit_gaussians* g, const gsfit_proj* proj, const gsfit_camera* cams, int V, float* grad2d,
-                float* grads, cudaStream_t s) {
+                float* grads, int32_t* status, cudaStream_t s) {
     switch (g->sh_degree) {
-        case 0: return project_bwd_ft<0>(g, proj, cams, V, grad2d, grads, s);
-        case 1: return project_bwd_ft<1>(g, proj, cams, V, grad2d, grads, s);
-        case 2: return project_bwd_ft<2>(g, proj, cams, V, grad2d, grads, s);
-        default: return project_bwd_ft<3>(g, proj, cams, V, grad2d, grads, s);
+        case 0: return project_bwd_ft<0>(g, proj, cams, V, grad2d, grads, status, s);
+        case 1: return project_bwd_ft<1>(g, proj, cams, V, grad2d, grads, status, s);
+        case 2: return project_bwd_ft<2>(g, proj, cams, V, grad2d, grads, status, s);
+        default: return project_bwd_ft<3>(g, proj, cams, V, grad2d, grads, status, s);
     }
 }
 

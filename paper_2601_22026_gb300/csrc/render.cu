@@ -766,7 +766,7 @@ __global__ void __launch_bounds__(TILE * TILE) render_count_kernel(
 bool valid_proj(const gsfit_proj* p);
 bool valid_gaussians(const gsfit_gaussians* g);
 int project_bwd(const gsfit_gaussians* g, const gsfit_proj* proj, const gsfit_camera* cams, int V, float* grad2d,
-                float* grads, cudaStream_t s);
+                float* grads, int32_t* status, cudaStream_t s);
 
 }  // namespace gsfit
 
@@ -965,12 +965,18 @@ extern "C" int gsfit_blend_bwd(const gsfit_proj* proj, const gsfit_camera* cams,
                    c, total_tiles, stream);
 }
 
+namespace {
+bool project_bwd_ok(const gsfit_gaussians* g, const gsfit_proj* proj, const gsfit_camera* cams, int n_views,
+                    const float* grad2d, const float* grads) {
+    return valid_gaussians(g) && valid_proj(proj) && cams && n_views >= 1 && n_views <= GSFIT_MAX_VIEWS && grad2d &&
+           grads && (reinterpret_cast<uintptr_t>(grad2d) % 16) == 0 && (reinterpret_cast<uintptr_t>(grads) % 16) == 0;
+}
+}  // namespace
+
 extern "C" int gsfit_project_bwd(const gsfit_gaussians* g, const gsfit_proj* proj, const gsfit_camera* cams,
                                  int32_t n_views, float* grad2d, float* grads, cudaStream_t stream) {
-    if (!valid_gaussians(g) || !valid_proj(proj) || !cams || n_views < 1 || n_views > GSFIT_MAX_VIEWS || !grad2d ||
-        !grads || (reinterpret_cast<uintptr_t>(grad2d) % 16) != 0 || (reinterpret_cast<uintptr_t>(grads) % 16) != 0)
-        return GSFIT_ERR_INVALID_ARG;
-    return project_bwd(g, proj, cams, n_views, grad2d, grads, stream);
+    if (!project_bwd_ok(g, proj, cams, n_views, grad2d, grads)) return GSFIT_ERR_INVALID_ARG;
+    return project_bwd(g, proj, cams, n_views, grad2d, grads, nullptr, stream);
 }
 
 extern "C" int gsfit_render_bwd(const gsfit_gaussians* g, const gsfit_proj* proj, const gsfit_camera* cams,
@@ -978,11 +984,11 @@ extern "C" int gsfit_render_bwd(const gsfit_gaussians* g, const gsfit_proj* proj
                                 const uint32_t* tile_order, const float* bg, const float* T_final,
                                 const uint32_t* n_contrib, const float* dL_drgb, const float* dL_dalpha, float* grad2d,
                                 float* grads, const gsfit_render_opts* opts, int32_t* status, cudaStream_t stream) {
-    if (!valid_gaussians(g)) return GSFIT_ERR_INVALID_ARG;
+    if (!valid_gaussians(g) || !project_bwd_ok(g, proj, cams, n_views, grad2d, grads)) return GSFIT_ERR_INVALID_ARG;
     const int rc = gsfit_blend_bwd(proj, cams, n_views, g->n, total_tiles, vals, ranges, tile_order, bg, T_final,
                                    n_contrib, dL_drgb, dL_dalpha, grad2d, opts, status, stream);
     if (rc != GSFIT_OK) return rc;
-    return gsfit_project_bwd(g, proj, cams, n_views, grad2d, grads, stream);
+    return project_bwd(g, proj, cams, n_views, grad2d, grads, status, stream);
 }
 
 extern "C" int gsfit_render_count(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_views, int32_t n,

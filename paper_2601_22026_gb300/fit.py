@@ -27,6 +27,46 @@ def boosted_lr(scale: float = 1.5) -> dict:
     return lr
 
 
+class StageMarks:
+    """Timing events that a captured CUDA graph records as event-record
+    nodes, so that every replay timestamps the boundaries between its stages
+    (cudaEventRecordExternal; through PyTorch where its events support it,
+    else through the CUDA runtime PyTorch and the library share)."""
+
+    def __init__(self, count: int):
+        try:
+            self._ev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(count)]
+            self._rt = None
+        except TypeError:
+            import ctypes
+            self._rt = ctypes.CDLL("libcudart.so.13")
+            self._rt.cudaEventRecordWithFlags.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint]
+            self._rt.cudaEventElapsedTime.argtypes = [ctypes.POINTER(ctypes.c_float), ctypes.c_void_p,
+                                                      ctypes.c_void_p]
+            self._ev = []
+            for _ in range(count):
+                e = ctypes.c_void_p()
+                if self._rt.cudaEventCreate(ctypes.byref(e)) != 0:
+                    raise RuntimeError("cudaEventCreate failed")
+                self._ev.append(e)
+
+    def record(self, k: int, stream=None) -> None:
+        s = torch.cuda.current_stream() if stream is None else stream
+        if self._rt is None:
+            self._ev[k].record(s)
+        elif self._rt.cudaEventRecordWithFlags(self._ev[k], s.cuda_stream, 1) != 0:  # 1: cudaEventRecordExternal
+            raise RuntimeError("cudaEventRecordWithFlags failed")
+
+    def elapsed(self, a: int, b: int) -> float:
+        if self._rt is None:
+            return self._ev[a].elapsed_time(self._ev[b])
+        import ctypes
+        ms = ctypes.c_float()
+        if self._rt.cudaEventElapsedTime(ctypes.byref(ms), self._ev[a], self._ev[b]) != 0:
+            raise RuntimeError("cudaEventElapsedTime failed")
+        return float(ms.value)
+
+
 class FitState:
     """All device buffers of the fit step for one scene and one view batch."""
 
@@ -72,6 +112,7 @@ class FitState:
         self.capacity = 0
         self.ensure_capacity(capacity)
         self.graph = None
+        self.marks = None
 
     @classmethod
     def from_params(cls, params, sh_degree: int, cams: dict, **kw):
@@ -265,29 +306,50 @@ class FitState:
         self.bin_sort(stream)
         self.render_fwd(stream)
 
-    def step(self, stream=None):
-        """One fit iteration (no host synchronisation)."""
-        self.forward(stream)
-        self.loss(stream)
-        self.render_bwd(stream)
-        self.adam(stream)
+    def step(self, stream=None, marks: "StageMarks | None" = None):
+        """One fit iteration (no host synchronisation). marks: timing events
+        recorded before the first stage and after each of TIMED_STAGES (the
+        adjoint as its two halves, the same kernels as render_bwd)."""
+        if marks is None:
+            self.forward(stream)
+            self.loss(stream)
+            self.render_bwd(stream)
+            self.adam(stream)
+            return
+        marks.record(0, stream)
+        for k, name in enumerate(self.TIMED_STAGES):
+            with torch.cuda.nvtx.range(name):
+                getattr(self, name)(stream)
+            marks.record(k + 1, stream)
 
     STAGES = ("project", "bin_sort", "render_fwd", "loss", "render_bwd", "adam")
+    TIMED_STAGES = ("project", "bin_sort", "render_fwd", "loss", "blend_bwd", "project_bwd", "adam")
 
     # -- graphs ---------------------------------------------------------
-    def capture(self, warmup: int = 1):
-        """Captures one iteration in a CUDA graph (replay with .replay())."""
+    def capture(self, warmup: int = 1, stage_marks: bool = False):
+        """Captures one iteration in a CUDA graph (replay with .replay()).
+        stage_marks: the graph also records timing events between the
+        stages (event-record nodes), read with stage_times() after a replay."""
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s):
             for _ in range(warmup):
                 self.step(s)
         torch.cuda.current_stream().wait_stream(s)
+        self.marks = StageMarks(len(self.TIMED_STAGES) + 1) if stage_marks else None
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
-            self.step()
+            self.step(marks=self.marks)
         self.graph = g
         return g
+
+    def stage_times(self) -> dict:
+        """Per-stage milliseconds of the last replay of a graph captured with
+        stage_marks (synchronises)."""
+        if self.marks is None:
+            raise RuntimeError("capture(stage_marks=True) first")
+        torch.cuda.synchronize()
+        return {name: self.marks.elapsed(k, k + 1) for k, name in enumerate(self.TIMED_STAGES)}
 
     def replay(self):
         if self.graph is None:

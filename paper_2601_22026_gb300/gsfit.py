@@ -20,6 +20,7 @@ GSFIT_ERR_INVALID_ARG = -1
 GSFIT_ERR_CAPACITY = -2
 GSFIT_ERR_CUDA = -3
 GSFIT_ERR_TIMEOUT = -4
+GSFIT_ERR_NONFINITE = -5
 GSFIT_TILE = 16
 GSFIT_MAX_VIEWS = 256
 

@@ -71,7 +71,8 @@ def test_timed_out_status_makes_later_compositing_skip_its_work():
 def test_non_finite_gaussians_are_culled(field):
     """A set with NaN Gaussians renders exactly like the same set without
     them (an invariance of the culling, GPU against GPU), and the step's
-    gradients stay finite."""
+    gradients stay finite: the culled Gaussians' gradients are zero (they
+    reach no pixel), so nothing non-finite is reported either."""
     from paper_2601_22026_gb300.fit import FitState
     from test_parity_gpu import _case
     gs, cams, bg = _case("sh3_uneven_views")
@@ -93,4 +94,35 @@ def test_non_finite_gaussians_are_culled(field):
     torch.cuda.synchronize()
     assert with_nan.check_status() == 0
     g = with_nan.gradients()
-    assert all(np.isfinite(np.asarray(v)[~bad]).all() for v in g.values())
+    assert all(np.isfinite(np.asarray(v)).all() for v in g.values())
+    assert all((np.asarray(v)[bad] == 0).all() for v in g.values())
+
+
+def test_non_finite_gradient_is_reported():
+    """A non-finite upstream gradient (a NaN in dL/dimage at one pixel, as a
+    corrupt target image would give) makes the parameter gradients of the
+    Gaussians blended there non-finite: the adjoint reports it through the
+    status word (GSFIT_ERR_NONFINITE) instead of handing it on silently; the
+    same call on finite inputs reports nothing, and the context stays usable."""
+    from paper_2601_22026_gb300 import gsfit as G
+    from paper_2601_22026_gb300.fit import FitState
+    from test_parity_gpu import _case
+    gs, cams, bg = _case("sh1_ragged")
+    st = FitState(gs, cams, bg=bg)
+    st.forward()
+    torch.cuda.synchronize()
+    P = st.P
+    nc = st.n_contrib.cpu().numpy()
+    pix = int(np.flatnonzero(nc > 0)[0])  # a pixel where some Gaussian blends
+    st.dL_drgb.copy_(torch.from_numpy(scenes.cotangents(3 * P, 901, 1e-3)))
+    st.dL_dalpha.copy_(torch.from_numpy(scenes.cotangents(P, 902, 1e-3)))
+    st.render_bwd()
+    torch.cuda.synchronize()
+    assert st.check_status() == 0
+    assert torch.isfinite(st.grads).all()
+    st.dL_drgb[pix] = float("nan")
+    st.render_bwd()
+    torch.cuda.synchronize()
+    assert st.check_status() == G.GSFIT_ERR_NONFINITE
+    assert not torch.isfinite(st.grads).all()
+    _small_step_works()
