@@ -470,6 +470,36 @@ def test_graph_replay_matches_eager():
     np.testing.assert_allclose(pa, pb, rtol=0, atol=1e-4)
 
 
+def test_graph_stage_marks_time_the_replayed_stages():
+    """An iteration captured with stage marks records timing events between
+    its stages inside the graph: every replay gives one positive time per
+    stage, and they add up to the replay's own duration (events around it on
+    the same stream); the marked graph computes what the plain one does."""
+    from paper_2601_22026_gb300.fit import FitState
+    sc = scenes.plain_single_view(0)
+    gs, cams, bg = sc["gaussians"], sc["cameras"], sc["bg"]
+    tgt = oracle.render(sc["target_gaussians"], cams, np.zeros((1, 3)))
+    a = _fit_state(gs, cams, bg, target_rgb=tgt["rgb"], target_alpha=tgt["alpha"])
+    b = _fit_state(gs, cams, bg, target_rgb=tgt["rgb"], target_alpha=tgt["alpha"])
+    a.capture(warmup=0)
+    b.capture(warmup=0, stage_marks=True)
+    for _ in range(3):
+        a.replay()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        t = b.stage_times()
+        assert list(t) == list(FitState.TIMED_STAGES)
+        assert all(v > 0 for v in t.values())
+        total = e0.elapsed_time(e1)
+        assert sum(t.values()) <= total * 1.05 + 0.05
+        assert sum(t.values()) >= total * 0.5
+    # the same iteration (float atomics in the adjoint: equal up to their summation order)
+    np.testing.assert_allclose(a.params.cpu().numpy(), b.params.cpu().numpy(), rtol=0, atol=1e-4)
+
+
 def test_empty_view_renders_background():
     gs = scenes.random_gaussians(500, 0, 5)
     cams = scenes.stack_cameras([scenes.make_camera((0, 0, 3), (0, 0, 6), 40, 24, fx=30.0)])  # looks away
