@@ -424,7 +424,7 @@ def mixed_precision_rate(sc, st, bg_table, warmup: int, steps: int, features: st
     import torch
     from paper_2601_22026_gb300.fit import FitState, boosted_lr
     mp = FitState(sc["gaussians"], sc["cameras"], bg=sc["bg"], lr=boosted_lr(), features=features,
-                  tile=st.tile, batch=int(st.opts.batch), exp_half2=exp_half2)
+                  tile=st.tile, batch=int(st.opts.batch), batch_bwd=int(st.opts.batch_bwd), exp_half2=exp_half2)
     mp.target_rgb.copy_(st.target_rgb)
     mp.target_alpha.copy_(st.target_alpha)
     mp.capture()
@@ -470,7 +470,8 @@ def refinement_leg(sc, st, iters: int, replace_every: int = 10, n_replace: int =
     cams = sc["cameras"]
     V = len(cams["width"])
     zeros = np.zeros((V, 3), np.float32)
-    tgt = FitState(sc["target_gaussians"], cams, bg=zeros, tile=st.tile, batch=int(st.opts.batch))
+    tgt = FitState(sc["target_gaussians"], cams, bg=zeros, tile=st.tile, batch=int(st.opts.batch),
+                   batch_bwd=int(st.opts.batch_bwd))
     tgt.forward()
     t_rgb, t_alpha = tgt.rgb.clone(), tgt.alpha.clone()
 
@@ -495,7 +496,7 @@ def refinement_leg(sc, st, iters: int, replace_every: int = 10, n_replace: int =
     n_blocks = max(1, iters // every)
     # refinement loop, mixed precision
     tr = with_targets(FitState(sc["gaussians"], cams, bg=zeros, lr=boosted_lr(), features=features, tile=st.tile,
-                               batch=int(st.opts.batch)), t_rgb, t_alpha)
+                               batch=int(st.opts.batch), batch_bwd=int(st.opts.batch_bwd)), t_rgb, t_alpha)
     ev = with_targets(refine.view_state(tr, cams, bg=zeros), t_rgb, t_alpha)
     stream = (scenes.foveal_crops(0, 1, 10_000 + k) for k in itertools.count())
     loop = refine.ContinuousRefinement(tr, tgt, cams, stream, scenes.backgrounds(V, 21, n_steps=iters),
@@ -815,16 +816,16 @@ def main() -> None:
         from paper_2601_22026_gb300 import tune
         from paper_2601_22026_gb300.fit import FitState, boosted_lr
 
-        def make_state(tile, batch, features="f32"):
+        def make_state(tile, batch, batch_bwd, features="f32"):
             s2 = FitState(sc["gaussians"], sc["cameras"], bg=sc["bg"], lr=boosted_lr(), tile=tile, batch=batch,
-                          features=features)
+                          batch_bwd=batch_bwd, features=features)
             s2.target_rgb.copy_(st.target_rgb)
             s2.target_alpha.copy_(st.target_alpha)
             return s2
 
         tuned = tune.autotune(make_state, tune.signature(st.n, st.sh_degree, sc["cameras"]))
-        if (tuned["tile"], tuned["batch"]) != (st.tile, st.opts.batch):
-            best = make_state(tuned["tile"], tuned["batch"])
+        if (tuned["tile"], tuned["batch"], tuned["batch_bwd"]) != (st.tile, st.opts.batch, st.opts.batch_bwd):
+            best = make_state(tuned["tile"], tuned["batch"], tuned["batch_bwd"])
             del st
             torch.cuda.empty_cache()
             st = best
@@ -918,7 +919,7 @@ def main() -> None:
            "config": {"workload": WORKLOAD, "gaussians": st.n, "views": V, "pixels": st.P, "tiles": st.T,
                       "pairs_per_step": n_inst, "parallelism": "replicas" if world > 1 else "single",
                       "l2": "working set > L2 (no flush)", "graph": True, "loss_last": loss_now,
-                      "tile": st.tile, "batch": int(st.opts.batch),
+                      "tile": st.tile, "batch": int(st.opts.batch), "batch_bwd": int(st.opts.batch_bwd),
                       "autotune": None if tuned is None else
                       {"cached": tuned["cached"], "candidates": tuned["candidates"]}},
            "gpu_launches": launches_per_step * args.steps,

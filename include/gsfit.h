@@ -60,7 +60,7 @@
 extern "C" {
 #endif
 
-#define GSFIT_ABI_VERSION 4
+#define GSFIT_ABI_VERSION 5
 #define GSFIT_MAX_VIEWS 256
 #define GSFIT_TILE 16
 
@@ -254,7 +254,12 @@ int gsfit_bin_sort(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_v
  *          (8 or 16); a launch whose cameras say otherwise writes
  *          GSFIT_ERR_INVALID_ARG to the status word and does nothing.
  *   batch: records per shared-memory slot of the producer ring (the number of
- *          Gaussians staged per batch): 64, 128 or 256.
+ *          Gaussians staged per batch) of the forward passes (gsfit_render_fwd,
+ *          gsfit_render_importance): 64, 128 or 256. The ring holds 8 slots of
+ *          64 entries or 4 slots of 128 or 256.
+ *   batch_bwd: the same for the blend adjoint (gsfit_blend_bwd,
+ *          gsfit_render_bwd): 64, 128 or 256. The results do not depend on
+ *          either depth beyond the order of the adjoint's atomic sums.
  *   exp_half2: 1 evaluates exp(power) of each (pixel, Gaussian) pair in
  *          packed half precision (f16x2: the forward pass takes two Gaussians
  *          of a pixel per instruction), the half2-exponent option of the
@@ -266,16 +271,15 @@ int gsfit_bin_sort(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_v
  *          moves by the half-precision rounding of power and exp (up to about
  *          2^-10 relative in the weight) and by the threshold decisions that
  *          rounding moves.
- *   reserved: must be 0.
- * A null pointer or a 0 field selects the default (tile 16, batch 128, float32
- * exponent).
+ * A null pointer or a 0 field selects the default (tile 16, batch 128,
+ * batch_bwd 64, float32 exponent).
  * gsfit_render_autotune measures the batch depths on a caller's workload.
  */
 typedef struct gsfit_render_opts {
     int32_t tile;
     int32_t batch;
     int32_t exp_half2;
-    int32_t reserved;
+    int32_t batch_bwd;
 } gsfit_render_opts;
 
 /*
@@ -423,8 +427,9 @@ int gsfit_render_count(const gsfit_proj* proj, const gsfit_camera* cams, int32_t
  * forward launches and `reps` adjoint launches each, timed with CUDA events on
  * `stream`. The adjoint accumulates into grad2d, which this call zeroes again
  * at the end. Unlike the other calls it synchronises the stream (it measures)
- * and must not be captured in a graph. Writes the options with the smallest
- * forward + adjoint time to *best (tile = `tile`), and, if times_ms (host) is
+ * and must not be captured in a graph. Writes to *best (tile = `tile`) the
+ * depth with the smallest forward time as batch and the one with the smallest
+ * adjoint time as batch_bwd, and, if times_ms (host) is
  * not null, the mean times per depth: 2 floats per depth (forward, adjoint),
  * depths in increasing order. The tile size itself changes the projection
  * and the binning too; callers compare tile sizes on the whole iteration.

@@ -155,11 +155,17 @@ __device__ __forceinline__ void stage(Batch<N>& S, uint32_t idx, uint32_t end, c
 // kRing - 1 slots ahead of the slowest. A slot with count 0 ends the list.
 // Every wait is bounded (kWaitCycles, about a second): on expiry the status
 // word gets GSFIT_ERR_TIMEOUT, the warp stops, and later tiles skip their work.
-constexpr int kRing = 4;
+// Ring depth: 8 slots of 64 entries (the same shared memory as 4 of 128; the
+// deeper ring lets the pixel warps run further apart), else 4.
+template <int SLOT>
+struct RingDepth {
+    static constexpr int value = SLOT == 64 ? 8 : 4;
+};
 constexpr long long kWaitCycles = 1ll << 31;
 
 template <int SLOT>
 struct Ring {
+    static constexpr int kRing = RingDepth<SLOT>::value;
     // records as stored (u, v, depth, radius | a', b', c', opacity | r, g, b,
     // clamp mask), or, staged PAIRED for the adjoint, rearranged so that each
     // operand pair of its packed two-lane arithmetic is one aligned half of a
@@ -240,7 +246,7 @@ __device__ __forceinline__ uint32_t load_index(uint32_t idx, uint32_t end, const
 template <int SLOT>
 __device__ __forceinline__ void ring_init(Ring<SLOT>& R, int pixel_warps) {
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kRing; ++s) {
+        for (int s = 0; s < Ring<SLOT>::kRing; ++s) {
             mbar_init(&R.full[s], 32);
             mbar_init(&R.empty[s], 32 * pixel_warps);
         }
@@ -258,6 +264,7 @@ __device__ __forceinline__ bool ring_produce(Ring<SLOT>& R, int k, uint32_t b0, 
                                              const float4* __restrict__ xyd, const float4* __restrict__ conic,
                                              const float4* __restrict__ rgb, size_t rec0, int n,
                                              int32_t* status) {
+    constexpr int kRing = Ring<SLOT>::kRing;
     const int s = k % kRing;
     const int lane = threadIdx.x & 31;
     if (k >= kRing && !mbar_wait(&R.empty[s], ((k / kRing) & 1) ^ 1, status)) return false;
@@ -396,6 +403,7 @@ __global__ void __launch_bounds__(TileShape<TILE>::kThreads) render_fwd_kernel(
     bool wdone = __all_sync(0xffffffffu, done);
     if (wdone && lane == 0) atomicAdd(&s_done, 1);
     for (int k = 0;; ++k) {
+        constexpr int kRing = Ring<SLOT>::kRing;
         const int s = k % kRing;
         // warp-uniform, so that no lane leaves while the others reach a warp collective
         if (!__all_sync(0xffffffffu, mbar_wait(&R.full[s], (k / kRing) & 1, status))) break;
@@ -673,6 +681,7 @@ __global__ void __launch_bounds__(TileShape<TILE>::kThreads, 5) render_bwd_kerne
     const int slot = reduce9_slot(lane);
     const int slot_off = slot + slot / 3;  // floats (du dv do _ | da db dc _ | dr dg db _ | ....) of a record
     for (int k = 0;; ++k) {
+        constexpr int kRing = Ring<SLOT>::kRing;
         const int s = k % kRing;
         // warp-uniform, so that no lane leaves while the others reach a warp collective
         if (!__all_sync(0xffffffffu, mbar_wait(&R.full[s], (k / kRing) & 1, status))) break;
@@ -775,17 +784,20 @@ using namespace gsfit;
 namespace {
 
 struct RenderCfg {
-    int tile, batch;
+    int tile, batch, batch_bwd;
     bool e16 = false;  // half2 exponent
 };
 
-// Options -> a supported (tile, batch, exponent precision); false for unsupported values.
+bool supported_depth(int b) { return b == 64 || b == 128 || b == 256; }
+
+// Options -> a supported (tile, batch depths, exponent precision); false for unsupported values.
 bool resolve(const gsfit_render_opts* o, RenderCfg& c) {
     c.tile = (o && o->tile) ? o->tile : GSFIT_TILE;
     c.batch = (o && o->batch) ? o->batch : 128;
+    c.batch_bwd = (o && o->batch_bwd) ? o->batch_bwd : 64;
     c.e16 = o && o->exp_half2 == 1;
-    return (c.tile == 8 || c.tile == 16) && (c.batch == 64 || c.batch == 128 || c.batch == 256) &&
-           (!o || ((o->exp_half2 == 0 || o->exp_half2 == 1) && o->reserved == 0));
+    return (c.tile == 8 || c.tile == 16) && supported_depth(c.batch) && supported_depth(c.batch_bwd) &&
+           (!o || o->exp_half2 == 0 || o->exp_half2 == 1);
 }
 
 struct FwdArgs {
@@ -879,10 +891,10 @@ int run_fwd(const FwdArgs& a, const RenderCfg& c, int total_tiles, cudaStream_t 
 
 int run_bwd(const BwdArgs& a, const RenderCfg& c, int total_tiles, cudaStream_t s) {
     if (c.e16)
-        return c.tile == 8 ? dispatch_bwd<8, true>(a, c.batch, total_tiles, s)
-                           : dispatch_bwd<16, true>(a, c.batch, total_tiles, s);
-    return c.tile == 8 ? dispatch_bwd<8, false>(a, c.batch, total_tiles, s)
-                       : dispatch_bwd<16, false>(a, c.batch, total_tiles, s);
+        return c.tile == 8 ? dispatch_bwd<8, true>(a, c.batch_bwd, total_tiles, s)
+                           : dispatch_bwd<16, true>(a, c.batch_bwd, total_tiles, s);
+    return c.tile == 8 ? dispatch_bwd<8, false>(a, c.batch_bwd, total_tiles, s)
+                       : dispatch_bwd<16, false>(a, c.batch_bwd, total_tiles, s);
 }
 
 FwdArgs fwd_args(const gsfit_proj* proj, const gsfit_camera* cams, int n_views, int n, const uint32_t* vals,
@@ -1047,12 +1059,12 @@ extern "C" int gsfit_render_autotune(const gsfit_proj* proj, const gsfit_camera*
     Events ev;
     if (!ev.ok) return GSFIT_ERR_CUDA;
     const int depths[3] = {64, 128, 256};
-    float best_ms = 3.4e38f;
-    int best_depth = 128;
+    float best_fwd = 3.4e38f, best_bwd = 3.4e38f;
+    int best_depth = 128, best_depth_bwd = 64;
     for (int d = 0; d < 3; ++d) {
         RenderCfg c;
         c.tile = tile;
-        c.batch = depths[d];
+        c.batch = c.batch_bwd = depths[d];
         int rc = run_fwd(fa, c, total_tiles, stream);  // warm-up (and shared-memory opt-in)
         if (rc == GSFIT_OK) rc = run_bwd(ba, c, total_tiles, stream);
         if (rc != GSFIT_OK) return rc;
@@ -1072,9 +1084,13 @@ extern "C" int gsfit_render_autotune(const gsfit_proj* proj, const gsfit_camera*
             times_ms[2 * d] = tf;
             times_ms[2 * d + 1] = tb;
         }
-        if (tf + tb < best_ms) {
-            best_ms = tf + tb;
+        if (tf < best_fwd) {
+            best_fwd = tf;
             best_depth = depths[d];
+        }
+        if (tb < best_bwd) {
+            best_bwd = tb;
+            best_depth_bwd = depths[d];
         }
     }
     // the adjoint launches accumulated into grad2d: leave it zero, as the calls require
@@ -1083,7 +1099,7 @@ extern "C" int gsfit_render_autotune(const gsfit_proj* proj, const gsfit_camera*
     best->tile = tile;
     best->batch = best_depth;
     best->exp_half2 = 0;
-    best->reserved = 0;
+    best->batch_bwd = best_depth_bwd;
     return GSFIT_OK;
 }
 

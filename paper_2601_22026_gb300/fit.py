@@ -73,18 +73,19 @@ class FitState:
     def __init__(self, gaussians: dict, cams: dict, *, target_rgb=None, target_alpha=None, bg=None,
                  capacity: int | None = None, lr: dict | None = None, eps: float = 1e-15,
                  lam: float = 0.2, features: str = "f32", tile: int = 16, batch: int = 128,
-                 exp_half2: bool = False, device: str = "cuda"):
+                 batch_bwd: int = 64, exp_half2: bool = False, device: str = "cuda"):
         """features: "f32", or "f16" / "bf16" for the mixed-precision form
         (16-bit copy of the SH coefficients read by the projection, kept
         current by Adam; float32 master parameters and moments).
-        tile (8 or 16) and batch (64, 128, 256 records per shared-memory
-        slot): the compositing options; see tune.py for choosing them.
+        tile (8 or 16), batch and batch_bwd (64, 128, 256 records per
+        shared-memory slot of the forward and the adjoint compositing): the
+        compositing options; see tune.py for choosing them.
         exp_half2: evaluate the compositing exponent in packed half precision
         (the half2 option of the mixed-precision form)."""
         self.device = device
         self.tile = int(tile)
         self.exp_half2 = bool(exp_half2)
-        self.opts = G.RenderOpts(self.tile, int(batch), int(self.exp_half2))
+        self.opts = G.RenderOpts(self.tile, int(batch), int(self.exp_half2), int(batch_bwd))
         self.n = int(gaussians["means"].shape[0])
         self.sh_degree = int(round(gaussians["sh"].shape[1] ** 0.5)) - 1
         self.n_planes = G.num_planes(self.sh_degree)
@@ -284,8 +285,9 @@ class FitState:
     def tune_batch(self, reps: int = 3) -> dict:
         """Measures the compositing batch depths on this state's current view
         batch (one forward and loss first, for realistic lists and
-        cotangents), keeps the fastest in self.opts and drops any captured
-        graph. Returns {depth: (forward ms, adjoint ms)}; synchronises."""
+        cotangents), keeps the fastest forward and the fastest adjoint depth
+        in self.opts and drops any captured graph. Returns {depth: (forward
+        ms, adjoint ms)}; synchronises."""
         self.forward()
         self.loss()
         best, times = G.gsfit_render_autotune(self.proj, self.cams_dev, self.V, self.n, self.T, self.vals,

@@ -36,7 +36,7 @@ class Gaussians(ctypes.Structure):
                 ("reserved", _i32)]
 
 
-ABI_VERSION = 4  # GSFIT_ABI_VERSION of include/gsfit.h
+ABI_VERSION = 5  # GSFIT_ABI_VERSION of include/gsfit.h
 
 # gsfit_gaussians.feature_dtype values (GSFIT_FEATURES_*)
 FEATURES = {"f32": 0, "f16": 1, "bf16": 2}
@@ -53,9 +53,10 @@ class Camera(ctypes.Structure):
 
 
 class RenderOpts(ctypes.Structure):
-    """gsfit_render_opts: tile edge (8 or 16), batch depth (64, 128, 256) and
-    the half2-exponent switch (0 or 1)."""
-    _fields_ = [("tile", _i32), ("batch", _i32), ("exp_half2", _i32), ("reserved", _i32)]
+    """gsfit_render_opts: tile edge (8 or 16), the forward passes' batch depth
+    (64, 128, 256), the half2-exponent switch (0 or 1) and the adjoint's batch
+    depth (64, 128, 256); 0 selects a field's default."""
+    _fields_ = [("tile", _i32), ("batch", _i32), ("exp_half2", _i32), ("batch_bwd", _i32)]
 
 
 assert ctypes.sizeof(Camera) == 128
@@ -281,7 +282,7 @@ def gsfit_bin_sort(proj: ProjBuffers, cams_dev, n_views, n, total_tiles, ws, key
 
 
 def _opts(opts):
-    """None, a RenderOpts, or a (tile, batch[, exp_half2]) tuple -> a pointer argument."""
+    """None, a RenderOpts, or a (tile, batch[, exp_half2[, batch_bwd]]) tuple -> a pointer argument."""
     if opts is None:
         return None
     if not isinstance(opts, RenderOpts):

@@ -111,7 +111,8 @@ def view_state(src, cams: dict, bg=None, **kw):
     Gaussians: built around a one-Gaussian placeholder, then sharing src's
     parameters, 16-bit copy and optimiser state."""
     from .fit import FitState
-    st = FitState(src.gaussians_first(), cams, bg=bg, capacity=16, tile=src.tile, batch=int(src.opts.batch), **kw)
+    st = FitState(src.gaussians_first(), cams, bg=bg, capacity=16, tile=src.tile, batch=int(src.opts.batch),
+                  batch_bwd=int(src.opts.batch_bwd), **kw)
     st.n = src.n
     share_parameters(st, src)
     st.set_cameras(cams, bg=bg)

@@ -1,8 +1,9 @@
-"""Autotuner of the batched launch: the tile edge and the batch depth of the
-compositing kernels (the number of Gaussians staged per shared-memory slot).
+"""Autotuner of the batched launch: the tile edge and the batch depths of the
+compositing kernels (the number of Gaussians staged per shared-memory slot,
+chosen for the forward and the adjoint kernel separately).
 
-The batch depth only changes the compositing kernels, so the library measures
-it itself (gsfit_render_autotune, through FitState.tune_batch). The tile edge
+The batch depths only change the compositing kernels, so the library measures
+them itself (gsfit_render_autotune, through FitState.tune_batch). The tile edge
 changes the projection's rectangles, the pair count and the sort as well, so
 it is compared on whole iterations: for each tile edge a state is built,
 its batch depth tuned, one iteration captured as a CUDA graph and replayed.
@@ -64,25 +65,27 @@ def time_iterations(st, steps: int = 20, warmup: int = 3) -> float:
 
 
 def autotune(make_state, key: str, tiles=TILES, steps: int = 20, use_cache: bool = True) -> dict:
-    """Picks (tile, batch) for a workload. make_state(tile, batch) returns a
-    FitState of the workload (targets set) laid out for that tile edge. Returns
-    {"tile", "batch", "ms_per_step", "candidates": {tile: {...}}, "cached"}."""
+    """Picks (tile, batch, batch_bwd) for a workload. make_state(tile, batch,
+    batch_bwd) returns a FitState of the workload (targets set) laid out for
+    that tile edge. Returns {"tile", "batch", "batch_bwd", "ms_per_step",
+    "candidates": {tile: {...}}, "cached"}."""
     import torch
     if use_cache:
         hit = _load_cache().get(key)
-        if hit:
+        if hit and "batch_bwd" in hit:
             return dict(hit, cached=True)
     cands = {}
     for tile in tiles:
-        st = make_state(tile, 128)
+        st = make_state(tile, 128, 64)
         depth_ms = st.tune_batch()
         ms = time_iterations(st, steps)
-        cands[int(tile)] = {"batch": int(st.opts.batch), "ms_per_step": ms,
+        cands[int(tile)] = {"batch": int(st.opts.batch), "batch_bwd": int(st.opts.batch_bwd), "ms_per_step": ms,
                             "depth_ms": {int(d): [float(f), float(b)] for d, (f, b) in depth_ms.items()}}
         del st
         torch.cuda.empty_cache()
     tile = min(cands, key=lambda t: cands[t]["ms_per_step"])
-    entry = {"tile": int(tile), "batch": cands[tile]["batch"], "ms_per_step": cands[tile]["ms_per_step"],
+    entry = {"tile": int(tile), "batch": cands[tile]["batch"], "batch_bwd": cands[tile]["batch_bwd"],
+             "ms_per_step": cands[tile]["ms_per_step"],
              "candidates": {str(t): c for t, c in cands.items()}}
     _store(key, entry)
     return dict(entry, cached=False)

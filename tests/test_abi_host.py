@@ -37,7 +37,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version_and_status_strings(lib):
-    assert lib.gsfit_abi_version() == 4
+    assert lib.gsfit_abi_version() == 5
     assert lib.gsfit_status_string(G.GSFIT_ERR_CAPACITY) == b"instance capacity exceeded"
     assert lib.gsfit_status_string(G.GSFIT_ERR_TIMEOUT) == b"bounded device wait ran out"
 
@@ -150,7 +150,7 @@ def test_render_options_rejected_on_host(lib):
     fake = 256
     p = G.Proj(fake, fake, fake, fake)
     for opts in [G.RenderOpts(8, 100), G.RenderOpts(32, 128), G.RenderOpts(12, 64), G.RenderOpts(16, 128, 2),
-                 G.RenderOpts(16, 128, 0, 1)]:
+                 G.RenderOpts(16, 128, 0, 1), G.RenderOpts(16, 128, 0, 100), G.RenderOpts(16, 128, 0, 512)]:
         assert lib.gsfit_render_fwd(ctypes.byref(p), fake, 1, 10, 4, fake, fake, None, fake, fake, fake, fake, fake,
                                     ctypes.byref(opts), None, None) == G.GSFIT_ERR_INVALID_ARG
         assert lib.gsfit_blend_bwd(ctypes.byref(p), fake, 1, 10, 4, fake, fake, None, fake, fake, fake, fake, fake,

@@ -1,5 +1,6 @@
 """The tunables of the batched launch against the FP64 oracle: every
-(tile edge, batch depth) variant of the compositing kernels gives the same
+(tile edge, forward batch depth, adjoint batch depth) variant of the
+compositing kernels gives the same
 keys, sorted lists and ranges as the oracle at that tile edge (bit for bit),
 the same images (1e-4) and gradients (1e-3); a compositing call told a tile
 edge the cameras were not laid out for reports it and does nothing; the
@@ -14,7 +15,9 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 F = oracle.F
-VARIANTS = [(8, 64), (8, 128), (8, 256), (16, 64), (16, 256)]
+# (16, 128, 64) is the default, which the parity tests run
+VARIANTS = [(8, 64, 64), (8, 128, 128), (8, 256, 256), (16, 64, 128), (16, 256, 256), (16, 128, 128),
+            (16, 64, 64)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -25,17 +28,17 @@ def _built():
     pkg.build()
 
 
-def _state(gs, cams, bg, tile, batch):
+def _state(gs, cams, bg, tile, batch, batch_bwd=64):
     from paper_2601_22026_gb300.fit import FitState
-    return FitState(gs, cams, bg=bg, tile=tile, batch=batch)
+    return FitState(gs, cams, bg=bg, tile=tile, batch=batch, batch_bwd=batch_bwd)
 
 
-@pytest.mark.parametrize("tile,batch", VARIANTS)
-def test_variant_matches_oracle(tile, batch):
+@pytest.mark.parametrize("tile,batch,batch_bwd", VARIANTS)
+def test_variant_matches_oracle(tile, batch, batch_bwd):
     from test_parity_gpu import (_case, _grad_check, _pairs_excluding, _pixel_tile_mask, _radius_flips,
                                  _rgb_to_pixels)
     gs, cams, bg = _case("sh3_uneven_views")
-    st = _state(gs, cams, bg, tile, batch)
+    st = _state(gs, cams, bg, tile, batch, batch_bwd)
     P = scenes.num_pixels(cams)
     w_rgb = scenes.cotangents(3 * P, 801, 1e-3)
     w_a = scenes.cotangents(P, 802, 1e-3)
@@ -116,7 +119,9 @@ def test_batch_tuner(tile):
     rgb0 = st.rgb.clone()
     times = st.tune_batch(reps=2)
     assert st.check_status() == 0
-    assert st.opts.tile == tile and st.opts.batch in (64, 128, 256)
+    assert st.opts.tile == tile and st.opts.batch in (64, 128, 256) and st.opts.batch_bwd in (64, 128, 256)
+    assert st.opts.batch == min(times, key=lambda d: times[d][0])
+    assert st.opts.batch_bwd == min(times, key=lambda d: times[d][1])
     assert set(times) == {64, 128, 256} and all(f > 0 and b > 0 for f, b in times.values())
     assert float(st.grad2d.abs().max().item()) == 0.0
     # the forward result does not depend on the batch depth
