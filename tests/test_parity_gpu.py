@@ -239,6 +239,56 @@ def test_sort_with_constant_digits_bit_exact(name):
         np.testing.assert_array_equal(ranges, ref["ranges"])
 
 
+def _dense_tile_scene(n, tie_every=0):
+    """n small splats on a short column along the view axis of a 48 x 48
+    camera, all projecting inside tile (1, 1), which then holds all n pairs.
+    With tie_every k, every k-th splat lies on one plane facing the camera
+    (the same depth for all of them: equal keys, ordered by index)."""
+    g = scenes.rng(31)
+    gs = scenes.random_gaussians(n, 1, 32, log_scale_mean=-5.0, log_scale_std=0.2)
+    gs["means"][:, 0] = g.uniform(-1.5, 1.5, n)
+    gs["means"][:, 1:] = g.uniform(-0.08, 0.08, (n, 2))
+    if tie_every:
+        gs["means"][::tie_every, 0] = 0.25
+    return gs, scenes.stack_cameras([scenes.make_camera((5, 0, 0), (0, 0, 0), 48, 48, fx=48.0)])
+
+
+# one tile holding all n pairs (one tile id over one to five 4096-pair radix
+# partitions), with and without equal depths
+DENSE_CASES = {"small_block": (1500, 0), "small_block_ties": (2000, 3), "large_block": (6000, 0),
+               "large_block_ties": (9000, 4), "global_buffers": (20000, 0), "global_buffers_ties": (16000, 5)}
+
+
+@pytest.mark.parametrize("name", list(DENSE_CASES))
+def test_dense_tile_sort_bit_exact(name):
+    n, tie = DENSE_CASES[name]
+    gs, cams = _dense_tile_scene(n, tie)
+    proj = oracle.project(gs, cams)
+    rk, rv, rranges = oracle.bin_tiles(proj, cams)
+    lens = rranges[:, 1].astype(np.int64) - rranges[:, 0].astype(np.int64)
+    assert lens.max() >= 0.95 * n  # the case's precondition: one tile holds (nearly) all pairs
+    if tie:
+        depth = proj[0, :, F["depth32"]].astype(np.float32)
+        assert np.sum(depth[::tie] == depth[0]) == len(depth[::tie])
+    st = _fit_state(gs, cams, scenes.backgrounds(1, 79))
+    st.project()
+    st.bin_sort()
+    torch.cuda.synchronize()
+    assert st.check_status() == 0
+    n_inst = int(st.n_instances.item())
+    keys = st.keys[:n_inst].cpu().numpy().view(np.uint64)
+    vals = st.vals[:n_inst].cpu().numpy().view(np.uint32)
+    ranges = st.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2)
+    flips = _radius_flips(st, proj)
+    gk, gv, bad_g = _pairs_excluding(keys, vals, proj, cams, st.n, flips)
+    ok_, ov, _ = _pairs_excluding(rk, rv, proj, cams, st.n, flips)
+    np.testing.assert_array_equal(gk, ok_)
+    np.testing.assert_array_equal(gv, ov)
+    if not bad_g:
+        assert n_inst == len(rk)
+        np.testing.assert_array_equal(ranges, rranges)
+
+
 def _pixel_tile_mask(cams, bad_tiles):
     """Per-pixel mask of pixels lying in the given global tiles."""
     out = []
