@@ -18,7 +18,7 @@
 // never changes a result) and walks only those, one branch-free step per
 // entry. The adjoint keeps no per-(pixel, Gaussian) state: it restarts from
 // the stored final transmittance and contributor count and recovers T_i =
-// T_{i+1} / (1 - alpha_i) walking backwards. Where at most 16 lanes blend a
+// T_{i+1} / (1 - alpha_i) walking backwards. Where at most 14 lanes blend a
 // Gaussian, each adds its nine gradient terms with three 16-byte vector
 // atomics; otherwise the warp sums them with a transposed butterfly (12
 // shuffles instead of 45) that leaves each total in its own lane, so one
@@ -483,10 +483,10 @@ __global__ void __launch_bounds__(TileShape<TILE>::kThreads) render_fwd_kernel(
 // warp reduction: each blending lane adds its nine terms to the record's
 // grad2d entry itself with three 16-byte vector atomics (no more L2 atomic
 // operations than the nine-lane scalar atomic after the butterfly for up to
-// three lanes; measured fastest at 16 on the bench workload: fewer lanes
-// leave more visits to the 42-instruction butterfly, more flood the L2 with
-// atomics).
-constexpr int kDirectLanes = 16;
+// three lanes; measured fastest at 14 on the bench workload with 64-entry
+// batches: fewer lanes leave more visits to the 42-instruction butterfly,
+// more flood the L2 with atomics).
+constexpr int kDirectLanes = 14;
 
 // Adds (a, b, c, 0) to the 16-byte-aligned float4 at addr (one vector atomic).
 __device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float c) {
