@@ -871,14 +871,15 @@ def main() -> None:
     n_vis = int((st.proj.tiles > 0).sum().item())
 
     # per-stage durations from the graph's own event nodes: the last timed
-    # replay, and the mean over ten more replays; eager launches bracketed by
-    # events for comparison. The roofline uses the replayed graph's mean.
+    # replay, and the median over ten more replays; eager launches bracketed by
+    # events for comparison. The roofline uses the replayed graph's median.
     reps = []
     for k in range(10):
         st.bg.copy_(bg_table[k % len(bg_table)])
         st.replay()
         reps.append(st.stage_times())
-    stage_ms = {k: float(np.mean([r[k] for r in reps])) for k in TIMED_STAGES}
+    # the median: robust to one slow replay (a reduced case showed the first one after the timed loop slow)
+    stage_ms = {k: float(np.median([r[k] for r in reps])) for k in TIMED_STAGES}
     stage_ms_eager = time_stages(st, reps=max(5, min(30, args.steps // 10)))
     blended = st.blended_pairs()
     tile_passes = max(1, (int(np.ceil(np.log2(max(2, st.T)))) + 7) // 8)
@@ -924,7 +925,7 @@ def main() -> None:
                       {"cached": tuned["cached"], "candidates": tuned["candidates"]}},
            "gpu_launches": launches_per_step * args.steps,
            "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
-           "stage_ms_source": "event nodes of the replayed CUDA graph (mean of 10 replays after the timed ones)",
+           "stage_ms_source": "event nodes of the replayed CUDA graph (median of 10 replays after the timed ones)",
            "stage_ms_last_timed_replay": {k: round(v, 4) for k, v in stage_ms_last.items()},
            "stage_ms_eager": {k: round(v, 4) for k, v in stage_ms_eager.items()}, "blended_pairs": blended,
            "roofline": roof, "clocks": clk,
