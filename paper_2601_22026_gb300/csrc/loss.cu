@@ -142,15 +142,32 @@ __device__ __forceinline__ void prefetch_item(LossSmem& S, const gsfit_camera* _
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const bool interior = ox >= 10 && oy >= 10 && ox + kOut + 10 <= W && oy + kOut + 10 <= H;
     // warp w copies rows w, w + 8, ...; lane l columns l and l + 32
-    for (int r = wid; r < kR2; r += kLossThreads / 32) {
-        const int gy = oy - 10 + r;
-        for (int c = lane; c < kR2; c += 32) {
-            const int gx = ox - 10 + c;
-            const bool ok = interior || (gx >= 0 && gx < W && gy >= 0 && gy < H);
-            const long long q = ok ? (long long)gy * W + gx : 0;
-            cp_async4(&S.a.xy[r][c].x, X + q, ok);
-            cp_async4(&S.a.xy[r][c].y, Yt + q, ok);
-            cp_async4(&S.b.st.at[r][c], At + q, ok);
+    if (interior) {
+        // the region lies inside the image: no bounds, row pointers advanced by 8 rows
+        const long long row0 = (long long)(oy - 10 + wid) * W + (ox - 10);
+        const long long step = (long long)(kLossThreads / 32) * W;
+        const float* xr = X + row0;
+        const float* yr = Yt + row0;
+        const float* ar = At + row0;
+        for (int r = wid; r < kR2; r += kLossThreads / 32, xr += step, yr += step, ar += step) {
+#pragma unroll
+            for (int c = lane; c < kR2; c += 32) {
+                cp_async4(&S.a.xy[r][c].x, xr + c, true);
+                cp_async4(&S.a.xy[r][c].y, yr + c, true);
+                cp_async4(&S.b.st.at[r][c], ar + c, true);
+            }
+        }
+    } else {
+        for (int r = wid; r < kR2; r += kLossThreads / 32) {
+            const int gy = oy - 10 + r;
+            for (int c = lane; c < kR2; c += 32) {
+                const int gx = ox - 10 + c;
+                const bool ok = gx >= 0 && gx < W && gy >= 0 && gy < H;
+                const long long q = ok ? (long long)gy * W + gx : 0;
+                cp_async4(&S.a.xy[r][c].x, X + q, ok);
+                cp_async4(&S.a.xy[r][c].y, Yt + q, ok);
+                cp_async4(&S.b.st.at[r][c], At + q, ok);
+            }
         }
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
