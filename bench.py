@@ -764,7 +764,9 @@ def run_reference(args) -> None:
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "iters/s", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD + " (FP64 CPU oracle, bounded sample per step)"},
+           # the same workload as the GPU arm; how the oracle samples it per step is in cpu_baseline.sample
+           "config": {"workload": WORKLOAD, "gaussians": int(len(sc["gaussians"]["means"])),
+                      "views": int(len(sc["cameras"]["width"])), "pixels": int(scenes.num_pixels(sc["cameras"]))},
            "cpu_baseline": {"value": v, "unit": "iters/s", "cores": vals[0]["cores"], "kind": "oracle",
                             "sample": vals[0]["sample"]},
            "e2e": {"value": v, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
