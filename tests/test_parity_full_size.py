@@ -7,7 +7,9 @@ configuration the benchmark times:
     one of its 24 orbit views of 1024^2 (one view per iteration).
 The oracle cannot render these whole, so it computes sampled outputs one by
 one: every pixel and the sorted list of sampled tiles, and the complete
-gradients of sampled Gaussians."""
+gradients of sampled Gaussians. The batched periphery also runs in its
+mixed-precision form (SH coefficients stored as IEEE half), on features
+snapped to half values on the host so that both sides read the same set."""
 import numpy as np
 import pytest
 
@@ -20,19 +22,32 @@ pytestmark = pytest.mark.gpu
 F = oracle.F
 
 
-@pytest.fixture(scope="module")
-def batch():
+def _batched(features):
     if not torch.cuda.is_available():
         pytest.skip("needs a CUDA device")
     import paper_2601_22026_gb300 as pkg
     from paper_2601_22026_gb300.fit import FitState
     pkg.build()
     sc = scenes.batched_periphery_scene(0)
-    st = FitState(sc["gaussians"], sc["cameras"], bg=sc["bg"])
+    if features == "f16":
+        gs = dict(sc["gaussians"])
+        gs["sh"] = gs["sh"].astype(np.float16).astype(np.float32)  # exact in half
+        sc = dict(sc, gaussians=gs)
+    st = FitState(sc["gaussians"], sc["cameras"], bg=sc["bg"], features=features)
     st.forward()
     torch.cuda.synchronize()
     assert st.check_status() == 0
     return sc, st
+
+
+@pytest.fixture(scope="module")
+def batch():
+    return _batched("f32")
+
+
+@pytest.fixture(scope="module")
+def batch_f16():
+    return _batched("f16")
 
 
 def _sample_items(sc, per_view=4, seed=9):
@@ -80,9 +95,12 @@ def ct_view():
     return sc, st
 
 
-@pytest.fixture(params=["batched_1M_16views", "ct_200k_1024"])
+WORKLOADS = {"batched_1M_16views": "batch", "batched_1M_16views_f16": "batch_f16", "ct_200k_1024": "ct_view"}
+
+
+@pytest.fixture(params=list(WORKLOADS))
 def workload(request):
-    return request.getfixturevalue("batch" if request.param == "batched_1M_16views" else "ct_view")
+    return request.getfixturevalue(WORKLOADS[request.param])
 
 
 def test_full_size_sampled_tiles(workload):
