@@ -1,4 +1,4 @@
-"""Fit-step driver: device buffers for one Gaussian set and one view batch,
+"""Fit-step runner: device buffers for one Gaussian set and one view batch,
 the iteration project -> bin/sort -> render -> loss -> adjoint -> Adam as
 calls into libgsfit, CUDA-graph capture of the whole iteration, and a
 torch.autograd.Function around render.

@@ -7,7 +7,7 @@ more than 5 degrees against, every view already in the set). The paper
 simplifies continual training to periodic restarts that reload the current
 Gaussians and discard the optimiser state (ContinuousRefinement.restart).
 
-The driver keeps a fixed-size batch of V views (the periphery frames plus
+The loop keeps a fixed-size batch of V views (the periphery frames plus
 foveal crops); every `replace_every` iterations the oldest `n_replace` crops
 are replaced by newly streamed views that pass Eq. 1, their targets are
 rendered from the target set, and the iteration is captured again as a CUDA
