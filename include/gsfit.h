@@ -60,9 +60,12 @@
 extern "C" {
 #endif
 
-#define GSFIT_ABI_VERSION 5
+#define GSFIT_ABI_VERSION 6
 #define GSFIT_MAX_VIEWS 256
 #define GSFIT_TILE 16
+/* Words after the tile permutation in a tile_order buffer (gsfit_bin_sort):
+ * the number of non-empty tiles. */
+#define GSFIT_TILE_ORDER_EXTRA 1
 
 /* Return and status codes. */
 #define GSFIT_OK 0
@@ -235,11 +238,14 @@ size_t gsfit_bin_sort_workspace_size(int64_t n_records, int64_t capacity, int32_
  *   2 * total_tiles entries; status: device int32, set to GSFIT_ERR_CAPACITY
  *   when the pairs exceed capacity (nothing is then emitted and every range
  *   is empty) and to GSFIT_ERR_TIMEOUT if a bounded wait of the sort ran out;
- *   it is not cleared by this call. tile_order (device uint32, total_tiles
- *   entries, may be null): a permutation of the tiles, longest lists first
- *   (bucketed by log2 of the list length, any order within a bucket); the
- *   compositing calls launch tiles in this order so the longest lists start
- *   first and do not form the tail of the grid.
+ *   it is not cleared by this call. tile_order (device uint32, total_tiles +
+ *   GSFIT_TILE_ORDER_EXTRA entries, may be null): entries [0, total_tiles)
+ *   a permutation of the tiles, longest lists first (bucketed by log2 of the
+ *   list length, any order within a bucket), so the non-empty tiles lead;
+ *   entry total_tiles the number of non-empty tiles. The compositing calls
+ *   launch tiles in this order, so the longest lists start first and do not
+ *   form the tail of the grid, and the CTAs of empty tiles leave at once
+ *   (the forward pass writing the background first).
  * Errors: GSFIT_ERR_INVALID_ARG (null pointers, sizes, workspace too small,
  *   capacity >= 2^30, n_views * n >= 2^32), GSFIT_ERR_CUDA.
  */
@@ -293,7 +299,8 @@ typedef struct gsfit_render_opts {
  * Arguments: bg: device float, 3 per view; rgb: 3 * total_pixels floats,
  *   alpha, T_final: total_pixels floats, n_contrib: total_pixels uint32
  *   (device). vals/ranges/tile_order from gsfit_bin_sort (tile_order may be
- *   null: tiles in id order; the results do not depend on the order).
+ *   null: tiles in id order, every tile composited in full; the results do
+ *   not depend on the order).
  *   status: device int32 or null. The kernel's warps hand records to each
  *   other through shared-memory barriers whose waits are bounded (about a
  *   second); if one runs out (which a correct launch never does) the kernel

@@ -356,16 +356,54 @@ __device__ __forceinline__ float2 exp_half2(float a, float b) {
     return __half22float2(h2exp(__floats2half2_rn(a, b)));
 }
 
+// With a tile order (gsfit_bin_sort), its positions from the non-empty count
+// on hold the empty tiles, whose CTAs have nothing to composite: they leave
+// before any setup (the forward pass after writing the background), so the
+// about five in six tiles of a periphery batch that no splat reaches cost
+// little more than their launch. A tile-edge mismatch is reported here too.
+template <int TILE>
+__device__ __forceinline__ bool past_nonempty(const gsfit_camera* cams_g, const uint32_t* tile_order,
+                                              int total_tiles, int32_t* status) {
+    if (!tile_order || blockIdx.x < tile_order[total_tiles]) return false;
+    if (threadIdx.x == 0 && tile_of(cams_g[0]) != TILE && status) atomicExch(status, GSFIT_ERR_INVALID_ARG);
+    return true;
+}
+
+// The outputs of an empty tile at this thread's pixel: the background,
+// alpha 0, T 1, no contributor (the camera table read from global memory).
+template <int TILE>
+__device__ __forceinline__ void fill_background(const gsfit_camera* cams_g, int n_views, int t,
+                                                const float* __restrict__ bg, float* __restrict__ out_rgb,
+                                                float* __restrict__ out_alpha, float* __restrict__ out_T,
+                                                uint32_t* __restrict__ out_nc) {
+    if (tile_of(cams_g[0]) != TILE) return;
+    const TileCtx c = tile_ctx<TILE>(cams_g, n_views, t);
+    if (!c.inside) return;
+    const float* bgv = bg + 3 * c.view;
+    out_rgb[c.rgb_base] = bgv[0];
+    out_rgb[c.rgb_base + c.plane] = bgv[1];
+    out_rgb[c.rgb_base + 2 * c.plane] = bgv[2];
+    out_alpha[c.pix] = 0.0f;
+    out_T[c.pix] = 1.0f;
+    out_nc[c.pix] = 0u;
+}
+
 // IMP: also accumulate each Gaussian's blend weight alpha T over the batch
 // into importance[g] (a warp sum per (warp, Gaussian), then one atomic).
 // E16: the half2-exponent option (two Gaussians of a pixel per exp instruction).
 template <int TILE, int SLOT, bool IMP, bool E16>
-__global__ void __launch_bounds__(TileShape<TILE>::kThreads) render_fwd_kernel(
+__global__ void __launch_bounds__(TileShape<TILE>::kThreads, 5) render_fwd_kernel(
     const float4* __restrict__ xyd, const float4* __restrict__ conic, const float4* __restrict__ rgb, int n,
     const gsfit_camera* __restrict__ cams_g, int n_views, const uint32_t* __restrict__ vals,
-    const uint2* __restrict__ ranges, const uint32_t* __restrict__ tile_order, const float* __restrict__ bg,
-    float* __restrict__ out_rgb, float* __restrict__ out_alpha, float* __restrict__ out_T,
-    uint32_t* __restrict__ out_nc, int32_t* __restrict__ status, float* __restrict__ importance) {
+    const uint2* __restrict__ ranges, const uint32_t* __restrict__ tile_order, int total_tiles,
+    const float* __restrict__ bg, float* __restrict__ out_rgb, float* __restrict__ out_alpha,
+    float* __restrict__ out_T, uint32_t* __restrict__ out_nc, int32_t* __restrict__ status,
+    float* __restrict__ importance) {
+    if (past_nonempty<TILE>(cams_g, tile_order, total_tiles, status)) {  // block-uniform
+        if (threadIdx.x < TileShape<TILE>::kPixels)
+            fill_background<TILE>(cams_g, n_views, (int)tile_order[blockIdx.x], bg, out_rgb, out_alpha, out_T, out_nc);
+        return;
+    }
     constexpr int kWarps = TileShape<TILE>::kWarps;
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     gsfit_camera* cams = reinterpret_cast<gsfit_camera*>(smem_dyn);
@@ -613,10 +651,11 @@ template <int TILE, int SLOT, bool E16>
 __global__ void __launch_bounds__(TileShape<TILE>::kThreads, 5) render_bwd_kernel(
     const float4* __restrict__ xyd, const float4* __restrict__ conic, const float4* __restrict__ rgb, int n,
     const gsfit_camera* __restrict__ cams_g, int n_views, const uint32_t* __restrict__ vals,
-    const uint2* __restrict__ ranges, const uint32_t* __restrict__ tile_order, const float* __restrict__ bg,
-    const float* __restrict__ T_final,
+    const uint2* __restrict__ ranges, const uint32_t* __restrict__ tile_order, int total_tiles,
+    const float* __restrict__ bg, const float* __restrict__ T_final,
     const uint32_t* __restrict__ n_contrib, const float* __restrict__ dL_drgb, const float* __restrict__ dL_dalpha,
     float* __restrict__ grad2d, int32_t* __restrict__ status) {
+    if (past_nonempty<TILE>(cams_g, tile_order, total_tiles, status)) return;  // an empty tile: no gradient
     constexpr int kWarps = TileShape<TILE>::kWarps;
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     gsfit_camera* cams = reinterpret_cast<gsfit_camera*>(smem_dyn);
@@ -839,8 +878,8 @@ int launch_fwd_v(const FwdArgs& a, int total_tiles, cudaStream_t s) {
     const int rc = opt_in_smem(once, render_fwd_kernel<TILE, SLOT, IMP, E16>, render_smem<SLOT>(GSFIT_MAX_VIEWS));
     if (rc != GSFIT_OK) return rc;
     render_fwd_kernel<TILE, SLOT, IMP, E16><<<total_tiles, TileShape<TILE>::kThreads, render_smem<SLOT>(a.n_views), s>>>(
-        a.xyd, a.conic, a.rgb, a.n, a.cams, a.n_views, a.vals, a.ranges, a.tile_order, a.bg, a.out_rgb, a.out_alpha,
-        a.out_T, a.out_nc, a.status, a.importance);
+        a.xyd, a.conic, a.rgb, a.n, a.cams, a.n_views, a.vals, a.ranges, a.tile_order, total_tiles, a.bg, a.out_rgb,
+        a.out_alpha, a.out_T, a.out_nc, a.status, a.importance);
     GSFIT_LAUNCH_CHECK();
     return GSFIT_OK;
 }
@@ -857,8 +896,8 @@ int launch_bwd(const BwdArgs& a, int total_tiles, cudaStream_t s) {
     const int rc = opt_in_smem(once, render_bwd_kernel<TILE, SLOT, E16>, render_smem<SLOT>(GSFIT_MAX_VIEWS));
     if (rc != GSFIT_OK) return rc;
     render_bwd_kernel<TILE, SLOT, E16><<<total_tiles, TileShape<TILE>::kThreads, render_smem<SLOT>(a.n_views), s>>>(
-        a.xyd, a.conic, a.rgb, a.n, a.cams, a.n_views, a.vals, a.ranges, a.tile_order, a.bg, a.T_final, a.n_contrib,
-        a.dL_drgb, a.dL_dalpha, a.grad2d, a.status);
+        a.xyd, a.conic, a.rgb, a.n, a.cams, a.n_views, a.vals, a.ranges, a.tile_order, total_tiles, a.bg, a.T_final,
+        a.n_contrib, a.dL_drgb, a.dL_dalpha, a.grad2d, a.status);
     GSFIT_LAUNCH_CHECK();
     return GSFIT_OK;
 }

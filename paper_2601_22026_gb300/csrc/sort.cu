@@ -670,6 +670,8 @@ __global__ void __launch_bounds__(256) order_hist_kernel(const uint32_t* __restr
     if (threadIdx.x < 32 && h[threadIdx.x]) atomicAdd(&ctl->order_hist[threadIdx.x], h[threadIdx.x]);
 }
 
+// Also writes, after the permutation, the number of non-empty tiles (bucket
+// 0 holds exactly the empty ones, placed last).
 __global__ void __launch_bounds__(256) order_scatter_kernel(const uint32_t* __restrict__ ranges, int total_tiles,
                                                             SortCtl* __restrict__ ctl,
                                                             uint32_t* __restrict__ tile_order) {
@@ -681,6 +683,7 @@ __global__ void __launch_bounds__(256) order_scatter_kernel(const uint32_t* __re
             o += ctl->order_hist[b];
         }
     }
+    if (blockIdx.x == 0 && threadIdx.x == 0) tile_order[total_tiles] = (uint32_t)total_tiles - ctl->order_hist[0];
     // per 256 tiles: bucket counts in shared memory, then one global
     // reservation per (block, bucket)
     __shared__ uint32_t cnt[32], res[32];

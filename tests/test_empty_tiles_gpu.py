@@ -1,0 +1,112 @@
+"""Empty tiles in the compositing launches: with a tile order, the CTAs past
+its non-empty count leave before any setup (the forward pass after writing
+the background into its tile). What must hold: the forward outputs equal
+those of the launch without an order, which composites every tile in full,
+bit for bit (each pixel's sum runs in its own list order either way); the
+adjoint's 2D gradients equal them up to the order of their float atomics;
+and an empty tile holds the background, alpha 0, T 1 and no contributor."""
+import numpy as np
+import pytest
+
+import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import paper_2601_22026_gb300 as pkg
+    pkg.build()
+
+
+def _state(gs, cams, bg, **kw):
+    from paper_2601_22026_gb300.fit import FitState
+    return FitState(gs, cams, bg=bg, **kw)
+
+
+def _case(name):
+    if name == "clustered":  # splats clustered to one side: most tiles empty
+        gs = scenes.random_gaussians(2500, 2, 31, log_scale_mean=-2.6)
+        gs["means"] = (gs["means"] * np.float32(0.1) + np.float32([0.6, 0.3, 0.0])).astype(np.float32)
+        cams = scenes.stack_cameras([scenes.make_camera((0, 0, 3), (0, 0, 0), 333, 250, fx=260.0),
+                                     scenes.make_camera((0.4, -2.8, 1.0), (0, 0, 0), 97, 61, fx=70.0),
+                                     scenes.make_camera((2.5, 1.0, 1.0), (0, 0, 0), 200, 136, fx=150.0)])
+        return gs, cams
+    # the largest view count the calls accept, ragged 24 x 17 views
+    return scenes.random_gaussians(400, 1, 15, log_scale_mean=-2.8), scenes.orbit_cameras(256, 24, 17, 60.0, 3.0, 16)
+
+
+def _fwd_unordered(st):
+    from paper_2601_22026_gb300 import gsfit as G
+    out = [torch.empty_like(x) for x in (st.rgb, st.alpha, st.T_final, st.n_contrib)]
+    G.gsfit_render_fwd(st.proj, st.cams_dev, st.V, st.n, st.T, st.vals, st.ranges, st.bg, *out,
+                       None, None, st.status, st.opts)
+    return out
+
+
+@pytest.mark.parametrize("case", ["clustered", "max_views"])
+@pytest.mark.parametrize("tile", [16, 8])
+def test_forward_with_order_matches_unordered_launch(case, tile):
+    gs, cams = _case(case)
+    bg = scenes.backgrounds(len(cams["width"]), 5)
+    st = _state(gs, cams, bg, tile=tile, batch=64 if tile == 8 else 128)
+    st.project()
+    st.bin_sort()
+    st.render_fwd()
+    ref = _fwd_unordered(st)
+    torch.cuda.synchronize()
+    assert st.check_status() == 0
+    T = st.T
+    words = st.tile_order.cpu().numpy().view(np.uint32).astype(np.int64)
+    ranges = st.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2).astype(np.int64)
+    lens = ranges[:, 1] - ranges[:, 0]
+    n_work = int(words[T])
+    assert n_work == int(np.count_nonzero(lens)) and 0 < n_work <= T
+    if case == "clustered":
+        assert n_work < T  # empty tiles too
+    for a, b in zip((st.rgb, st.alpha, st.T_final, st.n_contrib), ref):
+        np.testing.assert_array_equal(a.cpu().numpy(), b.cpu().numpy())
+    # empty tiles: the background, alpha 0, T 1, no contributor
+    empty = words[n_work:T]
+    assert np.all(lens[empty] == 0)
+    rgb, alpha, T_f, nc = (x.cpu().numpy() for x in (st.rgb, st.alpha, st.T_final, st.n_contrib))
+    W_all, H_all = cams["width"].astype(np.int64), cams["height"].astype(np.int64)
+    off = np.concatenate([[0], np.cumsum(W_all * H_all)])
+    tiles_x, tiles_y = -(-W_all // tile), -(-H_all // tile)
+    toff = np.concatenate([[0], np.cumsum(tiles_x * tiles_y)])
+    for t in empty[:: max(1, len(empty) // 40)]:
+        v = int(np.searchsorted(toff, t, side="right") - 1)
+        W, H = int(W_all[v]), int(H_all[v])
+        tx, ty = (t - toff[v]) % tiles_x[v], (t - toff[v]) // tiles_x[v]
+        ys, xs = np.mgrid[ty * tile:min((ty + 1) * tile, H), tx * tile:min((tx + 1) * tile, W)]
+        pix = off[v] + ys * W + xs
+        assert np.all(alpha[pix] == 0) and np.all(T_f[pix] == 1) and np.all(nc[pix] == 0)
+        for ch in range(3):
+            assert np.all(rgb[3 * off[v] + ch * W * H + ys * W + xs] == np.float32(bg[v, ch]))
+
+
+@pytest.mark.parametrize("tile", [16, 8])
+def test_adjoint_with_order_matches_unordered_launch(tile):
+    from paper_2601_22026_gb300 import gsfit as G
+    gs, cams = _case("clustered")
+    bg = scenes.backgrounds(len(cams["width"]), 6)
+    st = _state(gs, cams, bg, tile=tile, batch=64 if tile == 8 else 128)
+    st.forward()
+    P = st.P
+    st.dL_drgb.copy_(torch.from_numpy(scenes.cotangents(3 * P, 801, 1e-3)))
+    st.dL_dalpha.copy_(torch.from_numpy(scenes.cotangents(P, 802, 1e-3)))
+    st.grad2d.zero_()
+    st.blend_bwd()
+    torch.cuda.synchronize()
+    got = st.grad2d.cpu().numpy().copy()
+    st.grad2d.zero_()
+    G.gsfit_blend_bwd(st.proj, st.cams_dev, st.V, st.n, st.T, st.vals, st.ranges, st.bg, st.T_final, st.n_contrib,
+                      st.dL_drgb, st.dL_dalpha, st.grad2d, None, None, st.status, st.opts)
+    torch.cuda.synchronize()
+    assert st.check_status() == 0
+    ref = st.grad2d.cpu().numpy()
+    assert np.abs(ref).max() > 0
+    np.testing.assert_allclose(got, ref, rtol=1e-5, atol=1e-6 * np.abs(ref).max())

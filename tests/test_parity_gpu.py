@@ -163,12 +163,15 @@ def test_keys_sort_ranges_bit_exact(name):
     assert len(rk) > 0
     np.testing.assert_array_equal(gk, ok_)
     np.testing.assert_array_equal(gv, ov)
-    # heavy-first launch order: a permutation with non-increasing log2 lengths
-    order = st.tile_order.cpu().numpy().view(np.uint32).astype(np.int64)
+    # heavy-first order: a permutation with non-increasing log2 lengths, then
+    # the number of non-empty tiles (which lead it)
+    words = st.tile_order.cpu().numpy().view(np.uint32).astype(np.int64)
+    order = words[:len(ranges)]
     assert np.array_equal(np.sort(order), np.arange(len(ranges)))
     lens = (ranges[:, 1].astype(np.int64) - ranges[:, 0].astype(np.int64))[order]
     buckets = np.floor(np.log2(lens + 1)).astype(np.int64)
     assert np.all(np.diff(buckets) <= 0)
+    assert words[len(ranges)] == np.count_nonzero(lens) and np.all(lens[:words[len(ranges)]] > 0)
     bad = np.array(sorted(bad_g | bad_o), dtype=np.int64)
     if not bad.size:
         assert n_inst == len(rk)
