@@ -52,10 +52,10 @@ struct TileCtx {
 };
 
 template <int TILE>
-__device__ __forceinline__ TileCtx tile_ctx(const gsfit_camera* cams, int n_views, int t) {
+__device__ __forceinline__ TileCtx tile_ctx_in_view(const gsfit_camera* cams, int view, int t) {
     TileCtx c;
-    c.view = view_of_tile(cams, n_views, t);
-    const gsfit_camera& cam = cams[c.view];
+    c.view = view;
+    const gsfit_camera& cam = cams[view];
     const int local = t - cam.tile_offset;
     const int txn = tiles_x_of(cam);
     const int ty = local / txn, tx = local - ty * txn;
@@ -70,6 +70,11 @@ __device__ __forceinline__ TileCtx tile_ctx(const gsfit_camera* cams, int n_view
     c.box_x0 = (float)(tx * TILE + bx);
     c.box_y0 = (float)(ty * TILE + by);
     return c;
+}
+
+template <int TILE>
+__device__ __forceinline__ TileCtx tile_ctx(const gsfit_camera* cams, int n_views, int t) {
+    return tile_ctx_in_view<TILE>(cams, view_of_tile(cams, n_views, t), t);
 }
 
 // Cull parameters of a splat: alpha >= 1/255 needs o exp(-q/2) >= 1/255, i.e.
@@ -369,6 +374,19 @@ __device__ __forceinline__ bool past_nonempty(const gsfit_camera* cams_g, const 
     return true;
 }
 
+// The view owning global tile t, by one warp: a ballot over the views' first
+// tiles, 32 views per round (the views' tile ranges are laid out in order).
+// Its loads do not wait for t, so they overlap the load that produces it.
+__device__ __forceinline__ int view_of_tile_warp(const gsfit_camera* cams_g, int n_views, int t) {
+    const int lane = threadIdx.x & 31;
+    int below = 0;
+    for (int v0 = 0; v0 < n_views; v0 += 32) {
+        const int v = v0 + lane;
+        below += __popc(__ballot_sync(0xffffffffu, v < n_views && cams_g[v].tile_offset <= t));
+    }
+    return below - 1;
+}
+
 // The outputs of an empty tile at this thread's pixel: the background,
 // alpha 0, T 1, no contributor (the camera table read from global memory).
 template <int TILE>
@@ -377,7 +395,7 @@ __device__ __forceinline__ void fill_background(const gsfit_camera* cams_g, int 
                                                 float* __restrict__ out_alpha, float* __restrict__ out_T,
                                                 uint32_t* __restrict__ out_nc) {
     if (tile_of(cams_g[0]) != TILE) return;
-    const TileCtx c = tile_ctx<TILE>(cams_g, n_views, t);
+    const TileCtx c = tile_ctx_in_view<TILE>(cams_g, view_of_tile_warp(cams_g, n_views, t), t);
     if (!c.inside) return;
     const float* bgv = bg + 3 * c.view;
     out_rgb[c.rgb_base] = bgv[0];
@@ -399,10 +417,13 @@ __global__ void __launch_bounds__(TileShape<TILE>::kThreads, 5) render_fwd_kerne
     const float* __restrict__ bg, float* __restrict__ out_rgb, float* __restrict__ out_alpha,
     float* __restrict__ out_T, uint32_t* __restrict__ out_nc, int32_t* __restrict__ status,
     float* __restrict__ importance) {
-    if (past_nonempty<TILE>(cams_g, tile_order, total_tiles, status)) {  // block-uniform
-        if (threadIdx.x < TileShape<TILE>::kPixels)
-            fill_background<TILE>(cams_g, n_views, (int)tile_order[blockIdx.x], bg, out_rgb, out_alpha, out_T, out_nc);
-        return;
+    if (tile_order) {  // the tile id is loaded with the non-empty count, for an empty tile's fill
+        const int t_empty = (int)tile_order[blockIdx.x];
+        if (past_nonempty<TILE>(cams_g, tile_order, total_tiles, status)) {  // block-uniform
+            if (threadIdx.x < TileShape<TILE>::kPixels)
+                fill_background<TILE>(cams_g, n_views, t_empty, bg, out_rgb, out_alpha, out_T, out_nc);
+            return;
+        }
     }
     constexpr int kWarps = TileShape<TILE>::kWarps;
     extern __shared__ __align__(128) unsigned char smem_dyn[];
