@@ -60,12 +60,13 @@
 extern "C" {
 #endif
 
-#define GSFIT_ABI_VERSION 6
+#define GSFIT_ABI_VERSION 7
 #define GSFIT_MAX_VIEWS 256
 #define GSFIT_TILE 16
-/* Words after the tile permutation in a tile_order buffer (gsfit_bin_sort):
- * the number of non-empty tiles. */
-#define GSFIT_TILE_ORDER_EXTRA 1
+/* Words of a tile_order buffer for total_tiles tiles (gsfit_bin_sort):
+ * the heavy-first permutation, the number of non-empty tiles, each tile's
+ * furthest contributor and the adjoint's launch order. */
+#define GSFIT_TILE_ORDER_WORDS(total_tiles) (3 * (total_tiles) + 2)
 
 /* Return and status codes. */
 #define GSFIT_OK 0
@@ -238,14 +239,18 @@ size_t gsfit_bin_sort_workspace_size(int64_t n_records, int64_t capacity, int32_
  *   2 * total_tiles entries; status: device int32, set to GSFIT_ERR_CAPACITY
  *   when the pairs exceed capacity (nothing is then emitted and every range
  *   is empty) and to GSFIT_ERR_TIMEOUT if a bounded wait of the sort ran out;
- *   it is not cleared by this call. tile_order (device uint32, total_tiles +
- *   GSFIT_TILE_ORDER_EXTRA entries, may be null): entries [0, total_tiles)
- *   a permutation of the tiles, longest lists first (bucketed by log2 of the
- *   list length, any order within a bucket), so the non-empty tiles lead;
- *   entry total_tiles the number of non-empty tiles. The compositing calls
- *   launch tiles in this order, so the longest lists start first and do not
- *   form the tail of the grid, and the CTAs of empty tiles leave at once
- *   (the forward pass writing the background first).
+ *   it is not cleared by this call. tile_order (device uint32,
+ *   GSFIT_TILE_ORDER_WORDS(total_tiles) entries, may be null), with
+ *   T = total_tiles: entries [0, T) a permutation of the tiles, longest lists
+ *   first (bucketed by log2 of the list length, any order within a bucket),
+ *   so the non-empty tiles lead; entry T the number of non-empty tiles;
+ *   entries [T + 1, 2T + 1) each tile's furthest contributor, set to zero
+ *   here and written by gsfit_render_fwd; entries [2T + 1, 3T + 1) the
+ *   adjoint's launch order and entry 3T + 1 the non-empty count again,
+ *   written by gsfit_blend_bwd. The forward pass
+ *   launches tiles in the heavy-first order, so the longest lists start first
+ *   and do not form the tail of the grid; the CTAs of empty tiles leave at
+ *   once (the forward pass writing the background first).
  * Errors: GSFIT_ERR_INVALID_ARG (null pointers, sizes, workspace too small,
  *   capacity >= 2^30, n_views * n >= 2^32), GSFIT_ERR_CUDA.
  */
@@ -300,7 +305,10 @@ typedef struct gsfit_render_opts {
  *   alpha, T_final: total_pixels floats, n_contrib: total_pixels uint32
  *   (device). vals/ranges/tile_order from gsfit_bin_sort (tile_order may be
  *   null: tiles in id order, every tile composited in full; the results do
- *   not depend on the order).
+ *   not depend on the order). With a tile_order the call also records each
+ *   non-empty tile's furthest contributor (the largest n_contrib of its
+ *   pixels) in it, from which the adjoint orders its launch; compositing
+ *   calls that share a tile_order must therefore not run concurrently.
  *   status: device int32 or null. The kernel's warps hand records to each
  *   other through shared-memory barriers whose waits are bounded (about a
  *   second); if one runs out (which a correct launch never does) the kernel
@@ -313,7 +321,7 @@ typedef struct gsfit_render_opts {
  *   device, through status.
  */
 int gsfit_render_fwd(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_views, int32_t n,
-                     int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges, const uint32_t* tile_order,
+                     int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges, uint32_t* tile_order,
                      const float* bg, float* rgb, float* alpha, float* T_final, uint32_t* n_contrib,
                      const gsfit_render_opts* opts, int32_t* status, cudaStream_t stream);
 
@@ -391,7 +399,7 @@ int gsfit_loss_noalloc(const gsfit_camera* cams, int32_t n_views, const float* r
  */
 int gsfit_render_bwd(const gsfit_gaussians* g, const gsfit_proj* proj, const gsfit_camera* cams,
                      int32_t n_views, int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges,
-                     const uint32_t* tile_order, const float* bg, const float* T_final, const uint32_t* n_contrib,
+                     uint32_t* tile_order, const float* bg, const float* T_final, const uint32_t* n_contrib,
                      const float* dL_drgb, const float* dL_dalpha, float* grad2d, float* grads,
                      const gsfit_render_opts* opts, int32_t* status, cudaStream_t stream);
 
@@ -402,12 +410,18 @@ int gsfit_render_bwd(const gsfit_gaussians* g, const gsfit_proj* proj, const gsf
  * (u, v, conic, opacity, rgb) into grad2d (which must be zero on entry);
  * gsfit_project_bwd chains them through the projection, sums them over views
  * into `grads` (fully overwritten) and zeroes grad2d again. Arguments as for
- * gsfit_render_bwd (opts and status only for gsfit_blend_bwd). Errors:
+ * gsfit_render_bwd (opts and status only for gsfit_blend_bwd). With a
+ * tile_order, gsfit_blend_bwd first orders the non-empty tiles by the
+ * furthest contributor the forward pass recorded (descending, in quarter
+ * octaves; a tile's adjoint walks its list up to that position), into the
+ * order's last region, and launches them in that order, which ends the
+ * launch with short tiles (list length predicts a tile's adjoint work less
+ * well); the results do not depend on the order. Errors:
  * GSFIT_ERR_INVALID_ARG, GSFIT_ERR_CUDA; GSFIT_ERR_TIMEOUT on the device,
  * through status.
  */
 int gsfit_blend_bwd(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_views, int32_t n,
-                    int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges, const uint32_t* tile_order,
+                    int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges, uint32_t* tile_order,
                     const float* bg, const float* T_final, const uint32_t* n_contrib, const float* dL_drgb,
                     const float* dL_dalpha, float* grad2d, const gsfit_render_opts* opts, int32_t* status,
                     cudaStream_t stream);
@@ -446,7 +460,7 @@ int gsfit_render_count(const gsfit_proj* proj, const gsfit_camera* cams, int32_t
  */
 int gsfit_render_autotune(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_views, int32_t n,
                           int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges,
-                          const uint32_t* tile_order, const float* bg, float* rgb, float* alpha, float* T_final,
+                          uint32_t* tile_order, const float* bg, float* rgb, float* alpha, float* T_final,
                           uint32_t* n_contrib, const float* dL_drgb, const float* dL_dalpha, float* grad2d,
                           int32_t tile, int32_t reps, gsfit_render_opts* best, float* times_ms, int32_t* status,
                           cudaStream_t stream);
@@ -498,7 +512,7 @@ int gsfit_features_refresh(const float* params, int32_t n, int32_t n_planes, voi
  */
 int gsfit_render_importance(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_views, int32_t n,
                             int32_t total_tiles, const uint32_t* vals, const uint32_t* ranges,
-                            const uint32_t* tile_order, const float* bg, float* rgb, float* alpha, float* T_final,
+                            uint32_t* tile_order, const float* bg, float* rgb, float* alpha, float* T_final,
                             uint32_t* n_contrib, float* importance, const gsfit_render_opts* opts, int32_t* status,
                             cudaStream_t stream);
 

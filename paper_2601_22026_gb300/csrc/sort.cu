@@ -671,7 +671,8 @@ __global__ void __launch_bounds__(256) order_hist_kernel(const uint32_t* __restr
 }
 
 // Also writes, after the permutation, the number of non-empty tiles (bucket
-// 0 holds exactly the empty ones, placed last).
+// 0 holds exactly the empty ones, placed last), and zeroes each tile's
+// furthest-contributor word, which the forward pass raises.
 __global__ void __launch_bounds__(256) order_scatter_kernel(const uint32_t* __restrict__ ranges, int total_tiles,
                                                             SortCtl* __restrict__ ctl,
                                                             uint32_t* __restrict__ tile_order) {
@@ -697,7 +698,10 @@ __global__ void __launch_bounds__(256) order_scatter_kernel(const uint32_t* __re
         if (threadIdx.x < 32 && cnt[threadIdx.x])
             res[threadIdx.x] = atomicAdd(&ctl->order_fill[threadIdx.x], cnt[threadIdx.x]);
         __syncthreads();
-        if (t < total_tiles) tile_order[off[b] + res[b] + local] = (uint32_t)t;
+        if (t < total_tiles) {
+            tile_order[off[b] + res[b] + local] = (uint32_t)t;
+            tile_order[total_tiles + 1 + t] = 0u;
+        }
         __syncthreads();
     }
 }

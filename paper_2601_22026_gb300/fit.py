@@ -198,8 +198,9 @@ class FitState:
         self.target_rgb = torch.zeros(3 * self.P, dtype=f32, device=dev)
         self.target_alpha = torch.zeros(self.P, dtype=f32, device=dev)
         self.ranges = torch.zeros(2 * self.T, dtype=torch.int32, device=dev)
-        # the heavy-first tile permutation, then the number of non-empty tiles
-        self.tile_order = torch.zeros(self.T + G.GSFIT_TILE_ORDER_EXTRA, dtype=torch.int32, device=dev)
+        # the heavy-first tile permutation, the number of non-empty tiles, each
+        # tile's furthest contributor and the adjoint's launch order
+        self.tile_order = torch.zeros(G.tile_order_words(self.T), dtype=torch.int32, device=dev)
         self.grad2d = torch.zeros(self.V * self.n * 16, dtype=f32, device=dev)
         self.loss_ws = torch.zeros(G.gsfit_loss_workspace_size(self.V) // 4 + 1, dtype=f32, device=dev)
         bgv = np.zeros((self.V, 3), np.float32) if bg is None else np.asarray(bg, np.float32).reshape(self.V, 3)

@@ -23,7 +23,14 @@ GSFIT_ERR_TIMEOUT = -4
 GSFIT_ERR_NONFINITE = -5
 GSFIT_TILE = 16
 GSFIT_MAX_VIEWS = 256
-GSFIT_TILE_ORDER_EXTRA = 1  # words after the tile permutation: the number of non-empty tiles
+
+
+def tile_order_words(total_tiles: int) -> int:
+    """GSFIT_TILE_ORDER_WORDS: the heavy-first permutation, the number of
+    non-empty tiles, each tile's furthest contributor, the adjoint's launch
+    order and the count again."""
+    return 3 * int(total_tiles) + 2
+
 
 _P = ctypes.c_void_p
 _i32 = ctypes.c_int32
@@ -37,7 +44,7 @@ class Gaussians(ctypes.Structure):
                 ("reserved", _i32)]
 
 
-ABI_VERSION = 6  # GSFIT_ABI_VERSION of include/gsfit.h
+ABI_VERSION = 7  # GSFIT_ABI_VERSION of include/gsfit.h
 
 # gsfit_gaussians.feature_dtype values (GSFIT_FEATURES_*)
 FEATURES = {"f32": 0, "f16": 1, "bf16": 2}

@@ -1,10 +1,15 @@
-"""Empty tiles in the compositing launches: with a tile order, the CTAs past
-its non-empty count leave before any setup (the forward pass after writing
-the background into its tile). What must hold: the forward outputs equal
+"""The tile order's use in the compositing launches. With an order, the CTAs
+past its non-empty count leave before any setup (the forward pass after
+writing the background into its tile); the forward pass records each
+non-empty tile's furthest contributor, and the adjoint launches the
+non-empty tiles sorted by it. What must hold: the forward outputs equal
 those of the launch without an order, which composites every tile in full,
 bit for bit (each pixel's sum runs in its own list order either way); the
 adjoint's 2D gradients equal them up to the order of their float atomics;
-and an empty tile holds the background, alpha 0, T 1 and no contributor."""
+an empty tile holds the background, alpha 0, T 1 and no contributor; the
+recorded contributor is the tile's largest n_contrib; and the adjoint's
+order is a permutation of the non-empty tiles in descending quarter octaves
+of it."""
 import numpy as np
 import pytest
 
@@ -102,6 +107,7 @@ def test_adjoint_with_order_matches_unordered_launch(tile):
     st.blend_bwd()
     torch.cuda.synchronize()
     got = st.grad2d.cpu().numpy().copy()
+    _check_adjoint_order(st, cams, tile)
     st.grad2d.zero_()
     G.gsfit_blend_bwd(st.proj, st.cams_dev, st.V, st.n, st.T, st.vals, st.ranges, st.bg, st.T_final, st.n_contrib,
                       st.dL_drgb, st.dL_dalpha, st.grad2d, None, None, st.status, st.opts)
@@ -110,3 +116,48 @@ def test_adjoint_with_order_matches_unordered_launch(tile):
     ref = st.grad2d.cpu().numpy()
     assert np.abs(ref).max() > 0
     np.testing.assert_allclose(got, ref, rtol=1e-5, atol=1e-6 * np.abs(ref).max())
+
+
+def _tile_max_contrib(st, cams, tile):
+    """The largest n_contrib of each tile's pixels (host)."""
+    nc = st.n_contrib.cpu().numpy().view(np.uint32).astype(np.int64)
+    out, off = [], 0
+    for W, H in zip(cams["width"].astype(np.int64), cams["height"].astype(np.int64)):
+        tx, ty = -(-W // tile), -(-H // tile)
+        pad = np.zeros((ty * tile, tx * tile), np.int64)
+        pad[:H, :W] = nc[off:off + W * H].reshape(H, W)
+        out.append(pad.reshape(ty, tile, tx, tile).max(axis=(1, 3)).reshape(-1))
+        off += W * H
+    return np.concatenate(out)
+
+
+def _bucket(m):
+    """Quarter octave of m + 1 (floor of 4 log2, from the two bits below the leading one)."""
+    x = np.asarray(m, np.int64) + 1
+    l = np.floor(np.log2(x)).astype(np.int64)
+    f = np.where(l >= 2, (x >> np.maximum(l - 2, 0)) & 3, (x << np.maximum(2 - l, 0)) & 3)
+    return 4 * l + f
+
+
+def _check_adjoint_order(st, cams, tile):
+    T = st.T
+    words = st.tile_order.cpu().numpy().view(np.uint32).astype(np.int64)
+    assert len(words) == 3 * T + 2
+    n_work = int(words[T])
+    key = words[T + 1:2 * T + 1]
+    nonempty = words[:n_work]
+    np.testing.assert_array_equal(key[nonempty], _tile_max_contrib(st, cams, tile)[nonempty])
+    adj = words[2 * T + 1:2 * T + 1 + n_work]
+    assert words[3 * T + 1] == n_work
+    np.testing.assert_array_equal(np.sort(adj), np.sort(nonempty))
+    assert np.all(np.diff(_bucket(key[adj])) <= 0)
+
+
+def test_contributor_bucket_matches_its_definition():
+    """The host restatement of the quarter-octave bucket used above, against
+    4 floor(log2(m + 1)) + the two bits below the leading one, by brute force."""
+    for m in list(range(0, 300)) + [1000, 4095, 4096, 65535, 10 ** 6]:
+        x = m + 1
+        l = x.bit_length() - 1
+        f = (x >> (l - 2)) & 3 if l >= 2 else (x << (2 - l)) & 3
+        assert _bucket(m) == 4 * l + f
