@@ -241,8 +241,10 @@ size_t gsfit_bin_sort_workspace_size(int64_t n_records, int64_t capacity, int32_
  *   is empty) and to GSFIT_ERR_TIMEOUT if a bounded wait of the sort ran out;
  *   it is not cleared by this call. tile_order (device uint32,
  *   GSFIT_TILE_ORDER_WORDS(total_tiles) entries, may be null), with
- *   T = total_tiles: entries [0, T) a permutation of the tiles, longest lists
- *   first (bucketed by log2 of the list length, any order within a bucket),
+ *   T = total_tiles: entries [0, T) a permutation of the tiles, most work
+ *   first (bucketed by quarter octaves of the furthest contributor the last
+ *   gsfit_render_fwd recorded in this buffer, capped at the list length, or
+ *   of the list length where it recorded none; any order within a bucket),
  *   so the non-empty tiles lead; entry T the number of non-empty tiles;
  *   entries [T + 1, 2T + 1) each tile's furthest contributor, set to zero
  *   here and written by gsfit_render_fwd; entries [2T + 1, 3T + 1) the

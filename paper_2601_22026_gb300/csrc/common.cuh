@@ -126,6 +126,19 @@ __device__ __forceinline__ void load_cameras(gsfit_camera* dst, const gsfit_came
     for (int k = threadIdx.x; k < words; k += blockDim.x) d[k] = s[k];
 }
 
+// Work buckets of the tile orders: quarter octaves of a count.
+constexpr int kOrderBuckets = 128;
+
+// Quarter octave of a count m: 4 floor(log2(m + 1)) plus the two bits below
+// the leading one of m + 1, capped at 127 (the tile orders' work buckets).
+__device__ __forceinline__ int quarter_octave(uint32_t m) {
+    if (m >= 0x40000000u) return 127;
+    const uint32_t x = m + 1u;
+    const int l = 31 - __clz(x);  // floor(log2 x)
+    const int f = l >= 2 ? (int)((x >> (l - 2)) & 3u) : (int)((x << (2 - l)) & 3u);
+    return 4 * l + f;
+}
+
 // Tile edge of a camera's batch layout: 8 or 16 (16 for any other value).
 __device__ __forceinline__ int tile_of(const gsfit_camera& c) { return c.tile == 8 ? 8 : 16; }
 __device__ __forceinline__ int tiles_x_of(const gsfit_camera& c) {

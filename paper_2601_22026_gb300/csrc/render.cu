@@ -812,17 +812,8 @@ __global__ void splat_power_selftest_kernel(const float4* __restrict__ conic, co
 // a histogram of the buckets in shared memory, its exclusive scan from the
 // top bucket down, then each tile placed at its bucket's next position
 // (any order within a bucket).
-constexpr int kOrderBuckets = 128;    // quarter octaves of a 32-bit count
 constexpr int kOrderThreads = 1024;
 constexpr int kOrderItems = 8;        // tiles per thread and round, loaded together
-
-__device__ __forceinline__ int contributor_bucket(uint32_t m) {
-    if (m >= 0x40000000u) return kOrderBuckets - 1;
-    const uint32_t x = m + 1u;
-    const int l = 31 - __clz(x);  // floor(log2 x)
-    const int f = l >= 2 ? (int)((x >> (l - 2)) & 3u) : (int)((x << (2 - l)) & 3u);
-    return 4 * l + f;
-}
 
 __global__ void __launch_bounds__(kOrderThreads) adjoint_order_kernel(uint32_t* __restrict__ tile_order,
                                                                       int total_tiles) {
@@ -843,7 +834,7 @@ __global__ void __launch_bounds__(kOrderThreads) adjoint_order_kernel(uint32_t* 
                 t[j] = k < n_work ? tile_order[k] : T;
             }
 #pragma unroll
-            for (int j = 0; j < kOrderItems; ++j) b[j] = t[j] < T ? contributor_bucket(key[t[j]]) : -1;
+            for (int j = 0; j < kOrderItems; ++j) b[j] = t[j] < T ? quarter_octave(key[t[j]]) : -1;
 #pragma unroll
             for (int j = 0; j < kOrderItems; ++j) {
                 if (b[j] < 0) continue;

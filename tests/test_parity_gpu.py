@@ -163,13 +163,15 @@ def test_keys_sort_ranges_bit_exact(name):
     assert len(rk) > 0
     np.testing.assert_array_equal(gk, ok_)
     np.testing.assert_array_equal(gv, ov)
-    # heavy-first order: a permutation with non-increasing log2 lengths, then
-    # the number of non-empty tiles (which lead it)
+    # heavy-first order of a fresh state (no contributors recorded yet): a
+    # permutation with non-increasing quarter octaves of the list length, the
+    # empty tiles last, then the number of non-empty tiles
     words = st.tile_order.cpu().numpy().view(np.uint32).astype(np.int64)
     order = words[:len(ranges)]
     assert np.array_equal(np.sort(order), np.arange(len(ranges)))
     lens = (ranges[:, 1].astype(np.int64) - ranges[:, 0].astype(np.int64))[order]
-    buckets = np.floor(np.log2(lens + 1)).astype(np.int64)
+    from test_tile_order_gpu import _bucket
+    buckets = np.where(lens > 0, 1 + _bucket(lens), 0)
     assert np.all(np.diff(buckets) <= 0)
     assert words[len(ranges)] == np.count_nonzero(lens) and np.all(lens[:words[len(ranges)]] > 0)
     bad = np.array(sorted(bad_g | bad_o), dtype=np.int64)

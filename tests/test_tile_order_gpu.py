@@ -161,3 +161,35 @@ def test_contributor_bucket_matches_its_definition():
         l = x.bit_length() - 1
         f = (x >> (l - 2)) & 3 if l >= 2 else (x << (2 - l)) & 3
         assert _bucket(m) == 4 * l + f
+
+
+def test_next_order_follows_the_recorded_contributors():
+    """bin_sort of the next iteration orders the non-empty tiles by the
+    furthest contributor the forward pass recorded (capped at the new list
+    length; the length where none was recorded), the empty tiles last, and
+    zeroes the recorded words for the next forward pass."""
+    gs, cams = _case("clustered")
+    bg = scenes.backgrounds(len(cams["width"]), 8)
+    st = _state(gs, cams, bg)
+    st.forward()
+    torch.cuda.synchronize()
+    T = st.T
+    key = st.tile_order.cpu().numpy().view(np.uint32)[T + 1:2 * T + 1].astype(np.int64).copy()
+    assert key.max() > 0
+    gs2 = dict(gs)
+    gs2["means"] = (gs["means"] + np.float32(0.01)).astype(np.float32)  # the next iteration's scene, moved a little
+    from paper_2601_22026_gb300 import gsfit as G
+    st.params.copy_(torch.from_numpy(G.pack_params(gs2)).to(st.params.device))
+    st.project()
+    st.bin_sort()
+    torch.cuda.synchronize()
+    words = st.tile_order.cpu().numpy().view(np.uint32).astype(np.int64)
+    ranges = st.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2).astype(np.int64)
+    lens = ranges[:, 1] - ranges[:, 0]
+    order = words[:T]
+    assert np.array_equal(np.sort(order), np.arange(T))
+    work = np.where((key > 0) & (key < lens), key, lens)[order]
+    buckets = np.where(lens[order] > 0, np.minimum(127, 1 + _bucket(work)), 0)
+    assert np.all(np.diff(buckets) <= 0)
+    assert words[T] == np.count_nonzero(lens)
+    assert np.all(words[T + 1:2 * T + 1] == 0)
