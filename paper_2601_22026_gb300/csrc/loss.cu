@@ -173,6 +173,28 @@ __device__ __forceinline__ void prefetch_item(LossSmem& S, const gsfit_camera* _
     asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
 
+// Adds the block's sums of the three loss terms to a view's accumulators
+// (sum |x - y|, sum SSIM, sum |A - A*|); ends with a barrier.
+__device__ __forceinline__ void block_loss_sums(float (&s_red)[3][kLossThreads / 32], float* acc_v, float l1,
+                                                float ssim_sum, float la) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    ssim_sum = warp_sum(ssim_sum);
+    l1 = warp_sum(l1);
+    la = warp_sum(la);
+    if (lane == 0) {
+        s_red[0][wid] = l1;
+        s_red[1][wid] = ssim_sum;
+        s_red[2][wid] = la;
+    }
+    __syncthreads();
+    if (tid < 3) {
+        float sacc = 0.f;
+        for (int k = 0; k < kLossThreads / 32; ++k) sacc += s_red[tid][k];
+        atomicAdd(&acc_v[tid], sacc);
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(kLossThreads, kLossCtasPerSm) loss_kernel(
     const gsfit_camera* __restrict__ cams_g, int n_views, const float* __restrict__ rgb,
     const float* __restrict__ alpha, const float* __restrict__ t_rgb, const float* __restrict__ t_alpha,
@@ -212,24 +234,61 @@ __global__ void __launch_bounds__(kLossThreads, kLossCtasPerSm) loss_kernel(
         const float inv3PV = 1.0f / (3.0f * (float)P * (float)n_views);
 
         // 1. the copied inputs: target composited over the background (zero
-        //    outside the image)
+        //    outside the image); and whether render and target agree over the
+        //    whole region
         asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         __syncthreads();
+        bool differ = false;
         if (ox >= 10 && oy >= 10 && ox + kOut + 10 <= W && oy + kOut + 10 <= H) {  // the region lies inside
             float2* xyf = &S.a.xy[0][0];
             const float* af = &S.b.st.at[0][0];
-            for (int k = tid; k < kR2 * kR2; k += kLossThreads) xyf[k].y += (1.0f - af[k]) * bgc;
+            for (int k = tid; k < kR2 * kR2; k += kLossThreads) {
+                const float yv = xyf[k].y + (1.0f - af[k]) * bgc;
+                xyf[k].y = yv;
+                differ = differ || !(xyf[k].x == yv);
+            }
         } else {
             for (int r = wid; r < kR2; r += kLossThreads / 32) {
                 const int gy = oy - 10 + r;
                 for (int c = lane; c < kR2; c += 32) {
                     const int gx = ox - 10 + c;
                     const bool ok = gx >= 0 && gx < W && gy >= 0 && gy < H;
-                    S.a.xy[r][c].y = ok ? S.a.xy[r][c].y + (1.0f - S.b.st.at[r][c]) * bgc : 0.0f;
+                    const float yv = ok ? S.a.xy[r][c].y + (1.0f - S.b.st.at[r][c]) * bgc : 0.0f;
+                    S.a.xy[r][c].y = yv;
+                    differ = differ || !(S.a.xy[r][c].x == yv);
                 }
             }
         }
-        __syncthreads();
+        // Render and target equal over the whole input region (the tile and
+        // the 10-pixel reach of a gradient: windows of radius 5 around pixels
+        // within 5): every window in play has x = y, so SSIM 1 there, and
+        // zero gradient (SSIM(., y) is largest at y, and the L1 subgradient
+        // at 0 is 0). The item then needs no stencil: the exact results are
+        // written directly (the stencil would give them up to rounding). In a
+        // periphery batch this is every item inside the background around
+        // the splats, where both are the background colour bit for bit.
+        if (__syncthreads_or(differ) == 0) {
+            // the input region is no longer read: copy the next item's inputs
+            if (next < n_items) prefetch_item(S, cams_g, next, s_view, s_first, rgb, t_rgb, t_alpha);
+            float ssim_n = 0.f, la = 0.f;
+            const int cidx = tid % kOut, r0 = (tid / kOut) * 4;
+#pragma unroll
+            for (int o = 0; o < 4; ++o) {
+                const int gy = oy + r0 + o, gx = ox + cidx;
+                if (gy >= H || gx >= W) continue;
+                const long long q = (long long)gy * W + gx;
+                g_rgb[3ll * cam.pixel_offset + ch * P + q] = 0.0f;
+                ssim_n += 1.0f;
+                if (ch == 0) {
+                    const float da = alpha[cam.pixel_offset + q] - At[q];
+                    la += fabsf(da);
+                    g_alpha[cam.pixel_offset + q] =
+                        (da > 0.f ? 1.f : (da < 0.f ? -1.f : 0.f)) / ((float)P * (float)n_views);
+                }
+            }
+            block_loss_sums(s_red, acc + 3 * v, 0.f, ssim_n, la);
+            continue;
+        }
         // 2. horizontal pass of x, y, x^2 + y^2, xy: 52 rows x 42 columns in
         //    strips of 3 (728 strips: 95% of the threads busy over three
         //    rounds); and a copy of the output pixels
@@ -350,22 +409,7 @@ __global__ void __launch_bounds__(kLossThreads, kLossCtasPerSm) loss_kernel(
                 }
             }
         }
-        // block sums of the loss terms
-        ssim_sum = warp_sum(ssim_sum);
-        l1 = warp_sum(l1);
-        la = warp_sum(la);
-        if (lane == 0) {
-            s_red[0][wid] = l1;
-            s_red[1][wid] = ssim_sum;
-            s_red[2][wid] = la;
-        }
-        __syncthreads();
-        if (tid < 3) {
-            float sacc = 0.f;
-            for (int k = 0; k < kLossThreads / 32; ++k) sacc += s_red[tid][k];
-            atomicAdd(&acc[3 * v + tid], sacc);
-        }
-        __syncthreads();
+        block_loss_sums(s_red, acc + 3 * v, l1, ssim_sum, la);
     }
 }
 

@@ -458,6 +458,76 @@ def test_loss_matches_oracle():
     np.testing.assert_allclose(d_a.cpu().numpy(), ga, rtol=1e-6, atol=1e-12)
 
 
+def test_loss_with_matching_regions_matches_oracle():
+    """Images whose render equals the composited target over large regions
+    (the background around the splats of a periphery batch), where the loss
+    kernel skips the SSIM stencil: exact equality in both precisions (target
+    alpha 0, target colour 0 and the render the background; or target alpha 1
+    and target colour the render), the render's alpha different from the
+    target's there (its L1 term still counts). Against the oracle as above,
+    and the colour gradient exactly zero on output tiles whose whole input
+    region matches."""
+    cams = scenes.stack_cameras([scenes.make_camera((0, 0, 3), (0, 0, 0), w, h, fx=50.0)
+                                 for w, h in [(160, 128), (45, 37), (97, 61)]])
+    V = 3
+    g = scenes.rng(35)
+    img = scenes.smooth_images(cams, 36, channels=4)
+    tgt = scenes.smooth_images(cams, 37, channels=4)
+    bg = scenes.backgrounds(V, 38)
+    off = oracle.pixel_offsets(cams)
+    rgb, alpha, trgb, talpha, match = [], [], [], [], []
+    for v in range(V):
+        W, H = int(cams["width"][v]), int(cams["height"][v])
+        P = W * H
+        a = img[4 * off[v]:4 * off[v + 1]].copy()
+        b = tgt[4 * off[v]:4 * off[v + 1]].copy()
+        x, A = a[:3 * P].reshape(3, H, W), a[3 * P:].reshape(H, W)
+        y, At = b[:3 * P].reshape(3, H, W), b[3 * P:].reshape(H, W)
+        x += g.normal(0, 0.05, x.shape).astype(np.float32)
+        cols = np.arange(W)[None, :].repeat(H, 0)
+        bgm = cols < int(0.6 * W)                                   # background kind
+        opq = (cols >= int(0.8 * W)) & (np.arange(H)[:, None] < H // 2)  # opaque kind
+        for ch in range(3):
+            x[ch][bgm] = np.float32(bg[v, ch])
+            y[ch][bgm] = 0.0
+            y[ch][opq] = x[ch][opq]
+        At[bgm] = 0.0
+        At[opq] = 1.0
+        A[bgm | opq] = np.float32(0.6)
+        rgb.append(x.reshape(-1)); alpha.append(A.reshape(-1)); trgb.append(y.reshape(-1)); talpha.append(At.reshape(-1))
+        match.append(bgm | opq)
+    rgb, alpha, trgb, talpha = map(np.concatenate, (rgb, alpha, trgb, talpha))
+    from paper_2601_22026_gb300 import gsfit as G
+    table = G.camera_table(cams)
+    cams_dev = G.cameras_to_device(table)
+    t = lambda z: torch.from_numpy(np.ascontiguousarray(z, np.float32)).cuda()
+    d_rgb, d_a = torch.zeros(3 * table.total_pixels, device="cuda"), torch.zeros(table.total_pixels, device="cuda")
+    L = torch.zeros(1, device="cuda")
+    ws = torch.zeros(G.gsfit_loss_workspace_size(V) // 4, device="cuda")
+    G.gsfit_loss(cams_dev, V, t(rgb), t(alpha), t(trgb), t(talpha), t(bg), 0.2, d_rgb, d_a, L, ws)
+    torch.cuda.synchronize()
+    Lr, gr, ga, _ = oracle.loss(rgb, alpha, trgb, talpha, bg, cams)
+    assert float(L.item()) == pytest.approx(Lr, rel=2e-5)
+    gg = d_rgb.cpu().numpy()
+    assert np.abs(gg - gr).max() <= 1e-3 * np.abs(gr).max()
+    np.testing.assert_allclose(d_a.cpu().numpy(), ga, rtol=1e-6, atol=1e-12)
+    # output tiles whose 52 x 52 input region (zero outside the image) matches: exactly zero
+    skipped = 0
+    for v in range(V):
+        W, H = int(cams["width"][v]), int(cams["height"][v])
+        m = np.pad(match[v], 10, constant_values=True)
+        for oy in range(0, H, 32):
+            for ox in range(0, W, 32):
+                if m[oy:oy + 52, ox:ox + 52].all():
+                    for ch in range(3):
+                        blk = gg[3 * off[v] + ch * W * H:3 * off[v] + (ch + 1) * W * H].reshape(H, W)
+                        assert np.all(blk[oy:oy + 32, ox:ox + 32] == 0.0)
+                        ref = gr[3 * off[v] + ch * W * H:3 * off[v] + (ch + 1) * W * H].reshape(H, W)
+                        assert np.abs(ref[oy:oy + 32, ox:ox + 32]).max() <= 1e-9 * np.abs(gr).max()
+                    skipped += 1
+    assert skipped >= 6
+
+
 def test_adam_matches_oracle():
     from paper_2601_22026_gb300 import gsfit as G
     n, deg = 1003, 1
