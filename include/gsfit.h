@@ -336,7 +336,10 @@ int gsfit_render_fwd(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n
  *   SSIM with an 11 x 11 Gaussian window (sigma 1.5), zero padding, C1 =
  *   0.01^2, C2 = 0.03^2, averaged over channels and pixels (3DGS). Writes
  *   dL/drgb and dL/dalpha (the L1 subgradient at 0 is 0) and, if loss_out is
- *   not null, the scalar loss (device float).
+ *   not null, the scalar loss (device float). Where render and composited
+ *   target are equal (in float32) over a 32 x 32 output tile and the 10
+ *   pixels around it, the windows there have SSIM 1 and the colour gradient
+ *   is zero: such tiles are written directly, without the SSIM stencil.
  * Arguments: images in the packed layout (device); ws: device workspace of
  *   gsfit_loss_workspace_size(n_views) bytes.
  * Errors: GSFIT_ERR_INVALID_ARG, GSFIT_ERR_CUDA.
