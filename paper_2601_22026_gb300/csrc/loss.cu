@@ -173,6 +173,14 @@ __device__ __forceinline__ void prefetch_item(LossSmem& S, const gsfit_camera* _
     asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
 
+// Whether a view's rows can be read in 16-byte pieces: width and pixel offset
+// multiples of 4 (so every channel plane and row starts 16-byte aligned, and
+// a 4-pixel piece starting at a multiple of 4 lies wholly inside or outside
+// the image), and the three input arrays 16-byte aligned.
+__device__ __forceinline__ bool rows16(const gsfit_camera& cam, bool bases16) {
+    return bases16 && (cam.width & 3) == 0 && (cam.pixel_offset & 3) == 0;
+}
+
 // Adds the block's sums of the three loss terms to a view's accumulators
 // (sum |x - y|, sum SSIM, sum |A - A*|); ends with a barrier.
 __device__ __forceinline__ void block_loss_sums(float (&s_red)[3][kLossThreads / 32], float* acc_v, float l1,
@@ -214,7 +222,10 @@ __global__ void __launch_bounds__(kLossThreads, kLossCtasPerSm) loss_kernel(
     // horizontal-pass buffer free).
     if (tid == 0 && (int)blockIdx.x < n_items) locate_item(cams_g, blockIdx.x, s_view, s_first);
     __syncthreads();
-    if ((int)blockIdx.x < n_items) prefetch_item(S, cams_g, blockIdx.x, s_view, s_first, rgb, t_rgb, t_alpha);
+    const bool bases16 = ((reinterpret_cast<uintptr_t>(rgb) | reinterpret_cast<uintptr_t>(t_rgb) |
+                           reinterpret_cast<uintptr_t>(t_alpha)) & 15u) == 0;
+    if ((int)blockIdx.x < n_items && !rows16(cams_g[s_view], bases16))
+        prefetch_item(S, cams_g, blockIdx.x, s_view, s_first, rgb, t_rgb, t_alpha);
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int v = s_view;
         const int first = s_first;
@@ -233,29 +244,62 @@ __global__ void __launch_bounds__(kLossThreads, kLossCtasPerSm) loss_kernel(
         const float bgc = bg[3 * v + ch];
         const float inv3PV = 1.0f / (3.0f * (float)P * (float)n_views);
 
-        // 1. the copied inputs: target composited over the background (zero
-        //    outside the image); and whether render and target agree over the
-        //    whole region
-        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-        __syncthreads();
+        // 1. the inputs: target composited over the background (zero outside
+        //    the image); and whether render and target agree over the whole
+        //    region
         bool differ = false;
-        if (ox >= 10 && oy >= 10 && ox + kOut + 10 <= W && oy + kOut + 10 <= H) {  // the region lies inside
-            float2* xyf = &S.a.xy[0][0];
-            const float* af = &S.b.st.at[0][0];
-            for (int k = tid; k < kR2 * kR2; k += kLossThreads) {
-                const float yv = xyf[k].y + (1.0f - af[k]) * bgc;
-                xyf[k].y = yv;
-                differ = differ || !(xyf[k].x == yv);
+        if (rows16(cam, bases16)) {
+            // 16-byte loads into registers, the composite and the comparison
+            // there, then the region into shared memory as (x, y) pairs: the
+            // window is read 2 columns wider on each side (columns ox - 12 ..
+            // ox + 43, 14 pieces of 4 per row) so that every piece is aligned;
+            // comparing the extra columns only makes the agreement test
+            // stricter. No copy into shared memory is pending for such a view
+            // (none is started for it).
+            constexpr int kPC = 14, kPN = kR2 * kPC;
+            static_assert(4 * kPC == kR2 + 4, "pieces cover the region and 2 columns each side");
+            const float* X = rgb + 3ll * cam.pixel_offset + ch * P;
+            const float* Yt = t_rgb + 3ll * cam.pixel_offset + ch * P;
+            for (int k = tid; k < kPN; k += kLossThreads) {
+                const int r = k / kPC, pq = k - r * kPC;
+                const int gy = oy - 10 + r, gx = ox - 12 + 4 * pq;
+                const bool ok = gy >= 0 && gy < H && gx >= 0 && gx < W;
+                float4 xv = make_float4(0.f, 0.f, 0.f, 0.f), yv = xv;
+                if (ok) {
+                    const long long o = (long long)gy * W + gx;
+                    xv = __ldg(reinterpret_cast<const float4*>(X + o));
+                    const float4 t = __ldg(reinterpret_cast<const float4*>(Yt + o));
+                    const float4 a = __ldg(reinterpret_cast<const float4*>(At + o));
+                    yv = make_float4(t.x + (1.0f - a.x) * bgc, t.y + (1.0f - a.y) * bgc, t.z + (1.0f - a.z) * bgc,
+                                     t.w + (1.0f - a.w) * bgc);
+                }
+                differ = differ || !(xv.x == yv.x) || !(xv.y == yv.y) || !(xv.z == yv.z) || !(xv.w == yv.w);
+                const int c = 4 * pq - 2;  // shared-memory column of the piece's first pixel
+                if (c >= 0) *reinterpret_cast<float4*>(&S.a.xy[r][c]) = make_float4(xv.x, yv.x, xv.y, yv.y);
+                if (c + 2 < kR2) *reinterpret_cast<float4*>(&S.a.xy[r][c + 2]) = make_float4(xv.z, yv.z, xv.w, yv.w);
             }
         } else {
-            for (int r = wid; r < kR2; r += kLossThreads / 32) {
-                const int gy = oy - 10 + r;
-                for (int c = lane; c < kR2; c += 32) {
-                    const int gx = ox - 10 + c;
-                    const bool ok = gx >= 0 && gx < W && gy >= 0 && gy < H;
-                    const float yv = ok ? S.a.xy[r][c].y + (1.0f - S.b.st.at[r][c]) * bgc : 0.0f;
-                    S.a.xy[r][c].y = yv;
-                    differ = differ || !(S.a.xy[r][c].x == yv);
+            // the copies started while the previous item finished
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+            __syncthreads();  // block-uniform branch: the view decides it
+            if (ox >= 10 && oy >= 10 && ox + kOut + 10 <= W && oy + kOut + 10 <= H) {  // the region lies inside
+                float2* xyf = &S.a.xy[0][0];
+                const float* af = &S.b.st.at[0][0];
+                for (int k = tid; k < kR2 * kR2; k += kLossThreads) {
+                    const float yv = xyf[k].y + (1.0f - af[k]) * bgc;
+                    xyf[k].y = yv;
+                    differ = differ || !(xyf[k].x == yv);
+                }
+            } else {
+                for (int r = wid; r < kR2; r += kLossThreads / 32) {
+                    const int gy = oy - 10 + r;
+                    for (int c = lane; c < kR2; c += 32) {
+                        const int gx = ox - 10 + c;
+                        const bool ok = gx >= 0 && gx < W && gy >= 0 && gy < H;
+                        const float yv = ok ? S.a.xy[r][c].y + (1.0f - S.b.st.at[r][c]) * bgc : 0.0f;
+                        S.a.xy[r][c].y = yv;
+                        differ = differ || !(S.a.xy[r][c].x == yv);
+                    }
                 }
             }
         }
@@ -269,7 +313,8 @@ __global__ void __launch_bounds__(kLossThreads, kLossCtasPerSm) loss_kernel(
         // the splats, where both are the background colour bit for bit.
         if (__syncthreads_or(differ) == 0) {
             // the input region is no longer read: copy the next item's inputs
-            if (next < n_items) prefetch_item(S, cams_g, next, s_view, s_first, rgb, t_rgb, t_alpha);
+            if (next < n_items && !rows16(cams_g[s_view], bases16))
+                prefetch_item(S, cams_g, next, s_view, s_first, rgb, t_rgb, t_alpha);
             float ssim_n = 0.f, la = 0.f;
             const int cidx = tid % kOut, r0 = (tid / kOut) * 4;
 #pragma unroll
@@ -375,7 +420,8 @@ __global__ void __launch_bounds__(kLossThreads, kLossCtasPerSm) loss_kernel(
         }
         __syncthreads();
         // the input region and the alpha buffer are free: copy the next item's inputs
-        if (next < n_items) prefetch_item(S, cams_g, next, s_view, s_first, rgb, t_rgb, t_alpha);
+        if (next < n_items && !rows16(cams_g[s_view], bases16))
+            prefetch_item(S, cams_g, next, s_view, s_first, rgb, t_rgb, t_alpha);
         // 5. vertical pass onto the tile (a 4-pixel column strip per thread) and
         //    the gradient
         float l1 = 0.f, la = 0.f;

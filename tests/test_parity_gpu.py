@@ -421,11 +421,21 @@ def test_autograd_function_matches_oracle():
     _grad_check(gpu, ref["grads"], amb)
 
 
-def test_loss_matches_oracle():
+LOSS_VIEWS = {
     # ragged views; the 128 x 96 view has tiles whose 52 x 52 input region lies inside the image (the
-    # kernel's path without per-element bounds tests), the others only border tiles
+    # kernel's copy without per-element bounds tests), the others only border tiles; no view's rows are
+    # 16-byte aligned (the first is 45 wide, every later one starts at an odd pixel offset)
+    "copied": [(45, 37), (64, 64), (100, 33), (7, 5), (128, 96)],
+    # the same sizes with the 128 x 96 and 64 x 64 views first: their rows are 16-byte aligned (width and
+    # pixel offset multiples of 4), read with 16-byte loads into registers; interior and border tiles
+    "rows16": [(128, 96), (64, 64), (45, 37), (100, 33), (7, 5)],
+}
+
+
+@pytest.mark.parametrize("layout", list(LOSS_VIEWS))
+def test_loss_matches_oracle(layout):
     cams = scenes.stack_cameras([scenes.make_camera((0, 0, 3), (0, 0, 0), w, h, fx=50.0)
-                                 for w, h in [(45, 37), (64, 64), (100, 33), (7, 5), (128, 96)]])
+                                 for w, h in LOSS_VIEWS[layout]])
     V = 5
     g = scenes.rng(31)
     img = scenes.smooth_images(cams, 32, channels=4)
