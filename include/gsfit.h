@@ -60,7 +60,7 @@
 extern "C" {
 #endif
 
-#define GSFIT_ABI_VERSION 7
+#define GSFIT_ABI_VERSION 8
 #define GSFIT_MAX_VIEWS 256
 #define GSFIT_TILE 16
 /* Words of a tile_order buffer for total_tiles tiles (gsfit_bin_sort):
@@ -340,11 +340,19 @@ int gsfit_render_fwd(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n
  *   target are equal (in float32) over a 32 x 32 output tile and the 10
  *   pixels around it, the windows there have SSIM 1 and the colour gradient
  *   is zero: such tiles are written directly, without the SSIM stencil.
- * Arguments: images in the packed layout (device); ws: device workspace of
- *   gsfit_loss_workspace_size(n_views) bytes.
+ *   With a workspace of gsfit_loss_workspace_size(cams, n_views) bytes a
+ *   pre-pass first records, per 16 x 16 pixel block and channel, whether
+ *   render and target agree over the block, and tiles whose surrounding
+ *   blocks all agree are settled without loading their inputs; with the
+ *   accumulators only (gsfit_loss_workspace_size(NULL, n_views) bytes) every
+ *   tile tests its own region. The results are the same.
+ * Arguments: images in the packed layout (device); ws: device workspace of at
+ *   least gsfit_loss_workspace_size(NULL, n_views) bytes; cams of the size
+ *   query: the host copy of the camera table (as gsfit_camera_layout fills
+ *   it), or NULL for the accumulators only.
  * Errors: GSFIT_ERR_INVALID_ARG, GSFIT_ERR_CUDA.
  */
-size_t gsfit_loss_workspace_size(int32_t n_views);
+size_t gsfit_loss_workspace_size(const gsfit_camera* cams, int32_t n_views);
 int gsfit_loss(const gsfit_camera* cams, int32_t n_views, const float* rgb, const float* alpha,
                const float* target_rgb, const float* target_alpha, const float* bg, float lambda,
                float* dL_drgb, float* dL_dalpha, float* loss_out, void* ws, size_t ws_bytes,

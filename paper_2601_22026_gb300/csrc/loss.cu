@@ -107,15 +107,139 @@ __device__ __forceinline__ void strip11x2(const float* a, const float* b, float2
     }
 }
 
-// The view owning work item `item` and the index of that view's first item.
-__device__ __forceinline__ void locate_item(const gsfit_camera* __restrict__ cams, int item, int& v, int& first) {
+// Edge of the blocks whose agreement the match pre-pass records (per channel).
+constexpr int kBlk = 16;
+
+__host__ __device__ inline int blocks_of(const gsfit_camera& c) {
+    return ((c.width + kBlk - 1) / kBlk) * ((c.height + kBlk - 1) / kBlk);
+}
+
+// Loss workspace: the per-view accumulators, then (when the workspace holds
+// them) one agreement byte per 16-pixel block and channel.
+__host__ __device__ inline size_t flags_offset(int n_views) { return ((size_t)n_views * 3 * sizeof(float) + 255) & ~(size_t)255; }
+
+// The view owning work item `item`, the index of that view's first item and
+// of its first 16-pixel block.
+__device__ __forceinline__ void locate_item(const gsfit_camera* __restrict__ cams, int item, int& v, int& first,
+                                            int& boff) {
     v = 0;
     first = 0;
+    boff = 0;
     for (;; ++v) {
         const int k = 3 * ((cams[v].width + kOut - 1) / kOut) * ((cams[v].height + kOut - 1) / kOut);
         if (item < first + k) break;
         first += k;
+        boff += blocks_of(cams[v]);
     }
+}
+
+// Whether a view's rows can be read in 16-byte pieces: width and pixel offset
+// multiples of 4 (so every channel plane and row starts 16-byte aligned, and
+// a 4-pixel piece starting at a multiple of 4 lies wholly inside or outside
+// the image), and the three input arrays 16-byte aligned.
+__device__ __forceinline__ bool rows16(const gsfit_camera& cam, bool bases16) {
+    return bases16 && (cam.width & 3) == 0 && (cam.pixel_offset & 3) == 0;
+}
+
+// The match pre-pass: for every 16 x 16 pixel block and colour channel,
+// whether the render equals the target composited over the background
+// (the same expression as the loss kernel's) at every pixel of the block. One
+// warp per block (lane l: row l / 2, eight pixels from column 8 (l mod 2)),
+// the loads coalesced in 64-byte row pieces, 16-byte loads where the view's
+// rows allow them (all seven maps of a piece in flight together); the whole
+// images are read once.
+__global__ void __launch_bounds__(256) match_kernel(const gsfit_camera* __restrict__ cams_g, int n_views,
+                                                    const float* __restrict__ rgb, const float* __restrict__ t_rgb,
+                                                    const float* __restrict__ t_alpha, const float* __restrict__ bg,
+                                                    uint8_t* __restrict__ flags, size_t flag_bytes) {
+    int n_blocks = 0;
+    for (int v = 0; v < n_views; ++v) n_blocks += blocks_of(cams_g[v]);
+    if (3 * (size_t)n_blocks > flag_bytes) return;  // no room: the loss kernel then tests every item itself
+    const bool bases16 = ((reinterpret_cast<uintptr_t>(rgb) | reinterpret_cast<uintptr_t>(t_rgb) |
+                           reinterpret_cast<uintptr_t>(t_alpha)) & 15u) == 0;
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x / 32);
+    for (int b = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); b < n_blocks; b += warps) {
+        int v = 0, base = 0;
+        for (;; ++v) {  // the block's view (warp-uniform)
+            const int nb = blocks_of(cams_g[v]);
+            if (b < base + nb) break;
+            base += nb;
+        }
+        const gsfit_camera& cam = cams_g[v];
+        const int W = cam.width, H = cam.height, nbx = (W + kBlk - 1) / kBlk;
+        const int local = b - base, by = local / nbx, bx = local - by * nbx;
+        const int gy = by * kBlk + (lane >> 1), gx0 = bx * kBlk + (lane & 1) * 8;
+        const long long P = (long long)W * H;
+        const float* X = rgb + 3ll * cam.pixel_offset;
+        const float* Yt = t_rgb + 3ll * cam.pixel_offset;
+        const float* At = t_alpha + cam.pixel_offset;
+        bool d0 = false, d1 = false, d2 = false;
+        const float b0 = bg[3 * v + 0], b1 = bg[3 * v + 1], b2 = bg[3 * v + 2];
+        auto same4 = [](float4 x, float4 t, float4 a, float b) {
+            return x.x == t.x + (1.0f - a.x) * b && x.y == t.y + (1.0f - a.y) * b && x.z == t.z + (1.0f - a.z) * b &&
+                   x.w == t.w + (1.0f - a.w) * b;
+        };
+        if (gy < H && rows16(cam, bases16)) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int gx = gx0 + 4 * h;
+                if (gx >= W) break;  // W is a multiple of 4: a piece lies wholly inside or outside
+                const long long q = (long long)gy * W + gx;
+                const float4 a = __ldg(reinterpret_cast<const float4*>(At + q));
+                const float4 t0 = __ldg(reinterpret_cast<const float4*>(Yt + q));
+                const float4 t1 = __ldg(reinterpret_cast<const float4*>(Yt + P + q));
+                const float4 t2 = __ldg(reinterpret_cast<const float4*>(Yt + 2 * P + q));
+                const float4 x0 = __ldg(reinterpret_cast<const float4*>(X + q));
+                const float4 x1 = __ldg(reinterpret_cast<const float4*>(X + P + q));
+                const float4 x2 = __ldg(reinterpret_cast<const float4*>(X + 2 * P + q));
+                d0 = d0 || !same4(x0, t0, a, b0);
+                d1 = d1 || !same4(x1, t1, a, b1);
+                d2 = d2 || !same4(x2, t2, a, b2);
+            }
+        } else if (gy < H) {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int gx = gx0 + e;
+                if (gx >= W) break;
+                const long long q = (long long)gy * W + gx;
+                const float a = __ldg(At + q);
+                const float y0 = __ldg(Yt + q) + (1.0f - a) * b0;
+                const float y1 = __ldg(Yt + P + q) + (1.0f - a) * b1;
+                const float y2 = __ldg(Yt + 2 * P + q) + (1.0f - a) * b2;
+                d0 = d0 || !(__ldg(X + q) == y0);
+                d1 = d1 || !(__ldg(X + P + q) == y1);
+                d2 = d2 || !(__ldg(X + 2 * P + q) == y2);
+            }
+        }
+        const bool a0 = __any_sync(0xffffffffu, d0), a1 = __any_sync(0xffffffffu, d1),
+                   a2 = __any_sync(0xffffffffu, d2);
+        if (lane == 0) {
+            flags[3 * (size_t)b + 0] = a0 ? 0 : 1;
+            flags[3 * (size_t)b + 1] = a1 ? 0 : 1;
+            flags[3 * (size_t)b + 2] = a2 ? 0 : 1;
+        }
+    }
+}
+
+// Whether the 16-pixel blocks that cover work item `it`'s 52 x 52 input
+// region (4 x 4 of them: columns ox - 16 .. ox + 47) all agree in its channel,
+// blocks outside the image counting as agreeing (block-uniform; one barrier).
+// Then the item's exact agreement test would pass too, and it needs no loads.
+__device__ __forceinline__ bool blocks_agree(const uint8_t* __restrict__ flags, const gsfit_camera* __restrict__ cams_g,
+                                             int it, int v, int first, int boff) {
+    const gsfit_camera& cam = cams_g[v];
+    const int W = cam.width, H = cam.height;
+    const int txn = (W + kOut - 1) / kOut, nbx = (W + kBlk - 1) / kBlk, nby = (H + kBlk - 1) / kBlk;
+    const int local = it - first, ch = local % 3, tile = local / 3;
+    const int oy = (tile / txn) * kOut, ox = (tile % txn) * kOut;
+    bool differ = false;
+    if (threadIdx.x < 16) {
+        const int bx = ((ox - 10) >> 4) + (threadIdx.x & 3), by = ((oy - 10) >> 4) + (threadIdx.x >> 2);
+        if (bx >= 0 && bx < nbx && by >= 0 && by < nby)
+            differ = flags[3 * ((size_t)boff + (size_t)by * nbx + bx) + ch] == 0;
+    }
+    return __syncthreads_or(differ) == 0;
 }
 
 __device__ __forceinline__ void cp_async4(float* smem, const float* gmem, bool ok) {
@@ -173,14 +297,6 @@ __device__ __forceinline__ void prefetch_item(LossSmem& S, const gsfit_camera* _
     asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
 
-// Whether a view's rows can be read in 16-byte pieces: width and pixel offset
-// multiples of 4 (so every channel plane and row starts 16-byte aligned, and
-// a 4-pixel piece starting at a multiple of 4 lies wholly inside or outside
-// the image), and the three input arrays 16-byte aligned.
-__device__ __forceinline__ bool rows16(const gsfit_camera& cam, bool bases16) {
-    return bases16 && (cam.width & 3) == 0 && (cam.pixel_offset & 3) == 0;
-}
-
 // Adds the block's sums of the three loss terms to a view's accumulators
 // (sum |x - y|, sum SSIM, sum |A - A*|); ends with a barrier.
 __device__ __forceinline__ void block_loss_sums(float (&s_red)[3][kLossThreads / 32], float* acc_v, float l1,
@@ -207,31 +323,42 @@ __global__ void __launch_bounds__(kLossThreads, kLossCtasPerSm) loss_kernel(
     const gsfit_camera* __restrict__ cams_g, int n_views, const float* __restrict__ rgb,
     const float* __restrict__ alpha, const float* __restrict__ t_rgb, const float* __restrict__ t_alpha,
     const float* __restrict__ bg, float lambda, float* __restrict__ g_rgb, float* __restrict__ g_alpha,
-    float* __restrict__ acc /* 3 per view: sum|x-y|, sum SSIM, sum|A-A*| */) {
+    float* __restrict__ acc /* 3 per view: sum|x-y|, sum SSIM, sum|A-A*| */,
+    const uint8_t* __restrict__ flags /* the match pre-pass's, or null */, size_t flag_bytes) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     LossSmem& S = *reinterpret_cast<LossSmem*>(smem_raw);
     __shared__ float s_red[3][kLossThreads / 32];
-    __shared__ int s_view, s_first;
+    __shared__ int s_view, s_first, s_boff;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    int n_items = 0;
-    for (int v = 0; v < n_views; ++v)
+    int n_items = 0, n_blocks = 0;
+    for (int v = 0; v < n_views; ++v) {
         n_items += 3 * ((cams_g[v].width + kOut - 1) / kOut) * ((cams_g[v].height + kOut - 1) / kOut);
+        n_blocks += blocks_of(cams_g[v]);
+    }
+    if (3 * (size_t)n_blocks > flag_bytes) flags = nullptr;  // as the pre-pass decided
 
     // The inputs of each item are copied asynchronously while the previous
     // item finishes (its last pass leaves the input region and most of the
     // horizontal-pass buffer free).
-    if (tid == 0 && (int)blockIdx.x < n_items) locate_item(cams_g, blockIdx.x, s_view, s_first);
+    if (tid == 0 && (int)blockIdx.x < n_items) locate_item(cams_g, blockIdx.x, s_view, s_first, s_boff);
     __syncthreads();
     const bool bases16 = ((reinterpret_cast<uintptr_t>(rgb) | reinterpret_cast<uintptr_t>(t_rgb) |
                            reinterpret_cast<uintptr_t>(t_alpha)) & 15u) == 0;
-    if ((int)blockIdx.x < n_items && !rows16(cams_g[s_view], bases16))
-        prefetch_item(S, cams_g, blockIdx.x, s_view, s_first, rgb, t_rgb, t_alpha);
+    // An item is started (its inputs copied, where they are copied) only if
+    // the match flags do not already settle it.
+    auto start_item = [&](int it) -> bool {  // block-uniform; the item's location in s_view, s_first, s_boff
+        if (it >= n_items) return false;
+        if (flags && blocks_agree(flags, cams_g, it, s_view, s_first, s_boff)) return true;
+        if (!rows16(cams_g[s_view], bases16)) prefetch_item(S, cams_g, it, s_view, s_first, rgb, t_rgb, t_alpha);
+        return false;
+    };
+    bool settled = start_item(blockIdx.x);  // the current item agrees by the match flags
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int v = s_view;
         const int first = s_first;
         const int next = item + gridDim.x;
         __syncthreads();  // every thread has read this item's view
-        if (tid == 0 && next < n_items) locate_item(cams_g, next, s_view, s_first);
+        if (tid == 0 && next < n_items) locate_item(cams_g, next, s_view, s_first, s_boff);
         const gsfit_camera& cam = cams_g[v];
         const int W = cam.width, H = cam.height;
         const int txn = (W + kOut - 1) / kOut;
@@ -248,7 +375,9 @@ __global__ void __launch_bounds__(kLossThreads, kLossCtasPerSm) loss_kernel(
         //    the image); and whether render and target agree over the whole
         //    region
         bool differ = false;
-        if (rows16(cam, bases16)) {
+        if (settled) {
+            // nothing to load
+        } else if (rows16(cam, bases16)) {
             // 16-byte loads into registers, the composite and the comparison
             // there, then the region into shared memory as (x, y) pairs: the
             // window is read 2 columns wider on each side (columns ox - 12 ..
@@ -311,10 +440,9 @@ __global__ void __launch_bounds__(kLossThreads, kLossCtasPerSm) loss_kernel(
         // written directly (the stencil would give them up to rounding). In a
         // periphery batch this is every item inside the background around
         // the splats, where both are the background colour bit for bit.
-        if (__syncthreads_or(differ) == 0) {
-            // the input region is no longer read: copy the next item's inputs
-            if (next < n_items && !rows16(cams_g[s_view], bases16))
-                prefetch_item(S, cams_g, next, s_view, s_first, rgb, t_rgb, t_alpha);
+        if (__syncthreads_or(differ) == 0) {  // (also: the next item's location is visible)
+            // the input region is no longer read: start the next item
+            settled = start_item(next);
             float ssim_n = 0.f, la = 0.f;
             const int cidx = tid % kOut, r0 = (tid / kOut) * 4;
 #pragma unroll
@@ -419,9 +547,8 @@ __global__ void __launch_bounds__(kLossThreads, kLossCtasPerSm) loss_kernel(
             }
         }
         __syncthreads();
-        // the input region and the alpha buffer are free: copy the next item's inputs
-        if (next < n_items && !rows16(cams_g[s_view], bases16))
-            prefetch_item(S, cams_g, next, s_view, s_first, rgb, t_rgb, t_alpha);
+        // the input region and the alpha buffer are free: start the next item
+        settled = start_item(next);
         // 5. vertical pass onto the tile (a 4-pixel column strip per thread) and
         //    the gradient
         float l1 = 0.f, la = 0.f;
@@ -482,9 +609,12 @@ int enable_loss_smem() { return opt_in_smem(g_loss_smem_once, loss_kernel, sizeo
 
 using namespace gsfit;
 
-extern "C" size_t gsfit_loss_workspace_size(int32_t n_views) {
+extern "C" size_t gsfit_loss_workspace_size(const gsfit_camera* cams, int32_t n_views) {
     if (n_views < 1 || n_views > GSFIT_MAX_VIEWS) return 0;
-    return (size_t)(3 * n_views) * sizeof(float);
+    if (!cams) return (size_t)(3 * n_views) * sizeof(float);  // the accumulators only
+    size_t blocks = 0;
+    for (int v = 0; v < n_views; ++v) blocks += (size_t)blocks_of(cams[v]);
+    return flags_offset(n_views) + 3 * blocks;
 }
 
 extern "C" int gsfit_loss(const gsfit_camera* cams, int32_t n_views, const float* rgb, const float* alpha,
@@ -492,7 +622,7 @@ extern "C" int gsfit_loss(const gsfit_camera* cams, int32_t n_views, const float
                           float* dL_drgb, float* dL_dalpha, float* loss_out, void* ws, size_t ws_bytes,
                           cudaStream_t stream) {
     if (!cams || n_views < 1 || n_views > GSFIT_MAX_VIEWS || !rgb || !alpha || !target_rgb || !target_alpha ||
-        !bg || !dL_drgb || !dL_dalpha || !ws || ws_bytes < gsfit_loss_workspace_size(n_views))
+        !bg || !dL_drgb || !dL_dalpha || !ws || ws_bytes < gsfit_loss_workspace_size(nullptr, n_views))
         return GSFIT_ERR_INVALID_ARG;
     const size_t smem = sizeof(LossSmem);
     const int rc = enable_loss_smem();
@@ -502,8 +632,17 @@ extern "C" int gsfit_loss(const gsfit_camera* cams, int32_t n_views, const float
     GSFIT_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     float* acc = static_cast<float*>(ws);
     GSFIT_CUDA_CHECK(cudaMemsetAsync(acc, 0, sizeof(float) * 3 * n_views, stream));
+    // the match flags, where the workspace holds them (the kernels check the size)
+    uint8_t* flags = nullptr;
+    size_t flag_bytes = 0;
+    if (ws_bytes > flags_offset(n_views)) {
+        flags = static_cast<uint8_t*>(ws) + flags_offset(n_views);
+        flag_bytes = ws_bytes - flags_offset(n_views);
+        match_kernel<<<8 * sms, 256, 0, stream>>>(cams, n_views, rgb, target_rgb, target_alpha, bg, flags, flag_bytes);
+        GSFIT_LAUNCH_CHECK();
+    }
     loss_kernel<<<kLossCtasPerSm * sms, kLossThreads, smem, stream>>>(cams, n_views, rgb, alpha, target_rgb, target_alpha, bg,
-                                                         lambda, dL_drgb, dL_dalpha, acc);
+                                                         lambda, dL_drgb, dL_dalpha, acc, flags, flag_bytes);
     GSFIT_LAUNCH_CHECK();
     if (loss_out) {
         loss_finalize_kernel<<<1, 32, 0, stream>>>(cams, n_views, lambda, acc, loss_out);
@@ -578,7 +717,7 @@ extern "C" int gsfit_loss_noalloc(const gsfit_camera* cams, int32_t n_views, con
     // the array keeps the previous call's sums: clear this call's part first
     GSFIT_CUDA_CHECK(cudaMemsetAsync(acc, 0, sizeof(float) * 3 * n_views, stream));
     loss_kernel<<<kLossCtasPerSm * sms, kLossThreads, smem, stream>>>(cams, n_views, rgb, alpha, target_rgb, target_alpha, bg,
-                                                         lambda, dL_drgb, dL_dalpha, acc);
+                                                         lambda, dL_drgb, dL_dalpha, acc, nullptr, 0);
     GSFIT_LAUNCH_CHECK();
     if (loss_out) {
         loss_finalize_kernel<<<1, 32, 0, stream>>>(cams, n_views, lambda, acc, loss_out);

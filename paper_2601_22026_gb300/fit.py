@@ -202,7 +202,7 @@ class FitState:
         # tile's furthest contributor and the adjoint's launch order
         self.tile_order = torch.zeros(G.tile_order_words(self.T), dtype=torch.int32, device=dev)
         self.grad2d = torch.zeros(self.V * self.n * 16, dtype=f32, device=dev)
-        self.loss_ws = torch.zeros(G.gsfit_loss_workspace_size(self.V) // 4 + 1, dtype=f32, device=dev)
+        self.loss_ws = torch.zeros(G.gsfit_loss_workspace_size(self.table) // 4 + 1, dtype=f32, device=dev)
         bgv = np.zeros((self.V, 3), np.float32) if bg is None else np.asarray(bg, np.float32).reshape(self.V, 3)
         self.bg = torch.from_numpy(bgv.copy()).to(dev)
         self.graph = None

@@ -44,7 +44,7 @@ class Gaussians(ctypes.Structure):
                 ("reserved", _i32)]
 
 
-ABI_VERSION = 7  # GSFIT_ABI_VERSION of include/gsfit.h
+ABI_VERSION = 8  # GSFIT_ABI_VERSION of include/gsfit.h
 
 # gsfit_gaussians.feature_dtype values (GSFIT_FEATURES_*)
 FEATURES = {"f32": 0, "f16": 1, "bf16": 2}
@@ -79,7 +79,7 @@ SIGNATURES = {
     "gsfit_bin_sort_workspace_size": (_size, [_i64, _i64, _i32]),
     "gsfit_bin_sort": (ctypes.c_int, [_P, _P, _i32, _i32, _i32, _P, _size, _P, _P, _i64, _P, _P, _P, _P, _P]),
     "gsfit_render_fwd": (ctypes.c_int, [_P, _P, _i32, _i32, _i32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
-    "gsfit_loss_workspace_size": (_size, [_i32]),
+    "gsfit_loss_workspace_size": (_size, [_P, _i32]),
     "gsfit_loss": (ctypes.c_int, [_P, _i32, _P, _P, _P, _P, _P, _f32, _P, _P, _P, _P, _size, _P]),
     "gsfit_loss_noalloc": (ctypes.c_int, [_P, _i32, _P, _P, _P, _P, _P, _f32, _P, _P, _P, _P]),
     "gsfit_render_bwd": (ctypes.c_int, [_P, _P, _P, _i32, _i32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
@@ -307,8 +307,12 @@ def gsfit_render_fwd(proj: ProjBuffers, cams_dev, n_views, n, total_tiles, vals,
            "gsfit_render_fwd")
 
 
-def gsfit_loss_workspace_size(n_views) -> int:
-    return int(load().gsfit_loss_workspace_size(n_views))
+def gsfit_loss_workspace_size(table) -> int:
+    """Workspace bytes of gsfit_loss for a camera table (with the match flags),
+    or, given a view count, for the accumulators only."""
+    if isinstance(table, CameraTable):
+        return int(load().gsfit_loss_workspace_size(ctypes.cast(table.host, _P), table.n_views))
+    return int(load().gsfit_loss_workspace_size(None, int(table)))
 
 
 def gsfit_loss(cams_dev, n_views, rgb, alpha, target_rgb, target_alpha, bg, lam, dL_drgb, dL_dalpha, loss_out, ws,

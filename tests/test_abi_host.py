@@ -37,7 +37,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version_and_status_strings(lib):
-    assert lib.gsfit_abi_version() == 7
+    assert lib.gsfit_abi_version() == 8
     assert lib.gsfit_status_string(G.GSFIT_ERR_CAPACITY) == b"instance capacity exceeded"
     assert lib.gsfit_status_string(G.GSFIT_ERR_TIMEOUT) == b"bounded device wait ran out"
 
@@ -97,7 +97,7 @@ def test_invalid_arguments_rejected_on_host(lib):
                               None, fake, None) == G.GSFIT_ERR_INVALID_ARG
     assert lib.gsfit_adam_step(fake, fake, fake, fake, 10, 17, None, 0.9, 0.999, 1e-15, fake, None, 0,
                                None) == G.GSFIT_ERR_INVALID_ARG
-    assert lib.gsfit_loss_workspace_size(0) == 0
+    assert lib.gsfit_loss_workspace_size(None, 0) == 0
 
 
 def test_reproject_alignment_rejected_on_host(lib):

@@ -458,7 +458,7 @@ def test_loss_matches_oracle(layout):
     t = lambda x: torch.from_numpy(np.ascontiguousarray(x, np.float32)).cuda()
     d_rgb, d_a = torch.zeros(3 * table.total_pixels, device="cuda"), torch.zeros(table.total_pixels, device="cuda")
     L = torch.zeros(1, device="cuda")
-    ws = torch.zeros(G.gsfit_loss_workspace_size(V) // 4, device="cuda")
+    ws = torch.zeros(G.gsfit_loss_workspace_size(table) // 4 + 1, device="cuda")
     G.gsfit_loss(cams_dev, V, t(rgb), t(alpha), t(trgb), t(talpha), t(bg), 0.2, d_rgb, d_a, L, ws)
     torch.cuda.synchronize()
     Lr, gr, ga, _ = oracle.loss(rgb, alpha, trgb, talpha, bg, cams)
@@ -513,7 +513,7 @@ def test_loss_with_matching_regions_matches_oracle():
     t = lambda z: torch.from_numpy(np.ascontiguousarray(z, np.float32)).cuda()
     d_rgb, d_a = torch.zeros(3 * table.total_pixels, device="cuda"), torch.zeros(table.total_pixels, device="cuda")
     L = torch.zeros(1, device="cuda")
-    ws = torch.zeros(G.gsfit_loss_workspace_size(V) // 4, device="cuda")
+    ws = torch.zeros(G.gsfit_loss_workspace_size(table) // 4 + 1, device="cuda")
     G.gsfit_loss(cams_dev, V, t(rgb), t(alpha), t(trgb), t(talpha), t(bg), 0.2, d_rgb, d_a, L, ws)
     torch.cuda.synchronize()
     Lr, gr, ga, _ = oracle.loss(rgb, alpha, trgb, talpha, bg, cams)
@@ -536,6 +536,16 @@ def test_loss_with_matching_regions_matches_oracle():
                         assert np.abs(ref[oy:oy + 32, ox:ox + 32]).max() <= 1e-9 * np.abs(gr).max()
                     skipped += 1
     assert skipped >= 6
+    # without the match flags (a workspace of the accumulators only) every tile tests its own region: the
+    # same gradients bit for bit, the same loss up to the order of the float atomics
+    d_rgb2, d_a2, L2 = torch.zeros_like(d_rgb), torch.zeros_like(d_a), torch.zeros(1, device="cuda")
+    ws2 = torch.zeros(G.gsfit_loss_workspace_size(V) // 4, device="cuda")
+    assert G.gsfit_loss_workspace_size(V) < G.gsfit_loss_workspace_size(table)
+    G.gsfit_loss(cams_dev, V, t(rgb), t(alpha), t(trgb), t(talpha), t(bg), 0.2, d_rgb2, d_a2, L2, ws2)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(d_rgb2.cpu().numpy(), gg)
+    np.testing.assert_array_equal(d_a2.cpu().numpy(), d_a.cpu().numpy())
+    assert float(L2.item()) == pytest.approx(float(L.item()), rel=1e-6)
 
 
 def test_adam_matches_oracle():
