@@ -60,7 +60,7 @@
 extern "C" {
 #endif
 
-#define GSFIT_ABI_VERSION 8
+#define GSFIT_ABI_VERSION 9
 #define GSFIT_MAX_VIEWS 256
 #define GSFIT_TILE 16
 /* Words of a tile_order buffer for total_tiles tiles (gsfit_bin_sort):
@@ -234,7 +234,10 @@ size_t gsfit_bin_sort_workspace_size(int64_t n_records, int64_t capacity, int32_
  *   total_tiles = sum over views of tiles); ws/ws_bytes: device workspace of
  *   at least gsfit_bin_sort_workspace_size bytes (contents need not be
  *   initialised); keys (uint64) and vals (uint32): device, `capacity`
- *   entries each, sorted output; n_instances: device uint32, receives the
+ *   entries each, sorted output; keys may be null when the caller needs only
+ *   the lists (vals) and ranges, which are then the same: the tile-bit passes
+ *   then sort 32-bit tile ids with the values (8 bytes per pair and pass
+ *   instead of 12); n_instances: device uint32, receives the
  *   number of pairs (also when it exceeds capacity); ranges: device uint32,
  *   2 * total_tiles entries; status: device int32, set to GSFIT_ERR_CAPACITY
  *   when the pairs exceed capacity (nothing is then emitted and every range

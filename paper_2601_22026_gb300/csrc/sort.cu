@@ -320,12 +320,26 @@ __global__ void __launch_bounds__(kScanThreads) reduce_sorted_kernel(const unsig
 // counts), so every store is coalesced and a large splat does not hold up the
 // other lanes. The next row's record gather is issued before the current row
 // is dealt out.
+// A pair's key: (tile << 32) | depth bits, or the tile id alone when the
+// tile passes sort 32-bit keys.
+template <typename K>
+__device__ __forceinline__ K pair_key(uint32_t tile, uint32_t depth);
+template <>
+__device__ __forceinline__ unsigned long long pair_key<unsigned long long>(uint32_t tile, uint32_t depth) {
+    return ((unsigned long long)tile << 32) | depth;
+}
+template <>
+__device__ __forceinline__ uint32_t pair_key<uint32_t>(uint32_t tile, uint32_t) {
+    return tile;
+}
+
+template <typename K>
 __global__ void __launch_bounds__(kScanThreads, kEmitBlocksPerSm) emit_kernel(
     const unsigned long long* __restrict__ rkeys0, const uint32_t* __restrict__ rvals0,
     const unsigned long long* __restrict__ rkeys1, const uint32_t* __restrict__ rvals1,
     const float4* __restrict__ xyd, int n, int n_views, const gsfit_camera* __restrict__ cams_g,
     const uint32_t* __restrict__ sums, const uint32_t* __restrict__ seg_off, SortCtl* __restrict__ ctl,
-    int n_tile_passes, unsigned long long* __restrict__ keys, uint32_t* __restrict__ vals) {
+    int n_tile_passes, K* __restrict__ keys, uint32_t* __restrict__ vals) {
     constexpr int kRows = kEmitSeg / 32;
     extern __shared__ gsfit_camera cams[];
     __shared__ uint32_t s_hist[kMaxPasses - kDepthPasses][kRadix];
@@ -402,7 +416,7 @@ __global__ void __launch_bounds__(kScanThreads, kEmitBlocksPerSm) emit_kernel(
                     if (dy * o_rw > q) --dy;  // exact floor(q / rw) after the float estimate
                     else if ((dy + 1u) * o_rw <= q) ++dy;
                     const uint32_t tile = o_t0 + dy * o_txn + (q - dy * o_rw);
-                    keys[offset + k] = ((unsigned long long)tile << 32) | o_depth;
+                    keys[offset + k] = pair_key<K>(tile, o_depth);
                     vals[offset + k] = o_gi;
                     for (int p = 0; p < n_tile_passes; ++p) atomicAdd(&s_hist[p][(tile >> (8 * p)) & 0xff], 1u);
                 }
@@ -463,8 +477,12 @@ __global__ void lookback_selftest_kernel(const uint32_t* word, int limit, int32_
     lookback_window(word, 0, 0, excl, status, limit);  // partition 0's word of digit 0: word[0] only
 }
 
+// K: the key type, 64-bit (the depth passes' (tile count, depth) records, and
+// the tile passes when the sorted keys are an output) or 32-bit (the tile
+// passes over tile ids alone).
+template <typename K>
 struct OnesweepSmem {
-    unsigned long long keys[kPart];
+    K keys[kPart];
     uint32_t vals[kPart];
     uint32_t vals_in[kPart];  // this partition's values in input order
     uint32_t warp_hist[kSortWarps][kRadix + 1];  // bin kRadix collects padding keys
@@ -476,14 +494,15 @@ struct OnesweepSmem {
 
 // One stable counting pass over the 8-bit digit at bit `shift` of *n_ptr keys;
 // `pass` indexes the histogram and partition counter of this launch.
-__global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(unsigned long long* keys_a, uint32_t* vals_a,
-                                                                unsigned long long* keys_b, uint32_t* vals_b,
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(K* keys_a, uint32_t* vals_a, K* keys_b,
+                                                                uint32_t* vals_b,
                                                                 SortCtl* __restrict__ ctl, int pass, int shift,
                                                                 const uint32_t* __restrict__ n_ptr,
                                                                 uint32_t* __restrict__ lookback,
                                                                 int32_t* __restrict__ status, int depth_pass) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    OnesweepSmem& S = *reinterpret_cast<OnesweepSmem*>(smem_raw);
+    OnesweepSmem<K>& S = *reinterpret_cast<OnesweepSmem<K>*>(smem_raw);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t n = *n_ptr;
     const uint32_t n_parts = (n + kPart - 1) / kPart;
@@ -499,16 +518,16 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(unsigned long
         if (identity) return;
         swap = depth_buffer(ctl, pass, n) != 0;
     }
-    const unsigned long long* __restrict__ keys_in = swap ? keys_b : keys_a;
+    const K* __restrict__ keys_in = swap ? keys_b : keys_a;
     const uint32_t* __restrict__ vals_in = swap ? vals_b : vals_a;
-    unsigned long long* __restrict__ keys_out = swap ? keys_a : keys_b;
+    K* __restrict__ keys_out = swap ? keys_a : keys_b;
     uint32_t* __restrict__ vals_out = swap ? vals_a : vals_b;
     const uint32_t part = S.part;
     if (part >= n_parts) return;
     const uint32_t base = part * kPart;
     const uint32_t valid = min((uint32_t)kPart, n - base);
     if (identity) {  // block-uniform: copy the partition in place of ranking it
-        unsigned long long kc[kSortItems];
+        K kc[kSortItems];
         uint32_t vc[kSortItems];
 #pragma unroll
         for (int j = 0; j < kSortItems; ++j) {
@@ -531,14 +550,14 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(unsigned long
 
     // Load (warp-striped, coalesced) and rank within the warp per digit. Keys
     // stay in registers; values wait in shared memory in input order.
-    unsigned long long k_reg[kSortItems];
+    K k_reg[kSortItems];
     uint32_t r_reg[kSortItems];
     const uint32_t lt_mask = (1u << lane) - 1u;
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
         const uint32_t idx = (uint32_t)wid * (32 * kSortItems) + j * 32 + lane;
         const bool ok = idx < valid;
-        k_reg[j] = ok ? keys_in[base + idx] : ~0ull;
+        k_reg[j] = ok ? keys_in[base + idx] : static_cast<K>(~static_cast<K>(0));
         if (ok) S.vals_in[idx] = vals_in[base + idx];
     }
     // global exclusive offset of digit threadIdx.x over all keys of this pass
@@ -612,7 +631,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(unsigned long
     __syncthreads();
     // write runs of equal digits to consecutive global addresses
     for (uint32_t j = threadIdx.x; j < valid; j += kSortThreads) {
-        const unsigned long long key = S.keys[j];
+        const K key = S.keys[j];
         const uint32_t dd = (uint32_t)((key >> shift) & 0xff);
         const uint32_t o = S.glob_off[dd] + j;
         if (o < n) {  // always true unless a look-back wait ran out
@@ -627,20 +646,21 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(unsigned long
 // (block-striped), with all of a chunk's loads issued before any compare.
 constexpr int kRangeItems = 4;
 constexpr int kRangeBlocksPerSm = 8;
-__global__ void __launch_bounds__(256) ranges_kernel(const unsigned long long* __restrict__ keys,
+// hi: the sorted keys' tile ids, one every `stride` words (the upper word of
+// each 64-bit key, or each 32-bit key).
+__global__ void __launch_bounds__(256) ranges_kernel(const uint32_t* __restrict__ hi, int stride,
                                                      const SortCtl* __restrict__ ctl,
                                                      uint32_t* __restrict__ ranges, uint32_t total_tiles) {
     const uint32_t n = ctl->n_sort;
-    const uint32_t* hi = reinterpret_cast<const uint32_t*>(keys) + 1;  // tile id: the upper word of each key
     for (long long base = (long long)blockIdx.x * (256 * kRangeItems) + threadIdx.x; base < n;
          base += (long long)gridDim.x * (256 * kRangeItems)) {
         uint32_t t[kRangeItems], prev[kRangeItems], next[kRangeItems];
 #pragma unroll
         for (int i = 0; i < kRangeItems; ++i) {
             const long long k = base + 256 * i;
-            t[i] = k < n ? __ldg(hi + 2 * k) : 0xffffffffu;
-            prev[i] = k < n && k > 0 ? __ldg(hi + 2 * (k - 1)) : 0xffffffffu;
-            next[i] = k + 1 < n ? __ldg(hi + 2 * (k + 1)) : 0xffffffffu;
+            t[i] = k < n ? __ldg(hi + stride * k) : 0xffffffffu;
+            prev[i] = k < n && k > 0 ? __ldg(hi + stride * (k - 1)) : 0xffffffffu;
+            next[i] = k + 1 < n ? __ldg(hi + stride * (k + 1)) : 0xffffffffu;
         }
 #pragma unroll
         for (int i = 0; i < kRangeItems; ++i) {
@@ -760,9 +780,10 @@ SortLayout layout(long long n_rec, long long capacity, int total_tiles) {
 }
 
 // Opt-in to more than 48 KB of dynamic shared memory, once per device and context.
-int enable_onesweep_smem(size_t smem) {
+template <typename K>
+int enable_onesweep_smem() {
     static ContextOnce once;
-    return opt_in_smem(once, onesweep_kernel, smem);
+    return opt_in_smem(once, onesweep_kernel<K>, sizeof(OnesweepSmem<K>));
 }
 
 }  // namespace
@@ -783,7 +804,7 @@ extern "C" int gsfit_bin_sort(const gsfit_proj* proj, const gsfit_camera* cams, 
                               int64_t capacity, uint32_t* n_instances, uint32_t* ranges, uint32_t* tile_order,
                               int32_t* status, cudaStream_t stream) {
     if (!valid_proj(proj) || !cams || n_views < 1 || n_views > GSFIT_MAX_VIEWS || n < 1 || total_tiles < 1 ||
-        !ws || !keys || !vals || !n_instances || !ranges || !status || capacity < 1 ||
+        !ws || !vals || !n_instances || !ranges || !status || capacity < 1 ||
         capacity >= (int64_t)kFlagAgg)
         return GSFIT_ERR_INVALID_ARG;
     const long long n_rec = (long long)n * n_views;
@@ -802,8 +823,10 @@ extern "C" int gsfit_bin_sort(const gsfit_proj* proj, const gsfit_camera* cams, 
                                  reinterpret_cast<unsigned long long*>(base + L.rkeys[1])};
     uint32_t* rv[2] = {reinterpret_cast<uint32_t*>(base + L.rvals[0]), reinterpret_cast<uint32_t*>(base + L.rvals[1])};
     unsigned long long* keys_out = reinterpret_cast<unsigned long long*>(keys);
-    const size_t smem = sizeof(OnesweepSmem);
-    const int rc = enable_onesweep_smem(smem);
+    const bool narrow = keys == nullptr;  // the tile passes sort 32-bit tile ids; no keys are written
+    const size_t smem = sizeof(OnesweepSmem<unsigned long long>), smem32 = sizeof(OnesweepSmem<uint32_t>);
+    int rc = enable_onesweep_smem<unsigned long long>();
+    if (rc == GSFIT_OK && narrow) rc = enable_onesweep_smem<uint32_t>();
     if (rc != GSFIT_OK) return rc;
 
     reduce_kernel<<<L.n_blocks, kScanThreads, 0, stream>>>(proj->tiles, n_rec, pair_sums, rec_sums);
@@ -818,8 +841,8 @@ extern "C" int gsfit_bin_sort(const gsfit_proj* proj, const gsfit_camera* cams, 
     // result depends on how many passes were identities; the kernels after them check)
     uint32_t* lb = lookback;
     for (int p = 0; p < kDepthPasses; ++p) {
-        onesweep_kernel<<<(unsigned)L.max_rec_parts, kSortThreads, smem, stream>>>(rk[0], rv[0], rk[1], rv[1], ctl, p,
-                                                                                    8 * p, &ctl->n_rec, lb, status, 1);
+        onesweep_kernel<unsigned long long><<<(unsigned)L.max_rec_parts, kSortThreads, smem, stream>>>(
+            rk[0], rv[0], rk[1], rv[1], ctl, p, 8 * p, &ctl->n_rec, lb, status, 1);
         GSFIT_LAUNCH_CHECK();
         lb += (size_t)L.max_rec_parts * kRadix;
     }
@@ -830,32 +853,51 @@ extern "C" int gsfit_bin_sort(const gsfit_proj* proj, const gsfit_camera* cams, 
     GSFIT_LAUNCH_CHECK();
     // pairs go to the buffer that, after the tile passes' ping-pong, leaves the result in keys/vals
     const bool emit_to_alt = (L.tile_passes % 2) == 1;
-    unsigned long long* k_cur = emit_to_alt ? keys_alt : keys_out;
     uint32_t* v_cur = emit_to_alt ? vals_alt : vals;
-    unsigned long long* k_nxt = emit_to_alt ? keys_out : keys_alt;
     uint32_t* v_nxt = emit_to_alt ? vals : vals_alt;
     int dev = 0, sms = 0;
     GSFIT_CUDA_CHECK(cudaGetDevice(&dev));
     GSFIT_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const long long segs = (long long)L.n_blocks * kSegsPerChunk;
-    emit_kernel<<<(unsigned)std::min<long long>((long long)kEmitBlocksPerSm * sms, (segs + 7) / 8), kScanThreads,
-                  sizeof(gsfit_camera) * n_views, stream>>>(rk[0], rv[0], rk[1], rv[1],
-                                                            reinterpret_cast<const float4*>(proj->xyd),
-                                                            n, n_views, cams, sorted_sums, seg_off, ctl,
-                                                            L.tile_passes, k_cur, v_cur);
-    GSFIT_LAUNCH_CHECK();
-    for (int q = 0; q < L.tile_passes; ++q) {
-        onesweep_kernel<<<(unsigned)L.max_parts, kSortThreads, smem, stream>>>(
-            k_cur, v_cur, k_nxt, v_nxt, ctl, kDepthPasses + q, 32 + 8 * q, &ctl->n_sort, lb, status, 0);
+    const unsigned emit_grid = (unsigned)std::min<long long>((long long)kEmitBlocksPerSm * sms, (segs + 7) / 8);
+    const unsigned range_grid = (unsigned)std::min<long long>((long long)kRangeBlocksPerSm * sms,
+                                                              (capacity + 256 * kRangeItems - 1) / (256 * kRangeItems));
+    if (narrow) {  // 32-bit keys in the two halves of the alternate key buffer
+        uint32_t* k_cur = reinterpret_cast<uint32_t*>(keys_alt);
+        uint32_t* k_nxt = k_cur + capacity;
+        emit_kernel<uint32_t><<<emit_grid, kScanThreads, sizeof(gsfit_camera) * n_views, stream>>>(
+            rk[0], rv[0], rk[1], rv[1], reinterpret_cast<const float4*>(proj->xyd), n, n_views, cams, sorted_sums,
+            seg_off, ctl, L.tile_passes, k_cur, v_cur);
         GSFIT_LAUNCH_CHECK();
-        lb += (size_t)L.max_parts * kRadix;
-        std::swap(k_cur, k_nxt);
-        std::swap(v_cur, v_nxt);
+        for (int q = 0; q < L.tile_passes; ++q) {
+            onesweep_kernel<uint32_t><<<(unsigned)L.max_parts, kSortThreads, smem32, stream>>>(
+                k_cur, v_cur, k_nxt, v_nxt, ctl, kDepthPasses + q, 8 * q, &ctl->n_sort, lb, status, 0);
+            GSFIT_LAUNCH_CHECK();
+            lb += (size_t)L.max_parts * kRadix;
+            std::swap(k_cur, k_nxt);
+            std::swap(v_cur, v_nxt);
+        }
+        ranges_kernel<<<range_grid, 256, 0, stream>>>(k_cur, 1, ctl, ranges, (uint32_t)total_tiles);
+        GSFIT_LAUNCH_CHECK();
+    } else {
+        unsigned long long* k_cur = emit_to_alt ? keys_alt : keys_out;
+        unsigned long long* k_nxt = emit_to_alt ? keys_out : keys_alt;
+        emit_kernel<unsigned long long><<<emit_grid, kScanThreads, sizeof(gsfit_camera) * n_views, stream>>>(
+            rk[0], rv[0], rk[1], rv[1], reinterpret_cast<const float4*>(proj->xyd), n, n_views, cams, sorted_sums,
+            seg_off, ctl, L.tile_passes, k_cur, v_cur);
+        GSFIT_LAUNCH_CHECK();
+        for (int q = 0; q < L.tile_passes; ++q) {
+            onesweep_kernel<unsigned long long><<<(unsigned)L.max_parts, kSortThreads, smem, stream>>>(
+                k_cur, v_cur, k_nxt, v_nxt, ctl, kDepthPasses + q, 32 + 8 * q, &ctl->n_sort, lb, status, 0);
+            GSFIT_LAUNCH_CHECK();
+            lb += (size_t)L.max_parts * kRadix;
+            std::swap(k_cur, k_nxt);
+            std::swap(v_cur, v_nxt);
+        }
+        ranges_kernel<<<range_grid, 256, 0, stream>>>(reinterpret_cast<const uint32_t*>(keys_out) + 1, 2, ctl, ranges,
+                                                      (uint32_t)total_tiles);
+        GSFIT_LAUNCH_CHECK();
     }
-    ranges_kernel<<<(unsigned)std::min<long long>((long long)kRangeBlocksPerSm * sms,
-                                                 (capacity + 256 * kRangeItems - 1) / (256 * kRangeItems)),
-                    256, 0, stream>>>(keys_out, ctl, ranges, (uint32_t)total_tiles);
-    GSFIT_LAUNCH_CHECK();
     if (tile_order) {
         const int ob = min(152, (total_tiles + 255) / 256);
         order_hist_kernel<<<ob, 256, 0, stream>>>(ranges, total_tiles, tile_order + total_tiles + 1, ctl);

@@ -73,7 +73,7 @@ class FitState:
     def __init__(self, gaussians: dict, cams: dict, *, target_rgb=None, target_alpha=None, bg=None,
                  capacity: int | None = None, lr: dict | None = None, eps: float = 1e-15,
                  lam: float = 0.2, features: str = "f32", tile: int = 16, batch: int = 128,
-                 batch_bwd: int = 64, exp_half2: bool = False, device: str = "cuda"):
+                 batch_bwd: int = 64, exp_half2: bool = False, keep_keys: bool = False, device: str = "cuda"):
         """features: "f32", or "f16" / "bf16" for the mixed-precision form
         (16-bit copy of the SH coefficients read by the projection, kept
         current by Adam; float32 master parameters and moments).
@@ -81,8 +81,12 @@ class FitState:
         shared-memory slot of the forward and the adjoint compositing): the
         compositing options; see tune.py for choosing them.
         exp_half2: evaluate the compositing exponent in packed half precision
-        (the half2 option of the mixed-precision form)."""
+        (the half2 option of the mixed-precision form).
+        keep_keys: also write the sorted (tile, depth) keys to self.keys; the
+        fit needs only the lists and ranges, which the sort then produces
+        with 32-bit tile keys."""
         self.device = device
+        self.keep_keys = bool(keep_keys)
         self.tile = int(tile)
         self.exp_half2 = bool(exp_half2)
         self.opts = G.RenderOpts(self.tile, int(batch), int(self.exp_half2), int(batch_bwd))
@@ -231,7 +235,7 @@ class FitState:
             return
         self.capacity = int(need)
         dev = self.device
-        self.keys = torch.empty(self.capacity, dtype=torch.int64, device=dev)
+        self.keys = torch.empty(self.capacity, dtype=torch.int64, device=dev) if self.keep_keys else None
         self.vals = torch.empty(self.capacity, dtype=torch.int32, device=dev)
         ws_bytes = G.gsfit_bin_sort_workspace_size(self.V * self.n, self.capacity, self.T)
         self.sort_ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)

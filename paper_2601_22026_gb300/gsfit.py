@@ -44,7 +44,7 @@ class Gaussians(ctypes.Structure):
                 ("reserved", _i32)]
 
 
-ABI_VERSION = 8  # GSFIT_ABI_VERSION of include/gsfit.h
+ABI_VERSION = 9  # GSFIT_ABI_VERSION of include/gsfit.h
 
 # gsfit_gaussians.feature_dtype values (GSFIT_FEATURES_*)
 FEATURES = {"f32": 0, "f16": 1, "bf16": 2}

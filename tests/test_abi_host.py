@@ -37,7 +37,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version_and_status_strings(lib):
-    assert lib.gsfit_abi_version() == 8
+    assert lib.gsfit_abi_version() == 9
     assert lib.gsfit_status_string(G.GSFIT_ERR_CAPACITY) == b"instance capacity exceeded"
     assert lib.gsfit_status_string(G.GSFIT_ERR_TIMEOUT) == b"bounded device wait ran out"
 

@@ -58,7 +58,7 @@ def _snapped(gs, kind):
 
 def _state(gs, cams, bg, kind):
     from paper_2601_22026_gb300.fit import FitState
-    return FitState(gs, cams, bg=bg, features=kind)
+    return FitState(gs, cams, bg=bg, features=kind, keep_keys=True)
 
 
 def _scene(name):

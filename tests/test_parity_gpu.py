@@ -26,6 +26,7 @@ def _built():
 
 def _fit_state(gs, cams, bg=None, **kw):
     from paper_2601_22026_gb300.fit import FitState
+    kw.setdefault("keep_keys", True)  # these tests compare the sorted keys too
     return FitState(gs, cams, bg=bg, **kw)
 
 
@@ -546,6 +547,43 @@ def test_loss_with_matching_regions_matches_oracle():
     np.testing.assert_array_equal(d_rgb2.cpu().numpy(), gg)
     np.testing.assert_array_equal(d_a2.cpu().numpy(), d_a.cpu().numpy())
     assert float(L2.item()) == pytest.approx(float(L.item()), rel=1e-6)
+
+
+@pytest.mark.parametrize("name", ["sh3_uneven_views", "big_splats", "max_views", "plain_single_view"])
+@pytest.mark.parametrize("tile", [16, 8])
+def test_sort_without_keys_gives_the_same_lists(name, tile):
+    """gsfit_bin_sort without the keys output sorts 32-bit tile ids in its
+    tile passes: the lists, ranges, pair count and tile order equal those of
+    the sort with 64-bit keys bit for bit."""
+    gs, cams, bg = _case(name)
+    a = _fit_state(gs, cams, bg, tile=tile, keep_keys=True)
+    b = _fit_state(gs, cams, bg, tile=tile, keep_keys=False)
+    assert b.keys is None
+    for st in (a, b):
+        st.project()
+        st.bin_sort()
+    torch.cuda.synchronize()
+    assert a.check_status() == 0 and b.check_status() == 0
+    n = int(a.n_instances.item())
+    assert n == int(b.n_instances.item()) and n > 0
+    np.testing.assert_array_equal(a.vals[:n].cpu().numpy(), b.vals[:n].cpu().numpy())
+    np.testing.assert_array_equal(a.ranges.cpu().numpy(), b.ranges.cpu().numpy())
+    T = a.T
+    # the tile order: the same count and the same bucket at every position (within a bucket the order is
+    # that of atomic reservations)
+    oa = a.tile_order[:T + 1].cpu().numpy().view(np.uint32).astype(np.int64)
+    ob = b.tile_order[:T + 1].cpu().numpy().view(np.uint32).astype(np.int64)
+    assert oa[T] == ob[T]
+    lens = (lambda r: r[:, 1] - r[:, 0])(a.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2).astype(np.int64))
+    from test_tile_order_gpu import _bucket
+    bucket = lambda o: np.where(lens[o] > 0, 1 + _bucket(lens[o]), 0)
+    np.testing.assert_array_equal(bucket(oa[:T]), bucket(ob[:T]))
+    np.testing.assert_array_equal(np.sort(oa[:T]), np.sort(ob[:T]))
+    # the tile ids of the wide keys are the lists' tiles
+    keys = a.keys[:n].cpu().numpy().view(np.uint64)
+    r = a.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2).astype(np.int64)
+    tiles = np.repeat(np.arange(T), r[:, 1] - r[:, 0])
+    np.testing.assert_array_equal((keys >> np.uint64(32)).astype(np.int64), tiles)
 
 
 def test_adam_matches_oracle():

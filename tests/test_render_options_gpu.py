@@ -30,7 +30,7 @@ def _built():
 
 def _state(gs, cams, bg, tile, batch, batch_bwd=64):
     from paper_2601_22026_gb300.fit import FitState
-    return FitState(gs, cams, bg=bg, tile=tile, batch=batch, batch_bwd=batch_bwd)
+    return FitState(gs, cams, bg=bg, tile=tile, batch=batch, batch_bwd=batch_bwd, keep_keys=True)
 
 
 @pytest.mark.parametrize("tile,batch,batch_bwd", VARIANTS)
