@@ -100,6 +100,23 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.gsfit_loss_workspace_size(None, 0) == 0
 
 
+def test_loss_workspace_size_with_match_flags(lib):
+    """With the host camera table the loss workspace holds the accumulators
+    (3 floats per view, padded to 256 bytes) and one flag byte per 16 x 16
+    block and channel; without it, the accumulators only."""
+    import scenes
+    cams = scenes.stack_cameras([scenes.make_camera((0, 0, 3), (0, 0, 0), w, h, fx=50.0)
+                                 for w, h in [(45, 37), (1920, 1920), (7, 5), (513, 257)]])
+    table = G.camera_table(cams)
+    V = table.n_views
+    blocks = sum(-(-int(w) // 16) * -(-int(h) // 16) for w, h in zip(cams["width"], cams["height"]))
+    assert G.gsfit_loss_workspace_size(table) == ((12 * V + 255) // 256) * 256 + 3 * blocks
+    assert G.gsfit_loss_workspace_size(V) == 12 * V
+    assert lib.gsfit_loss_workspace_size(None, G.GSFIT_MAX_VIEWS + 1) == 0
+    # the tile order: permutation, count, furthest contributors, the adjoint's order, count
+    assert G.tile_order_words(table.total_tiles) == 3 * table.total_tiles + 2
+
+
 def test_reproject_alignment_rejected_on_host(lib):
     """zbuf takes 64-bit atomics and clip 16-byte stores: misaligned pointers
     are refused before any launch."""
