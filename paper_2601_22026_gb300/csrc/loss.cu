@@ -13,6 +13,11 @@
 // each input region once from DRAM (the output pixels' own values a second
 // time, from L2, for the gradient) and writes each gradient once. Channel-0 items
 // also handle the alpha term. Persistent CTAs stride over the items.
+// Where render and target are equal over an item's whole input region (the
+// background around the splats), SSIM is 1 there and the colour gradient
+// zero: such items skip the stencil. A pre-pass reads the images once and
+// records per 16 x 16 block and channel whether they agree, so that most such
+// items are settled without loading their regions.
 #include "common.cuh"
 
 namespace gsfit {

@@ -7,9 +7,12 @@
 // 1e-4, C = sum c alpha T + T_N bg, A = 1 - T_N.
 //
 // Design: one CTA per tile (TILE = 16: eight pixel warps; 8: two), one pixel
-// per thread, warp w owning an 8 x 4 pixel box, plus one producer warp. Tiles
-// are launched in the heavy-first order gsfit_bin_sort produces, so the
-// longest lists do not form the tail of the grid. The producer gathers the
+// per thread, warp w owning an 8 x 4 pixel box, plus one producer warp. The
+// forward pass launches tiles in the order gsfit_bin_sort produces (most work
+// first, the empty tiles last), the adjoint in the order of the furthest
+// contributors the forward pass recorded, so the longest walks do not form the
+// tail of the grid; the CTAs of empty tiles leave at once (the forward pass's
+// after writing the background). The producer gathers the
 // tile's records into a ring of shared-memory slots (cp.async, mbarrier
 // hand-over, bounded waits); each pixel warp compacts, with a ballot, the slot
 // entries that can reach alpha >= 1/255 at one of its pixels still in play
