@@ -448,7 +448,9 @@ __global__ void __launch_bounds__(kLossThreads, kLossCtasPerSm) loss_kernel(
         if (__syncthreads_or(differ) == 0) {  // (also: the next item's location is visible)
             // the input region is no longer read: start the next item
             settled = start_item(next);
-            float ssim_n = 0.f, la = 0.f;
+            // the item's sums: L1 0, SSIM 1 per pixel (added as a count) and, in channel 0, the alpha
+            // term (a warp sum and one atomic per warp): no block reduction
+            float la = 0.f;
             const int cidx = tid % kOut, r0 = (tid / kOut) * 4;
 #pragma unroll
             for (int o = 0; o < 4; ++o) {
@@ -456,7 +458,6 @@ __global__ void __launch_bounds__(kLossThreads, kLossCtasPerSm) loss_kernel(
                 if (gy >= H || gx >= W) continue;
                 const long long q = (long long)gy * W + gx;
                 g_rgb[3ll * cam.pixel_offset + ch * P + q] = 0.0f;
-                ssim_n += 1.0f;
                 if (ch == 0) {
                     const float da = alpha[cam.pixel_offset + q] - At[q];
                     la += fabsf(da);
@@ -464,7 +465,11 @@ __global__ void __launch_bounds__(kLossThreads, kLossCtasPerSm) loss_kernel(
                         (da > 0.f ? 1.f : (da < 0.f ? -1.f : 0.f)) / ((float)P * (float)n_views);
                 }
             }
-            block_loss_sums(s_red, acc + 3 * v, 0.f, ssim_n, la);
+            if (ch == 0) {
+                la = warp_sum(la);
+                if (lane == 0 && la != 0.f) atomicAdd(&acc[3 * v + 2], la);
+            }
+            if (tid == 0) atomicAdd(&acc[3 * v + 1], (float)(min(kOut, W - ox) * min(kOut, H - oy)));
             continue;
         }
         // 2. horizontal pass of x, y, x^2 + y^2, xy: 52 rows x 42 columns in
