@@ -896,8 +896,10 @@ def main() -> None:
     dominant = max(stage_ms, key=stage_ms.get)
     # project 1; bin_sort: reduce, scan, compact, 4 depth passes, sorted
     # reduce + scan, emit, tile passes, ranges, 2 tile-order kernels; render 1;
-    # loss (memset node excluded) 2; adjoint: blend 1 + projection 1; adam 2
-    launches_per_step = 1 + (13 + tile_passes) + 1 + 2 + 2 + 2
+    # loss (memset node excluded): match pre-pass, loss, finalize 3; adjoint:
+    # order, blend, projection 3; adam 2 (25 per step with two tile passes, as
+    # in the launch list)
+    launches_per_step = 1 + (13 + tile_passes) + 1 + 3 + 3 + 2
     kernel_of = {"blend_bwd": "render_bwd_kernel", "render_fwd": "render_fwd_kernel", "loss": "loss_kernel",
                  "project": "project_kernel", "adam": "adam_kernel", "project_bwd": "project_bwd_kernel"}
     traffic = measured_traffic(kernel_of.get(dominant, dominant))
