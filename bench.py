@@ -203,10 +203,12 @@ def stage_bytes(st, n_inst: int, n_vis: int, tile_passes: int) -> dict:
         "loss": P * 4 * 12,
         # p, g, m, v read; p, m, v written: 28 bytes per parameter (float4 planes)
         "adam": npl * n * 16 * 7,
+        # the projection adjoint with Adam fused: p, m, v read and written (24
+        # bytes per parameter, no gradient buffer); the radius of every (view,
+        # Gaussian) record read (4 B); per binned record its 2D gradients read
+        # and zeroed (96 B) and its conic and colour read (32 B)
+        "project_bwd_adam": npl * n * 16 * 6 + V * n * 4 + n_vis * 128,
     }
-
-
-TIMED_STAGES = ("project", "bin_sort", "render_fwd", "loss", "blend_bwd", "project_bwd", "adam")
 
 
 def aggregate(ms_total: float, steps: int, world: int, device: str = "cuda") -> tuple:
@@ -224,10 +226,10 @@ def aggregate(ms_total: float, steps: int, world: int, device: str = "cuda") -> 
 
 def time_stages(st, reps: int) -> dict:
     import torch
-    evs = {k: [] for k in TIMED_STAGES}
+    evs = {k: [] for k in st.TIMED_STAGES}
     for _ in range(reps):
         marks = []
-        for name in TIMED_STAGES:
+        for name in st.TIMED_STAGES:
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
             getattr(st, name)()
@@ -660,7 +662,8 @@ def ct_periphery_leg(iters: int = 240, warmup: int = 10) -> dict:
            "iters_per_s": 1000.0 / ms, "ms_per_iter": ms, "iterations": iters,
            "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()}, "pairs_per_iter": n_inst,
            "blended_pairs": blended,
-           "hbm_frac": {k: round(sb[k] / (stage_ms[k] * 1e-3) / 1e9 / peaks["hbm_gbs"], 4) for k in sb},
+           "hbm_frac": {k: round(sb[k] / (stage_ms[k] * 1e-3) / 1e9 / peaks["hbm_gbs"], 4) for k in sb
+                        if k in stage_ms},
            "alu_tflops": {k: round(blended * f / (stage_ms[k] * 1e-3) / 1e12, 3) for k, f in FLOP_PER_BLEND.items()},
            "all_24_views_before": {"loss": loss0, "psnr_db": psnr0},
            "all_24_views_after": {"loss": loss1, "psnr_db": psnr1}}
@@ -881,13 +884,13 @@ def main() -> None:
         st.replay()
         reps.append(st.stage_times())
     # the median: robust to one slow replay (a reduced case showed the first one after the timed loop slow)
-    stage_ms = {k: float(np.median([r[k] for r in reps])) for k in TIMED_STAGES}
+    stage_ms = {k: float(np.median([r[k] for r in reps])) for k in st.TIMED_STAGES}
     stage_ms_eager = time_stages(st, reps=max(5, min(30, args.steps // 10)))
     blended = st.blended_pairs()
     tile_passes = max(1, (int(np.ceil(np.log2(max(2, st.T)))) + 7) // 8)
     sb = stage_bytes(st, n_inst, n_vis, tile_passes)
     peaks = measured_peaks()
-    hbm_stages = {k: sb[k] / (stage_ms[k] * 1e-3) / 1e9 for k in sb}
+    hbm_stages = {k: sb[k] / (stage_ms[k] * 1e-3) / 1e9 for k in sb if k in stage_ms}
     alu = measure_alu_peaks()
     # the FP32 denominator: the measured packed-FMA rate if higher (the
     # compositing kernels issue packed two-lane FMAs), else the scalar one
@@ -897,13 +900,15 @@ def main() -> None:
     # project 1; bin_sort: reduce, scan, compact, 4 depth passes, sorted
     # reduce + scan, emit, tile passes, ranges, 2 tile-order kernels; render 1;
     # loss (memset node excluded): match pre-pass, loss, finalize 3; adjoint:
-    # order, blend, projection 3; adam 2 (25 per step with two tile passes, as
-    # in the launch list)
-    launches_per_step = 1 + (13 + tile_passes) + 1 + 3 + 3 + 2
+    # order, blend 2; projection adjoint 1 and Adam 2 (25 per step with two
+    # tile passes, as in the launch list; fused, the projection adjoint with
+    # Adam and the step count 2)
+    launches_per_step = 1 + (13 + tile_passes) + 1 + 3 + 2 + (2 if st.fuse_adam else 3)
     kernel_of = {"blend_bwd": "render_bwd_kernel", "render_fwd": "render_fwd_kernel", "loss": "loss_kernel",
-                 "project": "project_kernel", "adam": "adam_kernel", "project_bwd": "project_bwd_kernel"}
+                 "project": "project_kernel", "adam": "adam_kernel", "project_bwd": "project_bwd_kernel",
+                 "project_bwd_adam": "project_bwd_adam_kernel"}
     traffic = measured_traffic(kernel_of.get(dominant, dominant))
-    if dominant in sb:
+    if dominant in hbm_stages:
         roof = {"kernel": dominant, "bound": "hbm", "achieved": hbm_stages[dominant], "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": hbm_stages[dominant] / peaks["hbm_gbs"], "traffic": traffic,
                 "peak_source": peaks["source"]}

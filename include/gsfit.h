@@ -14,6 +14,9 @@
  *                     adjoint of the projection, summed over views
  *   gsfit_adam_step   Adam update of all parameters
  *
+ * (gsfit_blend_bwd followed by gsfit_project_bwd_adam runs the last two
+ * stages with the projection adjoint and Adam fused into one pass.)
+ *
  * The paper does not write the splatting math out; every convention is that
  * of standard 3DGS (Kerbl et al. 2023, EWA splatting after Zwicker et al.
  * 2001) and is stated at each call below.
@@ -60,7 +63,7 @@
 extern "C" {
 #endif
 
-#define GSFIT_ABI_VERSION 9
+#define GSFIT_ABI_VERSION 10
 #define GSFIT_MAX_VIEWS 256
 #define GSFIT_TILE 16
 /* Words of a tile_order buffer for total_tiles tiles (gsfit_bin_sort):
@@ -443,6 +446,36 @@ int gsfit_blend_bwd(const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_
                     cudaStream_t stream);
 int gsfit_project_bwd(const gsfit_gaussians* g, const gsfit_proj* proj, const gsfit_camera* cams, int32_t n_views,
                       float* grad2d, float* grads, cudaStream_t stream);
+
+/*
+ * gsfit_project_bwd_adam -- gsfit_project_bwd and gsfit_adam_step in one
+ * pass over the Gaussians: the fit iteration's last two stages (the fitted
+ * 3DGS model of Section 4.2, with its Adam rates and restarts as in
+ * gsfit_adam_step). Each Gaussian's gradient, summed over the views, goes
+ * straight into its Adam update instead of through a gradient buffer, which
+ * saves writing and reading n_planes * n float4 and the gradient buffer
+ * itself. The gradient equals gsfit_project_bwd's up to rounding (the
+ * compiler may contract the chain's products and sums into fused
+ * multiply-adds differently in the two kernels); given that gradient, the
+ * update equals gsfit_adam_step's bit for bit. On GB300 the two separate
+ * calls are faster for the fit step: the fused pass runs at the projection
+ * adjoint's register budget, with too few warps in flight for Adam's
+ * stream.
+ * Arguments: g, proj, cams, n_views, grad2d as for gsfit_project_bwd (grad2d
+ *   zeroed again); g->params and, with a 16-bit feature type, g->features
+ *   are UPDATED IN PLACE, so both must be writable device memory; grads:
+ *   device, n_planes * n float4, or null; when given, it also receives the
+ *   gradient as gsfit_project_bwd writes it. m, v, lr, beta1, beta2, eps,
+ *   step: as for gsfit_adam_step, with n_planes = gsfit_num_planes
+ *   (g->sh_degree); *step is incremented on the device afterwards. status:
+ *   device int32 or null; a non-finite gradient sets GSFIT_ERR_NONFINITE
+ *   there, as gsfit_render_bwd does. params, grads, m and v are distinct
+ *   buffers.
+ * Errors: GSFIT_ERR_INVALID_ARG, GSFIT_ERR_CUDA.
+ */
+int gsfit_project_bwd_adam(const gsfit_gaussians* g, const gsfit_proj* proj, const gsfit_camera* cams,
+                           int32_t n_views, float* grad2d, float* grads, float* m, float* v, const float* lr,
+                           float beta1, float beta2, float eps, int32_t* step, int32_t* status, cudaStream_t stream);
 
 /*
  * gsfit_render_count -- diagnostic: the number of blended (pixel, Gaussian)

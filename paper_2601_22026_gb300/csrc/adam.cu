@@ -16,12 +16,6 @@ namespace gsfit {
 
 namespace {
 
-constexpr int kMaxPlanes = 16;
-
-struct LrTable {
-    float4 lr[kMaxPlanes];
-};
-
 template <int FT>
 __global__ void __launch_bounds__(256) adam_kernel(float4* __restrict__ p, const float4* __restrict__ g,
                                                    float4* __restrict__ m, float4* __restrict__ v, int n,
@@ -29,25 +23,13 @@ __global__ void __launch_bounds__(256) adam_kernel(float4* __restrict__ p, const
                                                    const int32_t* __restrict__ step, uint2* __restrict__ feat) {
     const int plane = blockIdx.y;
     const float4 lr = lrt.lr[plane];
-    const int t = *step + 1;
-    const float bc1 = 1.0f - powf(b1, (float)t);
-    const float bc2 = 1.0f - powf(b2, (float)t);
-    const float rbc2 = rsqrtf(bc2);
-    const float s1 = 1.0f / bc1;
+    const AdamCoef c = adam_coef(b1, b2, eps, *step);
     const size_t base = (size_t)plane * n;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const size_t k = base + i;
         const float4 gg = g[k];
         float4 mm = m[k], vv = v[k], pp = p[k];
-#define GSFIT_ADAM_LANE(c)                                                     \
-    mm.c = b1 * mm.c + (1.0f - b1) * gg.c;                                     \
-    vv.c = b2 * vv.c + (1.0f - b2) * gg.c * gg.c;                              \
-    pp.c -= lr.c * (mm.c * s1) / (sqrtf(vv.c) * rbc2 + eps);
-        GSFIT_ADAM_LANE(x)
-        GSFIT_ADAM_LANE(y)
-        GSFIT_ADAM_LANE(z)
-        GSFIT_ADAM_LANE(w)
-#undef GSFIT_ADAM_LANE
+        adam_update(pp, mm, vv, gg, lr, c);
         m[k] = mm;
         v[k] = vv;
         p[k] = pp;
@@ -68,6 +50,12 @@ __global__ void __launch_bounds__(256) refresh_kernel(const float4* __restrict__
 __global__ void step_increment_kernel(int32_t* step) { *step += 1; }
 
 }  // namespace
+
+int step_increment(int32_t* step, cudaStream_t s) {
+    step_increment_kernel<<<1, 1, 0, s>>>(step);
+    GSFIT_LAUNCH_CHECK();
+    return GSFIT_OK;
+}
 
 }  // namespace gsfit
 
@@ -108,9 +96,7 @@ extern "C" int gsfit_adam_step(float* params, const float* grads, float* m, floa
         adam_kernel<GSFIT_FEATURES_F32><<<grid, 256, 0, stream>>>(p4, g4, m4, v4, n, t, beta1, beta2, eps, step,
                                                                   nullptr);
     GSFIT_LAUNCH_CHECK();
-    step_increment_kernel<<<1, 1, 0, stream>>>(step);
-    GSFIT_LAUNCH_CHECK();
-    return GSFIT_OK;
+    return step_increment(step, stream);
 }
 
 extern "C" int gsfit_features_refresh(const float* params, int32_t n, int32_t n_planes, void* features,

@@ -245,4 +245,55 @@ __device__ __forceinline__ float4 load_plane(const float4* __restrict__ P, const
     }
 }
 
+// Adam (Kingma & Ba) with bias correction, shared by the plain update and the
+// update fused into the projection adjoint. At step t = done + 1 (done:
+// completed steps):
+//   m = b1 m + (1 - b1) g;  v = b2 v + (1 - b2) g^2;
+//   p -= lr (m / (1 - b1^t)) / (sqrt(v) / sqrt(1 - b2^t) + eps).
+// Each operation is an explicit round-to-nearest intrinsic, which the
+// compiler never contracts, so both kernels compute the same floats from the
+// same gradient.
+constexpr int kMaxPlanes = 16;
+
+struct LrTable {
+    float4 lr[kMaxPlanes];  // the rate of each component of each plane
+};
+
+struct AdamCoef {
+    float b1, b2, eps;
+    float omb1, omb2;  // 1 - b1, 1 - b2
+    float s1;          // 1 / (1 - b1^t)
+    float rbc2;        // 1 / sqrt(1 - b2^t)
+};
+
+__device__ __forceinline__ AdamCoef adam_coef(float b1, float b2, float eps, int32_t done) {
+    const int t = done + 1;
+    const float bc1 = __fsub_rn(1.0f, powf(b1, (float)t));
+    const float bc2 = __fsub_rn(1.0f, powf(b2, (float)t));
+    AdamCoef c;
+    c.b1 = b1;
+    c.b2 = b2;
+    c.eps = eps;
+    c.omb1 = __fsub_rn(1.0f, b1);
+    c.omb2 = __fsub_rn(1.0f, b2);
+    c.rbc2 = rsqrtf(bc2);
+    c.s1 = __fdiv_rn(1.0f, bc1);
+    return c;
+}
+
+__device__ __forceinline__ void adam_lane(float& p, float& m, float& v, float g, float lr, const AdamCoef& c) {
+    m = __fmaf_rn(c.b1, m, __fmul_rn(c.omb1, g));
+    v = __fmaf_rn(c.b2, v, __fmul_rn(__fmul_rn(c.omb2, g), g));
+    const float den = __fmaf_rn(sqrtf(v), c.rbc2, c.eps);
+    p = __fsub_rn(p, __fdiv_rn(__fmul_rn(lr, __fmul_rn(m, c.s1)), den));
+}
+
+__device__ __forceinline__ void adam_update(float4& p, float4& m, float4& v, float4 g, float4 lr,
+                                            const AdamCoef& c) {
+    adam_lane(p.x, m.x, v.x, g.x, lr.x, c);
+    adam_lane(p.y, m.y, v.y, g.y, lr.y, c);
+    adam_lane(p.z, m.z, v.z, g.z, lr.z, c);
+    adam_lane(p.w, m.w, v.w, g.w, lr.w, c);
+}
+
 }  // namespace gsfit

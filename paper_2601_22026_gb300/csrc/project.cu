@@ -14,6 +14,9 @@
 
 namespace gsfit {
 
+// Adds one to the device step count after an Adam update (adam.cu).
+int step_increment(int32_t* step, cudaStream_t s);
+
 namespace {
 
 // Real SH constants N_lm * (polynomial factor), from
@@ -414,23 +417,21 @@ __device__ __forceinline__ bool finite4(float4 q) {
     return isfinite(q.x) && isfinite(q.y) && isfinite(q.z) && isfinite(q.w);
 }
 
+// The gradient of Gaussian i summed over the views that binned it: planes
+// 0-2 (means and opacity logit, quaternion, log-scales) in gq, the SH planes
+// in this thread's shared-memory accumulators, which the caller zeroed.
+// Zeroes the records' 2D gradients it reads. Returns false, with gq zero,
+// for a Gaussian that no view binned: it contributes to no pixel, so its
+// gradient is zero (also where its parameters are not finite and the chain
+// would give 0 x NaN). P and F carry no __restrict__ here: the fused Adam
+// kernel updates them in place after this returns.
 template <int DEG, int FT>
-__global__ void __launch_bounds__(kProjBwdThreads, 2) project_bwd_kernel(
-    const float4* __restrict__ P, const uint2* __restrict__ F, int n, const gsfit_camera* __restrict__ cams_g,
-    int n_views, const float4* __restrict__ xyd, const float4* __restrict__ conic, const float4* __restrict__ rgbm,
-    float4* __restrict__ grad2d, float4* __restrict__ G, int32_t* __restrict__ status) {
-    // dynamic shared memory: the camera table, then 3K SH-gradient accumulators
-    // per thread (kept out of registers)
-    extern __shared__ __align__(16) unsigned char smem_pb[];
-    gsfit_camera* cams = reinterpret_cast<gsfit_camera*>(smem_pb);
-    float* s_dsh = reinterpret_cast<float*>(smem_pb + sizeof(gsfit_camera) * n_views);
+__device__ __forceinline__ bool gaussian_grad(const float4* P, const uint2* F, int n, int i,
+                                              const gsfit_camera* cams, int n_views,
+                                              const float4* __restrict__ xyd, const float4* __restrict__ conic,
+                                              const float4* __restrict__ rgbm, float4* __restrict__ grad2d,
+                                              float* s_dsh, float4 (&gq)[3]) {
     constexpr int K = SH<DEG>::K;
-    load_cameras(cams, cams_g, n_views);
-#pragma unroll
-    for (int k = 0; k < 3 * K; ++k) dsh_acc(s_dsh, k) = 0.f;
-    __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
     Gauss g;
     load_gauss<FT>(P, F, n, i, g);
 
@@ -486,13 +487,8 @@ __global__ void __launch_bounds__(kProjBwdThreads, 2) project_bwd_kernel(
         }
     }
     if (!binned) {
-        // a Gaussian no view binned contributes to no pixel: its gradient is
-        // zero (written as such, also where its parameters are not finite and
-        // the chain below would give 0 x NaN)
-        constexpr int NPL = 3 + (3 * K + 3) / 4;
-#pragma unroll
-        for (int p = 0; p < NPL; ++p) G[(size_t)p * n + i] = zero;
-        return;
+        gq[0] = gq[1] = gq[2] = zero;
+        return false;
     }
     const float opacity = 1.0f / (1.0f + expf(-g.logit));
     const float dlogit = dop * opacity * (1.f - opacity);
@@ -528,26 +524,135 @@ __global__ void __launch_bounds__(kProjBwdThreads, 2) project_bwd_kernel(
     const float4 g1 = make_float4((dq[0] - w * qd) * iq, (dq[1] - x * qd) * iq, (dq[2] - y * qd) * iq,
                                   (dq[3] - z * qd) * iq);
     const float4 g2 = make_float4(dls[0], dls[1], dls[2], 0.f);
-    G[i] = g0;
-    G[(size_t)n + i] = g1;
-    G[2 * (size_t)n + i] = g2;
-    bool finite = finite4(g0) && finite4(g1) && finite4(g2);
-    constexpr int K3 = 3 * K;
-    constexpr int NP = (K3 + 3) / 4;
+    gq[0] = make_float4(dmean[0], dmean[1], dmean[2], dlogit);
+    gq[1] = make_float4((dq[0] - w * qd) * iq, (dq[1] - x * qd) * iq, (dq[2] - y * qd) * iq, (dq[3] - z * qd) * iq);
+    gq[2] = make_float4(dls[0], dls[1], dls[2], 0.f);
+    return true;
+}
+
+// This thread's SH gradient plane q (3 K accumulators, zero past them).
+template <int DEG>
+__device__ __forceinline__ float4 sh_grad_plane(float* s_dsh, int q) {
+    constexpr int K3 = 3 * SH<DEG>::K;
+    float4 r;
+    r.x = (4 * q + 0 < K3) ? dsh_acc(s_dsh, 4 * q + 0) : 0.f;
+    r.y = (4 * q + 1 < K3) ? dsh_acc(s_dsh, 4 * q + 1) : 0.f;
+    r.z = (4 * q + 2 < K3) ? dsh_acc(s_dsh, 4 * q + 2) : 0.f;
+    r.w = (4 * q + 3 < K3) ? dsh_acc(s_dsh, 4 * q + 3) : 0.f;
+    return r;
+}
+
+template <int DEG, int FT>
+__global__ void __launch_bounds__(kProjBwdThreads, 2) project_bwd_kernel(
+    const float4* __restrict__ P, const uint2* __restrict__ F, int n, const gsfit_camera* __restrict__ cams_g,
+    int n_views, const float4* __restrict__ xyd, const float4* __restrict__ conic, const float4* __restrict__ rgbm,
+    float4* __restrict__ grad2d, float4* __restrict__ G, int32_t* __restrict__ status) {
+    // dynamic shared memory: the camera table, then 3K SH-gradient accumulators
+    // per thread (kept out of registers)
+    extern __shared__ __align__(16) unsigned char smem_pb[];
+    gsfit_camera* cams = reinterpret_cast<gsfit_camera*>(smem_pb);
+    float* s_dsh = reinterpret_cast<float*>(smem_pb + sizeof(gsfit_camera) * n_views);
+    constexpr int K = SH<DEG>::K;
+    load_cameras(cams, cams_g, n_views);
+#pragma unroll
+    for (int k = 0; k < 3 * K; ++k) dsh_acc(s_dsh, k) = 0.f;
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float4 gq[3];
+    const bool binned = gaussian_grad<DEG, FT>(P, F, n, i, cams, n_views, xyd, conic, rgbm, grad2d, s_dsh, gq);
+    constexpr int NP = (3 * K + 3) / 4;
+    bool finite = finite4(gq[0]) && finite4(gq[1]) && finite4(gq[2]);
+#pragma unroll
+    for (int p = 0; p < 3; ++p) G[(size_t)p * n + i] = gq[p];
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-        float4 q;
-        q.x = (4 * p + 0 < K3) ? dsh_acc(s_dsh, 4 * p + 0) : 0.f;
-        q.y = (4 * p + 1 < K3) ? dsh_acc(s_dsh, 4 * p + 1) : 0.f;
-        q.z = (4 * p + 2 < K3) ? dsh_acc(s_dsh, 4 * p + 2) : 0.f;
-        q.w = (4 * p + 3 < K3) ? dsh_acc(s_dsh, 4 * p + 3) : 0.f;
+        const float4 q = sh_grad_plane<DEG>(s_dsh, p);
         G[(size_t)(3 + p) * n + i] = q;
         finite = finite && finite4(q);
     }
     // a non-finite gradient (from a non-finite image, cotangent or 2D
     // gradient upstream) is reported, not hidden: the first such Gaussian sets
     // the status word unless an earlier error already has
-    if (!finite && status) atomicCAS(status, GSFIT_OK, GSFIT_ERR_NONFINITE);
+    if (binned && !finite && status) atomicCAS(status, GSFIT_OK, GSFIT_ERR_NONFINITE);
+}
+
+// Adam over the C planes p0 .. p0 + C - 1 of Gaussian i: every load of the
+// chunk first, then the updates and stores (G, when given, receives the
+// gradient; F the 16-bit copy of the SH planes).
+template <int C, int FT, int NG>
+__device__ __forceinline__ void adam_chunk(float4* P, uint2* F, float4* __restrict__ m, float4* __restrict__ v,
+                                           float4* __restrict__ G, int n, int i, int p0, const float4 (&g)[NG],
+                                           const float4* s_lr, const AdamCoef& c) {
+    static_assert(C <= NG, "chunk larger than its gradients");
+    float4 pp[C], mm[C], vv[C];
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+        const size_t k = (size_t)(p0 + j) * n + i;
+        pp[j] = P[k];
+        mm[j] = m[k];
+        vv[j] = v[k];
+    }
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+        const size_t k = (size_t)(p0 + j) * n + i;
+        if (G) G[k] = g[j];
+        adam_update(pp[j], mm[j], vv[j], g[j], s_lr[p0 + j], c);
+        P[k] = pp[j];
+        m[k] = mm[j];
+        v[k] = vv[j];
+        if constexpr (FT != GSFIT_FEATURES_F32) {
+            if (p0 + j >= kFeaturePlane0) F[(size_t)(p0 + j - kFeaturePlane0) * n + i] = pack_features<FT>(pp[j]);
+        }
+    }
+}
+
+// project_bwd_kernel and the Adam update in one pass: each thread takes its
+// Gaussian's gradient from gaussian_grad straight into adam_update (the same
+// arithmetic as adam_kernel) plane by plane, so the gradient never goes
+// through memory unless G is given. P and F (the 16-bit copy of the SH
+// planes) are read by the chain and then rewritten by the same thread only.
+template <int DEG, int FT>
+__global__ void __launch_bounds__(kProjBwdThreads, 2) project_bwd_adam_kernel(
+    float4* P, uint2* F, int n, const gsfit_camera* __restrict__ cams_g, int n_views,
+    const float4* __restrict__ xyd, const float4* __restrict__ conic, const float4* __restrict__ rgbm,
+    float4* __restrict__ grad2d, float4* __restrict__ G, float4* __restrict__ m, float4* __restrict__ v,
+    LrTable lrt, float b1, float b2, float eps, const int32_t* __restrict__ step, int32_t* __restrict__ status) {
+    extern __shared__ __align__(16) unsigned char smem_pb[];
+    __shared__ float4 s_lr[kMaxPlanes];
+    gsfit_camera* cams = reinterpret_cast<gsfit_camera*>(smem_pb);
+    float* s_dsh = reinterpret_cast<float*>(smem_pb + sizeof(gsfit_camera) * n_views);
+    constexpr int K = SH<DEG>::K;
+    constexpr int NP = (3 * K + 3) / 4;
+    load_cameras(cams, cams_g, n_views);
+    if (threadIdx.x < kMaxPlanes) s_lr[threadIdx.x] = lrt.lr[threadIdx.x];
+#pragma unroll
+    for (int k = 0; k < 3 * K; ++k) dsh_acc(s_dsh, k) = 0.f;
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float4 gq[3];
+    const bool binned = gaussian_grad<DEG, FT>(P, F, n, i, cams, n_views, xyd, conic, rgbm, grad2d, s_dsh, gq);
+    const AdamCoef c = adam_coef(b1, b2, eps, *step);
+    bool finite = finite4(gq[0]) && finite4(gq[1]) && finite4(gq[2]);
+    // planes 0-2, then the SH planes three at a time: each chunk loads all its
+    // parameters and moments before its first store, so a thread has a
+    // chunk's loads in flight at once (a later plane's loads cannot move above
+    // an earlier plane's stores to P, which the compiler cannot tell apart)
+    adam_chunk<3, FT>(P, F, m, v, G, n, i, 0, gq, s_lr, c);
+#pragma unroll
+    for (int q0 = 0; q0 < NP; q0 += 3) {
+        float4 gg[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            gg[j] = q0 + j < NP ? sh_grad_plane<DEG>(s_dsh, q0 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+            finite = finite && finite4(gg[j]);
+        }
+        if (NP - q0 >= 3) adam_chunk<3, FT>(P, F, m, v, G, n, i, 3 + q0, gg, s_lr, c);
+        else if (NP - q0 == 2) adam_chunk<2, FT>(P, F, m, v, G, n, i, 3 + q0, gg, s_lr, c);
+        else adam_chunk<1, FT>(P, F, m, v, G, n, i, 3 + q0, gg, s_lr, c);
+    }
+    if (binned && !finite && status) atomicCAS(status, GSFIT_OK, GSFIT_ERR_NONFINITE);
 }
 
 template <int DEG, int FT>
@@ -605,6 +710,50 @@ int project_bwd_ft(const gsfit_gaussians* g, const gsfit_proj* proj, const gsfit
     }
 }
 
+// The Adam arguments of the fused adjoint, as gsfit_adam_step takes them.
+struct AdamArgs {
+    float* m;
+    float* v;
+    LrTable lrt;
+    float b1, b2, eps;
+    int32_t* step;
+};
+
+template <int DEG, int FT>
+int launch_project_bwd_adam(const gsfit_gaussians* g, const gsfit_proj* proj, const gsfit_camera* cams, int V,
+                            float* grad2d, float* grads, const AdamArgs& a, int32_t* status, cudaStream_t s) {
+    const int threads = kProjBwdThreads;
+    const int blocks = (g->n + threads - 1) / threads;
+    // the parameters and their 16-bit copy are updated in place
+    float4* P = reinterpret_cast<float4*>(const_cast<float*>(g->params));
+    uint2* F = reinterpret_cast<uint2*>(const_cast<void*>(g->features));
+    const size_t smem = sizeof(gsfit_camera) * V + sizeof(float) * 3 * SH<DEG>::K * threads;
+    static ContextOnce once;
+    const size_t max_smem = sizeof(gsfit_camera) * GSFIT_MAX_VIEWS + sizeof(float) * 3 * SH<DEG>::K * threads;
+    const int rc = opt_in_smem(once, project_bwd_adam_kernel<DEG, FT>, max_smem);
+    if (rc != GSFIT_OK) return rc;
+    project_bwd_adam_kernel<DEG, FT><<<blocks, threads, smem, s>>>(
+        P, F, g->n, cams, V, reinterpret_cast<const float4*>(proj->xyd), reinterpret_cast<const float4*>(proj->conic),
+        reinterpret_cast<const float4*>(proj->rgb), reinterpret_cast<float4*>(grad2d),
+        reinterpret_cast<float4*>(grads), reinterpret_cast<float4*>(a.m), reinterpret_cast<float4*>(a.v), a.lrt,
+        a.b1, a.b2, a.eps, a.step, status);
+    GSFIT_LAUNCH_CHECK();
+    return step_increment(a.step, s);
+}
+
+template <int DEG>
+int project_bwd_adam_ft(const gsfit_gaussians* g, const gsfit_proj* proj, const gsfit_camera* cams, int V,
+                        float* grad2d, float* grads, const AdamArgs& a, int32_t* status, cudaStream_t s) {
+    switch (g->feature_dtype) {
+        case GSFIT_FEATURES_F16:
+            return launch_project_bwd_adam<DEG, GSFIT_FEATURES_F16>(g, proj, cams, V, grad2d, grads, a, status, s);
+        case GSFIT_FEATURES_BF16:
+            return launch_project_bwd_adam<DEG, GSFIT_FEATURES_BF16>(g, proj, cams, V, grad2d, grads, a, status, s);
+        default:
+            return launch_project_bwd_adam<DEG, GSFIT_FEATURES_F32>(g, proj, cams, V, grad2d, grads, a, status, s);
+    }
+}
+
 }  // namespace
 
 bool valid_gaussians(const gsfit_gaussians* g) {
@@ -648,5 +797,33 @@ extern "C" int gsfit_project(const gsfit_gaussians* g, const gsfit_camera* cams,
         case 1: return gsfit::project_ft<1>(g, cams, n_views, out, stream);
         case 2: return gsfit::project_ft<2>(g, cams, n_views, out, stream);
         default: return gsfit::project_ft<3>(g, cams, n_views, out, stream);
+    }
+}
+
+extern "C" int gsfit_project_bwd_adam(const gsfit_gaussians* g, const gsfit_proj* proj, const gsfit_camera* cams,
+                                      int32_t n_views, float* grad2d, float* grads, float* m, float* v,
+                                      const float* lr, float beta1, float beta2, float eps, int32_t* step,
+                                      int32_t* status, cudaStream_t stream) {
+    if (!gsfit::valid_gaussians(g) || !gsfit::valid_proj(proj) || !cams || n_views < 1 || n_views > GSFIT_MAX_VIEWS || !grad2d ||
+        !m || !v || !lr || !step)
+        return GSFIT_ERR_INVALID_ARG;
+    for (const float* q : {(const float*)grad2d, (const float*)grads, (const float*)m, (const float*)v})
+        if ((reinterpret_cast<uintptr_t>(q) % 16) != 0) return GSFIT_ERR_INVALID_ARG;
+    const int n_planes = gsfit_num_planes(g->sh_degree);
+    gsfit::AdamArgs a;
+    a.m = m;
+    a.v = v;
+    for (int k = 0; k < gsfit::kMaxPlanes; ++k)
+        a.lrt.lr[k] = k < n_planes ? make_float4(lr[4 * k], lr[4 * k + 1], lr[4 * k + 2], lr[4 * k + 3])
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+    a.b1 = beta1;
+    a.b2 = beta2;
+    a.eps = eps;
+    a.step = step;
+    switch (g->sh_degree) {
+        case 0: return gsfit::project_bwd_adam_ft<0>(g, proj, cams, n_views, grad2d, grads, a, status, stream);
+        case 1: return gsfit::project_bwd_adam_ft<1>(g, proj, cams, n_views, grad2d, grads, a, status, stream);
+        case 2: return gsfit::project_bwd_adam_ft<2>(g, proj, cams, n_views, grad2d, grads, a, status, stream);
+        default: return gsfit::project_bwd_adam_ft<3>(g, proj, cams, n_views, grad2d, grads, a, status, stream);
     }
 }

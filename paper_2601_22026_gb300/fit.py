@@ -73,7 +73,8 @@ class FitState:
     def __init__(self, gaussians: dict, cams: dict, *, target_rgb=None, target_alpha=None, bg=None,
                  capacity: int | None = None, lr: dict | None = None, eps: float = 1e-15,
                  lam: float = 0.2, features: str = "f32", tile: int = 16, batch: int = 128,
-                 batch_bwd: int = 64, exp_half2: bool = False, keep_keys: bool = False, device: str = "cuda"):
+                 batch_bwd: int = 64, exp_half2: bool = False, keep_keys: bool = False, fuse_adam: bool = False,
+                 keep_grads: bool = False, device: str = "cuda"):
         """features: "f32", or "f16" / "bf16" for the mixed-precision form
         (16-bit copy of the SH coefficients read by the projection, kept
         current by Adam; float32 master parameters and moments).
@@ -84,9 +85,19 @@ class FitState:
         (the half2 option of the mixed-precision form).
         keep_keys: also write the sorted (tile, depth) keys to self.keys; the
         fit needs only the lists and ranges, which the sort then produces
-        with 32-bit tile keys."""
+        with 32-bit tile keys.
+        fuse_adam: step() runs the projection adjoint and Adam as one pass
+        (gsfit_project_bwd_adam), which passes each Gaussian's gradient
+        straight into its update and needs no gradient buffer; on GB300 the
+        two separate kernels are faster (the fused pass runs at the register
+        budget of the projection adjoint, too few warps for Adam's stream),
+        so it is off by default. keep_grads: that pass also writes the
+        gradient to self.grads (render_bwd() and project_bwd() always do)."""
         self.device = device
         self.keep_keys = bool(keep_keys)
+        self.fuse_adam = bool(fuse_adam)
+        self.keep_grads = bool(keep_grads)
+        self.TIMED_STAGES = self.TIMED_STAGES_FUSED if self.fuse_adam else self.TIMED_STAGES_SEPARATE
         self.tile = int(tile)
         self.exp_half2 = bool(exp_half2)
         self.opts = G.RenderOpts(self.tile, int(batch), int(self.exp_half2), int(batch_bwd))
@@ -281,6 +292,11 @@ class FitState:
         G.gsfit_project_bwd(self.params, self.n, self.sh_degree, self.proj, self.cams_dev, self.V, self.grad2d,
                             self.grads, stream, self.features, self.feature_dtype)
 
+    def project_bwd_adam(self, stream=None):
+        G.gsfit_project_bwd_adam(self.params, self.n, self.sh_degree, self.proj, self.cams_dev, self.V, self.grad2d,
+                                 self.grads if self.keep_grads else None, self.m, self.v, self.lr, 0.9, 0.999,
+                                 self.eps, self.step_count, stream, self.features, self.feature_dtype, self.status)
+
     def blended_pairs(self) -> int:
         """Blended (pixel, Gaussian) pairs of the last forward pass (syncs)."""
         cnt = torch.zeros(1, dtype=torch.int64, device=self.device)
@@ -317,12 +333,17 @@ class FitState:
     def step(self, stream=None, marks: "StageMarks | None" = None):
         """One fit iteration (no host synchronisation). marks: timing events
         recorded before the first stage and after each of TIMED_STAGES (the
-        adjoint as its two halves, the same kernels as render_bwd)."""
+        adjoint as its two halves, the same kernels as render_bwd; with
+        fuse_adam the second half and Adam as one stage)."""
         if marks is None:
             self.forward(stream)
             self.loss(stream)
-            self.render_bwd(stream)
-            self.adam(stream)
+            if self.fuse_adam:
+                self.blend_bwd(stream)
+                self.project_bwd_adam(stream)
+            else:
+                self.render_bwd(stream)
+                self.adam(stream)
             return
         marks.record(0, stream)
         for k, name in enumerate(self.TIMED_STAGES):
@@ -331,7 +352,9 @@ class FitState:
             marks.record(k + 1, stream)
 
     STAGES = ("project", "bin_sort", "render_fwd", "loss", "render_bwd", "adam")
-    TIMED_STAGES = ("project", "bin_sort", "render_fwd", "loss", "blend_bwd", "project_bwd", "adam")
+    TIMED_STAGES_SEPARATE = ("project", "bin_sort", "render_fwd", "loss", "blend_bwd", "project_bwd", "adam")
+    TIMED_STAGES_FUSED = ("project", "bin_sort", "render_fwd", "loss", "blend_bwd", "project_bwd_adam")
+    TIMED_STAGES = TIMED_STAGES_SEPARATE  # the default state's; each state sets its own from fuse_adam
 
     # -- graphs ---------------------------------------------------------
     def capture(self, warmup: int = 1, stage_marks: bool = False):

@@ -44,7 +44,7 @@ class Gaussians(ctypes.Structure):
                 ("reserved", _i32)]
 
 
-ABI_VERSION = 9  # GSFIT_ABI_VERSION of include/gsfit.h
+ABI_VERSION = 10  # GSFIT_ABI_VERSION of include/gsfit.h
 
 # gsfit_gaussians.feature_dtype values (GSFIT_FEATURES_*)
 FEATURES = {"f32": 0, "f16": 1, "bf16": 2}
@@ -86,6 +86,8 @@ SIGNATURES = {
                                         _P]),
     "gsfit_blend_bwd": (ctypes.c_int, [_P, _P, _i32, _i32, _i32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "gsfit_project_bwd": (ctypes.c_int, [_P, _P, _P, _i32, _P, _P, _P]),
+    "gsfit_project_bwd_adam": (ctypes.c_int, [_P, _P, _P, _i32, _P, _P, _P, _P, _P, _f32, _f32, _f32, _P, _P,
+                                              _P]),
     "gsfit_render_count": (ctypes.c_int, [_P, _P, _i32, _i32, _i32, _P, _P, _P, _P, _P, _P, _P]),
     "gsfit_render_autotune": (ctypes.c_int, [_P, _P, _i32, _i32, _i32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                                              _i32, _i32, _P, _P, _P, _P]),
@@ -363,6 +365,22 @@ def gsfit_project_bwd(params, n, sh_degree, proj: ProjBuffers, cams_dev, n_views
     _check(load().gsfit_project_bwd(ctypes.byref(g), ctypes.byref(p), _ptr(cams_dev), n_views, _ptr(grad2d),
                                     _ptr(grads), _stream(stream)),
            "gsfit_project_bwd")
+
+
+def gsfit_project_bwd_adam(params, n, sh_degree, proj: ProjBuffers, cams_dev, n_views, grad2d, grads, m, v,
+                           lr: np.ndarray, beta1, beta2, eps, step, stream=None, features=None, feature_dtype=0,
+                           status=None):
+    """The projection adjoint and Adam in one pass; params (and features)
+    are updated in place; grads may be None (the gradient is then not
+    written)."""
+    lr = np.ascontiguousarray(lr, dtype=np.float32).reshape(-1)
+    assert lr.size == 4 * num_planes(sh_degree)
+    g = gaussians_struct(params, n, sh_degree, features, feature_dtype)
+    p = proj.struct()
+    _check(load().gsfit_project_bwd_adam(ctypes.byref(g), ctypes.byref(p), _ptr(cams_dev), n_views, _ptr(grad2d),
+                                         _ptr(grads), _ptr(m), _ptr(v), lr.ctypes.data_as(_P), float(beta1),
+                                         float(beta2), float(eps), _ptr(step), _ptr(status), _stream(stream)),
+           "gsfit_project_bwd_adam")
 
 
 def gsfit_render_count(proj: ProjBuffers, cams_dev, n_views, n, total_tiles, vals, ranges, n_contrib, count,

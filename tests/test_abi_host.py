@@ -37,7 +37,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version_and_status_strings(lib):
-    assert lib.gsfit_abi_version() == 9
+    assert lib.gsfit_abi_version() == 10
     assert lib.gsfit_status_string(G.GSFIT_ERR_CAPACITY) == b"instance capacity exceeded"
     assert lib.gsfit_status_string(G.GSFIT_ERR_TIMEOUT) == b"bounded device wait ran out"
 
@@ -115,6 +115,27 @@ def test_loss_workspace_size_with_match_flags(lib):
     assert lib.gsfit_loss_workspace_size(None, G.GSFIT_MAX_VIEWS + 1) == 0
     # the tile order: permutation, count, furthest contributors, the adjoint's order, count
     assert G.tile_order_words(table.total_tiles) == 3 * table.total_tiles + 2
+
+
+def test_fused_adjoint_adam_arguments_rejected_on_host(lib):
+    """The projection adjoint with Adam: missing moments, learning rates or
+    step count, misaligned buffers and a 16-bit feature type without its copy
+    are refused before any launch."""
+    fake = 256
+    g = G.Gaussians(fake, 10, 3)
+    p = G.Proj(fake, fake, fake, fake)
+    lr = (ctypes.c_float * 64)()
+    call = lambda gg, grad2d, grads, m, v, lrp, step: lib.gsfit_project_bwd_adam(
+        ctypes.byref(gg), ctypes.byref(p), fake, 2, grad2d, grads, m, v, lrp, 0.9, 0.999, 1e-15, step, None, None)
+    for args in [(fake, None, None, fake, lr, fake), (fake, None, fake, None, lr, fake),
+                 (fake, None, fake, fake, None, fake), (fake, None, fake, fake, lr, None),
+                 (None, None, fake, fake, lr, fake), (fake + 4, None, fake, fake, lr, fake),
+                 (fake, fake + 8, fake, fake, lr, fake), (fake, None, fake + 4, fake, lr, fake)]:
+        assert call(g, *args) == G.GSFIT_ERR_INVALID_ARG
+    half = G.Gaussians(fake, 10, 3, None, G.FEATURES["f16"], 0)
+    assert call(half, fake, None, fake, fake, lr, fake) == G.GSFIT_ERR_INVALID_ARG
+    assert lib.gsfit_project_bwd_adam(None, ctypes.byref(p), fake, 2, fake, None, fake, fake, lr, 0.9, 0.999,
+                                      1e-15, fake, None, None) == G.GSFIT_ERR_INVALID_ARG
 
 
 def test_reproject_alignment_rejected_on_host(lib):

@@ -125,4 +125,12 @@ def test_non_finite_gradient_is_reported():
     torch.cuda.synchronize()
     assert st.check_status() == G.GSFIT_ERR_NONFINITE
     assert not torch.isfinite(st.grads).all()
+    # the projection adjoint fused with Adam reports it the same way
+    st.status.zero_()
+    st.keep_grads = True
+    st.blend_bwd()
+    st.project_bwd_adam()
+    torch.cuda.synchronize()
+    assert st.check_status() == G.GSFIT_ERR_NONFINITE
+    assert not torch.isfinite(st.grads).all()
     _small_step_works()

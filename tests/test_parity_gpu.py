@@ -27,6 +27,7 @@ def _built():
 def _fit_state(gs, cams, bg=None, **kw):
     from paper_2601_22026_gb300.fit import FitState
     kw.setdefault("keep_keys", True)  # these tests compare the sorted keys too
+    kw.setdefault("keep_grads", True)  # and read the gradient after a fused step
     return FitState(gs, cams, bg=bg, **kw)
 
 
@@ -605,6 +606,89 @@ def test_adam_matches_oracle():
     torch.cuda.synchronize()
     assert int(step.item()) == 3
     np.testing.assert_allclose(P.cpu().numpy().reshape(-1), rp, rtol=0, atol=2e-6)
+
+
+FUSED_CASES = [("sh1_ragged", "f32"), ("sh3_uneven_views", "f32"), ("sh3_uneven_views", "f16"),
+               ("big_splats", "bf16"), ("max_views", "f32"), ("deg0", "f32")]
+
+
+@pytest.mark.parametrize("name,features", FUSED_CASES)
+def test_fused_adjoint_adam_equals_separate(name, features):
+    """gsfit_project_bwd_adam against gsfit_project_bwd and gsfit_adam_step,
+    both from the same 2D gradients (one blend adjoint whose output is copied:
+    its float atomics sum in no fixed order), after two fused steps so that
+    the moments and bias corrections are not trivial. The kept gradient
+    equals the separate kernel's up to rounding (the two kernels contract the
+    chain's products and sums into fused multiply-adds differently; the SH
+    planes, plain sums, agree exactly); the Adam part is exact: gsfit_adam_step
+    applied to the kept gradient gives the fused pass's parameters, moments
+    and 16-bit copy bit for bit. The 2D gradients are zero again and the step
+    count advances once."""
+    if name == "deg0":
+        gs, cams = scenes.random_gaussians(700, 0, 19, log_scale_mean=-2.6), _uneven_views()
+        bg = scenes.backgrounds(len(cams["width"]), 77)
+    else:
+        gs, cams, bg = _case(name)
+    st = _fit_state(gs, cams, bg, features=features)
+    st.forward()
+    torch.cuda.synchronize()
+    P = st.P
+    st.dL_drgb.copy_(torch.from_numpy(scenes.cotangents(3 * P, 31, 1e-3)))
+    st.dL_dalpha.copy_(torch.from_numpy(scenes.cotangents(P, 32, 1e-3)))
+    for _ in range(2):
+        st.blend_bwd()
+        st.project_bwd_adam()
+    st.blend_bwd()
+    names = ["params", "m", "v", "step_count", "grad2d"] + (["features"] if st.features is not None else [])
+    before = {k: getattr(st, k).clone() for k in names}
+    assert float(before["grad2d"].abs().max().item()) > 0.0
+    st.project_bwd()
+    separate_grads = st.grads.clone()
+    for k in names:
+        getattr(st, k).copy_(before[k])
+    st.grads.fill_(float("nan"))
+    st.project_bwd_adam()
+    torch.cuda.synchronize()
+    assert st.check_status() == 0
+    assert int(st.step_count.item()) == 3
+    assert float(st.grad2d.abs().max().item()) == 0.0
+    fused = {k: getattr(st, k).clone() for k in names}
+    kept = st.grads.clone()
+    # the gradient: up to rounding, relative to each plane component's scale
+    a, b = kept.cpu().numpy().astype(np.float64), separate_grads.cpu().numpy().astype(np.float64)
+    scale = np.abs(b).max(axis=1, keepdims=True)
+    assert np.all(np.abs(a - b) <= 1e-5 * scale + 1e-4 * np.abs(b)), np.abs(a - b).max()
+    assert np.array_equal(a[3:], b[3:]), "the SH planes' gradients are plain sums"
+    # the Adam part: the separate update from the kept gradient, bit for bit
+    for k in names:
+        getattr(st, k).copy_(before[k])
+    st.grads.copy_(kept)
+    st.adam()
+    torch.cuda.synchronize()
+    for k in ("params", "m", "v", "step_count") + (("features",) if st.features is not None else ()):
+        assert torch.equal(getattr(st, k), fused[k]), k
+    assert not torch.equal(fused["params"], before["params"])
+
+
+def test_fused_adjoint_adam_without_gradient_output():
+    """Without a gradient buffer the fused pass updates the same parameters
+    and leaves the caller's gradient buffer untouched."""
+    gs, cams, bg = _case("sh3_uneven_views")
+    a = _fit_state(gs, cams, bg)
+    b = _fit_state(gs, cams, bg, keep_grads=False)
+    for st in (a, b):
+        st.forward()
+        torch.cuda.synchronize()
+        st.dL_drgb.copy_(torch.from_numpy(scenes.cotangents(3 * st.P, 41, 1e-3)))
+        st.dL_dalpha.copy_(torch.from_numpy(scenes.cotangents(st.P, 42, 1e-3)))
+    b.grads.fill_(7.0)
+    a.blend_bwd()
+    b.grad2d.copy_(a.grad2d)
+    a.project_bwd_adam()
+    b.project_bwd_adam()
+    torch.cuda.synchronize()
+    assert torch.equal(a.params, b.params) and torch.equal(a.m, b.m) and torch.equal(a.v, b.v)
+    assert bool((b.grads == 7.0).all())
 
 
 def test_full_step_plain_single_view():
