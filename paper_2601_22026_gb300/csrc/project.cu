@@ -424,7 +424,9 @@ __device__ __forceinline__ bool finite4(float4 q) {
 // for a Gaussian that no view binned: it contributes to no pixel, so its
 // gradient is zero (also where its parameters are not finite and the chain
 // would give 0 x NaN). P and F carry no __restrict__ here: the fused Adam
-// kernel updates them in place after this returns.
+// kernel updates them in place after this returns. (project_bwd_kernel keeps
+// its own copy of this chain: calling this function from it measured 5%
+// slower.)
 template <int DEG, int FT>
 __device__ __forceinline__ bool gaussian_grad(const float4* P, const uint2* F, int n, int i,
                                               const gsfit_camera* cams, int n_views,
@@ -559,22 +561,123 @@ __global__ void __launch_bounds__(kProjBwdThreads, 2) project_bwd_kernel(
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    float4 gq[3];
-    const bool binned = gaussian_grad<DEG, FT>(P, F, n, i, cams, n_views, xyd, conic, rgbm, grad2d, s_dsh, gq);
-    constexpr int NP = (3 * K + 3) / 4;
-    bool finite = finite4(gq[0]) && finite4(gq[1]) && finite4(gq[2]);
+    Gauss g;
+    load_gauss<FT>(P, F, n, i, g);
+
+    float dmean[3] = {0.f, 0.f, 0.f};
+    float dSig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // xx xy xz yy yz zz (symmetric, dL/dSigma_ij)
+    float dop = 0.f;
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    bool binned = false;  // some view binned this Gaussian
+
+    for (int v0 = 0; v0 < n_views; v0 += 32) {
+        // visibility of up to 32 views first: independent loads, one latency
+        uint32_t vis = 0;
+        const int vn = min(32, n_views - v0);
+#pragma unroll 8
+        for (int k = 0; k < vn; ++k)
+            if (__ldg(&xyd[(size_t)(v0 + k) * n + i].w) != 0.0f) vis |= 1u << k;
+        if (!vis) continue;
+        binned = true;
+        int v = v0 + __ffs(vis) - 1;
+        vis &= vis - 1;
+        RecIn cur = load_rec(grad2d, conic, rgbm, (size_t)v * n + i);
+        for (;;) {
+            // the next binned view's loads go out before this view's chain
+            const int vnext = vis ? v0 + __ffs(vis) - 1 : -1;
+            vis &= vis - 1;
+            RecIn nxt;
+            if (vnext >= 0) nxt = load_rec(grad2d, conic, rgbm, (size_t)vnext * n + i);
+            const size_t r = (size_t)v * n + i;
+            grad2d[4 * r + 0] = zero;  // the adjoint's atomics fill these three
+            grad2d[4 * r + 1] = zero;
+            grad2d[4 * r + 2] = zero;
+            const gsfit_camera& cam = cams[v];
+            float dm[3], dS[6], gcol[3];
+            record_bwd<DEG, FT>(cam, g, cur.ga, cur.gb, cur.gc, cur.cq, cur.cm, P, F, n, i, dm, dS, gcol);
+            dmean[0] += dm[0]; dmean[1] += dm[1]; dmean[2] += dm[2];
+            dop += cur.ga.z;
 #pragma unroll
-    for (int p = 0; p < 3; ++p) G[(size_t)p * n + i] = gq[p];
+            for (int k = 0; k < 6; ++k) dSig[k] += dS[k];
+            float dx = g.mx - cam.campos[0], dy = g.my - cam.campos[1], dz = g.mz - cam.campos[2];
+            const float idist = rsqrtf(dx * dx + dy * dy + dz * dz);
+            dx *= idist; dy *= idist; dz *= idist;
+            float Y[K];
+            sh_basis<DEG>(dx, dy, dz, Y);
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                dsh_acc(s_dsh, 3 * k + 0) += Y[k] * gcol[0];
+                dsh_acc(s_dsh, 3 * k + 1) += Y[k] * gcol[1];
+                dsh_acc(s_dsh, 3 * k + 2) += Y[k] * gcol[2];
+            }
+            if (vnext < 0) break;
+            v = vnext;
+            cur = nxt;
+        }
+    }
+    if (!binned) {
+        // a Gaussian no view binned contributes to no pixel: its gradient is
+        // zero (written as such, also where its parameters are not finite and
+        // the chain below would give 0 x NaN)
+        constexpr int NPL = 3 + (3 * K + 3) / 4;
+#pragma unroll
+        for (int p = 0; p < NPL; ++p) G[(size_t)p * n + i] = zero;
+        return;
+    }
+    const float opacity = 1.0f / (1.0f + expf(-g.logit));
+    const float dlogit = dop * opacity * (1.f - opacity);
+
+    // Sigma = Ms Ms^T, Ms = R diag(s): dMs = 2 dSigma Ms
+    const float* R = g.R;
+    float dls[3], dR[9];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        // column k of Ms is s_k R[:, k]
+        const float c0 = R[0 + k] * g.s[k], c1 = R[3 + k] * g.s[k], c2 = R[6 + k] * g.s[k];
+        const float m0 = 2.f * (dSig[0] * c0 + dSig[1] * c1 + dSig[2] * c2);
+        const float m1 = 2.f * (dSig[1] * c0 + dSig[3] * c1 + dSig[4] * c2);
+        const float m2 = 2.f * (dSig[2] * c0 + dSig[4] * c1 + dSig[5] * c2);
+        dls[k] = (m0 * R[0 + k] + m1 * R[3 + k] + m2 * R[6 + k]) * g.s[k];
+        dR[0 + k] = m0 * g.s[k];
+        dR[3 + k] = m1 * g.s[k];
+        dR[6 + k] = m2 * g.s[k];
+    }
+    const float w = g.qw, x = g.qx, y = g.qy, z = g.qz;
+    float dq[4];
+    dq[0] = 2.f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
+    dq[1] = 2.f * (y * dR[1] + z * dR[2] + y * dR[3] - 2.f * x * dR[4] - w * dR[5] + z * dR[6] + w * dR[7] -
+                   2.f * x * dR[8]);
+    dq[2] = 2.f * (-2.f * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] - w * dR[6] + z * dR[7] -
+                   2.f * y * dR[8]);
+    dq[3] = 2.f * (-2.f * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.f * z * dR[4] + y * dR[5] +
+                   x * dR[6] + y * dR[7]);
+    const float qd = w * dq[0] + x * dq[1] + y * dq[2] + z * dq[3];
+    const float iq = 1.0f / g.qn;
+
+    const float4 g0 = make_float4(dmean[0], dmean[1], dmean[2], dlogit);
+    const float4 g1 = make_float4((dq[0] - w * qd) * iq, (dq[1] - x * qd) * iq, (dq[2] - y * qd) * iq,
+                                  (dq[3] - z * qd) * iq);
+    const float4 g2 = make_float4(dls[0], dls[1], dls[2], 0.f);
+    G[i] = g0;
+    G[(size_t)n + i] = g1;
+    G[2 * (size_t)n + i] = g2;
+    bool finite = finite4(g0) && finite4(g1) && finite4(g2);
+    constexpr int K3 = 3 * K;
+    constexpr int NP = (K3 + 3) / 4;
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-        const float4 q = sh_grad_plane<DEG>(s_dsh, p);
+        float4 q;
+        q.x = (4 * p + 0 < K3) ? dsh_acc(s_dsh, 4 * p + 0) : 0.f;
+        q.y = (4 * p + 1 < K3) ? dsh_acc(s_dsh, 4 * p + 1) : 0.f;
+        q.z = (4 * p + 2 < K3) ? dsh_acc(s_dsh, 4 * p + 2) : 0.f;
+        q.w = (4 * p + 3 < K3) ? dsh_acc(s_dsh, 4 * p + 3) : 0.f;
         G[(size_t)(3 + p) * n + i] = q;
         finite = finite && finite4(q);
     }
     // a non-finite gradient (from a non-finite image, cotangent or 2D
     // gradient upstream) is reported, not hidden: the first such Gaussian sets
     // the status word unless an earlier error already has
-    if (binned && !finite && status) atomicCAS(status, GSFIT_OK, GSFIT_ERR_NONFINITE);
+    if (!finite && status) atomicCAS(status, GSFIT_OK, GSFIT_ERR_NONFINITE);
 }
 
 // Adam over the C planes p0 .. p0 + C - 1 of Gaussian i: every load of the
