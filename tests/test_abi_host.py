@@ -205,3 +205,16 @@ def test_splat_power_selftest_arguments_rejected_on_host(lib):
     assert lib.gsfit_selftest_splat_power(fake, None, 1, fake, None) == G.GSFIT_ERR_INVALID_ARG
     assert lib.gsfit_selftest_splat_power(fake, fake, -1, fake, None) == G.GSFIT_ERR_INVALID_ARG
     assert lib.gsfit_selftest_splat_power(None, None, 0, None, None) == G.GSFIT_OK  # empty: nothing launched
+
+
+def test_fit_stage_lists_name_state_methods():
+    """The timed stage lists (the separate adjoint and Adam, and the fused
+    pass) name FitState methods, which the graph capture and the bench call
+    by name; the default list is the separate kernels'."""
+    from paper_2601_22026_gb300.fit import FitState
+    for stages in (FitState.TIMED_STAGES_SEPARATE, FitState.TIMED_STAGES_FUSED):
+        for name in stages:
+            assert callable(getattr(FitState, name, None)), name
+    assert FitState.TIMED_STAGES == FitState.TIMED_STAGES_SEPARATE
+    assert FitState.TIMED_STAGES_FUSED[-1] == "project_bwd_adam"
+    assert set(FitState.STAGES) - {"render_bwd"} <= set(FitState.TIMED_STAGES_SEPARATE)
